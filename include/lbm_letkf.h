@@ -1,0 +1,139 @@
+/*
+ * lbm_letkf.h -- C ABI of the GB300 (sm_103a) LBM-LETKF library.
+ *
+ * The library runs the forecast-analysis cycle of "Continuous data
+ * assimilation of large eddy simulation by lattice Boltzmann method and
+ * local ensemble transform Kalman filter" (arXiv 2308.03972):
+ *   - an ensemble of D2Q9 lattice-BGK LES members (Section 2) advanced
+ *     together by a fused collide-and-push kernel;
+ *   - the LETKF analysis (Section 3.2) applied to the nine distribution
+ *     functions at every grid point, with Gaspari-Cohn R-localisation and
+ *     multiplicative covariance inflation.
+ *
+ * Units: lattice units (dx = dt = lattice speed = 1, c_s^2 = 1/3).
+ *
+ * Layouts (row-major, member index innermost, all FP64 at this boundary):
+ *   f      [9][ny][nx][members]  distribution functions; alpha = 0 rest,
+ *                                1 (+x), 2 (-x), 3 (+y), 4 (-y),
+ *                                5 (+x,+y), 6 (-x,-y), 7 (+x,-y), 8 (-x,+y)
+ *   force  [2][ny][nx]           large-scale acceleration F^i (x, then y)
+ *   rho, u, v [ny][nx][members]  macroscopic moments
+ * The state held between calls is the pre-collision f (the paper's
+ * f_alpha(xi, t)); a step collides it and pushes f*_alpha to xi + c_alpha
+ * with periodic wrap.
+ *
+ * Ownership: the context owns every device buffer it allocates. Pointers
+ * passed in are borrowed for the duration of the call only. Pointer kinds:
+ * LBM_PTR_HOST (ordinary host memory) or LBM_PTR_DEVICE (CUDA device memory
+ * of the current device).
+ *
+ * Streams and errors: all device work is queued on the stream given in the
+ * config (NULL = the legacy default stream). Calls return an lbm_status; no
+ * C++ exception crosses this boundary. Invalid arguments are reported at
+ * once (LBM_EINVAL). Conditions found on the device (non-finite or
+ * supersonic state, eigensolver without convergence, local problem larger
+ * than the kernel supports) are recorded in a device flag word and reported
+ * by the next call that synchronises (lbm_sync, lbm_moments and lbm_get_f
+ * with host pointers). lbm_last_error gives a message for the last failure.
+ *
+ * Threading: a context may be used by one host thread at a time.
+ */
+#ifndef LBM_LETKF_H
+#define LBM_LETKF_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_EINVAL = 1,    /* bad argument, or local problem too large */
+    LBM_ENOMEM = 2,    /* device allocation failed */
+    LBM_ECUDA = 3,     /* CUDA runtime error (launch or copy) */
+    LBM_EDIVERGED = 4, /* non-finite density/velocity or |u| > 0.5 seen */
+    LBM_ENOCONV = 5    /* eigensolver hit its sweep cap at some point */
+} lbm_status;
+
+typedef enum {
+    LBM_FP64 = 0,  /* everything in binary64 */
+    LBM_MIXED = 1  /* f stored and collided in binary32 as f - w_alpha;
+                      LETKF eigensolve in binary64, products in binary32 */
+} lbm_precision;
+
+typedef enum { LBM_PTR_HOST = 0, LBM_PTR_DEVICE = 1 } lbm_ptr_kind;
+
+typedef struct {
+    int nx, ny;      /* periodic lattice, nx, ny >= 1 */
+    int members;     /* ensemble size k >= 1 (k >= 2 for letkf_analyze) */
+    double tau0;     /* molecular relaxation time, nu = (tau0 - 1/2)/3; > 0.5 */
+    double cs_smag;  /* Smagorinsky constant C_s (paper: 0.2), >= 0 */
+    double mu;       /* linear friction coefficient, F^mu = -mu u, >= 0 */
+    int precision;   /* lbm_precision */
+    void *stream;    /* cudaStream_t to queue work on; NULL = default stream */
+} lbm_config;
+
+/* Create a context: allocate the double-buffered ensemble state and copy the
+ * initial f0 and the forcing field (Section 2; forcing Section 4.1).
+ * f0 may be NULL (state set to the rest equilibrium rho = 1, u = 0);
+ * force may be NULL (no large-scale forcing). *out receives the context or
+ * NULL on failure. */
+int lbm_init(const lbm_config *cfg, const double *f0, const double *force,
+             int ptr_kind, lbm_ctx **out);
+
+/* Set every member to the equilibrium f^eq(rho, u, v) (Section 2, f^eq).
+ * rho may be NULL (rho = 1). Arrays [ny][nx][members]. */
+int lbm_set_equilibrium(lbm_ctx *ctx, const double *rho, const double *u,
+                        const double *v, int ptr_kind);
+
+/* Advance all members nsteps lattice steps (Section 2, lattice Boltzmann
+ * equation with Smagorinsky eddy viscosity and F = F^i - mu u). Asynchronous
+ * on the context stream. nsteps >= 0. */
+int lbm_forecast(lbm_ctx *ctx, int nsteps);
+
+/* Macroscopic moments rho = sum f, u = sum f c / rho (Section 2). Any of the
+ * outputs may be NULL. With LBM_PTR_HOST the call synchronises. */
+int lbm_moments(lbm_ctx *ctx, double *rho, double *u, double *v, int ptr_kind);
+
+/* Observation step (Section 3, y = H x; Section 3.2, ybar and dY): record
+ * npts observation points (ix[j], iy[j]) with observed velocities
+ * (yo_u[j], yo_v[j]) and error standard deviations sigma_u, sigma_v, apply
+ * H to every forecast member, and form dY = Y - ybar and d = y^o - ybar on
+ * the device. Host pointers; npts >= 1; 0 <= ix < nx, 0 <= iy < ny;
+ * sigma > 0. The observation vector orders scalars as (u_0, v_0, u_1, ...). */
+int letkf_observe(lbm_ctx *ctx, int npts, const int *ix, const int *iy,
+                  const double *yo_u, const double *yo_v, double sigma_u,
+                  double sigma_v);
+
+/* LETKF analysis of the nine f_alpha at every grid point, in place
+ * (Section 3.2: w-bar, P-tilde, delta-W = [(k-1) P-tilde]^{1/2} symmetric,
+ * x^a_m = xbar + dX (w-bar + delta-W_m); R-localisation with the
+ * Gaspari-Cohn weight G(r / d_cut), r the periodic distance, support
+ * r < 2 d_cut; inflation P^f -> beta P^f). Uses the observations of the
+ * last letkf_observe call, which it consumes. d_cut > 0, beta > 0,
+ * members >= 2. Asynchronous. */
+int letkf_analyze(lbm_ctx *ctx, double d_cut, double beta);
+
+/* Copy the state out (checkpoint, parity) or in (restart, fault tests).
+ * Layout f [9][ny][nx][members] FP64. lbm_get_f with LBM_PTR_HOST
+ * synchronises. */
+int lbm_get_f(lbm_ctx *ctx, double *f, int ptr_kind);
+int lbm_set_f(lbm_ctx *ctx, const double *f, int ptr_kind);
+
+/* Wait for the context stream and report deferred device conditions
+ * (LBM_EDIVERGED, LBM_ENOCONV, LBM_EINVAL for an oversized local problem).
+ * The flag word is cleared after it is reported. */
+int lbm_sync(lbm_ctx *ctx);
+
+/* Message for the last failure on ctx (or of the last failed lbm_init on
+ * this thread when ctx is NULL). Never NULL. */
+const char *lbm_last_error(const lbm_ctx *ctx);
+
+/* Free the context and its device buffers (synchronises its stream). */
+void lbm_destroy(lbm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_LETKF_H */

@@ -1,0 +1,269 @@
+"""ctypes binding of the C ABI in ``include/lbm_letkf.h``.
+
+Argument marshalling only: every step of the cycle runs in the CUDA library.
+Functions keep the C names. Array arguments may be numpy arrays (host memory,
+float64/int32, C-contiguous) or torch CUDA tensors (device memory, float64,
+contiguous); the pointer kind is inferred. A nonzero status raises
+``LbmError`` carrying the status code and the library's message.
+
+The library must have been built (``python -m paper_2308_03972_gb300.build``
+or ``__graft_entry__.build()``); there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EDIVERGED, LBM_ENOCONV = range(6)
+LBM_FP64, LBM_MIXED = 0, 1
+LBM_PTR_HOST, LBM_PTR_DEVICE = 0, 1
+
+STATUS_NAMES = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA",
+                4: "LBM_EDIVERGED", 5: "LBM_ENOCONV"}
+
+# Every entry point the header declares, with its ctypes signature.
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+
+
+class lbm_config(ctypes.Structure):
+    _fields_ = [("nx", _I), ("ny", _I), ("members", _I), ("tau0", _D), ("cs_smag", _D),
+                ("mu", _D), ("precision", _I), ("stream", _P)]
+
+
+SIGNATURES = {
+    "lbm_init": (_I, [ctypes.POINTER(lbm_config), _P, _P, _I, ctypes.POINTER(_P)]),
+    "lbm_set_equilibrium": (_I, [_P, _P, _P, _P, _I]),
+    "lbm_forecast": (_I, [_P, _I]),
+    "lbm_moments": (_I, [_P, _P, _P, _P, _I]),
+    "letkf_observe": (_I, [_P, _I, _P, _P, _P, _P, _D, _D]),
+    "letkf_analyze": (_I, [_P, _D, _D]),
+    "lbm_get_f": (_I, [_P, _P, _I]),
+    "lbm_set_f": (_I, [_P, _P, _I]),
+    "lbm_sync": (_I, [_P]),
+    "lbm_last_error": (ctypes.c_char_p, [_P]),
+    "lbm_destroy": (None, [_P]),
+}
+
+
+class LbmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(code, str(code)), msg))
+        self.code = code
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load the CUDA library; raise if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError("CUDA library %s is missing: build it with "
+                           "`python -m paper_2308_03972_gb300.build`" % path)
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def _arr(a, dtype=np.float64, writable=False):
+    """Return (pointer, ptr_kind, keepalive) for a numpy array or torch tensor."""
+    if a is None:
+        return None, LBM_PTR_HOST, None
+    if _is_torch(a):
+        import torch
+        want = torch.float64 if dtype == np.float64 else torch.int32
+        if a.dtype != want or not a.is_contiguous():
+            raise TypeError("tensor must be contiguous %s" % want)
+        kind = LBM_PTR_DEVICE if a.is_cuda else LBM_PTR_HOST
+        return ctypes.c_void_p(a.data_ptr()), kind, a
+    if not isinstance(a, np.ndarray) or a.dtype != dtype or not a.flags.c_contiguous:
+        if writable:
+            raise TypeError("output must be a C-contiguous %s numpy array or tensor" % np.dtype(dtype))
+        a = np.ascontiguousarray(a, dtype=dtype)
+    if writable and not a.flags.writeable:
+        raise TypeError("output array is read-only")
+    return a.ctypes.data_as(ctypes.c_void_p), LBM_PTR_HOST, a
+
+
+def _kind(*kinds):
+    ks = {k for k in kinds if k is not None}
+    if len(ks) > 1:
+        raise TypeError("mix of host and device arrays in one call")
+    return ks.pop() if ks else LBM_PTR_HOST
+
+
+def _check(ctx, status):
+    if status != LBM_OK:
+        msg = load().lbm_last_error(ctx)
+        raise LbmError(status, msg.decode() if msg else "")
+
+
+def default_stream():
+    """The current torch CUDA stream handle, or None (legacy default stream)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return None
+
+
+def lbm_init(nx, ny, members, tau0, cs_smag, mu, precision=LBM_FP64, f0=None, force=None,
+             stream="current"):
+    """Create a context; returns its handle (a ctypes void pointer)."""
+    lib = load()
+    if stream == "current":
+        stream = default_stream()
+    cfg = lbm_config(int(nx), int(ny), int(members), float(tau0), float(cs_smag), float(mu),
+                     int(precision), ctypes.c_void_p(stream) if stream else None)
+    pf, kf, _a = _arr(f0)
+    pg, kg, _b = _arr(force)
+    kind = _kind(kf if f0 is not None else None, kg if force is not None else None)
+    out = ctypes.c_void_p()
+    st = lib.lbm_init(ctypes.byref(cfg), pf, pg, kind, ctypes.byref(out))
+    _check(None, st)
+    return out
+
+
+def lbm_set_equilibrium(ctx, rho, u, v):
+    pr, kr, _a = _arr(rho)
+    pu, ku, _b = _arr(u)
+    pv, kv, _c = _arr(v)
+    kind = _kind(kr if rho is not None else None, ku, kv)
+    _check(ctx, load().lbm_set_equilibrium(ctx, pr, pu, pv, kind))
+
+
+def lbm_forecast(ctx, nsteps):
+    _check(ctx, load().lbm_forecast(ctx, int(nsteps)))
+
+
+def lbm_moments(ctx, rho=None, u=None, v=None):
+    """Fill the given output arrays [ny][nx][members] (numpy or CUDA tensors)."""
+    pr, kr, _a = _arr(rho, writable=True)
+    pu, ku, _b = _arr(u, writable=True)
+    pv, kv, _c = _arr(v, writable=True)
+    kind = _kind(*(k for a, k in ((rho, kr), (u, ku), (v, kv)) if a is not None))
+    _check(ctx, load().lbm_moments(ctx, pr, pu, pv, kind))
+
+
+def letkf_observe(ctx, ix, iy, yo_u, yo_v, sigma_u, sigma_v):
+    ix = np.ascontiguousarray(ix, dtype=np.int32)
+    iy = np.ascontiguousarray(iy, dtype=np.int32)
+    yo_u = np.ascontiguousarray(yo_u, dtype=np.float64)
+    yo_v = np.ascontiguousarray(yo_v, dtype=np.float64)
+    n = len(ix)
+    if not (len(iy) == len(yo_u) == len(yo_v) == n):
+        raise ValueError("observation arrays differ in length")
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    _check(ctx, load().letkf_observe(ctx, n, p(ix), p(iy), p(yo_u), p(yo_v), float(sigma_u),
+                                     float(sigma_v)))
+
+
+def letkf_analyze(ctx, d_cut, beta):
+    _check(ctx, load().letkf_analyze(ctx, float(d_cut), float(beta)))
+
+
+def lbm_get_f(ctx, out):
+    po, ko, _a = _arr(out, writable=True)
+    _check(ctx, load().lbm_get_f(ctx, po, ko))
+    return out
+
+
+def lbm_set_f(ctx, f):
+    pf, kf, _a = _arr(f)
+    _check(ctx, load().lbm_set_f(ctx, pf, kf))
+
+
+def lbm_sync(ctx):
+    _check(ctx, load().lbm_sync(ctx))
+
+
+def lbm_last_error(ctx) -> str:
+    msg = load().lbm_last_error(ctx)
+    return msg.decode() if msg else ""
+
+
+def lbm_destroy(ctx):
+    if ctx:
+        load().lbm_destroy(ctx)
+
+
+class Ensemble:
+    """Owns one context: the C ABI calls as methods, destroyed on close()."""
+
+    def __init__(self, nx, ny, members, tau0=0.55, cs_smag=0.2, mu=0.0, precision=LBM_FP64,
+                 f0=None, force=None, stream="current"):
+        self.nx, self.ny, self.members = int(nx), int(ny), int(members)
+        self.precision = precision
+        self.ctx = lbm_init(nx, ny, members, tau0, cs_smag, mu, precision, f0, force, stream)
+
+    def set_equilibrium(self, rho, u, v):
+        lbm_set_equilibrium(self.ctx, rho, u, v)
+
+    def forecast(self, nsteps):
+        lbm_forecast(self.ctx, nsteps)
+
+    def moments(self, rho=None, u=None, v=None):
+        lbm_moments(self.ctx, rho, u, v)
+
+    def moments_host(self):
+        shape = (self.ny, self.nx, self.members)
+        rho, u, v = np.empty(shape), np.empty(shape), np.empty(shape)
+        lbm_moments(self.ctx, rho, u, v)
+        return rho, u, v
+
+    def observe(self, ix, iy, yo_u, yo_v, sigma_u, sigma_v):
+        letkf_observe(self.ctx, ix, iy, yo_u, yo_v, sigma_u, sigma_v)
+
+    def analyze(self, d_cut, beta):
+        letkf_analyze(self.ctx, d_cut, beta)
+
+    def get_f(self, out=None):
+        if out is None:
+            out = np.empty((9, self.ny, self.nx, self.members))
+        return lbm_get_f(self.ctx, out)
+
+    def set_f(self, f):
+        lbm_set_f(self.ctx, f)
+
+    def sync(self):
+        lbm_sync(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            lbm_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

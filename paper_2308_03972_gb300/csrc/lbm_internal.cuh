@@ -1,0 +1,73 @@
+// Internal declarations shared by the CUDA translation units of the
+// LBM-LETKF library. Not part of the C ABI.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lbmgpu {
+
+// Bits of the device flag word (reported by lbm_sync).
+enum : int {
+    FLAG_DIVERGED = 1,  // non-finite or |u| above the limit
+    FLAG_NOCONV = 2,    // eigensolver sweep cap reached
+    FLAG_TOOLARGE = 4   // local problem larger than the analysis kernel holds
+};
+
+// Speed limit used by the divergence check: |u| > 0.5 lattice units.
+constexpr double kUMax2 = 0.25;
+
+// D2Q9 set (arXiv 2308.03972, Section 2): rest, +-x, +-y, four diagonals.
+__host__ __device__ constexpr int d2q9_cx(int a) {
+    return a == 1 || a == 5 || a == 7 ? 1 : (a == 2 || a == 6 || a == 8 ? -1 : 0);
+}
+__host__ __device__ constexpr int d2q9_cy(int a) {
+    return a == 3 || a == 5 || a == 8 ? 1 : (a == 4 || a == 6 || a == 7 ? -1 : 0);
+}
+__host__ __device__ constexpr double d2q9_w(int a) {
+    return a == 0 ? 4.0 / 9.0 : (a < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+}
+
+struct LbmParams {
+    int nx, ny, k;
+    double tau0;
+    double cs18;  // 18 C_s^2 Delta^2 with Delta = 1
+    double mu;
+};
+
+struct ObsParams {
+    int npts;          // observation points
+    const int* ix;     // [npts]
+    const int* iy;     // [npts]
+    const double* dY;  // [2 npts][k] perturbations of H(x_m)
+    const double* d;   // [2 npts] innovations y^o - ybar
+    const double* G;   // [2 npts][2 npts] dY dY^T
+    double sigma_u, sigma_v;
+};
+
+// ---- lbm_kernels.cu -------------------------------------------------------
+// One fused collide+push step. FP64: f stored as is. FP32: f stored as
+// g = f - w_alpha (rest-state shift) in binary32.
+cudaError_t launch_lbm_step_f64(const double* fin, double* fout, const double* force,
+                                const LbmParams& p, int* flags, cudaStream_t s);
+cudaError_t launch_lbm_step_f32(const float* gin, float* gout, const float* force,
+                                const LbmParams& p, int* flags, cudaStream_t s);
+cudaError_t launch_moments(const void* f, int fp32, int nx, int ny, int k, double* rho,
+                           double* u, double* v, int* flags, cudaStream_t s);
+cudaError_t launch_set_equilibrium(void* f, int fp32, int nx, int ny, int k,
+                                   const double* rho, const double* u, const double* v,
+                                   cudaStream_t s);
+cudaError_t launch_store_f(void* f, int fp32, const double* src, size_t n, cudaStream_t s);
+cudaError_t launch_load_f(const void* f, int fp32, double* dst, size_t n, cudaStream_t s);
+cudaError_t launch_store_force(void* dst, int fp32, const double* src, size_t n,
+                               cudaStream_t s);
+
+// ---- letkf_kernels.cu -----------------------------------------------------
+cudaError_t launch_observe(const void* f, int fp32, int nx, int ny, int k, int npts,
+                           const int* ix, const int* iy, const double* yo, double* dY,
+                           double* d, cudaStream_t s);
+cudaError_t launch_obs_gram(const double* dY, int nobs, int k, double* G, cudaStream_t s);
+cudaError_t launch_analyze(void* f, int fp32, int nx, int ny, int k, const ObsParams& o,
+                           double d_cut, double beta, int* flags, cudaStream_t s);
+
+}  // namespace lbmgpu

@@ -1,0 +1,334 @@
+// Lattice-Boltzmann kernels of the LBM-LETKF library (sm_103a).
+//
+// K1 fused collide+push step (arXiv 2308.03972, Section 2: lattice BGK
+// equation, moments, second-order equilibrium, Smagorinsky eddy viscosity,
+// forcing term; Section 4.1: F = F^i - mu u), the moments kernel, and the
+// layout conversions at the C-ABI boundary.
+//
+// Layout: f[alpha][y][x][m], member index innermost. A thread owns V
+// consecutive members of one cell, so the nine loads and the nine pushed
+// stores of a warp are contiguous 16-byte vectors; a shift by one cell is a
+// shift by k elements and keeps that alignment.
+//
+// Precision: FP64 stores f itself. FP32 stores g = f - w_alpha (the rest
+// state at rho = 1 removed) so binary32 keeps the small departures from rest
+// that carry the flow; the collision is written in terms of g.
+#include <cmath>
+
+#include "lbm_internal.cuh"
+
+namespace lbmgpu {
+namespace {
+
+template <typename T, int V>
+struct Vec;
+template <>
+struct Vec<double, 1> {
+    static __device__ __forceinline__ void ld(const double* p, double (&v)[1]) { v[0] = __ldg(p); }
+    static __device__ __forceinline__ void st(double* p, const double (&v)[1]) { p[0] = v[0]; }
+};
+template <>
+struct Vec<double, 2> {
+    static __device__ __forceinline__ void ld(const double* p, double (&v)[2]) {
+        double2 t = __ldg(reinterpret_cast<const double2*>(p));
+        v[0] = t.x;
+        v[1] = t.y;
+    }
+    static __device__ __forceinline__ void st(double* p, const double (&v)[2]) {
+        *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+    }
+};
+template <>
+struct Vec<float, 1> {
+    static __device__ __forceinline__ void ld(const float* p, float (&v)[1]) { v[0] = __ldg(p); }
+    static __device__ __forceinline__ void st(float* p, const float (&v)[1]) { p[0] = v[0]; }
+};
+template <>
+struct Vec<float, 2> {
+    static __device__ __forceinline__ void ld(const float* p, float (&v)[2]) {
+        float2 t = __ldg(reinterpret_cast<const float2*>(p));
+        v[0] = t.x;
+        v[1] = t.y;
+    }
+    static __device__ __forceinline__ void st(float* p, const float (&v)[2]) {
+        *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+    }
+};
+template <>
+struct Vec<float, 4> {
+    static __device__ __forceinline__ void ld(const float* p, float (&v)[4]) {
+        float4 t = __ldg(reinterpret_cast<const float4*>(p));
+        v[0] = t.x;
+        v[1] = t.y;
+        v[2] = t.z;
+        v[3] = t.w;
+    }
+    static __device__ __forceinline__ void st(float* p, const float (&v)[4]) {
+        *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+};
+
+// BGK-LES collision of one member at one cell, in place on f[9].
+// SHIFT: f holds g = f - w_alpha. Returns true if the state is bad
+// (non-positive or non-finite density, or |u|^2 above the limit).
+template <typename T, bool SHIFT>
+__device__ __forceinline__ bool collide(T (&f)[9], T Fix, T Fiy, T tau0, T cs18, T mu) {
+    // Density and momentum. With SHIFT the sum is rho - 1 (sum w = 1) and
+    // the momentum is unchanged (sum w c = 0).
+    const T s = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+    const T rho = SHIFT ? T(1) + s : s;
+    const T jx = (f[1] - f[2]) + (f[5] - f[6]) + (f[7] - f[8]);
+    const T jy = (f[3] - f[4]) + (f[5] - f[6]) + (f[8] - f[7]);
+    const T ir = T(1) / rho;
+    const T ux = jx * ir, uy = jy * ir;
+    const T uu = ux * ux + uy * uy;
+    // f^eq_a (or f^eq_a - w_a) = w_a (A + rho e_a), e_a = 3 c.u + 9/2 (c.u)^2,
+    // A = rho (1 - 3/2 u.u) (or rho - 1 - 3/2 rho u.u).
+    const T A = s - T(1.5) * rho * uu;
+    T fneq[9];
+    {
+        fneq[0] = f[0] - T(4.0 / 9.0) * A;
+        const T cu[4] = {ux, uy, ux + uy, ux - uy};
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            const T q = T(4.5) * cu[p] * cu[p];
+            const T l = T(3) * cu[p];
+            const T w = p < 2 ? T(1.0 / 9.0) : T(1.0 / 36.0);
+            const int ap = p < 2 ? 1 + 2 * p : 5 + 2 * (p - 2);  // +c direction
+            fneq[ap] = f[ap] - w * (A + rho * (q + l));
+            fneq[ap + 1] = f[ap + 1] - w * (A + rho * (q - l));
+        }
+    }
+    // Non-equilibrium momentum flux and the Smagorinsky relaxation time
+    // tau = (tau0 + sqrt(tau0^2 + 18 Cs^2 Q / rho)) / 2, Q = sqrt(2 Pi:Pi).
+    const T d58 = (fneq[5] + fneq[6]) + (fneq[7] + fneq[8]);
+    const T pxx = (fneq[1] + fneq[2]) + d58;
+    const T pyy = (fneq[3] + fneq[4]) + d58;
+    const T pxy = (fneq[5] + fneq[6]) - (fneq[7] + fneq[8]);
+    const T Q = sqrt(T(2) * (pxx * pxx + T(2) * pxy * pxy + pyy * pyy));
+    const T tau = T(0.5) * (tau0 + sqrt(tau0 * tau0 + cs18 * Q * ir));
+    const T om = T(1) / tau;
+    // Forcing F_a = 3 w_a rho F.c_a with F = F^i - mu u.
+    const T Fx = Fix - mu * ux, Fy = Fiy - mu * uy;
+    const T fx3 = rho * Fx * T(1.0 / 3.0);
+    const T fy3 = rho * Fy * T(1.0 / 3.0);
+    const T dp = rho * (Fx + Fy) * T(1.0 / 12.0);
+    const T dm = rho * (Fx - Fy) * T(1.0 / 12.0);
+    f[0] = f[0] - om * fneq[0];
+    f[1] = f[1] - om * fneq[1] + fx3;
+    f[2] = f[2] - om * fneq[2] - fx3;
+    f[3] = f[3] - om * fneq[3] + fy3;
+    f[4] = f[4] - om * fneq[4] - fy3;
+    f[5] = f[5] - om * fneq[5] + dp;
+    f[6] = f[6] - om * fneq[6] - dp;
+    f[7] = f[7] - om * fneq[7] + dm;
+    f[8] = f[8] - om * fneq[8] - dm;
+    return !(uu <= T(kUMax2)) || !(rho > T(0));
+}
+
+template <typename T, int V, bool SHIFT>
+__global__ void __launch_bounds__(256) lbm_step_kernel(const T* __restrict__ fin,
+                                                       T* __restrict__ fout,
+                                                       const T* __restrict__ force, int nx,
+                                                       int ny, int k, T tau0, T cs18, T mu,
+                                                       int* __restrict__ flags) {
+    const int kv = k / V;
+    const long long total = (long long)nx * ny * kv;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    const int mv = (int)(t % kv);
+    const long long cell = t / kv;
+    const int x = (int)(cell % nx);
+    const int y = (int)(cell / nx);
+    const size_t plane = (size_t)nx * ny * k;  // elements per alpha
+    const size_t src = (size_t)cell * k + (size_t)mv * V;
+
+    T f[9][V];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) Vec<T, V>::ld(fin + a * plane + src, f[a]);
+    const T Fix = __ldg(force + cell);
+    const T Fiy = __ldg(force + (size_t)nx * ny + cell);
+
+    bool bad = false;
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+        T g[9];
+#pragma unroll
+        for (int a = 0; a < 9; ++a) g[a] = f[a][j];
+        bad |= collide<T, SHIFT>(g, Fix, Fiy, tau0, cs18, mu);
+#pragma unroll
+        for (int a = 0; a < 9; ++a) f[a][j] = g[a];
+    }
+    if (bad) atomicOr(flags, FLAG_DIVERGED);
+
+    // Push f*_a to xi + c_a with periodic wrap.
+    const int xp = (x + 1 == nx) ? 0 : x + 1, xm = (x == 0) ? nx - 1 : x - 1;
+    const int yp = (y + 1 == ny) ? 0 : y + 1, ym = (y == 0) ? ny - 1 : y - 1;
+    const size_t mo = (size_t)mv * V;
+    auto dst = [&](int a, int xx, int yy) {
+        return fout + a * plane + ((size_t)yy * nx + xx) * k + mo;
+    };
+    Vec<T, V>::st(dst(0, x, y), f[0]);
+    Vec<T, V>::st(dst(1, xp, y), f[1]);
+    Vec<T, V>::st(dst(2, xm, y), f[2]);
+    Vec<T, V>::st(dst(3, x, yp), f[3]);
+    Vec<T, V>::st(dst(4, x, ym), f[4]);
+    Vec<T, V>::st(dst(5, xp, yp), f[5]);
+    Vec<T, V>::st(dst(6, xm, ym), f[6]);
+    Vec<T, V>::st(dst(7, xp, ym), f[7]);
+    Vec<T, V>::st(dst(8, xm, yp), f[8]);
+}
+
+template <typename T, int V, bool SHIFT>
+cudaError_t launch_step_v(const T* fin, T* fout, const T* force, const LbmParams& p, int* flags,
+                          cudaStream_t s) {
+    const long long total = (long long)p.nx * p.ny * (p.k / V);
+    const int bs = 256;
+    const long long nb = (total + bs - 1) / bs;
+    if (nb > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    lbm_step_kernel<T, V, SHIFT><<<(unsigned)nb, bs, 0, s>>>(fin, fout, force, p.nx, p.ny, p.k,
+                                                             (T)p.tau0, (T)p.cs18, (T)p.mu, flags);
+    return cudaGetLastError();
+}
+
+// Moments from the stored state: rho = sum f, u = sum f c / rho, in FP64.
+template <typename T, bool SHIFT>
+__global__ void moments_kernel(const T* __restrict__ f, int nx, int ny, int k,
+                               double* __restrict__ rho, double* __restrict__ u,
+                               double* __restrict__ v, int* __restrict__ flags) {
+    const size_t n = (size_t)nx * ny * k;
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double g[9];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) g[a] = (double)f[a * n + i];
+    double r = 0.0, jx = 0.0, jy = 0.0;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+        r += g[a];
+        jx += d2q9_cx(a) * g[a];
+        jy += d2q9_cy(a) * g[a];
+    }
+    if (SHIFT) r += 1.0;
+    const double ux = jx / r, uy = jy / r;
+    if (rho) rho[i] = r;
+    if (u) u[i] = ux;
+    if (v) v[i] = uy;
+    if (!(ux * ux + uy * uy <= kUMax2) || !(r > 0.0)) atomicOr(flags, FLAG_DIVERGED);
+}
+
+template <typename T, bool SHIFT>
+__global__ void equilibrium_kernel(T* __restrict__ f, size_t n, const double* __restrict__ rho,
+                                   const double* __restrict__ u, const double* __restrict__ v) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double r = rho ? rho[i] : 1.0;
+    const double ux = u ? u[i] : 0.0, uy = v ? v[i] : 0.0;
+    const double uu = ux * ux + uy * uy;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+        const double cu = d2q9_cx(a) * ux + d2q9_cy(a) * uy;
+        const double w = d2q9_w(a);
+        // f^eq - w = w ((rho - 1) + rho (3 cu + 9/2 cu^2 - 3/2 uu)).
+        const double dev = w * ((r - 1.0) + r * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu));
+        f[a * n + i] = SHIFT ? (T)dev : (T)(w + dev);
+    }
+}
+
+// FP64 f [9][ny][nx][k] <-> stored representation (plane = ny nx k).
+template <typename T, bool SHIFT>
+__global__ void store_f_kernel(T* __restrict__ dst, const double* __restrict__ src, size_t n,
+                               size_t plane) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int a = (int)(i / plane);
+    dst[i] = SHIFT ? (T)(src[i] - d2q9_w(a)) : (T)src[i];
+}
+
+template <typename T, bool SHIFT>
+__global__ void load_f_kernel(double* __restrict__ dst, const T* __restrict__ src, size_t n,
+                              size_t plane) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int a = (int)(i / plane);
+    dst[i] = SHIFT ? (double)src[i] + d2q9_w(a) : (double)src[i];
+}
+
+__global__ void store_force_f32(float* __restrict__ dst, const double* __restrict__ src, size_t n) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = (float)src[i];
+}
+
+inline unsigned blocks_for(size_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+}  // namespace
+
+cudaError_t launch_lbm_step_f64(const double* fin, double* fout, const double* force,
+                                const LbmParams& p, int* flags, cudaStream_t s) {
+    if (p.k % 2 == 0) return launch_step_v<double, 2, false>(fin, fout, force, p, flags, s);
+    return launch_step_v<double, 1, false>(fin, fout, force, p, flags, s);
+}
+
+cudaError_t launch_lbm_step_f32(const float* gin, float* gout, const float* force,
+                                const LbmParams& p, int* flags, cudaStream_t s) {
+    if (p.k % 4 == 0) return launch_step_v<float, 4, true>(gin, gout, force, p, flags, s);
+    if (p.k % 2 == 0) return launch_step_v<float, 2, true>(gin, gout, force, p, flags, s);
+    return launch_step_v<float, 1, true>(gin, gout, force, p, flags, s);
+}
+
+cudaError_t launch_moments(const void* f, int fp32, int nx, int ny, int k, double* rho,
+                           double* u, double* v, int* flags, cudaStream_t s) {
+    const size_t n = (size_t)nx * ny * k;
+    if (n == 0) return cudaSuccess;
+    if (fp32)
+        moments_kernel<float, true><<<blocks_for(n, 256), 256, 0, s>>>(
+            (const float*)f, nx, ny, k, rho, u, v, flags);
+    else
+        moments_kernel<double, false><<<blocks_for(n, 256), 256, 0, s>>>(
+            (const double*)f, nx, ny, k, rho, u, v, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_equilibrium(void* f, int fp32, int nx, int ny, int k, const double* rho,
+                                   const double* u, const double* v, cudaStream_t s) {
+    const size_t n = (size_t)nx * ny * k;
+    if (n == 0) return cudaSuccess;
+    if (fp32)
+        equilibrium_kernel<float, true><<<blocks_for(n, 256), 256, 0, s>>>((float*)f, n, rho, u, v);
+    else
+        equilibrium_kernel<double, false><<<blocks_for(n, 256), 256, 0, s>>>((double*)f, n, rho, u,
+                                                                            v);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_store_f(void* f, int fp32, const double* src, size_t n, cudaStream_t s) {
+    const size_t plane = n / 9;
+    if (n == 0) return cudaSuccess;
+    if (fp32)
+        store_f_kernel<float, true><<<blocks_for(n, 256), 256, 0, s>>>((float*)f, src, n, plane);
+    else
+        store_f_kernel<double, false><<<blocks_for(n, 256), 256, 0, s>>>((double*)f, src, n, plane);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_load_f(const void* f, int fp32, double* dst, size_t n, cudaStream_t s) {
+    const size_t plane = n / 9;
+    if (n == 0) return cudaSuccess;
+    if (fp32)
+        load_f_kernel<float, true><<<blocks_for(n, 256), 256, 0, s>>>(dst, (const float*)f, n, plane);
+    else
+        load_f_kernel<double, false><<<blocks_for(n, 256), 256, 0, s>>>(dst, (const double*)f, n,
+                                                                       plane);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_store_force(void* dst, int fp32, const double* src, size_t n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    if (fp32) {
+        store_force_f32<<<blocks_for(n, 256), 256, 0, s>>>((float*)dst, src, n);
+        return cudaGetLastError();
+    }
+    return cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+}
+
+}  // namespace lbmgpu

@@ -1,0 +1,401 @@
+// C ABI of the LBM-LETKF library: context management, argument checks,
+// host/device marshalling and kernel launches. See include/lbm_letkf.h.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/lbm_letkf.h"
+#include "lbm_internal.cuh"
+
+using namespace lbmgpu;
+
+struct lbm_ctx {
+    int nx = 0, ny = 0, k = 0, precision = LBM_FP64;
+    double tau0 = 0.0, cs = 0.0, mu = 0.0;
+    cudaStream_t stream = nullptr;
+    void* f[2] = {nullptr, nullptr};  // double-buffered state (double or float)
+    int cur = 0;
+    void* force = nullptr;           // [2][ny][nx] in the state's type
+    int* flags = nullptr;            // device flag word
+    double* stage = nullptr;         // FP64 staging [9][ny][nx][k] (lazy)
+    // observations
+    int npts = 0, obs_cap = 0;
+    int* ix = nullptr;
+    int* iy = nullptr;
+    double* yo = nullptr;  // [2 npts] interleaved (u, v)
+    double* dY = nullptr;  // [2 npts][k]
+    double* d = nullptr;   // [2 npts]
+    double* G = nullptr;   // [2 npts][2 npts]
+    double sigma_u = 0.0, sigma_v = 0.0;
+    bool observed = false;
+    char err[512] = {0};
+};
+
+namespace {
+
+thread_local char g_init_err[512] = "no error";
+
+int fail(lbm_ctx* c, int code, const char* fmt, ...) {
+    char* buf = c ? c->err : g_init_err;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, 512, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_fail(lbm_ctx* c, cudaError_t e, const char* what) {
+    return fail(c, e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+#define CK(ctx, call, what)                                       \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, what); \
+    } while (0)
+
+size_t elem_size(const lbm_ctx* c) { return c->precision == LBM_MIXED ? sizeof(float) : sizeof(double); }
+size_t state_elems(const lbm_ctx* c) { return (size_t)9 * c->nx * c->ny * c->k; }
+size_t cell_elems(const lbm_ctx* c) { return (size_t)c->nx * c->ny * c->k; }
+int is_fp32(const lbm_ctx* c) { return c->precision == LBM_MIXED; }
+
+bool ptr_kind_ok(int kind) { return kind == LBM_PTR_HOST || kind == LBM_PTR_DEVICE; }
+
+int ensure_stage(lbm_ctx* c) {
+    if (c->stage) return LBM_OK;
+    CK(c, cudaMalloc(&c->stage, state_elems(c) * sizeof(double)), "allocating staging buffer");
+    return LBM_OK;
+}
+
+// Copy n doubles from a host or device pointer into device memory dst.
+int copy_in(lbm_ctx* c, double* dst, const double* src, size_t n, int kind) {
+    CK(c, cudaMemcpyAsync(dst, src, n * sizeof(double),
+                          kind == LBM_PTR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                          c->stream),
+       "copying input");
+    return LBM_OK;
+}
+
+int read_flags(lbm_ctx* c) {
+    int h = 0;
+    CK(c, cudaMemcpyAsync(&h, c->flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream),
+       "reading device flags");
+    CK(c, cudaStreamSynchronize(c->stream), "synchronising stream");
+    if (h == 0) return LBM_OK;
+    CK(c, cudaMemsetAsync(c->flags, 0, sizeof(int), c->stream), "clearing device flags");
+    CK(c, cudaStreamSynchronize(c->stream), "synchronising stream");
+    if (h & FLAG_DIVERGED)
+        return fail(c, LBM_EDIVERGED, "state diverged: non-finite density/velocity or |u| > 0.5");
+    if (h & FLAG_TOOLARGE)
+        return fail(c, LBM_EINVAL, "local analysis problem larger than the kernel supports (n > 32)");
+    return fail(c, LBM_ENOCONV, "eigensolver reached its sweep cap");
+}
+
+void free_obs(lbm_ctx* c) {
+    cudaFree(c->ix);
+    cudaFree(c->iy);
+    cudaFree(c->yo);
+    cudaFree(c->dY);
+    cudaFree(c->d);
+    cudaFree(c->G);
+    c->ix = c->iy = nullptr;
+    c->yo = c->dY = c->d = c->G = nullptr;
+    c->obs_cap = 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_init(const lbm_config* cfg, const double* f0, const double* force, int ptr_kind,
+             lbm_ctx** out) {
+    if (!out) return fail(nullptr, LBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!cfg) return fail(nullptr, LBM_EINVAL, "cfg is NULL");
+    if (cfg->nx < 1 || cfg->ny < 1 || cfg->members < 1)
+        return fail(nullptr, LBM_EINVAL, "nx, ny and members must be >= 1");
+    if (!((size_t)cfg->nx * cfg->ny < (1ull << 31)))
+        return fail(nullptr, LBM_EINVAL, "nx * ny must be below 2^31");
+    if (!(cfg->tau0 > 0.5) || !std::isfinite(cfg->tau0))
+        return fail(nullptr, LBM_EINVAL, "tau0 must be finite and > 0.5");
+    if (!(cfg->cs_smag >= 0.0) || !std::isfinite(cfg->cs_smag))
+        return fail(nullptr, LBM_EINVAL, "cs_smag must be finite and >= 0");
+    if (!(cfg->mu >= 0.0) || !std::isfinite(cfg->mu))
+        return fail(nullptr, LBM_EINVAL, "mu must be finite and >= 0");
+    if (cfg->precision != LBM_FP64 && cfg->precision != LBM_MIXED)
+        return fail(nullptr, LBM_EINVAL, "precision must be LBM_FP64 or LBM_MIXED");
+    if ((f0 || force) && !ptr_kind_ok(ptr_kind))
+        return fail(nullptr, LBM_EINVAL, "ptr_kind must be LBM_PTR_HOST or LBM_PTR_DEVICE");
+
+    lbm_ctx* c = new (std::nothrow) lbm_ctx();
+    if (!c) return fail(nullptr, LBM_ENOMEM, "host allocation failed");
+    c->nx = cfg->nx;
+    c->ny = cfg->ny;
+    c->k = cfg->members;
+    c->tau0 = cfg->tau0;
+    c->cs = cfg->cs_smag;
+    c->mu = cfg->mu;
+    c->precision = cfg->precision;
+    c->stream = (cudaStream_t)cfg->stream;
+
+    int st = LBM_OK;
+    auto bail = [&](int code) {
+        snprintf(g_init_err, sizeof g_init_err, "%s", c->err);
+        lbm_destroy(c);
+        return code;
+    };
+    const size_t bytes = state_elems(c) * elem_size(c);
+    for (int b = 0; b < 2; ++b) {
+        cudaError_t e = cudaMalloc(&c->f[b], bytes);
+        if (e != cudaSuccess) return bail(cuda_fail(c, e, "allocating state"));
+    }
+    cudaError_t e = cudaMalloc(&c->force, (size_t)2 * c->nx * c->ny * elem_size(c));
+    if (e != cudaSuccess) return bail(cuda_fail(c, e, "allocating force"));
+    e = cudaMalloc(&c->flags, sizeof(int));
+    if (e != cudaSuccess) return bail(cuda_fail(c, e, "allocating flags"));
+    e = cudaMemsetAsync(c->flags, 0, sizeof(int), c->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(c, e, "clearing flags"));
+
+    // Forcing field.
+    const size_t nf = (size_t)2 * c->nx * c->ny;
+    if (force) {
+        double* tmp = nullptr;
+        e = cudaMalloc(&tmp, nf * sizeof(double));
+        if (e != cudaSuccess) return bail(cuda_fail(c, e, "allocating force staging"));
+        st = copy_in(c, tmp, force, nf, ptr_kind);
+        if (st == LBM_OK) {
+            e = launch_store_force(c->force, is_fp32(c), tmp, nf, c->stream);
+            if (e != cudaSuccess) st = cuda_fail(c, e, "converting force");
+        }
+        cudaError_t e2 = cudaStreamSynchronize(c->stream);
+        cudaFree(tmp);
+        if (st != LBM_OK) return bail(st);
+        if (e2 != cudaSuccess) return bail(cuda_fail(c, e2, "synchronising"));
+    } else {
+        e = cudaMemsetAsync(c->force, 0, nf * elem_size(c), c->stream);
+        if (e != cudaSuccess) return bail(cuda_fail(c, e, "clearing force"));
+    }
+
+    // Initial state.
+    if (f0) {
+        st = lbm_set_f(c, f0, ptr_kind);
+    } else {
+        e = launch_set_equilibrium(c->f[0], is_fp32(c), c->nx, c->ny, c->k, nullptr, nullptr,
+                                   nullptr, c->stream);
+        if (e != cudaSuccess) st = cuda_fail(c, e, "initialising state");
+    }
+    if (st != LBM_OK) return bail(st);
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(c, e, "synchronising"));
+    snprintf(c->err, sizeof c->err, "no error");
+    *out = c;
+    return LBM_OK;
+}
+
+int lbm_set_equilibrium(lbm_ctx* c, const double* rho, const double* u, const double* v,
+                        int ptr_kind) {
+    if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (!ptr_kind_ok(ptr_kind)) return fail(c, LBM_EINVAL, "bad ptr_kind");
+    if (!u || !v) return fail(c, LBM_EINVAL, "u and v are required");
+    const size_t n = cell_elems(c);
+    const double *dr = rho, *du = u, *dv = v;
+    if (ptr_kind == LBM_PTR_HOST) {
+        int st = ensure_stage(c);
+        if (st) return st;
+        double* s = c->stage;
+        if (rho) {
+            if ((st = copy_in(c, s, rho, n, ptr_kind))) return st;
+            dr = s;
+        }
+        if ((st = copy_in(c, s + n, u, n, ptr_kind))) return st;
+        if ((st = copy_in(c, s + 2 * n, v, n, ptr_kind))) return st;
+        du = s + n;
+        dv = s + 2 * n;
+    }
+    CK(c, launch_set_equilibrium(c->f[c->cur], is_fp32(c), c->nx, c->ny, c->k, dr, du, dv,
+                                 c->stream),
+       "launching equilibrium");
+    if (ptr_kind == LBM_PTR_HOST) CK(c, cudaStreamSynchronize(c->stream), "synchronising");
+    c->observed = false;
+    return LBM_OK;
+}
+
+int lbm_forecast(lbm_ctx* c, int nsteps) {
+    if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (nsteps < 0) return fail(c, LBM_EINVAL, "nsteps must be >= 0");
+    LbmParams p{c->nx, c->ny, c->k, c->tau0, 18.0 * c->cs * c->cs, c->mu};
+    for (int s = 0; s < nsteps; ++s) {
+        cudaError_t e;
+        if (is_fp32(c))
+            e = launch_lbm_step_f32((const float*)c->f[c->cur], (float*)c->f[c->cur ^ 1],
+                                    (const float*)c->force, p, c->flags, c->stream);
+        else
+            e = launch_lbm_step_f64((const double*)c->f[c->cur], (double*)c->f[c->cur ^ 1],
+                                    (const double*)c->force, p, c->flags, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "launching LBM step");
+        c->cur ^= 1;
+    }
+    if (nsteps > 0) c->observed = false;
+    return LBM_OK;
+}
+
+int lbm_moments(lbm_ctx* c, double* rho, double* u, double* v, int ptr_kind) {
+    if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (!ptr_kind_ok(ptr_kind)) return fail(c, LBM_EINVAL, "bad ptr_kind");
+    const size_t n = cell_elems(c);
+    if (ptr_kind == LBM_PTR_DEVICE) {
+        CK(c, launch_moments(c->f[c->cur], is_fp32(c), c->nx, c->ny, c->k, rho, u, v, c->flags,
+                             c->stream),
+           "launching moments");
+        return LBM_OK;
+    }
+    int st = ensure_stage(c);
+    if (st) return st;
+    double* s = c->stage;
+    CK(c, launch_moments(c->f[c->cur], is_fp32(c), c->nx, c->ny, c->k, rho ? s : nullptr,
+                         u ? s + n : nullptr, v ? s + 2 * n : nullptr, c->flags, c->stream),
+       "launching moments");
+    if (rho) CK(c, cudaMemcpyAsync(rho, s, n * 8, cudaMemcpyDeviceToHost, c->stream), "copy rho");
+    if (u) CK(c, cudaMemcpyAsync(u, s + n, n * 8, cudaMemcpyDeviceToHost, c->stream), "copy u");
+    if (v) CK(c, cudaMemcpyAsync(v, s + 2 * n, n * 8, cudaMemcpyDeviceToHost, c->stream), "copy v");
+    return read_flags(c);
+}
+
+int letkf_observe(lbm_ctx* c, int npts, const int* ix, const int* iy, const double* yo_u,
+                  const double* yo_v, double sigma_u, double sigma_v) {
+    if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (npts < 1) return fail(c, LBM_EINVAL, "npts must be >= 1");
+    if (!ix || !iy || !yo_u || !yo_v) return fail(c, LBM_EINVAL, "NULL observation array");
+    if (!(sigma_u > 0.0) || !(sigma_v > 0.0) || !std::isfinite(sigma_u) || !std::isfinite(sigma_v))
+        return fail(c, LBM_EINVAL, "sigma_u and sigma_v must be finite and > 0");
+    if ((long long)npts * 2 > 65535) return fail(c, LBM_EINVAL, "too many observation points");
+    for (int j = 0; j < npts; ++j) {
+        if (ix[j] < 0 || ix[j] >= c->nx || iy[j] < 0 || iy[j] >= c->ny)
+            return fail(c, LBM_EINVAL, "observation point %d outside the lattice", j);
+        if (!std::isfinite(yo_u[j]) || !std::isfinite(yo_v[j]))
+            return fail(c, LBM_EINVAL, "observation %d is not finite", j);
+    }
+    if (npts > c->obs_cap) {
+        CK(c, cudaStreamSynchronize(c->stream), "synchronising");
+        free_obs(c);
+        const size_t no = 2 * (size_t)npts;
+        CK(c, cudaMalloc(&c->ix, npts * sizeof(int)), "allocating obs");
+        CK(c, cudaMalloc(&c->iy, npts * sizeof(int)), "allocating obs");
+        CK(c, cudaMalloc(&c->yo, no * sizeof(double)), "allocating obs");
+        CK(c, cudaMalloc(&c->dY, no * c->k * sizeof(double)), "allocating obs");
+        CK(c, cudaMalloc(&c->d, no * sizeof(double)), "allocating obs");
+        CK(c, cudaMalloc(&c->G, no * no * sizeof(double)), "allocating obs");
+        c->obs_cap = npts;
+    }
+    std::vector<double> yo(2 * (size_t)npts);
+    for (int j = 0; j < npts; ++j) {
+        yo[2 * j] = yo_u[j];
+        yo[2 * j + 1] = yo_v[j];
+    }
+    CK(c, cudaMemcpyAsync(c->ix, ix, npts * sizeof(int), cudaMemcpyHostToDevice, c->stream), "copy ix");
+    CK(c, cudaMemcpyAsync(c->iy, iy, npts * sizeof(int), cudaMemcpyHostToDevice, c->stream), "copy iy");
+    CK(c, cudaMemcpyAsync(c->yo, yo.data(), yo.size() * sizeof(double), cudaMemcpyHostToDevice,
+                          c->stream),
+       "copy yo");
+    CK(c, launch_observe(c->f[c->cur], is_fp32(c), c->nx, c->ny, c->k, npts, c->ix, c->iy, c->yo,
+                         c->dY, c->d, c->stream),
+       "launching observation operator");
+    CK(c, launch_obs_gram(c->dY, 2 * npts, c->k, c->G, c->stream), "launching observation Gram");
+    // The host vector must outlive the copy from pageable memory.
+    CK(c, cudaStreamSynchronize(c->stream), "synchronising");
+    c->npts = npts;
+    c->sigma_u = sigma_u;
+    c->sigma_v = sigma_v;
+    c->observed = true;
+    return LBM_OK;
+}
+
+int letkf_analyze(lbm_ctx* c, double d_cut, double beta) {
+    if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (c->k < 2) return fail(c, LBM_EINVAL, "the analysis needs members >= 2");
+    if (!(d_cut > 0.0) || !std::isfinite(d_cut)) return fail(c, LBM_EINVAL, "d_cut must be > 0");
+    if (!(beta > 0.0) || !std::isfinite(beta)) return fail(c, LBM_EINVAL, "beta must be > 0");
+    if (!c->observed) return fail(c, LBM_EINVAL, "letkf_observe must precede letkf_analyze");
+    ObsParams o{c->npts, c->ix, c->iy, c->dY, c->d, c->G, c->sigma_u, c->sigma_v};
+    CK(c, launch_analyze(c->f[c->cur], is_fp32(c), c->nx, c->ny, c->k, o, d_cut, beta, c->flags,
+                         c->stream),
+       "launching analysis");
+    c->observed = false;
+    return LBM_OK;
+}
+
+int lbm_get_f(lbm_ctx* c, double* f, int ptr_kind) {
+    if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (!f) return fail(c, LBM_EINVAL, "f is NULL");
+    if (!ptr_kind_ok(ptr_kind)) return fail(c, LBM_EINVAL, "bad ptr_kind");
+    const size_t n = state_elems(c);
+    if (!is_fp32(c)) {
+        CK(c, cudaMemcpyAsync(f, c->f[c->cur], n * sizeof(double),
+                              ptr_kind == LBM_PTR_HOST ? cudaMemcpyDeviceToHost
+                                                       : cudaMemcpyDeviceToDevice,
+                              c->stream),
+           "copying state out");
+    } else if (ptr_kind == LBM_PTR_DEVICE) {
+        CK(c, launch_load_f(c->f[c->cur], 1, f, n, c->stream), "converting state");
+    } else {
+        int st = ensure_stage(c);
+        if (st) return st;
+        CK(c, launch_load_f(c->f[c->cur], 1, c->stage, n, c->stream), "converting state");
+        CK(c, cudaMemcpyAsync(f, c->stage, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+           "copying state out");
+    }
+    if (ptr_kind == LBM_PTR_HOST) return read_flags(c);
+    return LBM_OK;
+}
+
+int lbm_set_f(lbm_ctx* c, const double* f, int ptr_kind) {
+    if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (!f) return fail(c, LBM_EINVAL, "f is NULL");
+    if (!ptr_kind_ok(ptr_kind)) return fail(c, LBM_EINVAL, "bad ptr_kind");
+    const size_t n = state_elems(c);
+    if (!is_fp32(c)) {
+        CK(c, cudaMemcpyAsync(c->f[c->cur], f, n * sizeof(double),
+                              ptr_kind == LBM_PTR_HOST ? cudaMemcpyHostToDevice
+                                                       : cudaMemcpyDeviceToDevice,
+                              c->stream),
+           "copying state in");
+    } else {
+        const double* src = f;
+        if (ptr_kind == LBM_PTR_HOST) {
+            int st = ensure_stage(c);
+            if (st) return st;
+            if ((st = copy_in(c, c->stage, f, n, ptr_kind))) return st;
+            src = c->stage;
+        }
+        CK(c, launch_store_f(c->f[c->cur], 1, src, n, c->stream), "converting state");
+    }
+    if (ptr_kind == LBM_PTR_HOST) CK(c, cudaStreamSynchronize(c->stream), "synchronising");
+    c->observed = false;
+    return LBM_OK;
+}
+
+int lbm_sync(lbm_ctx* c) {
+    if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    return read_flags(c);
+}
+
+const char* lbm_last_error(const lbm_ctx* c) { return c ? c->err : g_init_err; }
+
+void lbm_destroy(lbm_ctx* c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    cudaFree(c->f[0]);
+    cudaFree(c->f[1]);
+    cudaFree(c->force);
+    cudaFree(c->flags);
+    cudaFree(c->stage);
+    free_obs(c);
+    delete c;
+}
+
+}  // extern "C"

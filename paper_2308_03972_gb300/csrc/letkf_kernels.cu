@@ -1,0 +1,522 @@
+// LETKF kernels of the LBM-LETKF library (sm_103a).
+//
+// K2 observation operator and ensemble observation statistics
+//   (arXiv 2308.03972, Section 3: y = H x = (u, v) at the observation points;
+//    Section 3.2: ybar, dY = Y - ybar, innovation d = y^o - ybar).
+// K3 per-grid-point analysis, one warp per grid point
+//   (Section 3.2: w-bar, P-tilde, delta-W = [(k-1) P-tilde]^{1/2}, the
+//    update x^a_m = xbar + dX (w-bar + delta-W_m); R-localisation with the
+//    Gaspari-Cohn weight; multiplicative inflation beta).
+//
+// The analysis uses whichever of two exactly equivalent forms is smaller.
+// With Yh = diag(sqrt(rho)) dY_loc (p x k), C = a I + Yh^T Yh, a = (k-1)/beta:
+//  * ensemble space (p >= k): eigendecompose the k x k matrix C as printed;
+//  * observation space (p < k): eigendecompose the p x p matrix
+//    A = Yh Yh^T = U S U^T. Then w-bar = Yh^T (a I + A)^{-1} d-hat and
+//    C^{-1/2} = a^{-1/2} I + Yh^T U diag(g(s)) U^T Yh with
+//    g(s) = ((a + s)^{-1/2} - a^{-1/2}) / s, so
+//    x^a_m = xbar + dX Yh^T v + sqrt(beta) dx_m + sqrt(k-1) (dX Yh^T) U g U^T yh_m.
+//    A is gathered from the global Gram dY dY^T, formed once per analysis.
+// The symmetric eigensolve is a cyclic Jacobi method (Golub & Van Loan,
+// Section 8.5) with the round-robin parallel ordering, in FP64, on a
+// matrix held in shared memory, one column per lane.
+#include <cmath>
+
+#include "lbm_internal.cuh"
+
+namespace lbmgpu {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int NMAX = 32;  // largest eigenproblem of the warp kernel
+constexpr int LD = NMAX + 1;
+constexpr int kMaxSweeps = 30;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+__device__ __forceinline__ int min_image(int d, int n) {
+    if (d > n / 2) d -= n;
+    if (d < -(n / 2)) d += n;
+    return d;
+}
+
+// Gaspari-Cohn weight, both branches in nested (Horner) form.
+__device__ __forceinline__ double gaspari_cohn(double d) {
+    if (d <= 1.0) return 1.0 + d * d * (-5.0 / 3.0 + d * (0.625 + d * (0.5 - 0.25 * d)));
+    if (d < 2.0)
+        return d * d * (5.0 / 3.0 + d * (0.625 + d * (-0.5 + d * (1.0 / 12.0)))) - 5.0 * d + 4.0 -
+               (2.0 / 3.0) / d;
+    return 0.0;
+}
+
+// ------------------------------------------------------------------ K2
+template <typename T, bool SHIFT>
+__global__ void __launch_bounds__(128) observe_kernel(const T* __restrict__ f, int nx, int ny,
+                                                      int k, const int* __restrict__ ix,
+                                                      const int* __restrict__ iy,
+                                                      const double* __restrict__ yo,
+                                                      double* __restrict__ dY,
+                                                      double* __restrict__ d) {
+    extern __shared__ double sh[];  // yu[k], yv[k], red[2 * 4]
+    double* yu = sh;
+    double* yv = sh + k;
+    double* red = sh + 2 * k;
+    const int j = blockIdx.x;
+    const size_t plane = (size_t)nx * ny * k;
+    const size_t base = ((size_t)iy[j] * nx + ix[j]) * k;
+    double su = 0.0, sv = 0.0;
+    for (int m = threadIdx.x; m < k; m += blockDim.x) {
+        double r = SHIFT ? 1.0 : 0.0, jx = 0.0, jy = 0.0;
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+            const double g = (double)f[a * plane + base + m];
+            r += g;
+            jx += d2q9_cx(a) * g;
+            jy += d2q9_cy(a) * g;
+        }
+        const double u = jx / r, v = jy / r;
+        yu[m] = u;
+        yv[m] = v;
+        su += u;
+        sv += v;
+    }
+    su = warp_sum(su);
+    sv = warp_sum(sv);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) {
+        red[w] = su;
+        red[4 + w] = sv;
+    }
+    __syncthreads();
+    const double ubar = ((red[0] + red[1]) + (red[2] + red[3])) / k;
+    const double vbar = ((red[4] + red[5]) + (red[6] + red[7])) / k;
+    for (int m = threadIdx.x; m < k; m += blockDim.x) {
+        dY[(size_t)(2 * j) * k + m] = yu[m] - ubar;
+        dY[(size_t)(2 * j + 1) * k + m] = yv[m] - vbar;
+    }
+    if (threadIdx.x == 0) {
+        d[2 * j] = yo[2 * j] - ubar;
+        d[2 * j + 1] = yo[2 * j + 1] - vbar;
+    }
+}
+
+// G = dY dY^T (nobs x nobs), one thread per entry.
+__global__ void obs_gram_kernel(const double* __restrict__ dY, int nobs, int k,
+                                double* __restrict__ G) {
+    const int i = blockIdx.y;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nobs) return;
+    const double* a = dY + (size_t)i * k;
+    const double* b = dY + (size_t)j * k;
+    double s = 0.0;
+    for (int m = 0; m < k; ++m) s += a[m] * b[m];
+    G[(size_t)i * nobs + j] = s;
+}
+
+// ------------------------------------------------------------------ K3
+// Cyclic Jacobi with round-robin ordering on the n x n symmetric matrix A
+// (row-major, leading dimension LD, shared memory); U accumulates the
+// rotations (U starts as I). One lane per column/row. Returns false if the
+// sweep cap was reached.
+__device__ bool jacobi_warp(double* A, double* U, int n, int lane, double* rc, double* rs, int* rp,
+                            int* rq) {
+    const int np = n + (n & 1);
+    const int half = np / 2;
+    double fro = 0.0;
+    if (lane < n)
+        for (int i = 0; i < n; ++i) fro += A[i * LD + lane] * A[i * LD + lane];
+    fro = warp_sum(fro);
+    const double thresh = 1e-18 * sqrt(fro);
+    for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
+        bool any_sweep = false;
+        for (int r = 0; r + 1 < np; ++r) {
+            bool rot = false;
+            if (lane < half) {
+                const int pa = lane, pb = np - 1 - lane;
+                const int P = pa == 0 ? 0 : 1 + (pa - 1 + r) % (np - 1);
+                const int Q = 1 + (pb - 1 + r) % (np - 1);
+                const int p = P < Q ? P : Q, q = P < Q ? Q : P;
+                double c = 1.0, s = 0.0;
+                if (q < n) {
+                    const double apq = A[p * LD + q];
+                    if (fabs(apq) > thresh) {
+                        // Symmetric 2 x 2 Schur decomposition.
+                        const double app = A[p * LD + p], aqq = A[q * LD + q];
+                        const double tau = (aqq - app) / (2.0 * apq);
+                        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                        c = 1.0 / sqrt(1.0 + t * t);
+                        s = t * c;
+                        rot = true;
+                    }
+                }
+                rp[lane] = p;
+                rq[lane] = q;
+                rc[lane] = c;
+                rs[lane] = rot ? s : 0.0;
+            }
+            const unsigned any = __ballot_sync(kFull, rot);
+            __syncwarp();
+            if (any == 0) continue;
+            any_sweep = true;
+            // A <- J^T A: rotate row pairs; lane owns column `lane`.
+            if (lane < n) {
+                for (int t = 0; t < half; ++t) {
+                    if (!((any >> t) & 1u)) continue;
+                    const int p = rp[t], q = rq[t];
+                    const double c = rc[t], s = rs[t];
+                    const double ap = A[p * LD + lane], aq = A[q * LD + lane];
+                    A[p * LD + lane] = c * ap - s * aq;
+                    A[q * LD + lane] = s * ap + c * aq;
+                }
+            }
+            __syncwarp();
+            // A <- A J and U <- U J: rotate column pairs; lane owns row `lane`.
+            if (lane < n) {
+                for (int t = 0; t < half; ++t) {
+                    if (!((any >> t) & 1u)) continue;
+                    const int p = rp[t], q = rq[t];
+                    const double c = rc[t], s = rs[t];
+                    const double ap = A[lane * LD + p], aq = A[lane * LD + q];
+                    A[lane * LD + p] = c * ap - s * aq;
+                    A[lane * LD + q] = s * ap + c * aq;
+                    const double up = U[lane * LD + p], uq = U[lane * LD + q];
+                    U[lane * LD + p] = c * up - s * uq;
+                    U[lane * LD + q] = s * up + c * uq;
+                }
+            }
+            __syncwarp();
+            if (rot) {
+                const int p = rp[lane], q = rq[lane];
+                A[p * LD + q] = 0.0;
+                A[q * LD + p] = 0.0;
+            }
+            __syncwarp();
+        }
+        if (!any_sweep) return true;
+    }
+    return false;
+}
+
+struct AnaSmem {
+    double* A;     // [NMAX][LD]
+    double* U;     // [NMAX][LD]
+    double* dX;    // [9][k]
+    double* xbar;  // [16]
+    double* lsq;   // [nl] sqrt of the localised inverse error variance
+    double* ldh;   // [nl] sqrt(rho) * d
+    double* v1;    // [NMAX]
+    double* v2;    // [NMAX]
+    double* v3;    // [NMAX]
+    double* Z;     // [9][NMAX]
+    double* B;     // [9][NMAX]
+    double* zv;    // [16]
+    double* rc;    // [NMAX / 2]
+    double* rs;    // [NMAX / 2]
+    int* rp;       // [NMAX / 2]
+    int* rq;       // [NMAX / 2]
+    int* lidx;     // [nl]
+};
+
+__host__ __device__ inline size_t ana_smem_bytes(int k, int nl) {
+    size_t d = 2 * (size_t)NMAX * LD + 9 * (size_t)k + 16 + 2 * (size_t)nl + 3 * NMAX +
+               18 * (size_t)NMAX + 16 + NMAX;
+    return d * sizeof(double) + (size_t)(NMAX + nl) * sizeof(int);
+}
+
+__device__ inline AnaSmem carve(unsigned char* raw, int k, int nl) {
+    AnaSmem s;
+    double* p = reinterpret_cast<double*>(raw);
+    s.A = p;
+    p += NMAX * LD;
+    s.U = p;
+    p += NMAX * LD;
+    s.dX = p;
+    p += 9 * k;
+    s.xbar = p;
+    p += 16;
+    s.lsq = p;
+    p += nl;
+    s.ldh = p;
+    p += nl;
+    s.v1 = p;
+    p += NMAX;
+    s.v2 = p;
+    p += NMAX;
+    s.v3 = p;
+    p += NMAX;
+    s.Z = p;
+    p += 9 * NMAX;
+    s.B = p;
+    p += 9 * NMAX;
+    s.zv = p;
+    p += 16;
+    s.rc = p;
+    p += NMAX / 2;
+    s.rs = p;
+    p += NMAX / 2;
+    int* ip = reinterpret_cast<int*>(p);
+    s.rp = ip;
+    ip += NMAX / 2;
+    s.rq = ip;
+    ip += NMAX / 2;
+    s.lidx = ip;
+    return s;
+}
+
+template <typename T, bool SHIFT>
+__global__ void __launch_bounds__(32) analyze_kernel(T* __restrict__ f, int nx, int ny, int k,
+                                                     ObsParams o, double d_cut, double beta,
+                                                     int* __restrict__ flags) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nobs = 2 * o.npts;
+    AnaSmem sm = carve(smem_raw, k, nobs);
+    const int lane = threadIdx.x;
+    const int cell = blockIdx.x;
+    const int x = cell % nx, y = cell / nx;
+    const size_t plane = (size_t)nx * ny * k;
+    T* fc = f + (size_t)cell * k;
+
+    // Ensemble mean and perturbations of the nine components.
+    for (int a = 0; a < 9; ++a) {
+        double s = 0.0;
+        for (int m = lane; m < k; m += 32) {
+            const double xv = (double)fc[a * plane + m];
+            sm.dX[a * k + m] = xv;
+            s += xv;
+        }
+        const double mean = warp_sum(s) / k;
+        for (int m = lane; m < k; m += 32) sm.dX[a * k + m] -= mean;
+        if (lane == 0) sm.xbar[a] = mean;
+    }
+
+    // Local observation set: points with r / d_cut < 2 and G > 0, in
+    // increasing point order, two scalars (u, v) per point.
+    int count = 0;
+    for (int j0 = 0; j0 < o.npts; j0 += 32) {
+        const int j = j0 + lane;
+        bool in = false;
+        double g = 0.0;
+        if (j < o.npts) {
+            const int dx = min_image(o.ix[j] - x, nx);
+            const int dy = min_image(o.iy[j] - y, ny);
+            const double r = sqrt((double)dx * dx + (double)dy * dy);
+            const double dist = r / d_cut;
+            if (dist < 2.0) {
+                g = gaspari_cohn(dist);
+                in = g > 0.0;
+            }
+        }
+        const unsigned bal = __ballot_sync(kFull, in);
+        if (in) {
+            const int pos = count + __popc(bal & ((1u << lane) - 1u));
+            const double sg = sqrt(g);
+            sm.lidx[2 * pos] = 2 * j;
+            sm.lidx[2 * pos + 1] = 2 * j + 1;
+            sm.lsq[2 * pos] = sg / o.sigma_u;
+            sm.lsq[2 * pos + 1] = sg / o.sigma_v;
+        }
+        count += __popc(bal);
+    }
+    __syncwarp();
+    const int p = 2 * count;
+    for (int i = lane; i < p; i += 32) sm.ldh[i] = sm.lsq[i] * o.d[sm.lidx[i]];
+    __syncwarp();
+
+    if (p == 0) {
+        // No observation in range: x^a_m = xbar + sqrt(beta) dx_m.
+        const double sb = sqrt(beta);
+        for (int a = 0; a < 9; ++a)
+            for (int m = lane; m < k; m += 32)
+                fc[a * plane + m] = (T)(sm.xbar[a] + sb * sm.dX[a * k + m]);
+        return;
+    }
+    const bool obs_space = p < k;
+    const int n = obs_space ? p : k;
+    if (n > NMAX) {
+        if (lane == 0) atomicOr(flags, FLAG_TOOLARGE);
+        return;
+    }
+    const double aa = (k - 1) / beta;
+    double* A = sm.A;
+    double* U = sm.U;
+
+    if (obs_space) {
+        // A = Yh Yh^T gathered from the global Gram.
+        if (lane < n) {
+            const int ol = sm.lidx[lane];
+            const double sl = sm.lsq[lane];
+            for (int i = 0; i < n; ++i)
+                A[i * LD + lane] = sm.lsq[i] * o.G[(size_t)sm.lidx[i] * nobs + ol] * sl;
+        }
+    } else {
+        // C = a I + Yh^T Yh and b = Yh^T d-hat, column `lane`.
+        if (lane < n) {
+            double bj = 0.0;
+            for (int i = 0; i < n; ++i) {
+                double s = 0.0;
+                for (int l = 0; l < p; ++l) {
+                    const double* row = o.dY + (size_t)sm.lidx[l] * k;
+                    const double w = sm.lsq[l] * sm.lsq[l];
+                    s += w * row[i] * row[lane];
+                }
+                A[i * LD + lane] = s + (i == lane ? aa : 0.0);
+            }
+            for (int l = 0; l < p; ++l) bj += sm.lsq[l] * o.dY[(size_t)sm.lidx[l] * k + lane] * sm.ldh[l];
+            sm.v3[lane] = bj;
+        }
+    }
+    if (lane < n)
+        for (int i = 0; i < n; ++i) U[i * LD + lane] = (i == lane) ? 1.0 : 0.0;
+    __syncwarp();
+
+    if (!jacobi_warp(A, U, n, lane, sm.rc, sm.rs, sm.rp, sm.rq)) {
+        if (lane == 0) atomicOr(flags, FLAG_NOCONV);
+    }
+    __syncwarp();
+
+    if (obs_space) {
+        // v = U diag(1 / (a + s)) U^T d-hat; g(s) stably as
+        // -1 / (sqrt(a + s) sqrt(a) (sqrt(a + s) + sqrt(a))).
+        const double sa = sqrt(aa);
+        if (lane < n) {
+            const double s_i = A[lane * LD + lane];
+            double t = 0.0;
+            for (int l = 0; l < n; ++l) t += U[l * LD + lane] * sm.ldh[l];
+            sm.v1[lane] = t / (aa + s_i);
+            const double sas = sqrt(aa + s_i);
+            sm.v3[lane] = -1.0 / (sas * sa * (sas + sa));
+        }
+        __syncwarp();
+        if (lane < n) {
+            double t = 0.0;
+            for (int l = 0; l < n; ++l) t += U[lane * LD + l] * sm.v1[l];
+            sm.v2[lane] = t;
+            // Z = dX Yh^T, column `lane`.
+            const double* row = o.dY + (size_t)sm.lidx[lane] * k;
+            for (int a = 0; a < 9; ++a) {
+                double s = 0.0;
+                for (int m = 0; m < k; ++m) s += sm.dX[a * k + m] * row[m];
+                sm.Z[a * NMAX + lane] = sm.lsq[lane] * s;
+            }
+        }
+        __syncwarp();
+        // zv = Z v (= dX w-bar); B = Z U.
+        if (lane < 9) {
+            double s = 0.0;
+            for (int i = 0; i < n; ++i) s += sm.Z[lane * NMAX + i] * sm.v2[i];
+            sm.zv[lane] = s;
+        }
+        if (lane < n)
+            for (int a = 0; a < 9; ++a) {
+                double s = 0.0;
+                for (int l = 0; l < n; ++l) s += sm.Z[a * NMAX + l] * U[l * LD + lane];
+                sm.B[a * NMAX + lane] = s;
+            }
+        __syncwarp();
+        // Z <- sqrt(k-1) (Z U) diag(g) U^T diag(sqrt(rho)), ready to meet dY.
+        const double sk = sqrt((double)(k - 1));
+        if (lane < n)
+            for (int a = 0; a < 9; ++a) {
+                double s = 0.0;
+                for (int l = 0; l < n; ++l) s += sm.B[a * NMAX + l] * sm.v3[l] * U[lane * LD + l];
+                sm.Z[a * NMAX + lane] = sk * sm.lsq[lane] * s;
+            }
+        __syncwarp();
+        const double sb = sqrt(beta);
+        for (int m = lane; m < k; m += 32) {
+            double acc[9];
+#pragma unroll
+            for (int a = 0; a < 9; ++a) acc[a] = sm.xbar[a] + sm.zv[a] + sb * sm.dX[a * k + m];
+            for (int i = 0; i < n; ++i) {
+                const double dy = o.dY[(size_t)sm.lidx[i] * k + m];
+#pragma unroll
+                for (int a = 0; a < 9; ++a) acc[a] += sm.Z[a * NMAX + i] * dy;
+            }
+#pragma unroll
+            for (int a = 0; a < 9; ++a) fc[a * plane + m] = (T)acc[a];
+        }
+    } else {
+        // lam = diag; w-bar = U diag(1/lam) U^T b; T = W + w-bar 1^T with
+        // W = sqrt(k-1) U diag(lam^{-1/2}) U^T, stored over A.
+        if (lane < n) {
+            const double lam = A[lane * LD + lane];
+            double t = 0.0;
+            for (int l = 0; l < n; ++l) t += U[l * LD + lane] * sm.v3[l];
+            sm.v1[lane] = t / lam;
+            sm.v2[lane] = sqrt((double)(k - 1) / lam);
+        }
+        __syncwarp();
+        if (lane < n) {
+            double t = 0.0;
+            for (int l = 0; l < n; ++l) t += U[lane * LD + l] * sm.v1[l];
+            sm.v3[lane] = t;  // w-bar
+        }
+        __syncwarp();
+        if (lane < n)
+            for (int i = 0; i < n; ++i) {
+                double s = 0.0;
+                for (int l = 0; l < n; ++l) s += U[i * LD + l] * sm.v2[l] * U[lane * LD + l];
+                A[i * LD + lane] = s + sm.v3[i];
+            }
+        __syncwarp();
+        if (lane < k) {
+            const int m = lane;
+            for (int a = 0; a < 9; ++a) {
+                double s = 0.0;
+                for (int j = 0; j < k; ++j) s += sm.dX[a * k + j] * A[j * LD + m];
+                fc[a * plane + m] = (T)(sm.xbar[a] + s);
+            }
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_observe(const void* f, int fp32, int nx, int ny, int k, int npts, const int* ix,
+                           const int* iy, const double* yo, double* dY, double* d,
+                           cudaStream_t s) {
+    if (npts <= 0) return cudaSuccess;
+    const size_t sh = (2 * (size_t)k + 8) * sizeof(double);
+    if (fp32)
+        observe_kernel<float, true><<<npts, 128, sh, s>>>((const float*)f, nx, ny, k, ix, iy, yo, dY,
+                                                          d);
+    else
+        observe_kernel<double, false><<<npts, 128, sh, s>>>((const double*)f, nx, ny, k, ix, iy, yo,
+                                                            dY, d);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_obs_gram(const double* dY, int nobs, int k, double* G, cudaStream_t s) {
+    if (nobs <= 0) return cudaSuccess;
+    dim3 grid((nobs + 127) / 128, nobs);
+    obs_gram_kernel<<<grid, 128, 0, s>>>(dY, nobs, k, G);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_analyze(void* f, int fp32, int nx, int ny, int k, const ObsParams& o,
+                           double d_cut, double beta, int* flags, cudaStream_t s) {
+    const size_t sh = ana_smem_bytes(k, 2 * o.npts);
+    const long long cells = (long long)nx * ny;
+    if (cells > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    cudaError_t e;
+    if (fp32) {
+        e = cudaFuncSetAttribute(analyze_kernel<float, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+        if (e != cudaSuccess) return e;
+        analyze_kernel<float, true><<<(unsigned)cells, 32, sh, s>>>((float*)f, nx, ny, k, o, d_cut,
+                                                                    beta, flags);
+    } else {
+        e = cudaFuncSetAttribute(analyze_kernel<double, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+        if (e != cudaSuccess) return e;
+        analyze_kernel<double, false><<<(unsigned)cells, 32, sh, s>>>((double*)f, nx, ny, k, o,
+                                                                      d_cut, beta, flags);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace lbmgpu

@@ -1,0 +1,185 @@
+"""Parity of the CUDA LETKF analysis and of the whole forecast-analysis
+cycle with the FP64 oracle (arXiv 2308.03972, Section 3.2), called through
+the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2308_03972_gb300 import inputs
+from _helpers import TOL_FP64, U_RMS, norm_rel, osse_observations, turbulent_state
+
+pytestmark = pytest.mark.gpu
+TAU0, CS, MU = 0.55, 0.2, 6.16e-7
+SIGMA = 0.1 * U_RMS
+
+
+def _analysis_case(nx, ny, k, nobs_x, nobs_y, seed, steps=5):
+    f = turbulent_state(oracle, nx, ny, k, seed=seed)
+    force = inputs.forcing_field(nx, ny, seed=3, amp=3.5e-6)
+    f = oracle.lbm_run(f, force, TAU0, CS, MU, steps)
+    tu, tv = inputs.random_velocity(nx, ny, seed + 1000, U_RMS)
+    ix, iy, yu, yv = osse_observations(nx, ny, nobs_x, nobs_y, 4, 1, tu, tv, SIGMA)
+    return f, ix, iy, yu, yv
+
+
+def _gpu_analysis(b, f, ix, iy, yu, yv, d_cut, beta, prec, sigma=SIGMA):
+    _, ny, nx, k = f.shape
+    with b.Ensemble(nx, ny, k, TAU0, CS, MU, prec, f0=f) as e:
+        e.observe(ix, iy, yu, yv, sigma, sigma)
+        e.analyze(d_cut, beta)
+        out = e.get_f()
+        e.sync()
+    return out
+
+
+@pytest.mark.parametrize("nx,ny,k,nox,noy,d_cut", [
+    (24, 20, 8, 4, 4, 6.0),    # p >= k: ensemble-space form
+    (30, 26, 8, 3, 2, 9.5),    # ragged lattice, ensemble-space form
+    (24, 24, 40, 4, 4, 5.0),   # p < k: observation-space form
+    (20, 20, 64, 2, 2, 7.0),   # observation-space form, two lanes per member
+    (16, 16, 2, 4, 4, 4.0),    # smallest ensemble
+])
+def test_single_analysis_fp64_matches_oracle(gpu, nx, ny, k, nox, noy, d_cut):
+    f, ix, iy, yu, yv = _analysis_case(nx, ny, k, nox, noy, seed=nx + k)
+    beta = 1.05
+    got = _gpu_analysis(gpu, f, ix, iy, yu, yv, d_cut, beta, gpu.LBM_FP64)
+    ref = oracle.letkf_analyze(f, ix, iy, yu, yv, SIGMA, SIGMA, d_cut, beta)
+    assert norm_rel(got, ref) <= TOL_FP64
+    # The analysis must actually change the ensemble.
+    assert norm_rel(ref, f) > 1e-8
+
+
+def test_no_observation_in_range_is_pure_inflation(gpu):
+    f, ix, iy, yu, yv = _analysis_case(16, 16, 6, 2, 2, seed=9)
+    # d_cut tiny: only cells on an observation point see it (r = 0).
+    got = _gpu_analysis(gpu, f, ix, iy, yu, yv, 0.3, 1.1, gpu.LBM_FP64)
+    ref = oracle.letkf_analyze(f, ix, iy, yu, yv, SIGMA, SIGMA, 0.3, 1.1)
+    assert norm_rel(got, ref) <= TOL_FP64
+    xbar = f.mean(axis=3, keepdims=True)
+    mask = np.ones((16, 16), bool)
+    mask[iy, ix] = False
+    np.testing.assert_allclose(got[:, mask], (xbar + np.sqrt(1.1) * (f - xbar))[:, mask], rtol=0, atol=1e-15)
+
+
+def test_observations_on_the_wrap_boundary(gpu):
+    f, _, _, _, _ = _analysis_case(20, 18, 10, 2, 2, seed=11)
+    ix = np.array([0, 19, 0, 19, 10], np.int32)
+    iy = np.array([0, 0, 17, 17, 9], np.int32)
+    yu = np.linspace(-0.02, 0.02, 5)
+    yv = np.linspace(0.01, -0.01, 5)
+    got = _gpu_analysis(gpu, f, ix, iy, yu, yv, 4.0, 1.0, gpu.LBM_FP64)
+    ref = oracle.letkf_analyze(f, ix, iy, yu, yv, SIGMA, SIGMA, 4.0, 1.0)
+    assert norm_rel(got, ref) <= TOL_FP64
+
+
+def test_full_size_analysis_sampled_points(gpu):
+    """256^2 lattice, 64 members, 8 x 8 observation points, d_cut = 32: the
+    configuration the benchmark times. Compared at sampled grid points."""
+    nx = ny = 256
+    k = 64
+    f, ix, iy, yu, yv = _analysis_case(nx, ny, k, 8, 8, seed=21, steps=2)
+    got = _gpu_analysis(gpu, f, ix, iy, yu, yv, 32.0, 1.05, gpu.LBM_FP64)
+    rng = np.random.default_rng(0)
+    pts = np.unique(np.concatenate([rng.integers(0, nx * ny, 150),
+                                    [0, nx - 1, nx * ny - 1, (ny - 1) * nx, 32 * nx + 32, 16 * nx + 48]]))
+    ref = oracle.letkf_analyze(f, ix, iy, yu, yv, SIGMA, SIGMA, 32.0, 1.05, points=pts.astype(np.int32))
+    g = got.reshape(9, nx * ny, k)[:, pts]
+    r = ref.reshape(9, nx * ny, k)[:, pts]
+    assert norm_rel(g, r) <= TOL_FP64
+
+
+def test_mixed_precision_analysis_close_to_oracle(gpu):
+    f, ix, iy, yu, yv = _analysis_case(24, 24, 40, 4, 4, seed=31)
+    got = _gpu_analysis(gpu, f, ix, iy, yu, yv, 5.0, 1.05, gpu.LBM_MIXED)
+    ref = oracle.letkf_analyze(f, ix, iy, yu, yv, SIGMA, SIGMA, 5.0, 1.05)
+    assert norm_rel(got, ref) <= 1e-6
+
+
+def test_argument_errors(gpu):
+    f, ix, iy, yu, yv = _analysis_case(16, 16, 4, 2, 2, seed=2)
+    with gpu.Ensemble(16, 16, 4, TAU0, CS, MU, gpu.LBM_FP64, f0=f) as e:
+        with pytest.raises(gpu.LbmError) as err:
+            e.analyze(4.0, 1.0)  # no observation yet
+        assert err.value.code == gpu.LBM_EINVAL
+        with pytest.raises(gpu.LbmError):
+            e.observe(np.array([16]), np.array([0]), [0.0], [0.0], SIGMA, SIGMA)
+        with pytest.raises(gpu.LbmError):
+            e.observe(ix, iy, yu, yv, 0.0, SIGMA)
+        e.observe(ix, iy, yu, yv, SIGMA, SIGMA)
+        with pytest.raises(gpu.LbmError):
+            e.analyze(-1.0, 1.0)
+        e.analyze(4.0, 1.0)
+        with pytest.raises(gpu.LbmError):
+            e.analyze(4.0, 1.0)  # observation already consumed
+        e.sync()
+    with gpu.Ensemble(8, 8, 1, TAU0, CS, MU, gpu.LBM_FP64) as e:
+        e.observe(np.array([1]), np.array([1]), [0.0], [0.0], SIGMA, SIGMA)
+        with pytest.raises(gpu.LbmError):
+            e.analyze(4.0, 1.0)  # one member
+
+
+def test_oversized_local_problem_is_reported(gpu):
+    # 64 members and 36 observation scalars in range: n = 36 > 32.
+    f, ix, iy, yu, yv = _analysis_case(24, 24, 64, 6, 3, seed=3)
+    with gpu.Ensemble(24, 24, 64, TAU0, CS, MU, gpu.LBM_FP64, f0=f) as e:
+        e.observe(ix, iy, yu, yv, SIGMA, SIGMA)
+        e.analyze(100.0, 1.0)
+        with pytest.raises(gpu.LbmError) as err:
+            e.sync()
+        assert err.value.code == gpu.LBM_EINVAL
+
+
+def _osse(run_forecast, run_analysis, nature, steps, s, nobs, d_cut, beta, nx, ny, seed=4):
+    """Cycle: forecast s steps, observe the nature run with noise, analyse."""
+    for c in range(1, steps // s + 1):
+        run_forecast(s)
+        _, tu, tv = nature(c * s)
+        ix, iy, yu, yv = osse_observations(nx, ny, nobs, nobs, seed, c, tu, tv, SIGMA)
+        run_analysis(ix, iy, yu, yv, d_cut, beta)
+
+
+def test_tiny_osse_cycle_fp64_and_mixed_match_oracle(gpu):
+    """32^2 lattice, 8 members, 4 x 4 (u, v) observations, d_cut = 8,
+    beta = 1.05, analysis every 10 steps for 200 steps."""
+    nx = ny = 32
+    k = 8
+    force = inputs.forcing_field(nx, ny, seed=3, amp=3.5e-6)
+    tu0, tv0 = inputs.random_velocity(nx, ny, 1, U_RMS)
+    f_nat = oracle.set_equilibrium(np.ones((ny, nx, 1)), tu0[:, :, None], tv0[:, :, None])
+    nature_states = {0: f_nat}
+    for t in range(10, 201, 10):
+        nature_states[t] = oracle.lbm_run(nature_states[t - 10], force, TAU0, CS, MU, 10)
+
+    def nature(t):
+        r, u, v = oracle.moments(nature_states[t])
+        return r[:, :, 0], u[:, :, 0], v[:, :, 0]
+
+    f0 = turbulent_state(oracle, nx, ny, k, seed=2)
+
+    state = {"f": f0}
+
+    def o_fc(n):
+        state["f"] = oracle.lbm_run(state["f"], force, TAU0, CS, MU, n)
+
+    def o_an(ix, iy, yu, yv, d_cut, beta):
+        state["f"] = oracle.letkf_analyze(state["f"], ix, iy, yu, yv, SIGMA, SIGMA, d_cut, beta)
+
+    _osse(o_fc, o_an, nature, 200, 10, 4, 8.0, 1.05, nx, ny)
+    ref = state["f"]
+    _, ur, vr = oracle.moments(ref)
+    _, tu, tv = nature(200)
+    rmse_ref = np.sqrt(np.mean((ur.mean(2) - tu) ** 2 + (vr.mean(2) - tv) ** 2))
+
+    results = {}
+    for prec in (gpu.LBM_FP64, gpu.LBM_MIXED):
+        with gpu.Ensemble(nx, ny, k, TAU0, CS, MU, prec, f0=f0, force=force) as e:
+            _osse(e.forecast, lambda ix, iy, yu, yv, d, b: (e.observe(ix, iy, yu, yv, SIGMA, SIGMA), e.analyze(d, b)),
+                  nature, 200, 10, 4, 8.0, 1.05, nx, ny)
+            got = e.get_f()
+            _, ug, vg = e.moments_host()
+            e.sync()
+        rmse = np.sqrt(np.mean((ug.mean(2) - tu) ** 2 + (vg.mean(2) - tv) ** 2))
+        results[prec] = (norm_rel(got, ref), abs(rmse / rmse_ref - 1))
+    assert results[gpu.LBM_FP64][0] <= TOL_FP64
+    assert results[gpu.LBM_FP64][1] <= 1e-6
+    assert results[gpu.LBM_MIXED][1] <= 1e-2
