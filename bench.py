@@ -1,0 +1,378 @@
+"""Benchmark of the LBM-LETKF forecast-analysis cycle on GB300.
+
+One step = one DA cycle of the ensemble at the paper-scale workload
+(256^2 lattice, 64 members, 8 x 8 (u, v) observation points, d_cut = 32,
+beta = 1.05, 10 LBM steps per cycle): 10 fused LBM steps, the observation
+operator and the LETKF analysis at all 65,536 grid points. The metric is
+cycles/s; the primary line is the mixed-precision path, with the plain FP64
+path measured on the same GPU alongside.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+With N > 1 (torchrun) every rank runs an independent replica (the cycle has
+no exchange step on one lattice); value = cycles of all ranks / max time.
+--impl reference times the FP64 CPU oracle on a bounded sample instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "LBM-LETKF cycles/s at 256^2 x 64 members (mixed precision; FP64 alongside)"
+HBM_FALLBACK_GBS = 6800.0
+FP64_NOMINAL_GFLOPS = 1250.0  # GB300 FP64 (CUDA-core and tensor) nominal rate
+L2_NOTE = "state larger than L2: 151 MB per buffer in FP32, 302 MB in FP64 (L2 = 129 MiB)"
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu), "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return None
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def local_obs_counts(cfg):
+    """Number of local observation scalars at every grid point (host geometry:
+    points with r / d_cut < 2 and a positive Gaspari-Cohn weight)."""
+    from paper_2308_03972_gb300 import inputs
+
+    ix, iy = inputs.uniform_obs_points(cfg.nx, cfg.ny, cfg.nobs_x, cfg.nobs_y)
+    x = np.arange(cfg.nx)[None, :, None]
+    y = np.arange(cfg.ny)[:, None, None]
+    dx = np.abs(ix[None, None, :] - x)
+    dx = np.minimum(dx, cfg.nx - dx)
+    dy = np.abs(iy[None, None, :] - y)
+    dy = np.minimum(dy, cfg.ny - dy)
+    d = np.sqrt(dx * dx + dy * dy) / cfg.d_cut
+    return 2 * (d < 2.0).sum(axis=2)
+
+
+def analysis_flops(cfg, p):
+    """Algorithmic FP64 flops of one analysis: per grid point with p local
+    scalars and n = min(k, p) the eigensolve counts 9 n^3 (symmetric
+    eigenvalues and vectors) and the dense products count 2 flops per
+    multiply-add of their definition (observation-space form when p < k)."""
+    k = cfg.members
+    p = p.astype(np.float64)
+    obs = p < k
+    n = np.where(obs, p, k)
+    eig = 9.0 * n ** 3
+    prod_obs = 2 * (p * p + 2 * n * n + 9 * k * p + 2 * 9 * n * n + 9 * k * p)
+    prod_ens = 2 * (k * k * p + k * p + 2 * k * k + k ** 3 + 9 * k * k)
+    return float(np.sum(eig + np.where(obs, prod_obs, prod_ens)))
+
+
+def measure(cfg, precision, steps, warmup, sample_clocks=False, gpu_index=0):
+    import torch
+
+    from paper_2308_03972_gb300 import binding
+    from paper_2308_03972_gb300.cycle import Osse
+
+    stream = torch.cuda.current_stream()
+    osse = Osse(cfg, precision, stream=stream.cuda_stream)
+    obs = osse.observations(warmup + steps)
+    for c in range(warmup):
+        osse.cycle(obs[c])
+    osse.ens.sync()
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(gpu_index) if sample_clocks else None
+    if sampler:
+        sampler.__enter__()
+    try:
+        torch.cuda.synchronize()
+        start.record(stream)
+        for c in range(steps):
+            e = ev[c]
+            yo = obs[warmup + c]
+            e[0].record(stream)
+            osse.ens.forecast(cfg.steps_per_cycle)
+            e[1].record(stream)
+            osse.ens.observe(osse.ix, osse.iy, yo[0], yo[1], cfg.sigma, cfg.sigma)
+            e[2].record(stream)
+            osse.ens.analyze(cfg.d_cut, cfg.beta)
+            e[3].record(stream)
+        end.record(stream)
+        torch.cuda.synchronize()
+    finally:
+        if sampler:
+            sampler.__exit__()
+    osse.ens.sync()
+    total_ms = start.elapsed_time(end)
+    lbm = [e[0].elapsed_time(e[1]) / cfg.steps_per_cycle for e in ev]
+    obs_ms = [e[1].elapsed_time(e[2]) for e in ev]
+    ana = [e[2].elapsed_time(e[3]) for e in ev]
+    rmse = osse.rmse()
+    osse.close()
+    return {"ms_per_cycle": total_ms / steps, "lbm_step_ms": statistics.mean(lbm),
+            "observe_ms": statistics.mean(obs_ms), "analysis_ms": statistics.mean(ana),
+            "rmse": rmse, "clocks": sampler.summary() if sampler else None,
+            "launches_per_cycle": cfg.steps_per_cycle + 3}
+
+
+def measure_e2e(cfg, precision, steps, warmup):
+    """Public API with host buffers: each cycle copies its observations from
+    host memory (pinned staging) and reads the ensemble-mean velocity back."""
+    import torch
+
+    from paper_2308_03972_gb300.cycle import Osse
+
+    osse = Osse(cfg, precision)
+    obs = osse.observations(warmup + steps)
+    um = np.empty((cfg.ny, cfg.nx))
+    vm = np.empty((cfg.ny, cfg.nx))
+    for c in range(warmup):
+        osse.cycle(obs[c])
+        osse.ens.mean_velocity(um, vm)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for c in range(steps):
+        osse.cycle(obs[warmup + c])
+        osse.ens.mean_velocity(um, vm)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    osse.close()
+    npts = cfg.nobs_x * cfg.nobs_y
+    return {"value": steps / dt, "unit": "cycles/s", "h2d_bytes_per_step": npts * (2 * 4 + 2 * 8),
+            "d2h_bytes_per_step": 2 * cfg.nx * cfg.ny * 8}
+
+
+def oracle_cycle_sample(cfg, npoints=8192, lbm_steps=1, seed=0):
+    """Time the FP64 oracle on a bounded sample of one cycle: lbm_steps LBM
+    steps of the whole ensemble and the LETKF analysis at npoints grid
+    points; extrapolate to 10 steps + all grid points."""
+    import oracle
+    from paper_2308_03972_gb300 import inputs
+
+    nx, ny, k = cfg.nx, cfg.ny, cfg.members
+    u, v = inputs.ensemble_velocity(nx, ny, k, cfg.seeds["ensemble"], cfg.u_rms, cfg.ens_pert)
+    f = oracle.set_equilibrium(np.ones_like(u), u, v)
+    force = inputs.forcing_field(nx, ny, cfg.seeds["forcing"], cfg.force_amp, cfg.force_kmin, cfg.force_kmax)
+    t0 = time.perf_counter()
+    for _ in range(lbm_steps):
+        f = oracle.lbm_step(f, force, cfg.tau0, cfg.cs_smag, cfg.mu)
+    t_step = (time.perf_counter() - t0) / lbm_steps
+    ix, iy = inputs.uniform_obs_points(nx, ny, cfg.nobs_x, cfg.nobs_y)
+    tu, tv = inputs.random_velocity(nx, ny, cfg.seeds["nature"], cfg.u_rms)
+    eu, ev = inputs.obs_noise(cfg.seeds["noise"], 1, len(ix))
+    rng = np.random.default_rng(seed)
+    pts = np.sort(rng.choice(nx * ny, size=min(npoints, nx * ny), replace=False)).astype(np.int32)
+    t0 = time.perf_counter()
+    oracle.letkf_analyze(f, ix, iy, tu[iy, ix] + cfg.sigma * eu, tv[iy, ix] + cfg.sigma * ev,
+                         cfg.sigma, cfg.sigma, cfg.d_cut, cfg.beta, points=pts)
+    t_ana = (time.perf_counter() - t0) * (nx * ny) / len(pts)
+    t_cycle = cfg.steps_per_cycle * t_step + t_ana
+    return {"value": 1.0 / t_cycle, "unit": "cycles/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "%d LBM step(s) of the 256^2 x 64 ensemble + LETKF analysis at %d of %d grid points, "
+                      "extrapolated to one cycle (10 steps + all points); FP64 C oracle, OpenMP"
+                      % (lbm_steps, len(pts), nx * ny),
+            "lbm_step_s": t_step, "analysis_s": t_ana}
+
+
+def run_reference(args, cfg):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_cycle_sample(cfg, npoints=1024)
+    vals = [oracle_cycle_sample(cfg, npoints=args.ref_points, seed=s) for s in range(args.steps)]
+    value = statistics.mean(v["value"] for v in vals)
+    base = dict(vals[0])
+    base["value"] = value
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "cycles/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": cfg.name(), "l2": "n/a (CPU)"},
+            "cpu_baseline": base,
+            "e2e": {"value": value, "unit": "cycles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--ref-points", type=int, default=8192)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+
+    from paper_2308_03972_gb300.cycle import PAPER_SCALE
+    cfg = PAPER_SCALE
+    if args.impl == "reference":
+        run_reference(args, cfg)
+        return
+
+    import torch
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    from paper_2308_03972_gb300 import binding, build
+
+    build.build()
+    binding.load()
+
+    def barrier_max(x):
+        if world == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    mixed = measure(cfg, binding.LBM_MIXED, args.steps, args.warmup, sample_clocks=(rank == 0), gpu_index=local)
+    ms = barrier_max(mixed["ms_per_cycle"])
+    fp64 = measure(cfg, binding.LBM_FP64, max(3, args.steps // 3), args.warmup)
+    ms64 = barrier_max(fp64["ms_per_cycle"])
+    e2e = measure_e2e(cfg, binding.LBM_MIXED, args.steps, args.warmup)
+    e2e_val = barrier_max(1.0 / e2e["value"])
+
+    peaks = _peaks()
+    hbm = peaks.get("hbm_gbs", HBM_FALLBACK_GBS)
+    p = local_obs_counts(cfg)
+    flops = analysis_flops(cfg, p)
+    ncell = cfg.nx * cfg.ny * cfg.members
+    lbm_bytes32 = 2 * 9 * 4 * ncell
+    lbm_bytes64 = 2 * 9 * 8 * ncell
+    kern = {
+        "lbm_step_f32": {"ms": mixed["lbm_step_ms"], "launches_per_cycle": cfg.steps_per_cycle,
+                         "bound": "hbm", "achieved_gbs": lbm_bytes32 / (mixed["lbm_step_ms"] * 1e6),
+                         "peak_gbs": hbm},
+        "analysis_mixed": {"ms": mixed["analysis_ms"], "launches_per_cycle": 1, "bound": "alu",
+                           "achieved_gflops": flops / (mixed["analysis_ms"] * 1e6),
+                           "peak_gflops": FP64_NOMINAL_GFLOPS},
+        "observe_mixed": {"ms": mixed["observe_ms"]},
+        "lbm_step_f64": {"ms": fp64["lbm_step_ms"], "achieved_gbs": lbm_bytes64 / (fp64["lbm_step_ms"] * 1e6)},
+        "analysis_fp64": {"ms": fp64["analysis_ms"],
+                          "achieved_gflops": flops / (fp64["analysis_ms"] * 1e6)},
+    }
+    lbm_share = mixed["lbm_step_ms"] * cfg.steps_per_cycle
+    if lbm_share >= mixed["analysis_ms"]:
+        ach = kern["lbm_step_f32"]["achieved_gbs"]
+        roof = {"kernel": "lbm_step_kernel<float,4,shift>", "bound": "hbm", "achieved": ach, "peak": hbm,
+                "unit": "GB/s", "frac": ach / hbm, "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback"}
+    else:
+        ach = kern["analysis_mixed"]["achieved_gflops"]
+        roof = {"kernel": "analyze_kernel<float,shift>", "bound": "alu", "achieved": ach / 1000.0,
+                "peak": FP64_NOMINAL_GFLOPS / 1000.0, "unit": "TFLOP/s", "frac": ach / FP64_NOMINAL_GFLOPS,
+                "traffic": None, "peak_source": "GB300 FP64 nominal 1.25 TFLOP/s"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_cycle_sample(cfg)
+
+    if rank == 0:
+        value = world * 1000.0 / ms
+        line = {
+            "metric": METRIC, "value": value, "unit": "cycles/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 LBM + f64 eigensolve (mixed)", "data": "synthetic",
+            "config": {"workload": cfg.name(), "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": L2_NOTE},
+            "fp64": {"value": world * 1000.0 / ms64, "unit": "cycles/s", "ms_per_step": ms64,
+                     "dtype": "f64"},
+            "e2e": {"value": world / e2e_val, "unit": "cycles/s",
+                    "h2d_bytes_per_step": e2e["h2d_bytes_per_step"],
+                    "d2h_bytes_per_step": e2e["d2h_bytes_per_step"]},
+            "gpu_launches": args.steps * mixed["launches_per_cycle"],
+            "roofline": roof, "kernels": kern,
+            "rmse": {"mixed": mixed["rmse"], "fp64": fp64["rmse"], "obs_noise_rms": cfg.sigma * np.sqrt(2)},
+            "clocks": mixed["clocks"], "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -96,12 +96,19 @@ int lbm_forecast(lbm_ctx *ctx, int nsteps);
  * outputs may be NULL. With LBM_PTR_HOST the call synchronises. */
 int lbm_moments(lbm_ctx *ctx, double *rho, double *u, double *v, int ptr_kind);
 
+/* Ensemble-mean velocity ubar = M^{-1} sum_m u_m, the best estimate the
+ * paper scores against the truth (Section 4.3, RMSE). u, v: [ny][nx]; either
+ * may be NULL. With LBM_PTR_HOST the call synchronises. */
+int lbm_mean_velocity(lbm_ctx *ctx, double *u, double *v, int ptr_kind);
+
 /* Observation step (Section 3, y = H x; Section 3.2, ybar and dY): record
  * npts observation points (ix[j], iy[j]) with observed velocities
  * (yo_u[j], yo_v[j]) and error standard deviations sigma_u, sigma_v, apply
  * H to every forecast member, and form dY = Y - ybar and d = y^o - ybar on
- * the device. Host pointers; npts >= 1; 0 <= ix < nx, 0 <= iy < ny;
- * sigma > 0. The observation vector orders scalars as (u_0, v_0, u_1, ...). */
+ * the device. Host pointers (read before the call returns; the values are
+ * staged through a pinned buffer, so the call does not wait for the
+ * device); npts >= 1; 0 <= ix < nx, 0 <= iy < ny; sigma > 0. The
+ * observation vector orders scalars as (u_0, v_0, u_1, ...). */
 int letkf_observe(lbm_ctx *ctx, int npts, const int *ix, const int *iy,
                   const double *yo_u, const double *yo_v, double sigma_u,
                   double sigma_v);

@@ -41,6 +41,7 @@ SIGNATURES = {
     "lbm_set_equilibrium": (_I, [_P, _P, _P, _P, _I]),
     "lbm_forecast": (_I, [_P, _I]),
     "lbm_moments": (_I, [_P, _P, _P, _P, _I]),
+    "lbm_mean_velocity": (_I, [_P, _P, _P, _I]),
     "letkf_observe": (_I, [_P, _I, _P, _P, _P, _P, _D, _D]),
     "letkf_analyze": (_I, [_P, _D, _D]),
     "lbm_get_f": (_I, [_P, _P, _I]),
@@ -168,6 +169,14 @@ def lbm_moments(ctx, rho=None, u=None, v=None):
     _check(ctx, load().lbm_moments(ctx, pr, pu, pv, kind))
 
 
+def lbm_mean_velocity(ctx, u=None, v=None):
+    """Fill the given ensemble-mean outputs [ny][nx] (numpy or CUDA tensors)."""
+    pu, ku, _b = _arr(u, writable=True)
+    pv, kv, _c = _arr(v, writable=True)
+    kind = _kind(*(k for a, k in ((u, ku), (v, kv)) if a is not None))
+    _check(ctx, load().lbm_mean_velocity(ctx, pu, pv, kind))
+
+
 def letkf_observe(ctx, ix, iy, yo_u, yo_v, sigma_u, sigma_v):
     ix = np.ascontiguousarray(ix, dtype=np.int32)
     iy = np.ascontiguousarray(iy, dtype=np.int32)
@@ -233,6 +242,13 @@ class Ensemble:
         rho, u, v = np.empty(shape), np.empty(shape), np.empty(shape)
         lbm_moments(self.ctx, rho, u, v)
         return rho, u, v
+
+    def mean_velocity(self, u=None, v=None):
+        if u is None and v is None:
+            u = np.empty((self.ny, self.nx))
+            v = np.empty((self.ny, self.nx))
+        lbm_mean_velocity(self.ctx, u, v)
+        return u, v
 
     def observe(self, ix, iy, yo_u, yo_v, sigma_u, sigma_v):
         letkf_observe(self.ctx, ix, iy, yo_u, yo_v, sigma_u, sigma_v)

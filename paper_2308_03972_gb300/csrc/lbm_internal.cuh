@@ -54,6 +54,8 @@ cudaError_t launch_lbm_step_f32(const float* gin, float* gout, const float* forc
                                 const LbmParams& p, int* flags, cudaStream_t s);
 cudaError_t launch_moments(const void* f, int fp32, int nx, int ny, int k, double* rho,
                            double* u, double* v, int* flags, cudaStream_t s);
+cudaError_t launch_mean_velocity(const void* f, int fp32, int nx, int ny, int k, double* u,
+                                 double* v, int* flags, cudaStream_t s);
 cudaError_t launch_set_equilibrium(void* f, int fp32, int nx, int ny, int k,
                                    const double* rho, const double* u, const double* v,
                                    cudaStream_t s);

@@ -217,6 +217,44 @@ __global__ void moments_kernel(const T* __restrict__ f, int nx, int ny, int k,
     if (!(ux * ux + uy * uy <= kUMax2) || !(r > 0.0)) atomicOr(flags, FLAG_DIVERGED);
 }
 
+// Ensemble-mean velocity: one warp per cell, lanes over members.
+template <typename T, bool SHIFT>
+__global__ void mean_velocity_kernel(const T* __restrict__ f, int nx, int ny, int k,
+                                     double* __restrict__ um, double* __restrict__ vm,
+                                     int* __restrict__ flags) {
+    const long long cell = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (cell >= (long long)nx * ny) return;
+    const size_t n = (size_t)nx * ny * k;
+    double su = 0.0, sv = 0.0;
+    bool bad = false;
+    for (int m = lane; m < k; m += 32) {
+        const size_t i = (size_t)cell * k + m;
+        double r = SHIFT ? 1.0 : 0.0, jx = 0.0, jy = 0.0;
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+            const double g = (double)f[a * n + i];
+            r += g;
+            jx += d2q9_cx(a) * g;
+            jy += d2q9_cy(a) * g;
+        }
+        const double ux = jx / r, uy = jy / r;
+        su += ux;
+        sv += uy;
+        bad |= !(ux * ux + uy * uy <= kUMax2) || !(r > 0.0);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        su += __shfl_xor_sync(0xffffffffu, su, o);
+        sv += __shfl_xor_sync(0xffffffffu, sv, o);
+    }
+    if (lane == 0) {
+        if (um) um[cell] = su / k;
+        if (vm) vm[cell] = sv / k;
+    }
+    if (bad) atomicOr(flags, FLAG_DIVERGED);
+}
+
 template <typename T, bool SHIFT>
 __global__ void equilibrium_kernel(T* __restrict__ f, size_t n, const double* __restrict__ rho,
                                    const double* __restrict__ u, const double* __restrict__ v) {
@@ -286,6 +324,19 @@ cudaError_t launch_moments(const void* f, int fp32, int nx, int ny, int k, doubl
     else
         moments_kernel<double, false><<<blocks_for(n, 256), 256, 0, s>>>(
             (const double*)f, nx, ny, k, rho, u, v, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mean_velocity(const void* f, int fp32, int nx, int ny, int k, double* u,
+                                 double* v, int* flags, cudaStream_t s) {
+    const size_t threads = (size_t)nx * ny * 32;
+    if (threads == 0) return cudaSuccess;
+    if (fp32)
+        mean_velocity_kernel<float, true><<<blocks_for(threads, 256), 256, 0, s>>>(
+            (const float*)f, nx, ny, k, u, v, flags);
+    else
+        mean_velocity_kernel<double, false><<<blocks_for(threads, 256), 256, 0, s>>>(
+            (const double*)f, nx, ny, k, u, v, flags);
     return cudaGetLastError();
 }
 

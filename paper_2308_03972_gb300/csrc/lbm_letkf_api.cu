@@ -30,6 +30,10 @@ struct lbm_ctx {
     double* dY = nullptr;  // [2 npts][k]
     double* d = nullptr;   // [2 npts]
     double* G = nullptr;   // [2 npts][2 npts]
+    double* h_yo = nullptr;  // pinned staging [2 cap]
+    int* h_ixy = nullptr;    // pinned staging [2 cap] (ix then iy)
+    cudaEvent_t obs_copied = nullptr;  // last staging copy done
+    bool obs_pending = false;
     double sigma_u = 0.0, sigma_v = 0.0;
     bool observed = false;
     char err[512] = {0};
@@ -97,8 +101,13 @@ int read_flags(lbm_ctx* c) {
 }
 
 void free_obs(lbm_ctx* c) {
+    if (c->obs_pending && c->obs_copied) cudaEventSynchronize(c->obs_copied);
+    c->obs_pending = false;
+    cudaFreeHost(c->h_yo);
+    cudaFreeHost(c->h_ixy);
+    c->h_yo = nullptr;
+    c->h_ixy = nullptr;
     cudaFree(c->ix);
-    cudaFree(c->iy);
     cudaFree(c->yo);
     cudaFree(c->dY);
     cudaFree(c->d);
@@ -266,6 +275,27 @@ int lbm_moments(lbm_ctx* c, double* rho, double* u, double* v, int ptr_kind) {
     return read_flags(c);
 }
 
+int lbm_mean_velocity(lbm_ctx* c, double* u, double* v, int ptr_kind) {
+    if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (!ptr_kind_ok(ptr_kind)) return fail(c, LBM_EINVAL, "bad ptr_kind");
+    const size_t n = (size_t)c->nx * c->ny;
+    if (ptr_kind == LBM_PTR_DEVICE) {
+        CK(c, launch_mean_velocity(c->f[c->cur], is_fp32(c), c->nx, c->ny, c->k, u, v, c->flags,
+                                   c->stream),
+           "launching mean velocity");
+        return LBM_OK;
+    }
+    int st = ensure_stage(c);
+    if (st) return st;
+    double* s = c->stage;
+    CK(c, launch_mean_velocity(c->f[c->cur], is_fp32(c), c->nx, c->ny, c->k, u ? s : nullptr,
+                               v ? s + n : nullptr, c->flags, c->stream),
+       "launching mean velocity");
+    if (u) CK(c, cudaMemcpyAsync(u, s, n * 8, cudaMemcpyDeviceToHost, c->stream), "copy u");
+    if (v) CK(c, cudaMemcpyAsync(v, s + n, n * 8, cudaMemcpyDeviceToHost, c->stream), "copy v");
+    return read_flags(c);
+}
+
 int letkf_observe(lbm_ctx* c, int npts, const int* ix, const int* iy, const double* yo_u,
                   const double* yo_v, double sigma_u, double sigma_v) {
     if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
@@ -280,34 +310,42 @@ int letkf_observe(lbm_ctx* c, int npts, const int* ix, const int* iy, const doub
         if (!std::isfinite(yo_u[j]) || !std::isfinite(yo_v[j]))
             return fail(c, LBM_EINVAL, "observation %d is not finite", j);
     }
+    if (!c->obs_copied)
+        CK(c, cudaEventCreateWithFlags(&c->obs_copied, cudaEventDisableTiming), "creating event");
     if (npts > c->obs_cap) {
         CK(c, cudaStreamSynchronize(c->stream), "synchronising");
         free_obs(c);
         const size_t no = 2 * (size_t)npts;
-        CK(c, cudaMalloc(&c->ix, npts * sizeof(int)), "allocating obs");
-        CK(c, cudaMalloc(&c->iy, npts * sizeof(int)), "allocating obs");
+        CK(c, cudaMalloc(&c->ix, 2 * npts * sizeof(int)), "allocating obs");
+        c->iy = c->ix + npts;
         CK(c, cudaMalloc(&c->yo, no * sizeof(double)), "allocating obs");
         CK(c, cudaMalloc(&c->dY, no * c->k * sizeof(double)), "allocating obs");
         CK(c, cudaMalloc(&c->d, no * sizeof(double)), "allocating obs");
         CK(c, cudaMalloc(&c->G, no * no * sizeof(double)), "allocating obs");
+        CK(c, cudaMallocHost(&c->h_yo, no * sizeof(double)), "allocating pinned staging");
+        CK(c, cudaMallocHost(&c->h_ixy, 2 * npts * sizeof(int)), "allocating pinned staging");
         c->obs_cap = npts;
     }
-    std::vector<double> yo(2 * (size_t)npts);
+    // The staging buffer may still be read by the previous copy.
+    if (c->obs_pending) CK(c, cudaEventSynchronize(c->obs_copied), "waiting for staging copy");
     for (int j = 0; j < npts; ++j) {
-        yo[2 * j] = yo_u[j];
-        yo[2 * j + 1] = yo_v[j];
+        c->h_yo[2 * j] = yo_u[j];
+        c->h_yo[2 * j + 1] = yo_v[j];
+        c->h_ixy[j] = ix[j];
+        c->h_ixy[npts + j] = iy[j];
     }
-    CK(c, cudaMemcpyAsync(c->ix, ix, npts * sizeof(int), cudaMemcpyHostToDevice, c->stream), "copy ix");
-    CK(c, cudaMemcpyAsync(c->iy, iy, npts * sizeof(int), cudaMemcpyHostToDevice, c->stream), "copy iy");
-    CK(c, cudaMemcpyAsync(c->yo, yo.data(), yo.size() * sizeof(double), cudaMemcpyHostToDevice,
+    c->iy = c->ix + npts;
+    CK(c, cudaMemcpyAsync(c->ix, c->h_ixy, 2 * npts * sizeof(int), cudaMemcpyHostToDevice, c->stream),
+       "copy positions");
+    CK(c, cudaMemcpyAsync(c->yo, c->h_yo, 2 * npts * sizeof(double), cudaMemcpyHostToDevice,
                           c->stream),
-       "copy yo");
+       "copy observations");
+    CK(c, cudaEventRecord(c->obs_copied, c->stream), "recording event");
+    c->obs_pending = true;
     CK(c, launch_observe(c->f[c->cur], is_fp32(c), c->nx, c->ny, c->k, npts, c->ix, c->iy, c->yo,
                          c->dY, c->d, c->stream),
        "launching observation operator");
     CK(c, launch_obs_gram(c->dY, 2 * npts, c->k, c->G, c->stream), "launching observation Gram");
-    // The host vector must outlive the copy from pageable memory.
-    CK(c, cudaStreamSynchronize(c->stream), "synchronising");
     c->npts = npts;
     c->sigma_u = sigma_u;
     c->sigma_v = sigma_v;
@@ -395,6 +433,7 @@ void lbm_destroy(lbm_ctx* c) {
     cudaFree(c->flags);
     cudaFree(c->stage);
     free_obs(c);
+    if (c->obs_copied) cudaEventDestroy(c->obs_copied);
     delete c;
 }
 

@@ -118,3 +118,16 @@ def test_device_pointer_io_matches_host_io(gpu):
         _, u_h, _ = e.moments_host()
     np.testing.assert_array_equal(dev.cpu().numpy(), host)
     np.testing.assert_array_equal(u_d.cpu().numpy(), u_h)
+
+
+def test_mean_velocity_matches_oracle_moments(gpu):
+    nx, ny, k = 21, 13, 7
+    f = random_state(nx, ny, k, seed=6)
+    for prec, tol in ((gpu.LBM_FP64, 1e-15), (gpu.LBM_MIXED, 1e-7)):
+        with _ens(gpu, f, None, prec) as e:
+            e.forecast(2)
+            um, vm = e.mean_velocity()
+        ref = oracle.lbm_run(f, np.zeros((2, ny, nx)), TAU0, CS, MU, 2)
+        _, u, v = oracle.moments(ref)
+        assert np.max(np.abs(um - u.mean(axis=2))) <= tol
+        assert np.max(np.abs(vm - v.mean(axis=2))) <= tol

@@ -183,3 +183,19 @@ def test_tiny_osse_cycle_fp64_and_mixed_match_oracle(gpu):
     assert results[gpu.LBM_FP64][0] <= TOL_FP64
     assert results[gpu.LBM_FP64][1] <= 1e-6
     assert results[gpu.LBM_MIXED][1] <= 1e-2
+
+
+def test_repeated_observe_calls_reuse_staging(gpu):
+    """letkf_observe does not wait for the device: consecutive cycles with
+    different observation sets give the oracle's result."""
+    nx, ny, k = 20, 20, 6
+    f, ix, iy, yu, yv = _analysis_case(nx, ny, k, 4, 4, seed=41)
+    ref = f
+    with gpu.Ensemble(nx, ny, k, TAU0, CS, MU, gpu.LBM_FP64, f0=f) as e:
+        for c in range(3):
+            sel = slice(c, None)  # fewer points each cycle
+            e.observe(ix[sel], iy[sel], yu[sel] * (1 + c), yv[sel], SIGMA, SIGMA)
+            e.analyze(5.0, 1.05)
+            ref = oracle.letkf_analyze(ref, ix[sel], iy[sel], yu[sel] * (1 + c), yv[sel], SIGMA, SIGMA, 5.0, 1.05)
+        got = e.get_f()
+    assert norm_rel(got, ref) <= TOL_FP64
