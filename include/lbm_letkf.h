@@ -133,12 +133,43 @@ int lbm_set_f(lbm_ctx *ctx, const double *f, int ptr_kind);
  * The flag word is cleared after it is reported. */
 int lbm_sync(lbm_ctx *ctx);
 
-/* Message for the last failure on ctx (or of the last failed lbm_init on
- * this thread when ctx is NULL). Never NULL. */
+/* Message for the last failure on ctx (or, when ctx is NULL, of the last
+ * failed lbm_init or letkf_analyze_noalloc on this thread). Never NULL. */
 const char *lbm_last_error(const lbm_ctx *ctx);
 
 /* Free the context and its device buffers (synchronises its stream). */
 void lbm_destroy(lbm_ctx *ctx);
+
+/* Limits of letkf_analyze_noalloc. */
+#define LBM_NOALLOC_MAX_POINTS 256   /* observation points (512 scalars) */
+#define LBM_NOALLOC_MAX_MEMBERS 128  /* ensemble members */
+
+/* Allocation-free LETKF analysis, for callers that cannot call cudaMalloc
+ * (an embedding whose memory manager owns the device pool, or code that
+ * must not trigger an allocation's implicit synchronisation). The paper has
+ * no counterpart; this is a library-interface addition. It performs the
+ * same observation step and analysis as letkf_observe + letkf_analyze, on
+ * an FP64 ensemble state the caller owns, without a context:
+ *   f      device pointer, [9][ny][nx][members] FP64, updated in place;
+ *   ix, iy, yo_u, yo_v  host arrays of npts observation points and values
+ *          (checked on the host, then copied);
+ *   stream cudaStream_t (NULL = legacy default stream).
+ * Intermediates (dY, d, dY dY^T, positions, a flag word) live in one fixed
+ * file-scope device array of about 2.6 MB that every GPU loading the
+ * library holds until exit; nothing is allocated or freed. Sizes above
+ * LBM_NOALLOC_MAX_POINTS / LBM_NOALLOC_MAX_MEMBERS are rejected with
+ * LBM_EINVAL. The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture. Every call shares the array and overwrites
+ * it; two calls that overlap on the GPU (different streams, or different
+ * host threads) race on it and must be serialised by the caller. The call
+ * synchronises the stream and returns LBM_OK, LBM_EINVAL (bad argument or
+ * local problem larger than the kernel holds), LBM_ENOCONV or LBM_ECUDA;
+ * lbm_last_error(NULL) gives the message. */
+int letkf_analyze_noalloc(double *f, int nx, int ny, int members, int npts,
+                          const int *ix, const int *iy, const double *yo_u,
+                          const double *yo_v, double sigma_u, double sigma_v,
+                          double d_cut, double beta, void *stream);
 
 #ifdef __cplusplus
 }

@@ -49,6 +49,7 @@ SIGNATURES = {
     "lbm_sync": (_I, [_P]),
     "lbm_last_error": (ctypes.c_char_p, [_P]),
     "lbm_destroy": (None, [_P]),
+    "letkf_analyze_noalloc": (_I, [_P, _I, _I, _I, _I, _P, _P, _P, _P, _D, _D, _D, _D, _P]),
 }
 
 
@@ -217,6 +218,26 @@ def lbm_last_error(ctx) -> str:
 def lbm_destroy(ctx):
     if ctx:
         load().lbm_destroy(ctx)
+
+
+def letkf_analyze_noalloc(f, ix, iy, yo_u, yo_v, sigma_u, sigma_v, d_cut, beta, stream="current"):
+    """Allocation-free analysis of a caller-owned FP64 CUDA tensor
+    f [9][ny][nx][members] in place; observations are host arrays."""
+    if not _is_torch(f) or not f.is_cuda or f.dim() != 4:
+        raise TypeError("f must be a 4-d CUDA float64 tensor [9][ny][nx][members]")
+    pf, _, _a = _arr(f)
+    ix = np.ascontiguousarray(ix, dtype=np.int32)
+    iy = np.ascontiguousarray(iy, dtype=np.int32)
+    yo_u = np.ascontiguousarray(yo_u, dtype=np.float64)
+    yo_v = np.ascontiguousarray(yo_v, dtype=np.float64)
+    if stream == "current":
+        stream = default_stream()
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    _, ny, nx, k = f.shape
+    st = load().letkf_analyze_noalloc(pf, nx, ny, k, len(ix), p(ix), p(iy), p(yo_u), p(yo_v),
+                                      float(sigma_u), float(sigma_v), float(d_cut), float(beta),
+                                      ctypes.c_void_p(stream) if stream else None)
+    _check(None, st)
 
 
 class Ensemble:

@@ -119,6 +119,11 @@ void free_obs(lbm_ctx* c) {
 
 }  // namespace
 
+namespace lbmgpu {
+// Error message of a context-free entry point, read by lbm_last_error(NULL).
+void set_context_free_error(const char* msg) { snprintf(g_init_err, sizeof g_init_err, "%s", msg); }
+}  // namespace lbmgpu
+
 extern "C" {
 
 int lbm_init(const lbm_config* cfg, const double* f0, const double* force, int ptr_kind,
