@@ -43,6 +43,7 @@ struct ObsParams {
     const double* d;   // [2 npts] innovations y^o - ybar
     const double* G;   // [2 npts][2 npts] dY dY^T
     double sigma_u, sigma_v;
+    float* dY32;       // [2 npts][k] binary32 copy of dY (mixed precision only)
 };
 
 // ---- lbm_kernels.cu -------------------------------------------------------

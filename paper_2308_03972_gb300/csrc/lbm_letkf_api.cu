@@ -30,6 +30,7 @@ struct lbm_ctx {
     double* dY = nullptr;  // [2 npts][k]
     double* d = nullptr;   // [2 npts]
     double* G = nullptr;   // [2 npts][2 npts]
+    float* dY32 = nullptr; // [2 npts][k] binary32 copy (mixed precision)
     double* h_yo = nullptr;  // pinned staging [2 cap]
     int* h_ixy = nullptr;    // pinned staging [2 cap] (ix then iy)
     cudaEvent_t obs_copied = nullptr;  // last staging copy done
@@ -112,6 +113,8 @@ void free_obs(lbm_ctx* c) {
     cudaFree(c->dY);
     cudaFree(c->d);
     cudaFree(c->G);
+    cudaFree(c->dY32);
+    c->dY32 = nullptr;
     c->ix = c->iy = nullptr;
     c->yo = c->dY = c->d = c->G = nullptr;
     c->obs_cap = 0;
@@ -327,6 +330,7 @@ int letkf_observe(lbm_ctx* c, int npts, const int* ix, const int* iy, const doub
         CK(c, cudaMalloc(&c->dY, no * c->k * sizeof(double)), "allocating obs");
         CK(c, cudaMalloc(&c->d, no * sizeof(double)), "allocating obs");
         CK(c, cudaMalloc(&c->G, no * no * sizeof(double)), "allocating obs");
+        if (is_fp32(c)) CK(c, cudaMalloc(&c->dY32, no * c->k * sizeof(float)), "allocating obs");
         CK(c, cudaMallocHost(&c->h_yo, no * sizeof(double)), "allocating pinned staging");
         CK(c, cudaMallocHost(&c->h_ixy, 2 * npts * sizeof(int)), "allocating pinned staging");
         c->obs_cap = npts;
@@ -364,7 +368,7 @@ int letkf_analyze(lbm_ctx* c, double d_cut, double beta) {
     if (!(d_cut > 0.0) || !std::isfinite(d_cut)) return fail(c, LBM_EINVAL, "d_cut must be > 0");
     if (!(beta > 0.0) || !std::isfinite(beta)) return fail(c, LBM_EINVAL, "beta must be > 0");
     if (!c->observed) return fail(c, LBM_EINVAL, "letkf_observe must precede letkf_analyze");
-    ObsParams o{c->npts, c->ix, c->iy, c->dY, c->d, c->G, c->sigma_u, c->sigma_v};
+    ObsParams o{c->npts, c->ix, c->iy, c->dY, c->d, c->G, c->sigma_u, c->sigma_v, c->dY32};
     CK(c, launch_analyze(c->f[c->cur], is_fp32(c), c->nx, c->ny, c->k, o, d_cut, beta, c->flags,
                          c->stream),
        "launching analysis");

@@ -32,7 +32,8 @@ constexpr int NMAX = 32;  // largest eigenproblem of the warp kernel
 constexpr int LD = NMAX + 1;
 constexpr int kMaxSweeps = 30;
 
-__device__ __forceinline__ double warp_sum(double v) {
+template <typename R>
+__device__ __forceinline__ R warp_sum(R v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
     return v;
@@ -120,18 +121,20 @@ __global__ void obs_gram_kernel(const double* __restrict__ dY, int nobs, int k,
 // ------------------------------------------------------------------ K3
 // Cyclic Jacobi with round-robin ordering on the n x n symmetric matrix A
 // (row-major, leading dimension LD, shared memory); U accumulates the
-// rotations (U starts as I). One lane per column/row. Returns false if the
-// sweep cap was reached.
-__device__ bool jacobi_warp(double* A, double* U, int n, int lane, double* rc, double* rs, int* rp,
-                            int* rq) {
+// rotations (U starts as I). One lane per column/row. A rotation is skipped
+// when |a_pq| <= rel * ||A||_F; the solve stops after a sweep without
+// rotations. Returns false if max_sweeps was reached. R is double or float.
+template <typename R>
+__device__ bool jacobi_warp(R* A, R* U, int n, int lane, R* rc, R* rs, int* rp, int* rq, R rel,
+                            int max_sweeps) {
     const int np = n + (n & 1);
     const int half = np / 2;
-    double fro = 0.0;
+    R fro = R(0);
     if (lane < n)
         for (int i = 0; i < n; ++i) fro += A[i * LD + lane] * A[i * LD + lane];
     fro = warp_sum(fro);
-    const double thresh = 1e-18 * sqrt(fro);
-    for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
+    const R thresh = rel * sqrt(fro);
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
         bool any_sweep = false;
         for (int r = 0; r + 1 < np; ++r) {
             bool rot = false;
@@ -140,15 +143,15 @@ __device__ bool jacobi_warp(double* A, double* U, int n, int lane, double* rc, d
                 const int P = pa == 0 ? 0 : 1 + (pa - 1 + r) % (np - 1);
                 const int Q = 1 + (pb - 1 + r) % (np - 1);
                 const int p = P < Q ? P : Q, q = P < Q ? Q : P;
-                double c = 1.0, s = 0.0;
+                R c = R(1), s = R(0);
                 if (q < n) {
-                    const double apq = A[p * LD + q];
+                    const R apq = A[p * LD + q];
                     if (fabs(apq) > thresh) {
                         // Symmetric 2 x 2 Schur decomposition.
-                        const double app = A[p * LD + p], aqq = A[q * LD + q];
-                        const double tau = (aqq - app) / (2.0 * apq);
-                        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-                        c = 1.0 / sqrt(1.0 + t * t);
+                        const R app = A[p * LD + p], aqq = A[q * LD + q];
+                        const R tau = (aqq - app) / (R(2) * apq);
+                        const R t = (tau >= R(0) ? R(1) : R(-1)) / (fabs(tau) + sqrt(R(1) + tau * tau));
+                        c = R(1) / sqrt(R(1) + t * t);
                         s = t * c;
                         rot = true;
                     }
@@ -156,7 +159,7 @@ __device__ bool jacobi_warp(double* A, double* U, int n, int lane, double* rc, d
                 rp[lane] = p;
                 rq[lane] = q;
                 rc[lane] = c;
-                rs[lane] = rot ? s : 0.0;
+                rs[lane] = rot ? s : R(0);
             }
             const unsigned any = __ballot_sync(kFull, rot);
             __syncwarp();
@@ -167,8 +170,8 @@ __device__ bool jacobi_warp(double* A, double* U, int n, int lane, double* rc, d
                 for (int t = 0; t < half; ++t) {
                     if (!((any >> t) & 1u)) continue;
                     const int p = rp[t], q = rq[t];
-                    const double c = rc[t], s = rs[t];
-                    const double ap = A[p * LD + lane], aq = A[q * LD + lane];
+                    const R c = rc[t], s = rs[t];
+                    const R ap = A[p * LD + lane], aq = A[q * LD + lane];
                     A[p * LD + lane] = c * ap - s * aq;
                     A[q * LD + lane] = s * ap + c * aq;
                 }
@@ -179,11 +182,11 @@ __device__ bool jacobi_warp(double* A, double* U, int n, int lane, double* rc, d
                 for (int t = 0; t < half; ++t) {
                     if (!((any >> t) & 1u)) continue;
                     const int p = rp[t], q = rq[t];
-                    const double c = rc[t], s = rs[t];
-                    const double ap = A[lane * LD + p], aq = A[lane * LD + q];
+                    const R c = rc[t], s = rs[t];
+                    const R ap = A[lane * LD + p], aq = A[lane * LD + q];
                     A[lane * LD + p] = c * ap - s * aq;
                     A[lane * LD + q] = s * ap + c * aq;
-                    const double up = U[lane * LD + p], uq = U[lane * LD + q];
+                    const R up = U[lane * LD + p], uq = U[lane * LD + q];
                     U[lane * LD + p] = c * up - s * uq;
                     U[lane * LD + q] = s * up + c * uq;
                 }
@@ -191,8 +194,8 @@ __device__ bool jacobi_warp(double* A, double* U, int n, int lane, double* rc, d
             __syncwarp();
             if (rot) {
                 const int p = rp[lane], q = rq[lane];
-                A[p * LD + q] = 0.0;
-                A[q * LD + p] = 0.0;
+                A[p * LD + q] = R(0);
+                A[q * LD + p] = R(0);
             }
             __syncwarp();
         }
@@ -373,7 +376,7 @@ __global__ void __launch_bounds__(32) analyze_kernel(T* __restrict__ f, int nx, 
         for (int i = 0; i < n; ++i) U[i * LD + lane] = (i == lane) ? 1.0 : 0.0;
     __syncwarp();
 
-    if (!jacobi_warp(A, U, n, lane, sm.rc, sm.rs, sm.rp, sm.rq)) {
+    if (!jacobi_warp<double>(A, U, n, lane, sm.rc, sm.rs, sm.rp, sm.rq, 1e-18, kMaxSweeps)) {
         if (lane == 0) atomicOr(flags, FLAG_NOCONV);
     }
     __syncwarp();
@@ -474,6 +477,443 @@ __global__ void __launch_bounds__(32) analyze_kernel(T* __restrict__ f, int nx, 
     }
 }
 
+// ------------------------------------------------------------------ K3, mixed precision
+// The state is binary32 (g = f - w). The eigensolve is FP64-accurate at a
+// fraction of the FP64 work: a binary32 cyclic Jacobi gives a basis X; in
+// FP64 it is re-orthonormalised (Cholesky QR, Y = X L^{-T} with X^T X = L L^T),
+// the Rayleigh-Ritz matrix S = Y^T A Y is formed, and the matrix functions
+// f(A) = Y f(S) Y^T are evaluated to first order in the off-diagonal of S
+// (Daleckii-Krein: f(S)_ii = f(s_ii), f(S)_ij = s_ij f[s_ii, s_jj], with the
+// divided differences in closed form). The error is second order in the
+// off-diagonal of S (relative ~1e-13 at these sizes). Products that apply
+// the transform to the ensemble run in binary32 with binary32 accumulation.
+
+struct MixSmem {
+    double* A;     // [NMAX][LD] matrix (FP64), then S = Y^T A Y
+    double* Y;     // [NMAX][LD] FP64 basis
+    double* W;     // [NMAX][LD] X^T X, its Cholesky factor, then A Y
+    float* A32;    // [NMAX][LD] binary32 copy for the Jacobi pre-pass (inside W)
+    float* F32;    // [NMAX][LD] f(S) in binary32, then T (inside W)
+    float* U32;    // [NMAX][LD] binary32 rotations, then Y in binary32
+    double* lsq;   // [nl]
+    double* ldh;   // [nl]
+    double* vb;    // [NMAX]
+    double* v1;    // [NMAX]
+    double* v2;    // [NMAX]
+    double* vu;    // [NMAX]
+    double* vinv;  // [NMAX]
+    float* dX;     // [9][k]
+    float* xbar;   // [16]
+    float* Z;      // [9][NMAX]
+    float* B;      // [9][NMAX]
+    float* zv;     // [16]
+    float* vf;     // [NMAX]
+    float* rc;     // [NMAX / 2]
+    float* rs;     // [NMAX / 2]
+    int* rp;       // [NMAX / 2]
+    int* rq;       // [NMAX / 2]
+    int* lidx;     // [nl]
+};
+
+__host__ __device__ inline size_t mix_smem_bytes(int k, int nl) {
+    const size_t d = 3 * (size_t)NMAX * LD + 2 * (size_t)nl + 5 * NMAX;
+    const size_t f = (size_t)NMAX * LD + 9 * (size_t)k + 16 + 18 * NMAX + 16 + NMAX + NMAX;
+    const size_t i = NMAX + (size_t)nl;
+    return d * sizeof(double) + ((f * sizeof(float) + 7) / 8) * 8 + i * sizeof(int);
+}
+
+__device__ inline MixSmem carve_mix(unsigned char* raw, int k, int nl) {
+    MixSmem s;
+    double* p = reinterpret_cast<double*>(raw);
+    s.A = p;
+    p += NMAX * LD;
+    s.Y = p;
+    p += NMAX * LD;
+    s.W = p;
+    s.A32 = reinterpret_cast<float*>(p);
+    s.F32 = reinterpret_cast<float*>(p);
+    p += NMAX * LD;
+    s.lsq = p;
+    p += nl;
+    s.ldh = p;
+    p += nl;
+    s.vb = p;
+    p += NMAX;
+    s.v1 = p;
+    p += NMAX;
+    s.v2 = p;
+    p += NMAX;
+    s.vu = p;
+    p += NMAX;
+    s.vinv = p;
+    p += NMAX;
+    float* q = reinterpret_cast<float*>(p);
+    s.U32 = q;
+    q += NMAX * LD;
+    s.dX = q;
+    q += 9 * k;
+    s.xbar = q;
+    q += 16;
+    s.Z = q;
+    q += 9 * NMAX;
+    s.B = q;
+    q += 9 * NMAX;
+    s.zv = q;
+    q += 16;
+    s.vf = q;
+    q += NMAX;
+    s.rc = q;
+    q += NMAX / 2;
+    s.rs = q;
+    q += NMAX / 2;
+    const size_t fbytes = (size_t)(q - reinterpret_cast<float*>(p)) * sizeof(float);
+    int* ip = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(p) + ((fbytes + 7) / 8) * 8);
+    s.rp = ip;
+    ip += NMAX / 2;
+    s.rq = ip;
+    ip += NMAX / 2;
+    s.lidx = ip;
+    return s;
+}
+
+// FP64 refinement of the binary32 basis U32 of the symmetric matrix A:
+// Y = X L^{-T} (X = U32, X^T X = L L^T), then A <- S = Y^T A Y.
+__device__ void refine_basis(double* A, double* Y, double* W, double* vinv, const float* U32,
+                             int n, int lane) {
+    if (lane < n)
+        for (int c = 0; c < n; ++c) Y[lane * LD + c] = (double)U32[lane * LD + c];
+    __syncwarp();
+    if (lane < n)
+        for (int i = 0; i < n; ++i) {
+            double s = 0.0;
+            for (int r = 0; r < n; ++r) s += Y[r * LD + i] * Y[r * LD + lane];
+            W[i * LD + lane] = s;
+        }
+    __syncwarp();
+    // Cholesky factor of X^T X (close to I), lower triangle of W.
+    for (int j = 0; j < n; ++j) {
+        if (lane == j) {
+            double s = W[j * LD + j];
+            for (int c = 0; c < j; ++c) s -= W[j * LD + c] * W[j * LD + c];
+            const double inv = rsqrt(s);
+            W[j * LD + j] = s * inv;
+            vinv[j] = inv;
+        }
+        __syncwarp();
+        if (lane > j && lane < n) {
+            double s = W[lane * LD + j];
+            for (int c = 0; c < j; ++c) s -= W[lane * LD + c] * W[j * LD + c];
+            W[lane * LD + j] = s * vinv[j];
+        }
+        __syncwarp();
+    }
+    // Y <- X L^{-T}, row `lane` by forward substitution.
+    if (lane < n)
+        for (int j = 0; j < n; ++j) {
+            double z = Y[lane * LD + j];
+            for (int c = 0; c < j; ++c) z -= Y[lane * LD + c] * W[j * LD + c];
+            Y[lane * LD + j] = z * vinv[j];
+        }
+    __syncwarp();
+    // W = A Y, then A <- Y^T W.
+    if (lane < n)
+        for (int i = 0; i < n; ++i) {
+            double s = 0.0;
+            for (int c = 0; c < n; ++c) s += A[i * LD + c] * Y[c * LD + lane];
+            W[i * LD + lane] = s;
+        }
+    __syncwarp();
+    if (lane < n)
+        for (int i = 0; i < n; ++i) {
+            double s = 0.0;
+            for (int r = 0; r < n; ++r) s += Y[r * LD + i] * W[r * LD + lane];
+            A[i * LD + lane] = s;
+        }
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f, int nx, int ny,
+                                                           int k, ObsParams o, double d_cut,
+                                                           double beta, int* __restrict__ flags) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nobs = 2 * o.npts;
+    MixSmem sm = carve_mix(smem_raw, k, nobs);
+    const int lane = threadIdx.x;
+    const int cell = blockIdx.x;
+    const int x = cell % nx, y = cell / nx;
+    const size_t plane = (size_t)nx * ny * k;
+    float* fc = f + (size_t)cell * k;
+
+    // Ensemble mean and perturbations in binary32.
+    for (int a = 0; a < 9; ++a) {
+        float s = 0.0f;
+        for (int m = lane; m < k; m += 32) {
+            const float xv = fc[a * plane + m];
+            sm.dX[a * k + m] = xv;
+            s += xv;
+        }
+        const float mean = warp_sum(s) / (float)k;
+        for (int m = lane; m < k; m += 32) sm.dX[a * k + m] -= mean;
+        if (lane == 0) sm.xbar[a] = mean;
+    }
+
+    // Local observation set (FP64 decisions, as in the FP64 kernel).
+    int count = 0;
+    for (int j0 = 0; j0 < o.npts; j0 += 32) {
+        const int j = j0 + lane;
+        bool in = false;
+        double g = 0.0;
+        if (j < o.npts) {
+            const int dx = min_image(o.ix[j] - x, nx);
+            const int dy = min_image(o.iy[j] - y, ny);
+            const double r = sqrt((double)dx * dx + (double)dy * dy);
+            const double dist = r / d_cut;
+            if (dist < 2.0) {
+                g = gaspari_cohn(dist);
+                in = g > 0.0;
+            }
+        }
+        const unsigned bal = __ballot_sync(kFull, in);
+        if (in) {
+            const int pos = count + __popc(bal & ((1u << lane) - 1u));
+            const double sg = sqrt(g);
+            sm.lidx[2 * pos] = 2 * j;
+            sm.lidx[2 * pos + 1] = 2 * j + 1;
+            sm.lsq[2 * pos] = sg / o.sigma_u;
+            sm.lsq[2 * pos + 1] = sg / o.sigma_v;
+        }
+        count += __popc(bal);
+    }
+    __syncwarp();
+    const int p = 2 * count;
+    for (int i = lane; i < p; i += 32) sm.ldh[i] = sm.lsq[i] * o.d[sm.lidx[i]];
+    __syncwarp();
+
+    if (p == 0) {
+        const float sb = (float)sqrt(beta);
+        for (int a = 0; a < 9; ++a)
+            for (int m = lane; m < k; m += 32) fc[a * plane + m] = sm.xbar[a] + sb * sm.dX[a * k + m];
+        return;
+    }
+    const bool obs_space = p < k;
+    const int n = obs_space ? p : k;
+    if (n > NMAX) {
+        if (lane == 0) atomicOr(flags, FLAG_TOOLARGE);
+        return;
+    }
+    const double aa = (k - 1) / beta;
+    double* A = sm.A;
+    double* Y = sm.Y;
+
+    // The symmetric matrix in FP64: A = Yh Yh^T (observation space) or
+    // C = a I + Yh^T Yh with b = Yh^T d-hat (ensemble space).
+    if (obs_space) {
+        if (lane < n) {
+            const int ol = sm.lidx[lane];
+            const double sl = sm.lsq[lane];
+            for (int i = 0; i < n; ++i)
+                A[i * LD + lane] = sm.lsq[i] * o.G[(size_t)sm.lidx[i] * nobs + ol] * sl;
+        }
+    } else if (lane < n) {
+        double bj = 0.0;
+        for (int i = 0; i < n; ++i) {
+            double s = 0.0;
+            for (int l = 0; l < p; ++l) {
+                const double* row = o.dY + (size_t)sm.lidx[l] * k;
+                s += sm.lsq[l] * sm.lsq[l] * row[i] * row[lane];
+            }
+            A[i * LD + lane] = s + (i == lane ? aa : 0.0);
+        }
+        for (int l = 0; l < p; ++l) bj += sm.lsq[l] * o.dY[(size_t)sm.lidx[l] * k + lane] * sm.ldh[l];
+        sm.vb[lane] = bj;
+    }
+    __syncwarp();
+    if (lane < n)
+        for (int i = 0; i < n; ++i) {
+            sm.A32[i * LD + lane] = (float)A[i * LD + lane];
+            sm.U32[i * LD + lane] = (i == lane) ? 1.0f : 0.0f;
+        }
+    __syncwarp();
+    if (!jacobi_warp<float>(sm.A32, sm.U32, n, lane, sm.rc, sm.rs, sm.rp, sm.rq, 3e-8f, kMaxSweeps)) {
+        if (lane == 0) atomicOr(flags, FLAG_NOCONV);
+    }
+    __syncwarp();
+    refine_basis(A, Y, sm.W, sm.vinv, sm.U32, n, lane);
+    // Y in binary32 for the transform products.
+    if (lane < n)
+        for (int c = 0; c < n; ++c) sm.U32[lane * LD + c] = (float)Y[lane * LD + c];
+    __syncwarp();
+    float* Y32 = sm.U32;
+    float* F32 = sm.F32;
+    const float sk = (float)sqrt((double)(k - 1));
+
+    if (obs_space) {
+        // Functions of a + S: h = 1/(a+s) for the weights, g(s) = q[s, 0] with
+        // q(s) = (a+s)^{-1/2} for the square root. u_i = sqrt(a + s_ii).
+        const double r = sqrt(aa);
+        if (lane < n) {
+            const double u = sqrt(aa + A[lane * LD + lane]);
+            sm.vu[lane] = u;
+            sm.vinv[lane] = 1.0 / (u * (u + r));  // alpha_i
+            // t1 = Y^T d-hat
+            double t = 0.0;
+            for (int c = 0; c < n; ++c) t += Y[c * LD + lane] * sm.ldh[c];
+            sm.v1[lane] = t;
+        }
+        __syncwarp();
+        if (lane < n) {
+            // t2 = h(S) t1 with h(S)_ii = 1/u_i^2, h(S)_ij = -s_ij / (u_i^2 u_j^2).
+            const double hi = 1.0 / (sm.vu[lane] * sm.vu[lane]);
+            double t = 0.0;
+            for (int j = 0; j < n; ++j) {
+                if (j == lane) continue;
+                const double hj = 1.0 / (sm.vu[j] * sm.vu[j]);
+                t += A[lane * LD + j] * hj * sm.v1[j];
+            }
+            sm.v2[lane] = hi * (sm.v1[lane] - t);
+            // g(S) in binary32: diagonal -alpha_i / r, off-diagonal
+            // s_ij (u_i + u_j + r) alpha_i alpha_j / (r (u_i + u_j)).
+            const float ai = (float)sm.vinv[lane];
+            const float ui = (float)sm.vu[lane];
+            const float rf = (float)r;
+            for (int i = 0; i < n; ++i) {
+                float v;
+                if (i == lane) {
+                    v = (float)(-sm.vinv[lane] / r);
+                } else {
+                    const float uj = (float)sm.vu[i];
+                    const float aj = (float)sm.vinv[i];
+                    v = (float)A[i * LD + lane] * (ui + uj + rf) * ai * aj / (rf * (ui + uj));
+                }
+                F32[i * LD + lane] = v;
+            }
+        }
+        __syncwarp();
+        if (lane < n) {
+            double t = 0.0;
+            for (int c = 0; c < n; ++c) t += Y[lane * LD + c] * sm.v2[c];
+            sm.vf[lane] = (float)t;  // v = (a I + A)^{-1} d-hat
+            // Z = dX Yh^T, column `lane`.
+            const float* row = o.dY32 + (size_t)sm.lidx[lane] * k;
+            const float sl = (float)sm.lsq[lane];
+            for (int a = 0; a < 9; ++a) {
+                float s = 0.0f;
+                for (int m = 0; m < k; ++m) s += sm.dX[a * k + m] * row[m];
+                sm.Z[a * NMAX + lane] = sl * s;
+            }
+        }
+        __syncwarp();
+        if (lane < 9) {
+            float s = 0.0f;
+            for (int i = 0; i < n; ++i) s += sm.Z[lane * NMAX + i] * sm.vf[i];
+            sm.zv[lane] = s;
+        }
+        if (lane < n)
+            for (int a = 0; a < 9; ++a) {
+                float s = 0.0f;
+                for (int c = 0; c < n; ++c) s += sm.Z[a * NMAX + c] * Y32[c * LD + lane];
+                sm.B[a * NMAX + lane] = s;  // Z Y
+            }
+        __syncwarp();
+        if (lane < n)
+            for (int a = 0; a < 9; ++a) {
+                float s = 0.0f;
+                for (int j = 0; j < n; ++j) s += sm.B[a * NMAX + j] * F32[j * LD + lane];
+                sm.Z[a * NMAX + lane] = s;  // Z Y g(S)
+            }
+        __syncwarp();
+        if (lane < n) {
+            const float sl = sk * (float)sm.lsq[lane];
+            for (int a = 0; a < 9; ++a) {
+                float s = 0.0f;
+                for (int i = 0; i < n; ++i) s += sm.Z[a * NMAX + i] * Y32[lane * LD + i];
+                sm.B[a * NMAX + lane] = sl * s;  // sqrt(k-1) Z g(A) diag(sqrt(rho))
+            }
+        }
+        __syncwarp();
+        const float sb = (float)sqrt(beta);
+        for (int m = lane; m < k; m += 32) {
+            float acc[9];
+#pragma unroll
+            for (int a = 0; a < 9; ++a) acc[a] = sm.xbar[a] + sm.zv[a] + sb * sm.dX[a * k + m];
+            for (int i = 0; i < n; ++i) {
+                const float dy = o.dY32[(size_t)sm.lidx[i] * k + m];
+#pragma unroll
+                for (int a = 0; a < 9; ++a) acc[a] += sm.B[a * NMAX + i] * dy;
+            }
+#pragma unroll
+            for (int a = 0; a < 9; ++a) fc[a * plane + m] = acc[a];
+        }
+    } else {
+        // Functions of S directly: 1/lambda for P-tilde, lambda^{-1/2} for W.
+        if (lane < n) {
+            const double lam = A[lane * LD + lane];
+            sm.vu[lane] = sqrt(lam);
+            sm.vinv[lane] = 1.0 / lam;
+            double t = 0.0;
+            for (int c = 0; c < n; ++c) t += Y[c * LD + lane] * sm.vb[c];
+            sm.v1[lane] = t;  // Y^T b
+        }
+        __syncwarp();
+        if (lane < n) {
+            // t2 = f1(S) t1, f1(S)_ii = 1/l_i, f1(S)_ij = -s_ij / (l_i l_j).
+            double t = 0.0;
+            for (int j = 0; j < n; ++j)
+                if (j != lane) t += A[lane * LD + j] * sm.vinv[j] * sm.v1[j];
+            sm.v2[lane] = sm.vinv[lane] * (sm.v1[lane] - t);
+            // f2(S) = S^{-1/2}: diagonal 1/sqrt(l_i), off-diagonal
+            // -s_ij / (sqrt(l_i) sqrt(l_j) (sqrt(l_i) + sqrt(l_j))).
+            const float si = (float)sm.vu[lane];
+            for (int i = 0; i < n; ++i) {
+                float v;
+                if (i == lane) {
+                    v = (float)(1.0 / sm.vu[lane]);
+                } else {
+                    const float sj = (float)sm.vu[i];
+                    v = -(float)A[i * LD + lane] / (si * sj * (si + sj));
+                }
+                F32[i * LD + lane] = v;
+            }
+        }
+        __syncwarp();
+        float* YF = reinterpret_cast<float*>(A);  // S is no longer needed after w-bar
+        if (lane < n) {
+            double t = 0.0;
+            for (int c = 0; c < n; ++c) t += Y[lane * LD + c] * sm.v2[c];
+            sm.vf[lane] = (float)t;  // w-bar
+        }
+        __syncwarp();
+        if (lane < n)
+            for (int i = 0; i < n; ++i) {
+                float s = 0.0f;
+                for (int l = 0; l < n; ++l) s += Y32[i * LD + l] * F32[l * LD + lane];
+                YF[i * LD + lane] = s;
+            }
+        __syncwarp();
+        // T = sqrt(k-1) Y f2(S) Y^T + w-bar 1^T, over F32.
+        if (lane < n)
+            for (int i = 0; i < n; ++i) {
+                float s = 0.0f;
+                for (int l = 0; l < n; ++l) s += YF[i * LD + l] * Y32[lane * LD + l];
+                F32[i * LD + lane] = sk * s + sm.vf[i];
+            }
+        __syncwarp();
+        if (lane < k) {
+            const int m = lane;
+            for (int a = 0; a < 9; ++a) {
+                float s = 0.0f;
+                for (int j = 0; j < k; ++j) s += sm.dX[a * k + j] * F32[j * LD + m];
+                fc[a * plane + m] = sm.xbar[a] + s;
+            }
+        }
+    }
+}
+
+__global__ void to_f32_kernel(const double* __restrict__ src, float* __restrict__ dst, size_t n) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = (float)src[i];
+}
+
 }  // namespace
 
 cudaError_t launch_observe(const void* f, int fp32, int nx, int ny, int k, int npts, const int* ix,
@@ -499,17 +939,21 @@ cudaError_t launch_obs_gram(const double* dY, int nobs, int k, double* G, cudaSt
 
 cudaError_t launch_analyze(void* f, int fp32, int nx, int ny, int k, const ObsParams& o,
                            double d_cut, double beta, int* flags, cudaStream_t s) {
-    const size_t sh = ana_smem_bytes(k, 2 * o.npts);
     const long long cells = (long long)nx * ny;
     if (cells > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     cudaError_t e;
     if (fp32) {
-        e = cudaFuncSetAttribute(analyze_kernel<float, true>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+        if (!o.dY32) return cudaErrorInvalidValue;
+        const size_t nd = (size_t)2 * o.npts * k;
+        to_f32_kernel<<<(unsigned)((nd + 255) / 256), 256, 0, s>>>(o.dY, o.dY32, nd);
+        const size_t sh = mix_smem_bytes(k, 2 * o.npts);
+        e = cudaFuncSetAttribute(analyze_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sh);
         if (e != cudaSuccess) return e;
-        analyze_kernel<float, true><<<(unsigned)cells, 32, sh, s>>>((float*)f, nx, ny, k, o, d_cut,
-                                                                    beta, flags);
+        analyze_mixed_kernel<<<(unsigned)cells, 32, sh, s>>>((float*)f, nx, ny, k, o, d_cut, beta,
+                                                             flags);
     } else {
+        const size_t sh = ana_smem_bytes(k, 2 * o.npts);
         e = cudaFuncSetAttribute(analyze_kernel<double, false>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
         if (e != cudaSuccess) return e;
