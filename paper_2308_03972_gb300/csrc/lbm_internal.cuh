@@ -70,7 +70,9 @@ cudaError_t launch_observe(const void* f, int fp32, int nx, int ny, int k, int n
                            const int* ix, const int* iy, const double* yo, double* dY,
                            double* d, cudaStream_t s);
 cudaError_t launch_obs_gram(const double* dY, int nobs, int k, double* G, cudaStream_t s);
+// Scratch the analysis needs (bytes; 0 for the FP64 path).
+size_t analyze_scratch_bytes(int nx, int ny, int fp32);
 cudaError_t launch_analyze(void* f, int fp32, int nx, int ny, int k, const ObsParams& o,
-                           double d_cut, double beta, int* flags, cudaStream_t s);
+                           double d_cut, double beta, int* flags, float* scratch, cudaStream_t s);
 
 }  // namespace lbmgpu

@@ -31,6 +31,7 @@ struct lbm_ctx {
     double* d = nullptr;   // [2 npts]
     double* G = nullptr;   // [2 npts][2 npts]
     float* dY32 = nullptr; // [2 npts][k] binary32 copy (mixed precision)
+    float* ana_scratch = nullptr;  // analysis scratch (mixed precision)
     double* h_yo = nullptr;  // pinned staging [2 cap]
     int* h_ixy = nullptr;    // pinned staging [2 cap] (ix then iy)
     cudaEvent_t obs_copied = nullptr;  // last staging copy done
@@ -368,9 +369,12 @@ int letkf_analyze(lbm_ctx* c, double d_cut, double beta) {
     if (!(d_cut > 0.0) || !std::isfinite(d_cut)) return fail(c, LBM_EINVAL, "d_cut must be > 0");
     if (!(beta > 0.0) || !std::isfinite(beta)) return fail(c, LBM_EINVAL, "beta must be > 0");
     if (!c->observed) return fail(c, LBM_EINVAL, "letkf_observe must precede letkf_analyze");
+    const size_t scratch = analyze_scratch_bytes(c->nx, c->ny, is_fp32(c));
+    if (scratch && !c->ana_scratch)
+        CK(c, cudaMalloc(&c->ana_scratch, scratch), "allocating analysis scratch");
     ObsParams o{c->npts, c->ix, c->iy, c->dY, c->d, c->G, c->sigma_u, c->sigma_v, c->dY32};
     CK(c, launch_analyze(c->f[c->cur], is_fp32(c), c->nx, c->ny, c->k, o, d_cut, beta, c->flags,
-                         c->stream),
+                         c->ana_scratch, c->stream),
        "launching analysis");
     c->observed = false;
     return LBM_OK;
@@ -441,6 +445,7 @@ void lbm_destroy(lbm_ctx* c) {
     cudaFree(c->force);
     cudaFree(c->flags);
     cudaFree(c->stage);
+    cudaFree(c->ana_scratch);
     free_obs(c);
     if (c->obs_copied) cudaEventDestroy(c->obs_copied);
     delete c;

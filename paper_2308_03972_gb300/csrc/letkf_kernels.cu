@@ -479,185 +479,30 @@ __global__ void __launch_bounds__(32) analyze_kernel(T* __restrict__ f, int nx, 
 
 // ------------------------------------------------------------------ K3, mixed precision
 // The state is binary32 (g = f - w). The eigensolve is FP64-accurate at a
-// fraction of the FP64 work: a binary32 cyclic Jacobi gives a basis X; in
-// FP64 it is re-orthonormalised (Cholesky QR, Y = X L^{-T} with X^T X = L L^T),
-// the Rayleigh-Ritz matrix S = Y^T A Y is formed, and the matrix functions
-// f(A) = Y f(S) Y^T are evaluated to first order in the off-diagonal of S
-// (Daleckii-Krein: f(S)_ii = f(s_ii), f(S)_ij = s_ij f[s_ii, s_jj], with the
-// divided differences in closed form). The error is second order in the
-// off-diagonal of S (relative ~1e-13 at these sizes). Products that apply
-// the transform to the ensemble run in binary32 with binary32 accumulation.
+// fraction of the FP64 work, in two kernels over chunks of grid points:
+//  (A) mixed_jacobi_kernel: the local set, the matrix in FP64 rounded to
+//      binary32, and a binary32 cyclic Jacobi held in registers (no shared
+//      memory, so many warps per SM hide its latency). The basis X goes to a
+//      chunk-sized scratch that stays in L2.
+//  (B) analyze_mixed_kernel: in FP64, re-orthonormalise X (Cholesky QR,
+//      Y = X L^{-T} with X^T X = L L^T), form the Rayleigh-Ritz matrix
+//      S = Y^T A Y, and evaluate f(A) = Y f(S) Y^T to first order in the
+//      off-diagonal of S (Daleckii-Krein: f(S)_ii = f(s_ii),
+//      f(S)_ij = s_ij f[s_ii, s_jj], divided differences in closed form).
+//      The error is second order in the off-diagonal of S (relative ~1e-13
+//      at these sizes). The transform products and the update run in
+//      binary32 with binary32 accumulation.
 
-struct MixSmem {
-    double* A;     // [NMAX][LD] matrix (FP64), then S = Y^T A Y
-    double* Y;     // [NMAX][LD] FP64 basis
-    double* W;     // [NMAX][LD] X^T X, its Cholesky factor, then A Y
-    float* A32;    // [NMAX][LD] binary32 copy for the Jacobi pre-pass (inside W)
-    float* F32;    // [NMAX][LD] f(S) in binary32, then T (inside W)
-    float* U32;    // [NMAX][LD] binary32 rotations, then Y in binary32
-    double* lsq;   // [nl]
-    double* ldh;   // [nl]
-    double* vb;    // [NMAX]
-    double* v1;    // [NMAX]
-    double* v2;    // [NMAX]
-    double* vu;    // [NMAX]
-    double* vinv;  // [NMAX]
-    float* dX;     // [9][k]
-    float* xbar;   // [16]
-    float* Z;      // [9][NMAX]
-    float* B;      // [9][NMAX]
-    float* zv;     // [16]
-    float* vf;     // [NMAX]
-    float* rc;     // [NMAX / 2]
-    float* rs;     // [NMAX / 2]
-    int* rp;       // [NMAX / 2]
-    int* rq;       // [NMAX / 2]
-    int* lidx;     // [nl]
-};
+constexpr int kChunkCells = 16384;  // grid points per (A)+(B) pass
+constexpr int kJacWarps = 4;        // points per block in (A)
+constexpr size_t kXStride = (size_t)NMAX * NMAX;  // floats of X per point
 
-__host__ __device__ inline size_t mix_smem_bytes(int k, int nl) {
-    const size_t d = 3 * (size_t)NMAX * LD + 2 * (size_t)nl + 5 * NMAX;
-    const size_t f = (size_t)NMAX * LD + 9 * (size_t)k + 16 + 18 * NMAX + 16 + NMAX + NMAX;
-    const size_t i = NMAX + (size_t)nl;
-    return d * sizeof(double) + ((f * sizeof(float) + 7) / 8) * 8 + i * sizeof(int);
-}
-
-__device__ inline MixSmem carve_mix(unsigned char* raw, int k, int nl) {
-    MixSmem s;
-    double* p = reinterpret_cast<double*>(raw);
-    s.A = p;
-    p += NMAX * LD;
-    s.Y = p;
-    p += NMAX * LD;
-    s.W = p;
-    s.A32 = reinterpret_cast<float*>(p);
-    s.F32 = reinterpret_cast<float*>(p);
-    p += NMAX * LD;
-    s.lsq = p;
-    p += nl;
-    s.ldh = p;
-    p += nl;
-    s.vb = p;
-    p += NMAX;
-    s.v1 = p;
-    p += NMAX;
-    s.v2 = p;
-    p += NMAX;
-    s.vu = p;
-    p += NMAX;
-    s.vinv = p;
-    p += NMAX;
-    float* q = reinterpret_cast<float*>(p);
-    s.U32 = q;
-    q += NMAX * LD;
-    s.dX = q;
-    q += 9 * k;
-    s.xbar = q;
-    q += 16;
-    s.Z = q;
-    q += 9 * NMAX;
-    s.B = q;
-    q += 9 * NMAX;
-    s.zv = q;
-    q += 16;
-    s.vf = q;
-    q += NMAX;
-    s.rc = q;
-    q += NMAX / 2;
-    s.rs = q;
-    q += NMAX / 2;
-    const size_t fbytes = (size_t)(q - reinterpret_cast<float*>(p)) * sizeof(float);
-    int* ip = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(p) + ((fbytes + 7) / 8) * 8);
-    s.rp = ip;
-    ip += NMAX / 2;
-    s.rq = ip;
-    ip += NMAX / 2;
-    s.lidx = ip;
-    return s;
-}
-
-// FP64 refinement of the binary32 basis U32 of the symmetric matrix A:
-// Y = X L^{-T} (X = U32, X^T X = L L^T), then A <- S = Y^T A Y.
-__device__ void refine_basis(double* A, double* Y, double* W, double* vinv, const float* U32,
-                             int n, int lane) {
-    if (lane < n)
-        for (int c = 0; c < n; ++c) Y[lane * LD + c] = (double)U32[lane * LD + c];
-    __syncwarp();
-    if (lane < n)
-        for (int i = 0; i < n; ++i) {
-            double s = 0.0;
-            for (int r = 0; r < n; ++r) s += Y[r * LD + i] * Y[r * LD + lane];
-            W[i * LD + lane] = s;
-        }
-    __syncwarp();
-    // Cholesky factor of X^T X (close to I), lower triangle of W.
-    for (int j = 0; j < n; ++j) {
-        if (lane == j) {
-            double s = W[j * LD + j];
-            for (int c = 0; c < j; ++c) s -= W[j * LD + c] * W[j * LD + c];
-            const double inv = rsqrt(s);
-            W[j * LD + j] = s * inv;
-            vinv[j] = inv;
-        }
-        __syncwarp();
-        if (lane > j && lane < n) {
-            double s = W[lane * LD + j];
-            for (int c = 0; c < j; ++c) s -= W[lane * LD + c] * W[j * LD + c];
-            W[lane * LD + j] = s * vinv[j];
-        }
-        __syncwarp();
-    }
-    // Y <- X L^{-T}, row `lane` by forward substitution.
-    if (lane < n)
-        for (int j = 0; j < n; ++j) {
-            double z = Y[lane * LD + j];
-            for (int c = 0; c < j; ++c) z -= Y[lane * LD + c] * W[j * LD + c];
-            Y[lane * LD + j] = z * vinv[j];
-        }
-    __syncwarp();
-    // W = A Y, then A <- Y^T W.
-    if (lane < n)
-        for (int i = 0; i < n; ++i) {
-            double s = 0.0;
-            for (int c = 0; c < n; ++c) s += A[i * LD + c] * Y[c * LD + lane];
-            W[i * LD + lane] = s;
-        }
-    __syncwarp();
-    if (lane < n)
-        for (int i = 0; i < n; ++i) {
-            double s = 0.0;
-            for (int r = 0; r < n; ++r) s += Y[r * LD + i] * W[r * LD + lane];
-            A[i * LD + lane] = s;
-        }
-    __syncwarp();
-}
-
-__global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f, int nx, int ny,
-                                                           int k, ObsParams o, double d_cut,
-                                                           double beta, int* __restrict__ flags) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int nobs = 2 * o.npts;
-    MixSmem sm = carve_mix(smem_raw, k, nobs);
-    const int lane = threadIdx.x;
-    const int cell = blockIdx.x;
-    const int x = cell % nx, y = cell / nx;
-    const size_t plane = (size_t)nx * ny * k;
-    float* fc = f + (size_t)cell * k;
-
-    // Ensemble mean and perturbations in binary32.
-    for (int a = 0; a < 9; ++a) {
-        float s = 0.0f;
-        for (int m = lane; m < k; m += 32) {
-            const float xv = fc[a * plane + m];
-            sm.dX[a * k + m] = xv;
-            s += xv;
-        }
-        const float mean = warp_sum(s) / (float)k;
-        for (int m = lane; m < k; m += 32) sm.dX[a * k + m] -= mean;
-        if (lane == 0) sm.xbar[a] = mean;
-    }
-
-    // Local observation set (FP64 decisions, as in the FP64 kernel).
+// Local observation set of grid point (x, y), in increasing point order:
+// point j is in range when r / d_cut < 2 and G(r / d_cut) > 0; it gives the
+// two scalars 2j (u) and 2j+1 (v) with sqrt(rho) = sqrt(G) / sigma.
+// Returns the number of scalars p. Warp-cooperative.
+__device__ int local_set(const ObsParams& o, int x, int y, int nx, int ny, double d_cut, int lane,
+                         int* lidx, double* lsq) {
     int count = 0;
     for (int j0 = 0; j0 < o.npts; j0 += 32) {
         const int j = j0 + lane;
@@ -677,15 +522,386 @@ __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f
         if (in) {
             const int pos = count + __popc(bal & ((1u << lane) - 1u));
             const double sg = sqrt(g);
-            sm.lidx[2 * pos] = 2 * j;
-            sm.lidx[2 * pos + 1] = 2 * j + 1;
-            sm.lsq[2 * pos] = sg / o.sigma_u;
-            sm.lsq[2 * pos + 1] = sg / o.sigma_v;
+            lidx[2 * pos] = 2 * j;
+            lidx[2 * pos + 1] = 2 * j + 1;
+            lsq[2 * pos] = sg / o.sigma_u;
+            lsq[2 * pos + 1] = sg / o.sigma_v;
         }
         count += __popc(bal);
     }
     __syncwarp();
-    const int p = 2 * count;
+    return 2 * count;
+}
+
+// Binary32 cyclic Jacobi with the column of A and of U held in registers.
+// Lane a owns player (column) a of an NS-player round-robin tournament
+// (NS even, NS >= n; players n..NS-1 are zero padding). The rows of A are
+// kept in tournament-position order: in every round position t meets
+// position NS-1-t, so a row rotation always acts on the fixed register pair
+// (t, NS-1-t), and after the round the rows move one position
+// (q -> q-1 for q >= 2, 1 -> NS-1, 0 stays), a fixed register permutation.
+// Column rotations pair a lane with its partner through warp shuffles. The
+// player at position q in round r is 0 for q = 0, else 1 + (q-1+r) mod (NS-1).
+// On entry a[i] = A[i][lane] (row i at position i); on return u[i] holds
+// U[i][lane], the eigenvector of player `lane`.
+template <int NS>
+__device__ bool jacobi32_reg(float (&a)[NS], float (&u)[NS], int lane, float rel, int max_sweeps) {
+#pragma unroll
+    for (int i = 0; i < NS; ++i) u[i] = (i == lane) ? 1.0f : 0.0f;
+    float fro = 0.0f;
+#pragma unroll
+    for (int i = 0; i < NS; ++i) fro += a[i] * a[i];
+    fro = warp_sum(fro);
+    const float thresh = rel * sqrtf(fro);
+    const int m1 = NS - 1;
+    int r = 0;  // round index modulo NS - 1
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+        bool any_sweep = false;
+        for (int round = 0; round < m1; ++round) {
+            const int q = (lane == 0) ? 0 : 1 + ((lane - 1 - r + 2 * m1) % m1);
+            const int qp = m1 - q;
+            const int partner = (qp == 0) ? 0 : 1 + ((qp - 1 + r) % m1);
+            const bool pside = q < NS / 2;
+            float d = 0.0f, off = 0.0f;
+#pragma unroll
+            for (int i = 0; i < NS; ++i) {
+                if (i == q) d = a[i];
+                if (i == qp) off = a[i];
+            }
+            const float dp = __shfl_sync(kFull, d, partner & 31);
+            // Rotation of my pair (symmetric 2 x 2 Schur), on the p side.
+            float c = 1.0f, s = 0.0f;
+            bool rot = false;
+            if (pside && lane < NS && fabsf(off) > thresh) {
+                const float tau = (dp - d) / (2.0f * off);
+                const float t = (tau >= 0.0f ? 1.0f : -1.0f) / (fabsf(tau) + sqrtf(1.0f + tau * tau));
+                c = 1.0f / sqrtf(1.0f + t * t);
+                s = t * c;
+                rot = true;
+            }
+            if (__ballot_sync(kFull, rot) != 0u) {
+                any_sweep = true;
+                // Row rotations: position t (row p) with position NS-1-t (row q).
+#pragma unroll
+                for (int t = 0; t < NS / 2; ++t) {
+                    const int pl = (t == 0) ? 0 : 1 + ((t - 1 + r) % m1);
+                    const float ct = __shfl_sync(kFull, c, pl);
+                    const float st = __shfl_sync(kFull, s, pl);
+                    const float x0 = a[t], x1 = a[NS - 1 - t];
+                    a[t] = ct * x0 - st * x1;
+                    a[NS - 1 - t] = st * x0 + ct * x1;
+                }
+                // Column rotations with the partner lane.
+                const int pl_mine = pside ? lane : partner;
+                const float cm = __shfl_sync(kFull, c, pl_mine & 31);
+                const float sm_ = __shfl_sync(kFull, s, pl_mine & 31);
+                const float sg = pside ? -sm_ : sm_;
+#pragma unroll
+                for (int i = 0; i < NS; ++i) {
+                    const float th = __shfl_sync(kFull, a[i], partner & 31);
+                    a[i] = cm * a[i] + sg * th;
+                    const float tu = __shfl_sync(kFull, u[i], partner & 31);
+                    u[i] = cm * u[i] + sg * tu;
+                }
+                // The rotated off-diagonal entry is zero by construction.
+                if (sm_ != 0.0f) {
+#pragma unroll
+                    for (int i = 0; i < NS; ++i)
+                        if (i == qp) a[i] = 0.0f;
+                }
+            }
+            // Rows move one tournament position.
+            {
+                const float a1 = a[1];
+#pragma unroll
+                for (int i = 1; i < NS - 1; ++i) a[i] = a[i + 1];
+                a[NS - 1] = a1;
+            }
+            r = (r + 1 == m1) ? 0 : r + 1;
+        }
+        if (!any_sweep) return true;
+    }
+    return false;
+}
+
+// One point of kernel (A): build column `lane` of the matrix (FP64, rounded
+// to binary32), run the Jacobi, store X = U (row i of X at Xp + i * NMAX).
+template <int NS>
+__device__ void jacobi_point(const ObsParams& o, int k, int n, int p, bool obs_space, double aa,
+                             const int* lidx, const double* lsq, int lane, float* __restrict__ Xp,
+                             int* flags) {
+    const int nobs = 2 * o.npts;
+    float a[NS], u[NS];
+    if (obs_space) {
+        const bool own = lane < n;
+        const int ol = own ? lidx[lane] : 0;
+        const double sl = own ? lsq[lane] : 0.0;
+#pragma unroll
+        for (int i = 0; i < NS; ++i)
+            a[i] = (own && i < n) ? (float)(lsq[i] * o.G[(size_t)lidx[i] * nobs + ol] * sl) : 0.0f;
+    } else {
+        // C = a I + Yh^T Yh in FP64; lane owns column `lane`.
+#pragma unroll
+        for (int i = 0; i < NS; ++i) a[i] = 0.0f;
+        if (lane < n) {
+#pragma unroll
+            for (int i = 0; i < NS; ++i) {
+                if (i >= n) break;
+                double s = (i == lane) ? aa : 0.0;
+                for (int l = 0; l < p; ++l) {
+                    const double* row = o.dY + (size_t)lidx[l] * k;
+                    s += lsq[l] * lsq[l] * row[i] * row[lane];
+                }
+                a[i] = (float)s;
+            }
+        }
+    }
+    if (!jacobi32_reg<NS>(a, u, lane, 3e-8f, kMaxSweeps)) {
+        if (lane == 0) atomicOr(flags, FLAG_NOCONV);
+    }
+    if (lane < n) {
+#pragma unroll
+        for (int i = 0; i < NS; ++i)
+            if (i < n) Xp[(size_t)i * NMAX + lane] = u[i];
+    }
+}
+
+__global__ void __launch_bounds__(32 * kJacWarps) mixed_jacobi_kernel(int nx, int ny, int k,
+                                                                      ObsParams o, double d_cut,
+                                                                      double beta, int cell0,
+                                                                      int ncell,
+                                                                      float* __restrict__ X,
+                                                                      int* __restrict__ flags) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nobs = 2 * o.npts;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double* lsq = reinterpret_cast<double*>(smem_raw) + (size_t)w * nobs;
+    int* lidx = reinterpret_cast<int*>(reinterpret_cast<double*>(smem_raw) + (size_t)kJacWarps * nobs) +
+                (size_t)w * nobs;
+    const int li = blockIdx.x * kJacWarps + w;
+    if (li >= ncell) return;
+    const int cell = cell0 + li;
+    const int x = cell % nx, y = cell / nx;
+    const int p = local_set(o, x, y, nx, ny, d_cut, lane, lidx, lsq);
+    if (p == 0) return;
+    const bool obs_space = p < k;
+    const int n = obs_space ? p : k;
+    if (n > NMAX) return;  // reported by kernel (B)
+    const double aa = (k - 1) / beta;
+    float* Xp = X + (size_t)li * kXStride;
+    if (n <= 8)
+        jacobi_point<8>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, flags);
+    else if (n <= 16)
+        jacobi_point<16>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, flags);
+    else if (n <= 24)
+        jacobi_point<24>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, flags);
+    else if (n <= 28)
+        jacobi_point<28>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, flags);
+    else
+        jacobi_point<32>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, flags);
+}
+
+struct MixSmem {
+    double* A;     // [NMAX][LD] matrix (FP64), then S = Y^T A Y
+    double* Y;     // [NMAX][LD] FP64 basis
+    double* W;     // [NMAX][LD] X^T X, its Cholesky factor, then A Y
+    float* F32;    // [NMAX][LD] f(S) in binary32, then T (inside W)
+    float* Y32;    // [NMAX][LD] Y in binary32
+    double* lsq;   // [nl]
+    double* ldh;   // [nl]
+    double* vb;    // [NMAX]
+    double* v1;    // [NMAX]
+    double* v2;    // [NMAX]
+    double* vu;    // [NMAX]
+    double* vinv;  // [NMAX]
+    float* dX;     // [9][k]
+    float* xbar;   // [16]
+    float* Z;      // [9][NMAX]
+    float* B;      // [9][NMAX]
+    float* zv;     // [16]
+    float* vf;     // [NMAX]
+    int* lidx;     // [nl]
+};
+
+__host__ __device__ inline size_t mix_smem_bytes(int k, int nl) {
+    const size_t d = 3 * (size_t)NMAX * LD + 2 * (size_t)nl + 5 * NMAX;
+    const size_t f = (size_t)NMAX * LD + 9 * (size_t)k + 16 + 18 * NMAX + 16 + NMAX;
+    return d * sizeof(double) + ((f * sizeof(float) + 7) / 8) * 8 + (size_t)nl * sizeof(int);
+}
+
+__device__ inline MixSmem carve_mix(unsigned char* raw, int k, int nl) {
+    MixSmem s;
+    double* p = reinterpret_cast<double*>(raw);
+    s.A = p;
+    p += NMAX * LD;
+    s.Y = p;
+    p += NMAX * LD;
+    s.W = p;
+    s.F32 = reinterpret_cast<float*>(p);
+    p += NMAX * LD;
+    s.lsq = p;
+    p += nl;
+    s.ldh = p;
+    p += nl;
+    s.vb = p;
+    p += NMAX;
+    s.v1 = p;
+    p += NMAX;
+    s.v2 = p;
+    p += NMAX;
+    s.vu = p;
+    p += NMAX;
+    s.vinv = p;
+    p += NMAX;
+    float* q = reinterpret_cast<float*>(p);
+    s.Y32 = q;
+    q += NMAX * LD;
+    s.dX = q;
+    q += 9 * k;
+    s.xbar = q;
+    q += 16;
+    s.Z = q;
+    q += 9 * NMAX;
+    s.B = q;
+    q += 9 * NMAX;
+    s.zv = q;
+    q += 16;
+    s.vf = q;
+    q += NMAX;
+    const size_t fbytes = (size_t)(q - reinterpret_cast<float*>(p)) * sizeof(float);
+    s.lidx = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(p) + ((fbytes + 7) / 8) * 8);
+    return s;
+}
+
+// FP64 refinement of the basis already in Y (columns = approximate
+// eigenvectors of the symmetric matrix A): Y <- Y L^{-T} with Y^T Y = L L^T,
+// then A <- S = Y^T A Y. Dot products run four output entries at a time.
+__device__ void refine_basis(double* A, double* Y, double* W, double* vinv, int n, int lane) {
+    // W = Y^T Y, column `lane`.
+    if (lane < n)
+        for (int i0 = 0; i0 < n; i0 += 4) {
+            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+            for (int r = 0; r < n; ++r) {
+                const double yl = Y[r * LD + lane];
+                const double* yr = Y + r * LD + i0;
+                s0 += yr[0] * yl;
+                s1 += yr[1] * yl;
+                s2 += yr[2] * yl;
+                s3 += yr[3] * yl;
+            }
+            W[i0 * LD + lane] = s0;
+            if (i0 + 1 < n) W[(i0 + 1) * LD + lane] = s1;
+            if (i0 + 2 < n) W[(i0 + 2) * LD + lane] = s2;
+            if (i0 + 3 < n) W[(i0 + 3) * LD + lane] = s3;
+        }
+    __syncwarp();
+    // Cholesky factor of Y^T Y (close to I), lower triangle of W.
+    for (int j = 0; j < n; ++j) {
+        if (lane == j) {
+            double s0 = W[j * LD + j], s1 = 0.0;
+            int c = 0;
+            for (; c + 1 < j; c += 2) {
+                s0 -= W[j * LD + c] * W[j * LD + c];
+                s1 -= W[j * LD + c + 1] * W[j * LD + c + 1];
+            }
+            if (c < j) s0 -= W[j * LD + c] * W[j * LD + c];
+            const double s = s0 + s1;
+            const double inv = rsqrt(s);
+            W[j * LD + j] = s * inv;
+            vinv[j] = inv;
+        }
+        __syncwarp();
+        if (lane > j && lane < n) {
+            double s0 = W[lane * LD + j], s1 = 0.0;
+            int c = 0;
+            for (; c + 1 < j; c += 2) {
+                s0 -= W[lane * LD + c] * W[j * LD + c];
+                s1 -= W[lane * LD + c + 1] * W[j * LD + c + 1];
+            }
+            if (c < j) s0 -= W[lane * LD + c] * W[j * LD + c];
+            W[lane * LD + j] = (s0 + s1) * vinv[j];
+        }
+        __syncwarp();
+    }
+    // Y <- Y L^{-T}, row `lane` by forward substitution.
+    if (lane < n)
+        for (int j = 0; j < n; ++j) {
+            double z0 = Y[lane * LD + j], z1 = 0.0;
+            int c = 0;
+            for (; c + 1 < j; c += 2) {
+                z0 -= Y[lane * LD + c] * W[j * LD + c];
+                z1 -= Y[lane * LD + c + 1] * W[j * LD + c + 1];
+            }
+            if (c < j) z0 -= Y[lane * LD + c] * W[j * LD + c];
+            Y[lane * LD + j] = (z0 + z1) * vinv[j];
+        }
+    __syncwarp();
+    // W = A Y, column `lane`.
+    if (lane < n)
+        for (int i0 = 0; i0 < n; i0 += 4) {
+            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+            for (int c = 0; c < n; ++c) {
+                const double yc = Y[c * LD + lane];
+                s0 += A[i0 * LD + c] * yc;
+                s1 += A[(i0 + 1) * LD + c] * yc;
+                s2 += A[(i0 + 2) * LD + c] * yc;
+                s3 += A[(i0 + 3) * LD + c] * yc;
+            }
+            W[i0 * LD + lane] = s0;
+            if (i0 + 1 < n) W[(i0 + 1) * LD + lane] = s1;
+            if (i0 + 2 < n) W[(i0 + 2) * LD + lane] = s2;
+            if (i0 + 3 < n) W[(i0 + 3) * LD + lane] = s3;
+        }
+    __syncwarp();
+    // A <- S = Y^T W, column `lane`.
+    if (lane < n)
+        for (int i0 = 0; i0 < n; i0 += 4) {
+            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+            for (int r = 0; r < n; ++r) {
+                const double wl = W[r * LD + lane];
+                const double* yr = Y + r * LD + i0;
+                s0 += yr[0] * wl;
+                s1 += yr[1] * wl;
+                s2 += yr[2] * wl;
+                s3 += yr[3] * wl;
+            }
+            A[i0 * LD + lane] = s0;
+            if (i0 + 1 < n) A[(i0 + 1) * LD + lane] = s1;
+            if (i0 + 2 < n) A[(i0 + 2) * LD + lane] = s2;
+            if (i0 + 3 < n) A[(i0 + 3) * LD + lane] = s3;
+        }
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f, int nx, int ny,
+                                                           int k, ObsParams o, double d_cut,
+                                                           double beta, int cell0,
+                                                           const float* __restrict__ X,
+                                                           int* __restrict__ flags) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nobs = 2 * o.npts;
+    MixSmem sm = carve_mix(smem_raw, k, nobs);
+    const int lane = threadIdx.x;
+    const int li = blockIdx.x;
+    const int cell = cell0 + li;
+    const int x = cell % nx, y = cell / nx;
+    const size_t plane = (size_t)nx * ny * k;
+    float* fc = f + (size_t)cell * k;
+
+    // Ensemble mean and perturbations in binary32.
+    for (int a = 0; a < 9; ++a) {
+        float s = 0.0f;
+        for (int m = lane; m < k; m += 32) {
+            const float xv = fc[a * plane + m];
+            sm.dX[a * k + m] = xv;
+            s += xv;
+        }
+        const float mean = warp_sum(s) / (float)k;
+        for (int m = lane; m < k; m += 32) sm.dX[a * k + m] -= mean;
+        if (lane == 0) sm.xbar[a] = mean;
+    }
+
+    const int p = local_set(o, x, y, nx, ny, d_cut, lane, sm.lidx, sm.lsq);
     for (int i = lane; i < p; i += 32) sm.ldh[i] = sm.lsq[i] * o.d[sm.lidx[i]];
     __syncwarp();
 
@@ -706,44 +922,37 @@ __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f
     double* Y = sm.Y;
 
     // The symmetric matrix in FP64: A = Yh Yh^T (observation space) or
-    // C = a I + Yh^T Yh with b = Yh^T d-hat (ensemble space).
-    if (obs_space) {
-        if (lane < n) {
+    // C = a I + Yh^T Yh with b = Yh^T d-hat (ensemble space); the basis X
+    // from kernel (A).
+    const float* Xp = X + (size_t)li * kXStride;
+    if (lane < n) {
+        if (obs_space) {
             const int ol = sm.lidx[lane];
             const double sl = sm.lsq[lane];
             for (int i = 0; i < n; ++i)
                 A[i * LD + lane] = sm.lsq[i] * o.G[(size_t)sm.lidx[i] * nobs + ol] * sl;
-        }
-    } else if (lane < n) {
-        double bj = 0.0;
-        for (int i = 0; i < n; ++i) {
-            double s = 0.0;
-            for (int l = 0; l < p; ++l) {
-                const double* row = o.dY + (size_t)sm.lidx[l] * k;
-                s += sm.lsq[l] * sm.lsq[l] * row[i] * row[lane];
+        } else {
+            double bj = 0.0;
+            for (int i = 0; i < n; ++i) {
+                double s = 0.0;
+                for (int l = 0; l < p; ++l) {
+                    const double* row = o.dY + (size_t)sm.lidx[l] * k;
+                    s += sm.lsq[l] * sm.lsq[l] * row[i] * row[lane];
+                }
+                A[i * LD + lane] = s + (i == lane ? aa : 0.0);
             }
-            A[i * LD + lane] = s + (i == lane ? aa : 0.0);
+            for (int l = 0; l < p; ++l) bj += sm.lsq[l] * o.dY[(size_t)sm.lidx[l] * k + lane] * sm.ldh[l];
+            sm.vb[lane] = bj;
         }
-        for (int l = 0; l < p; ++l) bj += sm.lsq[l] * o.dY[(size_t)sm.lidx[l] * k + lane] * sm.ldh[l];
-        sm.vb[lane] = bj;
+        for (int i = 0; i < n; ++i) Y[i * LD + lane] = (double)Xp[(size_t)i * NMAX + lane];
     }
     __syncwarp();
-    if (lane < n)
-        for (int i = 0; i < n; ++i) {
-            sm.A32[i * LD + lane] = (float)A[i * LD + lane];
-            sm.U32[i * LD + lane] = (i == lane) ? 1.0f : 0.0f;
-        }
-    __syncwarp();
-    if (!jacobi_warp<float>(sm.A32, sm.U32, n, lane, sm.rc, sm.rs, sm.rp, sm.rq, 3e-8f, kMaxSweeps)) {
-        if (lane == 0) atomicOr(flags, FLAG_NOCONV);
-    }
-    __syncwarp();
-    refine_basis(A, Y, sm.W, sm.vinv, sm.U32, n, lane);
+    refine_basis(A, Y, sm.W, sm.vinv, n, lane);
     // Y in binary32 for the transform products.
     if (lane < n)
-        for (int c = 0; c < n; ++c) sm.U32[lane * LD + c] = (float)Y[lane * LD + c];
+        for (int c = 0; c < n; ++c) sm.Y32[lane * LD + c] = (float)Y[lane * LD + c];
     __syncwarp();
-    float* Y32 = sm.U32;
+    float* Y32 = sm.Y32;
     float* F32 = sm.F32;
     const float sk = (float)sqrt((double)(k - 1));
 
@@ -755,10 +964,14 @@ __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f
             const double u = sqrt(aa + A[lane * LD + lane]);
             sm.vu[lane] = u;
             sm.vinv[lane] = 1.0 / (u * (u + r));  // alpha_i
-            // t1 = Y^T d-hat
-            double t = 0.0;
-            for (int c = 0; c < n; ++c) t += Y[c * LD + lane] * sm.ldh[c];
-            sm.v1[lane] = t;
+            double t0 = 0.0, t1 = 0.0;  // Y^T d-hat
+            int c = 0;
+            for (; c + 1 < n; c += 2) {
+                t0 += Y[c * LD + lane] * sm.ldh[c];
+                t1 += Y[(c + 1) * LD + lane] * sm.ldh[c + 1];
+            }
+            if (c < n) t0 += Y[c * LD + lane] * sm.ldh[c];
+            sm.v1[lane] = t0 + t1;
         }
         __syncwarp();
         if (lane < n) {
@@ -790,17 +1003,27 @@ __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f
         }
         __syncwarp();
         if (lane < n) {
-            double t = 0.0;
-            for (int c = 0; c < n; ++c) t += Y[lane * LD + c] * sm.v2[c];
-            sm.vf[lane] = (float)t;  // v = (a I + A)^{-1} d-hat
-            // Z = dX Yh^T, column `lane`.
-            const float* row = o.dY32 + (size_t)sm.lidx[lane] * k;
-            const float sl = (float)sm.lsq[lane];
-            for (int a = 0; a < 9; ++a) {
-                float s = 0.0f;
-                for (int m = 0; m < k; ++m) s += sm.dX[a * k + m] * row[m];
-                sm.Z[a * NMAX + lane] = sl * s;
+            double t0 = 0.0, t1 = 0.0;
+            int c = 0;
+            for (; c + 1 < n; c += 2) {
+                t0 += Y[lane * LD + c] * sm.v2[c];
+                t1 += Y[lane * LD + c + 1] * sm.v2[c + 1];
             }
+            if (c < n) t0 += Y[lane * LD + c] * sm.v2[c];
+            sm.vf[lane] = (float)(t0 + t1);  // v = (a I + A)^{-1} d-hat
+            // Z = dX Yh^T, column `lane`: nine accumulators over members.
+            const float* row = o.dY32 + (size_t)sm.lidx[lane] * k;
+            float acc[9];
+#pragma unroll
+            for (int a = 0; a < 9; ++a) acc[a] = 0.0f;
+            for (int m = 0; m < k; ++m) {
+                const float dy = row[m];
+#pragma unroll
+                for (int a = 0; a < 9; ++a) acc[a] += sm.dX[a * k + m] * dy;
+            }
+            const float sl = (float)sm.lsq[lane];
+#pragma unroll
+            for (int a = 0; a < 9; ++a) sm.Z[a * NMAX + lane] = sl * acc[a];
         }
         __syncwarp();
         if (lane < 9) {
@@ -808,27 +1031,44 @@ __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f
             for (int i = 0; i < n; ++i) s += sm.Z[lane * NMAX + i] * sm.vf[i];
             sm.zv[lane] = s;
         }
-        if (lane < n)
-            for (int a = 0; a < 9; ++a) {
-                float s = 0.0f;
-                for (int c = 0; c < n; ++c) s += sm.Z[a * NMAX + c] * Y32[c * LD + lane];
-                sm.B[a * NMAX + lane] = s;  // Z Y
+        if (lane < n) {
+            float acc[9];
+#pragma unroll
+            for (int a = 0; a < 9; ++a) acc[a] = 0.0f;
+            for (int c = 0; c < n; ++c) {
+                const float yc = Y32[c * LD + lane];
+#pragma unroll
+                for (int a = 0; a < 9; ++a) acc[a] += sm.Z[a * NMAX + c] * yc;
             }
-        __syncwarp();
-        if (lane < n)
-            for (int a = 0; a < 9; ++a) {
-                float s = 0.0f;
-                for (int j = 0; j < n; ++j) s += sm.B[a * NMAX + j] * F32[j * LD + lane];
-                sm.Z[a * NMAX + lane] = s;  // Z Y g(S)
-            }
+#pragma unroll
+            for (int a = 0; a < 9; ++a) sm.B[a * NMAX + lane] = acc[a];  // Z Y
+        }
         __syncwarp();
         if (lane < n) {
-            const float sl = sk * (float)sm.lsq[lane];
-            for (int a = 0; a < 9; ++a) {
-                float s = 0.0f;
-                for (int i = 0; i < n; ++i) s += sm.Z[a * NMAX + i] * Y32[lane * LD + i];
-                sm.B[a * NMAX + lane] = sl * s;  // sqrt(k-1) Z g(A) diag(sqrt(rho))
+            float acc[9];
+#pragma unroll
+            for (int a = 0; a < 9; ++a) acc[a] = 0.0f;
+            for (int j = 0; j < n; ++j) {
+                const float fj = F32[j * LD + lane];
+#pragma unroll
+                for (int a = 0; a < 9; ++a) acc[a] += sm.B[a * NMAX + j] * fj;
             }
+#pragma unroll
+            for (int a = 0; a < 9; ++a) sm.Z[a * NMAX + lane] = acc[a];  // Z Y g(S)
+        }
+        __syncwarp();
+        if (lane < n) {
+            float acc[9];
+#pragma unroll
+            for (int a = 0; a < 9; ++a) acc[a] = 0.0f;
+            for (int i = 0; i < n; ++i) {
+                const float yi = Y32[lane * LD + i];
+#pragma unroll
+                for (int a = 0; a < 9; ++a) acc[a] += sm.Z[a * NMAX + i] * yi;
+            }
+            const float sl = sk * (float)sm.lsq[lane];
+#pragma unroll
+            for (int a = 0; a < 9; ++a) sm.B[a * NMAX + lane] = sl * acc[a];  // sqrt(k-1) Z g(A) sqrt(rho)
         }
         __syncwarp();
         const float sb = (float)sqrt(beta);
@@ -937,21 +1177,38 @@ cudaError_t launch_obs_gram(const double* dY, int nobs, int k, double* G, cudaSt
     return cudaGetLastError();
 }
 
+size_t analyze_scratch_bytes(int nx, int ny, int fp32) {
+    if (!fp32) return 0;
+    const long long cells = (long long)nx * ny;
+    const long long chunk = cells < kChunkCells ? cells : kChunkCells;
+    return (size_t)chunk * kXStride * sizeof(float);
+}
+
 cudaError_t launch_analyze(void* f, int fp32, int nx, int ny, int k, const ObsParams& o,
-                           double d_cut, double beta, int* flags, cudaStream_t s) {
+                           double d_cut, double beta, int* flags, float* scratch,
+                           cudaStream_t s) {
     const long long cells = (long long)nx * ny;
     if (cells > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     cudaError_t e;
     if (fp32) {
-        if (!o.dY32) return cudaErrorInvalidValue;
+        if (!o.dY32 || !scratch) return cudaErrorInvalidValue;
         const size_t nd = (size_t)2 * o.npts * k;
         to_f32_kernel<<<(unsigned)((nd + 255) / 256), 256, 0, s>>>(o.dY, o.dY32, nd);
-        const size_t sh = mix_smem_bytes(k, 2 * o.npts);
-        e = cudaFuncSetAttribute(analyze_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sh);
+        const size_t shA = (size_t)kJacWarps * 2 * o.npts * (sizeof(double) + sizeof(int));
+        const size_t shB = mix_smem_bytes(k, 2 * o.npts);
+        e = cudaFuncSetAttribute(mixed_jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)shA);
         if (e != cudaSuccess) return e;
-        analyze_mixed_kernel<<<(unsigned)cells, 32, sh, s>>>((float*)f, nx, ny, k, o, d_cut, beta,
-                                                             flags);
+        e = cudaFuncSetAttribute(analyze_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)shB);
+        if (e != cudaSuccess) return e;
+        for (long long c0 = 0; c0 < cells; c0 += kChunkCells) {
+            const int nc = (int)((cells - c0) < kChunkCells ? (cells - c0) : kChunkCells);
+            mixed_jacobi_kernel<<<(unsigned)((nc + kJacWarps - 1) / kJacWarps), 32 * kJacWarps, shA,
+                                  s>>>(nx, ny, k, o, d_cut, beta, (int)c0, nc, scratch, flags);
+            analyze_mixed_kernel<<<(unsigned)nc, 32, shB, s>>>((float*)f, nx, ny, k, o, d_cut, beta,
+                                                               (int)c0, scratch, flags);
+        }
     } else {
         const size_t sh = ana_smem_bytes(k, 2 * o.npts);
         e = cudaFuncSetAttribute(analyze_kernel<double, false>,
