@@ -70,9 +70,17 @@ cudaError_t launch_observe(const void* f, int fp32, int nx, int ny, int k, int n
                            const int* ix, const int* iy, const double* yo, double* dY,
                            double* d, cudaStream_t s);
 cudaError_t launch_obs_gram(const double* dY, int nobs, int k, double* G, cudaStream_t s);
+// Second stream and events the mixed-precision analysis uses to overlap its
+// binary32 Jacobi pass over one chunk of grid points with the FP64
+// refinement of the previous chunk.
+struct AnalyzeAux {
+    cudaStream_t s2;
+    cudaEvent_t start, jac_done[2], ref_done[2];
+};
 // Scratch the analysis needs (bytes; 0 for the FP64 path).
 size_t analyze_scratch_bytes(int nx, int ny, int fp32);
 cudaError_t launch_analyze(void* f, int fp32, int nx, int ny, int k, const ObsParams& o,
-                           double d_cut, double beta, int* flags, float* scratch, cudaStream_t s);
+                           double d_cut, double beta, int* flags, float* scratch,
+                           const AnalyzeAux* aux, cudaStream_t s);
 
 }  // namespace lbmgpu

@@ -32,6 +32,8 @@ struct lbm_ctx {
     double* G = nullptr;   // [2 npts][2 npts]
     float* dY32 = nullptr; // [2 npts][k] binary32 copy (mixed precision)
     float* ana_scratch = nullptr;  // analysis scratch (mixed precision)
+    AnalyzeAux aux{};              // second stream + events (mixed precision)
+    bool aux_ready = false;
     double* h_yo = nullptr;  // pinned staging [2 cap]
     int* h_ixy = nullptr;    // pinned staging [2 cap] (ix then iy)
     cudaEvent_t obs_copied = nullptr;  // last staging copy done
@@ -372,9 +374,18 @@ int letkf_analyze(lbm_ctx* c, double d_cut, double beta) {
     const size_t scratch = analyze_scratch_bytes(c->nx, c->ny, is_fp32(c));
     if (scratch && !c->ana_scratch)
         CK(c, cudaMalloc(&c->ana_scratch, scratch), "allocating analysis scratch");
+    if (is_fp32(c) && !c->aux_ready) {
+        CK(c, cudaStreamCreateWithFlags(&c->aux.s2, cudaStreamNonBlocking), "creating stream");
+        CK(c, cudaEventCreateWithFlags(&c->aux.start, cudaEventDisableTiming), "creating event");
+        for (int b = 0; b < 2; ++b) {
+            CK(c, cudaEventCreateWithFlags(&c->aux.jac_done[b], cudaEventDisableTiming), "creating event");
+            CK(c, cudaEventCreateWithFlags(&c->aux.ref_done[b], cudaEventDisableTiming), "creating event");
+        }
+        c->aux_ready = true;
+    }
     ObsParams o{c->npts, c->ix, c->iy, c->dY, c->d, c->G, c->sigma_u, c->sigma_v, c->dY32};
     CK(c, launch_analyze(c->f[c->cur], is_fp32(c), c->nx, c->ny, c->k, o, d_cut, beta, c->flags,
-                         c->ana_scratch, c->stream),
+                         c->ana_scratch, c->aux_ready ? &c->aux : nullptr, c->stream),
        "launching analysis");
     c->observed = false;
     return LBM_OK;
@@ -446,6 +457,15 @@ void lbm_destroy(lbm_ctx* c) {
     cudaFree(c->flags);
     cudaFree(c->stage);
     cudaFree(c->ana_scratch);
+    if (c->aux_ready) {
+        cudaStreamSynchronize(c->aux.s2);
+        cudaEventDestroy(c->aux.start);
+        for (int b = 0; b < 2; ++b) {
+            cudaEventDestroy(c->aux.jac_done[b]);
+            cudaEventDestroy(c->aux.ref_done[b]);
+        }
+        cudaStreamDestroy(c->aux.s2);
+    }
     free_obs(c);
     if (c->obs_copied) cudaEventDestroy(c->obs_copied);
     delete c;

@@ -493,7 +493,7 @@ __global__ void __launch_bounds__(32) analyze_kernel(T* __restrict__ f, int nx, 
 //      at these sizes). The transform products and the update run in
 //      binary32 with binary32 accumulation.
 
-constexpr int kChunkCells = 16384;  // grid points per (A)+(B) pass
+constexpr int kChunkCells = 8192;   // grid points per (A)+(B) pass
 constexpr int kJacWarps = 4;        // points per block in (A)
 constexpr size_t kXStride = (size_t)NMAX * NMAX;  // floats of X per point
 
@@ -773,53 +773,65 @@ __device__ inline MixSmem carve_mix(unsigned char* raw, int k, int nl) {
     return s;
 }
 
+// Symmetric product C = P^T Q for P = Q (or P^T Q known to be symmetric):
+// only the n(n+1)/2 entries i <= j are formed, spread over the lanes two at
+// a time, and mirrored. P, Q, C are [NMAX][LD] row-major in shared memory.
+__device__ void sym_product(const double* P, const double* Q, double* C, int n, int lane) {
+    const int ne = n * (n + 1) / 2;
+    for (int e0 = lane; e0 < ne; e0 += 64) {
+        const int e1 = e0 + 32;
+        // Entry e -> (i, j), i <= j, row-major over the upper triangle.
+        int i0 = 0, j0 = e0;
+        while (j0 >= n - i0) { j0 -= n - i0; ++i0; }
+        j0 += i0;
+        const bool has1 = e1 < ne;
+        int i1 = 0, j1 = has1 ? e1 : 0;
+        if (has1) {
+            while (j1 >= n - i1) { j1 -= n - i1; ++i1; }
+            j1 += i1;
+        }
+        double s0 = 0.0, s1 = 0.0;
+        for (int r = 0; r < n; ++r) {
+            s0 += P[r * LD + i0] * Q[r * LD + j0];
+            s1 += P[r * LD + i1] * Q[r * LD + j1];
+        }
+        C[i0 * LD + j0] = s0;
+        C[j0 * LD + i0] = s0;
+        if (has1) {
+            C[i1 * LD + j1] = s1;
+            C[j1 * LD + i1] = s1;
+        }
+    }
+}
+
 // FP64 refinement of the basis already in Y (columns = approximate
 // eigenvectors of the symmetric matrix A): Y <- Y L^{-T} with Y^T Y = L L^T,
-// then A <- S = Y^T A Y. Dot products run four output entries at a time.
+// then A <- S = Y^T A Y.
 __device__ void refine_basis(double* A, double* Y, double* W, double* vinv, int n, int lane) {
-    // W = Y^T Y, column `lane`.
-    if (lane < n)
-        for (int i0 = 0; i0 < n; i0 += 4) {
-            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-            for (int r = 0; r < n; ++r) {
-                const double yl = Y[r * LD + lane];
-                const double* yr = Y + r * LD + i0;
-                s0 += yr[0] * yl;
-                s1 += yr[1] * yl;
-                s2 += yr[2] * yl;
-                s3 += yr[3] * yl;
-            }
-            W[i0 * LD + lane] = s0;
-            if (i0 + 1 < n) W[(i0 + 1) * LD + lane] = s1;
-            if (i0 + 2 < n) W[(i0 + 2) * LD + lane] = s2;
-            if (i0 + 3 < n) W[(i0 + 3) * LD + lane] = s3;
-        }
+    sym_product(Y, Y, W, n, lane);  // W = Y^T Y
     __syncwarp();
-    // Cholesky factor of Y^T Y (close to I), lower triangle of W.
+    // Cholesky factor of Y^T Y (close to I), lower triangle of W. Every lane
+    // forms its row's candidate for column j in the same loop, so the warp
+    // does not diverge; the diagonal comes from lane j by a shuffle.
     for (int j = 0; j < n; ++j) {
-        if (lane == j) {
-            double s0 = W[j * LD + j], s1 = 0.0;
-            int c = 0;
-            for (; c + 1 < j; c += 2) {
-                s0 -= W[j * LD + c] * W[j * LD + c];
-                s1 -= W[j * LD + c + 1] * W[j * LD + c + 1];
-            }
-            if (c < j) s0 -= W[j * LD + c] * W[j * LD + c];
-            const double s = s0 + s1;
-            const double inv = rsqrt(s);
-            W[j * LD + j] = s * inv;
-            vinv[j] = inv;
-        }
-        __syncwarp();
-        if (lane > j && lane < n) {
-            double s0 = W[lane * LD + j], s1 = 0.0;
+        double s0 = (lane < n) ? W[lane * LD + j] : 1.0, s1 = 0.0;
+        if (lane < n) {
             int c = 0;
             for (; c + 1 < j; c += 2) {
                 s0 -= W[lane * LD + c] * W[j * LD + c];
                 s1 -= W[lane * LD + c + 1] * W[j * LD + c + 1];
             }
             if (c < j) s0 -= W[lane * LD + c] * W[j * LD + c];
-            W[lane * LD + j] = (s0 + s1) * vinv[j];
+        }
+        const double s = s0 + s1;
+        const double dj = __shfl_sync(kFull, s, j);
+        const double inv = rsqrt(dj);
+        __syncwarp();
+        if (lane == j) {
+            W[j * LD + j] = dj * inv;
+            vinv[j] = inv;
+        } else if (lane > j && lane < n) {
+            W[lane * LD + j] = s * inv;
         }
         __syncwarp();
     }
@@ -853,23 +865,7 @@ __device__ void refine_basis(double* A, double* Y, double* W, double* vinv, int 
             if (i0 + 3 < n) W[(i0 + 3) * LD + lane] = s3;
         }
     __syncwarp();
-    // A <- S = Y^T W, column `lane`.
-    if (lane < n)
-        for (int i0 = 0; i0 < n; i0 += 4) {
-            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-            for (int r = 0; r < n; ++r) {
-                const double wl = W[r * LD + lane];
-                const double* yr = Y + r * LD + i0;
-                s0 += yr[0] * wl;
-                s1 += yr[1] * wl;
-                s2 += yr[2] * wl;
-                s3 += yr[3] * wl;
-            }
-            A[i0 * LD + lane] = s0;
-            if (i0 + 1 < n) A[(i0 + 1) * LD + lane] = s1;
-            if (i0 + 2 < n) A[(i0 + 2) * LD + lane] = s2;
-            if (i0 + 3 < n) A[(i0 + 3) * LD + lane] = s3;
-        }
+    sym_product(Y, W, A, n, lane);  // A <- S = Y^T (A Y), symmetric
     __syncwarp();
 }
 
@@ -1181,17 +1177,17 @@ size_t analyze_scratch_bytes(int nx, int ny, int fp32) {
     if (!fp32) return 0;
     const long long cells = (long long)nx * ny;
     const long long chunk = cells < kChunkCells ? cells : kChunkCells;
-    return (size_t)chunk * kXStride * sizeof(float);
+    return 2 * (size_t)chunk * kXStride * sizeof(float);  // double-buffered
 }
 
 cudaError_t launch_analyze(void* f, int fp32, int nx, int ny, int k, const ObsParams& o,
                            double d_cut, double beta, int* flags, float* scratch,
-                           cudaStream_t s) {
+                           const AnalyzeAux* aux, cudaStream_t s) {
     const long long cells = (long long)nx * ny;
     if (cells > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     cudaError_t e;
     if (fp32) {
-        if (!o.dY32 || !scratch) return cudaErrorInvalidValue;
+        if (!o.dY32 || !scratch || !aux) return cudaErrorInvalidValue;
         const size_t nd = (size_t)2 * o.npts * k;
         to_f32_kernel<<<(unsigned)((nd + 255) / 256), 256, 0, s>>>(o.dY, o.dY32, nd);
         const size_t shA = (size_t)kJacWarps * 2 * o.npts * (sizeof(double) + sizeof(int));
@@ -1202,12 +1198,25 @@ cudaError_t launch_analyze(void* f, int fp32, int nx, int ny, int k, const ObsPa
         e = cudaFuncSetAttribute(analyze_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)shB);
         if (e != cudaSuccess) return e;
-        for (long long c0 = 0; c0 < cells; c0 += kChunkCells) {
-            const int nc = (int)((cells - c0) < kChunkCells ? (cells - c0) : kChunkCells);
+        const long long chunk = cells < kChunkCells ? cells : kChunkCells;
+        // Pipeline: (A) of chunk c on s2 overlaps (B) of chunk c-1 on s; the
+        // scratch is double-buffered, (A) of chunk c waits for (B) of c-2.
+        if ((e = cudaEventRecord(aux->start, s)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(aux->s2, aux->start, 0)) != cudaSuccess) return e;
+        int c = 0;
+        for (long long c0 = 0; c0 < cells; c0 += chunk, ++c) {
+            const int nc = (int)((cells - c0) < chunk ? (cells - c0) : chunk);
+            const int b = c & 1;
+            float* X = scratch + (size_t)b * chunk * kXStride;
+            if (c >= 2 && (e = cudaStreamWaitEvent(aux->s2, aux->ref_done[b], 0)) != cudaSuccess)
+                return e;
             mixed_jacobi_kernel<<<(unsigned)((nc + kJacWarps - 1) / kJacWarps), 32 * kJacWarps, shA,
-                                  s>>>(nx, ny, k, o, d_cut, beta, (int)c0, nc, scratch, flags);
+                                  aux->s2>>>(nx, ny, k, o, d_cut, beta, (int)c0, nc, X, flags);
+            if ((e = cudaEventRecord(aux->jac_done[b], aux->s2)) != cudaSuccess) return e;
+            if ((e = cudaStreamWaitEvent(s, aux->jac_done[b], 0)) != cudaSuccess) return e;
             analyze_mixed_kernel<<<(unsigned)nc, 32, shB, s>>>((float*)f, nx, ny, k, o, d_cut, beta,
-                                                               (int)c0, scratch, flags);
+                                                               (int)c0, X, flags);
+            if ((e = cudaEventRecord(aux->ref_done[b], s)) != cudaSuccess) return e;
         }
     } else {
         const size_t sh = ana_smem_bytes(k, 2 * o.npts);
