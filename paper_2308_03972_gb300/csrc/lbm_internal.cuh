@@ -78,9 +78,11 @@ struct AnalyzeAux {
     cudaEvent_t start, jac_done[2], ref_done[2];
 };
 // Scratch the analysis needs (bytes; 0 for the FP64 path).
-size_t analyze_scratch_bytes(int nx, int ny, int fp32);
+size_t analyze_scratch_bytes(int nx, int ny, int fp32, int npts);
+// nmax: largest local problem size n = min(p, k) over the grid (sizes the
+// mixed kernel's shared memory; points above it are reported as too large).
 cudaError_t launch_analyze(void* f, int fp32, int nx, int ny, int k, const ObsParams& o,
-                           double d_cut, double beta, int* flags, float* scratch,
+                           double d_cut, double beta, int nmax, int* flags, void* scratch,
                            const AnalyzeAux* aux, cudaStream_t s);
 
 }  // namespace lbmgpu

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -31,7 +32,13 @@ struct lbm_ctx {
     double* d = nullptr;   // [2 npts]
     double* G = nullptr;   // [2 npts][2 npts]
     float* dY32 = nullptr; // [2 npts][k] binary32 copy (mixed precision)
-    float* ana_scratch = nullptr;  // analysis scratch (mixed precision)
+    void* ana_scratch = nullptr;   // analysis scratch (mixed precision)
+    size_t ana_scratch_bytes = 0;
+    // Observation geometry of the last letkf_observe, and the largest local
+    // problem it gives for a cached d_cut.
+    std::vector<int> geo_ix, geo_iy;
+    double geo_dcut = -1.0;
+    int geo_nmax = 0;
     AnalyzeAux aux{};              // second stream + events (mixed precision)
     bool aux_ready = false;
     double* h_yo = nullptr;  // pinned staging [2 cap]
@@ -121,6 +128,39 @@ void free_obs(lbm_ctx* c) {
     c->ix = c->iy = nullptr;
     c->yo = c->dY = c->d = c->G = nullptr;
     c->obs_cap = 0;
+}
+
+// Largest local problem n = min(p, k) over the grid for the current
+// observation points and d_cut: p = 2 x (points with r / d_cut < 2), counted
+// by stamping a disc around every point. The test uses a tiny margin so the
+// count bounds the kernels' own (exact) selection from above.
+int largest_local_problem(lbm_ctx* c, double d_cut) {
+    if (c->geo_dcut == d_cut) return c->geo_nmax;
+    const int nx = c->nx, ny = c->ny;
+    std::vector<int> cnt((size_t)nx * ny, 0);
+    const int R = (int)std::ceil(2.0 * d_cut);
+    const int ox0 = -(nx / 2), ox1 = nx - 1 - nx / 2;
+    const int oy0 = -(ny / 2), oy1 = ny - 1 - ny / 2;
+    for (size_t j = 0; j < c->geo_ix.size(); ++j) {
+        for (int dy = (oy0 > -R ? oy0 : -R); dy <= (oy1 < R ? oy1 : R); ++dy) {
+            const int y = ((c->geo_iy[j] + dy) % ny + ny) % ny;
+            for (int dx = (ox0 > -R ? ox0 : -R); dx <= (ox1 < R ? ox1 : R); ++dx) {
+                const double r = std::sqrt((double)dx * dx + (double)dy * dy);
+                if (r / d_cut < 2.0 + 1e-12) {
+                    const int x = ((c->geo_ix[j] + dx) % nx + nx) % nx;
+                    ++cnt[(size_t)y * nx + x];
+                }
+            }
+        }
+    }
+    int nmax = 2;
+    for (int v : cnt) {
+        const int n = (2 * v < c->k) ? 2 * v : c->k;
+        if (n > nmax) nmax = n;
+    }
+    c->geo_dcut = d_cut;
+    c->geo_nmax = nmax;
+    return nmax;
 }
 
 }  // namespace
@@ -358,6 +398,12 @@ int letkf_observe(lbm_ctx* c, int npts, const int* ix, const int* iy, const doub
                          c->dY, c->d, c->stream),
        "launching observation operator");
     CK(c, launch_obs_gram(c->dY, 2 * npts, c->k, c->G, c->stream), "launching observation Gram");
+    if (c->geo_ix.size() != (size_t)npts || !std::equal(ix, ix + npts, c->geo_ix.begin()) ||
+        !std::equal(iy, iy + npts, c->geo_iy.begin())) {
+        c->geo_ix.assign(ix, ix + npts);
+        c->geo_iy.assign(iy, iy + npts);
+        c->geo_dcut = -1.0;
+    }
     c->npts = npts;
     c->sigma_u = sigma_u;
     c->sigma_v = sigma_v;
@@ -371,9 +417,16 @@ int letkf_analyze(lbm_ctx* c, double d_cut, double beta) {
     if (!(d_cut > 0.0) || !std::isfinite(d_cut)) return fail(c, LBM_EINVAL, "d_cut must be > 0");
     if (!(beta > 0.0) || !std::isfinite(beta)) return fail(c, LBM_EINVAL, "beta must be > 0");
     if (!c->observed) return fail(c, LBM_EINVAL, "letkf_observe must precede letkf_analyze");
-    const size_t scratch = analyze_scratch_bytes(c->nx, c->ny, is_fp32(c));
-    if (scratch && !c->ana_scratch)
+    const size_t scratch = analyze_scratch_bytes(c->nx, c->ny, is_fp32(c), c->npts);
+    if (scratch > c->ana_scratch_bytes) {
+        CK(c, cudaStreamSynchronize(c->stream), "synchronising");
+        cudaFree(c->ana_scratch);
+        c->ana_scratch = nullptr;
+        c->ana_scratch_bytes = 0;
         CK(c, cudaMalloc(&c->ana_scratch, scratch), "allocating analysis scratch");
+        c->ana_scratch_bytes = scratch;
+    }
+    const int nmax = is_fp32(c) ? largest_local_problem(c, d_cut) : 0;
     if (is_fp32(c) && !c->aux_ready) {
         CK(c, cudaStreamCreateWithFlags(&c->aux.s2, cudaStreamNonBlocking), "creating stream");
         CK(c, cudaEventCreateWithFlags(&c->aux.start, cudaEventDisableTiming), "creating event");
@@ -384,8 +437,8 @@ int letkf_analyze(lbm_ctx* c, double d_cut, double beta) {
         c->aux_ready = true;
     }
     ObsParams o{c->npts, c->ix, c->iy, c->dY, c->d, c->G, c->sigma_u, c->sigma_v, c->dY32};
-    CK(c, launch_analyze(c->f[c->cur], is_fp32(c), c->nx, c->ny, c->k, o, d_cut, beta, c->flags,
-                         c->ana_scratch, c->aux_ready ? &c->aux : nullptr, c->stream),
+    CK(c, launch_analyze(c->f[c->cur], is_fp32(c), c->nx, c->ny, c->k, o, d_cut, beta, nmax,
+                         c->flags, c->ana_scratch, c->aux_ready ? &c->aux : nullptr, c->stream),
        "launching analysis");
     c->observed = false;
     return LBM_OK;

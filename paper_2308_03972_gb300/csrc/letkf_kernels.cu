@@ -546,8 +546,12 @@ __device__ int local_set(const ObsParams& o, int x, int y, int nx, int ny, doubl
 // U[i][lane], the eigenvector of player `lane`.
 template <int NS>
 __device__ bool jacobi32_reg(float (&a)[NS], float (&u)[NS], int lane, float rel, int max_sweeps) {
+    float dg = 0.0f;  // my diagonal entry A[lane][lane], tracked analytically
 #pragma unroll
-    for (int i = 0; i < NS; ++i) u[i] = (i == lane) ? 1.0f : 0.0f;
+    for (int i = 0; i < NS; ++i) {
+        u[i] = (i == lane) ? 1.0f : 0.0f;
+        if (i == lane) dg = a[i];
+    }
     float fro = 0.0f;
 #pragma unroll
     for (int i = 0; i < NS; ++i) fro += a[i] * a[i];
@@ -562,19 +566,17 @@ __device__ bool jacobi32_reg(float (&a)[NS], float (&u)[NS], int lane, float rel
             const int qp = m1 - q;
             const int partner = (qp == 0) ? 0 : 1 + ((qp - 1 + r) % m1);
             const bool pside = q < NS / 2;
-            float d = 0.0f, off = 0.0f;
+            float off = 0.0f;
 #pragma unroll
-            for (int i = 0; i < NS; ++i) {
-                if (i == q) d = a[i];
+            for (int i = 0; i < NS; ++i)
                 if (i == qp) off = a[i];
-            }
-            const float dp = __shfl_sync(kFull, d, partner & 31);
+            const float dp = __shfl_sync(kFull, dg, partner & 31);
             // Rotation of my pair (symmetric 2 x 2 Schur), on the p side.
-            float c = 1.0f, s = 0.0f;
+            float c = 1.0f, s = 0.0f, t = 0.0f;
             bool rot = false;
             if (pside && lane < NS && fabsf(off) > thresh) {
-                const float tau = (dp - d) / (2.0f * off);
-                const float t = (tau >= 0.0f ? 1.0f : -1.0f) / (fabsf(tau) + sqrtf(1.0f + tau * tau));
+                const float tau = (dp - dg) / (2.0f * off);
+                t = (tau >= 0.0f ? 1.0f : -1.0f) / (fabsf(tau) + sqrtf(1.0f + tau * tau));
                 c = 1.0f / sqrtf(1.0f + t * t);
                 s = t * c;
                 rot = true;
@@ -583,18 +585,22 @@ __device__ bool jacobi32_reg(float (&a)[NS], float (&u)[NS], int lane, float rel
                 any_sweep = true;
                 // Row rotations: position t (row p) with position NS-1-t (row q).
 #pragma unroll
-                for (int t = 0; t < NS / 2; ++t) {
-                    const int pl = (t == 0) ? 0 : 1 + ((t - 1 + r) % m1);
+                for (int tt = 0; tt < NS / 2; ++tt) {
+                    const int pl = (tt == 0) ? 0 : 1 + ((tt - 1 + r) % m1);
                     const float ct = __shfl_sync(kFull, c, pl);
                     const float st = __shfl_sync(kFull, s, pl);
-                    const float x0 = a[t], x1 = a[NS - 1 - t];
-                    a[t] = ct * x0 - st * x1;
-                    a[NS - 1 - t] = st * x0 + ct * x1;
+                    const float x0 = a[tt], x1 = a[NS - 1 - tt];
+                    a[tt] = ct * x0 - st * x1;
+                    a[NS - 1 - tt] = st * x0 + ct * x1;
                 }
-                // Column rotations with the partner lane.
+                // Column rotations with the partner lane; the diagonal moves
+                // by -/+ t a_pq on the p/q side.
                 const int pl_mine = pside ? lane : partner;
                 const float cm = __shfl_sync(kFull, c, pl_mine & 31);
                 const float sm_ = __shfl_sync(kFull, s, pl_mine & 31);
+                const float tm = __shfl_sync(kFull, t, pl_mine & 31);
+                const float om = __shfl_sync(kFull, off, pl_mine & 31);
+                dg = pside ? dg - tm * om : dg + tm * om;
                 const float sg = pside ? -sm_ : sm_;
 #pragma unroll
                 for (int i = 0; i < NS; ++i) {
@@ -666,52 +672,78 @@ __device__ void jacobi_point(const ObsParams& o, int k, int n, int p, bool obs_s
     }
 }
 
+// Per-chunk scratch shared by kernels (A) and (B).
+struct MixScratch {
+    float* X;      // [chunk][NMAX][NMAX] binary32 basis, row i at i * NMAX
+    double* lsq;   // [chunk][nobs] sqrt(rho) of the local scalars
+    int* lidx;     // [chunk][nobs] their observation indices
+    int* pcount;   // [chunk] number of local scalars
+};
+
+__host__ __device__ inline size_t mix_scratch_bytes_per_point(int nobs) {
+    return kXStride * sizeof(float) + (size_t)nobs * (sizeof(double) + sizeof(int)) + sizeof(int);
+}
+
+__host__ __device__ inline MixScratch mix_scratch_at(void* base, int chunk, int nobs) {
+    MixScratch m;
+    unsigned char* p = reinterpret_cast<unsigned char*>(base);
+    m.X = reinterpret_cast<float*>(p);
+    p += (size_t)chunk * kXStride * sizeof(float);
+    m.lsq = reinterpret_cast<double*>(p);
+    p += (size_t)chunk * nobs * sizeof(double);
+    m.lidx = reinterpret_cast<int*>(p);
+    p += (size_t)chunk * nobs * sizeof(int);
+    m.pcount = reinterpret_cast<int*>(p);
+    return m;
+}
+
 __global__ void __launch_bounds__(32 * kJacWarps) mixed_jacobi_kernel(int nx, int ny, int k,
                                                                       ObsParams o, double d_cut,
                                                                       double beta, int cell0,
-                                                                      int ncell,
-                                                                      float* __restrict__ X,
+                                                                      int ncell, MixScratch sc,
                                                                       int* __restrict__ flags) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nobs = 2 * o.npts;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    double* lsq = reinterpret_cast<double*>(smem_raw) + (size_t)w * nobs;
-    int* lidx = reinterpret_cast<int*>(reinterpret_cast<double*>(smem_raw) + (size_t)kJacWarps * nobs) +
-                (size_t)w * nobs;
     const int li = blockIdx.x * kJacWarps + w;
     if (li >= ncell) return;
     const int cell = cell0 + li;
     const int x = cell % nx, y = cell / nx;
+    double* lsq = sc.lsq + (size_t)li * nobs;
+    int* lidx = sc.lidx + (size_t)li * nobs;
     const int p = local_set(o, x, y, nx, ny, d_cut, lane, lidx, lsq);
+    if (lane == 0) sc.pcount[li] = p;
     if (p == 0) return;
     const bool obs_space = p < k;
     const int n = obs_space ? p : k;
     if (n > NMAX) return;  // reported by kernel (B)
     const double aa = (k - 1) / beta;
-    float* Xp = X + (size_t)li * kXStride;
+    float* Xp = sc.X + (size_t)li * kXStride;
     if (n <= 8)
         jacobi_point<8>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, flags);
     else if (n <= 16)
         jacobi_point<16>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, flags);
     else if (n <= 24)
         jacobi_point<24>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, flags);
+    else if (n <= 26)
+        jacobi_point<26>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, flags);
     else if (n <= 28)
         jacobi_point<28>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, flags);
     else
         jacobi_point<32>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, flags);
 }
 
+// Shared memory of kernel (B). The matrices are nm x ld with nm the largest
+// local problem of this launch and ld = nm + 1 rounded to odd.
 struct MixSmem {
-    double* A;     // [NMAX][LD] matrix (FP64), then S = Y^T A Y
-    double* Y;     // [NMAX][LD] FP64 basis
-    double* W;     // [NMAX][LD] X^T X, its Cholesky factor, then A Y
-    float* F32;    // [NMAX][LD] f(S) in binary32, then T (inside W)
-    float* Y32;    // [NMAX][LD] Y in binary32
+    double* A;     // [nm][ld] matrix (FP64), then S = Y^T A Y
+    double* Y;     // [nm][ld] FP64 basis
+    double* W;     // [nm][ld] Y^T Y, its Cholesky factor, then A Y
+    float* F32;    // [nm][ld] f(S) in binary32, then T (inside W)
+    float* Y32;    // [nm][ld] Y in binary32
     double* lsq;   // [nl]
     double* ldh;   // [nl]
     double* vb;    // [NMAX]
     double* v1;    // [NMAX]
-    double* v2;    // [NMAX]
     double* vu;    // [NMAX]
     double* vinv;  // [NMAX]
     float* dX;     // [9][k]
@@ -720,25 +752,31 @@ struct MixSmem {
     float* B;      // [9][NMAX]
     float* zv;     // [16]
     float* vf;     // [NMAX]
+    float* t1f;    // [NMAX]
+    float* t2f;    // [NMAX]
     int* lidx;     // [nl]
 };
 
-__host__ __device__ inline size_t mix_smem_bytes(int k, int nl) {
-    const size_t d = 3 * (size_t)NMAX * LD + 2 * (size_t)nl + 5 * NMAX;
-    const size_t f = (size_t)NMAX * LD + 9 * (size_t)k + 16 + 18 * NMAX + 16 + NMAX;
+__host__ __device__ inline int mix_ld(int nm) { return (nm % 2 == 0) ? nm + 1 : nm; }
+
+__host__ __device__ inline size_t mix_smem_bytes(int k, int nl, int nm) {
+    const int ld = mix_ld(nm);
+    const size_t d = 3 * (size_t)nm * ld + 2 * (size_t)nl + 4 * NMAX;
+    const size_t f = (size_t)nm * ld + 9 * (size_t)k + 16 + 18 * NMAX + 16 + 3 * NMAX;
     return d * sizeof(double) + ((f * sizeof(float) + 7) / 8) * 8 + (size_t)nl * sizeof(int);
 }
 
-__device__ inline MixSmem carve_mix(unsigned char* raw, int k, int nl) {
+__device__ inline MixSmem carve_mix(unsigned char* raw, int k, int nl, int nm) {
+    const int ld = mix_ld(nm);
     MixSmem s;
     double* p = reinterpret_cast<double*>(raw);
     s.A = p;
-    p += NMAX * LD;
+    p += nm * ld;
     s.Y = p;
-    p += NMAX * LD;
+    p += nm * ld;
     s.W = p;
     s.F32 = reinterpret_cast<float*>(p);
-    p += NMAX * LD;
+    p += nm * ld;
     s.lsq = p;
     p += nl;
     s.ldh = p;
@@ -747,15 +785,13 @@ __device__ inline MixSmem carve_mix(unsigned char* raw, int k, int nl) {
     p += NMAX;
     s.v1 = p;
     p += NMAX;
-    s.v2 = p;
-    p += NMAX;
     s.vu = p;
     p += NMAX;
     s.vinv = p;
     p += NMAX;
     float* q = reinterpret_cast<float*>(p);
     s.Y32 = q;
-    q += NMAX * LD;
+    q += nm * ld;
     s.dX = q;
     q += 9 * k;
     s.xbar = q;
@@ -768,6 +804,10 @@ __device__ inline MixSmem carve_mix(unsigned char* raw, int k, int nl) {
     q += 16;
     s.vf = q;
     q += NMAX;
+    s.t1f = q;
+    q += NMAX;
+    s.t2f = q;
+    q += NMAX;
     const size_t fbytes = (size_t)(q - reinterpret_cast<float*>(p)) * sizeof(float);
     s.lidx = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(p) + ((fbytes + 7) / 8) * 8);
     return s;
@@ -775,8 +815,8 @@ __device__ inline MixSmem carve_mix(unsigned char* raw, int k, int nl) {
 
 // Symmetric product C = P^T Q for P = Q (or P^T Q known to be symmetric):
 // only the n(n+1)/2 entries i <= j are formed, spread over the lanes two at
-// a time, and mirrored. P, Q, C are [NMAX][LD] row-major in shared memory.
-__device__ void sym_product(const double* P, const double* Q, double* C, int n, int lane) {
+// a time, and mirrored. P, Q, C are [n][ld] row-major in shared memory.
+__device__ void sym_product(const double* P, const double* Q, double* C, int n, int ld, int lane) {
     const int ne = n * (n + 1) / 2;
     for (int e0 = lane; e0 < ne; e0 += 64) {
         const int e1 = e0 + 32;
@@ -792,14 +832,14 @@ __device__ void sym_product(const double* P, const double* Q, double* C, int n, 
         }
         double s0 = 0.0, s1 = 0.0;
         for (int r = 0; r < n; ++r) {
-            s0 += P[r * LD + i0] * Q[r * LD + j0];
-            s1 += P[r * LD + i1] * Q[r * LD + j1];
+            s0 += P[r * ld + i0] * Q[r * ld + j0];
+            s1 += P[r * ld + i1] * Q[r * ld + j1];
         }
-        C[i0 * LD + j0] = s0;
-        C[j0 * LD + i0] = s0;
+        C[i0 * ld + j0] = s0;
+        C[j0 * ld + i0] = s0;
         if (has1) {
-            C[i1 * LD + j1] = s1;
-            C[j1 * LD + i1] = s1;
+            C[i1 * ld + j1] = s1;
+            C[j1 * ld + i1] = s1;
         }
     }
 }
@@ -807,80 +847,93 @@ __device__ void sym_product(const double* P, const double* Q, double* C, int n, 
 // FP64 refinement of the basis already in Y (columns = approximate
 // eigenvectors of the symmetric matrix A): Y <- Y L^{-T} with Y^T Y = L L^T,
 // then A <- S = Y^T A Y.
-__device__ void refine_basis(double* A, double* Y, double* W, double* vinv, int n, int lane) {
-    sym_product(Y, Y, W, n, lane);  // W = Y^T Y
+__device__ void refine_basis(double* A, double* Y, double* W, double* vinv, int n, int ld,
+                             int lane) {
+    sym_product(Y, Y, W, n, ld, lane);  // W = Y^T Y
     __syncwarp();
     // Cholesky factor of Y^T Y (close to I), lower triangle of W. Every lane
     // forms its row's candidate for column j in the same loop, so the warp
     // does not diverge; the diagonal comes from lane j by a shuffle.
     for (int j = 0; j < n; ++j) {
-        double s0 = (lane < n) ? W[lane * LD + j] : 1.0, s1 = 0.0;
+        double s0 = (lane < n) ? W[lane * ld + j] : 1.0, s1 = 0.0;
         if (lane < n) {
             int c = 0;
             for (; c + 1 < j; c += 2) {
-                s0 -= W[lane * LD + c] * W[j * LD + c];
-                s1 -= W[lane * LD + c + 1] * W[j * LD + c + 1];
+                s0 -= W[lane * ld + c] * W[j * ld + c];
+                s1 -= W[lane * ld + c + 1] * W[j * ld + c + 1];
             }
-            if (c < j) s0 -= W[lane * LD + c] * W[j * LD + c];
+            if (c < j) s0 -= W[lane * ld + c] * W[j * ld + c];
         }
         const double s = s0 + s1;
         const double dj = __shfl_sync(kFull, s, j);
-        const double inv = rsqrt(dj);
+        // The basis is orthonormal to ~1e-5, so the pivot is 1 + e with tiny
+        // e: the binomial series 1/sqrt(1+e) = 1 - e/2 + 3e^2/8 - 5e^3/16
+        // truncates below 3e-17 for |e| < 1e-4; other pivots take rsqrt.
+        const double ej = dj - 1.0;
+        const double inv = (fabs(ej) < 1e-4) ? 1.0 + ej * (-0.5 + ej * (0.375 - 0.3125 * ej))
+                                             : rsqrt(dj);
         __syncwarp();
         if (lane == j) {
-            W[j * LD + j] = dj * inv;
+            W[j * ld + j] = dj * inv;
             vinv[j] = inv;
         } else if (lane > j && lane < n) {
-            W[lane * LD + j] = s * inv;
+            W[lane * ld + j] = s * inv;
         }
         __syncwarp();
     }
     // Y <- Y L^{-T}, row `lane` by forward substitution.
     if (lane < n)
         for (int j = 0; j < n; ++j) {
-            double z0 = Y[lane * LD + j], z1 = 0.0;
+            double z0 = Y[lane * ld + j], z1 = 0.0;
             int c = 0;
             for (; c + 1 < j; c += 2) {
-                z0 -= Y[lane * LD + c] * W[j * LD + c];
-                z1 -= Y[lane * LD + c + 1] * W[j * LD + c + 1];
+                z0 -= Y[lane * ld + c] * W[j * ld + c];
+                z1 -= Y[lane * ld + c + 1] * W[j * ld + c + 1];
             }
-            if (c < j) z0 -= Y[lane * LD + c] * W[j * LD + c];
-            Y[lane * LD + j] = (z0 + z1) * vinv[j];
+            if (c < j) z0 -= Y[lane * ld + c] * W[j * ld + c];
+            Y[lane * ld + j] = (z0 + z1) * vinv[j];
         }
     __syncwarp();
-    // W = A Y, column `lane`.
-    if (lane < n)
-        for (int i0 = 0; i0 < n; i0 += 4) {
+    // W = A Y, column `lane`: four rows at a time, then the remainder.
+    if (lane < n) {
+        int i0 = 0;
+        for (; i0 + 3 < n; i0 += 4) {
             double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
             for (int c = 0; c < n; ++c) {
-                const double yc = Y[c * LD + lane];
-                s0 += A[i0 * LD + c] * yc;
-                s1 += A[(i0 + 1) * LD + c] * yc;
-                s2 += A[(i0 + 2) * LD + c] * yc;
-                s3 += A[(i0 + 3) * LD + c] * yc;
+                const double yc = Y[c * ld + lane];
+                s0 += A[i0 * ld + c] * yc;
+                s1 += A[(i0 + 1) * ld + c] * yc;
+                s2 += A[(i0 + 2) * ld + c] * yc;
+                s3 += A[(i0 + 3) * ld + c] * yc;
             }
-            W[i0 * LD + lane] = s0;
-            if (i0 + 1 < n) W[(i0 + 1) * LD + lane] = s1;
-            if (i0 + 2 < n) W[(i0 + 2) * LD + lane] = s2;
-            if (i0 + 3 < n) W[(i0 + 3) * LD + lane] = s3;
+            W[i0 * ld + lane] = s0;
+            W[(i0 + 1) * ld + lane] = s1;
+            W[(i0 + 2) * ld + lane] = s2;
+            W[(i0 + 3) * ld + lane] = s3;
         }
+        for (; i0 < n; ++i0) {
+            double s0 = 0.0;
+            for (int c = 0; c < n; ++c) s0 += A[i0 * ld + c] * Y[c * ld + lane];
+            W[i0 * ld + lane] = s0;
+        }
+    }
     __syncwarp();
-    sym_product(Y, W, A, n, lane);  // A <- S = Y^T (A Y), symmetric
+    sym_product(Y, W, A, n, ld, lane);  // A <- S = Y^T (A Y), symmetric
     __syncwarp();
 }
 
 __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f, int nx, int ny,
                                                            int k, ObsParams o, double d_cut,
-                                                           double beta, int cell0,
-                                                           const float* __restrict__ X,
+                                                           double beta, int cell0, int nm,
+                                                           MixScratch sc,
                                                            int* __restrict__ flags) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nobs = 2 * o.npts;
-    MixSmem sm = carve_mix(smem_raw, k, nobs);
+    MixSmem sm = carve_mix(smem_raw, k, nobs, nm);
+    const int ld = mix_ld(nm);
     const int lane = threadIdx.x;
     const int li = blockIdx.x;
     const int cell = cell0 + li;
-    const int x = cell % nx, y = cell / nx;
     const size_t plane = (size_t)nx * ny * k;
     float* fc = f + (size_t)cell * k;
 
@@ -897,8 +950,15 @@ __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f
         if (lane == 0) sm.xbar[a] = mean;
     }
 
-    const int p = local_set(o, x, y, nx, ny, d_cut, lane, sm.lidx, sm.lsq);
-    for (int i = lane; i < p; i += 32) sm.ldh[i] = sm.lsq[i] * o.d[sm.lidx[i]];
+    // Local set from kernel (A).
+    const int p = sc.pcount[li];
+    for (int i = lane; i < p; i += 32) {
+        const int oi = sc.lidx[(size_t)li * nobs + i];
+        const double si = sc.lsq[(size_t)li * nobs + i];
+        sm.lidx[i] = oi;
+        sm.lsq[i] = si;
+        sm.ldh[i] = si * o.d[oi];
+    }
     __syncwarp();
 
     if (p == 0) {
@@ -909,7 +969,7 @@ __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f
     }
     const bool obs_space = p < k;
     const int n = obs_space ? p : k;
-    if (n > NMAX) {
+    if (n > nm) {
         if (lane == 0) atomicOr(flags, FLAG_TOOLARGE);
         return;
     }
@@ -920,13 +980,13 @@ __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f
     // The symmetric matrix in FP64: A = Yh Yh^T (observation space) or
     // C = a I + Yh^T Yh with b = Yh^T d-hat (ensemble space); the basis X
     // from kernel (A).
-    const float* Xp = X + (size_t)li * kXStride;
+    const float* Xp = sc.X + (size_t)li * kXStride;
     if (lane < n) {
         if (obs_space) {
             const int ol = sm.lidx[lane];
             const double sl = sm.lsq[lane];
             for (int i = 0; i < n; ++i)
-                A[i * LD + lane] = sm.lsq[i] * o.G[(size_t)sm.lidx[i] * nobs + ol] * sl;
+                A[i * ld + lane] = sm.lsq[i] * o.G[(size_t)sm.lidx[i] * nobs + ol] * sl;
         } else {
             double bj = 0.0;
             for (int i = 0; i < n; ++i) {
@@ -935,18 +995,18 @@ __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f
                     const double* row = o.dY + (size_t)sm.lidx[l] * k;
                     s += sm.lsq[l] * sm.lsq[l] * row[i] * row[lane];
                 }
-                A[i * LD + lane] = s + (i == lane ? aa : 0.0);
+                A[i * ld + lane] = s + (i == lane ? aa : 0.0);
             }
             for (int l = 0; l < p; ++l) bj += sm.lsq[l] * o.dY[(size_t)sm.lidx[l] * k + lane] * sm.ldh[l];
             sm.vb[lane] = bj;
         }
-        for (int i = 0; i < n; ++i) Y[i * LD + lane] = (double)Xp[(size_t)i * NMAX + lane];
+        for (int i = 0; i < n; ++i) Y[i * ld + lane] = (double)Xp[(size_t)i * NMAX + lane];
     }
     __syncwarp();
-    refine_basis(A, Y, sm.W, sm.vinv, n, lane);
+    refine_basis(A, Y, sm.W, sm.vinv, n, ld, lane);
     // Y in binary32 for the transform products.
     if (lane < n)
-        for (int c = 0; c < n; ++c) sm.Y32[lane * LD + c] = (float)Y[lane * LD + c];
+        for (int c = 0; c < n; ++c) sm.Y32[lane * ld + c] = (float)Y[lane * ld + c];
     __syncwarp();
     float* Y32 = sm.Y32;
     float* F32 = sm.F32;
@@ -957,29 +1017,24 @@ __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f
         // q(s) = (a+s)^{-1/2} for the square root. u_i = sqrt(a + s_ii).
         const double r = sqrt(aa);
         if (lane < n) {
-            const double u = sqrt(aa + A[lane * LD + lane]);
+            const double sii = A[lane * ld + lane];
+            const double u = sqrt(aa + sii);
             sm.vu[lane] = u;
             sm.vinv[lane] = 1.0 / (u * (u + r));  // alpha_i
-            double t0 = 0.0, t1 = 0.0;  // Y^T d-hat
-            int c = 0;
-            for (; c + 1 < n; c += 2) {
-                t0 += Y[c * LD + lane] * sm.ldh[c];
-                t1 += Y[(c + 1) * LD + lane] * sm.ldh[c + 1];
-            }
-            if (c < n) t0 += Y[c * LD + lane] * sm.ldh[c];
-            sm.v1[lane] = t0 + t1;
+            sm.vb[lane] = 1.0 / (aa + sii);       // h_i = 1 / u_i^2
+            // t1 = Y^T d-hat (binary32 transform product).
+            float t = 0.0f;
+            for (int c = 0; c < n; ++c) t += Y32[c * ld + lane] * (float)sm.ldh[c];
+            sm.t1f[lane] = t;
         }
         __syncwarp();
         if (lane < n) {
-            // t2 = h(S) t1 with h(S)_ii = 1/u_i^2, h(S)_ij = -s_ij / (u_i^2 u_j^2).
-            const double hi = 1.0 / (sm.vu[lane] * sm.vu[lane]);
-            double t = 0.0;
-            for (int j = 0; j < n; ++j) {
-                if (j == lane) continue;
-                const double hj = 1.0 / (sm.vu[j] * sm.vu[j]);
-                t += A[lane * LD + j] * hj * sm.v1[j];
-            }
-            sm.v2[lane] = hi * (sm.v1[lane] - t);
+            // t2 = h(S) t1 with h(S)_ii = h_i, h(S)_ij = -s_ij h_i h_j.
+            const float hi = (float)sm.vb[lane];
+            float t = 0.0f;
+            for (int j = 0; j < n; ++j)
+                if (j != lane) t += (float)A[lane * ld + j] * ((float)sm.vb[j] * sm.t1f[j]);
+            sm.t2f[lane] = hi * (sm.t1f[lane] - t);
             // g(S) in binary32: diagonal -alpha_i / r, off-diagonal
             // s_ij (u_i + u_j + r) alpha_i alpha_j / (r (u_i + u_j)).
             const float ai = (float)sm.vinv[lane];
@@ -992,21 +1047,16 @@ __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f
                 } else {
                     const float uj = (float)sm.vu[i];
                     const float aj = (float)sm.vinv[i];
-                    v = (float)A[i * LD + lane] * (ui + uj + rf) * ai * aj / (rf * (ui + uj));
+                    v = (float)A[i * ld + lane] * (ui + uj + rf) * ai * aj / (rf * (ui + uj));
                 }
-                F32[i * LD + lane] = v;
+                F32[i * ld + lane] = v;
             }
         }
         __syncwarp();
         if (lane < n) {
-            double t0 = 0.0, t1 = 0.0;
-            int c = 0;
-            for (; c + 1 < n; c += 2) {
-                t0 += Y[lane * LD + c] * sm.v2[c];
-                t1 += Y[lane * LD + c + 1] * sm.v2[c + 1];
-            }
-            if (c < n) t0 += Y[lane * LD + c] * sm.v2[c];
-            sm.vf[lane] = (float)(t0 + t1);  // v = (a I + A)^{-1} d-hat
+            float t = 0.0f;
+            for (int c = 0; c < n; ++c) t += Y32[lane * ld + c] * sm.t2f[c];
+            sm.vf[lane] = t;  // v = (a I + A)^{-1} d-hat
             // Z = dX Yh^T, column `lane`: nine accumulators over members.
             const float* row = o.dY32 + (size_t)sm.lidx[lane] * k;
             float acc[9];
@@ -1032,7 +1082,7 @@ __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f
 #pragma unroll
             for (int a = 0; a < 9; ++a) acc[a] = 0.0f;
             for (int c = 0; c < n; ++c) {
-                const float yc = Y32[c * LD + lane];
+                const float yc = Y32[c * ld + lane];
 #pragma unroll
                 for (int a = 0; a < 9; ++a) acc[a] += sm.Z[a * NMAX + c] * yc;
             }
@@ -1045,7 +1095,7 @@ __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f
 #pragma unroll
             for (int a = 0; a < 9; ++a) acc[a] = 0.0f;
             for (int j = 0; j < n; ++j) {
-                const float fj = F32[j * LD + lane];
+                const float fj = F32[j * ld + lane];
 #pragma unroll
                 for (int a = 0; a < 9; ++a) acc[a] += sm.B[a * NMAX + j] * fj;
             }
@@ -1058,7 +1108,7 @@ __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f
 #pragma unroll
             for (int a = 0; a < 9; ++a) acc[a] = 0.0f;
             for (int i = 0; i < n; ++i) {
-                const float yi = Y32[lane * LD + i];
+                const float yi = Y32[lane * ld + i];
 #pragma unroll
                 for (int a = 0; a < 9; ++a) acc[a] += sm.Z[a * NMAX + i] * yi;
             }
@@ -1083,20 +1133,20 @@ __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f
     } else {
         // Functions of S directly: 1/lambda for P-tilde, lambda^{-1/2} for W.
         if (lane < n) {
-            const double lam = A[lane * LD + lane];
+            const double lam = A[lane * ld + lane];
             sm.vu[lane] = sqrt(lam);
             sm.vinv[lane] = 1.0 / lam;
-            double t = 0.0;
-            for (int c = 0; c < n; ++c) t += Y[c * LD + lane] * sm.vb[c];
-            sm.v1[lane] = t;  // Y^T b
+            float t = 0.0f;
+            for (int c = 0; c < n; ++c) t += Y32[c * ld + lane] * (float)sm.vb[c];
+            sm.t1f[lane] = t;  // Y^T b
         }
         __syncwarp();
         if (lane < n) {
             // t2 = f1(S) t1, f1(S)_ii = 1/l_i, f1(S)_ij = -s_ij / (l_i l_j).
-            double t = 0.0;
+            float t = 0.0f;
             for (int j = 0; j < n; ++j)
-                if (j != lane) t += A[lane * LD + j] * sm.vinv[j] * sm.v1[j];
-            sm.v2[lane] = sm.vinv[lane] * (sm.v1[lane] - t);
+                if (j != lane) t += (float)A[lane * ld + j] * ((float)sm.vinv[j] * sm.t1f[j]);
+            sm.t2f[lane] = (float)sm.vinv[lane] * (sm.t1f[lane] - t);
             // f2(S) = S^{-1/2}: diagonal 1/sqrt(l_i), off-diagonal
             // -s_ij / (sqrt(l_i) sqrt(l_j) (sqrt(l_i) + sqrt(l_j))).
             const float si = (float)sm.vu[lane];
@@ -1106,39 +1156,39 @@ __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f
                     v = (float)(1.0 / sm.vu[lane]);
                 } else {
                     const float sj = (float)sm.vu[i];
-                    v = -(float)A[i * LD + lane] / (si * sj * (si + sj));
+                    v = -(float)A[i * ld + lane] / (si * sj * (si + sj));
                 }
-                F32[i * LD + lane] = v;
+                F32[i * ld + lane] = v;
             }
         }
         __syncwarp();
         float* YF = reinterpret_cast<float*>(A);  // S is no longer needed after w-bar
         if (lane < n) {
-            double t = 0.0;
-            for (int c = 0; c < n; ++c) t += Y[lane * LD + c] * sm.v2[c];
-            sm.vf[lane] = (float)t;  // w-bar
+            float t = 0.0f;
+            for (int c = 0; c < n; ++c) t += Y32[lane * ld + c] * sm.t2f[c];
+            sm.vf[lane] = t;  // w-bar
         }
         __syncwarp();
         if (lane < n)
             for (int i = 0; i < n; ++i) {
                 float s = 0.0f;
-                for (int l = 0; l < n; ++l) s += Y32[i * LD + l] * F32[l * LD + lane];
-                YF[i * LD + lane] = s;
+                for (int l = 0; l < n; ++l) s += Y32[i * ld + l] * F32[l * ld + lane];
+                YF[i * ld + lane] = s;
             }
         __syncwarp();
         // T = sqrt(k-1) Y f2(S) Y^T + w-bar 1^T, over F32.
         if (lane < n)
             for (int i = 0; i < n; ++i) {
                 float s = 0.0f;
-                for (int l = 0; l < n; ++l) s += YF[i * LD + l] * Y32[lane * LD + l];
-                F32[i * LD + lane] = sk * s + sm.vf[i];
+                for (int l = 0; l < n; ++l) s += YF[i * ld + l] * Y32[lane * ld + l];
+                F32[i * ld + lane] = sk * s + sm.vf[i];
             }
         __syncwarp();
         if (lane < k) {
             const int m = lane;
             for (int a = 0; a < 9; ++a) {
                 float s = 0.0f;
-                for (int j = 0; j < k; ++j) s += sm.dX[a * k + j] * F32[j * LD + m];
+                for (int j = 0; j < k; ++j) s += sm.dX[a * k + j] * F32[j * ld + m];
                 fc[a * plane + m] = sm.xbar[a] + s;
             }
         }
@@ -1173,32 +1223,31 @@ cudaError_t launch_obs_gram(const double* dY, int nobs, int k, double* G, cudaSt
     return cudaGetLastError();
 }
 
-size_t analyze_scratch_bytes(int nx, int ny, int fp32) {
+size_t analyze_scratch_bytes(int nx, int ny, int fp32, int npts) {
     if (!fp32) return 0;
     const long long cells = (long long)nx * ny;
     const long long chunk = cells < kChunkCells ? cells : kChunkCells;
-    return 2 * (size_t)chunk * kXStride * sizeof(float);  // double-buffered
+    return 2 * (size_t)chunk * mix_scratch_bytes_per_point(2 * npts);  // double-buffered
 }
 
 cudaError_t launch_analyze(void* f, int fp32, int nx, int ny, int k, const ObsParams& o,
-                           double d_cut, double beta, int* flags, float* scratch,
+                           double d_cut, double beta, int nmax, int* flags, void* scratch,
                            const AnalyzeAux* aux, cudaStream_t s) {
     const long long cells = (long long)nx * ny;
     if (cells > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     cudaError_t e;
     if (fp32) {
         if (!o.dY32 || !scratch || !aux) return cudaErrorInvalidValue;
-        const size_t nd = (size_t)2 * o.npts * k;
+        const int nobs = 2 * o.npts;
+        const int nm = nmax < 2 ? 2 : (nmax > NMAX ? NMAX : nmax);
+        const size_t nd = (size_t)nobs * k;
         to_f32_kernel<<<(unsigned)((nd + 255) / 256), 256, 0, s>>>(o.dY, o.dY32, nd);
-        const size_t shA = (size_t)kJacWarps * 2 * o.npts * (sizeof(double) + sizeof(int));
-        const size_t shB = mix_smem_bytes(k, 2 * o.npts);
-        e = cudaFuncSetAttribute(mixed_jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)shA);
-        if (e != cudaSuccess) return e;
+        const size_t shB = mix_smem_bytes(k, nobs, nm);
         e = cudaFuncSetAttribute(analyze_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)shB);
         if (e != cudaSuccess) return e;
         const long long chunk = cells < kChunkCells ? cells : kChunkCells;
+        const size_t buf_bytes = (size_t)chunk * mix_scratch_bytes_per_point(nobs);
         // Pipeline: (A) of chunk c on s2 overlaps (B) of chunk c-1 on s; the
         // scratch is double-buffered, (A) of chunk c waits for (B) of c-2.
         if ((e = cudaEventRecord(aux->start, s)) != cudaSuccess) return e;
@@ -1207,15 +1256,16 @@ cudaError_t launch_analyze(void* f, int fp32, int nx, int ny, int k, const ObsPa
         for (long long c0 = 0; c0 < cells; c0 += chunk, ++c) {
             const int nc = (int)((cells - c0) < chunk ? (cells - c0) : chunk);
             const int b = c & 1;
-            float* X = scratch + (size_t)b * chunk * kXStride;
+            const MixScratch sc = mix_scratch_at((unsigned char*)scratch + b * buf_bytes, (int)chunk,
+                                                 nobs);
             if (c >= 2 && (e = cudaStreamWaitEvent(aux->s2, aux->ref_done[b], 0)) != cudaSuccess)
                 return e;
-            mixed_jacobi_kernel<<<(unsigned)((nc + kJacWarps - 1) / kJacWarps), 32 * kJacWarps, shA,
-                                  aux->s2>>>(nx, ny, k, o, d_cut, beta, (int)c0, nc, X, flags);
+            mixed_jacobi_kernel<<<(unsigned)((nc + kJacWarps - 1) / kJacWarps), 32 * kJacWarps, 0,
+                                  aux->s2>>>(nx, ny, k, o, d_cut, beta, (int)c0, nc, sc, flags);
             if ((e = cudaEventRecord(aux->jac_done[b], aux->s2)) != cudaSuccess) return e;
             if ((e = cudaStreamWaitEvent(s, aux->jac_done[b], 0)) != cudaSuccess) return e;
             analyze_mixed_kernel<<<(unsigned)nc, 32, shB, s>>>((float*)f, nx, ny, k, o, d_cut, beta,
-                                                               (int)c0, X, flags);
+                                                               (int)c0, nm, sc, flags);
             if ((e = cudaEventRecord(aux->ref_done[b], s)) != cudaSuccess) return e;
         }
     } else {

@@ -130,7 +130,7 @@ extern "C" int letkf_analyze_noalloc(double* f, int nx, int ny, int members, int
     e = launch_obs_gram(dY, 2 * npts, members, G, s);
     if (e != cudaSuccess) return cuda_fail(e, "launching the observation Gram");
     ObsParams o{npts, ix_d, iy_d, dY, d, G, sigma_u, sigma_v};
-    e = launch_analyze(f, 0, nx, ny, members, o, d_cut, beta, flags, nullptr, nullptr, s);
+    e = launch_analyze(f, 0, nx, ny, members, o, d_cut, beta, 0, flags, nullptr, nullptr, s);
     if (e != cudaSuccess) return cuda_fail(e, "launching the analysis");
     int h = 0;
     e = cudaMemcpyAsync(&h, flags, sizeof(int), cudaMemcpyDeviceToHost, s);
