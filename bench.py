@@ -34,6 +34,14 @@ METRIC = "LBM-LETKF cycles/s at 256^2 x 64 members (mixed precision; FP64 alongs
 HBM_FALLBACK_GBS = 6800.0
 FP64_NOMINAL_GFLOPS = 1250.0  # GB300 FP64 (CUDA-core and tensor) nominal rate
 L2_NOTE = "state larger than L2: 151 MB per buffer in FP32, 302 MB in FP64 (L2 = 129 MiB)"
+# DRAM bytes (read + write) per launch from one ncu capture of the current
+# kernels (profiles/*_256x256_k64.md; ncu flushes L2 before each kernel).
+# Set an entry to None when its kernel changes until it is captured again.
+NCU_TRAFFIC = {
+    "analysis_mixed": 8 * (1.182208e6 + 0.963584e6 + 48.544e6 + 0.054528e6),  # 8 chunks
+    "lbm_step_f32": 151.546368e6 + 98.118144e6,
+    "analysis_fp64": 306.105344e6 + 242.158336e6,
+}
 
 
 def _dist():
@@ -334,16 +342,22 @@ def main():
                           "achieved_gflops": flops / (fp64["analysis_ms"] * 1e6)},
     }
     lbm_share = mixed["lbm_step_ms"] * cfg.steps_per_cycle
+    kern["lbm_step_f32"]["traffic"] = NCU_TRAFFIC["lbm_step_f32"]
+    kern["analysis_mixed"]["traffic"] = NCU_TRAFFIC["analysis_mixed"]
+    kern["analysis_fp64"]["traffic"] = NCU_TRAFFIC["analysis_fp64"]
     if lbm_share >= mixed["analysis_ms"]:
         ach = kern["lbm_step_f32"]["achieved_gbs"]
         roof = {"kernel": "lbm_step_kernel<float,4,shift>", "bound": "hbm", "achieved": ach, "peak": hbm,
-                "unit": "GB/s", "frac": ach / hbm, "traffic": None,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback"}
+                "unit": "GB/s", "frac": ach / hbm, "traffic": NCU_TRAFFIC["lbm_step_f32"],
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback"}
     else:
         ach = kern["analysis_mixed"]["achieved_gflops"]
-        roof = {"kernel": "analyze_kernel<float,shift>", "bound": "alu", "achieved": ach / 1000.0,
+        roof = {"kernel": "analysis stage: mixed_jacobi_kernel + analyze_mixed_kernel over 8 chunks",
+                "bound": "alu", "achieved": ach / 1000.0,
                 "peak": FP64_NOMINAL_GFLOPS / 1000.0, "unit": "TFLOP/s", "frac": ach / FP64_NOMINAL_GFLOPS,
-                "traffic": None, "peak_source": "GB300 FP64 nominal 1.25 TFLOP/s"}
+                "traffic": NCU_TRAFFIC["analysis_mixed"],
+                "peak_source": "GB300 FP64 nominal 1.25 TFLOP/s (FMA microbenchmark: 1.20)",
+                "work": "algorithmic FP64 flops: 9 n^3 symmetric eigensolve + 2 per multiply-add of the products"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
