@@ -40,7 +40,7 @@ L2_NOTE = "state larger than L2: 151 MB per buffer in FP32, 302 MB in FP64 (L2 =
 NCU_TRAFFIC = {
     "analysis_mixed": 8 * (1.182208e6 + 0.963584e6 + 48.544e6 + 0.054528e6),  # 8 chunks
     "lbm_step_f32": 151.546368e6 + 98.118144e6,
-    "analysis_fp64": 306.105344e6 + 242.158336e6,
+    "analysis_fp64": None,  # kernel changed since its capture
 }
 
 
