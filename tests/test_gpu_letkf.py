@@ -199,3 +199,18 @@ def test_repeated_observe_calls_reuse_staging(gpu):
             ref = oracle.letkf_analyze(ref, ix[sel], iy[sel], yu[sel] * (1 + c), yv[sel], SIGMA, SIGMA, 5.0, 1.05)
         got = e.get_f()
     assert norm_rel(got, ref) <= TOL_FP64
+
+
+@pytest.mark.parametrize("nx,ny,k,nox,noy,d_cut", [(24, 24, 40, 4, 4, 5.0), (24, 20, 8, 4, 4, 6.0)])
+def test_mixed_analysis_is_limited_by_binary32_products_only(gpu, nx, ny, k, nox, noy, d_cut):
+    """On a state whose f - w is exact in binary32, the mixed path differs from
+    the FP64 oracle only by its binary32 storage and transform products
+    (~1e-10 of max |f|), not by the eigensolve, which is refined in FP64."""
+    from _helpers import W_REST
+
+    f, ix, iy, yu, yv = _analysis_case(nx, ny, k, nox, noy, seed=61 + k)
+    w = np.asarray(W_REST)[:, None, None, None]
+    f = ((f - w).astype(np.float32).astype(np.float64)) + w
+    got = _gpu_analysis(gpu, f, ix, iy, yu, yv, d_cut, 1.05, gpu.LBM_MIXED)
+    ref = oracle.letkf_analyze(f, ix, iy, yu, yv, SIGMA, SIGMA, d_cut, 1.05)
+    assert norm_rel(got, ref) <= 1e-8

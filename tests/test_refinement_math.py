@@ -1,0 +1,117 @@
+"""The matrix-function identities the CUDA analysis relies on, checked in
+numpy against direct eigendecomposition (CPU only):
+
+* the observation-space form of the LETKF transform (p < k): with
+  Yh = diag(sqrt(rho)) dY, A = Yh Yh^T and a = (k-1)/beta,
+  w-bar = Yh^T (aI + A)^{-1} d-hat and
+  C^{-1/2} = a^{-1/2} I + Yh^T g(A) Yh, g(s) = ((a+s)^{-1/2} - a^{-1/2}) / s;
+* the closed-form divided differences used to evaluate f(S) to first order
+  in the off-diagonal of a nearly diagonal S (Daleckii-Krein);
+* the refinement of a binary32 eigenbasis in FP64 (Cholesky QR, Rayleigh-Ritz,
+  first-order matrix functions) reaching FP64-level accuracy.
+"""
+import numpy as np
+import pytest
+
+
+def _problem(k, p, seed, beta=1.05):
+    rng = np.random.default_rng(seed)
+    Yf = 0.003 * rng.standard_normal((p, k))
+    dY = Yf - Yf.mean(axis=1, keepdims=True)
+    rho = rng.uniform(0.01, 1.0, p) / 0.00289**2
+    d = 0.003 * rng.standard_normal(p)
+    return dY, rho, d, (k - 1) / beta
+
+
+def _fun(M, f):
+    w, V = np.linalg.eigh(M)
+    return V @ np.diag(f(w)) @ V.T
+
+
+def test_observation_space_form_equals_ensemble_space_form():
+    k, p = 64, 25
+    dY, rho, d, a = _problem(k, p, 1)
+    Yh = np.sqrt(rho)[:, None] * dY
+    C = a * np.eye(k) + Yh.T @ Yh
+    Pt = np.linalg.inv(C)
+    wbar = Pt @ Yh.T @ (np.sqrt(rho) * d)
+    Cih = _fun(C, lambda x: x ** -0.5)
+    A = Yh @ Yh.T
+    g = lambda s: ((a + s) ** -0.5 - a ** -0.5) / s  # noqa: E731
+    wbar_obs = Yh.T @ np.linalg.solve(a * np.eye(p) + A, np.sqrt(rho) * d)
+    Cih_obs = a ** -0.5 * np.eye(k) + Yh.T @ _fun(A, g) @ Yh
+    np.testing.assert_allclose(wbar_obs, wbar, rtol=1e-12, atol=1e-14 * np.abs(wbar).max())
+    np.testing.assert_allclose(Cih_obs, Cih, rtol=0, atol=1e-13 * np.abs(Cih).max())
+
+
+@pytest.mark.parametrize("x,y", [(3.0, 7.0), (100.0, 100.0 + 1e-9), (0.5, 900.0), (0.0, 1e-12)])
+def test_closed_form_divided_differences(x, y):
+    a = 60.0
+    r, u, w = np.sqrt(a), np.sqrt(a + x), np.sqrt(a + y)
+    # g(s) = q[s, 0], q(s) = (a+s)^{-1/2}; g[x, y] in closed form.
+    gxy = (u + w + r) / (r * u * w * (u + r) * (w + r) * (u + w))
+    # Reference in extended precision (mpmath-free: Python fractions of the
+    # series around the midpoint are overkill; use longdouble differences
+    # when x, y are well separated, the derivative otherwise).
+    g = lambda s: -1.0 / (np.sqrt(a + s) * r * (np.sqrt(a + s) + r))  # noqa: E731
+    if abs(x - y) > 1e-3:
+        ref = (g(x) - g(y)) / (x - y)
+    else:
+        m, h = 0.5 * (x + y), 1e-4
+        ref = (g(m + h) - g(m - h)) / (2 * h)
+    assert abs(gxy - ref) <= 1e-7 * abs(ref)
+    # h(s) = 1/(a+s): h[x, y] = -1 / ((a+x)(a+y)).
+    hxy = -1.0 / ((a + x) * (a + y))
+    if abs(x - y) > 1e-3:
+        assert abs(hxy - (1 / (a + x) - 1 / (a + y)) / (x - y)) <= 1e-12 * abs(hxy)
+
+
+def _jacobi32(A, sweeps=8):
+    A = A.astype(np.float32).copy()
+    n = A.shape[0]
+    U = np.eye(n, dtype=np.float32)
+    thresh = np.float32(3e-8) * np.sqrt(np.float32((A.astype(np.float64) ** 2).sum()))
+    for _ in range(sweeps):
+        for pp in range(n - 1):
+            for qq in range(pp + 1, n):
+                apq = A[pp, qq]
+                if abs(apq) <= thresh:
+                    continue
+                tau = (A[qq, qq] - A[pp, pp]) / (np.float32(2) * apq)
+                t = np.float32(1 if tau >= 0 else -1) / (abs(tau) + np.sqrt(np.float32(1) + tau * tau))
+                c = np.float32(1) / np.sqrt(np.float32(1) + t * t)
+                s = t * c
+                J = np.eye(n, dtype=np.float32)
+                J[pp, pp] = J[qq, qq] = c
+                J[pp, qq], J[qq, pp] = s, -s
+                A = J.T @ A @ J
+                U = U @ J
+    return U.astype(np.float64)
+
+
+def test_binary32_basis_refined_in_fp64_gives_fp64_matrix_functions():
+    k, p = 64, 20
+    dY, rho, d, a = _problem(k, p, 3)
+    Yh = np.sqrt(rho)[:, None] * dY
+    A = Yh @ Yh.T
+    X = _jacobi32(A)
+    # Cholesky QR in FP64, then the Rayleigh-Ritz matrix.
+    L = np.linalg.cholesky(X.T @ X)
+    Y = np.linalg.solve(L, X.T).T
+    S = Y.T @ A @ Y
+    s = np.diag(S)
+    r = np.sqrt(a)
+    u = np.sqrt(a + s)
+    alpha = 1.0 / (u * (u + r))
+    G = S * (u[:, None] + u[None, :] + r) * np.outer(alpha, alpha) / (r * (u[:, None] + u[None, :]))
+    np.fill_diagonal(G, -alpha / r)
+    H = -S / np.outer(a + s, a + s)
+    np.fill_diagonal(H, 1.0 / (a + s))
+    g = lambda x: ((a + x) ** -0.5 - a ** -0.5) / x  # noqa: E731
+    G_ref = _fun(A, g)
+    H_ref = np.linalg.inv(a * np.eye(p) + A)
+    assert np.abs(Y @ G @ Y.T - G_ref).max() <= 1e-12 * np.abs(G_ref).max()
+    assert np.abs(Y @ H @ Y.T - H_ref).max() <= 1e-12 * np.abs(H_ref).max()
+    # The binary32 basis alone is only good to ~1e-6.
+    w32 = np.diag(X.T @ A @ X)
+    assert np.abs(X @ np.diag(g(w32)) @ X.T - G_ref).max() > 1e-9 * np.abs(G_ref).max()
