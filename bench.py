@@ -51,6 +51,22 @@ def _dist():
     return rank, world, local
 
 
+def reduce_max(x: float, world: int) -> float:
+    """Max of x over the ranks of the process group (x itself at world 1)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(ms_per_cycle_max: float, world: int) -> float:
+    """Whole-job cycles/s of `world` independent replicas timed by the slowest."""
+    return world * 1000.0 / ms_per_cycle_max
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -309,13 +325,7 @@ def main():
     build.build()
     binding.load()
 
-    def barrier_max(x):
-        if world == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    barrier_max = lambda x: reduce_max(x, world)  # noqa: E731
 
     if world > 1:
         import torch.distributed as dist
@@ -371,14 +381,14 @@ def main():
         cpu = oracle_cycle_sample(cfg)
 
     if rank == 0:
-        value = world * 1000.0 / ms
+        value = replica_value(ms, world)
         line = {
             "metric": METRIC, "value": value, "unit": "cycles/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 LBM + f64 eigensolve (mixed)", "data": "synthetic",
             "config": {"workload": cfg.name(), "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": L2_NOTE},
-            "fp64": {"value": world * 1000.0 / ms64, "unit": "cycles/s", "ms_per_step": ms64,
+            "fp64": {"value": replica_value(ms64, world), "unit": "cycles/s", "ms_per_step": ms64,
                      "dtype": "f64"},
             "e2e": {"value": world / e2e_val, "unit": "cycles/s",
                     "h2d_bytes_per_step": e2e["h2d_bytes_per_step"],
