@@ -122,6 +122,17 @@ int letkf_observe(lbm_ctx *ctx, int npts, const int *ix, const int *iy,
  * members >= 2. Asynchronous. */
 int letkf_analyze(lbm_ctx *ctx, double d_cut, double beta);
 
+/* Nudging, the paper's comparison method (Section 3.1): every member is
+ * relaxed toward the equilibrium of the observed macroscopic field,
+ * f_alpha <- f_alpha + gamma (f^eq_alpha(rho^, u^, v^) - f_alpha), 0 <= gamma <= 1.
+ * The observations sit on the uniform periodic lattice of points
+ * (i nx/nobs_x, j ny/nobs_y): host arrays rho_o, u_o, v_o [nobs_y][nobs_x]
+ * (copied before the call returns). rho^, u^, v^ at a grid point are their
+ * bilinear interpolation (the paper's "simple linear interpolation"). nx and
+ * ny must be multiples of nobs_x and nobs_y. Asynchronous. */
+int lbm_nudge(lbm_ctx *ctx, int nobs_x, int nobs_y, const double *rho_o,
+              const double *u_o, const double *v_o, double gamma);
+
 /* Copy the state out (checkpoint, parity) or in (restart, fault tests).
  * Layout f [9][ny][nx][members] FP64. lbm_get_f with LBM_PTR_HOST
  * synchronises. */

@@ -65,6 +65,7 @@ def _load():
             "orc_local_obs": (I, [I, I, I, I, I, P, P, D, D, D, P, P]),
             "orc_letkf_analyze": (I, [I, I, I, P, I, P, P, P, P, D, D, D, D, I, P]),
             "orc_num_threads": (I, []),
+            "orc_nudge": (None, [I, I, I, P, I, I, P, P, P, D]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -216,6 +217,18 @@ def letkf_analyze(f: np.ndarray, ix, iy, yo_u, yo_v, sigma_u, sigma_v, d_cut, be
                                    float(sigma_u), float(sigma_v), float(d_cut), float(beta), npoints, _p(pts))
     if st != 0:
         raise RuntimeError("oracle eigensolver did not converge")
+    return f
+
+
+def nudge(f: np.ndarray, rho_o, u_o, v_o, gamma: float) -> np.ndarray:
+    """Nudging of f [9][ny][nx][k] toward f^eq of the observed fields
+    [noy][nox] on the uniform lattice (bilinear interpolation); new array."""
+    f = _f64(f).copy()
+    rho_o, u_o, v_o = _f64(rho_o), _f64(u_o), _f64(v_o)
+    _, ny, nx, k = f.shape
+    noy, nox = rho_o.shape
+    assert nx % nox == 0 and ny % noy == 0
+    _load().orc_nudge(nx, ny, k, _p(f), nox, noy, _p(rho_o), _p(u_o), _p(v_o), float(gamma))
     return f
 
 

@@ -156,3 +156,31 @@ void orc_observe(int nx, int ny, int k, const double *f, int npts,
             Yf[(size_t)(2 * j + 1) * k + m] = jy / r;
         }
 }
+
+/* Bilinear interpolation of a periodic field on the observation lattice. */
+static double interp_obs(const double *g, int nox, int noy, int px, int py, int x, int y) {
+    int i0 = x / px, j0 = y / py;
+    double tx = (double)(x - i0 * px) / px;
+    double ty = (double)(y - j0 * py) / py;
+    int i1 = (i0 + 1) % nox, j1 = (j0 + 1) % noy;
+    return (1.0 - tx) * (1.0 - ty) * g[(size_t)j0 * nox + i0] + tx * (1.0 - ty) * g[(size_t)j0 * nox + i1] +
+           (1.0 - tx) * ty * g[(size_t)j1 * nox + i0] + tx * ty * g[(size_t)j1 * nox + i1];
+}
+
+void orc_nudge(int nx, int ny, int k, double *f, int nox, int noy,
+               const double *rho_o, const double *u_o, const double *v_o,
+               double gamma) {
+    int px = nx / nox, py = ny / noy;
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            double feq[9];
+            orc_equilibrium(interp_obs(rho_o, nox, noy, px, py, x, y),
+                            interp_obs(u_o, nox, noy, px, py, x, y),
+                            interp_obs(v_o, nox, noy, px, py, x, y), feq);
+            for (int m = 0; m < k; ++m)
+                for (int a = 0; a < 9; ++a) {
+                    size_t i = fidx(a, y, x, m, nx, ny, k);
+                    f[i] = f[i] + gamma * (feq[a] - f[i]);
+                }
+        }
+}

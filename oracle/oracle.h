@@ -92,6 +92,16 @@ int orc_letkf_analyze(int nx, int ny, int k, double *f, int npts,
                       double d_cut, double beta, int npoints,
                       const int *points);
 
+/* Nudging (Section 3.1): every member is relaxed toward the equilibrium of
+ * the observed macroscopic field, f_a <- f_a + gamma (f^eq_a(rho^, u^, v^) - f_a).
+ * Observations sit on the uniform periodic lattice (i nx/nox, j ny/noy),
+ * arrays [noy][nox]; rho^, u^, v^ at a grid point are their bilinear
+ * interpolation ("simple linear interpolation" of the sparse data). nx must
+ * be a multiple of nox and ny of noy. In place on f. */
+void orc_nudge(int nx, int ny, int k, double *f, int nox, int noy,
+               const double *rho_o, const double *u_o, const double *v_o,
+               double gamma);
+
 /* Number of OpenMP threads the oracle will use (1 without OpenMP). */
 int orc_num_threads(void);
 

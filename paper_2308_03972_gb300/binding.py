@@ -44,6 +44,7 @@ SIGNATURES = {
     "lbm_mean_velocity": (_I, [_P, _P, _P, _I]),
     "letkf_observe": (_I, [_P, _I, _P, _P, _P, _P, _D, _D]),
     "letkf_analyze": (_I, [_P, _D, _D]),
+    "lbm_nudge": (_I, [_P, _I, _I, _P, _P, _P, _D]),
     "lbm_get_f": (_I, [_P, _P, _I]),
     "lbm_set_f": (_I, [_P, _P, _I]),
     "lbm_sync": (_I, [_P]),
@@ -195,6 +196,18 @@ def letkf_analyze(ctx, d_cut, beta):
     _check(ctx, load().letkf_analyze(ctx, float(d_cut), float(beta)))
 
 
+def lbm_nudge(ctx, rho_o, u_o, v_o, gamma):
+    """Nudge every member toward f^eq of observed fields [nobs_y][nobs_x]."""
+    rho_o = np.ascontiguousarray(rho_o, dtype=np.float64)
+    u_o = np.ascontiguousarray(u_o, dtype=np.float64)
+    v_o = np.ascontiguousarray(v_o, dtype=np.float64)
+    if not (rho_o.shape == u_o.shape == v_o.shape) or rho_o.ndim != 2:
+        raise ValueError("observation fields must share one 2-d shape [nobs_y][nobs_x]")
+    noy, nox = rho_o.shape
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    _check(ctx, load().lbm_nudge(ctx, nox, noy, p(rho_o), p(u_o), p(v_o), float(gamma)))
+
+
 def lbm_get_f(ctx, out):
     po, ko, _a = _arr(out, writable=True)
     _check(ctx, load().lbm_get_f(ctx, po, ko))
@@ -276,6 +289,9 @@ class Ensemble:
 
     def analyze(self, d_cut, beta):
         letkf_analyze(self.ctx, d_cut, beta)
+
+    def nudge(self, rho_o, u_o, v_o, gamma):
+        lbm_nudge(self.ctx, rho_o, u_o, v_o, gamma)
 
     def get_f(self, out=None):
         if out is None:

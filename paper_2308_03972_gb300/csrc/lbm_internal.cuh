@@ -53,6 +53,10 @@ cudaError_t launch_lbm_step_f64(const double* fin, double* fout, const double* f
                                 const LbmParams& p, int* flags, cudaStream_t s);
 cudaError_t launch_lbm_step_f32(const float* gin, float* gout, const float* force,
                                 const LbmParams& p, int* flags, cudaStream_t s);
+// Nudging toward f^eq of observations on a uniform lattice; obs = rho, u, v
+// fields [3][noy][nox] in device memory.
+cudaError_t launch_nudge(void* f, int fp32, int nx, int ny, int k, int nox, int noy,
+                         const double* obs, double gamma, cudaStream_t s);
 cudaError_t launch_moments(const void* f, int fp32, int nx, int ny, int k, double* rho,
                            double* u, double* v, int* flags, cudaStream_t s);
 cudaError_t launch_mean_velocity(const void* f, int fp32, int nx, int ny, int k, double* u,

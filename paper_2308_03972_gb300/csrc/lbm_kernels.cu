@@ -179,6 +179,59 @@ __global__ void __launch_bounds__(256) lbm_step_kernel(const T* __restrict__ fin
     Vec<T, V>::st(dst(8, xm, yp), f[8]);
 }
 
+// Nudging (arXiv 2308.03972, Section 3.1): f_a <- f_a + gamma (f^eq_a(rho^, u^, v^) - f_a)
+// for every member, with (rho^, u^, v^) the bilinear interpolation of the
+// observations on the uniform periodic lattice (spacing px, py) to the cell.
+template <typename T, int V, bool SHIFT>
+__global__ void __launch_bounds__(256) nudge_kernel(T* __restrict__ f, int nx, int ny, int k,
+                                                    int nox, int noy, const double* __restrict__ obs,
+                                                    double gamma) {
+    const int kv = k / V;
+    const long long total = (long long)nx * ny * kv;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    const int mv = (int)(t % kv);
+    const long long cell = t / kv;
+    const int x = (int)(cell % nx), y = (int)(cell / nx);
+    const int px = nx / nox, py = ny / noy;
+    const int i0 = x / px, j0 = y / py;
+    const double tx = (double)(x - i0 * px) / px, ty = (double)(y - j0 * py) / py;
+    const int i1 = (i0 + 1 == nox) ? 0 : i0 + 1, j1 = (j0 + 1 == noy) ? 0 : j0 + 1;
+    const size_t no = (size_t)nox * noy;
+    const size_t c00 = (size_t)j0 * nox + i0, c01 = (size_t)j0 * nox + i1;
+    const size_t c10 = (size_t)j1 * nox + i0, c11 = (size_t)j1 * nox + i1;
+    const double w00 = (1.0 - tx) * (1.0 - ty), w01 = tx * (1.0 - ty);
+    const double w10 = (1.0 - tx) * ty, w11 = tx * ty;
+    double q[3];
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+        const double* g = obs + v * no;
+        q[v] = w00 * g[c00] + w01 * g[c01] + w10 * g[c10] + w11 * g[c11];
+    }
+    const double rho = q[0], ux = q[1], uy = q[2];
+    const double uu = ux * ux + uy * uy;
+    T feq[9];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+        const double cu = d2q9_cx(a) * ux + d2q9_cy(a) * uy;
+        const double w = d2q9_w(a);
+        // f^eq (or f^eq - w) in FP64, then in the state's type.
+        const double dev = w * ((rho - 1.0) + rho * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu));
+        feq[a] = SHIFT ? (T)dev : (T)(w + dev);
+    }
+    const size_t plane = (size_t)nx * ny * k;
+    const size_t base = (size_t)cell * k + (size_t)mv * V;
+    const T gm = (T)gamma;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+        T v[V];
+        Vec<T, V>::ld(f + a * plane + base, v);
+#pragma unroll
+        for (int j = 0; j < V; ++j) v[j] = v[j] + gm * (feq[a] - v[j]);
+        Vec<T, V>::st(f + a * plane + base, v);
+    }
+}
+
 template <typename T, int V, bool SHIFT>
 cudaError_t launch_step_v(const T* fin, T* fout, const T* force, const LbmParams& p, int* flags,
                           cudaStream_t s) {
@@ -312,6 +365,28 @@ cudaError_t launch_lbm_step_f32(const float* gin, float* gout, const float* forc
     if (p.k % 4 == 0) return launch_step_v<float, 4, true>(gin, gout, force, p, flags, s);
     if (p.k % 2 == 0) return launch_step_v<float, 2, true>(gin, gout, force, p, flags, s);
     return launch_step_v<float, 1, true>(gin, gout, force, p, flags, s);
+}
+
+cudaError_t launch_nudge(void* f, int fp32, int nx, int ny, int k, int nox, int noy,
+                         const double* obs, double gamma, cudaStream_t s) {
+    const int V = fp32 ? (k % 4 == 0 ? 4 : (k % 2 == 0 ? 2 : 1)) : (k % 2 == 0 ? 2 : 1);
+    const long long total = (long long)nx * ny * (k / V);
+    const long long nb = (total + 255) / 256;
+    if (nb > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    if (fp32) {
+        if (V == 4)
+            nudge_kernel<float, 4, true><<<(unsigned)nb, 256, 0, s>>>((float*)f, nx, ny, k, nox, noy, obs, gamma);
+        else if (V == 2)
+            nudge_kernel<float, 2, true><<<(unsigned)nb, 256, 0, s>>>((float*)f, nx, ny, k, nox, noy, obs, gamma);
+        else
+            nudge_kernel<float, 1, true><<<(unsigned)nb, 256, 0, s>>>((float*)f, nx, ny, k, nox, noy, obs, gamma);
+    } else {
+        if (V == 2)
+            nudge_kernel<double, 2, false><<<(unsigned)nb, 256, 0, s>>>((double*)f, nx, ny, k, nox, noy, obs, gamma);
+        else
+            nudge_kernel<double, 1, false><<<(unsigned)nb, 256, 0, s>>>((double*)f, nx, ny, k, nox, noy, obs, gamma);
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_moments(const void* f, int fp32, int nx, int ny, int k, double* rho,

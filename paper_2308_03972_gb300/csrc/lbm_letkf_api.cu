@@ -41,6 +41,8 @@ struct lbm_ctx {
     int geo_nmax = 0;
     AnalyzeAux aux{};              // second stream + events (mixed precision)
     bool aux_ready = false;
+    double* nudge_obs = nullptr;  // [3][noy][nox] nudging observations
+    size_t nudge_cap = 0;
     double* h_yo = nullptr;  // pinned staging [2 cap]
     int* h_ixy = nullptr;    // pinned staging [2 cap] (ix then iy)
     cudaEvent_t obs_copied = nullptr;  // last staging copy done
@@ -444,6 +446,36 @@ int letkf_analyze(lbm_ctx* c, double d_cut, double beta) {
     return LBM_OK;
 }
 
+int lbm_nudge(lbm_ctx* c, int nobs_x, int nobs_y, const double* rho_o, const double* u_o,
+              const double* v_o, double gamma) {
+    if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (nobs_x < 1 || nobs_y < 1 || c->nx % nobs_x != 0 || c->ny % nobs_y != 0)
+        return fail(c, LBM_EINVAL, "nx, ny must be multiples of nobs_x, nobs_y");
+    if (!rho_o || !u_o || !v_o) return fail(c, LBM_EINVAL, "NULL observation field");
+    if (!(gamma >= 0.0 && gamma <= 1.0)) return fail(c, LBM_EINVAL, "gamma must be in [0, 1]");
+    const size_t no = (size_t)nobs_x * nobs_y;
+    for (size_t i = 0; i < no; ++i)
+        if (!std::isfinite(rho_o[i]) || !std::isfinite(u_o[i]) || !std::isfinite(v_o[i]) || !(rho_o[i] > 0.0))
+            return fail(c, LBM_EINVAL, "observation %zu is not finite or has rho <= 0", i);
+    if (3 * no > c->nudge_cap) {
+        CK(c, cudaStreamSynchronize(c->stream), "synchronising");
+        cudaFree(c->nudge_obs);
+        c->nudge_obs = nullptr;
+        c->nudge_cap = 0;
+        CK(c, cudaMalloc(&c->nudge_obs, 3 * no * sizeof(double)), "allocating nudging observations");
+        c->nudge_cap = 3 * no;
+    }
+    // Copies from pageable memory are staged before the call returns.
+    CK(c, cudaMemcpyAsync(c->nudge_obs, rho_o, no * 8, cudaMemcpyHostToDevice, c->stream), "copy rho");
+    CK(c, cudaMemcpyAsync(c->nudge_obs + no, u_o, no * 8, cudaMemcpyHostToDevice, c->stream), "copy u");
+    CK(c, cudaMemcpyAsync(c->nudge_obs + 2 * no, v_o, no * 8, cudaMemcpyHostToDevice, c->stream), "copy v");
+    CK(c, launch_nudge(c->f[c->cur], is_fp32(c), c->nx, c->ny, c->k, nobs_x, nobs_y, c->nudge_obs,
+                       gamma, c->stream),
+       "launching nudging");
+    c->observed = false;
+    return LBM_OK;
+}
+
 int lbm_get_f(lbm_ctx* c, double* f, int ptr_kind) {
     if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
     if (!f) return fail(c, LBM_EINVAL, "f is NULL");
@@ -510,6 +542,7 @@ void lbm_destroy(lbm_ctx* c) {
     cudaFree(c->flags);
     cudaFree(c->stage);
     cudaFree(c->ana_scratch);
+    cudaFree(c->nudge_obs);
     if (c->aux_ready) {
         cudaStreamSynchronize(c->aux.s2);
         cudaEventDestroy(c->aux.start);

@@ -219,3 +219,43 @@ def test_observation_of_equilibrium_returns_velocity():
     r2, u2, v2 = oracle.moments(f)
     np.testing.assert_allclose(r2, rho, rtol=1e-15)
     np.testing.assert_allclose(u2, u, rtol=0, atol=1e-16)
+
+
+def _obs_fields(nox, noy, seed):
+    rng = np.random.default_rng(seed)
+    return (1 + 0.01 * rng.standard_normal((noy, nox)), 0.03 * rng.standard_normal((noy, nox)),
+            0.03 * rng.standard_normal((noy, nox)))
+
+
+def test_nudging_limits_and_moments():
+    """Nudging (Section 3.1) is linear in gamma: gamma = 0 leaves f alone,
+    gamma = 1 replaces it by f^eq of the interpolated observations, and the
+    density moves as (1 - gamma) rho + gamma rho^."""
+    nx, ny, k = 12, 8, 3
+    f = inputs.random_positive_f(nx, ny, k, seed=21, base=W_REST, spread=0.05)
+    ro, uo, vo = _obs_fields(4, 2, 1)
+    np.testing.assert_array_equal(oracle.nudge(f, ro, uo, vo, 0.0), f)
+    f1 = oracle.nudge(f, ro, uo, vo, 1.0)
+    r1, u1, v1 = oracle.moments(f1)
+    # At observation points the interpolation returns the observation itself.
+    for j in range(2):
+        for i in range(4):
+            np.testing.assert_allclose(r1[j * 4, i * 3], ro[j, i], rtol=1e-14)
+            np.testing.assert_allclose(u1[j * 4, i * 3], uo[j, i], rtol=0, atol=1e-15)
+            np.testing.assert_allclose(v1[j * 4, i * 3], vo[j, i], rtol=0, atol=1e-15)
+    # Halfway between two observation points in x: the mean of the two.
+    np.testing.assert_allclose(u1[0, 1], (2 * uo[0, 0] + uo[0, 1]) / 3, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(u1[4, 10], (2 * uo[1, 3] + uo[1, 0]) / 3, rtol=0, atol=1e-15)
+    g = 0.3
+    r0, _, _ = oracle.moments(f)
+    rg, _, _ = oracle.moments(oracle.nudge(f, ro, uo, vo, g))
+    np.testing.assert_allclose(rg, (1 - g) * r0 + g * r1, rtol=1e-14)
+
+
+def test_dense_nudging_uses_the_observation_at_each_point():
+    nx, ny, k = 6, 5, 2
+    f = inputs.random_positive_f(nx, ny, k, seed=22, base=W_REST, spread=0.05)
+    ro, uo, vo = _obs_fields(nx, ny, 2)
+    r1, u1, v1 = oracle.moments(oracle.nudge(f, ro, uo, vo, 1.0))
+    np.testing.assert_allclose(r1, np.broadcast_to(ro[:, :, None], r1.shape), rtol=1e-14)
+    np.testing.assert_allclose(u1, np.broadcast_to(uo[:, :, None], u1.shape), rtol=0, atol=1e-15)
