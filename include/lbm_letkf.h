@@ -49,7 +49,7 @@ typedef struct lbm_ctx lbm_ctx;
 
 typedef enum {
     LBM_OK = 0,
-    LBM_EINVAL = 1,    /* bad argument, or local problem too large */
+    LBM_EINVAL = 1,    /* bad argument, or local problem too large (min(k, p) > 64) */
     LBM_ENOMEM = 2,    /* device allocation failed */
     LBM_ECUDA = 3,     /* CUDA runtime error (launch or copy) */
     LBM_EDIVERGED = 4, /* non-finite density/velocity or |u| > 0.5 seen */

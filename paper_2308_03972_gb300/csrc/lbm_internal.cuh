@@ -82,7 +82,7 @@ struct AnalyzeAux {
     cudaEvent_t start, jac_done[2], ref_done[2];
 };
 // Scratch the analysis needs (bytes; 0 for the FP64 path).
-size_t analyze_scratch_bytes(int nx, int ny, int fp32, int npts);
+size_t analyze_scratch_bytes(int nx, int ny, int fp32, int npts, int nmax);
 // nmax: largest local problem size n = min(p, k) over the grid (sizes the
 // mixed kernel's shared memory; points above it are reported as too large).
 cudaError_t launch_analyze(void* f, int fp32, int nx, int ny, int k, const ObsParams& o,

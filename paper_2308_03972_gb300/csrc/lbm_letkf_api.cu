@@ -109,7 +109,7 @@ int read_flags(lbm_ctx* c) {
     if (h & FLAG_DIVERGED)
         return fail(c, LBM_EDIVERGED, "state diverged: non-finite density/velocity or |u| > 0.5");
     if (h & FLAG_TOOLARGE)
-        return fail(c, LBM_EINVAL, "local analysis problem larger than the kernel supports (n > 32)");
+        return fail(c, LBM_EINVAL, "local analysis problem larger than the kernel supports (n = min(k, p) > 64)");
     return fail(c, LBM_ENOCONV, "eigensolver reached its sweep cap");
 }
 
@@ -419,7 +419,8 @@ int letkf_analyze(lbm_ctx* c, double d_cut, double beta) {
     if (!(d_cut > 0.0) || !std::isfinite(d_cut)) return fail(c, LBM_EINVAL, "d_cut must be > 0");
     if (!(beta > 0.0) || !std::isfinite(beta)) return fail(c, LBM_EINVAL, "beta must be > 0");
     if (!c->observed) return fail(c, LBM_EINVAL, "letkf_observe must precede letkf_analyze");
-    const size_t scratch = analyze_scratch_bytes(c->nx, c->ny, is_fp32(c), c->npts);
+    const int nmax = largest_local_problem(c, d_cut);
+    const size_t scratch = analyze_scratch_bytes(c->nx, c->ny, is_fp32(c), c->npts, nmax);
     if (scratch > c->ana_scratch_bytes) {
         CK(c, cudaStreamSynchronize(c->stream), "synchronising");
         cudaFree(c->ana_scratch);
@@ -428,7 +429,6 @@ int letkf_analyze(lbm_ctx* c, double d_cut, double beta) {
         CK(c, cudaMalloc(&c->ana_scratch, scratch), "allocating analysis scratch");
         c->ana_scratch_bytes = scratch;
     }
-    const int nmax = is_fp32(c) ? largest_local_problem(c, d_cut) : 0;
     if (is_fp32(c) && !c->aux_ready) {
         CK(c, cudaStreamCreateWithFlags(&c->aux.s2, cudaStreamNonBlocking), "creating stream");
         CK(c, cudaEventCreateWithFlags(&c->aux.start, cudaEventDisableTiming), "creating event");

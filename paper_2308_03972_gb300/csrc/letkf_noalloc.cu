@@ -130,7 +130,10 @@ extern "C" int letkf_analyze_noalloc(double* f, int nx, int ny, int members, int
     e = launch_obs_gram(dY, 2 * npts, members, G, s);
     if (e != cudaSuccess) return cuda_fail(e, "launching the observation Gram");
     ObsParams o{npts, ix_d, iy_d, dY, d, G, sigma_u, sigma_v};
-    e = launch_analyze(f, 0, nx, ny, members, o, d_cut, beta, 0, flags, nullptr, nullptr, s);
+    // No host-side stamp of the local sets here: size the kernel for the
+    // largest problem the inputs allow, min(k, p) with p = 2 * npts.
+    const int nmax = members < 2 * npts ? members : 2 * npts;
+    e = launch_analyze(f, 0, nx, ny, members, o, d_cut, beta, nmax, flags, nullptr, nullptr, s);
     if (e != cudaSuccess) return cuda_fail(e, "launching the analysis");
     int h = 0;
     e = cudaMemcpyAsync(&h, flags, sizeof(int), cudaMemcpyDeviceToHost, s);
@@ -138,7 +141,7 @@ extern "C" int letkf_analyze_noalloc(double* f, int nx, int ny, int members, int
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "synchronising");
     if (h & FLAG_DIVERGED) return fail(LBM_EDIVERGED, "state diverged");
-    if (h & FLAG_TOOLARGE) return fail(LBM_EINVAL, "local analysis problem larger than the kernel supports (n > 32)");
+    if (h & FLAG_TOOLARGE) return fail(LBM_EINVAL, "local analysis problem larger than the kernel supports (min(k, p) > 64)");
     if (h & FLAG_NOCONV) return fail(LBM_ENOCONV, "eigensolver reached its sweep cap");
     return LBM_OK;
 }

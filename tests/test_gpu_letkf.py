@@ -119,14 +119,31 @@ def test_argument_errors(gpu):
 
 
 def test_oversized_local_problem_is_reported(gpu):
-    # 64 members and 36 observation scalars in range: n = 36 > 32.
-    f, ix, iy, yu, yv = _analysis_case(24, 24, 64, 6, 3, seed=3)
-    with gpu.Ensemble(24, 24, 64, TAU0, CS, MU, gpu.LBM_FP64, f0=f) as e:
-        e.observe(ix, iy, yu, yv, SIGMA, SIGMA)
-        e.analyze(100.0, 1.0)
-        with pytest.raises(gpu.LbmError) as err:
-            e.sync()
-        assert err.value.code == gpu.LBM_EINVAL
+    # 80 members and 72 observation scalars in range: n = 72 > 64.
+    f, ix, iy, yu, yv = _analysis_case(24, 24, 80, 6, 6, seed=3)
+    for prec in (gpu.LBM_FP64, gpu.LBM_MIXED):
+        with gpu.Ensemble(24, 24, 80, TAU0, CS, MU, prec, f0=f) as e:
+            e.observe(ix, iy, yu, yv, SIGMA, SIGMA)
+            e.analyze(100.0, 1.0)
+            with pytest.raises(gpu.LbmError) as err:
+                e.sync()
+            assert err.value.code == gpu.LBM_EINVAL
+
+
+@pytest.mark.parametrize("nx,ny,k,nox,noy,d_cut", [
+    (24, 24, 64, 6, 3, 100.0),   # observation space, n = 36
+    (16, 16, 48, 8, 8, 100.0),   # ensemble space, n = k = 48
+    (20, 20, 64, 5, 5, 7.0),     # observation space, n up to ~40, ragged local sets
+])
+def test_larger_local_problems_match_oracle(gpu, nx, ny, k, nox, noy, d_cut):
+    """Local problems of 33..64 (two columns per lane; binary32 Jacobi in
+    shared memory on the mixed path)."""
+    f, ix, iy, yu, yv = _analysis_case(nx, ny, k, nox, noy, seed=70 + k)
+    ref = oracle.letkf_analyze(f, ix, iy, yu, yv, SIGMA, SIGMA, d_cut, 1.05)
+    got = _gpu_analysis(gpu, f, ix, iy, yu, yv, d_cut, 1.05, gpu.LBM_FP64)
+    assert norm_rel(got, ref) <= TOL_FP64
+    got = _gpu_analysis(gpu, f, ix, iy, yu, yv, d_cut, 1.05, gpu.LBM_MIXED)
+    assert norm_rel(got, ref) <= 1e-6
 
 
 def _osse(run_forecast, run_analysis, nature, steps, s, nobs, d_cut, beta, nx, ny, seed=4):
