@@ -1,7 +1,7 @@
 """CPU oracle for the LBM-LETKF cycle (arXiv 2308.03972).
 
 TEST INFRASTRUCTURE ONLY. The oracle is a plain FP64 C library (``lbm.c``,
-``eig.c``, ``letkf.c``) with this thin ctypes/numpy wrapper. It shares no code
+``eig.c``, ``letkf.c``, ``diag.c``) with this thin ctypes/numpy wrapper. It shares no code
 with the CUDA library and imports nothing from the product package. Only the
 test suite, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline leg
 load it.
@@ -19,7 +19,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRCS = ("lbm.c", "eig.c", "letkf.c")
+_SRCS = ("lbm.c", "eig.c", "letkf.c", "diag.c")
 _LIB_PATH = os.path.join(_HERE, "_build", "liblbm_letkf_oracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -66,6 +66,7 @@ def _load():
             "orc_letkf_analyze": (I, [I, I, I, P, I, P, P, P, P, D, D, D, D, I, P]),
             "orc_num_threads": (I, []),
             "orc_nudge": (None, [I, I, I, P, I, I, P, P, P, D]),
+            "orc_energy_spectrum": (None, [I, I, I, P, I, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -230,6 +231,23 @@ def nudge(f: np.ndarray, rho_o, u_o, v_o, gamma: float) -> np.ndarray:
     assert nx % nox == 0 and ny % noy == 0
     _load().orc_nudge(nx, ny, k, _p(f), nox, noy, _p(rho_o), _p(u_o), _p(v_o), float(gamma))
     return f
+
+
+def spectrum_shells(nx: int, ny: int) -> int:
+    """Number of shells that hold every wavenumber of an nx x ny lattice."""
+    return int(np.floor(np.hypot(nx // 2, ny // 2) + 0.5)) + 1
+
+
+def energy_spectrum(f: np.ndarray, nshells: int | None = None) -> np.ndarray:
+    """Member-averaged energy spectrum E[s] of f [9][ny][nx][k] (shells
+    s = floor(|k'| + 1/2))."""
+    f = _f64(f)
+    _, ny, nx, k = f.shape
+    if nshells is None:
+        nshells = spectrum_shells(nx, ny)
+    E = np.zeros(nshells)
+    _load().orc_energy_spectrum(nx, ny, k, _p(f), int(nshells), _p(E))
+    return E
 
 
 def num_threads() -> int:

@@ -96,11 +96,18 @@ int orc_letkf_analyze(int nx, int ny, int k, double *f, int npts,
  * the observed macroscopic field, f_a <- f_a + gamma (f^eq_a(rho^, u^, v^) - f_a).
  * Observations sit on the uniform periodic lattice (i nx/nox, j ny/noy),
  * arrays [noy][nox]; rho^, u^, v^ at a grid point are their bilinear
- * interpolation ("simple linear interpolation" of the sparse data). nx must
+ * interpolation (linear interpolation of the sparse data). nx must
  * be a multiple of nox and ny of noy. In place on f. */
 void orc_nudge(int nx, int ny, int k, double *f, int nox, int noy,
                const double *rho_o, const double *u_o, const double *v_o,
                double gamma);
+
+/* Energy spectrum of the ensemble (Section 4.1): for each member the 2D
+ * discrete Fourier transform u-hat(k') = N^{-1} sum u e^{-i k'.xi} of both
+ * velocity components, E(k') = |u-hat|^2 / 2 binned into integer shells
+ * s = floor(|k'| + 1/2), then the mean over members. E[nshells]; shells at
+ * or beyond nshells are dropped. */
+void orc_energy_spectrum(int nx, int ny, int k, const double *f, int nshells, double *E);
 
 /* Number of OpenMP threads the oracle will use (1 without OpenMP). */
 int orc_num_threads(void);
