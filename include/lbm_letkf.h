@@ -101,6 +101,19 @@ int lbm_moments(lbm_ctx *ctx, double *rho, double *u, double *v, int ptr_kind);
  * may be NULL. With LBM_PTR_HOST the call synchronises. */
 int lbm_mean_velocity(lbm_ctx *ctx, double *u, double *v, int ptr_kind);
 
+/* Energy spectrum of the ensemble (Section 4.1, shell-averaged spectrum;
+ * Section 4.3 takes the mean of the members' spectra). For every member,
+ * u-hat(k') = N^{-1} sum_xi u(xi) exp(-i k'.xi) over the N = nx*ny cells for
+ * both velocity components, E(k') = |u-hat(k')|^2 / 2, summed over the shell
+ * s - 1/2 <= |k'| < s + 1/2 (k' in signed integer wavenumbers), then averaged
+ * over members. E[nshells] receives shells s = 0 .. nshells-1; wavenumbers in
+ * higher shells are dropped (floor(hypot(nx/2, ny/2) + 1/2) + 1 shells hold
+ * them all). FP64 in both precisions. With LBM_PTR_HOST the call
+ * synchronises; the scratch it needs is allocated and released on the
+ * context stream. LBM_EINVAL if nshells < 1 or the lattice is too large for
+ * the diagnostic (nx or ny beyond about 1700). */
+int lbm_energy_spectrum(lbm_ctx *ctx, double *E, int nshells, int ptr_kind);
+
 /* Observation step (Section 3, y = H x; Section 3.2, ybar and dY): record
  * npts observation points (ix[j], iy[j]) with observed velocities
  * (yo_u[j], yo_v[j]) and error standard deviations sigma_u, sigma_v, apply

@@ -42,6 +42,7 @@ SIGNATURES = {
     "lbm_forecast": (_I, [_P, _I]),
     "lbm_moments": (_I, [_P, _P, _P, _P, _I]),
     "lbm_mean_velocity": (_I, [_P, _P, _P, _I]),
+    "lbm_energy_spectrum": (_I, [_P, _P, _I, _I]),
     "letkf_observe": (_I, [_P, _I, _P, _P, _P, _P, _D, _D]),
     "letkf_analyze": (_I, [_P, _D, _D]),
     "lbm_nudge": (_I, [_P, _I, _I, _P, _P, _P, _D]),
@@ -179,6 +180,18 @@ def lbm_mean_velocity(ctx, u=None, v=None):
     _check(ctx, load().lbm_mean_velocity(ctx, pu, pv, kind))
 
 
+def spectrum_shells(nx: int, ny: int) -> int:
+    """Shell count that holds every wavenumber of an nx x ny lattice."""
+    return int(np.floor(np.hypot(nx // 2, ny // 2) + 0.5)) + 1
+
+
+def lbm_energy_spectrum(ctx, E):
+    """Fill E [nshells] (numpy or CUDA tensor) with the member-averaged
+    shell energy spectrum."""
+    pe, ke, _b = _arr(E, writable=True)
+    _check(ctx, load().lbm_energy_spectrum(ctx, pe, int(E.numel() if _is_torch(E) else E.size), ke))
+
+
 def letkf_observe(ctx, ix, iy, yo_u, yo_v, sigma_u, sigma_v):
     ix = np.ascontiguousarray(ix, dtype=np.int32)
     iy = np.ascontiguousarray(iy, dtype=np.int32)
@@ -283,6 +296,12 @@ class Ensemble:
             v = np.empty((self.ny, self.nx))
         lbm_mean_velocity(self.ctx, u, v)
         return u, v
+
+    def energy_spectrum(self, E=None):
+        if E is None:
+            E = np.zeros(spectrum_shells(self.nx, self.ny))
+        lbm_energy_spectrum(self.ctx, E)
+        return E
 
     def observe(self, ix, iy, yo_u, yo_v, sigma_u, sigma_v):
         letkf_observe(self.ctx, ix, iy, yo_u, yo_v, sigma_u, sigma_v)

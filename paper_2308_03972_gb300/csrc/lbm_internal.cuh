@@ -89,4 +89,12 @@ cudaError_t launch_analyze(void* f, int fp32, int nx, int ny, int k, const ObsPa
                            double d_cut, double beta, int nmax, int* flags, void* scratch,
                            const AnalyzeAux* aux, cudaStream_t s);
 
+// ---- diag_kernels.cu ------------------------------------------------------
+// Member-averaged energy spectrum E[nshells] (device pointer); work holds
+// spectrum_work_bytes(nx, ny, k, nshells) bytes. Lattices whose row or column
+// pass does not fit shared memory give cudaErrorInvalidValue.
+size_t spectrum_work_bytes(int nx, int ny, int k, int nshells);
+cudaError_t launch_energy_spectrum(const void* f, int fp32, int nx, int ny, int k, double* E,
+                                   int nshells, void* work, int* flags, cudaStream_t s);
+
 }  // namespace lbmgpu

@@ -349,6 +349,37 @@ int lbm_mean_velocity(lbm_ctx* c, double* u, double* v, int ptr_kind) {
     return read_flags(c);
 }
 
+int lbm_energy_spectrum(lbm_ctx* c, double* E, int nshells, int ptr_kind) {
+    if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (!ptr_kind_ok(ptr_kind)) return fail(c, LBM_EINVAL, "bad ptr_kind");
+    if (!E) return fail(c, LBM_EINVAL, "E is NULL");
+    if (nshells < 1) return fail(c, LBM_EINVAL, "nshells must be >= 1");
+    // Shells past floor(hypot(nx/2, ny/2) + 1/2) hold no wavenumber.
+    const int all = (int)std::floor(std::hypot((double)(c->nx / 2), (double)(c->ny / 2)) + 0.5) + 1;
+    const int nsh = nshells < all ? nshells : all;
+    const size_t work = spectrum_work_bytes(c->nx, c->ny, c->k, nsh);
+    const size_t out = ptr_kind == LBM_PTR_HOST ? (size_t)nshells * sizeof(double) : 0;
+    void* buf = nullptr;
+    // Stream-ordered scratch: the diagnostic is occasional and its buffers
+    // (about 1 KiB per member and lattice row) are returned right after.
+    CK(c, cudaMallocAsync(&buf, work + out, c->stream), "allocating spectrum scratch");
+    double* Ed = ptr_kind == LBM_PTR_HOST
+                     ? reinterpret_cast<double*>(static_cast<unsigned char*>(buf) + work)
+                     : E;
+    cudaError_t e = launch_energy_spectrum(c->f[c->cur], is_fp32(c), c->nx, c->ny, c->k, Ed,
+                                           nsh, buf, c->flags, c->stream);
+    if (e == cudaSuccess && nshells > nsh)
+        e = cudaMemsetAsync(Ed + nsh, 0, (size_t)(nshells - nsh) * sizeof(double), c->stream);
+    if (e == cudaSuccess && ptr_kind == LBM_PTR_HOST)
+        e = cudaMemcpyAsync(E, Ed, out, cudaMemcpyDeviceToHost, c->stream);
+    const cudaError_t e2 = cudaFreeAsync(buf, c->stream);
+    if (e == cudaErrorInvalidValue)
+        return fail(c, LBM_EINVAL, "lattice too large for the spectrum diagnostic's shared memory");
+    CK(c, e, "launching the energy spectrum");
+    CK(c, e2, "freeing spectrum scratch");
+    return ptr_kind == LBM_PTR_HOST ? read_flags(c) : LBM_OK;
+}
+
 int letkf_observe(lbm_ctx* c, int npts, const int* ix, const int* iy, const double* yo_u,
                   const double* yo_v, double sigma_u, double sigma_v) {
     if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
