@@ -200,6 +200,18 @@ def measure(cfg, precision, steps, warmup, sample_clocks=False, gpu_index=0):
         if sampler:
             sampler.__exit__()
     osse.ens.sync()
+    # The nature run (one FP64 member) is the OSSE's truth, timed apart from
+    # the ensemble cycle: one cycle's worth of steps, a few times.
+    nat = []
+    for _ in range(3):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        osse.nature.forecast(cfg.steps_per_cycle)
+        b.record(stream)
+        nat.append((a, b))
+    torch.cuda.synchronize()
+    nature_ms = statistics.median(a.elapsed_time(b) for a, b in nat)
     total_ms = start.elapsed_time(end)
     lbm = [e[0].elapsed_time(e[1]) / cfg.steps_per_cycle for e in ev]
     obs_ms = [e[1].elapsed_time(e[2]) for e in ev]
@@ -213,7 +225,7 @@ def measure(cfg, precision, steps, warmup, sample_clocks=False, gpu_index=0):
     ana_launches = 1 if precision == binding.LBM_FP64 else 1 + 2 * chunks
     return {"ms_per_cycle": total_ms / steps, "lbm_step_ms": statistics.mean(lbm),
             "observe_ms": statistics.mean(obs_ms), "analysis_ms": statistics.mean(ana),
-            "rmse": rmse, "clocks": sampler.summary() if sampler else None,
+            "rmse": rmse, "clocks": sampler.summary() if sampler else None, "nature_ms": nature_ms,
             "launches_per_cycle": cfg.steps_per_cycle + 2 + ana_launches}
 
 
@@ -358,6 +370,14 @@ def main():
         "analysis_fp64": {"ms": fp64["analysis_ms"],
                           "achieved_gflops": flops / (fp64["analysis_ms"] * 1e6)},
     }
+    ncells = cfg.nx * cfg.ny
+    throughput = {
+        "mlups_x_members_f32": ncell / (mixed["lbm_step_ms"] * 1e3),
+        "mlups_x_members_f64": ncell / (fp64["lbm_step_ms"] * 1e3),
+        "grid_point_analyses_per_s_mixed": ncells / (mixed["analysis_ms"] * 1e-3),
+        "grid_point_analyses_per_s_fp64": ncells / (fp64["analysis_ms"] * 1e-3),
+        "nature_run_ms_per_cycle": mixed["nature_ms"],
+    }
     lbm_share = mixed["lbm_step_ms"] * cfg.steps_per_cycle
     kern["lbm_step_f32"]["traffic"] = NCU_TRAFFIC["lbm_step_f32"]
     kern["analysis_mixed"]["traffic"] = NCU_TRAFFIC["analysis_mixed"]
@@ -394,7 +414,7 @@ def main():
                     "h2d_bytes_per_step": e2e["h2d_bytes_per_step"],
                     "d2h_bytes_per_step": e2e["d2h_bytes_per_step"]},
             "gpu_launches": args.steps * mixed["launches_per_cycle"],
-            "roofline": roof, "kernels": kern,
+            "roofline": roof, "kernels": kern, "throughput": throughput,
             "rmse": {"mixed": mixed["rmse"], "fp64": fp64["rmse"], "obs_noise_rms": cfg.sigma * np.sqrt(2)},
             "clocks": mixed["clocks"], "cpu_baseline": cpu,
         }
