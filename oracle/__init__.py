@@ -67,6 +67,9 @@ def _load():
             "orc_num_threads": (I, []),
             "orc_nudge": (None, [I, I, I, P, I, I, P, P, P, D]),
             "orc_energy_spectrum": (None, [I, I, I, P, I, P]),
+            "orc_observe_vars": (None, [I, I, I, P, I, P, P, I, P]),
+            "orc_local_obs_vars": (I, [I, I, I, I, I, P, P, I, P, D, P, P]),
+            "orc_letkf_analyze_vars": (I, [I, I, I, P, I, P, P, I, P, P, D, D, I, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -216,6 +219,49 @@ def letkf_analyze(f: np.ndarray, ix, iy, yo_u, yo_v, sigma_u, sigma_v, d_cut, be
         npoints = len(pts)
     st = _load().orc_letkf_analyze(nx, ny, k, _p(f), len(ix), _p(ix), _p(iy), _p(yo_u), _p(yo_v),
                                    float(sigma_u), float(sigma_v), float(d_cut), float(beta), npoints, _p(pts))
+    if st != 0:
+        raise RuntimeError("oracle eigensolver did not converge")
+    return f
+
+
+def observe_vars(f: np.ndarray, ix, iy, nvar: int) -> np.ndarray:
+    """Yf [nvar*npts][k]: rows u, v (and rho when nvar = 3) of each point."""
+    f = _f64(f)
+    ix, iy = _i32(ix), _i32(iy)
+    _, ny, nx, k = f.shape
+    Y = np.empty((nvar * len(ix), k))
+    _load().orc_observe_vars(nx, ny, k, _p(f), len(ix), _p(ix), _p(iy), int(nvar), _p(Y))
+    return Y
+
+
+def local_obs_vars(nx, ny, x, y, ix, iy, sigma, d_cut):
+    """Local set with len(sigma) variables per point."""
+    ix, iy = _i32(ix), _i32(iy)
+    sigma = _f64(sigma)
+    nvar = len(sigma)
+    idx = np.zeros(nvar * len(ix), np.int32)
+    rl = np.zeros(nvar * len(ix), np.float64)
+    p = _load().orc_local_obs_vars(nx, ny, x, y, len(ix), _p(ix), _p(iy), nvar, _p(sigma),
+                                   float(d_cut), _p(idx), _p(rl))
+    return idx[:p].copy(), rl[:p].copy()
+
+
+def letkf_analyze_vars(f: np.ndarray, ix, iy, yo, sigma, d_cut, beta, points=None) -> np.ndarray:
+    """LETKF analysis with len(sigma) observed variables per point (u, v[,
+    rho]); yo [npts][nvar]. Returns a new array."""
+    f = _f64(f).copy()
+    ix, iy = _i32(ix), _i32(iy)
+    sigma = _f64(sigma)
+    nvar = len(sigma)
+    yo = _f64(yo).reshape(len(ix), nvar)
+    _, ny, nx, k = f.shape
+    if points is None:
+        npoints, pts = -1, np.zeros(1, np.int32)
+    else:
+        pts = _i32(points)
+        npoints = len(pts)
+    st = _load().orc_letkf_analyze_vars(nx, ny, k, _p(f), len(ix), _p(ix), _p(iy), nvar, _p(yo),
+                                        _p(sigma), float(d_cut), float(beta), npoints, _p(pts))
     if st != 0:
         raise RuntimeError("oracle eigensolver did not converge")
     return f

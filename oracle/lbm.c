@@ -141,8 +141,8 @@ void orc_set_equilibrium(int nx, int ny, int k, const double *rho,
             }
 }
 
-void orc_observe(int nx, int ny, int k, const double *f, int npts,
-                 const int *ix, const int *iy, double *Yf) {
+void orc_observe_vars(int nx, int ny, int k, const double *f, int npts,
+                      const int *ix, const int *iy, int nvar, double *Yf) {
     for (int j = 0; j < npts; ++j)
         for (int m = 0; m < k; ++m) {
             double r = 0.0, jx = 0.0, jy = 0.0;
@@ -152,9 +152,15 @@ void orc_observe(int nx, int ny, int k, const double *f, int npts,
                 jx += fa * CX[a];
                 jy += fa * CY[a];
             }
-            Yf[(size_t)(2 * j) * k + m] = jx / r;
-            Yf[(size_t)(2 * j + 1) * k + m] = jy / r;
+            Yf[(size_t)(nvar * j) * k + m] = jx / r;
+            Yf[(size_t)(nvar * j + 1) * k + m] = jy / r;
+            if (nvar == 3) Yf[(size_t)(nvar * j + 2) * k + m] = r;
         }
+}
+
+void orc_observe(int nx, int ny, int k, const double *f, int npts,
+                 const int *ix, const int *iy, double *Yf) {
+    orc_observe_vars(nx, ny, k, f, npts, ix, iy, 2, Yf);
 }
 
 /* Bilinear interpolation of a periodic field on the observation lattice. */

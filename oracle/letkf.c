@@ -7,7 +7,8 @@
  *    Section 3 prints a minus; the LETKF equations themselves are
  *    sign-correct and are what is implemented);
  *  - ybar is the mean of H(x_m) over members;
- *  - R is diagonal with sigma_u^2 for u and sigma_v^2 for v observations;
+ *  - R is diagonal with sigma_u^2 for u and sigma_v^2 for v observations
+ *    (sigma_rho^2 for rho where density is observed as well);
  *    R-localisation divides each variance by the Gaspari-Cohn weight
  *    G(r / d_cut), r the periodic minimum-image distance from the grid
  *    point to the observation point, and drops observations with
@@ -115,9 +116,9 @@ static int min_image(int dx, int n) {
     return dx;
 }
 
-int orc_local_obs(int nx, int ny, int x, int y, int npts, const int *ix,
-                  const int *iy, double sigma_u, double sigma_v, double d_cut,
-                  int *idx, double *rloc) {
+int orc_local_obs_vars(int nx, int ny, int x, int y, int npts, const int *ix,
+                       const int *iy, int nvar, const double *sigma, double d_cut,
+                       int *idx, double *rloc) {
     int p = 0;
     for (int j = 0; j < npts; ++j) {
         int dx = min_image(ix[j] - x, nx);
@@ -127,14 +128,20 @@ int orc_local_obs(int nx, int ny, int x, int y, int npts, const int *ix,
         if (!(dist < 2.0)) continue;
         double g = orc_gaspari_cohn(dist);
         if (!(g > 0.0)) continue;
-        idx[p] = 2 * j;
-        rloc[p] = g / (sigma_u * sigma_u);
-        ++p;
-        idx[p] = 2 * j + 1;
-        rloc[p] = g / (sigma_v * sigma_v);
-        ++p;
+        for (int q = 0; q < nvar; ++q) {
+            idx[p] = nvar * j + q;
+            rloc[p] = g / (sigma[q] * sigma[q]);
+            ++p;
+        }
     }
     return p;
+}
+
+int orc_local_obs(int nx, int ny, int x, int y, int npts, const int *ix,
+                  const int *iy, double sigma_u, double sigma_v, double d_cut,
+                  int *idx, double *rloc) {
+    const double sigma[2] = {sigma_u, sigma_v};
+    return orc_local_obs_vars(nx, ny, x, y, npts, ix, iy, 2, sigma, d_cut, idx, rloc);
 }
 
 int orc_letkf_analyze(int nx, int ny, int k, double *f, int npts,
@@ -142,19 +149,34 @@ int orc_letkf_analyze(int nx, int ny, int k, double *f, int npts,
                       const double *yo_v, double sigma_u, double sigma_v,
                       double d_cut, double beta, int npoints,
                       const int *points) {
-    int nobs = 2 * npts;
+    double *yo = (double *)malloc(sizeof(double) * 2 * (npts > 0 ? npts : 1));
+    for (int j = 0; j < npts; ++j) {
+        yo[2 * j] = yo_u[j];
+        yo[2 * j + 1] = yo_v[j];
+    }
+    const double sigma[2] = {sigma_u, sigma_v};
+    int status = orc_letkf_analyze_vars(nx, ny, k, f, npts, ix, iy, 2, yo, sigma, d_cut, beta,
+                                        npoints, points);
+    free(yo);
+    return status;
+}
+
+int orc_letkf_analyze_vars(int nx, int ny, int k, double *f, int npts,
+                           const int *ix, const int *iy, int nvar, const double *yo,
+                           const double *sigma, double d_cut, double beta, int npoints,
+                           const int *points) {
+    int nobs = nvar * npts;
     double *Yf = (double *)malloc(sizeof(double) * nobs * k);
     double *dYall = (double *)malloc(sizeof(double) * nobs * k);
     double *dall = (double *)malloc(sizeof(double) * nobs);
     /* y_m^f = H x_m^f; ybar = mean over members; dY = Y - ybar; d = y^o - ybar. */
-    orc_observe(nx, ny, k, f, npts, ix, iy, Yf);
+    orc_observe_vars(nx, ny, k, f, npts, ix, iy, nvar, Yf);
     for (int o = 0; o < nobs; ++o) {
         double mean = 0.0;
         for (int m = 0; m < k; ++m) mean += Yf[(size_t)o * k + m];
         mean /= k;
         for (int m = 0; m < k; ++m) dYall[(size_t)o * k + m] = Yf[(size_t)o * k + m] - mean;
-        double yo = (o % 2 == 0) ? yo_u[o / 2] : yo_v[o / 2];
-        dall[o] = yo - mean;
+        dall[o] = yo[o] - mean;
     }
     int total = (npoints < 0) ? nx * ny : npoints;
     int status = 0;
@@ -170,7 +192,7 @@ int orc_letkf_analyze(int nx, int ny, int k, double *f, int npts,
         double *dY = (double *)malloc(sizeof(double) * nobs * k);
         double *d = (double *)malloc(sizeof(double) * nobs);
         double *X = (double *)malloc(sizeof(double) * 9 * k);
-        int p = orc_local_obs(nx, ny, x, y, npts, ix, iy, sigma_u, sigma_v, d_cut, idx, rloc);
+        int p = orc_local_obs_vars(nx, ny, x, y, npts, ix, iy, nvar, sigma, d_cut, idx, rloc);
         for (int i = 0; i < p; ++i) {
             memcpy(dY + (size_t)i * k, dYall + (size_t)idx[i] * k, sizeof(double) * k);
             d[i] = dall[idx[i]];

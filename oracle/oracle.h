@@ -13,7 +13,8 @@
  *   force  [2][ny][nx]      large-scale acceleration F^i (x then y component)
  *   rho, u, v [ny][nx][k]   macroscopic moments
  *   Yf     [2*npts][k]      observed (u, v) of every member; row 2j is u at
- *                           observation point j, row 2j+1 is v there
+ *                           observation point j, row 2j+1 is v there (with
+ *                           density observed: [3*npts][k], rows u, v, rho)
  */
 #ifndef LBM_LETKF_ORACLE_H
 #define LBM_LETKF_ORACLE_H
@@ -46,6 +47,13 @@ void orc_set_equilibrium(int nx, int ny, int k, const double *rho,
 /* Observation operator H (Section 3, y = [u, v] at eta): Yf as above. */
 void orc_observe(int nx, int ny, int k, const double *f, int npts,
                  const int *ix, const int *iy, double *Yf);
+
+/* Observation operator with nvar = 2 (u, v) or 3 (u, v, rho) variables per
+ * point (Section 3, y = macroscopic variables at eta; Section 4.3 observes
+ * the density as well): row nvar*j + q of Yf [nvar*npts][k] is variable q
+ * of point j. */
+void orc_observe_vars(int nx, int ny, int k, const double *f, int npts,
+                      const int *ix, const int *iy, int nvar, double *Yf);
 
 /* Gaspari-Cohn localisation weight G(d) (Section 3.2.2). */
 double orc_gaspari_cohn(double d);
@@ -81,6 +89,12 @@ int orc_local_obs(int nx, int ny, int x, int y, int npts, const int *ix,
                   const int *iy, double sigma_u, double sigma_v, double d_cut,
                   int *idx, double *rloc);
 
+/* orc_local_obs for nvar variables per point with error sigma[q] for
+ * variable q; indices nvar*j + q. */
+int orc_local_obs_vars(int nx, int ny, int x, int y, int npts, const int *ix,
+                       const int *iy, int nvar, const double *sigma, double d_cut,
+                       int *idx, double *rloc);
+
 /* Full LETKF analysis of the nine f_alpha at grid points (Section 3.2):
  * H applied to the forecast ensemble, ybar, dY and d = y^o - ybar, then the
  * local transform and update at each selected point, in place on f.
@@ -91,6 +105,13 @@ int orc_letkf_analyze(int nx, int ny, int k, double *f, int npts,
                       const double *yo_v, double sigma_u, double sigma_v,
                       double d_cut, double beta, int npoints,
                       const int *points);
+
+/* orc_letkf_analyze with nvar variables per observation point (see
+ * orc_observe_vars): yo [npts][nvar], sigma [nvar]. */
+int orc_letkf_analyze_vars(int nx, int ny, int k, double *f, int npts,
+                           const int *ix, const int *iy, int nvar, const double *yo,
+                           const double *sigma, double d_cut, double beta, int npoints,
+                           const int *points);
 
 /* Nudging (Section 3.1): every member is relaxed toward the equilibrium of
  * the observed macroscopic field, f_a <- f_a + gamma (f^eq_a(rho^, u^, v^) - f_a).
