@@ -126,6 +126,18 @@ int letkf_observe(lbm_ctx *ctx, int npts, const int *ix, const int *iy,
                   const double *yo_u, const double *yo_v, double sigma_u,
                   double sigma_v);
 
+/* letkf_observe with the density observed as well (Section 4.3 observes
+ * rho at the same points as the velocity, with its own error level): the
+ * observation vector holds three scalars per point, (u_j, v_j, rho_j), with
+ * error standard deviations sigma_u, sigma_v, sigma_rho; rho_m = sum_alpha
+ * f_alpha of member m. Localisation gives the three scalars of a point the
+ * same Gaspari-Cohn weight. Same pointer rules and errors as letkf_observe;
+ * yo_rho must not be NULL and sigma_rho must be finite and > 0. The next
+ * letkf_analyze assimilates all three. */
+int letkf_observe_rho(lbm_ctx *ctx, int npts, const int *ix, const int *iy,
+                      const double *yo_u, const double *yo_v, const double *yo_rho,
+                      double sigma_u, double sigma_v, double sigma_rho);
+
 /* LETKF analysis of the nine f_alpha at every grid point, in place
  * (Section 3.2: w-bar, P-tilde, delta-W = [(k-1) P-tilde]^{1/2} symmetric,
  * x^a_m = xbar + dX (w-bar + delta-W_m); R-localisation with the

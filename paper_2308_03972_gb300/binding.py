@@ -44,6 +44,7 @@ SIGNATURES = {
     "lbm_mean_velocity": (_I, [_P, _P, _P, _I]),
     "lbm_energy_spectrum": (_I, [_P, _P, _I, _I]),
     "letkf_observe": (_I, [_P, _I, _P, _P, _P, _P, _D, _D]),
+    "letkf_observe_rho": (_I, [_P, _I, _P, _P, _P, _P, _P, _D, _D, _D]),
     "letkf_analyze": (_I, [_P, _D, _D]),
     "lbm_nudge": (_I, [_P, _I, _I, _P, _P, _P, _D]),
     "lbm_get_f": (_I, [_P, _P, _I]),
@@ -205,6 +206,20 @@ def letkf_observe(ctx, ix, iy, yo_u, yo_v, sigma_u, sigma_v):
                                      float(sigma_v)))
 
 
+def letkf_observe_rho(ctx, ix, iy, yo_u, yo_v, yo_rho, sigma_u, sigma_v, sigma_rho):
+    ix = np.ascontiguousarray(ix, dtype=np.int32)
+    iy = np.ascontiguousarray(iy, dtype=np.int32)
+    yo_u = np.ascontiguousarray(yo_u, dtype=np.float64)
+    yo_v = np.ascontiguousarray(yo_v, dtype=np.float64)
+    yo_rho = np.ascontiguousarray(yo_rho, dtype=np.float64)
+    n = len(ix)
+    if not (len(iy) == len(yo_u) == len(yo_v) == len(yo_rho) == n):
+        raise ValueError("observation arrays differ in length")
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    _check(ctx, load().letkf_observe_rho(ctx, n, p(ix), p(iy), p(yo_u), p(yo_v), p(yo_rho),
+                                         float(sigma_u), float(sigma_v), float(sigma_rho)))
+
+
 def letkf_analyze(ctx, d_cut, beta):
     _check(ctx, load().letkf_analyze(ctx, float(d_cut), float(beta)))
 
@@ -305,6 +320,9 @@ class Ensemble:
 
     def observe(self, ix, iy, yo_u, yo_v, sigma_u, sigma_v):
         letkf_observe(self.ctx, ix, iy, yo_u, yo_v, sigma_u, sigma_v)
+
+    def observe_rho(self, ix, iy, yo_u, yo_v, yo_rho, sigma_u, sigma_v, sigma_rho):
+        letkf_observe_rho(self.ctx, ix, iy, yo_u, yo_v, yo_rho, sigma_u, sigma_v, sigma_rho)
 
     def analyze(self, d_cut, beta):
         letkf_analyze(self.ctx, d_cut, beta)

@@ -35,15 +35,19 @@ struct LbmParams {
     double mu;
 };
 
+// Observation vector: nvar scalars per point, row nvar*j + q holding u
+// (q = 0), v (q = 1) and, when nvar = 3, rho (q = 2) at point j.
 struct ObsParams {
     int npts;          // observation points
     const int* ix;     // [npts]
     const int* iy;     // [npts]
-    const double* dY;  // [2 npts][k] perturbations of H(x_m)
-    const double* d;   // [2 npts] innovations y^o - ybar
-    const double* G;   // [2 npts][2 npts] dY dY^T
+    const double* dY;  // [nobs][k] perturbations of H(x_m), nobs = nvar npts
+    const double* d;   // [nobs] innovations y^o - ybar
+    const double* G;   // [nobs][nobs] dY dY^T
     double sigma_u, sigma_v;
-    float* dY32;       // [2 npts][k] binary32 copy of dY (mixed precision only)
+    float* dY32;       // [nobs][k] binary32 copy of dY (mixed precision only)
+    int nvar = 2;      // 2: (u, v); 3: (u, v, rho)
+    double sigma_r = 1.0;
 };
 
 // ---- lbm_kernels.cu -------------------------------------------------------
@@ -70,7 +74,7 @@ cudaError_t launch_store_force(void* dst, int fp32, const double* src, size_t n,
                                cudaStream_t s);
 
 // ---- letkf_kernels.cu -----------------------------------------------------
-cudaError_t launch_observe(const void* f, int fp32, int nx, int ny, int k, int npts,
+cudaError_t launch_observe(const void* f, int fp32, int nx, int ny, int k, int npts, int nvar,
                            const int* ix, const int* iy, const double* yo, double* dY,
                            double* d, cudaStream_t s);
 cudaError_t launch_obs_gram(const double* dY, int nobs, int k, double* G, cudaStream_t s);
@@ -82,7 +86,7 @@ struct AnalyzeAux {
     cudaEvent_t start, jac_done[2], ref_done[2];
 };
 // Scratch the analysis needs (bytes; 0 for the FP64 path).
-size_t analyze_scratch_bytes(int nx, int ny, int fp32, int npts, int nmax);
+size_t analyze_scratch_bytes(int nx, int ny, int fp32, int nobs, int nmax);
 // nmax: largest local problem size n = min(p, k) over the grid (sizes the
 // mixed kernel's shared memory; points above it are reported as too large).
 cudaError_t launch_analyze(void* f, int fp32, int nx, int ny, int k, const ObsParams& o,

@@ -24,14 +24,15 @@ struct lbm_ctx {
     int* flags = nullptr;            // device flag word
     double* stage = nullptr;         // FP64 staging [9][ny][nx][k] (lazy)
     // observations
-    int npts = 0, obs_cap = 0;
+    // nobs = nvar * npts scalars: (u, v) per point, or (u, v, rho).
+    int npts = 0, nvar = 2, pts_cap = 0, nobs_cap = 0;
     int* ix = nullptr;
     int* iy = nullptr;
-    double* yo = nullptr;  // [2 npts] interleaved (u, v)
-    double* dY = nullptr;  // [2 npts][k]
-    double* d = nullptr;   // [2 npts]
-    double* G = nullptr;   // [2 npts][2 npts]
-    float* dY32 = nullptr; // [2 npts][k] binary32 copy (mixed precision)
+    double* yo = nullptr;  // [nobs] interleaved per point
+    double* dY = nullptr;  // [nobs][k]
+    double* d = nullptr;   // [nobs]
+    double* G = nullptr;   // [nobs][nobs]
+    float* dY32 = nullptr; // [nobs][k] binary32 copy (mixed precision)
     void* ana_scratch = nullptr;   // analysis scratch (mixed precision)
     size_t ana_scratch_bytes = 0;
     // Observation geometry of the last letkf_observe, and the largest local
@@ -43,11 +44,11 @@ struct lbm_ctx {
     bool aux_ready = false;
     double* nudge_obs = nullptr;  // [3][noy][nox] nudging observations
     size_t nudge_cap = 0;
-    double* h_yo = nullptr;  // pinned staging [2 cap]
-    int* h_ixy = nullptr;    // pinned staging [2 cap] (ix then iy)
+    double* h_yo = nullptr;  // pinned staging [nobs_cap]
+    int* h_ixy = nullptr;    // pinned staging [2 pts_cap] (ix then iy)
     cudaEvent_t obs_copied = nullptr;  // last staging copy done
     bool obs_pending = false;
-    double sigma_u = 0.0, sigma_v = 0.0;
+    double sigma_u = 0.0, sigma_v = 0.0, sigma_r = 1.0;
     bool observed = false;
     char err[512] = {0};
 };
@@ -129,7 +130,7 @@ void free_obs(lbm_ctx* c) {
     c->dY32 = nullptr;
     c->ix = c->iy = nullptr;
     c->yo = c->dY = c->d = c->G = nullptr;
-    c->obs_cap = 0;
+    c->pts_cap = c->nobs_cap = 0;
 }
 
 // Largest local problem n = min(p, k) over the grid for the current
@@ -157,12 +158,89 @@ int largest_local_problem(lbm_ctx* c, double d_cut) {
     }
     int nmax = 2;
     for (int v : cnt) {
-        const int n = (2 * v < c->k) ? 2 * v : c->k;
+        const int n = (c->nvar * v < c->k) ? c->nvar * v : c->k;
         if (n > nmax) nmax = n;
     }
     c->geo_dcut = d_cut;
     c->geo_nmax = nmax;
     return nmax;
+}
+
+// Observation operator for (u, v) or, with yo_r, (u, v, rho) at each point:
+// checks, staging through pinned memory, H and the ensemble statistics, and
+// the global Gram dY dY^T the observation-space analysis gathers from.
+int observe_impl(lbm_ctx* c, int npts, const int* ix, const int* iy, const double* yo_u,
+                 const double* yo_v, const double* yo_r, double sigma_u, double sigma_v,
+                 double sigma_r) {
+    if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (npts < 1) return fail(c, LBM_EINVAL, "npts must be >= 1");
+    if (!ix || !iy || !yo_u || !yo_v) return fail(c, LBM_EINVAL, "NULL observation array");
+    if (!(sigma_u > 0.0) || !(sigma_v > 0.0) || !std::isfinite(sigma_u) || !std::isfinite(sigma_v))
+        return fail(c, LBM_EINVAL, "sigma_u and sigma_v must be finite and > 0");
+    if (yo_r && (!(sigma_r > 0.0) || !std::isfinite(sigma_r)))
+        return fail(c, LBM_EINVAL, "sigma_rho must be finite and > 0");
+    const int nvar = yo_r ? 3 : 2;
+    if ((long long)npts * nvar > 65535) return fail(c, LBM_EINVAL, "too many observation points");
+    for (int j = 0; j < npts; ++j) {
+        if (ix[j] < 0 || ix[j] >= c->nx || iy[j] < 0 || iy[j] >= c->ny)
+            return fail(c, LBM_EINVAL, "observation point %d outside the lattice", j);
+        if (!std::isfinite(yo_u[j]) || !std::isfinite(yo_v[j]) || (yo_r && !std::isfinite(yo_r[j])))
+            return fail(c, LBM_EINVAL, "observation %d is not finite", j);
+    }
+    const int nobs = nvar * npts;
+    if (!c->obs_copied)
+        CK(c, cudaEventCreateWithFlags(&c->obs_copied, cudaEventDisableTiming), "creating event");
+    if (npts > c->pts_cap || nobs > c->nobs_cap) {
+        CK(c, cudaStreamSynchronize(c->stream), "synchronising");
+        free_obs(c);
+        const size_t no = (size_t)nobs;
+        CK(c, cudaMalloc(&c->ix, 2 * npts * sizeof(int)), "allocating obs");
+        c->iy = c->ix + npts;
+        CK(c, cudaMalloc(&c->yo, no * sizeof(double)), "allocating obs");
+        CK(c, cudaMalloc(&c->dY, no * c->k * sizeof(double)), "allocating obs");
+        CK(c, cudaMalloc(&c->d, no * sizeof(double)), "allocating obs");
+        CK(c, cudaMalloc(&c->G, no * no * sizeof(double)), "allocating obs");
+        if (is_fp32(c)) CK(c, cudaMalloc(&c->dY32, no * c->k * sizeof(float)), "allocating obs");
+        CK(c, cudaMallocHost(&c->h_yo, no * sizeof(double)), "allocating pinned staging");
+        CK(c, cudaMallocHost(&c->h_ixy, 2 * npts * sizeof(int)), "allocating pinned staging");
+        c->pts_cap = npts;
+        c->nobs_cap = nobs;
+    }
+    // The staging buffer may still be read by the previous copy.
+    if (c->obs_pending) CK(c, cudaEventSynchronize(c->obs_copied), "waiting for staging copy");
+    for (int j = 0; j < npts; ++j) {
+        c->h_yo[nvar * j] = yo_u[j];
+        c->h_yo[nvar * j + 1] = yo_v[j];
+        if (yo_r) c->h_yo[nvar * j + 2] = yo_r[j];
+        c->h_ixy[j] = ix[j];
+        c->h_ixy[npts + j] = iy[j];
+    }
+    c->iy = c->ix + npts;
+    CK(c, cudaMemcpyAsync(c->ix, c->h_ixy, 2 * npts * sizeof(int), cudaMemcpyHostToDevice, c->stream),
+       "copy positions");
+    CK(c, cudaMemcpyAsync(c->yo, c->h_yo, (size_t)nobs * sizeof(double), cudaMemcpyHostToDevice,
+                          c->stream),
+       "copy observations");
+    CK(c, cudaEventRecord(c->obs_copied, c->stream), "recording event");
+    c->obs_pending = true;
+    CK(c, launch_observe(c->f[c->cur], is_fp32(c), c->nx, c->ny, c->k, npts, nvar, c->ix, c->iy,
+                         c->yo, c->dY, c->d, c->stream),
+       "launching observation operator");
+    CK(c, launch_obs_gram(c->dY, nobs, c->k, c->G, c->stream), "launching observation Gram");
+    if (c->nvar != nvar || c->geo_ix.size() != (size_t)npts ||
+        !std::equal(ix, ix + npts, c->geo_ix.begin()) ||
+        !std::equal(iy, iy + npts, c->geo_iy.begin())) {
+        c->geo_ix.assign(ix, ix + npts);
+        c->geo_iy.assign(iy, iy + npts);
+        c->geo_dcut = -1.0;
+    }
+    c->npts = npts;
+    c->nvar = nvar;
+    c->sigma_u = sigma_u;
+    c->sigma_v = sigma_v;
+    c->sigma_r = sigma_r;
+    c->observed = true;
+    return LBM_OK;
 }
 
 }  // namespace
@@ -382,66 +460,14 @@ int lbm_energy_spectrum(lbm_ctx* c, double* E, int nshells, int ptr_kind) {
 
 int letkf_observe(lbm_ctx* c, int npts, const int* ix, const int* iy, const double* yo_u,
                   const double* yo_v, double sigma_u, double sigma_v) {
-    if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
-    if (npts < 1) return fail(c, LBM_EINVAL, "npts must be >= 1");
-    if (!ix || !iy || !yo_u || !yo_v) return fail(c, LBM_EINVAL, "NULL observation array");
-    if (!(sigma_u > 0.0) || !(sigma_v > 0.0) || !std::isfinite(sigma_u) || !std::isfinite(sigma_v))
-        return fail(c, LBM_EINVAL, "sigma_u and sigma_v must be finite and > 0");
-    if ((long long)npts * 2 > 65535) return fail(c, LBM_EINVAL, "too many observation points");
-    for (int j = 0; j < npts; ++j) {
-        if (ix[j] < 0 || ix[j] >= c->nx || iy[j] < 0 || iy[j] >= c->ny)
-            return fail(c, LBM_EINVAL, "observation point %d outside the lattice", j);
-        if (!std::isfinite(yo_u[j]) || !std::isfinite(yo_v[j]))
-            return fail(c, LBM_EINVAL, "observation %d is not finite", j);
-    }
-    if (!c->obs_copied)
-        CK(c, cudaEventCreateWithFlags(&c->obs_copied, cudaEventDisableTiming), "creating event");
-    if (npts > c->obs_cap) {
-        CK(c, cudaStreamSynchronize(c->stream), "synchronising");
-        free_obs(c);
-        const size_t no = 2 * (size_t)npts;
-        CK(c, cudaMalloc(&c->ix, 2 * npts * sizeof(int)), "allocating obs");
-        c->iy = c->ix + npts;
-        CK(c, cudaMalloc(&c->yo, no * sizeof(double)), "allocating obs");
-        CK(c, cudaMalloc(&c->dY, no * c->k * sizeof(double)), "allocating obs");
-        CK(c, cudaMalloc(&c->d, no * sizeof(double)), "allocating obs");
-        CK(c, cudaMalloc(&c->G, no * no * sizeof(double)), "allocating obs");
-        if (is_fp32(c)) CK(c, cudaMalloc(&c->dY32, no * c->k * sizeof(float)), "allocating obs");
-        CK(c, cudaMallocHost(&c->h_yo, no * sizeof(double)), "allocating pinned staging");
-        CK(c, cudaMallocHost(&c->h_ixy, 2 * npts * sizeof(int)), "allocating pinned staging");
-        c->obs_cap = npts;
-    }
-    // The staging buffer may still be read by the previous copy.
-    if (c->obs_pending) CK(c, cudaEventSynchronize(c->obs_copied), "waiting for staging copy");
-    for (int j = 0; j < npts; ++j) {
-        c->h_yo[2 * j] = yo_u[j];
-        c->h_yo[2 * j + 1] = yo_v[j];
-        c->h_ixy[j] = ix[j];
-        c->h_ixy[npts + j] = iy[j];
-    }
-    c->iy = c->ix + npts;
-    CK(c, cudaMemcpyAsync(c->ix, c->h_ixy, 2 * npts * sizeof(int), cudaMemcpyHostToDevice, c->stream),
-       "copy positions");
-    CK(c, cudaMemcpyAsync(c->yo, c->h_yo, 2 * npts * sizeof(double), cudaMemcpyHostToDevice,
-                          c->stream),
-       "copy observations");
-    CK(c, cudaEventRecord(c->obs_copied, c->stream), "recording event");
-    c->obs_pending = true;
-    CK(c, launch_observe(c->f[c->cur], is_fp32(c), c->nx, c->ny, c->k, npts, c->ix, c->iy, c->yo,
-                         c->dY, c->d, c->stream),
-       "launching observation operator");
-    CK(c, launch_obs_gram(c->dY, 2 * npts, c->k, c->G, c->stream), "launching observation Gram");
-    if (c->geo_ix.size() != (size_t)npts || !std::equal(ix, ix + npts, c->geo_ix.begin()) ||
-        !std::equal(iy, iy + npts, c->geo_iy.begin())) {
-        c->geo_ix.assign(ix, ix + npts);
-        c->geo_iy.assign(iy, iy + npts);
-        c->geo_dcut = -1.0;
-    }
-    c->npts = npts;
-    c->sigma_u = sigma_u;
-    c->sigma_v = sigma_v;
-    c->observed = true;
-    return LBM_OK;
+    return observe_impl(c, npts, ix, iy, yo_u, yo_v, nullptr, sigma_u, sigma_v, 1.0);
+}
+
+int letkf_observe_rho(lbm_ctx* c, int npts, const int* ix, const int* iy, const double* yo_u,
+                      const double* yo_v, const double* yo_rho, double sigma_u, double sigma_v,
+                      double sigma_rho) {
+    if (c && !yo_rho) return fail(c, LBM_EINVAL, "NULL observation array");
+    return observe_impl(c, npts, ix, iy, yo_u, yo_v, yo_rho, sigma_u, sigma_v, sigma_rho);
 }
 
 int letkf_analyze(lbm_ctx* c, double d_cut, double beta) {
@@ -451,7 +477,7 @@ int letkf_analyze(lbm_ctx* c, double d_cut, double beta) {
     if (!(beta > 0.0) || !std::isfinite(beta)) return fail(c, LBM_EINVAL, "beta must be > 0");
     if (!c->observed) return fail(c, LBM_EINVAL, "letkf_observe must precede letkf_analyze");
     const int nmax = largest_local_problem(c, d_cut);
-    const size_t scratch = analyze_scratch_bytes(c->nx, c->ny, is_fp32(c), c->npts, nmax);
+    const size_t scratch = analyze_scratch_bytes(c->nx, c->ny, is_fp32(c), c->nvar * c->npts, nmax);
     if (scratch > c->ana_scratch_bytes) {
         CK(c, cudaStreamSynchronize(c->stream), "synchronising");
         cudaFree(c->ana_scratch);
@@ -469,7 +495,8 @@ int letkf_analyze(lbm_ctx* c, double d_cut, double beta) {
         }
         c->aux_ready = true;
     }
-    ObsParams o{c->npts, c->ix, c->iy, c->dY, c->d, c->G, c->sigma_u, c->sigma_v, c->dY32};
+    ObsParams o{c->npts, c->ix, c->iy, c->dY, c->d, c->G, c->sigma_u, c->sigma_v, c->dY32,
+                c->nvar, c->sigma_r};
     CK(c, launch_analyze(c->f[c->cur], is_fp32(c), c->nx, c->ny, c->k, o, d_cut, beta, nmax,
                          c->flags, c->ana_scratch, c->aux_ready ? &c->aux : nullptr, c->stream),
        "launching analysis");

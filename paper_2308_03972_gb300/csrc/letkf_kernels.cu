@@ -57,19 +57,21 @@ __device__ __forceinline__ double gaspari_cohn(double d) {
 // ------------------------------------------------------------------ K2
 template <typename T, bool SHIFT>
 __global__ void __launch_bounds__(128) observe_kernel(const T* __restrict__ f, int nx, int ny,
-                                                      int k, const int* __restrict__ ix,
+                                                      int k, int nvar, const int* __restrict__ ix,
                                                       const int* __restrict__ iy,
                                                       const double* __restrict__ yo,
                                                       double* __restrict__ dY,
                                                       double* __restrict__ d) {
-    extern __shared__ double sh[];  // yu[k], yv[k], red[2 * 4]
-    double* yu = sh;
-    double* yv = sh + k;
-    double* red = sh + 2 * k;
+    // One block per observation point: the nvar observed variables (u, v,
+    // and rho when nvar = 3) of every member, their ensemble means, the
+    // perturbations and the innovations.
+    extern __shared__ double sh[];  // y[3][k], red[3 * 4]
+    double* yv = sh;
+    double* red = sh + 3 * k;
     const int j = blockIdx.x;
     const size_t plane = (size_t)nx * ny * k;
     const size_t base = ((size_t)iy[j] * nx + ix[j]) * k;
-    double su = 0.0, sv = 0.0;
+    double acc[3] = {0.0, 0.0, 0.0};
     for (int m = threadIdx.x; m < k; m += blockDim.x) {
         double r = SHIFT ? 1.0 : 0.0, jx = 0.0, jy = 0.0;
 #pragma unroll
@@ -79,29 +81,25 @@ __global__ void __launch_bounds__(128) observe_kernel(const T* __restrict__ f, i
             jx += d2q9_cx(a) * g;
             jy += d2q9_cy(a) * g;
         }
-        const double u = jx / r, v = jy / r;
-        yu[m] = u;
-        yv[m] = v;
-        su += u;
-        sv += v;
+        const double val[3] = {jx / r, jy / r, r};
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            yv[q * k + m] = val[q];
+            acc[q] += val[q];
+        }
     }
-    su = warp_sum(su);
-    sv = warp_sum(sv);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) {
-        red[w] = su;
-        red[4 + w] = sv;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const double t = warp_sum(acc[q]);
+        if (l == 0) red[4 * q + w] = t;
     }
     __syncthreads();
-    const double ubar = ((red[0] + red[1]) + (red[2] + red[3])) / k;
-    const double vbar = ((red[4] + red[5]) + (red[6] + red[7])) / k;
-    for (int m = threadIdx.x; m < k; m += blockDim.x) {
-        dY[(size_t)(2 * j) * k + m] = yu[m] - ubar;
-        dY[(size_t)(2 * j + 1) * k + m] = yv[m] - vbar;
-    }
-    if (threadIdx.x == 0) {
-        d[2 * j] = yo[2 * j] - ubar;
-        d[2 * j + 1] = yo[2 * j + 1] - vbar;
+    for (int q = 0; q < nvar; ++q) {
+        const double mean = ((red[4 * q] + red[4 * q + 1]) + (red[4 * q + 2] + red[4 * q + 3])) / k;
+        for (int m = threadIdx.x; m < k; m += blockDim.x)
+            dY[(size_t)(nvar * j + q) * k + m] = yv[q * k + m] - mean;
+        if (threadIdx.x == 0) d[nvar * j + q] = yo[nvar * j + q] - mean;
     }
 }
 
@@ -120,7 +118,7 @@ __global__ void obs_gram_kernel(const double* __restrict__ dY, int nobs, int k,
 
 // Local observation set of grid point (x, y), in increasing point order:
 // point j is in range when r / d_cut < 2 and G(r / d_cut) > 0; it gives the
-// two scalars 2j (u) and 2j+1 (v) with sqrt(rho) = sqrt(G) / sigma.
+// nvar scalars nvar*j + q (u, v, rho) with sqrt(rho-tilde) = sqrt(G) / sigma_q.
 // Returns the number of scalars p. Warp-cooperative.
 __device__ int local_set(const ObsParams& o, int x, int y, int nx, int ny, double d_cut, int lane,
                          int* lidx, double* lsq) {
@@ -141,17 +139,21 @@ __device__ int local_set(const ObsParams& o, int x, int y, int nx, int ny, doubl
         }
         const unsigned bal = __ballot_sync(kFull, in);
         if (in) {
-            const int pos = count + __popc(bal & ((1u << lane) - 1u));
+            const int pos = o.nvar * (count + __popc(bal & ((1u << lane) - 1u)));
             const double sg = sqrt(g);
-            lidx[2 * pos] = 2 * j;
-            lidx[2 * pos + 1] = 2 * j + 1;
-            lsq[2 * pos] = sg / o.sigma_u;
-            lsq[2 * pos + 1] = sg / o.sigma_v;
+            lidx[pos] = o.nvar * j;
+            lidx[pos + 1] = o.nvar * j + 1;
+            lsq[pos] = sg / o.sigma_u;
+            lsq[pos + 1] = sg / o.sigma_v;
+            if (o.nvar == 3) {
+                lidx[pos + 2] = 3 * j + 2;
+                lsq[pos + 2] = sg / o.sigma_r;
+            }
         }
         count += __popc(bal);
     }
     __syncwarp();
-    return 2 * count;
+    return o.nvar * count;
 }
 
 // ------------------------------------------------------------------ K3, FP64
@@ -355,7 +357,7 @@ __global__ void __launch_bounds__(32) analyze_fp64_kernel(double* __restrict__ f
                                                           double beta, int* __restrict__ flags) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int ld = AnaSmem<NM>::kLd;
-    const int nobs = 2 * o.npts;
+    const int nobs = o.nvar * o.npts;
     AnaSmem<NM> sm;
     sm.carve(smem_raw, k, nobs);
     const int lane = threadIdx.x;
@@ -685,7 +687,7 @@ template <int NS>
 __device__ void jacobi_point(const ObsParams& o, int k, int n, int p, bool obs_space, double aa,
                              const int* lidx, const double* lsq, int lane, float* __restrict__ Xp,
                              int /*xr = NREG*/, int* flags) {
-    const int nobs = 2 * o.npts;
+    const int nobs = o.nvar * o.npts;
     float a[NS], u[NS];
     if (obs_space) {
         const bool own = lane < n;
@@ -765,7 +767,7 @@ __global__ void __launch_bounds__(32 * kJacWarps) mixed_jacobi_kernel(int nx, in
                                                                       int ncell, int nm,
                                                                       MixScratch sc,
                                                                       int* __restrict__ flags) {
-    const int nobs = 2 * o.npts;
+    const int nobs = o.nvar * o.npts;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int li = blockIdx.x * kJacWarps + w;
     if (li >= ncell) return;
@@ -803,7 +805,7 @@ __global__ void __launch_bounds__(32) mixed_jacobi_smem_kernel(int nx, int ny, i
                                                                int nm, MixScratch sc,
                                                                int* __restrict__ flags) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int nobs = 2 * o.npts;
+    const int nobs = o.nvar * o.npts;
     const int ld = nm + 1;
     float* A = reinterpret_cast<float*>(smem_raw);
     float* U = A + (size_t)nm * ld;
@@ -1078,7 +1080,7 @@ __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f
                                                            MixScratch sc,
                                                            int* __restrict__ flags) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int nobs = 2 * o.npts;
+    const int nobs = o.nvar * o.npts;
     MixSmem sm = carve_mix(smem_raw, k, nobs, nm);
     const int ld = mix_ld(nm);
     const int lane = threadIdx.x;
@@ -1355,17 +1357,18 @@ __global__ void to_f32_kernel(const double* __restrict__ src, float* __restrict_
 
 }  // namespace
 
-cudaError_t launch_observe(const void* f, int fp32, int nx, int ny, int k, int npts, const int* ix,
-                           const int* iy, const double* yo, double* dY, double* d,
+cudaError_t launch_observe(const void* f, int fp32, int nx, int ny, int k, int npts, int nvar,
+                           const int* ix, const int* iy, const double* yo, double* dY, double* d,
                            cudaStream_t s) {
     if (npts <= 0) return cudaSuccess;
-    const size_t sh = (2 * (size_t)k + 8) * sizeof(double);
+    if (nvar != 2 && nvar != 3) return cudaErrorInvalidValue;
+    const size_t sh = (3 * (size_t)k + 12) * sizeof(double);
     if (fp32)
-        observe_kernel<float, true><<<npts, 128, sh, s>>>((const float*)f, nx, ny, k, ix, iy, yo, dY,
-                                                          d);
+        observe_kernel<float, true><<<npts, 128, sh, s>>>((const float*)f, nx, ny, k, nvar, ix, iy,
+                                                          yo, dY, d);
     else
-        observe_kernel<double, false><<<npts, 128, sh, s>>>((const double*)f, nx, ny, k, ix, iy, yo,
-                                                            dY, d);
+        observe_kernel<double, false><<<npts, 128, sh, s>>>((const double*)f, nx, ny, k, nvar, ix,
+                                                            iy, yo, dY, d);
     return cudaGetLastError();
 }
 
@@ -1378,11 +1381,11 @@ cudaError_t launch_obs_gram(const double* dY, int nobs, int k, double* G, cudaSt
 
 static int mixed_nm(int nmax) { return nmax < 2 ? 2 : (nmax > NMAX ? NMAX : nmax); }
 
-size_t analyze_scratch_bytes(int nx, int ny, int fp32, int npts, int nmax) {
+size_t analyze_scratch_bytes(int nx, int ny, int fp32, int nobs, int nmax) {
     if (!fp32) return 0;
     const int nm = mixed_nm(nmax);
-    const long long chunk = mix_chunk((long long)nx * ny, 2 * npts, nm);
-    return 2 * (size_t)chunk * mix_scratch_bytes_per_point(2 * npts, nm);  // double-buffered
+    const long long chunk = mix_chunk((long long)nx * ny, nobs, nm);
+    return 2 * (size_t)chunk * mix_scratch_bytes_per_point(nobs, nm);  // double-buffered
 }
 
 cudaError_t launch_analyze(void* f, int fp32, int nx, int ny, int k, const ObsParams& o,
@@ -1393,7 +1396,7 @@ cudaError_t launch_analyze(void* f, int fp32, int nx, int ny, int k, const ObsPa
     cudaError_t e;
     if (fp32) {
         if (!o.dY32 || !scratch || !aux) return cudaErrorInvalidValue;
-        const int nobs = 2 * o.npts;
+        const int nobs = o.nvar * o.npts;
         const int nm = mixed_nm(nmax);
         const size_t nd = (size_t)nobs * k;
         to_f32_kernel<<<(unsigned)((nd + 255) / 256), 256, 0, s>>>(o.dY, o.dY32, nd);
@@ -1441,7 +1444,7 @@ cudaError_t launch_analyze(void* f, int fp32, int nx, int ny, int k, const ObsPa
             if ((e = cudaEventRecord(aux->ref_done[b], s)) != cudaSuccess) return e;
         }
     } else {
-        const int nobs = 2 * o.npts;
+        const int nobs = o.nvar * o.npts;
         if (nmax <= 32) {
             const size_t sh = AnaSmem<32>::bytes(k, nobs);
             e = cudaFuncSetAttribute(analyze_fp64_kernel<32>,

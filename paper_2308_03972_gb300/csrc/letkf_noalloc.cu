@@ -125,7 +125,7 @@ extern "C" int letkf_analyze_noalloc(double* f, int nx, int ny, int members, int
     if (e != cudaSuccess) return cuda_fail(e, "copying positions");
     e = cudaMemcpyAsync(yo_d, yo, 2 * (size_t)npts * sizeof(double), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail(e, "copying observations");
-    e = launch_observe(f, 0, nx, ny, members, npts, ix_d, iy_d, yo_d, dY, d, s);
+    e = launch_observe(f, 0, nx, ny, members, npts, 2, ix_d, iy_d, yo_d, dY, d, s);
     if (e != cudaSuccess) return cuda_fail(e, "launching the observation operator");
     e = launch_obs_gram(dY, 2 * npts, members, G, s);
     if (e != cudaSuccess) return cuda_fail(e, "launching the observation Gram");
