@@ -240,10 +240,17 @@ __device__ bool jacobi_sym_warp(R* A, R* U, int n, int ld, int lane, R* rc, R* r
                 const bool rP = (any >> P) & 1u, rQ = (any >> Q) & 1u;
                 if (!rP && !rQ) continue;
                 const int pP = rp[P], qP = rq[P], pQ = rp[Q], qQ = rq[Q];
-                if (qP >= n || qQ >= n) continue;  // padding player
+                // For odd n the padding player n is always the q of its pair
+                // (it is the largest index); its pair does not rotate, and its
+                // row and column do not exist: they read as zero and are not
+                // written, while the real member of that pair is still turned
+                // by the other pair's rotation.
+                const bool vP = qP < n, vQ = qQ < n;
                 const R cP = rc[P], sP = rs[P], cQ = rc[Q], sQ = rs[Q];
-                const R x00 = A[pP * ld + pQ], x01 = A[pP * ld + qQ];
-                const R x10 = A[qP * ld + pQ], x11 = A[qP * ld + qQ];
+                const R x00 = A[pP * ld + pQ];
+                const R x01 = vQ ? A[pP * ld + qQ] : R(0);
+                const R x10 = vP ? A[qP * ld + pQ] : R(0);
+                const R x11 = (vP && vQ) ? A[qP * ld + qQ] : R(0);
                 // J_P^T X: rows p, q.
                 const R y00 = cP * x00 - sP * x10, y01 = cP * x01 - sP * x11;
                 const R y10 = sP * x00 + cP * x10, y11 = sP * x01 + cP * x11;
@@ -252,12 +259,18 @@ __device__ bool jacobi_sym_warp(R* A, R* U, int n, int ld, int lane, R* rc, R* r
                 const R z10 = cQ * y10 - sQ * y11, z11 = sQ * y10 + cQ * y11;
                 A[pP * ld + pQ] = z00;
                 A[pQ * ld + pP] = z00;
-                A[pP * ld + qQ] = z01;
-                A[qQ * ld + pP] = z01;
-                A[qP * ld + pQ] = z10;
-                A[pQ * ld + qP] = z10;
-                A[qP * ld + qQ] = z11;
-                A[qQ * ld + qP] = z11;
+                if (vQ) {
+                    A[pP * ld + qQ] = z01;
+                    A[qQ * ld + pP] = z01;
+                }
+                if (vP) {
+                    A[qP * ld + pQ] = z10;
+                    A[pQ * ld + qP] = z10;
+                }
+                if (vP && vQ) {
+                    A[qP * ld + qQ] = z11;
+                    A[qQ * ld + qP] = z11;
+                }
             }
             // U <- U J: rotate column pairs; lanes own rows.
             for (int row = lane; row < n; row += 32) {

@@ -231,3 +231,19 @@ def test_mixed_analysis_stays_at_the_binary32_floor(gpu, nx, ny, k, nox, noy, d_
     got = _gpu_analysis(gpu, f, ix, iy, yu, yv, d_cut, 1.05, gpu.LBM_MIXED)
     ref = oracle.letkf_analyze(f, ix, iy, yu, yv, SIGMA, SIGMA, d_cut, 1.05)
     assert norm_rel(got, ref) <= 5e-8
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("nx,ny,k,nox,noy,d_cut", [
+    (24, 20, 7, 4, 4, 6.0),     # odd k, ensemble space, one lane per column
+    (20, 20, 33, 5, 5, 40.0),   # odd k, ensemble space, two columns per lane
+    (20, 20, 45, 5, 5, 40.0),   # odd k in the 33..64 range
+])
+def test_odd_problem_sizes_match_oracle(gpu, prec, nx, ny, k, nox, noy, d_cut):
+    """Odd n pads the round-robin with a player that never rotates; the
+    real member of its pair must still be turned by the other rotations."""
+    f, ix, iy, yu, yv = _analysis_case(nx, ny, k, nox, noy, seed=3 * k)
+    p = gpu.LBM_FP64 if prec == "fp64" else gpu.LBM_MIXED
+    got = _gpu_analysis(gpu, f, ix, iy, yu, yv, d_cut, 1.05, p)
+    ref = oracle.letkf_analyze(f, ix, iy, yu, yv, SIGMA, SIGMA, d_cut, 1.05)
+    assert norm_rel(got, ref) <= (TOL_FP64 if prec == "fp64" else 1e-6)
