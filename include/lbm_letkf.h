@@ -74,6 +74,27 @@ typedef struct {
     void *stream;    /* cudaStream_t to queue work on; NULL = default stream */
 } lbm_config;
 
+/* Observation window of a variational misfit (used by lbm_misfit and
+ * lbm_misfit_gradient): observations of (u, v) at npts points after every
+ * obs_every steps of an nsteps forecast, i.e. at t = obs_every,
+ * 2 obs_every, ..., nt obs_every with nt = nsteps / obs_every (integer
+ * division). All pointers are host arrays read during the call.
+ *   ix, iy      [npts] lattice coordinates (0 <= ix < nx, 0 <= iy < ny)
+ *   yo_u, yo_v  [nt][npts] observed velocities, time-major
+ *   sigma_u, sigma_v  observation error standard deviations (> 0)
+ *   checkpoint_every  states kept by the gradient's forward pass: every
+ *               checkpoint_every steps (>= 1); the backward pass recomputes
+ *               the states in between one segment at a time. */
+typedef struct {
+    int nsteps;
+    int obs_every;
+    int checkpoint_every;
+    int npts;
+    const int *ix, *iy;
+    const double *yo_u, *yo_v;
+    double sigma_u, sigma_v;
+} lbm_window;
+
 /* Create a context: allocate the double-buffered ensemble state and copy the
  * initial f0 and the forcing field (Section 2; forcing Section 4.1).
  * f0 may be NULL (state set to the rest equilibrium rho = 1, u = 0);
@@ -137,6 +158,34 @@ int letkf_observe(lbm_ctx *ctx, int npts, const int *ix, const int *iy,
 int letkf_observe_rho(lbm_ctx *ctx, int npts, const int *ix, const int *iy,
                       const double *yo_u, const double *yo_v, const double *yo_rho,
                       double sigma_u, double sigma_v, double sigma_rho);
+
+/* Set the Smagorinsky coefficient C_s of the eddy-viscosity closure
+ * (Section 2) used by the following forecasts; finite, >= 0. */
+int lbm_set_closure(lbm_ctx *ctx, double cs_smag);
+
+/* Windowed observation misfit of every member (the cost a variational
+ * method minimises; the paper's Section 1 contrasts it with the ensemble
+ * method): starting from the current state (left unchanged), forecast
+ * nsteps steps and accumulate
+ *   J_m = 1/2 sum_t sum_j [ (u_m(eta_j, t) - yo_u[t][j])^2 / sigma_u^2
+ *                          + (v_m(eta_j, t) - yo_v[t][j])^2 / sigma_v^2 ].
+ * J: host [members]. Synchronises. */
+int lbm_misfit(lbm_ctx *ctx, const lbm_window *win, double *J);
+
+/* lbm_misfit and its gradient by the hand-written adjoint of the forecast
+ * (reverse sweep through the transposed collision Jacobian and the pulled
+ * streaming, with the forward states recomputed from checkpoints). For
+ * F = sum_m w_m J_m (w: host [members], NULL = all ones):
+ *   grad_f0 [9][ny][nx][members]  dF/df at the current state (FP64; host
+ *                                 or device per ptr_kind),
+ *   grad_cs [members] (host)      w_m dJ_m/dC_s (their sum is dF/dC_s).
+ * Either output may be NULL. In mixed precision the forecast and the
+ * adjoint run in binary32 (C_s derivative summed in FP64); in FP64 mode
+ * everything is FP64. Scratch of about (nsteps / checkpoint_every +
+ * checkpoint_every + 3) states is allocated and released on the context
+ * stream. Synchronises. */
+int lbm_misfit_gradient(lbm_ctx *ctx, const lbm_window *win, const double *w, double *J,
+                        double *grad_f0, double *grad_cs, int ptr_kind);
 
 /* LETKF analysis of the nine f_alpha at every grid point, in place
  * (Section 3.2: w-bar, P-tilde, delta-W = [(k-1) P-tilde]^{1/2} symmetric,

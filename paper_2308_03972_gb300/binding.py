@@ -36,6 +36,11 @@ class lbm_config(ctypes.Structure):
                 ("mu", _D), ("precision", _I), ("stream", _P)]
 
 
+class lbm_window(ctypes.Structure):
+    _fields_ = [("nsteps", _I), ("obs_every", _I), ("checkpoint_every", _I), ("npts", _I),
+                ("ix", _P), ("iy", _P), ("yo_u", _P), ("yo_v", _P), ("sigma_u", _D), ("sigma_v", _D)]
+
+
 SIGNATURES = {
     "lbm_init": (_I, [ctypes.POINTER(lbm_config), _P, _P, _I, ctypes.POINTER(_P)]),
     "lbm_set_equilibrium": (_I, [_P, _P, _P, _P, _I]),
@@ -46,6 +51,9 @@ SIGNATURES = {
     "letkf_observe": (_I, [_P, _I, _P, _P, _P, _P, _D, _D]),
     "letkf_observe_rho": (_I, [_P, _I, _P, _P, _P, _P, _P, _D, _D, _D]),
     "letkf_analyze": (_I, [_P, _D, _D]),
+    "lbm_set_closure": (_I, [_P, _D]),
+    "lbm_misfit": (_I, [_P, ctypes.POINTER(lbm_window), _P]),
+    "lbm_misfit_gradient": (_I, [_P, ctypes.POINTER(lbm_window), _P, _P, _P, _P, _I]),
     "lbm_nudge": (_I, [_P, _I, _I, _P, _P, _P, _D]),
     "lbm_get_f": (_I, [_P, _P, _I]),
     "lbm_set_f": (_I, [_P, _P, _I]),
@@ -220,6 +228,44 @@ def letkf_observe_rho(ctx, ix, iy, yo_u, yo_v, yo_rho, sigma_u, sigma_v, sigma_r
                                          float(sigma_u), float(sigma_v), float(sigma_rho)))
 
 
+def lbm_set_closure(ctx, cs_smag):
+    _check(ctx, load().lbm_set_closure(ctx, float(cs_smag)))
+
+
+class Window:
+    """Observation window of the misfit (the C struct lbm_window with its
+    arrays kept alive): yo_u, yo_v [nsteps // obs_every][npts]."""
+
+    def __init__(self, nsteps, obs_every, ix, iy, yo_u, yo_v, sigma_u, sigma_v, checkpoint_every=20):
+        self.ix = np.ascontiguousarray(ix, dtype=np.int32)
+        self.iy = np.ascontiguousarray(iy, dtype=np.int32)
+        nt = int(nsteps) // int(obs_every)
+        self.yo_u = np.ascontiguousarray(yo_u, dtype=np.float64).reshape(nt, len(self.ix))
+        self.yo_v = np.ascontiguousarray(yo_v, dtype=np.float64).reshape(nt, len(self.ix))
+        p = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+        self.c = lbm_window(int(nsteps), int(obs_every), int(checkpoint_every), len(self.ix), p(self.ix),
+                            p(self.iy), p(self.yo_u), p(self.yo_v), float(sigma_u), float(sigma_v))
+
+
+def lbm_misfit(ctx, win: Window, members: int):
+    J = np.zeros(members)
+    _check(ctx, load().lbm_misfit(ctx, ctypes.byref(win.c), J.ctypes.data_as(ctypes.c_void_p)))
+    return J
+
+
+def lbm_misfit_gradient(ctx, win: Window, members: int, weights=None, grad_f0=None):
+    """Return (J [k], grad_cs [k]); grad_f0 (numpy or CUDA tensor, float64
+    [9][ny][nx][k]) is filled in place when given."""
+    J = np.zeros(members)
+    gcs = np.zeros(members)
+    w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
+    pw = None if w is None else w.ctypes.data_as(ctypes.c_void_p)
+    pg, kg, _keep = _arr(grad_f0, writable=True)
+    _check(ctx, load().lbm_misfit_gradient(ctx, ctypes.byref(win.c), pw, J.ctypes.data_as(ctypes.c_void_p),
+                                           pg, gcs.ctypes.data_as(ctypes.c_void_p), kg))
+    return J, gcs
+
+
 def letkf_analyze(ctx, d_cut, beta):
     _check(ctx, load().letkf_analyze(ctx, float(d_cut), float(beta)))
 
@@ -320,6 +366,19 @@ class Ensemble:
 
     def observe(self, ix, iy, yo_u, yo_v, sigma_u, sigma_v):
         letkf_observe(self.ctx, ix, iy, yo_u, yo_v, sigma_u, sigma_v)
+
+    def set_closure(self, cs_smag):
+        lbm_set_closure(self.ctx, cs_smag)
+
+    def misfit(self, win):
+        return lbm_misfit(self.ctx, win, self.members)
+
+    def misfit_gradient(self, win, weights=None, grad_f0=None):
+        """(J, grad_f0, grad_cs); grad_f0 is a new numpy array unless given."""
+        if grad_f0 is None:
+            grad_f0 = np.zeros((9, self.ny, self.nx, self.members))
+        J, gcs = lbm_misfit_gradient(self.ctx, win, self.members, weights, grad_f0)
+        return J, grad_f0, gcs
 
     def observe_rho(self, ix, iy, yo_u, yo_v, yo_rho, sigma_u, sigma_v, sigma_rho):
         letkf_observe_rho(self.ctx, ix, iy, yo_u, yo_v, yo_rho, sigma_u, sigma_v, sigma_rho)

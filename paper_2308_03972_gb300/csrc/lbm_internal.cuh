@@ -101,4 +101,24 @@ size_t spectrum_work_bytes(int nx, int ny, int k, int nshells);
 cudaError_t launch_energy_spectrum(const void* f, int fp32, int nx, int ny, int k, double* E,
                                    int nshells, void* work, int* flags, cudaStream_t s);
 
+// ---- adjoint_kernels.cu ---------------------------------------------------
+// Adjoint of one LBM step at the stored state f_t: lam_out = (df_{t+1}/df_t)^T
+// lam_in; dJ/dCs of every member added to gcs[k] (FP64). fp32: FP32 shifted
+// state and FP32 adjoint; else FP64 for both. force in the state's type.
+cudaError_t launch_adjoint_step(const void* ft, const void* lam_in, void* lam_out, const void* force,
+                                int fp32, const LbmParams& p, double cs, double* gcs,
+                                cudaStream_t s);
+// Misfit terms r[npts][k] of one observation time; yo [npts][2] (u, v).
+cudaError_t launch_misfit(const void* f, int fp32, int nx, int ny, int k, int npts, const int* ix,
+                          const int* iy, const double* yo, double sigma_u, double sigma_v,
+                          double* r, cudaStream_t s);
+// lam += w_m d(misfit of one time)/df at the observation points.
+cudaError_t launch_misfit_adjoint(const void* f, void* lam, int fp32, int nx, int ny, int k, int npts,
+                                  const int* ix, const int* iy, const double* yo, double sigma_u,
+                                  double sigma_v, const double* w, cudaStream_t s);
+// J[m] = sum_i r[i][m], i < nterms, in order.
+cudaError_t launch_misfit_reduce(const double* r, int nterms, int k, double* J, cudaStream_t s);
+// dst = (double) src, n elements (no shift: for adjoint fields).
+cudaError_t launch_widen(const void* src, int fp32, double* dst, size_t n, cudaStream_t s);
+
 }  // namespace lbmgpu

@@ -16,57 +16,10 @@
 #include <cmath>
 
 #include "lbm_internal.cuh"
+#include "vec.cuh"
 
 namespace lbmgpu {
 namespace {
-
-template <typename T, int V>
-struct Vec;
-template <>
-struct Vec<double, 1> {
-    static __device__ __forceinline__ void ld(const double* p, double (&v)[1]) { v[0] = __ldg(p); }
-    static __device__ __forceinline__ void st(double* p, const double (&v)[1]) { p[0] = v[0]; }
-};
-template <>
-struct Vec<double, 2> {
-    static __device__ __forceinline__ void ld(const double* p, double (&v)[2]) {
-        double2 t = __ldg(reinterpret_cast<const double2*>(p));
-        v[0] = t.x;
-        v[1] = t.y;
-    }
-    static __device__ __forceinline__ void st(double* p, const double (&v)[2]) {
-        *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
-    }
-};
-template <>
-struct Vec<float, 1> {
-    static __device__ __forceinline__ void ld(const float* p, float (&v)[1]) { v[0] = __ldg(p); }
-    static __device__ __forceinline__ void st(float* p, const float (&v)[1]) { p[0] = v[0]; }
-};
-template <>
-struct Vec<float, 2> {
-    static __device__ __forceinline__ void ld(const float* p, float (&v)[2]) {
-        float2 t = __ldg(reinterpret_cast<const float2*>(p));
-        v[0] = t.x;
-        v[1] = t.y;
-    }
-    static __device__ __forceinline__ void st(float* p, const float (&v)[2]) {
-        *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
-    }
-};
-template <>
-struct Vec<float, 4> {
-    static __device__ __forceinline__ void ld(const float* p, float (&v)[4]) {
-        float4 t = __ldg(reinterpret_cast<const float4*>(p));
-        v[0] = t.x;
-        v[1] = t.y;
-        v[2] = t.z;
-        v[3] = t.w;
-    }
-    static __device__ __forceinline__ void st(float* p, const float (&v)[4]) {
-        *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
-    }
-};
 
 // BGK-LES collision of one member at one cell, in place on f[9].
 // SHIFT: f holds g = f - w_alpha. Returns true if the state is bad

@@ -243,6 +243,183 @@ int observe_impl(lbm_ctx* c, int npts, const int* ix, const int* iy, const doubl
     return LBM_OK;
 }
 
+// Device buffers of one misfit/gradient call, allocated and released in
+// stream order on the context stream.
+struct StreamScratch {
+    cudaStream_t s;
+    std::vector<void*> bufs;
+    explicit StreamScratch(cudaStream_t st) : s(st) {}
+    cudaError_t get(void** p, size_t bytes) {
+        *p = nullptr;
+        cudaError_t e = cudaMallocAsync(p, bytes ? bytes : 16, s);
+        if (e == cudaSuccess) bufs.push_back(*p);
+        return e;
+    }
+    ~StreamScratch() {
+        for (void* b : bufs) cudaFreeAsync(b, s);
+    }
+};
+
+// Forward sweep of the window with the misfit, and (want_grad) the reverse
+// sweep: lambda_N from the last observation, then for every segment of
+// checkpoint_every steps (last first) the forward states are recomputed from
+// its checkpoint and the step adjoint runs back through them, adding the
+// misfit derivative at each observation time.
+int misfit_impl(lbm_ctx* c, const lbm_window* win, const double* w, double* J, double* grad_f0,
+                double* grad_cs, int ptr_kind, bool want_grad) {
+    if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (!win) return fail(c, LBM_EINVAL, "window is NULL");
+    if (!ptr_kind_ok(ptr_kind)) return fail(c, LBM_EINVAL, "bad ptr_kind");
+    const int N = win->nsteps, E = win->obs_every, C = win->checkpoint_every, np = win->npts;
+    if (N < 1 || E < 1 || C < 1 || np < 0)
+        return fail(c, LBM_EINVAL, "nsteps, obs_every, checkpoint_every must be >= 1 and npts >= 0");
+    const int nt = N / E;
+    if (np > 0) {
+        if (!win->ix || !win->iy || !win->yo_u || !win->yo_v)
+            return fail(c, LBM_EINVAL, "NULL observation array");
+        if (!(win->sigma_u > 0.0) || !(win->sigma_v > 0.0) || !std::isfinite(win->sigma_u) ||
+            !std::isfinite(win->sigma_v))
+            return fail(c, LBM_EINVAL, "sigma_u and sigma_v must be finite and > 0");
+        for (int j = 0; j < np; ++j)
+            if (win->ix[j] < 0 || win->ix[j] >= c->nx || win->iy[j] < 0 || win->iy[j] >= c->ny)
+                return fail(c, LBM_EINVAL, "observation point %d outside the lattice", j);
+        for (size_t i = 0; i < (size_t)nt * np; ++i)
+            if (!std::isfinite(win->yo_u[i]) || !std::isfinite(win->yo_v[i]))
+                return fail(c, LBM_EINVAL, "observation %zu is not finite", i);
+    }
+    if (w)
+        for (int m = 0; m < c->k; ++m)
+            if (!std::isfinite(w[m])) return fail(c, LBM_EINVAL, "weight %d is not finite", m);
+    const int fp32 = is_fp32(c);
+    const size_t S = state_elems(c) * elem_size(c);
+    const int k = c->k;
+    const LbmParams p{c->nx, c->ny, k, c->tau0, 18.0 * c->cs * c->cs, c->mu};
+    auto step = [&](const void* in, void* out) {
+        return fp32 ? launch_lbm_step_f32((const float*)in, (float*)out, (const float*)c->force, p,
+                                          c->flags, c->stream)
+                    : launch_lbm_step_f64((const double*)in, (double*)out,
+                                          (const double*)c->force, p, c->flags, c->stream);
+    };
+    StreamScratch sc(c->stream);
+    const int nck = want_grad ? (N + C - 1) / C : 0;
+    const int nseg = want_grad ? std::min(C, N) - 1 : 0;
+    std::vector<void*> ck(nck), seg(nseg);
+    void *tmp[2], *lam[2] = {nullptr, nullptr};
+    for (auto& b : ck) CK(c, sc.get(&b, S), "allocating checkpoints");
+    for (auto& b : seg) CK(c, sc.get(&b, S), "allocating segment states");
+    for (auto& b : tmp) CK(c, sc.get(&b, S), "allocating forecast states");
+    if (want_grad)
+        for (auto& b : lam) CK(c, sc.get(&b, S), "allocating adjoint states");
+    const size_t nterm = (size_t)nt * np;
+    void *d_pos, *d_yo, *d_w, *d_r, *d_J, *d_gcs;
+    CK(c, sc.get(&d_pos, 2 * (size_t)np * sizeof(int)), "allocating observations");
+    CK(c, sc.get(&d_yo, 2 * nterm * sizeof(double)), "allocating observations");
+    CK(c, sc.get(&d_w, (size_t)k * sizeof(double)), "allocating weights");
+    CK(c, sc.get(&d_r, nterm * k * sizeof(double)), "allocating misfit terms");
+    CK(c, sc.get(&d_J, (size_t)k * sizeof(double)), "allocating misfit");
+    CK(c, sc.get(&d_gcs, (size_t)k * sizeof(double)), "allocating C_s gradient");
+    // Host staging (pageable; the call synchronises before returning).
+    std::vector<int> hpos(2 * (size_t)np);
+    std::vector<double> hyo(2 * nterm), hw((size_t)k, 1.0);
+    for (int j = 0; j < np; ++j) {
+        hpos[j] = win->ix[j];
+        hpos[np + j] = win->iy[j];
+    }
+    for (size_t i = 0; i < nterm; ++i) {
+        hyo[2 * i] = win->yo_u[i];
+        hyo[2 * i + 1] = win->yo_v[i];
+    }
+    if (w) std::copy(w, w + k, hw.begin());
+    const int* ixd = (const int*)d_pos;
+    const int* iyd = ixd + np;
+    const double* yod = (const double*)d_yo;
+    if (np > 0) {
+        CK(c, cudaMemcpyAsync(d_pos, hpos.data(), hpos.size() * sizeof(int), cudaMemcpyHostToDevice,
+                              c->stream), "copy positions");
+        if (nterm)
+            CK(c, cudaMemcpyAsync(d_yo, hyo.data(), hyo.size() * sizeof(double),
+                                  cudaMemcpyHostToDevice, c->stream), "copy observations");
+    }
+    CK(c, cudaMemcpyAsync(d_w, hw.data(), (size_t)k * sizeof(double), cudaMemcpyHostToDevice, c->stream),
+       "copy weights");
+    auto obs_time = [&](int t) { return (np > 0 && t >= 1 && t % E == 0 && t / E <= nt) ? t / E - 1 : -1; };
+
+    // Forward sweep.
+    const void* prev = c->f[c->cur];
+    if (want_grad) {
+        CK(c, cudaMemcpyAsync(ck[0], prev, S, cudaMemcpyDeviceToDevice, c->stream), "checkpoint");
+    }
+    for (int t = 1; t <= N; ++t) {
+        void* out = (want_grad && t % C == 0 && t < N) ? ck[t / C] : tmp[t & 1];
+        CK(c, step(prev, out), "launching LBM step");
+        const int r = obs_time(t);
+        if (r >= 0)
+            CK(c, launch_misfit(out, fp32, c->nx, c->ny, k, np, ixd, iyd, yod + 2 * (size_t)r * np,
+                                win->sigma_u, win->sigma_v, (double*)d_r + (size_t)r * np * k, c->stream),
+               "launching misfit");
+        prev = out;
+    }
+    if (nterm) {
+        CK(c, launch_misfit_reduce((const double*)d_r, (int)nterm, k, (double*)d_J, c->stream),
+           "launching misfit reduction");
+    } else {
+        CK(c, cudaMemsetAsync(d_J, 0, (size_t)k * sizeof(double), c->stream), "clearing misfit");
+    }
+    if (J) CK(c, cudaMemcpyAsync(J, d_J, (size_t)k * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+              "copy misfit");
+
+    if (want_grad) {
+        // Reverse sweep.
+        const void* fN = prev;
+        int cur = 0;
+        CK(c, cudaMemsetAsync(lam[cur], 0, S, c->stream), "clearing adjoint");
+        CK(c, cudaMemsetAsync(d_gcs, 0, (size_t)k * sizeof(double), c->stream), "clearing C_s gradient");
+        if (obs_time(N) >= 0)
+            CK(c, launch_misfit_adjoint(fN, lam[cur], fp32, c->nx, c->ny, k, np, ixd, iyd,
+                                        yod + 2 * (size_t)obs_time(N) * np, win->sigma_u, win->sigma_v,
+                                        (const double*)d_w, c->stream),
+               "launching misfit adjoint");
+        std::vector<const void*> st((size_t)std::min(C, N));
+        for (int sgi = nck - 1; sgi >= 0; --sgi) {
+            const int t0 = sgi * C, t1 = std::min(t0 + C, N);
+            st[0] = ck[sgi];
+            for (int i = 1; i < t1 - t0; ++i) {
+                CK(c, step(st[i - 1], seg[i - 1]), "launching LBM step");
+                st[i] = seg[i - 1];
+            }
+            for (int t = t1 - 1; t >= t0; --t) {
+                CK(c, launch_adjoint_step(st[t - t0], lam[cur], lam[cur ^ 1], c->force, fp32, p, c->cs,
+                                          (double*)d_gcs, c->stream),
+                   "launching adjoint step");
+                cur ^= 1;
+                const int r = obs_time(t);
+                if (r >= 0)
+                    CK(c, launch_misfit_adjoint(st[t - t0], lam[cur], fp32, c->nx, c->ny, k, np, ixd, iyd,
+                                                yod + 2 * (size_t)r * np, win->sigma_u, win->sigma_v,
+                                                (const double*)d_w, c->stream),
+                       "launching misfit adjoint");
+            }
+        }
+        const size_t n = state_elems(c);
+        if (grad_f0) {
+            if (ptr_kind == LBM_PTR_DEVICE) {
+                CK(c, launch_widen(lam[cur], fp32, grad_f0, n, c->stream), "widening gradient");
+            } else {
+                int st2 = ensure_stage(c);
+                if (st2) return st2;
+                CK(c, launch_widen(lam[cur], fp32, c->stage, n, c->stream), "widening gradient");
+                CK(c, cudaMemcpyAsync(grad_f0, c->stage, n * sizeof(double), cudaMemcpyDeviceToHost,
+                                      c->stream), "copy gradient");
+            }
+        }
+        if (grad_cs)
+            CK(c, cudaMemcpyAsync(grad_cs, d_gcs, (size_t)k * sizeof(double), cudaMemcpyDeviceToHost,
+                                  c->stream), "copy C_s gradient");
+    }
+    CK(c, cudaStreamSynchronize(c->stream), "synchronising");
+    return read_flags(c);
+}
+
 }  // namespace
 
 namespace lbmgpu {
@@ -456,6 +633,23 @@ int lbm_energy_spectrum(lbm_ctx* c, double* E, int nshells, int ptr_kind) {
     CK(c, e, "launching the energy spectrum");
     CK(c, e2, "freeing spectrum scratch");
     return ptr_kind == LBM_PTR_HOST ? read_flags(c) : LBM_OK;
+}
+
+int lbm_set_closure(lbm_ctx* c, double cs_smag) {
+    if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (!(cs_smag >= 0.0) || !std::isfinite(cs_smag)) return fail(c, LBM_EINVAL, "cs_smag must be finite and >= 0");
+    c->cs = cs_smag;
+    return LBM_OK;
+}
+
+int lbm_misfit(lbm_ctx* c, const lbm_window* win, double* J) {
+    if (c && !J) return fail(c, LBM_EINVAL, "J is NULL");
+    return misfit_impl(c, win, nullptr, J, nullptr, nullptr, LBM_PTR_HOST, false);
+}
+
+int lbm_misfit_gradient(lbm_ctx* c, const lbm_window* win, const double* w, double* J,
+                        double* grad_f0, double* grad_cs, int ptr_kind) {
+    return misfit_impl(c, win, w, J, grad_f0, grad_cs, ptr_kind, true);
 }
 
 int letkf_observe(lbm_ctx* c, int npts, const int* ix, const int* iy, const double* yo_u,
