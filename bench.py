@@ -256,6 +256,66 @@ def measure_e2e(cfg, precision, steps, warmup):
             "d2h_bytes_per_step": 2 * cfg.nx * cfg.ny * 8}
 
 
+def measure_adjoint(cfg, reps=3):
+    """Gradient of a 200-step windowed (u, v) misfit for a batch of 64
+    initial states on the 256^2 lattice in binary32: observations of the
+    nature run at 16 x 16 points after every 10 steps (10% noise),
+    checkpoints every 20 steps, gradient left on the device."""
+    import torch
+
+    from paper_2308_03972_gb300 import binding, inputs
+
+    nsteps, every, side, ckpt = 200, 10, 16, 20
+    nx, ny, k = cfg.nx, cfg.ny, cfg.members
+    force = inputs.forcing_field(nx, ny, cfg.seeds["forcing"], cfg.force_amp, cfg.force_kmin, cfg.force_kmax)
+    ix, iy = inputs.uniform_obs_points(nx, ny, side, side)
+    tu, tv = inputs.random_velocity(nx, ny, cfg.seeds["nature"], cfg.u_rms)
+    nat = binding.Ensemble(nx, ny, 1, cfg.tau0, cfg.cs_smag, cfg.mu, binding.LBM_FP64, force=force)
+    nat.set_equilibrium(None, tu[:, :, None].copy(), tv[:, :, None].copy())
+    yu, yv = [], []
+    for t in range(every, nsteps + 1, every):
+        nat.forecast(every)
+        u, v = nat.mean_velocity()
+        nu, nv = inputs.obs_noise(cfg.seeds["noise"], t, len(ix))
+        yu.append(u[iy, ix] + cfg.sigma * nu)
+        yv.append(v[iy, ix] + cfg.sigma * nv)
+    nat.close()
+    win = binding.Window(nsteps, every, ix, iy, np.array(yu), np.array(yv), cfg.sigma, cfg.sigma, ckpt)
+    eu, ev = inputs.ensemble_velocity(nx, ny, k, cfg.seeds["ensemble"], cfg.u_rms, cfg.ens_pert)
+    ens = binding.Ensemble(nx, ny, k, cfg.tau0, cfg.cs_smag, cfg.mu, binding.LBM_MIXED, force=force)
+    ens.set_equilibrium(None, eu, ev)
+    grad = torch.empty((9, ny, nx, k), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    binding.lbm_misfit_gradient(ens.ctx, win, k, grad_f0=grad)  # warm-up
+    times, ftimes = [], []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        binding.lbm_misfit_gradient(ens.ctx, win, k, grad_f0=grad)
+        b.record(stream)
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+        a.record(stream)
+        ens.misfit(win)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ftimes.append(a.elapsed_time(b))
+    ens.close()
+    ms = statistics.median(times)
+    fms = statistics.median(ftimes)
+    upd = nx * ny * k
+    # Algorithmic HBM bytes: forward 200 steps and recomputation of 180 (read
+    # + write 9 binary32 values), 200 adjoint steps (read f_t and lambda,
+    # write lambda), the checkpoint copies, and the FP64 gradient write.
+    nrec = nsteps - nsteps // ckpt
+    byts = (nsteps + nrec) * 72 * upd + nsteps * 108 * upd + (nsteps // ckpt) * 72 * upd + 9 * 12 * upd
+    return {"workload": "256x256 x 64 initial states, 200-step window, (u,v) misfit at 16x16 points every "
+                        "10 steps, checkpoints every 20 steps, binary32 forecast and adjoint",
+            "ms_per_window_gradient": ms, "ms_per_window_misfit_only": fms,
+            "gradients_per_s": 1000.0 / ms, "algorithmic_bytes": byts,
+            "achieved_gbs": byts / (ms * 1e6)}
+
+
 def oracle_cycle_sample(cfg, npoints=8192, lbm_steps=1, seed=0):
     """Time the FP64 oracle on a bounded sample of one cycle: lbm_steps LBM
     steps of the whole ensemble and the LETKF analysis at npoints grid
@@ -315,6 +375,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--ref-points", type=int, default=8192)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--case", default="all", choices=["all", "adjoint"],
+                    help="adjoint: only the adjoint-window leg (for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -338,6 +400,11 @@ def main():
     binding.load()
 
     barrier_max = lambda x: reduce_max(x, world)  # noqa: E731
+    if args.case == "adjoint":
+        adj = measure_adjoint(cfg, reps=args.steps)
+        if rank == 0:
+            print(json.dumps({"case": "adjoint", **adj}))
+        return
 
     if world > 1:
         import torch.distributed as dist
@@ -396,6 +463,10 @@ def main():
                 "peak_source": "GB300 FP64 nominal 1.25 TFLOP/s (FMA microbenchmark: 1.20)",
                 "work": "algorithmic FP64 flops: 9 n^3 symmetric eigensolve + 2 per multiply-add of the products"}
 
+    adj = measure_adjoint(cfg)
+    adj["peak_gbs"] = hbm
+    adj["frac"] = adj["achieved_gbs"] / hbm
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = oracle_cycle_sample(cfg)
@@ -414,7 +485,7 @@ def main():
                     "h2d_bytes_per_step": e2e["h2d_bytes_per_step"],
                     "d2h_bytes_per_step": e2e["d2h_bytes_per_step"]},
             "gpu_launches": args.steps * mixed["launches_per_cycle"],
-            "roofline": roof, "kernels": kern, "throughput": throughput,
+            "roofline": roof, "kernels": kern, "throughput": throughput, "adjoint": adj,
             "rmse": {"mixed": mixed["rmse"], "fp64": fp64["rmse"], "obs_noise_rms": cfg.sigma * np.sqrt(2)},
             "clocks": mixed["clocks"], "cpu_baseline": cpu,
         }

@@ -113,7 +113,7 @@ __device__ __forceinline__ T collide_vjp(const T (&f)[9], const T (&g)[9], T (&o
 // summed per block in shared memory (FP64) and added to gcs[k] once per
 // block and member.
 template <typename T, int V, bool SHIFT>
-__global__ void __launch_bounds__(256) adjoint_step_kernel(const T* __restrict__ ft,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) adjoint_step_kernel(const T* __restrict__ ft,
                                                            const T* __restrict__ lam_in,
                                                            T* __restrict__ lam_out,
                                                            const T* __restrict__ force, int nx,
@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(256) adjoint_step_kernel(const T* __restrict__
         Vec<T, V>::ld(src(8, xm, yp), g[8]);
         const T Fix = __ldg(force + cell);
         const T Fiy = __ldg(force + (size_t)nx * ny + cell);
-        T out[9][V];
+        double dcs[V];
 #pragma unroll
         for (int j = 0; j < V; ++j) {
             T fj[9], gj[9], oj[9];
@@ -162,13 +162,26 @@ __global__ void __launch_bounds__(256) adjoint_step_kernel(const T* __restrict__
                 fj[a] = f[a][j];
                 gj[a] = g[a][j];
             }
-            const T dcs = collide_vjp<T, SHIFT>(fj, gj, oj, Fix, Fiy, tau0, cs, mu);
+            dcs[j] = (double)collide_vjp<T, SHIFT>(fj, gj, oj, Fix, Fiy, tau0, cs, mu);
 #pragma unroll
-            for (int a = 0; a < 9; ++a) out[a][j] = oj[a];
-            atomicAdd(&gblk[mo + j], (double)dcs);
+            for (int a = 0; a < 9; ++a) g[a][j] = oj[a];  // g now holds the output
         }
 #pragma unroll
-        for (int a = 0; a < 9; ++a) Vec<T, V>::st(lam_out + a * plane + here, out[a]);
+        for (int a = 0; a < 9; ++a) Vec<T, V>::st(lam_out + a * plane + here, g[a]);
+        // C_s derivative per member: lanes kv apart hold the same members when
+        // kv divides 32, so they combine by shuffles first.
+        const int lane = threadIdx.x & 31;
+        if (32 % kv == 0 && (blockDim.x & 31) == 0 && (long long)(t - lane) + 32 <= total) {
+            for (int o = 16; o >= kv; o >>= 1)
+#pragma unroll
+                for (int j = 0; j < V; ++j) dcs[j] += __shfl_xor_sync(0xffffffffu, dcs[j], o);
+            if (lane < kv)
+#pragma unroll
+                for (int j = 0; j < V; ++j) atomicAdd(&gblk[mo + j], dcs[j]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < V; ++j) atomicAdd(&gblk[mo + j], dcs[j]);
+        }
     }
     __syncthreads();
     for (int m = threadIdx.x; m < k; m += blockDim.x)
@@ -227,14 +240,21 @@ __global__ void misfit_adjoint_kernel(const T* __restrict__ f, T* __restrict__ l
         atomicAdd(&lam[b * plane + at], (T)(ru * (d2q9_cx(b) - u) + rv * (d2q9_cy(b) - v)));
 }
 
-// J[m] = sum over times and points of r, in a fixed order.
-__global__ void misfit_reduce_kernel(const double* __restrict__ r, int nterms, int k,
-                                     double* __restrict__ J) {
-    const int m = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= k) return;
+// J[m] = sum over times and points of r: one block per member, strided
+// partial sums then a shared-memory tree, in a fixed order.
+__global__ void __launch_bounds__(256) misfit_reduce_kernel(const double* __restrict__ r, int nterms,
+                                                            int k, double* __restrict__ J) {
+    __shared__ double part[256];
+    const int m = blockIdx.x;
     double s = 0.0;
-    for (int i = 0; i < nterms; ++i) s += r[(size_t)i * k + m];
-    J[m] = s;
+    for (int i = threadIdx.x; i < nterms; i += 256) s += r[(size_t)i * k + m];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) J[m] = part[0];
 }
 
 template <typename T>
@@ -270,13 +290,13 @@ cudaError_t launch_adjoint_step(const void* ft, const void* lam_in, void* lam_ou
     if (fp32) {
         const float *f = (const float*)ft, *li = (const float*)lam_in, *fo = (const float*)force;
         float* lo = (float*)lam_out;
-        if (p.k % 4 == 0) return adjoint_step_v<float, 4, true>(f, li, lo, fo, p, cs, gcs, s);
         if (p.k % 2 == 0) return adjoint_step_v<float, 2, true>(f, li, lo, fo, p, cs, gcs, s);
         return adjoint_step_v<float, 1, true>(f, li, lo, fo, p, cs, gcs, s);
     }
     const double *f = (const double*)ft, *li = (const double*)lam_in, *fo = (const double*)force;
     double* lo = (double*)lam_out;
-    if (p.k % 2 == 0) return adjoint_step_v<double, 2, false>(f, li, lo, fo, p, cs, gcs, s);
+    // FP64: one member per thread (the FP64 collision adjoint is bound by
+    // the FP64 units; two members per thread would spill).
     return adjoint_step_v<double, 1, false>(f, li, lo, fo, p, cs, gcs, s);
 }
 
@@ -311,7 +331,7 @@ cudaError_t launch_misfit_adjoint(const void* f, void* lam, int fp32, int nx, in
 }
 
 cudaError_t launch_misfit_reduce(const double* r, int nterms, int k, double* J, cudaStream_t s) {
-    misfit_reduce_kernel<<<blocks_of(k, 128), 128, 0, s>>>(r, nterms, k, J);
+    misfit_reduce_kernel<<<(unsigned)k, 256, 0, s>>>(r, nterms, k, J);
     return cudaGetLastError();
 }
 
