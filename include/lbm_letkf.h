@@ -159,6 +159,19 @@ int letkf_observe_rho(lbm_ctx *ctx, int npts, const int *ix, const int *iy,
                       const double *yo_u, const double *yo_v, const double *yo_rho,
                       double sigma_u, double sigma_v, double sigma_rho);
 
+/* Arithmetic of the local Gram matrix C = (k-1)/beta I + Yh^T Yh and of
+ * b = Yh^T d-hat (Section 3.2, with Yh = R_loc^{-1/2} dY_loc) in the
+ * ensemble-space form (p >= k) of a mixed-precision context's analysis:
+ *   LBM_PROD_FP64  FP64 products and sums (default);
+ *   LBM_PROD_FP32  binary32 products, binary32 accumulation (CUDA cores);
+ *   LBM_PROD_TF32  TF32 products on the tensor cores, binary32 accumulation;
+ *   LBM_PROD_BF16  BF16 products on the tensor cores, binary32 accumulation.
+ * The eigensolve stays FP64-accurate in every mode; the reduced modes apply
+ * for members <= 64 (larger ensembles keep FP64). LBM_EINVAL for an unknown
+ * mode or a reduced mode on an FP64 context. Applies to later analyses. */
+enum { LBM_PROD_FP64 = 0, LBM_PROD_FP32 = 1, LBM_PROD_TF32 = 2, LBM_PROD_BF16 = 3 };
+int letkf_set_products(lbm_ctx *ctx, int mode);
+
 /* Set the Smagorinsky coefficient C_s of the eddy-viscosity closure
  * (Section 2) used by the following forecasts; finite, >= 0. */
 int lbm_set_closure(lbm_ctx *ctx, double cs_smag);

@@ -21,6 +21,7 @@ from . import build as _build
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EDIVERGED, LBM_ENOCONV = range(6)
 LBM_FP64, LBM_MIXED = 0, 1
 LBM_PTR_HOST, LBM_PTR_DEVICE = 0, 1
+LBM_PROD_FP64, LBM_PROD_FP32, LBM_PROD_TF32, LBM_PROD_BF16 = range(4)
 
 STATUS_NAMES = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA",
                 4: "LBM_EDIVERGED", 5: "LBM_ENOCONV"}
@@ -52,6 +53,7 @@ SIGNATURES = {
     "letkf_observe_rho": (_I, [_P, _I, _P, _P, _P, _P, _P, _D, _D, _D]),
     "letkf_analyze": (_I, [_P, _D, _D]),
     "lbm_set_closure": (_I, [_P, _D]),
+    "letkf_set_products": (_I, [_P, _I]),
     "lbm_misfit": (_I, [_P, ctypes.POINTER(lbm_window), _P]),
     "lbm_misfit_gradient": (_I, [_P, ctypes.POINTER(lbm_window), _P, _P, _P, _P, _I]),
     "lbm_nudge": (_I, [_P, _I, _I, _P, _P, _P, _D]),
@@ -228,6 +230,10 @@ def letkf_observe_rho(ctx, ix, iy, yo_u, yo_v, yo_rho, sigma_u, sigma_v, sigma_r
                                          float(sigma_u), float(sigma_v), float(sigma_rho)))
 
 
+def letkf_set_products(ctx, mode):
+    _check(ctx, load().letkf_set_products(ctx, int(mode)))
+
+
 def lbm_set_closure(ctx, cs_smag):
     _check(ctx, load().lbm_set_closure(ctx, float(cs_smag)))
 
@@ -366,6 +372,9 @@ class Ensemble:
 
     def observe(self, ix, iy, yo_u, yo_v, sigma_u, sigma_v):
         letkf_observe(self.ctx, ix, iy, yo_u, yo_v, sigma_u, sigma_v)
+
+    def set_products(self, mode):
+        letkf_set_products(self.ctx, mode)
 
     def set_closure(self, cs_smag):
         lbm_set_closure(self.ctx, cs_smag)

@@ -14,6 +14,11 @@ enum : int {
     FLAG_TOOLARGE = 4   // local problem larger than the analysis kernel holds
 };
 
+// Arithmetic of the local Gram matrix C = a I + Yh^T Yh and b = Yh^T d-hat in
+// the ensemble-space form of the mixed-precision analysis: FP64 (default),
+// or binary32 accumulation of binary32 / TF32 / BF16 products.
+enum : int { PROD_FP64 = 0, PROD_FP32 = 1, PROD_TF32 = 2, PROD_BF16 = 3 };
+
 // Speed limit used by the divergence check: |u| > 0.5 lattice units.
 constexpr double kUMax2 = 0.25;
 
@@ -86,11 +91,12 @@ struct AnalyzeAux {
     cudaEvent_t start, jac_done[2], ref_done[2];
 };
 // Scratch the analysis needs (bytes; 0 for the FP64 path).
-size_t analyze_scratch_bytes(int nx, int ny, int fp32, int nobs, int nmax);
+size_t analyze_scratch_bytes(int nx, int ny, int fp32, int nobs, int nmax, int k, int prod);
 // nmax: largest local problem size n = min(p, k) over the grid (sizes the
 // mixed kernel's shared memory; points above it are reported as too large).
+// prod: PROD_* arithmetic of the ensemble-space Gram (mixed precision only).
 cudaError_t launch_analyze(void* f, int fp32, int nx, int ny, int k, const ObsParams& o,
-                           double d_cut, double beta, int nmax, int* flags, void* scratch,
+                           double d_cut, double beta, int nmax, int prod, int* flags, void* scratch,
                            const AnalyzeAux* aux, cudaStream_t s);
 
 // ---- diag_kernels.cu ------------------------------------------------------

@@ -49,6 +49,7 @@ struct lbm_ctx {
     cudaEvent_t obs_copied = nullptr;  // last staging copy done
     bool obs_pending = false;
     double sigma_u = 0.0, sigma_v = 0.0, sigma_r = 1.0;
+    int prod = PROD_FP64;  // ensemble-space Gram arithmetic (mixed precision)
     bool observed = false;
     char err[512] = {0};
 };
@@ -635,6 +636,15 @@ int lbm_energy_spectrum(lbm_ctx* c, double* E, int nshells, int ptr_kind) {
     return ptr_kind == LBM_PTR_HOST ? read_flags(c) : LBM_OK;
 }
 
+int letkf_set_products(lbm_ctx* c, int mode) {
+    if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (mode < LBM_PROD_FP64 || mode > LBM_PROD_BF16) return fail(c, LBM_EINVAL, "unknown product mode %d", mode);
+    if (mode != LBM_PROD_FP64 && !is_fp32(c))
+        return fail(c, LBM_EINVAL, "reduced-precision products need a mixed-precision context");
+    c->prod = mode;
+    return LBM_OK;
+}
+
 int lbm_set_closure(lbm_ctx* c, double cs_smag) {
     if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
     if (!(cs_smag >= 0.0) || !std::isfinite(cs_smag)) return fail(c, LBM_EINVAL, "cs_smag must be finite and >= 0");
@@ -671,7 +681,8 @@ int letkf_analyze(lbm_ctx* c, double d_cut, double beta) {
     if (!(beta > 0.0) || !std::isfinite(beta)) return fail(c, LBM_EINVAL, "beta must be > 0");
     if (!c->observed) return fail(c, LBM_EINVAL, "letkf_observe must precede letkf_analyze");
     const int nmax = largest_local_problem(c, d_cut);
-    const size_t scratch = analyze_scratch_bytes(c->nx, c->ny, is_fp32(c), c->nvar * c->npts, nmax);
+    const size_t scratch =
+        analyze_scratch_bytes(c->nx, c->ny, is_fp32(c), c->nvar * c->npts, nmax, c->k, c->prod);
     if (scratch > c->ana_scratch_bytes) {
         CK(c, cudaStreamSynchronize(c->stream), "synchronising");
         cudaFree(c->ana_scratch);
@@ -691,7 +702,7 @@ int letkf_analyze(lbm_ctx* c, double d_cut, double beta) {
     }
     ObsParams o{c->npts, c->ix, c->iy, c->dY, c->d, c->G, c->sigma_u, c->sigma_v, c->dY32,
                 c->nvar, c->sigma_r};
-    CK(c, launch_analyze(c->f[c->cur], is_fp32(c), c->nx, c->ny, c->k, o, d_cut, beta, nmax,
+    CK(c, launch_analyze(c->f[c->cur], is_fp32(c), c->nx, c->ny, c->k, o, d_cut, beta, nmax, c->prod,
                          c->flags, c->ana_scratch, c->aux_ready ? &c->aux : nullptr, c->stream),
        "launching analysis");
     c->observed = false;

@@ -21,6 +21,9 @@
 // Section 8.5) with the round-robin parallel ordering, in FP64, on a
 // matrix held in shared memory, one column per lane.
 #include <cmath>
+#include <cstdint>
+
+#include <cuda_bf16.h>
 
 #include "lbm_internal.cuh"
 
@@ -699,7 +702,7 @@ __device__ bool jacobi32_reg(float (&a)[NS], float (&u)[NS], int lane, float rel
 template <int NS>
 __device__ void jacobi_point(const ObsParams& o, int k, int n, int p, bool obs_space, double aa,
                              const int* lidx, const double* lsq, int lane, float* __restrict__ Xp,
-                             int /*xr = NREG*/, int* flags) {
+                             int /*xr = NREG*/, int* flags, const float* __restrict__ Cp) {
     const int nobs = o.nvar * o.npts;
     float a[NS], u[NS];
     if (obs_space) {
@@ -709,6 +712,10 @@ __device__ void jacobi_point(const ObsParams& o, int k, int n, int p, bool obs_s
 #pragma unroll
         for (int i = 0; i < NS; ++i)
             a[i] = (own && i < n) ? (float)(lsq[i] * o.G[(size_t)lidx[i] * nobs + ol] * sl) : 0.0f;
+    } else if (Cp) {
+        // C from the reduced-precision Gram pass.
+#pragma unroll
+        for (int i = 0; i < NS; ++i) a[i] = (lane < n && i < n) ? Cp[i * k + lane] : 0.0f;
     } else {
         // C = a I + Yh^T Yh in FP64; lane owns column `lane`.
 #pragma unroll
@@ -742,26 +749,31 @@ struct MixScratch {
     double* lsq;   // [chunk][nobs] sqrt(rho) of the local scalars
     int* lidx;     // [chunk][nobs] their observation indices
     int* pcount;   // [chunk] number of local scalars
+    float* C32;    // [chunk][k][k] a I + Yh^T Yh from the reduced-precision Gram, or null
+    float* b32;    // [chunk][k] Yh^T d-hat from the same pass, or null
 };
 
 // Row stride of the basis scratch: 128-byte rows for the register Jacobi.
 __host__ __device__ inline int mix_xr(int nm) { return nm <= NREG ? NREG : NMAX; }
 
-__host__ __device__ inline size_t mix_scratch_bytes_per_point(int nobs, int nm) {
+// kg: members k when the reduced-precision Gram pass is used (its C and b
+// per point), else 0.
+__host__ __device__ inline size_t mix_scratch_bytes_per_point(int nobs, int nm, int kg) {
     const int xr = mix_xr(nm);
     return (size_t)xr * xr * sizeof(float) + (size_t)nobs * (sizeof(double) + sizeof(int)) +
-           sizeof(int);
+           sizeof(int) + (size_t)kg * (kg + 1) * sizeof(float);
 }
 
 // Grid points per chunk: the double-buffered scratch stays within ~96 MB of L2.
-__host__ __device__ inline long long mix_chunk(long long cells, int nobs, int nm) {
-    long long c = (48ll << 20) / (long long)mix_scratch_bytes_per_point(nobs, nm);
+__host__ __device__ inline long long mix_chunk(long long cells, int nobs, int nm, int kg) {
+    long long c = (48ll << 20) / (long long)mix_scratch_bytes_per_point(nobs, nm, kg);
     if (c > kChunkCells) c = kChunkCells;
     if (c < 256) c = 256;
     return cells < c ? cells : c;
 }
 
-__host__ __device__ inline MixScratch mix_scratch_at(void* base, long long chunk, int nobs, int nm) {
+__host__ __device__ inline MixScratch mix_scratch_at(void* base, long long chunk, int nobs, int nm,
+                                                    int kg) {
     MixScratch m;
     unsigned char* p = reinterpret_cast<unsigned char*>(base);
     m.X = reinterpret_cast<float*>(p);
@@ -771,7 +783,250 @@ __host__ __device__ inline MixScratch mix_scratch_at(void* base, long long chunk
     m.lidx = reinterpret_cast<int*>(p);
     p += (size_t)chunk * nobs * sizeof(int);
     m.pcount = reinterpret_cast<int*>(p);
+    p += ((size_t)chunk * sizeof(int) + 15) / 16 * 16;
+    m.C32 = kg ? reinterpret_cast<float*>(p) : nullptr;
+    p += (size_t)chunk * kg * kg * sizeof(float);
+    m.b32 = kg ? reinterpret_cast<float*>(p) : nullptr;
     return m;
+}
+
+__host__ __device__ inline size_t mix_buf_bytes(long long chunk, int nobs, int nm, int kg) {
+    return (size_t)chunk * mix_scratch_bytes_per_point(nobs, nm, kg) + 16;
+}
+
+// ---- Local Gram matrices in reduced precision (ensemble-space form) --------
+// C = a I + Yh^T Yh and b = Yh^T d-hat for every grid point of a chunk, with
+// Yh = diag(sqrt(rho)) dY_loc (Section 3.2), from the binary32 copy of dY:
+// PROD_FP32 on the CUDA cores, PROD_TF32 (mma m16n8k8) and PROD_BF16 (mma
+// m16n8k16) on the tensor cores, all accumulating in binary32. A block takes
+// kGramPts consecutive grid points, one warp each; their local sets are
+// merged into one list of observation points, whose rows are staged once per
+// block in shared memory and weighted per point (rows outside a point's set
+// get weight 0). The weights are the same FP64 Gaspari-Cohn values the local
+// set uses, rounded to binary32.
+constexpr int kGramPts = 8;
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+__device__ __forceinline__ void mma_tf32(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2,
+                                         uint32_t a3, uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2,
+                                         uint32_t a3, uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// sqrt(G(r / d_cut)) of observation point j seen from (x, y), 0 outside the
+// support: the same FP64 operations as local_set.
+__device__ __forceinline__ double local_weight(const ObsParams& o, int j, int x, int y, int nx,
+                                               int ny, double d_cut) {
+    const int dx = min_image(o.ix[j] - x, nx);
+    const int dy = min_image(o.iy[j] - y, ny);
+    const double r = sqrt((double)dx * dx + (double)dy * dy);
+    const double dist = r / d_cut;
+    if (!(dist < 2.0)) return 0.0;
+    const double g = gaspari_cohn(dist);
+    return g > 0.0 ? sqrt(g) : 0.0;
+}
+
+template <int MODE, int K>
+__global__ void __launch_bounds__(32 * kGramPts, 1) local_gram_kernel(int nx, int ny, int k,
+                                                                     ObsParams o, double d_cut,
+                                                                     double aa, int cell0,
+                                                                     int ncell, MixScratch sc) {
+    constexpr int KC = MODE == PROD_TF32 ? 8 : 16;        // rows per stage
+    constexpr int LD = MODE == PROD_TF32 ? K + 8 : K + 4;  // conflict-free fragment reads
+    constexpr int MT = K / 16, NT = K / 8;
+    constexpr int NCOL = K > 32 ? 2 : 1;                   // columns per lane (FP32 path, b)
+    __shared__ float Ys[KC][LD];
+    __shared__ float Ws[kGramPts][KC];  // rho-tilde = (sqrt(G) / sigma)^2 per point and row
+    __shared__ float Ds[KC];
+    __shared__ int wcount[kGramPts];
+    extern __shared__ int U[];  // [npts] merged observation points
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int li0 = blockIdx.x * kGramPts;
+    const int nv = o.nvar;
+    const double sig[3] = {o.sigma_u, o.sigma_v, o.sigma_r};
+
+    // Merged local sets, in increasing point order.
+    int total = 0;
+    for (int j0 = 0; j0 < o.npts; j0 += 32 * kGramPts) {
+        const int j = j0 + threadIdx.x;
+        bool in = false;
+        if (j < o.npts) {
+            for (int q = 0; q < kGramPts && !in; ++q) {
+                if (li0 + q >= ncell) break;
+                const int cell = cell0 + li0 + q;
+                in = local_weight(o, j, cell % nx, cell / nx, nx, ny, d_cut) > 0.0;
+            }
+        }
+        const unsigned bal = __ballot_sync(kFull, in);
+        if (lane == 0) wcount[w] = __popc(bal);
+        __syncthreads();
+        int off = total, add = 0;
+        for (int q = 0; q < kGramPts; ++q) {
+            if (q < w) off += wcount[q];
+            add += wcount[q];
+        }
+        if (in) U[off + __popc(bal & ((1u << lane) - 1u))] = j;
+        total += add;
+        __syncthreads();
+    }
+
+    const int rows = total * nv;
+    const int g = lane >> 2, t = lane & 3;
+    float acc[MODE == PROD_FP32 ? 1 : MT][MODE == PROD_FP32 ? 1 : NT][4];
+    float accf[MODE == PROD_FP32 ? K : 1][NCOL];
+    float bacc[NCOL];
+#pragma unroll
+    for (int c = 0; c < NCOL; ++c) bacc[c] = 0.0f;
+    if constexpr (MODE == PROD_FP32) {
+#pragma unroll
+        for (int m = 0; m < K; ++m)
+#pragma unroll
+            for (int c = 0; c < NCOL; ++c) accf[m][c] = 0.0f;
+    } else {
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) acc[mt][nt][i] = 0.0f;
+    }
+    for (int r0 = 0; r0 < rows; r0 += KC) {
+        for (int e = threadIdx.x; e < KC * K; e += 32 * kGramPts) {
+            const int rr = e / K, c = e % K, r = r0 + rr;
+            float v = 0.0f;
+            if (r < rows && c < k) v = o.dY32[(size_t)(nv * U[r / nv] + r % nv) * k + c];
+            Ys[rr][c] = v;
+        }
+        if (threadIdx.x < KC * kGramPts) {
+            const int q = threadIdx.x / KC, rr = threadIdx.x % KC, r = r0 + rr;
+            float wv = 0.0f;
+            if (r < rows && li0 + q < ncell) {
+                const int cell = cell0 + li0 + q;
+                const double sg = local_weight(o, U[r / nv], cell % nx, cell / nx, nx, ny, d_cut);
+                const double l = sg / sig[r % nv];
+                wv = (float)(l * l);
+            }
+            Ws[q][rr] = wv;
+        }
+        if (threadIdx.x < KC) {
+            const int r = r0 + threadIdx.x;
+            Ds[threadIdx.x] = r < rows ? (float)o.d[nv * U[r / nv] + r % nv] : 0.0f;
+        }
+        __syncthreads();
+        if constexpr (MODE == PROD_FP32) {
+            for (int rr = 0; rr < KC; ++rr) {
+                const float wl = Ws[w][rr];
+                if (wl == 0.0f) continue;
+                float yc[NCOL];
+#pragma unroll
+                for (int c = 0; c < NCOL; ++c) {
+                    yc[c] = (lane + 32 * c < K) ? Ys[rr][lane + 32 * c] : 0.0f;
+                    bacc[c] += wl * Ds[rr] * yc[c];
+                }
+#pragma unroll
+                for (int m = 0; m < K; ++m) {
+                    const float ym = wl * Ys[rr][m];
+#pragma unroll
+                    for (int c = 0; c < NCOL; ++c) accf[m][c] += ym * yc[c];
+                }
+            }
+        } else {
+#pragma unroll
+            for (int rr = 0; rr < KC; ++rr) {
+                const float wl = Ws[w][rr];
+#pragma unroll
+                for (int c = 0; c < NCOL; ++c)
+                    if (lane + 32 * c < K) bacc[c] += wl * Ds[rr] * Ys[rr][lane + 32 * c];
+            }
+            if constexpr (MODE == PROD_TF32) {
+                const float wa = Ws[w][t], wb = Ws[w][t + 4];
+                uint32_t bf[NT][2];
+#pragma unroll
+                for (int nt = 0; nt < NT; ++nt) {
+                    bf[nt][0] = to_tf32(Ys[t][8 * nt + g]);
+                    bf[nt][1] = to_tf32(Ys[t + 4][8 * nt + g]);
+                }
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt) {
+                    const uint32_t a0 = to_tf32(wa * Ys[t][16 * mt + g]);
+                    const uint32_t a1 = to_tf32(wa * Ys[t][16 * mt + g + 8]);
+                    const uint32_t a2 = to_tf32(wb * Ys[t + 4][16 * mt + g]);
+                    const uint32_t a3 = to_tf32(wb * Ys[t + 4][16 * mt + g + 8]);
+#pragma unroll
+                    for (int nt = 0; nt < NT; ++nt) mma_tf32(acc[mt][nt], a0, a1, a2, a3, bf[nt][0], bf[nt][1]);
+                }
+            } else {
+                const int r0a = 2 * t, r1a = 2 * t + 1, r0b = 2 * t + 8, r1b = 2 * t + 9;
+                const float w0 = Ws[w][r0a], w1 = Ws[w][r1a], w8 = Ws[w][r0b], w9 = Ws[w][r1b];
+                uint32_t bf[NT][2];
+#pragma unroll
+                for (int nt = 0; nt < NT; ++nt) {
+                    bf[nt][0] = pack_bf16(Ys[r0a][8 * nt + g], Ys[r1a][8 * nt + g]);
+                    bf[nt][1] = pack_bf16(Ys[r0b][8 * nt + g], Ys[r1b][8 * nt + g]);
+                }
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt) {
+                    const int m0 = 16 * mt + g, m1 = m0 + 8;
+                    const uint32_t a0 = pack_bf16(w0 * Ys[r0a][m0], w1 * Ys[r1a][m0]);
+                    const uint32_t a1 = pack_bf16(w0 * Ys[r0a][m1], w1 * Ys[r1a][m1]);
+                    const uint32_t a2 = pack_bf16(w8 * Ys[r0b][m0], w9 * Ys[r1b][m0]);
+                    const uint32_t a3 = pack_bf16(w8 * Ys[r0b][m1], w9 * Ys[r1b][m1]);
+#pragma unroll
+                    for (int nt = 0; nt < NT; ++nt) mma_bf16(acc[mt][nt], a0, a1, a2, a3, bf[nt][0], bf[nt][1]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    const int li = li0 + w;
+    if (li >= ncell) return;
+    float* C = sc.C32 + (size_t)li * k * k;
+    const float fa = (float)aa;
+    if constexpr (MODE == PROD_FP32) {
+#pragma unroll
+        for (int m = 0; m < K; ++m)
+#pragma unroll
+            for (int c = 0; c < NCOL; ++c) {
+                const int n = lane + 32 * c;
+                if (m < k && n < k) C[m * k + n] = accf[m][c] + (m == n ? fa : 0.0f);
+            }
+    } else {
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int m = 16 * mt + g + (i >= 2 ? 8 : 0);
+                    const int n = 8 * nt + 2 * t + (i & 1);
+                    if (m < k && n < k) C[m * k + n] = acc[mt][nt][i] + (m == n ? fa : 0.0f);
+                }
+    }
+#pragma unroll
+    for (int c = 0; c < NCOL; ++c)
+        if (lane + 32 * c < k) sc.b32[(size_t)li * k + lane + 32 * c] = bacc[c];
 }
 
 __global__ void __launch_bounds__(32 * kJacWarps) mixed_jacobi_kernel(int nx, int ny, int k,
@@ -797,18 +1052,19 @@ __global__ void __launch_bounds__(32 * kJacWarps) mixed_jacobi_kernel(int nx, in
     const double aa = (k - 1) / beta;
     constexpr int xr = NREG;  // this kernel serves nm <= NREG
     float* Xp = sc.X + (size_t)li * xr * xr;
+    const float* Cp = sc.C32 ? sc.C32 + (size_t)li * k * k : nullptr;
     if (n <= 8)
-        jacobi_point<8>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, xr, flags);
+        jacobi_point<8>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, xr, flags, Cp);
     else if (n <= 16)
-        jacobi_point<16>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, xr, flags);
+        jacobi_point<16>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, xr, flags, Cp);
     else if (n <= 24)
-        jacobi_point<24>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, xr, flags);
+        jacobi_point<24>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, xr, flags, Cp);
     else if (n <= 26)
-        jacobi_point<26>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, xr, flags);
+        jacobi_point<26>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, xr, flags, Cp);
     else if (n <= 28)
-        jacobi_point<28>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, xr, flags);
+        jacobi_point<28>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, xr, flags, Cp);
     else
-        jacobi_point<32>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, xr, flags);
+        jacobi_point<32>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, xr, flags, Cp);
 }
 
 // Kernel (A) for local problems of 33..64: the binary32 Jacobi in shared
@@ -844,6 +1100,9 @@ __global__ void __launch_bounds__(32) mixed_jacobi_smem_kernel(int nx, int ny, i
             const int oc = lidx[c];
             const double sc_ = lsq[c];
             for (int i = 0; i < n; ++i) A[i * ld + c] = (float)(lsq[i] * o.G[(size_t)lidx[i] * nobs + oc] * sc_);
+        } else if (sc.C32) {
+            const float* Cp = sc.C32 + (size_t)li * k * k;
+            for (int i = 0; i < n; ++i) A[i * ld + c] = Cp[i * k + c];
         } else {
             for (int i = 0; i < n; ++i) {
                 double s = (i == c) ? aa : 0.0;
@@ -1153,6 +1412,10 @@ __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f
             const double sl = sm.lsq[c];
             for (int i = 0; i < n; ++i)
                 A[i * ld + c] = sm.lsq[i] * o.G[(size_t)sm.lidx[i] * nobs + oc] * sl;
+        } else if (sc.C32) {
+            const float* Cp = sc.C32 + (size_t)li * k * k;
+            for (int i = 0; i < n; ++i) A[i * ld + c] = (double)Cp[i * k + c];
+            sm.vb[c] = (double)sc.b32[(size_t)li * k + c];
         } else {
             double bj = 0.0;
             for (int i = 0; i < n; ++i) {
@@ -1394,15 +1657,48 @@ cudaError_t launch_obs_gram(const double* dY, int nobs, int k, double* G, cudaSt
 
 static int mixed_nm(int nmax) { return nmax < 2 ? 2 : (nmax > NMAX ? NMAX : nmax); }
 
-size_t analyze_scratch_bytes(int nx, int ny, int fp32, int nobs, int nmax) {
+// Members k when the reduced-precision Gram pass runs (mixed precision, a
+// reduced product mode, k <= 64), else 0.
+static int gram_k(int fp32, int k, int prod) {
+    return (fp32 && prod != PROD_FP64 && k <= NMAX) ? k : 0;
+}
+
+template <int MODE>
+static cudaError_t launch_gram_mode(int nx, int ny, int k, const ObsParams& o, double d_cut,
+                                    double aa, int cell0, int nc, const MixScratch& sc,
+                                    cudaStream_t s) {
+    const size_t sh = (size_t)(o.npts > 0 ? o.npts : 1) * sizeof(int);
+    const unsigned grid = (unsigned)((nc + kGramPts - 1) / kGramPts);
+    auto go = [&](auto kern) {
+        cudaError_t e = cudaSuccess;
+        if (sh > 48 * 1024)
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+        if (e != cudaSuccess) return e;
+        kern<<<grid, 32 * kGramPts, sh, s>>>(nx, ny, k, o, d_cut, aa, cell0, nc, sc);
+        return cudaGetLastError();
+    };
+    if (k <= 16) return go(local_gram_kernel<MODE, 16>);
+    if (k <= 32) return go(local_gram_kernel<MODE, 32>);
+    return go(local_gram_kernel<MODE, 64>);
+}
+
+static cudaError_t launch_gram(int prod, int nx, int ny, int k, const ObsParams& o, double d_cut,
+                               double aa, int cell0, int nc, const MixScratch& sc, cudaStream_t s) {
+    if (prod == PROD_FP32) return launch_gram_mode<PROD_FP32>(nx, ny, k, o, d_cut, aa, cell0, nc, sc, s);
+    if (prod == PROD_TF32) return launch_gram_mode<PROD_TF32>(nx, ny, k, o, d_cut, aa, cell0, nc, sc, s);
+    return launch_gram_mode<PROD_BF16>(nx, ny, k, o, d_cut, aa, cell0, nc, sc, s);
+}
+
+size_t analyze_scratch_bytes(int nx, int ny, int fp32, int nobs, int nmax, int k, int prod) {
     if (!fp32) return 0;
     const int nm = mixed_nm(nmax);
-    const long long chunk = mix_chunk((long long)nx * ny, nobs, nm);
-    return 2 * (size_t)chunk * mix_scratch_bytes_per_point(nobs, nm);  // double-buffered
+    const int kg = gram_k(fp32, k, prod);
+    const long long chunk = mix_chunk((long long)nx * ny, nobs, nm, kg);
+    return 2 * mix_buf_bytes(chunk, nobs, nm, kg);  // double-buffered
 }
 
 cudaError_t launch_analyze(void* f, int fp32, int nx, int ny, int k, const ObsParams& o,
-                           double d_cut, double beta, int nmax, int* flags, void* scratch,
+                           double d_cut, double beta, int nmax, int prod, int* flags, void* scratch,
                            const AnalyzeAux* aux, cudaStream_t s) {
     const long long cells = (long long)nx * ny;
     if (cells > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
@@ -1426,8 +1722,9 @@ cudaError_t launch_analyze(void* f, int fp32, int nx, int ny, int k, const ObsPa
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shA);
             if (e != cudaSuccess) return e;
         }
-        const long long chunk = mix_chunk(cells, nobs, nm);
-        const size_t buf_bytes = (size_t)chunk * mix_scratch_bytes_per_point(nobs, nm);
+        const int kg = gram_k(fp32, k, prod);
+        const long long chunk = mix_chunk(cells, nobs, nm, kg);
+        const size_t buf_bytes = mix_buf_bytes(chunk, nobs, nm, kg);
         // Pipeline: (A) of chunk c on s2 overlaps (B) of chunk c-1 on s; the
         // scratch is double-buffered, (A) of chunk c waits for (B) of c-2.
         if ((e = cudaEventRecord(aux->start, s)) != cudaSuccess) return e;
@@ -1437,8 +1734,11 @@ cudaError_t launch_analyze(void* f, int fp32, int nx, int ny, int k, const ObsPa
             const int nc = (int)((cells - c0) < chunk ? (cells - c0) : chunk);
             const int b = c & 1;
             const MixScratch sc =
-                mix_scratch_at((unsigned char*)scratch + b * buf_bytes, chunk, nobs, nm);
+                mix_scratch_at((unsigned char*)scratch + b * buf_bytes, chunk, nobs, nm, kg);
             if (c >= 2 && (e = cudaStreamWaitEvent(aux->s2, aux->ref_done[b], 0)) != cudaSuccess)
+                return e;
+            if (kg && (e = launch_gram(prod, nx, ny, k, o, d_cut, (k - 1) / beta, (int)c0, nc, sc,
+                                       aux->s2)) != cudaSuccess)
                 return e;
             if (nm <= NREG)
                 mixed_jacobi_kernel<<<(unsigned)((nc + kJacWarps - 1) / kJacWarps), 32 * kJacWarps, 0,
