@@ -316,6 +316,55 @@ def measure_adjoint(cfg, reps=3):
             "achieved_gbs": byts / (ms * 1e6)}
 
 
+def measure_sweep(cfg, reps=2):
+    """Analysis time of the precision sweep at 256^2 (binary32 LBM state):
+    k in {16, 32, 64, 128}, observation lattices 8^2 .. 64^2, d_cut = 32 and
+    d_cut = the observation spacing, Gram/b products FP64 / binary32 / TF32 /
+    BF16. Cases with local problems above 64 are listed as refused."""
+    import torch
+
+    from paper_2308_03972_gb300 import binding, inputs
+
+    nx, ny = cfg.nx, cfg.ny
+    force = inputs.forcing_field(nx, ny, cfg.seeds["forcing"], cfg.force_amp, cfg.force_kmin, cfg.force_kmax)
+    tu, tv = inputs.random_velocity(nx, ny, cfg.seeds["nature"], cfg.u_rms)
+    stream = torch.cuda.current_stream()
+    modes = (("fp64", binding.LBM_PROD_FP64), ("fp32", binding.LBM_PROD_FP32),
+             ("tf32", binding.LBM_PROD_TF32), ("bf16", binding.LBM_PROD_BF16))
+    out = []
+    for k in (16, 32, 64, 128):
+        eu, ev = inputs.ensemble_velocity(nx, ny, k, cfg.seeds["ensemble"], cfg.u_rms, cfg.ens_pert)
+        ens = binding.Ensemble(nx, ny, k, cfg.tau0, cfg.cs_smag, cfg.mu, binding.LBM_MIXED, force=force)
+        ens.set_equilibrium(None, eu, ev)
+        ens.forecast(10)
+        for no in (8, 16, 32, 64):
+            ix, iy = inputs.uniform_obs_points(nx, ny, no, no)
+            nu, nv = inputs.obs_noise(cfg.seeds["noise"], 1, len(ix))
+            yu, yv = tu[iy, ix] + cfg.sigma * nu, tv[iy, ix] + cfg.sigma * nv
+            for d_cut in sorted({32.0, float(nx // no)}):
+                row = {"k": k, "obs": "%dx%d" % (no, no), "d_cut": d_cut}
+                for name, mode in modes:
+                    ens.set_products(mode)
+                    ts = []
+                    try:
+                        for r in range(reps + 1):
+                            ens.observe(ix, iy, yu, yv, cfg.sigma, cfg.sigma)
+                            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                            a.record(stream)
+                            ens.analyze(d_cut, cfg.beta)
+                            b.record(stream)
+                            ens.sync()
+                            if r:
+                                ts.append(a.elapsed_time(b))
+                        row[name + "_ms"] = statistics.median(ts)
+                    except binding.LbmError as err:
+                        row["status"] = "refused: " + str(err).split(": ", 1)[-1]
+                        break
+                out.append(row)
+        ens.close()
+    return out
+
+
 def oracle_cycle_sample(cfg, npoints=8192, lbm_steps=1, seed=0):
     """Time the FP64 oracle on a bounded sample of one cycle: lbm_steps LBM
     steps of the whole ensemble and the LETKF analysis at npoints grid
@@ -375,8 +424,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--ref-points", type=int, default=8192)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--case", default="all", choices=["all", "adjoint"],
-                    help="adjoint: only the adjoint-window leg (for profiling)")
+    ap.add_argument("--case", default="all", choices=["all", "adjoint", "sweep"],
+                    help="adjoint: only the adjoint-window leg; sweep: precision-sweep timings")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -400,6 +449,11 @@ def main():
     binding.load()
 
     barrier_max = lambda x: reduce_max(x, world)  # noqa: E731
+    if args.case == "sweep":
+        for row in measure_sweep(cfg):
+            if rank == 0:
+                print(json.dumps({"case": "sweep", **row}))
+        return
     if args.case == "adjoint":
         adj = measure_adjoint(cfg, reps=args.steps)
         if rank == 0:

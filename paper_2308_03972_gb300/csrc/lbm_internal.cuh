@@ -53,6 +53,8 @@ struct ObsParams {
     float* dY32;       // [nobs][k] binary32 copy of dY (mixed precision only)
     int nvar = 2;      // 2: (u, v); 3: (u, v, rho)
     double sigma_r = 1.0;
+    int plmax = 0;     // capacity of one grid point's local list (0: nobs); a
+                       // point with more local scalars is reported too large
 };
 
 // ---- lbm_kernels.cu -------------------------------------------------------
@@ -91,7 +93,8 @@ struct AnalyzeAux {
     cudaEvent_t start, jac_done[2], ref_done[2];
 };
 // Scratch the analysis needs (bytes; 0 for the FP64 path).
-size_t analyze_scratch_bytes(int nx, int ny, int fp32, int nobs, int nmax, int k, int prod);
+// nl: capacity of a local list (ObsParams::plmax, or nobs).
+size_t analyze_scratch_bytes(int nx, int ny, int fp32, int nl, int nmax, int k, int prod);
 // nmax: largest local problem size n = min(p, k) over the grid (sizes the
 // mixed kernel's shared memory; points above it are reported as too large).
 // prod: PROD_* arithmetic of the ensemble-space Gram (mixed precision only).

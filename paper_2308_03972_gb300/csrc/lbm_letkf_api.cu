@@ -40,6 +40,7 @@ struct lbm_ctx {
     std::vector<int> geo_ix, geo_iy;
     double geo_dcut = -1.0;
     int geo_nmax = 0;
+    int geo_pmax = 0;  // largest local list (scalars) for geo_dcut
     AnalyzeAux aux{};              // second stream + events (mixed precision)
     bool aux_ready = false;
     double* nudge_obs = nullptr;  // [3][noy][nox] nudging observations
@@ -157,13 +158,15 @@ int largest_local_problem(lbm_ctx* c, double d_cut) {
             }
         }
     }
-    int nmax = 2;
+    int nmax = 2, vmax = 0;
     for (int v : cnt) {
         const int n = (c->nvar * v < c->k) ? c->nvar * v : c->k;
         if (n > nmax) nmax = n;
+        if (v > vmax) vmax = v;
     }
     c->geo_dcut = d_cut;
     c->geo_nmax = nmax;
+    c->geo_pmax = c->nvar * (vmax > 0 ? vmax : 1);
     return nmax;
 }
 
@@ -681,8 +684,8 @@ int letkf_analyze(lbm_ctx* c, double d_cut, double beta) {
     if (!(beta > 0.0) || !std::isfinite(beta)) return fail(c, LBM_EINVAL, "beta must be > 0");
     if (!c->observed) return fail(c, LBM_EINVAL, "letkf_observe must precede letkf_analyze");
     const int nmax = largest_local_problem(c, d_cut);
-    const size_t scratch =
-        analyze_scratch_bytes(c->nx, c->ny, is_fp32(c), c->nvar * c->npts, nmax, c->k, c->prod);
+    const int plmax = c->geo_pmax;
+    const size_t scratch = analyze_scratch_bytes(c->nx, c->ny, is_fp32(c), plmax, nmax, c->k, c->prod);
     if (scratch > c->ana_scratch_bytes) {
         CK(c, cudaStreamSynchronize(c->stream), "synchronising");
         cudaFree(c->ana_scratch);
@@ -701,7 +704,7 @@ int letkf_analyze(lbm_ctx* c, double d_cut, double beta) {
         c->aux_ready = true;
     }
     ObsParams o{c->npts, c->ix, c->iy, c->dY, c->d, c->G, c->sigma_u, c->sigma_v, c->dY32,
-                c->nvar, c->sigma_r};
+                c->nvar, c->sigma_r, plmax};
     CK(c, launch_analyze(c->f[c->cur], is_fp32(c), c->nx, c->ny, c->k, o, d_cut, beta, nmax, c->prod,
                          c->flags, c->ana_scratch, c->aux_ready ? &c->aux : nullptr, c->stream),
        "launching analysis");

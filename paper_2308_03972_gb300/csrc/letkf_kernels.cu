@@ -122,9 +122,10 @@ __global__ void obs_gram_kernel(const double* __restrict__ dY, int nobs, int k,
 // Local observation set of grid point (x, y), in increasing point order:
 // point j is in range when r / d_cut < 2 and G(r / d_cut) > 0; it gives the
 // nvar scalars nvar*j + q (u, v, rho) with sqrt(rho-tilde) = sqrt(G) / sigma_q.
-// Returns the number of scalars p. Warp-cooperative.
+// Returns the number of scalars p; at most cap of them are stored.
+// Warp-cooperative.
 __device__ int local_set(const ObsParams& o, int x, int y, int nx, int ny, double d_cut, int lane,
-                         int* lidx, double* lsq) {
+                         int* lidx, double* lsq, int cap) {
     int count = 0;
     for (int j0 = 0; j0 < o.npts; j0 += 32) {
         const int j = j0 + lane;
@@ -144,13 +145,17 @@ __device__ int local_set(const ObsParams& o, int x, int y, int nx, int ny, doubl
         if (in) {
             const int pos = o.nvar * (count + __popc(bal & ((1u << lane) - 1u)));
             const double sg = sqrt(g);
-            lidx[pos] = o.nvar * j;
-            lidx[pos + 1] = o.nvar * j + 1;
-            lsq[pos] = sg / o.sigma_u;
-            lsq[pos + 1] = sg / o.sigma_v;
-            if (o.nvar == 3) {
-                lidx[pos + 2] = 3 * j + 2;
-                lsq[pos + 2] = sg / o.sigma_r;
+            // Entries past the capacity are counted, not stored; the caller
+            // reports the point as too large.
+            if (pos + o.nvar <= cap) {
+                lidx[pos] = o.nvar * j;
+                lidx[pos + 1] = o.nvar * j + 1;
+                lsq[pos] = sg / o.sigma_u;
+                lsq[pos + 1] = sg / o.sigma_v;
+                if (o.nvar == 3) {
+                    lidx[pos + 2] = 3 * j + 2;
+                    lsq[pos + 2] = sg / o.sigma_r;
+                }
             }
         }
         count += __popc(bal);
@@ -374,8 +379,9 @@ __global__ void __launch_bounds__(32) analyze_fp64_kernel(double* __restrict__ f
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int ld = AnaSmem<NM>::kLd;
     const int nobs = o.nvar * o.npts;
+    const int cap = o.plmax > 0 ? o.plmax : nobs;
     AnaSmem<NM> sm;
-    sm.carve(smem_raw, k, nobs);
+    sm.carve(smem_raw, k, cap);
     const int lane = threadIdx.x;
     const int cell = blockIdx.x;
     const int x = cell % nx, y = cell / nx;
@@ -395,7 +401,11 @@ __global__ void __launch_bounds__(32) analyze_fp64_kernel(double* __restrict__ f
         if (lane == 0) sm.xbar[a] = mean;
     }
 
-    const int p = local_set(o, x, y, nx, ny, d_cut, lane, sm.lidx, sm.lsq);
+    const int p = local_set(o, x, y, nx, ny, d_cut, lane, sm.lidx, sm.lsq, cap);
+    if (p > cap) {
+        if (lane == 0) atomicOr(flags, FLAG_TOOLARGE);
+        return;
+    }
     for (int i = lane; i < p; i += 32) sm.ldh[i] = sm.lsq[i] * o.d[sm.lidx[i]];
     __syncwarp();
 
@@ -790,8 +800,10 @@ __host__ __device__ inline MixScratch mix_scratch_at(void* base, long long chunk
     return m;
 }
 
+// Bytes of one scratch buffer, rounded up to 256 so that the second buffer of
+// the pair starts as aligned as the first (its FP64 arrays need 8 bytes).
 __host__ __device__ inline size_t mix_buf_bytes(long long chunk, int nobs, int nm, int kg) {
-    return (size_t)chunk * mix_scratch_bytes_per_point(nobs, nm, kg) + 16;
+    return ((size_t)chunk * mix_scratch_bytes_per_point(nobs, nm, kg) + 16 + 255) / 256 * 256;
 }
 
 // ---- Local Gram matrices in reduced precision (ensemble-space form) --------
@@ -1041,11 +1053,12 @@ __global__ void __launch_bounds__(32 * kJacWarps) mixed_jacobi_kernel(int nx, in
     if (li >= ncell) return;
     const int cell = cell0 + li;
     const int x = cell % nx, y = cell / nx;
-    double* lsq = sc.lsq + (size_t)li * nobs;
-    int* lidx = sc.lidx + (size_t)li * nobs;
-    const int p = local_set(o, x, y, nx, ny, d_cut, lane, lidx, lsq);
+    const int cap = o.plmax > 0 ? o.plmax : nobs;
+    double* lsq = sc.lsq + (size_t)li * cap;
+    int* lidx = sc.lidx + (size_t)li * cap;
+    const int p = local_set(o, x, y, nx, ny, d_cut, lane, lidx, lsq, cap);
     if (lane == 0) sc.pcount[li] = p;
-    if (p == 0) return;
+    if (p == 0 || p > cap) return;  // p > cap: reported by kernel (B)
     const bool obs_space = p < k;
     const int n = obs_space ? p : k;
     if (n > nm || n > NREG) return;  // reported by kernel (B)
@@ -1086,11 +1099,12 @@ __global__ void __launch_bounds__(32) mixed_jacobi_smem_kernel(int nx, int ny, i
     const int li = blockIdx.x;
     const int cell = cell0 + li;
     const int x = cell % nx, y = cell / nx;
-    double* lsq = sc.lsq + (size_t)li * nobs;
-    int* lidx = sc.lidx + (size_t)li * nobs;
-    const int p = local_set(o, x, y, nx, ny, d_cut, lane, lidx, lsq);
+    const int cap = o.plmax > 0 ? o.plmax : nobs;
+    double* lsq = sc.lsq + (size_t)li * cap;
+    int* lidx = sc.lidx + (size_t)li * cap;
+    const int p = local_set(o, x, y, nx, ny, d_cut, lane, lidx, lsq, cap);
     if (lane == 0) sc.pcount[li] = p;
-    if (p == 0) return;
+    if (p == 0 || p > cap) return;  // p > cap: reported by kernel (B)
     const bool obs_space = p < k;
     const int n = obs_space ? p : k;
     if (n > nm) return;  // reported by kernel (B)
@@ -1353,7 +1367,8 @@ __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f
                                                            int* __restrict__ flags) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nobs = o.nvar * o.npts;
-    MixSmem sm = carve_mix(smem_raw, k, nobs, nm);
+    const int cap = o.plmax > 0 ? o.plmax : nobs;
+    MixSmem sm = carve_mix(smem_raw, k, cap, nm);
     const int ld = mix_ld(nm);
     const int lane = threadIdx.x;
     const int li = blockIdx.x;
@@ -1376,9 +1391,13 @@ __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f
 
     // Local set from kernel (A).
     const int p = sc.pcount[li];
+    if (p > cap) {
+        if (lane == 0) atomicOr(flags, FLAG_TOOLARGE);
+        return;
+    }
     for (int i = lane; i < p; i += 32) {
-        const int oi = sc.lidx[(size_t)li * nobs + i];
-        const double si = sc.lsq[(size_t)li * nobs + i];
+        const int oi = sc.lidx[(size_t)li * cap + i];
+        const double si = sc.lsq[(size_t)li * cap + i];
         sm.lidx[i] = oi;
         sm.lsq[i] = si;
         sm.ldh[i] = si * o.d[oi];
@@ -1689,12 +1708,12 @@ static cudaError_t launch_gram(int prod, int nx, int ny, int k, const ObsParams&
     return launch_gram_mode<PROD_BF16>(nx, ny, k, o, d_cut, aa, cell0, nc, sc, s);
 }
 
-size_t analyze_scratch_bytes(int nx, int ny, int fp32, int nobs, int nmax, int k, int prod) {
+size_t analyze_scratch_bytes(int nx, int ny, int fp32, int nl, int nmax, int k, int prod) {
     if (!fp32) return 0;
     const int nm = mixed_nm(nmax);
     const int kg = gram_k(fp32, k, prod);
-    const long long chunk = mix_chunk((long long)nx * ny, nobs, nm, kg);
-    return 2 * mix_buf_bytes(chunk, nobs, nm, kg);  // double-buffered
+    const long long chunk = mix_chunk((long long)nx * ny, nl, nm, kg);
+    return 2 * mix_buf_bytes(chunk, nl, nm, kg);  // double-buffered
 }
 
 cudaError_t launch_analyze(void* f, int fp32, int nx, int ny, int k, const ObsParams& o,
@@ -1709,7 +1728,8 @@ cudaError_t launch_analyze(void* f, int fp32, int nx, int ny, int k, const ObsPa
         const int nm = mixed_nm(nmax);
         const size_t nd = (size_t)nobs * k;
         to_f32_kernel<<<(unsigned)((nd + 255) / 256), 256, 0, s>>>(o.dY, o.dY32, nd);
-        const size_t shB = mix_smem_bytes(k, nobs, nm);
+        const int cap = o.plmax > 0 ? o.plmax : nobs;
+        const size_t shB = mix_smem_bytes(k, cap, nm);
         const size_t shA = nm > NREG ? 2 * (size_t)nm * (nm + 1) * sizeof(float) + 64 * (sizeof(float) + sizeof(int)) : 0;
         const bool wide = nm > NREG;
         e = wide ? cudaFuncSetAttribute(analyze_mixed_kernel<true>,
@@ -1723,8 +1743,8 @@ cudaError_t launch_analyze(void* f, int fp32, int nx, int ny, int k, const ObsPa
             if (e != cudaSuccess) return e;
         }
         const int kg = gram_k(fp32, k, prod);
-        const long long chunk = mix_chunk(cells, nobs, nm, kg);
-        const size_t buf_bytes = mix_buf_bytes(chunk, nobs, nm, kg);
+        const long long chunk = mix_chunk(cells, cap, nm, kg);
+        const size_t buf_bytes = mix_buf_bytes(chunk, cap, nm, kg);
         // Pipeline: (A) of chunk c on s2 overlaps (B) of chunk c-1 on s; the
         // scratch is double-buffered, (A) of chunk c waits for (B) of c-2.
         if ((e = cudaEventRecord(aux->start, s)) != cudaSuccess) return e;
@@ -1734,7 +1754,7 @@ cudaError_t launch_analyze(void* f, int fp32, int nx, int ny, int k, const ObsPa
             const int nc = (int)((cells - c0) < chunk ? (cells - c0) : chunk);
             const int b = c & 1;
             const MixScratch sc =
-                mix_scratch_at((unsigned char*)scratch + b * buf_bytes, chunk, nobs, nm, kg);
+                mix_scratch_at((unsigned char*)scratch + b * buf_bytes, chunk, cap, nm, kg);
             if (c >= 2 && (e = cudaStreamWaitEvent(aux->s2, aux->ref_done[b], 0)) != cudaSuccess)
                 return e;
             if (kg && (e = launch_gram(prod, nx, ny, k, o, d_cut, (k - 1) / beta, (int)c0, nc, sc,
@@ -1759,14 +1779,14 @@ cudaError_t launch_analyze(void* f, int fp32, int nx, int ny, int k, const ObsPa
     } else {
         const int nobs = o.nvar * o.npts;
         if (nmax <= 32) {
-            const size_t sh = AnaSmem<32>::bytes(k, nobs);
+            const size_t sh = AnaSmem<32>::bytes(k, o.plmax > 0 ? o.plmax : nobs);
             e = cudaFuncSetAttribute(analyze_fp64_kernel<32>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
             if (e != cudaSuccess) return e;
             analyze_fp64_kernel<32><<<(unsigned)cells, 32, sh, s>>>((double*)f, nx, ny, k, o, d_cut,
                                                                     beta, flags);
         } else {
-            const size_t sh = AnaSmem<64>::bytes(k, nobs);
+            const size_t sh = AnaSmem<64>::bytes(k, o.plmax > 0 ? o.plmax : nobs);
             e = cudaFuncSetAttribute(analyze_fp64_kernel<64>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
             if (e != cudaSuccess) return e;
