@@ -256,7 +256,7 @@ def measure_e2e(cfg, precision, steps, warmup):
             "d2h_bytes_per_step": 2 * cfg.nx * cfg.ny * 8}
 
 
-def measure_adjoint(cfg, reps=3):
+def measure_adjoint(cfg, reps=3, nsteps=200, ckpt=20):
     """Gradient of a 200-step windowed (u, v) misfit for a batch of 64
     initial states on the 256^2 lattice in binary32: observations of the
     nature run at 16 x 16 points after every 10 steps (10% noise),
@@ -265,7 +265,7 @@ def measure_adjoint(cfg, reps=3):
 
     from paper_2308_03972_gb300 import binding, inputs
 
-    nsteps, every, side, ckpt = 200, 10, 16, 20
+    every, side = 10, 16
     nx, ny, k = cfg.nx, cfg.ny, cfg.members
     force = inputs.forcing_field(nx, ny, cfg.seeds["forcing"], cfg.force_amp, cfg.force_kmin, cfg.force_kmax)
     ix, iy = inputs.uniform_obs_points(nx, ny, side, side)
@@ -309,8 +309,8 @@ def measure_adjoint(cfg, reps=3):
     # write lambda), the checkpoint copies, and the FP64 gradient write.
     nrec = nsteps - nsteps // ckpt
     byts = (nsteps + nrec) * 72 * upd + nsteps * 108 * upd + (nsteps // ckpt) * 72 * upd + 9 * 12 * upd
-    return {"workload": "256x256 x 64 initial states, 200-step window, (u,v) misfit at 16x16 points every "
-                        "10 steps, checkpoints every 20 steps, binary32 forecast and adjoint",
+    return {"workload": "256x256 x 64 initial states, %d-step window, (u,v) misfit at 16x16 points every "
+                        "10 steps, checkpoints every %d steps, binary32 forecast and adjoint" % (nsteps, ckpt),
             "ms_per_window_gradient": ms, "ms_per_window_misfit_only": fms,
             "gradients_per_s": 1000.0 / ms, "algorithmic_bytes": byts,
             "achieved_gbs": byts / (ms * 1e6)}
@@ -424,6 +424,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--ref-points", type=int, default=8192)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--window", type=int, default=200, help="adjoint window steps (--case adjoint)")
+    ap.add_argument("--checkpoint", type=int, default=20, help="adjoint checkpoint spacing (--case adjoint)")
     ap.add_argument("--case", default="all", choices=["all", "adjoint", "sweep"],
                     help="adjoint: only the adjoint-window leg; sweep: precision-sweep timings")
     args = ap.parse_args()
@@ -455,7 +457,7 @@ def main():
                 print(json.dumps({"case": "sweep", **row}))
         return
     if args.case == "adjoint":
-        adj = measure_adjoint(cfg, reps=args.steps)
+        adj = measure_adjoint(cfg, reps=args.steps, nsteps=args.window, ckpt=args.checkpoint)
         if rank == 0:
             print(json.dumps({"case": "adjoint", **adj}))
         return

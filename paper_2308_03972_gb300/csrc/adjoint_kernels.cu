@@ -76,7 +76,9 @@ __device__ __forceinline__ T collide_vjp(const T (&f)[9], const T (&g)[9], T (&o
     const T Q = sqrt(T(2) * (pxx * pxx + T(2) * pxy * pxy + pyy * pyy));
     const T cs18 = T(18) * cs * cs;
     const T S = sqrt(tau0 * tau0 + cs18 * Q * ir);
+    const T iS = T(1) / S;
     const T om = T(2) / (tau0 + S);
+    const T iQ = Q > T(0) ? T(1) / Q : T(0);
     // Contractions of the incoming adjoint.
     T grho = T(0), gjx = T(0), gjy = T(0), gF = T(0), gcx = T(0), gcy = T(0), h = T(0);
 #pragma unroll
@@ -92,8 +94,8 @@ __device__ __forceinline__ T collide_vjp(const T (&f)[9], const T (&g)[9], T (&o
         gcy += gw * cy;
         h += g[a] * fneq[a];
     }
-    const T kappa = h * om * om * cs18 / (T(4) * S);
-    const T qfac = Q > T(0) ? T(2) / (Q * rho) : T(0);
+    const T kappa = T(0.25) * h * om * om * cs18 * iS;
+    const T qfac = T(2) * ir * iQ;
     const T trp3 = (pxx + pyy) * T(1.0 / 3.0);
     const T base = om * grho + T(3) * gF - kappa * Q * ir * ir;
 #pragma unroll
@@ -104,7 +106,7 @@ __device__ __forceinline__ T collide_vjp(const T (&f)[9], const T (&g)[9], T (&o
         out[b] = (T(1) - om) * g[b] + base + om * (gjx * cx + gjy * cy) -
                  T(3) * mu * (gcx * cx + gcy * cy) + kappa * qfac * D;
     }
-    return h * om * om * T(9) * cs * Q / (rho * S);
+    return h * om * om * T(9) * cs * Q * ir * iS;
 }
 
 // One adjoint step: lam_out(xi) = collision VJP at f_t(xi) of the pulled
@@ -119,12 +121,14 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) adjoint_step_kern
                                                            const T* __restrict__ force, int nx,
                                                            int ny, int k, T tau0, T cs, T mu,
                                                            double* __restrict__ gcs) {
-    extern __shared__ double gblk[];  // [k]
-    for (int m = threadIdx.x; m < k; m += blockDim.x) gblk[m] = 0.0;
-    __syncthreads();
+    extern __shared__ unsigned char adj_smem[];
+    T* part = reinterpret_cast<T*>(adj_smem);  // [blockDim][V] C_s terms
     const int kv = k / V;
     const long long total = (long long)nx * ny * kv;
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    T dcs[V];
+#pragma unroll
+    for (int j = 0; j < V; ++j) dcs[j] = T(0);
     if (t < total) {
         const int mv = (int)(t % kv);
         const long long cell = t / kv;
@@ -153,7 +157,6 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) adjoint_step_kern
         Vec<T, V>::ld(src(8, xm, yp), g[8]);
         const T Fix = __ldg(force + cell);
         const T Fiy = __ldg(force + (size_t)nx * ny + cell);
-        double dcs[V];
 #pragma unroll
         for (int j = 0; j < V; ++j) {
             T fj[9], gj[9], oj[9];
@@ -162,30 +165,28 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) adjoint_step_kern
                 fj[a] = f[a][j];
                 gj[a] = g[a][j];
             }
-            dcs[j] = (double)collide_vjp<T, SHIFT>(fj, gj, oj, Fix, Fiy, tau0, cs, mu);
+            dcs[j] = collide_vjp<T, SHIFT>(fj, gj, oj, Fix, Fiy, tau0, cs, mu);
 #pragma unroll
             for (int a = 0; a < 9; ++a) g[a][j] = oj[a];  // g now holds the output
         }
 #pragma unroll
         for (int a = 0; a < 9; ++a) Vec<T, V>::st(lam_out + a * plane + here, g[a]);
-        // C_s derivative per member: lanes kv apart hold the same members when
-        // kv divides 32, so they combine by shuffles first.
-        const int lane = threadIdx.x & 31;
-        if (32 % kv == 0 && (blockDim.x & 31) == 0 && (long long)(t - lane) + 32 <= total) {
-            for (int o = 16; o >= kv; o >>= 1)
-#pragma unroll
-                for (int j = 0; j < V; ++j) dcs[j] += __shfl_xor_sync(0xffffffffu, dcs[j], o);
-            if (lane < kv)
-#pragma unroll
-                for (int j = 0; j < V; ++j) atomicAdd(&gblk[mo + j], dcs[j]);
-        } else {
-#pragma unroll
-            for (int j = 0; j < V; ++j) atomicAdd(&gblk[mo + j], dcs[j]);
-        }
     }
+    // C_s derivative per member: the block's terms of member m sit at the
+    // threads t0 with (t0 - first) % kv == m / V (slot m % V); they are summed
+    // in thread order and added to gcs once per block.
+#pragma unroll
+    for (int j = 0; j < V; ++j) part[threadIdx.x * V + j] = dcs[j];
     __syncthreads();
-    for (int m = threadIdx.x; m < k; m += blockDim.x)
-        if (gblk[m] != 0.0) atomicAdd(&gcs[m], gblk[m]);
+    const long long first = (long long)blockIdx.x * blockDim.x;
+    for (int m = threadIdx.x; m < k; m += blockDim.x) {
+        const int mv = m / V, j = m % V;
+        // First thread of the block holding member group mv.
+        int t0 = (int)((mv - first % kv + kv) % kv);
+        double acc = 0.0;
+        for (; t0 < (int)blockDim.x; t0 += kv) acc += (double)part[t0 * V + j];
+        if (acc != 0.0) atomicAdd(&gcs[m], acc);
+    }
 }
 
 // Misfit terms of one observation time: for point j and member m,
@@ -271,12 +272,7 @@ cudaError_t adjoint_step_v(const T* ft, const T* lin, T* lout, const T* force, c
     const long long total = (long long)p.nx * p.ny * (p.k / V);
     const long long nb = (total + 255) / 256;
     if (nb > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    const size_t sh = (size_t)p.k * sizeof(double);
-    if (sh > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(adjoint_step_kernel<T, V, SHIFT>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
-        if (e != cudaSuccess) return e;
-    }
+    const size_t sh = (size_t)256 * V * sizeof(T);
     adjoint_step_kernel<T, V, SHIFT><<<(unsigned)nb, 256, sh, s>>>(ft, lin, lout, force, p.nx, p.ny, p.k,
                                                                    (T)p.tau0, (T)cs, (T)p.mu, gcs);
     return cudaGetLastError();

@@ -41,6 +41,7 @@ struct lbm_ctx {
     double geo_dcut = -1.0;
     int geo_nmax = 0;
     int geo_pmax = 0;  // largest local list (scalars) for geo_dcut
+    bool geo_any_ens = false;  // some grid point has p >= k (ensemble-space form)
     AnalyzeAux aux{};              // second stream + events (mixed precision)
     bool aux_ready = false;
     double* nudge_obs = nullptr;  // [3][noy][nox] nudging observations
@@ -167,6 +168,7 @@ int largest_local_problem(lbm_ctx* c, double d_cut) {
     c->geo_dcut = d_cut;
     c->geo_nmax = nmax;
     c->geo_pmax = c->nvar * (vmax > 0 ? vmax : 1);
+    c->geo_any_ens = c->nvar * vmax >= c->k;
     return nmax;
 }
 
@@ -685,7 +687,9 @@ int letkf_analyze(lbm_ctx* c, double d_cut, double beta) {
     if (!c->observed) return fail(c, LBM_EINVAL, "letkf_observe must precede letkf_analyze");
     const int nmax = largest_local_problem(c, d_cut);
     const int plmax = c->geo_pmax;
-    const size_t scratch = analyze_scratch_bytes(c->nx, c->ny, is_fp32(c), plmax, nmax, c->k, c->prod);
+    // The reduced-precision Gram pass serves ensemble-space points only.
+    const int prod = c->geo_any_ens ? c->prod : PROD_FP64;
+    const size_t scratch = analyze_scratch_bytes(c->nx, c->ny, is_fp32(c), plmax, nmax, c->k, prod);
     if (scratch > c->ana_scratch_bytes) {
         CK(c, cudaStreamSynchronize(c->stream), "synchronising");
         cudaFree(c->ana_scratch);
@@ -705,7 +709,7 @@ int letkf_analyze(lbm_ctx* c, double d_cut, double beta) {
     }
     ObsParams o{c->npts, c->ix, c->iy, c->dY, c->d, c->G, c->sigma_u, c->sigma_v, c->dY32,
                 c->nvar, c->sigma_r, plmax};
-    CK(c, launch_analyze(c->f[c->cur], is_fp32(c), c->nx, c->ny, c->k, o, d_cut, beta, nmax, c->prod,
+    CK(c, launch_analyze(c->f[c->cur], is_fp32(c), c->nx, c->ny, c->k, o, d_cut, beta, nmax, prod,
                          c->flags, c->ana_scratch, c->aux_ready ? &c->aux : nullptr, c->stream),
        "launching analysis");
     c->observed = false;

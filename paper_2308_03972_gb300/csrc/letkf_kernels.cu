@@ -127,6 +127,7 @@ __global__ void obs_gram_kernel(const double* __restrict__ dY, int nobs, int k,
 __device__ int local_set(const ObsParams& o, int x, int y, int nx, int ny, double d_cut, int lane,
                          int* lidx, double* lsq, int cap) {
     int count = 0;
+    const double lim2 = (2.0 * d_cut + 1.0) * (2.0 * d_cut + 1.0);
     for (int j0 = 0; j0 < o.npts; j0 += 32) {
         const int j = j0 + lane;
         bool in = false;
@@ -134,11 +135,15 @@ __device__ int local_set(const ObsParams& o, int x, int y, int nx, int ny, doubl
         if (j < o.npts) {
             const int dx = min_image(o.ix[j] - x, nx);
             const int dy = min_image(o.iy[j] - y, ny);
-            const double r = sqrt((double)dx * dx + (double)dy * dy);
-            const double dist = r / d_cut;
-            if (dist < 2.0) {
-                g = gaspari_cohn(dist);
-                in = g > 0.0;
+            const double d2 = (double)dx * dx + (double)dy * dy;
+            // Integer prefilter well outside the support (r > 2 d_cut + 1);
+            // the decision itself is r / d_cut < 2 in FP64.
+            if (d2 <= lim2) {
+                const double dist = sqrt(d2) / d_cut;
+                if (dist < 2.0) {
+                    g = gaspari_cohn(dist);
+                    in = g > 0.0;
+                }
             }
         }
         const unsigned bal = __ballot_sync(kFull, in);
@@ -853,8 +858,9 @@ __device__ __forceinline__ double local_weight(const ObsParams& o, int j, int x,
                                                int ny, double d_cut) {
     const int dx = min_image(o.ix[j] - x, nx);
     const int dy = min_image(o.iy[j] - y, ny);
-    const double r = sqrt((double)dx * dx + (double)dy * dy);
-    const double dist = r / d_cut;
+    const double d2 = (double)dx * dx + (double)dy * dy;
+    if (d2 > (2.0 * d_cut + 1.0) * (2.0 * d_cut + 1.0)) return 0.0;
+    const double dist = sqrt(d2) / d_cut;
     if (!(dist < 2.0)) return 0.0;
     const double g = gaspari_cohn(dist);
     return g > 0.0 ? sqrt(g) : 0.0;
@@ -873,23 +879,32 @@ __global__ void __launch_bounds__(32 * kGramPts, 1) local_gram_kernel(int nx, in
     __shared__ float Ws[kGramPts][KC];  // rho-tilde = (sqrt(G) / sigma)^2 per point and row
     __shared__ float Ds[KC];
     __shared__ int wcount[kGramPts];
+    __shared__ int pcnt[kGramPts];  // local points of each grid point
     extern __shared__ int U[];  // [npts] merged observation points
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int li0 = blockIdx.x * kGramPts;
     const int nv = o.nvar;
     const double sig[3] = {o.sigma_u, o.sigma_v, o.sigma_r};
 
-    // Merged local sets, in increasing point order.
+    // Merged local sets, in increasing point order, and each grid point's count.
+    if (threadIdx.x < kGramPts) pcnt[threadIdx.x] = 0;
+    __syncthreads();
     int total = 0;
     for (int j0 = 0; j0 < o.npts; j0 += 32 * kGramPts) {
         const int j = j0 + threadIdx.x;
-        bool in = false;
+        unsigned bits = 0u;
         if (j < o.npts) {
-            for (int q = 0; q < kGramPts && !in; ++q) {
+            for (int q = 0; q < kGramPts; ++q) {
                 if (li0 + q >= ncell) break;
                 const int cell = cell0 + li0 + q;
-                in = local_weight(o, j, cell % nx, cell / nx, nx, ny, d_cut) > 0.0;
+                if (local_weight(o, j, cell % nx, cell / nx, nx, ny, d_cut) > 0.0) bits |= 1u << q;
             }
+        }
+        const bool in = bits != 0u;
+#pragma unroll
+        for (int q = 0; q < kGramPts; ++q) {
+            const unsigned bq = __ballot_sync(kFull, (bits >> q) & 1u);
+            if (lane == 0 && bq) atomicAdd(&pcnt[q], __popc(bq));
         }
         const unsigned bal = __ballot_sync(kFull, in);
         if (lane == 0) wcount[w] = __popc(bal);
@@ -904,6 +919,10 @@ __global__ void __launch_bounds__(32 * kGramPts, 1) local_gram_kernel(int nx, in
         __syncthreads();
     }
 
+    // Only grid points in the ensemble-space form (p >= k) read C and b.
+    bool any_ens = false;
+    for (int q = 0; q < kGramPts; ++q) any_ens |= pcnt[q] * nv >= k;
+    if (!any_ens) return;
     const int rows = total * nv;
     const int g = lane >> 2, t = lane & 3;
     float acc[MODE == PROD_FP32 ? 1 : MT][MODE == PROD_FP32 ? 1 : NT][4];
