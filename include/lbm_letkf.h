@@ -269,6 +269,53 @@ int letkf_analyze_noalloc(double *f, int nx, int ny, int members, int npts,
                           const double *yo_v, double sigma_u, double sigma_v,
                           double d_cut, double beta, void *stream);
 
+/* ---- Batches of independent experiments ----------------------------------
+ * Many DA experiments of uneven lattice, ensemble and observation sizes
+ * (the "thousands of trial-and-error experiments" of Section 1) advanced
+ * together. A batch groups existing contexts (1..64, one precision, one
+ * shared stream; the contexts stay owned by the caller and must outlive the
+ * batch). */
+typedef struct lbm_batch lbm_batch;
+
+/* Create a batch over ctxs[0..n-1]. LBM_EINVAL if a context is NULL or
+ * repeated, or the contexts differ in stream or precision. */
+int lbm_batch_create(lbm_ctx *const *ctxs, int n, lbm_batch **out);
+
+/* Advance every context nsteps LBM steps (Section 2) in ONE cooperative
+ * persistent launch: the grid strides over the work items of all
+ * experiments, and a grid barrier separates the steps. Each barrier wait is
+ * bounded (a few seconds); a timeout is reported by lbm_batch_sync.
+ * Results are identical to lbm_forecast on each context. Asynchronous. */
+int lbm_batch_forecast(lbm_batch *b, int nsteps);
+
+/* Pick the persistent launch shape (threads per block, blocks) by timing
+ * candidates on the batch's own experiments: block sizes 128/256/512 times
+ * 1..max co-resident blocks per SM, one step each into the spare buffers
+ * (the current states are unchanged). threads/blocks may be NULL.
+ * Synchronises. */
+int lbm_batch_autotune(lbm_batch *b, int *threads, int *blocks);
+
+/* One DA cycle of every experiment i: forecast nsteps (one persistent
+ * launch for all), observe (u, v) at npts[i] points (ix[i], iy[i]) with
+ * values yo_u[i], yo_v[i] and errors sigma[2i], sigma[2i+1], and the LETKF
+ * analysis with d_cut[i], beta[i]. With use_graph, once a cycle has run
+ * uncaptured with the same positions, nsteps, d_cut and beta, the next call
+ * captures the whole cycle of all experiments in a CUDA graph and later
+ * calls replay it, staging only the new observed values through pinned
+ * memory (nsteps must be even so the state buffers return to their roles).
+ * A change of plan falls back to an uncaptured cycle. Asynchronous except
+ * for waiting on the previous cycle's copies; errors surface at
+ * lbm_batch_sync. Host arrays are read before the call returns. */
+int lbm_batch_cycle(lbm_batch *b, int nsteps, const int *npts, const int *const *ix,
+                    const int *const *iy, const double *const *yo_u, const double *const *yo_v,
+                    const double *sigma, const double *d_cut, const double *beta, int use_graph);
+
+/* Wait for the batch's work; reports a timed-out grid barrier, then each
+ * context's deferred status (as lbm_sync). */
+int lbm_batch_sync(lbm_batch *b);
+const char *lbm_batch_last_error(const lbm_batch *b);
+void lbm_batch_destroy(lbm_batch *b);
+
 #ifdef __cplusplus
 }
 #endif

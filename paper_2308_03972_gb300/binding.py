@@ -62,6 +62,13 @@ SIGNATURES = {
     "lbm_sync": (_I, [_P]),
     "lbm_last_error": (ctypes.c_char_p, [_P]),
     "lbm_destroy": (None, [_P]),
+    "lbm_batch_create": (_I, [_P, _I, ctypes.POINTER(_P)]),
+    "lbm_batch_forecast": (_I, [_P, _I]),
+    "lbm_batch_autotune": (_I, [_P, _P, _P]),
+    "lbm_batch_cycle": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _P, _P, _I]),
+    "lbm_batch_sync": (_I, [_P]),
+    "lbm_batch_last_error": (ctypes.c_char_p, [_P]),
+    "lbm_batch_destroy": (None, [_P]),
     "letkf_analyze_noalloc": (_I, [_P, _I, _I, _I, _I, _P, _P, _P, _P, _D, _D, _D, _D, _P]),
 }
 
@@ -425,3 +432,62 @@ class Ensemble:
             self.close()
         except Exception:
             pass
+
+
+def _bcheck(b, status):
+    if status != LBM_OK:
+        msg = load().lbm_batch_last_error(b)
+        raise LbmError(status, msg.decode() if msg else "")
+
+
+class Batch:
+    """Independent experiments (Ensemble objects sharing one stream and
+    precision) advanced together: one persistent launch per forecast, and a
+    captured CUDA graph per DA cycle."""
+
+    def __init__(self, ensembles):
+        self.ens = list(ensembles)
+        arr = (_P * len(self.ens))(*[e.ctx for e in self.ens])
+        out = _P()
+        _bcheck(None, load().lbm_batch_create(arr, len(self.ens), ctypes.byref(out)))
+        self.b = out
+
+    def forecast(self, nsteps):
+        _bcheck(self.b, load().lbm_batch_forecast(self.b, int(nsteps)))
+
+    def autotune(self):
+        t, n = ctypes.c_int(0), ctypes.c_int(0)
+        _bcheck(self.b, load().lbm_batch_autotune(self.b, ctypes.byref(t), ctypes.byref(n)))
+        return t.value, n.value
+
+    def cycle(self, nsteps, obs, d_cut, beta, use_graph=True):
+        """obs: per experiment (ix, iy, yo_u, yo_v, sigma_u, sigma_v)."""
+        n = len(self.ens)
+        keep = []
+
+        def arrs(i, dt):
+            a = [np.ascontiguousarray(o[i], dtype=dt) for o in obs]
+            keep.extend(a)
+            return (_P * n)(*[x.ctypes.data_as(_P) for x in a])
+        npts = np.array([len(o[0]) for o in obs], dtype=np.int32)
+        sig = np.array([[o[4], o[5]] for o in obs], dtype=np.float64).ravel()
+        dc = np.ascontiguousarray(d_cut, dtype=np.float64)
+        bt = np.ascontiguousarray(beta, dtype=np.float64)
+        p = lambda a: a.ctypes.data_as(_P)  # noqa: E731
+        _bcheck(self.b, load().lbm_batch_cycle(self.b, int(nsteps), p(npts), arrs(0, np.int32), arrs(1, np.int32),
+                                               arrs(2, np.float64), arrs(3, np.float64), p(sig), p(dc), p(bt),
+                                               1 if use_graph else 0))
+
+    def sync(self):
+        _bcheck(self.b, load().lbm_batch_sync(self.b))
+
+    def close(self):
+        if self.b:
+            load().lbm_batch_destroy(self.b)
+            self.b = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

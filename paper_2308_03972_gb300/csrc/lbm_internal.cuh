@@ -64,6 +64,26 @@ cudaError_t launch_lbm_step_f64(const double* fin, double* fout, const double* f
                                 const LbmParams& p, int* flags, cudaStream_t s);
 cudaError_t launch_lbm_step_f32(const float* gin, float* gout, const float* force,
                                 const LbmParams& p, int* flags, cudaStream_t s);
+// One experiment of a persistent multi-ensemble forecast: its state buffers
+// (f[cur] holds the current state), forcing, flag word, lattice, members,
+// parameters, members per work item V (1, 2 or 4; 4 means 2 in FP64) and
+// its range [offset, offset + items) of the global work-item index.
+struct MultiExp {
+    void* f[2];
+    const void* force;
+    int* flags;
+    int nx, ny, k, V, cur;
+    double tau0, cs18, mu;
+    long long offset, items;
+};
+constexpr int kMaxMultiExp = 64;
+// Cooperative launch of `blocks` x `threads` advancing every experiment
+// nsteps steps (ex_dev: device array). bar: two zeroed words (reset here);
+// status: set to 1 if a grid barrier timed out.
+cudaError_t launch_lbm_multi(const MultiExp* ex_dev, int nexp, long long total, int nsteps, int fp32,
+                             int blocks, int threads, unsigned* bar, int* status, cudaStream_t s);
+// Largest co-resident grid for the multi kernel (0 on error).
+int lbm_multi_max_blocks(int fp32, int threads);
 // Nudging toward f^eq of observations on a uniform lattice; obs = rho, u, v
 // fields [3][noy][nox] in device memory.
 cudaError_t launch_nudge(void* f, int fp32, int nx, int ny, int k, int nox, int noy,

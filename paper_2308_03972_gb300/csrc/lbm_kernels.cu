@@ -79,16 +79,14 @@ __device__ __forceinline__ bool collide(T (&f)[9], T Fix, T Fiy, T tau0, T cs18,
     return !(uu <= T(kUMax2)) || !(rho > T(0));
 }
 
+// One work item of a step: V consecutive members (group mv) of one cell,
+// item index t in [0, nx * ny * k / V). Collide, then push.
 template <typename T, int V, bool SHIFT>
-__global__ void __launch_bounds__(256) lbm_step_kernel(const T* __restrict__ fin,
-                                                       T* __restrict__ fout,
-                                                       const T* __restrict__ force, int nx,
-                                                       int ny, int k, T tau0, T cs18, T mu,
-                                                       int* __restrict__ flags) {
+__device__ __forceinline__ void step_item(const T* __restrict__ fin, T* __restrict__ fout,
+                                          const T* __restrict__ force, int nx, int ny, int k,
+                                          T tau0, T cs18, T mu, int* __restrict__ flags,
+                                          long long t) {
     const int kv = k / V;
-    const long long total = (long long)nx * ny * kv;
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= total) return;
     const int mv = (int)(t % kv);
     const long long cell = t / kv;
     const int x = (int)(cell % nx);
@@ -130,6 +128,94 @@ __global__ void __launch_bounds__(256) lbm_step_kernel(const T* __restrict__ fin
     Vec<T, V>::st(dst(6, xm, ym), f[6]);
     Vec<T, V>::st(dst(7, xp, ym), f[7]);
     Vec<T, V>::st(dst(8, xm, yp), f[8]);
+}
+
+template <typename T, int V, bool SHIFT>
+__global__ void __launch_bounds__(256) lbm_step_kernel(const T* __restrict__ fin,
+                                                       T* __restrict__ fout,
+                                                       const T* __restrict__ force, int nx,
+                                                       int ny, int k, T tau0, T cs18, T mu,
+                                                       int* __restrict__ flags) {
+    const long long total = (long long)nx * ny * (k / V);
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    step_item<T, V, SHIFT>(fin, fout, force, nx, ny, k, tau0, cs18, mu, flags, t);
+}
+
+// ---- Many independent ensembles in one persistent launch -------------------
+// Every experiment (its own lattice, members, parameters and state buffers)
+// contributes nx * ny * k / V work items per step; a cooperative grid strides
+// over the items of all experiments, then meets at a grid barrier before the
+// next step. The barrier spins at most kBarrierSpins rounds (with a short
+// sleep): on timeout the block records it in status and the kernel stops.
+constexpr long long kBarrierSpins = 20000000;  // ~2-4 s of 100 ns sleeps
+
+template <typename T>
+__device__ __forceinline__ void multi_item(const MultiExp& e, int step, long long t) {
+    const int b = (e.cur + step) & 1;
+    const T* fin = reinterpret_cast<const T*>(e.f[b]);
+    T* fout = reinterpret_cast<T*>(e.f[b ^ 1]);
+    const T* force = reinterpret_cast<const T*>(e.force);
+    constexpr bool SHIFT = sizeof(T) == 4;
+    if (e.V == 4)
+        step_item<T, sizeof(T) == 4 ? 4 : 2, SHIFT>(fin, fout, force, e.nx, e.ny, e.k, (T)e.tau0,
+                                                    (T)e.cs18, (T)e.mu, e.flags, t);
+    else if (e.V == 2)
+        step_item<T, 2, SHIFT>(fin, fout, force, e.nx, e.ny, e.k, (T)e.tau0, (T)e.cs18, (T)e.mu,
+                               e.flags, t);
+    else
+        step_item<T, 1, SHIFT>(fin, fout, force, e.nx, e.ny, e.k, (T)e.tau0, (T)e.cs18, (T)e.mu,
+                               e.flags, t);
+}
+
+// Sense-reversing grid barrier over gridDim.x blocks (count, gen in global
+// memory, both zero before the launch). Returns false on timeout.
+__device__ bool grid_barrier(unsigned* count, unsigned* gen, int* status) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        volatile unsigned* vg = gen;
+        const unsigned g = *vg;
+        __threadfence();
+        if (atomicAdd(count, 1u) == gridDim.x - 1) {
+            *count = 0u;
+            __threadfence();
+            atomicAdd(gen, 1u);
+        } else {
+            long long spins = 0;
+            while (*vg == g) {
+                if (++spins > kBarrierSpins) {
+                    atomicOr(status, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) lbm_multi_kernel(const MultiExp* __restrict__ ex, int nexp,
+                                                        long long total, int nsteps,
+                                                        unsigned* __restrict__ bar,
+                                                        int* __restrict__ status) {
+    __shared__ MultiExp se[kMaxMultiExp];
+    for (int i = threadIdx.x; i < nexp; i += blockDim.x) se[i] = ex[i];
+    __syncthreads();
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (int step = 0; step < nsteps; ++step) {
+        int e = 0;
+        for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += stride) {
+            while (t >= se[e].offset + se[e].items) ++e;  // items are in experiment order
+            multi_item<T>(se[e], step, t - se[e].offset);
+        }
+        if (step + 1 < nsteps && !grid_barrier(bar, bar + 1, status)) return;
+    }
 }
 
 // Nudging (arXiv 2308.03972, Section 3.1): f_a <- f_a + gamma (f^eq_a(rho^, u^, v^) - f_a)
@@ -318,6 +404,32 @@ cudaError_t launch_lbm_step_f32(const float* gin, float* gout, const float* forc
     if (p.k % 4 == 0) return launch_step_v<float, 4, true>(gin, gout, force, p, flags, s);
     if (p.k % 2 == 0) return launch_step_v<float, 2, true>(gin, gout, force, p, flags, s);
     return launch_step_v<float, 1, true>(gin, gout, force, p, flags, s);
+}
+
+cudaError_t launch_lbm_multi(const MultiExp* ex_dev, int nexp, long long total, int nsteps, int fp32,
+                             int blocks, int threads, unsigned* bar, int* status, cudaStream_t s) {
+    if (nexp < 1 || nexp > kMaxMultiExp || nsteps < 1 || blocks < 1) return cudaErrorInvalidValue;
+    void* args[] = {(void*)&ex_dev, (void*)&nexp, (void*)&total, (void*)&nsteps, (void*)&bar,
+                    (void*)&status};
+    cudaError_t e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    if (fp32)
+        return cudaLaunchCooperativeKernel((const void*)lbm_multi_kernel<float>, dim3(blocks),
+                                           dim3(threads), args, 0, s);
+    return cudaLaunchCooperativeKernel((const void*)lbm_multi_kernel<double>, dim3(blocks),
+                                       dim3(threads), args, 0, s);
+}
+
+int lbm_multi_max_blocks(int fp32, int threads) {
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    cudaError_t e = fp32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, lbm_multi_kernel<float>,
+                                                                         threads, 0)
+                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, lbm_multi_kernel<double>,
+                                                                         threads, 0);
+    if (e != cudaSuccess) return 0;
+    return per * sms;
 }
 
 cudaError_t launch_nudge(void* f, int fp32, int nx, int ny, int k, int nox, int noy,

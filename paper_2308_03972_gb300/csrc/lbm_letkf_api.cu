@@ -426,6 +426,68 @@ int misfit_impl(lbm_ctx* c, const lbm_window* win, const double* w, double* J, d
     return read_flags(c);
 }
 
+// Host part of an analysis: argument checks, the largest local problem of
+// the geometry (cached), scratch and the mixed path's second stream. No
+// device work is queued, so it may precede a stream capture.
+struct AnalysisPlan {
+    double d_cut = 0.0, beta = 0.0;
+    int nmax = 0, plmax = 0, prod = PROD_FP64;
+};
+
+int analyze_prepare(lbm_ctx* c, double d_cut, double beta, AnalysisPlan* plan) {
+    if (c->k < 2) return fail(c, LBM_EINVAL, "the analysis needs members >= 2");
+    if (!(d_cut > 0.0) || !std::isfinite(d_cut)) return fail(c, LBM_EINVAL, "d_cut must be > 0");
+    if (!(beta > 0.0) || !std::isfinite(beta)) return fail(c, LBM_EINVAL, "beta must be > 0");
+    const int nmax = largest_local_problem(c, d_cut);
+    const int plmax = c->geo_pmax;
+    // The reduced-precision Gram pass serves ensemble-space points only.
+    const int prod = c->geo_any_ens ? c->prod : PROD_FP64;
+    const size_t scratch = analyze_scratch_bytes(c->nx, c->ny, is_fp32(c), plmax, nmax, c->k, prod);
+    if (scratch > c->ana_scratch_bytes) {
+        CK(c, cudaStreamSynchronize(c->stream), "synchronising");
+        cudaFree(c->ana_scratch);
+        c->ana_scratch = nullptr;
+        c->ana_scratch_bytes = 0;
+        CK(c, cudaMalloc(&c->ana_scratch, scratch), "allocating analysis scratch");
+        c->ana_scratch_bytes = scratch;
+    }
+    if (is_fp32(c) && !c->aux_ready) {
+        CK(c, cudaStreamCreateWithFlags(&c->aux.s2, cudaStreamNonBlocking), "creating stream");
+        CK(c, cudaEventCreateWithFlags(&c->aux.start, cudaEventDisableTiming), "creating event");
+        for (int b = 0; b < 2; ++b) {
+            CK(c, cudaEventCreateWithFlags(&c->aux.jac_done[b], cudaEventDisableTiming), "creating event");
+            CK(c, cudaEventCreateWithFlags(&c->aux.ref_done[b], cudaEventDisableTiming), "creating event");
+        }
+        c->aux_ready = true;
+    }
+    *plan = AnalysisPlan{d_cut, beta, nmax, plmax, prod};
+    return LBM_OK;
+}
+
+// Device part: the analysis kernels on the context stream (capturable).
+int analyze_launch(lbm_ctx* c, const AnalysisPlan& pl) {
+    ObsParams o{c->npts, c->ix, c->iy, c->dY, c->d, c->G, c->sigma_u, c->sigma_v, c->dY32,
+                c->nvar, c->sigma_r, pl.plmax};
+    CK(c, launch_analyze(c->f[c->cur], is_fp32(c), c->nx, c->ny, c->k, o, pl.d_cut, pl.beta, pl.nmax,
+                         pl.prod, c->flags, c->ana_scratch, c->aux_ready ? &c->aux : nullptr, c->stream),
+       "launching analysis");
+    return LBM_OK;
+}
+
+// Observation step from a pinned host buffer of nvar * npts values, for
+// positions already on the device (set by an earlier observe_impl): the copy,
+// H and the Gram, all on the context stream (capturable).
+int observe_from_pinned(lbm_ctx* c, const double* h_yo) {
+    const int nobs = c->nvar * c->npts;
+    CK(c, cudaMemcpyAsync(c->yo, h_yo, (size_t)nobs * sizeof(double), cudaMemcpyHostToDevice, c->stream),
+       "copy observations");
+    CK(c, launch_observe(c->f[c->cur], is_fp32(c), c->nx, c->ny, c->k, c->npts, c->nvar, c->ix, c->iy,
+                         c->yo, c->dY, c->d, c->stream),
+       "launching observation operator");
+    CK(c, launch_obs_gram(c->dY, nobs, c->k, c->G, c->stream), "launching observation Gram");
+    return LBM_OK;
+}
+
 }  // namespace
 
 namespace lbmgpu {
@@ -681,37 +743,12 @@ int letkf_observe_rho(lbm_ctx* c, int npts, const int* ix, const int* iy, const 
 
 int letkf_analyze(lbm_ctx* c, double d_cut, double beta) {
     if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
-    if (c->k < 2) return fail(c, LBM_EINVAL, "the analysis needs members >= 2");
-    if (!(d_cut > 0.0) || !std::isfinite(d_cut)) return fail(c, LBM_EINVAL, "d_cut must be > 0");
-    if (!(beta > 0.0) || !std::isfinite(beta)) return fail(c, LBM_EINVAL, "beta must be > 0");
     if (!c->observed) return fail(c, LBM_EINVAL, "letkf_observe must precede letkf_analyze");
-    const int nmax = largest_local_problem(c, d_cut);
-    const int plmax = c->geo_pmax;
-    // The reduced-precision Gram pass serves ensemble-space points only.
-    const int prod = c->geo_any_ens ? c->prod : PROD_FP64;
-    const size_t scratch = analyze_scratch_bytes(c->nx, c->ny, is_fp32(c), plmax, nmax, c->k, prod);
-    if (scratch > c->ana_scratch_bytes) {
-        CK(c, cudaStreamSynchronize(c->stream), "synchronising");
-        cudaFree(c->ana_scratch);
-        c->ana_scratch = nullptr;
-        c->ana_scratch_bytes = 0;
-        CK(c, cudaMalloc(&c->ana_scratch, scratch), "allocating analysis scratch");
-        c->ana_scratch_bytes = scratch;
-    }
-    if (is_fp32(c) && !c->aux_ready) {
-        CK(c, cudaStreamCreateWithFlags(&c->aux.s2, cudaStreamNonBlocking), "creating stream");
-        CK(c, cudaEventCreateWithFlags(&c->aux.start, cudaEventDisableTiming), "creating event");
-        for (int b = 0; b < 2; ++b) {
-            CK(c, cudaEventCreateWithFlags(&c->aux.jac_done[b], cudaEventDisableTiming), "creating event");
-            CK(c, cudaEventCreateWithFlags(&c->aux.ref_done[b], cudaEventDisableTiming), "creating event");
-        }
-        c->aux_ready = true;
-    }
-    ObsParams o{c->npts, c->ix, c->iy, c->dY, c->d, c->G, c->sigma_u, c->sigma_v, c->dY32,
-                c->nvar, c->sigma_r, plmax};
-    CK(c, launch_analyze(c->f[c->cur], is_fp32(c), c->nx, c->ny, c->k, o, d_cut, beta, nmax, prod,
-                         c->flags, c->ana_scratch, c->aux_ready ? &c->aux : nullptr, c->stream),
-       "launching analysis");
+    AnalysisPlan plan;
+    int st = analyze_prepare(c, d_cut, beta, &plan);
+    if (st) return st;
+    st = analyze_launch(c, plan);
+    if (st) return st;
     c->observed = false;
     return LBM_OK;
 }
@@ -825,6 +862,354 @@ void lbm_destroy(lbm_ctx* c) {
     free_obs(c);
     if (c->obs_copied) cudaEventDestroy(c->obs_copied);
     delete c;
+}
+
+}  // extern "C"
+
+// ---- Batches of independent experiments ------------------------------------
+
+struct lbm_batch {
+    std::vector<lbm_ctx*> ctx;
+    cudaStream_t stream = nullptr;
+    int fp32 = 0;
+    MultiExp* ex_dev = nullptr;   // device copy of the experiment table
+    std::vector<MultiExp> ex;
+    long long total = 0;
+    unsigned* bar = nullptr;      // grid barrier words
+    int* status = nullptr;        // barrier timeout flag (device)
+    int threads = 256, blocks = 0;
+    bool tuned = false;
+    // Cycle state: fixed observation positions per experiment, pinned
+    // staging of the observed values, the captured cycle graph.
+    std::vector<double*> h_yo;
+    std::vector<int> npts;
+    std::vector<std::vector<int>> pos;
+    int cycles = 0;
+    int graph_steps = -1;
+    std::vector<double> graph_dcut, graph_beta, graph_sigma;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t done = nullptr;
+    cudaStream_t cap = nullptr;   // capture stream (the shared stream may be the legacy one)
+    bool launched = false;
+    char err[512] = {0};
+};
+
+namespace {
+
+int bfail(lbm_batch* b, int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(b ? b->err : g_init_err, sizeof b->err, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define BK(b, call, what)                                                       \
+    do {                                                                        \
+        cudaError_t e_ = (call);                                                \
+        if (e_ != cudaSuccess)                                                  \
+            return bfail((b), e_ == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, "%s: %s", \
+                         what, cudaGetErrorString(e_));                         \
+    } while (0)
+
+// Experiment table from the contexts' current buffers and parameters.
+void batch_table(lbm_batch* b) {
+    b->ex.clear();
+    long long off = 0;
+    for (lbm_ctx* c : b->ctx) {
+        MultiExp e{};
+        e.f[0] = c->f[0];
+        e.f[1] = c->f[1];
+        e.force = c->force;
+        e.flags = c->flags;
+        e.nx = c->nx;
+        e.ny = c->ny;
+        e.k = c->k;
+        e.V = b->fp32 ? (c->k % 4 == 0 ? 4 : (c->k % 2 == 0 ? 2 : 1)) : (c->k % 2 == 0 ? 2 : 1);
+        e.cur = c->cur;
+        e.tau0 = c->tau0;
+        e.cs18 = 18.0 * c->cs * c->cs;
+        e.mu = c->mu;
+        e.offset = off;
+        e.items = (long long)c->nx * c->ny * (c->k / e.V);
+        off += e.items;
+        b->ex.push_back(e);
+    }
+    b->total = off;
+}
+
+int batch_forecast_impl(lbm_batch* b, int nsteps) {
+    batch_table(b);
+    BK(b, cudaMemcpyAsync(b->ex_dev, b->ex.data(), b->ex.size() * sizeof(MultiExp), cudaMemcpyHostToDevice,
+                          b->stream),
+       "copy experiment table");
+    BK(b, launch_lbm_multi(b->ex_dev, (int)b->ex.size(), b->total, nsteps, b->fp32, b->blocks, b->threads,
+                           b->bar, b->status, b->stream),
+       "launching persistent forecast");
+    for (lbm_ctx* c : b->ctx) {
+        c->cur = (c->cur + nsteps) & 1;
+        c->observed = false;
+    }
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_batch_create(lbm_ctx* const* ctxs, int n, lbm_batch** out) {
+    if (!out) return bfail(nullptr, LBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!ctxs || n < 1 || n > kMaxMultiExp) return bfail(nullptr, LBM_EINVAL, "need 1..%d contexts", kMaxMultiExp);
+    for (int i = 0; i < n; ++i) {
+        if (!ctxs[i]) return bfail(nullptr, LBM_EINVAL, "context %d is NULL", i);
+        if (ctxs[i]->stream != ctxs[0]->stream)
+            return bfail(nullptr, LBM_EINVAL, "the contexts of a batch must share one stream");
+        if (is_fp32(ctxs[i]) != is_fp32(ctxs[0]))
+            return bfail(nullptr, LBM_EINVAL, "the contexts of a batch must share one precision");
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == ctxs[i]) return bfail(nullptr, LBM_EINVAL, "context %d appears twice", i);
+    }
+    lbm_batch* b = new (std::nothrow) lbm_batch;
+    if (!b) return bfail(nullptr, LBM_ENOMEM, "out of host memory");
+    b->ctx.assign(ctxs, ctxs + n);
+    b->stream = ctxs[0]->stream;
+    b->fp32 = is_fp32(ctxs[0]);
+    auto bail = [&](int code) {
+        lbm_batch_destroy(b);
+        return code;
+    };
+    cudaError_t e = cudaMalloc(&b->ex_dev, kMaxMultiExp * sizeof(MultiExp));
+    if (e == cudaSuccess) e = cudaMalloc(&b->bar, 4 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(&b->status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->status, 0, sizeof(int), b->stream);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
+    if (e != cudaSuccess)
+        return bail(bfail(nullptr, LBM_ECUDA, "creating batch: %s", cudaGetErrorString(e)));
+    b->blocks = lbm_multi_max_blocks(b->fp32, b->threads);
+    if (b->blocks < 1) return bail(bfail(nullptr, LBM_ECUDA, "no co-resident grid for the persistent kernel"));
+    b->h_yo.assign(n, nullptr);
+    b->npts.assign(n, 0);
+    b->pos.assign(n, std::vector<int>());
+    *out = b;
+    return LBM_OK;
+}
+
+int lbm_batch_forecast(lbm_batch* b, int nsteps) {
+    if (!b) return bfail(nullptr, LBM_EINVAL, "batch is NULL");
+    if (nsteps < 0) return bfail(b, LBM_EINVAL, "nsteps must be >= 0");
+    if (nsteps == 0) return LBM_OK;
+    return batch_forecast_impl(b, nsteps);
+}
+
+int lbm_batch_autotune(lbm_batch* b, int* threads, int* blocks) {
+    if (!b) return bfail(nullptr, LBM_EINVAL, "batch is NULL");
+    // Candidates: block size x co-resident blocks per SM, each timed on one
+    // step from the current states into the spare buffers (the current
+    // states are not changed), best of three runs.
+    int dev = 0, sms = 0;
+    BK(b, cudaGetDevice(&dev), "querying device");
+    BK(b, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "querying SMs");
+    batch_table(b);
+    BK(b, cudaMemcpyAsync(b->ex_dev, b->ex.data(), b->ex.size() * sizeof(MultiExp), cudaMemcpyHostToDevice,
+                          b->stream),
+       "copy experiment table");
+    cudaEvent_t t0, t1;
+    BK(b, cudaEventCreate(&t0), "creating event");
+    BK(b, cudaEventCreate(&t1), "creating event");
+    float best = 1e30f;
+    int bt = b->threads, bb = b->blocks;
+    const int cand_t[] = {128, 256, 512};  // the kernel's launch bound is 512
+    for (int th : cand_t) {
+        const int maxb = lbm_multi_max_blocks(b->fp32, th);
+        if (maxb < 1) continue;
+        const int per = maxb / sms;
+        for (int q = 1; q <= per; ++q) {
+            const int nb = q * sms;
+            float tbest = 1e30f;
+            for (int r = 0; r < 3; ++r) {
+                cudaEventRecord(t0, b->stream);
+                cudaError_t e = launch_lbm_multi(b->ex_dev, (int)b->ex.size(), b->total, 1, b->fp32, nb, th,
+                                                 b->bar, b->status, b->stream);
+                cudaEventRecord(t1, b->stream);
+                if (e != cudaSuccess || cudaEventSynchronize(t1) != cudaSuccess) {
+                    cudaEventDestroy(t0);
+                    cudaEventDestroy(t1);
+                    return bfail(b, LBM_ECUDA, "autotune launch: %s", cudaGetErrorString(e));
+                }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, t0, t1);
+                if (ms < tbest) tbest = ms;
+            }
+            if (tbest < best) {
+                best = tbest;
+                bt = th;
+                bb = nb;
+            }
+        }
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    b->threads = bt;
+    b->blocks = bb;
+    b->tuned = true;
+    if (threads) *threads = bt;
+    if (blocks) *blocks = bb;
+    return LBM_OK;
+}
+
+int lbm_batch_cycle(lbm_batch* b, int nsteps, const int* npts, const int* const* ix, const int* const* iy,
+                    const double* const* yo_u, const double* const* yo_v, const double* sigma,
+                    const double* d_cut, const double* beta, int use_graph) {
+    if (!b) return bfail(nullptr, LBM_EINVAL, "batch is NULL");
+    const int n = (int)b->ctx.size();
+    if (nsteps < 1) return bfail(b, LBM_EINVAL, "nsteps must be >= 1");
+    if (!npts || !ix || !iy || !yo_u || !yo_v || !sigma || !d_cut || !beta)
+        return bfail(b, LBM_EINVAL, "NULL argument");
+    if (use_graph && (nsteps & 1))
+        return bfail(b, LBM_EINVAL, "a captured cycle needs an even nsteps (the state buffers alternate)");
+    for (int i = 0; i < n; ++i) {
+        if (npts[i] < 1 || !ix[i] || !iy[i] || !yo_u[i] || !yo_v[i])
+            return bfail(b, LBM_EINVAL, "experiment %d: missing observations", i);
+        for (int j = 0; j < npts[i]; ++j)
+            if (!std::isfinite(yo_u[i][j]) || !std::isfinite(yo_v[i][j]))
+                return bfail(b, LBM_EINVAL, "experiment %d: observation %d is not finite", i, j);
+    }
+    const bool same_geometry = b->cycles > 0 && [&] {
+        for (int i = 0; i < n; ++i) {
+            if (npts[i] != b->npts[i]) return false;
+            for (int j = 0; j < npts[i]; ++j)
+                if (b->pos[i][j] != ix[i][j] || b->pos[i][npts[i] + j] != iy[i][j]) return false;
+        }
+        return true;
+    }();
+    const bool same_plan = same_geometry && b->graph_steps == nsteps &&
+                           std::equal(d_cut, d_cut + n, b->graph_dcut.begin()) &&
+                           std::equal(beta, beta + n, b->graph_beta.begin()) &&
+                           std::equal(sigma, sigma + 2 * n, b->graph_sigma.begin());
+    // The pinned staging may still be read by the previous graph launch.
+    if (b->launched) BK(b, cudaEventSynchronize(b->done), "waiting for the previous cycle");
+    if (!use_graph || !same_plan) {
+        // Uncaptured cycle (also the first one, which sets positions, caches
+        // the local-problem bounds and allocates scratch).
+        if (b->exec) {
+            cudaGraphExecDestroy(b->exec);
+            b->exec = nullptr;
+        }
+        if (b->graph) {
+            cudaGraphDestroy(b->graph);
+            b->graph = nullptr;
+        }
+        int st = batch_forecast_impl(b, nsteps);
+        if (st) return st;
+        for (int i = 0; i < n; ++i) {
+            lbm_ctx* c = b->ctx[i];
+            st = letkf_observe(c, npts[i], ix[i], iy[i], yo_u[i], yo_v[i], sigma[2 * i], sigma[2 * i + 1]);
+            if (st) return bfail(b, st, "experiment %d: %s", i, c->err);
+            st = letkf_analyze(c, d_cut[i], beta[i]);
+            if (st) return bfail(b, st, "experiment %d: %s", i, c->err);
+            if (npts[i] > b->npts[i]) {
+                if (b->h_yo[i]) cudaFreeHost(b->h_yo[i]);
+                b->h_yo[i] = nullptr;
+                BK(b, cudaMallocHost(&b->h_yo[i], 2 * (size_t)npts[i] * sizeof(double)), "allocating staging");
+            }
+            b->npts[i] = npts[i];
+            b->pos[i].assign(ix[i], ix[i] + npts[i]);
+            b->pos[i].insert(b->pos[i].end(), iy[i], iy[i] + npts[i]);
+        }
+        b->graph_steps = nsteps;
+        b->graph_dcut.assign(d_cut, d_cut + n);
+        b->graph_beta.assign(beta, beta + n);
+        b->graph_sigma.assign(sigma, sigma + 2 * n);
+        ++b->cycles;
+        BK(b, cudaEventRecord(b->done, b->stream), "recording event");
+        b->launched = true;
+        return LBM_OK;
+    }
+    // Captured cycle: stage this cycle's values, then replay (capturing the
+    // graph the first time with the plan of the previous, uncaptured cycle).
+    for (int i = 0; i < n; ++i) {
+        for (int j = 0; j < npts[i]; ++j) {
+            b->h_yo[i][2 * j] = yo_u[i][j];
+            b->h_yo[i][2 * j + 1] = yo_v[i][j];
+        }
+    }
+    if (!b->exec) {
+        std::vector<AnalysisPlan> plans(n);
+        for (int i = 0; i < n; ++i) {
+            lbm_ctx* c = b->ctx[i];
+            int st = analyze_prepare(c, d_cut[i], beta[i], &plans[i]);
+            if (st) return bfail(b, st, "experiment %d: %s", i, c->err);
+        }
+        batch_table(b);
+        BK(b, cudaMemcpyAsync(b->ex_dev, b->ex.data(), b->ex.size() * sizeof(MultiExp),
+                              cudaMemcpyHostToDevice, b->stream),
+           "copy experiment table");
+        BK(b, cudaStreamSynchronize(b->stream), "synchronising");
+        // Capture on a stream of our own (the shared stream may be the
+        // legacy default stream, which cannot be captured): the contexts
+        // queue on it while the capture lasts.
+        if (!b->cap) BK(b, cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking), "creating stream");
+        const cudaStream_t shared = b->stream;
+        for (lbm_ctx* c : b->ctx) c->stream = b->cap;
+        BK(b, cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal), "beginning capture");
+        cudaError_t e = launch_lbm_multi(b->ex_dev, n, b->total, nsteps, b->fp32, b->blocks, b->threads, b->bar,
+                                         b->status, b->cap);
+        int st = e == cudaSuccess ? LBM_OK : LBM_ECUDA;
+        for (int i = 0; i < n && st == LBM_OK; ++i) {
+            st = observe_from_pinned(b->ctx[i], b->h_yo[i]);
+            if (st == LBM_OK) st = analyze_launch(b->ctx[i], plans[i]);
+        }
+        cudaGraph_t g = nullptr;
+        const cudaError_t ee = cudaStreamEndCapture(b->cap, &g);
+        for (lbm_ctx* c : b->ctx) c->stream = shared;
+        if (st != LBM_OK || e != cudaSuccess || ee != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return bfail(b, LBM_ECUDA, "capturing the cycle: %s",
+                         cudaGetErrorString(e != cudaSuccess ? e : (ee != cudaSuccess ? ee : cudaErrorUnknown)));
+        }
+        b->graph = g;
+        BK(b, cudaGraphInstantiate(&b->exec, b->graph, 0), "instantiating the cycle graph");
+    }
+    BK(b, cudaGraphLaunch(b->exec, b->stream), "launching the cycle graph");
+    BK(b, cudaEventRecord(b->done, b->stream), "recording event");
+    b->launched = true;
+    ++b->cycles;
+    return LBM_OK;
+}
+
+int lbm_batch_sync(lbm_batch* b) {
+    if (!b) return bfail(nullptr, LBM_EINVAL, "batch is NULL");
+    BK(b, cudaStreamSynchronize(b->stream), "synchronising");
+    int h = 0;
+    BK(b, cudaMemcpy(&h, b->status, sizeof(int), cudaMemcpyDeviceToHost), "reading barrier status");
+    if (h) {
+        cudaMemset(b->status, 0, sizeof(int));
+        return bfail(b, LBM_ECUDA, "a grid barrier of the persistent forecast timed out");
+    }
+    for (size_t i = 0; i < b->ctx.size(); ++i) {
+        const int st = lbm_sync(b->ctx[i]);
+        if (st) return bfail(b, st, "experiment %zu: %s", i, b->ctx[i]->err);
+    }
+    return LBM_OK;
+}
+
+const char* lbm_batch_last_error(const lbm_batch* b) { return b ? b->err : g_init_err; }
+
+void lbm_batch_destroy(lbm_batch* b) {
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->done) cudaEventDestroy(b->done);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    for (double* p : b->h_yo)
+        if (p) cudaFreeHost(p);
+    cudaFree(b->ex_dev);
+    cudaFree(b->bar);
+    cudaFree(b->status);
+    delete b;
 }
 
 }  // extern "C"

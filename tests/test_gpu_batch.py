@@ -1,0 +1,164 @@
+"""Batches of independent experiments (lbm_batch_*): one persistent
+cooperative launch advancing uneven ensembles, the launch-shape autotuner,
+and DA cycles captured in a CUDA graph. Each is compared with the same
+experiments run one call at a time through the single-context ABI (same
+kernels, so bit-identical), and one experiment with the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2308_03972_gb300 import inputs
+from _helpers import TOL_FP64, U_RMS, norm_rel, turbulent_state
+
+pytestmark = pytest.mark.gpu
+TAU0, CS, MU = 0.55, 0.2, 6.16e-7
+SIGMA = 0.1 * U_RMS
+# Uneven experiments: lattice, members (k = 5 and 6 exercise 1 and 2 members
+# per work item), observation lattice and radius.
+EXPS = [(32, 24, 8, 4, 4, 6.0), (48, 40, 12, 6, 5, 9.0), (20, 20, 5, 4, 4, 5.0), (40, 32, 6, 5, 4, 7.0)]
+
+
+def _states(precision_seed=0):
+    out = []
+    for i, (nx, ny, k, _, _, _) in enumerate(EXPS):
+        f = turbulent_state(oracle, nx, ny, k, seed=10 + i + precision_seed, pert=0.2)
+        force = inputs.forcing_field(nx, ny, seed=3 + i, amp=3.5e-6)
+        out.append((f, force))
+    return out
+
+
+def _ensembles(gpu, prec, states):
+    return [gpu.Ensemble(nx, ny, k, TAU0, CS, MU, prec, f0=f, force=force)
+            for (nx, ny, k, _, _, _), (f, force) in zip(EXPS, states)]
+
+
+def _obs(cycle):
+    obs = []
+    for i, (nx, ny, _, nox, noy, _) in enumerate(EXPS):
+        ix, iy = inputs.uniform_obs_points(nx, ny, nox, noy)
+        tu, tv = inputs.random_velocity(nx, ny, 200 + i, U_RMS)
+        nu, nv = inputs.obs_noise(4, cycle, len(ix))
+        obs.append((ix, iy, tu[iy, ix] + SIGMA * nu, tv[iy, ix] + SIGMA * nv, SIGMA, SIGMA))
+    return obs
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_persistent_forecast_equals_single_context_forecasts(gpu, prec):
+    p = gpu.LBM_FP64 if prec == "fp64" else gpu.LBM_MIXED
+    states = _states()
+    ref = []
+    for e in _ensembles(gpu, p, states):
+        e.forecast(7)
+        ref.append(e.get_f())
+        e.close()
+    ens = _ensembles(gpu, p, states)
+    with gpu.Batch(ens) as b:
+        b.forecast(3)
+        b.forecast(4)
+        b.sync()
+    for e, r in zip(ens, ref):
+        assert np.array_equal(e.get_f(), r)
+        e.close()
+
+
+def test_autotuned_shape_gives_the_same_forecast(gpu):
+    states = _states()
+    ens = _ensembles(gpu, gpu.LBM_MIXED, states)
+    before = [e.get_f() for e in ens]
+    with gpu.Batch(ens) as b:
+        threads, blocks = b.autotune()
+        assert threads in (128, 256, 512) and blocks >= 1
+        for e, f0 in zip(ens, before):
+            assert np.array_equal(e.get_f(), f0)  # tuning leaves the states alone
+        b.forecast(5)
+        b.sync()
+    ref = _ensembles(gpu, gpu.LBM_MIXED, states)
+    for e, r in zip(ens, ref):
+        r.forecast(5)
+        assert np.array_equal(e.get_f(), r.get_f())
+        e.close()
+        r.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_graph_cycles_equal_single_context_cycles(gpu, prec):
+    p = gpu.LBM_FP64 if prec == "fp64" else gpu.LBM_MIXED
+    states = _states()
+    d_cut = [e[5] for e in EXPS]
+    ncycles = 4
+    ref = _ensembles(gpu, p, states)
+    for c in range(1, ncycles + 1):
+        for e, (ix, iy, yu, yv, su, sv), dc in zip(ref, _obs(c), d_cut):
+            e.forecast(10)
+            e.observe(ix, iy, yu, yv, su, sv)
+            e.analyze(dc, 1.05)
+    ens = _ensembles(gpu, p, states)
+    with gpu.Batch(ens) as b:
+        for c in range(1, ncycles + 1):
+            b.cycle(10, _obs(c), d_cut, [1.05] * len(EXPS), use_graph=True)
+        b.sync()
+    for e, r in zip(ens, ref):
+        assert np.array_equal(e.get_f(), r.get_f())
+        e.close()
+        r.close()
+
+
+def test_graph_cycle_of_one_experiment_matches_oracle(gpu):
+    nx, ny, k, nox, noy, d_cut = EXPS[0]
+    f, force = _states()[0]
+    ix, iy = inputs.uniform_obs_points(nx, ny, nox, noy)
+    ref = f
+    e = gpu.Ensemble(nx, ny, k, TAU0, CS, MU, gpu.LBM_FP64, f0=f, force=force)
+    with gpu.Batch([e]) as b:
+        for c in range(1, 4):
+            o = _obs(c)[0]
+            ref = oracle.lbm_run(ref, force, TAU0, CS, MU, 10)
+            ref = oracle.letkf_analyze(ref, ix, iy, o[2], o[3], SIGMA, SIGMA, d_cut, 1.05)
+            b.cycle(10, [o], [d_cut], [1.05], use_graph=True)
+        b.sync()
+    assert norm_rel(e.get_f(), ref) <= TOL_FP64
+    e.close()
+
+
+def test_changed_plan_falls_back_and_still_matches(gpu):
+    states = _states()
+    d1 = [e[5] for e in EXPS]
+    d2 = [x + 1.0 for x in d1]
+    plan = [(1, d1), (2, d1), (3, d2), (4, d2), (5, d1)]
+    ref = _ensembles(gpu, gpu.LBM_MIXED, states)
+    for c, dc in plan:
+        for e, (ix, iy, yu, yv, su, sv), d in zip(ref, _obs(c), dc):
+            e.forecast(10)
+            e.observe(ix, iy, yu, yv, su, sv)
+            e.analyze(d, 1.05)
+    ens = _ensembles(gpu, gpu.LBM_MIXED, states)
+    with gpu.Batch(ens) as b:
+        for c, dc in plan:
+            b.cycle(10, _obs(c), dc, [1.05] * len(EXPS), use_graph=True)
+        b.sync()
+    for e, r in zip(ens, ref):
+        assert np.array_equal(e.get_f(), r.get_f())
+        e.close()
+        r.close()
+
+
+def test_batch_argument_errors(gpu):
+    import torch
+
+    states = _states()
+    a = _ensembles(gpu, gpu.LBM_MIXED, states[:1])
+    c = _ensembles(gpu, gpu.LBM_FP64, states[1:2])
+    with pytest.raises(gpu.LbmError):
+        gpu.Batch(a + c)  # mixed precisions
+    with pytest.raises(gpu.LbmError):
+        gpu.Batch(a + a)  # repeated context
+    s = torch.cuda.Stream()
+    nx, ny, k = EXPS[1][:3]
+    other = gpu.Ensemble(nx, ny, k, TAU0, CS, MU, gpu.LBM_MIXED, f0=states[1][0], stream=s.cuda_stream)
+    with pytest.raises(gpu.LbmError):
+        gpu.Batch(a + [other])  # different streams
+    with gpu.Batch(a) as b:
+        with pytest.raises(gpu.LbmError):
+            b.cycle(9, _obs(1)[:1], [6.0], [1.05], use_graph=True)  # odd nsteps with a graph
+    for e in a + c + [other]:
+        e.close()
