@@ -365,6 +365,93 @@ def measure_sweep(cfg, reps=2):
     return out
 
 
+# Twelve uneven DA experiments (lattice, members, observation lattice side,
+# localisation radius), all within local problems of n <= 64.
+BATCH_EXPERIMENTS = [
+    (128, 16, 8, 16.0), (128, 32, 16, 16.0), (128, 64, 8, 16.0), (128, 128, 8, 16.0),
+    (256, 16, 16, 32.0), (256, 32, 8, 32.0), (256, 64, 8, 32.0), (256, 128, 16, 16.0),
+    (512, 16, 32, 32.0), (512, 32, 16, 64.0), (512, 64, 8, 64.0), (512, 128, 32, 16.0),
+]
+
+
+def measure_batch(cfg, cycles=3):
+    """Twelve independent experiments (lattices 128^2..512^2, k 16..128,
+    observations 8^2..32^2, d_cut 16..64), binary32 LBM, s = 10: one batch
+    cycle = persistent forecast of all + observe + analysis of all. Timed
+    as a captured CUDA graph and as plain per-context calls."""
+    import torch
+
+    from paper_2308_03972_gb300 import binding, inputs
+
+    stream = torch.cuda.current_stream()
+    ens, obs_pos, truths, dcs = [], [], [], []
+    for i, (n, k, no, dc) in enumerate(BATCH_EXPERIMENTS):
+        force = inputs.forcing_field(n, n, cfg.seeds["forcing"] + i, cfg.force_amp, cfg.force_kmin, cfg.force_kmax)
+        eu, ev = inputs.ensemble_velocity(n, n, k, cfg.seeds["ensemble"] + i, cfg.u_rms, cfg.ens_pert)
+        e = binding.Ensemble(n, n, k, cfg.tau0, cfg.cs_smag, cfg.mu, binding.LBM_MIXED, force=force)
+        e.set_equilibrium(None, eu, ev)
+        ens.append(e)
+        obs_pos.append(inputs.uniform_obs_points(n, n, no, no))
+        truths.append(inputs.random_velocity(n, n, cfg.seeds["nature"] + i, cfg.u_rms))
+        dcs.append(dc)
+
+    def obs(c):
+        out = []
+        for (ix, iy), (tu, tv) in zip(obs_pos, truths):
+            nu, nv = inputs.obs_noise(cfg.seeds["noise"], c, len(ix))
+            out.append((ix, iy, tu[iy, ix] + cfg.sigma * nu, tv[iy, ix] + cfg.sigma * nv, cfg.sigma, cfg.sigma))
+        return out
+
+    betas = [cfg.beta] * len(ens)
+    res = {"experiments": [{"n": n, "k": k, "obs": "%dx%d" % (no, no), "d_cut": dc}
+                           for n, k, no, dc in BATCH_EXPERIMENTS]}
+    with binding.Batch(ens) as b:
+        res["autotuned_threads"], res["autotuned_blocks"] = b.autotune()
+        c = 1
+        for _ in range(2):  # uncaptured first cycle, then capture
+            b.cycle(10, obs(c), dcs, betas, use_graph=True)
+            c += 1
+        b.sync()
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(cycles):
+            b.cycle(10, obs(c), dcs, betas, use_graph=True)
+            c += 1
+        z.record(stream)
+        b.sync()
+        graph_ms = a.elapsed_time(z) / cycles
+        a.record(stream)
+        b.forecast(10)
+        z.record(stream)
+        b.sync()
+        res["persistent_forecast_ms"] = a.elapsed_time(z)
+    # The same cycles through the single-context calls.
+    a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(cycles):
+        for e, (ix, iy, yu, yv, su, sv), dc in zip(ens, obs(c), dcs):
+            e.forecast(10)
+            e.observe(ix, iy, yu, yv, su, sv)
+            e.analyze(dc, cfg.beta)
+        c += 1
+    z.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = a.elapsed_time(z) / cycles
+    a.record(stream)
+    for e in ens:
+        e.forecast(10)
+    z.record(stream)
+    torch.cuda.synchronize()
+    res["per_context_forecast_ms"] = a.elapsed_time(z)
+    for e in ens:
+        e.close()
+    upd = sum(n * n * k for n, k, _, _ in BATCH_EXPERIMENTS) * 10
+    res.update({"ms_per_batch_cycle_graph": graph_ms, "ms_per_batch_cycle_plain": plain_ms,
+                "experiment_cycles_per_s": len(BATCH_EXPERIMENTS) * 1000.0 / graph_ms,
+                "forecast_gbs_persistent": upd * 72 / (res["persistent_forecast_ms"] * 1e6)})
+    return res
+
+
 def oracle_cycle_sample(cfg, npoints=8192, lbm_steps=1, seed=0):
     """Time the FP64 oracle on a bounded sample of one cycle: lbm_steps LBM
     steps of the whole ensemble and the LETKF analysis at npoints grid
@@ -426,8 +513,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--window", type=int, default=200, help="adjoint window steps (--case adjoint)")
     ap.add_argument("--checkpoint", type=int, default=20, help="adjoint checkpoint spacing (--case adjoint)")
-    ap.add_argument("--case", default="all", choices=["all", "adjoint", "sweep"],
-                    help="adjoint: only the adjoint-window leg; sweep: precision-sweep timings")
+    ap.add_argument("--case", default="all", choices=["all", "adjoint", "sweep", "batch"],
+                    help="adjoint: only the adjoint-window leg; sweep: precision-sweep timings; "
+                         "batch: twelve uneven experiments")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -451,6 +539,11 @@ def main():
     binding.load()
 
     barrier_max = lambda x: reduce_max(x, world)  # noqa: E731
+    if args.case == "batch":
+        res = measure_batch(cfg)
+        if rank == 0:
+            print(json.dumps({"case": "batch", **res}))
+        return
     if args.case == "sweep":
         for row in measure_sweep(cfg):
             if rank == 0:
@@ -522,6 +615,7 @@ def main():
     adj = measure_adjoint(cfg)
     adj["peak_gbs"] = hbm
     adj["frac"] = adj["achieved_gbs"] / hbm
+    batch = measure_batch(cfg)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -541,7 +635,7 @@ def main():
                     "h2d_bytes_per_step": e2e["h2d_bytes_per_step"],
                     "d2h_bytes_per_step": e2e["d2h_bytes_per_step"]},
             "gpu_launches": args.steps * mixed["launches_per_cycle"],
-            "roofline": roof, "kernels": kern, "throughput": throughput, "adjoint": adj,
+            "roofline": roof, "kernels": kern, "throughput": throughput, "adjoint": adj, "batch": batch,
             "rmse": {"mixed": mixed["rmse"], "fp64": fp64["rmse"], "obs_noise_rms": cfg.sigma * np.sqrt(2)},
             "clocks": mixed["clocks"], "cpu_baseline": cpu,
         }
