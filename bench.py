@@ -513,9 +513,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--window", type=int, default=200, help="adjoint window steps (--case adjoint)")
     ap.add_argument("--checkpoint", type=int, default=20, help="adjoint checkpoint spacing (--case adjoint)")
-    ap.add_argument("--case", default="all", choices=["all", "adjoint", "sweep", "batch"],
-                    help="adjoint: only the adjoint-window leg; sweep: precision-sweep timings; "
-                         "batch: twelve uneven experiments")
+    ap.add_argument("--case", default="all", choices=["all", "cycle", "adjoint", "sweep", "batch"],
+                    help="cycle: the headline line without the adjoint and batch legs; adjoint: only "
+                         "the adjoint-window leg; sweep: precision-sweep timings; batch: twelve uneven "
+                         "experiments")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -612,10 +613,12 @@ def main():
                 "peak_source": "GB300 FP64 nominal 1.25 TFLOP/s (FMA microbenchmark: 1.20)",
                 "work": "algorithmic FP64 flops: 9 n^3 symmetric eigensolve + 2 per multiply-add of the products"}
 
-    adj = measure_adjoint(cfg)
-    adj["peak_gbs"] = hbm
-    adj["frac"] = adj["achieved_gbs"] / hbm
-    batch = measure_batch(cfg)
+    adj = batch = None
+    if args.case == "all":
+        adj = measure_adjoint(cfg)
+        adj["peak_gbs"] = hbm
+        adj["frac"] = adj["achieved_gbs"] / hbm
+        batch = measure_batch(cfg)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -603,13 +603,14 @@ __global__ void __launch_bounds__(32) analyze_fp64_kernel(double* __restrict__ f
 //      binary32, and a binary32 cyclic Jacobi held in registers (no shared
 //      memory, so many warps per SM hide its latency). The basis X goes to a
 //      chunk-sized scratch that stays in L2.
-//  (B) analyze_mixed_kernel: in FP64, re-orthonormalise X (Cholesky QR,
-//      Y = X L^{-T} with X^T X = L L^T), form the Rayleigh-Ritz matrix
-//      S = Y^T A Y, and evaluate f(A) = Y f(S) Y^T to first order in the
-//      off-diagonal of S (Daleckii-Krein: f(S)_ii = f(s_ii),
+//  (B) analyze_mixed_kernel: in FP64, form the Rayleigh-Ritz matrix
+//      S = X^T A X and the non-orthogonality E = X^T X - I of the binary32
+//      basis, correct S to first order in E (refine_rr), and evaluate
+//      f(A) = X (f(S') - E o (f_i + f_j)/2) X^T with f(S') to first order in
+//      the off-diagonal of S' (Daleckii-Krein: f(S)_ii = f(s_ii),
 //      f(S)_ij = s_ij f[s_ii, s_jj], divided differences in closed form).
-//      The error is second order in the off-diagonal of S (relative ~1e-13
-//      at these sizes). The transform products and the update run in
+//      The error is second order in E and in the off-diagonal of S
+//      (relative ~1e-11 at these sizes). The transform products and the update run in
 //      binary32 with binary32 accumulation.
 
 constexpr int kChunkCells = 8192;   // grid points per (A)+(B) pass (at most)
@@ -1165,9 +1166,10 @@ __global__ void __launch_bounds__(32) mixed_jacobi_smem_kernel(int nx, int ny, i
 struct MixSmem {
     double* A;     // [nm][ld] matrix (FP64), then S = Y^T A Y
     double* Y;     // [nm][ld] FP64 basis
-    double* W;     // [nm][ld] Y^T Y, its Cholesky factor, then A Y
+    double* W;     // [nm][ld] Y^T Y, then A Y
     float* F32;    // [nm][ld] f(S) in binary32, then T (inside W)
     float* Y32;    // [nm][ld] Y in binary32
+    float* E32;    // [nm][ld] E = Y^T Y - I (non-orthogonality of the basis)
     double* lsq;   // [nl]
     double* ldh;   // [nl]
     double* vb;    // [nm]
@@ -1190,7 +1192,7 @@ __host__ __device__ inline int mix_ld(int nm) { return (nm % 2 == 0) ? nm + 1 : 
 __host__ __device__ inline size_t mix_smem_bytes(int k, int nl, int nm) {
     const int ld = mix_ld(nm);
     const size_t d = 3 * (size_t)nm * ld + 2 * (size_t)nl + 4 * (size_t)nm;
-    const size_t f = (size_t)nm * ld + 9 * (size_t)k + 16 + 18 * (size_t)nm + 16 + 3 * (size_t)nm;
+    const size_t f = 2 * (size_t)nm * ld + 9 * (size_t)k + 16 + 18 * (size_t)nm + 16 + 3 * (size_t)nm;
     return d * sizeof(double) + ((f * sizeof(float) + 7) / 8) * 8 + (size_t)nl * sizeof(int);
 }
 
@@ -1219,6 +1221,8 @@ __device__ inline MixSmem carve_mix(unsigned char* raw, int k, int nl, int nm) {
     p += nm;
     float* q = reinterpret_cast<float*>(p);
     s.Y32 = q;
+    q += nm * ld;
+    s.E32 = q;
     q += nm * ld;
     s.dX = q;
     q += 9 * k;
@@ -1278,76 +1282,22 @@ __device__ void sym_product(const double* P, const double* Q, double* C, int n, 
     }
 }
 
-// FP64 refinement of the basis already in Y (columns = approximate
-// eigenvectors of the symmetric matrix A): Y <- Y L^{-T} with Y^T Y = L L^T,
-// then A <- S = Y^T A Y. n <= 64: lanes own rows/columns lane and lane + 32.
+// FP64 Rayleigh-Ritz refinement of the binary32 basis Y without
+// re-orthonormalising it. With E = Y^T Y - I (|E| ~ 1e-6), Y M^{-1/2}
+// (M = I + E) is orthonormal and M^{-1/2} = I - E/2 + O(E^2), so
+//   S' = M^{-1/2} (Y^T A Y) M^{-1/2} = S - (E S + S E)/2 + O(E^2)
+// and, S being diagonal up to O(1e-6), (E S + S E)/2 = E o (d_i + d_j)/2 up
+// to O(E |S_offdiag|): A <- S' costs O(n^2) instead of a Cholesky factor and
+// a triangular solve. The same first-order factor returns in the matrix
+// functions (F - E o (f_i + f_j)/2, applied by the caller). The neglected
+// terms are O(|E|^2) ~ 1e-11 relative. Leaves E in E32, diag(S) in d.
 template <bool WIDE>
-__device__ void refine_basis(double* A, double* Y, double* W, double* vinv, int n, int ld,
-                             int lane) {
+__device__ void refine_rr(double* A, const double* Y, double* W, float* E32, double* d, int n, int ld,
+                          int lane) {
     sym_product(Y, Y, W, n, ld, lane);  // W = Y^T Y
     __syncwarp();
-    // Cholesky factor of Y^T Y (close to I), lower triangle of W. Every lane
-    // forms its rows' candidates for column j in the same loop, so the warp
-    // does not diverge; the diagonal comes from the owning lane by a shuffle.
-    const int r0 = lane, r1 = lane + 32;
-    for (int j = 0; j < n; ++j) {
-        double sa = 1.0, sb = 1.0;
-        if (r0 < n) {
-            double s0 = W[r0 * ld + j], s1 = 0.0;
-            int c = 0;
-            for (; c + 1 < j; c += 2) {
-                s0 -= W[r0 * ld + c] * W[j * ld + c];
-                s1 -= W[r0 * ld + c + 1] * W[j * ld + c + 1];
-            }
-            if (c < j) s0 -= W[r0 * ld + c] * W[j * ld + c];
-            sa = s0 + s1;
-        }
-        if (WIDE && r1 < n) {
-            double s0 = W[r1 * ld + j], s1 = 0.0;
-            int c = 0;
-            for (; c + 1 < j; c += 2) {
-                s0 -= W[r1 * ld + c] * W[j * ld + c];
-                s1 -= W[r1 * ld + c + 1] * W[j * ld + c + 1];
-            }
-            if (c < j) s0 -= W[r1 * ld + c] * W[j * ld + c];
-            sb = s0 + s1;
-        }
-        const double dj = __shfl_sync(kFull, (WIDE && j >= 32) ? sb : sa, j & 31);
-        // The basis is orthonormal to ~1e-5, so the pivot is 1 + e with tiny
-        // e: the binomial series 1/sqrt(1+e) = 1 - e/2 + 3e^2/8 - 5e^3/16
-        // truncates below 3e-17 for |e| < 1e-4; other pivots take rsqrt.
-        const double ej = dj - 1.0;
-        const double inv = (fabs(ej) < 1e-4) ? 1.0 + ej * (-0.5 + ej * (0.375 - 0.3125 * ej))
-                                             : rsqrt(dj);
-        __syncwarp();
-        if (r0 == j) {
-            W[j * ld + j] = dj * inv;
-            vinv[j] = inv;
-        } else if (r0 > j && r0 < n) {
-            W[r0 * ld + j] = sa * inv;
-        }
-        if (WIDE) {
-            if (r1 == j) {
-                W[j * ld + j] = dj * inv;
-                vinv[j] = inv;
-            } else if (r1 > j && r1 < n) {
-                W[r1 * ld + j] = sb * inv;
-            }
-        }
-        __syncwarp();
-    }
-    // Y <- Y L^{-T}, rows by forward substitution.
-    for_cols<WIDE>(lane, n, [&](int row) {
-        for (int j = 0; j < n; ++j) {
-            double z0 = Y[row * ld + j], z1 = 0.0;
-            int c = 0;
-            for (; c + 1 < j; c += 2) {
-                z0 -= Y[row * ld + c] * W[j * ld + c];
-                z1 -= Y[row * ld + c + 1] * W[j * ld + c + 1];
-            }
-            if (c < j) z0 -= Y[row * ld + c] * W[j * ld + c];
-            Y[row * ld + j] = (z0 + z1) * vinv[j];
-        }
+    for_cols<WIDE>(lane, n, [&](int c) {
+        for (int i = 0; i < n; ++i) E32[i * ld + c] = (float)(W[i * ld + c] - (i == c ? 1.0 : 0.0));
     });
     __syncwarp();
     // W = A Y, columns: four rows at a time, then the remainder.
@@ -1375,6 +1325,14 @@ __device__ void refine_basis(double* A, double* Y, double* W, double* vinv, int 
     });
     __syncwarp();
     sym_product(Y, W, A, n, ld, lane);  // A <- S = Y^T (A Y), symmetric
+    __syncwarp();
+    for_cols<WIDE>(lane, n, [&](int c) { d[c] = A[c * ld + c]; });
+    __syncwarp();
+    for_cols<WIDE>(lane, n, [&](int c) {
+        const double dc = d[c];
+        for (int i = 0; i < n; ++i)
+            A[i * ld + c] -= (double)E32[i * ld + c] * (i == c ? dc : 0.5 * (d[i] + dc));
+    });
     __syncwarp();
 }
 
@@ -1470,7 +1428,8 @@ __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f
         for (int i = 0; i < n; ++i) Y[i * ld + c] = (double)Xp[(size_t)i * xr + c];
     });
     __syncwarp();
-    refine_basis<WIDE>(A, Y, sm.W, sm.vinv, n, ld, lane);
+    refine_rr<WIDE>(A, Y, sm.W, sm.E32, sm.v1, n, ld, lane);
+    const float* E32 = sm.E32;
     // Y in binary32 for the transform products.
     for_cols<WIDE>(lane, n, [&](int row) {
         for (int c = 0; c < n; ++c) sm.Y32[row * ld + c] = (float)Y[row * ld + c];
@@ -1497,27 +1456,32 @@ __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f
         });
         __syncwarp();
         for_cols<WIDE>(lane, n, [&](int c) {
-            // t2 = h(S) t1 with h(S)_ii = h_i, h(S)_ij = -s_ij h_i h_j.
+            // t2 = h(S) t1 with h(S)_ii = h_i, h(S)_ij = -s_ij h_i h_j, and the
+            // basis factor: minus E o (h_i + h_j)/2.
             const float hi = (float)sm.vb[c];
-            float t = 0.0f;
-            for (int j = 0; j < n; ++j)
-                if (j != c) t += (float)A[c * ld + j] * ((float)sm.vb[j] * sm.t1f[j]);
-            sm.t2f[c] = hi * (sm.t1f[c] - t);
+            float t = 0.0f, te = 0.0f;
+            for (int j = 0; j < n; ++j) {
+                const float hj = (float)sm.vb[j];
+                if (j != c) t += (float)A[c * ld + j] * (hj * sm.t1f[j]);
+                te += E32[c * ld + j] * (0.5f * (hi + hj)) * sm.t1f[j];
+            }
+            sm.t2f[c] = hi * (sm.t1f[c] - t) - te;
             // g(S) in binary32: diagonal -alpha_i / r, off-diagonal
             // s_ij (u_i + u_j + r) alpha_i alpha_j / (r (u_i + u_j)).
             const float ai = (float)sm.vinv[c];
             const float ui = (float)sm.vu[c];
             const float rf = (float)r;
+            const float gc = -ai / rf;
             for (int i = 0; i < n; ++i) {
                 float v;
+                const float aj = (float)sm.vinv[i];
                 if (i == c) {
                     v = (float)(-sm.vinv[c] / r);
                 } else {
                     const float uj = (float)sm.vu[i];
-                    const float aj = (float)sm.vinv[i];
                     v = (float)A[i * ld + c] * (ui + uj + rf) * ai * aj / (rf * (ui + uj));
                 }
-                F32[i * ld + c] = v;
+                F32[i * ld + c] = v - E32[i * ld + c] * (0.5f * (gc - aj / rf));
             }
         });
         __syncwarp();
@@ -1610,23 +1574,28 @@ __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f
         });
         __syncwarp();
         for_cols<WIDE>(lane, n, [&](int c) {
-            // t2 = f1(S) t1, f1(S)_ii = 1/l_i, f1(S)_ij = -s_ij / (l_i l_j).
-            float t = 0.0f;
-            for (int j = 0; j < n; ++j)
-                if (j != c) t += (float)A[c * ld + j] * ((float)sm.vinv[j] * sm.t1f[j]);
-            sm.t2f[c] = (float)sm.vinv[c] * (sm.t1f[c] - t);
+            // t2 = f1(S) t1, f1(S)_ii = 1/l_i, f1(S)_ij = -s_ij / (l_i l_j), and
+            // the basis factor: minus E o (f1_i + f1_j)/2.
+            const float fc1 = (float)sm.vinv[c];
+            float t = 0.0f, te = 0.0f;
+            for (int j = 0; j < n; ++j) {
+                const float fj = (float)sm.vinv[j];
+                if (j != c) t += (float)A[c * ld + j] * (fj * sm.t1f[j]);
+                te += E32[c * ld + j] * (0.5f * (fc1 + fj)) * sm.t1f[j];
+            }
+            sm.t2f[c] = fc1 * (sm.t1f[c] - t) - te;
             // f2(S) = S^{-1/2}: diagonal 1/sqrt(l_i), off-diagonal
             // -s_ij / (sqrt(l_i) sqrt(l_j) (sqrt(l_i) + sqrt(l_j))).
             const float si = (float)sm.vu[c];
             for (int i = 0; i < n; ++i) {
                 float v;
+                const float sj = (float)sm.vu[i];
                 if (i == c) {
                     v = (float)(1.0 / sm.vu[c]);
                 } else {
-                    const float sj = (float)sm.vu[i];
                     v = -(float)A[i * ld + c] / (si * sj * (si + sj));
                 }
-                F32[i * ld + c] = v;
+                F32[i * ld + c] = v - E32[i * ld + c] * (0.5f * (1.0f / si + 1.0f / sj));
             }
         });
         __syncwarp();

@@ -7,8 +7,9 @@ numpy against direct eigendecomposition (CPU only):
   C^{-1/2} = a^{-1/2} I + Yh^T g(A) Yh, g(s) = ((a+s)^{-1/2} - a^{-1/2}) / s;
 * the closed-form divided differences used to evaluate f(S) to first order
   in the off-diagonal of a nearly diagonal S (Daleckii-Krein);
-* the refinement of a binary32 eigenbasis in FP64 (Cholesky QR, Rayleigh-Ritz,
-  first-order matrix functions) reaching FP64-level accuracy.
+* the refinement of a binary32 eigenbasis in FP64 (Rayleigh-Ritz, with the
+  basis' non-orthogonality E = X^T X - I taken to first order instead of
+  re-orthonormalising, first-order matrix functions): error O(|E|^2).
 """
 import numpy as np
 import pytest
@@ -115,3 +116,46 @@ def test_binary32_basis_refined_in_fp64_gives_fp64_matrix_functions():
     # The binary32 basis alone is only good to ~1e-6.
     w32 = np.diag(X.T @ A @ X)
     assert np.abs(X @ np.diag(g(w32)) @ X.T - G_ref).max() > 1e-9 * np.abs(G_ref).max()
+
+
+def _refined_functions(A, X, a):
+    """The analysis kernel's refinement: S' = S - E o (d_i + d_j)/2,
+    first-order h(S') and g(S'), then F - E o (f_i + f_j)/2, in the basis X."""
+    p = A.shape[0]
+    E = X.T @ X - np.eye(p)
+    S = X.T @ A @ X
+    d = np.diag(S).copy()
+    Sp = S - E * (d[:, None] + d[None, :]) / 2
+    s = np.diag(Sp)
+    r = np.sqrt(a)
+    u = np.sqrt(a + s)
+    alpha = 1.0 / (u * (u + r))
+    G = Sp * (u[:, None] + u[None, :] + r) * np.outer(alpha, alpha) / (r * (u[:, None] + u[None, :]))
+    np.fill_diagonal(G, -alpha / r)
+    H = -Sp / np.outer(a + s, a + s)
+    np.fill_diagonal(H, 1.0 / (a + s))
+    gd, hd = np.diag(G).copy(), np.diag(H).copy()
+    G = G - E * (gd[:, None] + gd[None, :]) / 2
+    H = H - E * (hd[:, None] + hd[None, :]) / 2
+    return G, H, np.abs(E).max()
+
+
+@pytest.mark.parametrize("k,p,seed", [(64, 20, 3), (64, 28, 4), (40, 30, 5), (64, 12, 6)])
+def test_first_order_refinement_of_a_binary32_basis(k, p, seed):
+    dY, rho, d, a = _problem(k, p, seed)
+    Yh = np.sqrt(rho)[:, None] * dY
+    A = Yh @ Yh.T
+    X = _jacobi32(A)
+    G, H, e = _refined_functions(A, X, a)
+    g = lambda x: ((a + x) ** -0.5 - a ** -0.5) / x  # noqa: E731
+    G_ref = _fun(A, g)
+    H_ref = np.linalg.inv(a * np.eye(p) + A)
+    # Second order in the non-orthogonality (|E| ~ 5e-6 here).
+    bound = max(5 * e * e, 1e-13)
+    assert np.abs(X @ G @ X.T - G_ref).max() <= bound * np.abs(G_ref).max()
+    assert np.abs(X @ H @ X.T - H_ref).max() <= bound * np.abs(H_ref).max()
+    # Without the first-order terms the error is first order in E.
+    E = X.T @ X - np.eye(p)
+    S = X.T @ A @ X
+    s = np.diag(S)
+    assert np.abs(X @ np.diag(g(s)) @ X.T - G_ref).max() > 10 * bound * np.abs(G_ref).max()
