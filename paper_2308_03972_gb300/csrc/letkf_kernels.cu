@@ -658,9 +658,17 @@ __device__ bool jacobi32_reg(float (&a)[NS], float (&u)[NS], int lane, float rel
             float c = 1.0f, s = 0.0f, t = 0.0f;
             bool rot = false;
             if (pside && lane < NS && fabsf(off) > thresh) {
-                const float tau = (dp - dg) / (2.0f * off);
-                t = (tau >= 0.0f ? 1.0f : -1.0f) / (fabsf(tau) + sqrtf(1.0f + tau * tau));
-                c = 1.0f / sqrtf(1.0f + t * t);
+                // The binary32 Jacobi only has to shrink the off-diagonal (the
+                // FP64 refinement takes the basis from there), so the angle
+                // uses the approximate reciprocal and reciprocal square root
+                // (a few ulp, no special-case branches). sqrt(x) = x rsqrt(x)
+                // for x in [1, 1e30]; the clamp keeps tau^2 finite, where the
+                // rotation is negligible anyway (t ~ 1/(2 tau)).
+                const float tau = __fdividef(dp - dg, 2.0f * off);
+                const float x = fminf(fmaf(tau, tau, 1.0f), 1e30f);
+                const float root = x * rsqrtf(x);
+                t = __fdividef(tau >= 0.0f ? 1.0f : -1.0f, fabsf(tau) + root);
+                c = rsqrtf(fmaf(t, t, 1.0f));
                 s = t * c;
                 rot = true;
             }
@@ -1061,7 +1069,7 @@ __global__ void __launch_bounds__(32 * kGramPts, 1) local_gram_kernel(int nx, in
         if (lane + 32 * c < k) sc.b32[(size_t)li * k + lane + 32 * c] = bacc[c];
 }
 
-__global__ void __launch_bounds__(32 * kJacWarps) mixed_jacobi_kernel(int nx, int ny, int k,
+__global__ void __launch_bounds__(32 * kJacWarps, 5) mixed_jacobi_kernel(int nx, int ny, int k,
                                                                       ObsParams o, double d_cut,
                                                                       double beta, int cell0,
                                                                       int ncell, int nm,
