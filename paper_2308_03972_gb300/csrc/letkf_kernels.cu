@@ -1173,8 +1173,8 @@ __global__ void __launch_bounds__(32) mixed_jacobi_smem_kernel(int nx, int ny, i
 // nm entries.
 struct MixSmem {
     double* A;     // [nm][ld] matrix (FP64), then S = Y^T A Y
-    double* Y;     // [nm][ld] FP64 basis
-    double* W;     // [nm][ld] Y^T Y, then A Y
+    double* Y;     // [nm][ld] scratch: the binary32 halves of A in the refinement
+    double* W;     // [nm][ld] scratch: the binary32 halves of A Y, then F32
     float* F32;    // [nm][ld] f(S) in binary32, then T (inside W)
     float* Y32;    // [nm][ld] Y in binary32
     float* E32;    // [nm][ld] E = Y^T Y - I (non-orthogonality of the basis)
@@ -1253,86 +1253,109 @@ __device__ inline MixSmem carve_mix(unsigned char* raw, int k, int nl, int nm) {
     return s;
 }
 
-// Symmetric product C = P^T Q for P = Q (or P^T Q known to be symmetric):
-// only the n(n+1)/2 entries i <= j are formed, spread over the lanes two at
-// a time, and mirrored. P, Q, C are [n][ld] row-major in shared memory.
-__device__ void sym_product(const double* P, const double* Q, double* C, int n, int ld, int lane) {
+// ---- Double-binary32 products ---------------------------------------------
+// GB300 issues FP64 at 1/64 of the binary32 rate, so the refinement's three
+// n^3 products run in binary32 with error-free transformations and a second
+// accumulator (Knuth's TwoSum; the product error from one FMA, as in
+// Dekker's double-length products; accumulated as in Ogita, Rump and Oishi,
+// "Accurate sum and dot product", 2005). A binary32 basis entry y is exact,
+// an FP64 matrix entry is split into hi + lo binary32 parts, so every term
+// a y = ah y + al y enters with ah y exact and al y to 2^-48; the sums carry
+// a relative error ~ n 2^-48 of sum |terms|, FP64-class. The _rn intrinsics
+// keep the compiler from fusing or reordering these steps.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float z = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
+}
+
+// (s, c) += (ah + al) y.
+__device__ __forceinline__ void df_acc(float& s, float& c, float ah, float al, float y) {
+    const float p = __fmul_rn(ah, y);
+    const float e = __fmaf_rn(ah, y, -p);  // ah y - p, exactly
+    float t;
+    two_sum(s, p, s, t);
+    c = __fadd_rn(c, __fadd_rn(t, __fmaf_rn(al, y, e)));
+}
+
+__device__ __forceinline__ double df_value(float s, float c) { return (double)s + (double)c; }
+
+// C = P^T Q over the upper triangle (mirrored) in double-binary32: P binary32,
+// Q = Qhi + Qlo (Qlo may be null). store(i, j, value) writes both halves.
+template <typename Store>
+__device__ void sym_product_df(const float* P, const float* Qhi, const float* Qlo, int n, int ld, int lane,
+                               Store&& store) {
     const int ne = n * (n + 1) / 2;
-    for (int e0 = lane; e0 < ne; e0 += 64) {
-        const int e1 = e0 + 32;
-        // Entry e -> (i, j), i <= j, row-major over the upper triangle.
-        int i0 = 0, j0 = e0;
-        while (j0 >= n - i0) {
-            j0 -= n - i0;
-            ++i0;
+    for (int e0 = lane; e0 < ne; e0 += 32) {
+        int i = 0, j = e0;
+        while (j >= n - i) {
+            j -= n - i;
+            ++i;
         }
-        j0 += i0;
-        const bool has1 = e1 < ne;
-        int i1 = 0, j1 = has1 ? e1 : 0;
-        if (has1) {
-            while (j1 >= n - i1) {
-                j1 -= n - i1;
-                ++i1;
-            }
-            j1 += i1;
-        }
-        double s0 = 0.0, s1 = 0.0;
-        for (int r = 0; r < n; ++r) {
-            s0 += P[r * ld + i0] * Q[r * ld + j0];
-            s1 += P[r * ld + i1] * Q[r * ld + j1];
-        }
-        C[i0 * ld + j0] = s0;
-        C[j0 * ld + i0] = s0;
-        if (has1) {
-            C[i1 * ld + j1] = s1;
-            C[j1 * ld + i1] = s1;
-        }
+        j += i;
+        float s = 0.0f, c = 0.0f;
+        for (int r = 0; r < n; ++r)
+            df_acc(s, c, Qhi[r * ld + j], Qlo ? Qlo[r * ld + j] : 0.0f, P[r * ld + i]);
+        store(i, j, df_value(s, c));
     }
 }
 
-// FP64 Rayleigh-Ritz refinement of the binary32 basis Y without
-// re-orthonormalising it. With E = Y^T Y - I (|E| ~ 1e-6), Y M^{-1/2}
-// (M = I + E) is orthonormal and M^{-1/2} = I - E/2 + O(E^2), so
+// Rayleigh-Ritz refinement of the binary32 basis Y32 (exact) of the FP64
+// matrix A without re-orthonormalising it. With E = Y^T Y - I (|E| ~ 1e-6),
+// Y M^{-1/2} (M = I + E) is orthonormal and M^{-1/2} = I - E/2 + O(E^2), so
 //   S' = M^{-1/2} (Y^T A Y) M^{-1/2} = S - (E S + S E)/2 + O(E^2)
 // and, S being diagonal up to O(1e-6), (E S + S E)/2 = E o (d_i + d_j)/2 up
 // to O(E |S_offdiag|): A <- S' costs O(n^2) instead of a Cholesky factor and
 // a triangular solve. The same first-order factor returns in the matrix
 // functions (F - E o (f_i + f_j)/2, applied by the caller). The neglected
-// terms are O(|E|^2) ~ 1e-11 relative. Leaves E in E32, diag(S) in d.
+// terms are O(|E|^2) ~ 1e-11 relative. The products Y^T Y, A Y and
+// Y^T (A Y) are double-binary32. Scratch: Ah, Al (binary32 halves of A) and
+// Wh, Wl (of A Y), each [n][ld]. Leaves E in E32, S' in A, diag(S) in d.
 template <bool WIDE>
-__device__ void refine_rr(double* A, const double* Y, double* W, float* E32, double* d, int n, int ld,
-                          int lane) {
-    sym_product(Y, Y, W, n, ld, lane);  // W = Y^T Y
-    __syncwarp();
+__device__ void refine_rr(double* A, const float* Y32, float* Ah, float* Al, float* Wh, float* Wl,
+                          float* E32, double* d, int n, int ld, int lane) {
+    // E = Y^T Y - I.
+    sym_product_df(Y32, Y32, nullptr, n, ld, lane, [&](int i, int j, double v) {
+        const float e = (float)(v - (i == j ? 1.0 : 0.0));
+        E32[i * ld + j] = e;
+        E32[j * ld + i] = e;
+    });
+    // A = Ah + Al.
     for_cols<WIDE>(lane, n, [&](int c) {
-        for (int i = 0; i < n; ++i) E32[i * ld + c] = (float)(W[i * ld + c] - (i == c ? 1.0 : 0.0));
+        for (int i = 0; i < n; ++i) {
+            const double a = A[i * ld + c];
+            const float h = __double2float_rn(a);
+            Ah[i * ld + c] = h;
+            Al[i * ld + c] = __double2float_rn(a - (double)h);
+        }
     });
     __syncwarp();
-    // W = A Y, columns: four rows at a time, then the remainder.
+    // W = A Y, column col: four rows at a time, then the remainder.
     for_cols<WIDE>(lane, n, [&](int col) {
         int i0 = 0;
         for (; i0 + 3 < n; i0 += 4) {
-            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-            for (int c = 0; c < n; ++c) {
-                const double yc = Y[c * ld + col];
-                s0 += A[i0 * ld + c] * yc;
-                s1 += A[(i0 + 1) * ld + c] * yc;
-                s2 += A[(i0 + 2) * ld + c] * yc;
-                s3 += A[(i0 + 3) * ld + c] * yc;
+            float s[4] = {0.0f, 0.0f, 0.0f, 0.0f}, c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            for (int cc = 0; cc < n; ++cc) {
+                const float y = Y32[cc * ld + col];
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+                    df_acc(s[r], c[r], Ah[(i0 + r) * ld + cc], Al[(i0 + r) * ld + cc], y);
             }
-            W[i0 * ld + col] = s0;
-            W[(i0 + 1) * ld + col] = s1;
-            W[(i0 + 2) * ld + col] = s2;
-            W[(i0 + 3) * ld + col] = s3;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) two_sum(s[r], c[r], Wh[(i0 + r) * ld + col], Wl[(i0 + r) * ld + col]);
         }
         for (; i0 < n; ++i0) {
-            double s0 = 0.0;
-            for (int c = 0; c < n; ++c) s0 += A[i0 * ld + c] * Y[c * ld + col];
-            W[i0 * ld + col] = s0;
+            float s = 0.0f, c = 0.0f;
+            for (int cc = 0; cc < n; ++cc) df_acc(s, c, Ah[i0 * ld + cc], Al[i0 * ld + cc], Y32[cc * ld + col]);
+            two_sum(s, c, Wh[i0 * ld + col], Wl[i0 * ld + col]);
         }
     });
     __syncwarp();
-    sym_product(Y, W, A, n, ld, lane);  // A <- S = Y^T (A Y), symmetric
+    // A <- S = Y^T (A Y), symmetric.
+    sym_product_df(Y32, Wh, Wl, n, ld, lane, [&](int i, int j, double v) {
+        A[i * ld + j] = v;
+        A[j * ld + i] = v;
+    });
     __syncwarp();
     for_cols<WIDE>(lane, n, [&](int c) { d[c] = A[c * ld + c]; });
     __syncwarp();
@@ -1403,7 +1426,6 @@ __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f
     }
     const double aa = (k - 1) / beta;
     double* A = sm.A;
-    double* Y = sm.Y;
 
     // The symmetric matrix in FP64: A = Yh Yh^T (observation space) or
     // C = a I + Yh^T Yh with b = Yh^T d-hat (ensemble space); the basis X
@@ -1433,16 +1455,15 @@ __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f
             for (int l = 0; l < p; ++l) bj += sm.lsq[l] * o.dY[(size_t)sm.lidx[l] * k + c] * sm.ldh[l];
             sm.vb[c] = bj;
         }
-        for (int i = 0; i < n; ++i) Y[i * ld + c] = (double)Xp[(size_t)i * xr + c];
+        for (int i = 0; i < n; ++i) sm.Y32[i * ld + c] = Xp[(size_t)i * xr + c];
     });
     __syncwarp();
-    refine_rr<WIDE>(A, Y, sm.W, sm.E32, sm.v1, n, ld, lane);
+    // Scratch of the refinement: the basis region holds A's binary32 halves,
+    // the W region those of A Y.
+    float* Yf = reinterpret_cast<float*>(sm.Y);
+    float* Wf = reinterpret_cast<float*>(sm.W);
+    refine_rr<WIDE>(A, sm.Y32, Yf, Yf + nm * ld, Wf, Wf + nm * ld, sm.E32, sm.v1, n, ld, lane);
     const float* E32 = sm.E32;
-    // Y in binary32 for the transform products.
-    for_cols<WIDE>(lane, n, [&](int row) {
-        for (int c = 0; c < n; ++c) sm.Y32[row * ld + c] = (float)Y[row * ld + c];
-    });
-    __syncwarp();
     float* Y32 = sm.Y32;
     float* F32 = sm.F32;
     const float sk = (float)sqrt((double)(k - 1));

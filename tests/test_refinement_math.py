@@ -159,3 +159,56 @@ def test_first_order_refinement_of_a_binary32_basis(k, p, seed):
     S = X.T @ A @ X
     s = np.diag(S)
     assert np.abs(X @ np.diag(g(s)) @ X.T - G_ref).max() > 10 * bound * np.abs(G_ref).max()
+
+
+def _two_sum(a, b):
+    f = np.float32
+    s = (a + b).astype(f)
+    z = (s - a).astype(f)
+    return s, ((a - (s - z)).astype(f) + (b - z).astype(f)).astype(f)
+
+
+def _df_acc(s, c, ah, al, y):
+    """(s, c) += (ah + al) y in binary32 with an exact product error (the
+    float64 product of two binary32 numbers is exact), as the kernel's FMA
+    gives it."""
+    f = np.float32
+    p = (ah * y).astype(f)
+    e = (ah.astype(np.float64) * y - p).astype(f)
+    s, t = _two_sum(s, p)
+    low = (al.astype(np.float64) * y + e).astype(f)  # one rounding, like an FMA
+    return s, (c + (t + low).astype(f)).astype(f)
+
+
+@pytest.mark.parametrize("k,p,seed", [(64, 20, 3), (40, 30, 5)])
+def test_double_binary32_products_are_fp64_class(k, p, seed):
+    """Y^T Y, A Y and Y^T (A Y) from binary32 arithmetic with error-free
+    transformations: the basis is binary32 (exact), A is split into binary32
+    halves; the results match FP64 products of the same numbers to a few
+    1e-14 of |A| (plain binary32 would give ~1e-7)."""
+    dY, rho, d, a = _problem(k, p, seed)
+    Yh = np.sqrt(rho)[:, None] * dY
+    A = Yh @ Yh.T
+    X = _jacobi32(A).astype(np.float32)
+    n = p
+    f = np.float32
+    Ah = A.astype(f)
+    Al = (A - Ah.astype(np.float64)).astype(f)
+    z = np.zeros((n, n), f)
+    s, c = z.copy(), z.copy()
+    for r in range(n):  # W = A X
+        s, c = _df_acc(s, c, Ah[:, r][:, None], Al[:, r][:, None], X[r, :][None, :])
+    Wh, Wl = _two_sum(s, c)
+    s, c, s2, c2 = z.copy(), z.copy(), z.copy(), z.copy()
+    for r in range(n):  # S = X^T W, E = X^T X - I
+        s, c = _df_acc(s, c, Wh[r, :][None, :], Wl[r, :][None, :], X[r, :][:, None])
+        s2, c2 = _df_acc(s2, c2, X[r, :][None, :], z[r, :][None, :], X[r, :][:, None])
+    S = s.astype(np.float64) + c
+    E = s2.astype(np.float64) + c2 - np.eye(n)
+    Xd = X.astype(np.float64)
+    scale = np.abs(A).max()
+    assert np.abs(S - Xd.T @ A @ Xd).max() <= 1e-13 * scale
+    assert np.abs(E - (Xd.T @ Xd - np.eye(n))).max() <= 1e-13
+    # The same sums in plain binary32 are orders of magnitude worse.
+    S32 = (X.T @ (Ah @ X)).astype(np.float64)
+    assert np.abs(S32 - Xd.T @ A @ Xd).max() > 1e-9 * scale
