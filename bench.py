@@ -38,7 +38,7 @@ L2_NOTE = "state larger than L2: 151 MB per buffer in FP32, 302 MB in FP64 (L2 =
 # kernels (profiles/*_256x256_k64.md; ncu flushes L2 before each kernel).
 # Set an entry to None when its kernel changes until it is captured again.
 NCU_TRAFFIC = {
-    "analysis_mixed": 8 * (1.209856e6 + 0.982528e6 + 48.17024e6 + 0.037888e6),  # 8 chunks
+    "analysis_mixed": 8 * (1.20832e6 + 0.973312e6 + 48.159488e6 + 0.028672e6),  # 8 chunks
     "lbm_step_f32": 151.54816e6 + 98.665472e6,
     "analysis_fp64": 307.476736e6 + 242.607616e6,
 }
