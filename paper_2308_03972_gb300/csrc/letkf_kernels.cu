@@ -693,18 +693,15 @@ __device__ bool jacobi32_reg(float (&a)[NS], float (&u)[NS], int lane, float rel
                 const float om = __shfl_sync(kFull, off, pl_mine & 31);
                 dg = pside ? dg - tm * om : dg + tm * om;
                 const float sg = pside ? -sm_ : sm_;
+                // The rotated off-diagonal entry (row position qp) is zero by
+                // construction; it is set so in the same pass.
+                const int zq = (sm_ != 0.0f) ? qp : -1;
 #pragma unroll
                 for (int i = 0; i < NS; ++i) {
                     const float th = __shfl_sync(kFull, a[i], partner & 31);
-                    a[i] = cm * a[i] + sg * th;
+                    a[i] = (i == zq) ? 0.0f : cm * a[i] + sg * th;
                     const float tu = __shfl_sync(kFull, u[i], partner & 31);
                     u[i] = cm * u[i] + sg * tu;
-                }
-                // The rotated off-diagonal entry is zero by construction.
-                if (sm_ != 0.0f) {
-#pragma unroll
-                    for (int i = 0; i < NS; ++i)
-                        if (i == qp) a[i] = 0.0f;
                 }
             }
             // Rows move one tournament position.
