@@ -1169,16 +1169,17 @@ __global__ void __launch_bounds__(32) mixed_jacobi_smem_kernel(int nx, int ny, i
 // local problem of this launch and ld = nm + 1 rounded to odd; vectors have
 // nm entries.
 struct MixSmem {
-    double* A;     // [nm][ld] matrix (FP64), then S = Y^T A Y
-    double* Y;     // [nm][ld] scratch: the binary32 halves of A in the refinement
-    double* W;     // [nm][ld] scratch: the binary32 halves of A Y, then F32
-    float* F32;    // [nm][ld] f(S) in binary32, then T (inside W)
-    float* Y32;    // [nm][ld] Y in binary32
+    // Six binary32 matrices, reused as the analysis proceeds:
+    float* Ah;     // [nm][ld] A, high binary32 half; then S' off the diagonal
+    float* Al;     // [nm][ld] A, low half; then Y f2(S) (ensemble space)
+    float* Wh;     // [nm][ld] A Y, high half; then f(S) in binary32 (F32), then T
+    float* Wl;     // [nm][ld] A Y, low half
+    float* Y32;    // [nm][ld] the basis (binary32, exact)
     float* E32;    // [nm][ld] E = Y^T Y - I (non-orthogonality of the basis)
     double* lsq;   // [nl]
     double* ldh;   // [nl]
     double* vb;    // [nm]
-    double* v1;    // [nm]
+    double* dS;    // [nm] diagonal of S' (FP64)
     double* vu;    // [nm]
     double* vinv;  // [nm]
     float* dX;     // [9][k]
@@ -1196,8 +1197,8 @@ __host__ __device__ inline int mix_ld(int nm) { return (nm % 2 == 0) ? nm + 1 : 
 
 __host__ __device__ inline size_t mix_smem_bytes(int k, int nl, int nm) {
     const int ld = mix_ld(nm);
-    const size_t d = 3 * (size_t)nm * ld + 2 * (size_t)nl + 4 * (size_t)nm;
-    const size_t f = 2 * (size_t)nm * ld + 9 * (size_t)k + 16 + 18 * (size_t)nm + 16 + 3 * (size_t)nm;
+    const size_t d = 2 * (size_t)nl + 4 * (size_t)nm;
+    const size_t f = 6 * (size_t)nm * ld + 9 * (size_t)k + 16 + 18 * (size_t)nm + 16 + 3 * (size_t)nm;
     return d * sizeof(double) + ((f * sizeof(float) + 7) / 8) * 8 + (size_t)nl * sizeof(int);
 }
 
@@ -1205,26 +1206,27 @@ __device__ inline MixSmem carve_mix(unsigned char* raw, int k, int nl, int nm) {
     const int ld = mix_ld(nm);
     MixSmem s;
     double* p = reinterpret_cast<double*>(raw);
-    s.A = p;
-    p += nm * ld;
-    s.Y = p;
-    p += nm * ld;
-    s.W = p;
-    s.F32 = reinterpret_cast<float*>(p);
-    p += nm * ld;
     s.lsq = p;
     p += nl;
     s.ldh = p;
     p += nl;
     s.vb = p;
     p += nm;
-    s.v1 = p;
+    s.dS = p;
     p += nm;
     s.vu = p;
     p += nm;
     s.vinv = p;
     p += nm;
     float* q = reinterpret_cast<float*>(p);
+    s.Ah = q;
+    q += nm * ld;
+    s.Al = q;
+    q += nm * ld;
+    s.Wh = q;
+    q += nm * ld;
+    s.Wl = q;
+    q += nm * ld;
     s.Y32 = q;
     q += nm * ld;
     s.E32 = q;
@@ -1298,35 +1300,28 @@ __device__ void sym_product_df(const float* P, const float* Qhi, const float* Ql
 }
 
 // Rayleigh-Ritz refinement of the binary32 basis Y32 (exact) of the FP64
-// matrix A without re-orthonormalising it. With E = Y^T Y - I (|E| ~ 1e-6),
-// Y M^{-1/2} (M = I + E) is orthonormal and M^{-1/2} = I - E/2 + O(E^2), so
+// matrix A = Ah + Al (two binary32 halves) without re-orthonormalising it.
+// With E = Y^T Y - I (|E| ~ 1e-6), Y M^{-1/2} (M = I + E) is orthonormal
+// and M^{-1/2} = I - E/2 + O(E^2), so
 //   S' = M^{-1/2} (Y^T A Y) M^{-1/2} = S - (E S + S E)/2 + O(E^2)
 // and, S being diagonal up to O(1e-6), (E S + S E)/2 = E o (d_i + d_j)/2 up
-// to O(E |S_offdiag|): A <- S' costs O(n^2) instead of a Cholesky factor and
-// a triangular solve. The same first-order factor returns in the matrix
+// to O(E |S_offdiag|): S' costs O(n^2) instead of a Cholesky factor and a
+// triangular solve. The same first-order factor returns in the matrix
 // functions (F - E o (f_i + f_j)/2, applied by the caller). The neglected
 // terms are O(|E|^2) ~ 1e-11 relative. The products Y^T Y, A Y and
-// Y^T (A Y) are double-binary32. Scratch: Ah, Al (binary32 halves of A) and
-// Wh, Wl (of A Y), each [n][ld]. Leaves E in E32, S' in A, diag(S) in d.
+// Y^T (A Y) are double-binary32 (A Y goes to Wh + Wl). Leaves E in E32, the
+// diagonal of S' in dS (FP64) and its off-diagonal in Soff (binary32: the
+// entries are ~1e-6 of |A| and enter the matrix functions to first order).
+// Soff may alias Ah (A is not read after A Y).
 template <bool WIDE>
-__device__ void refine_rr(double* A, const float* Y32, float* Ah, float* Al, float* Wh, float* Wl,
-                          float* E32, double* d, int n, int ld, int lane) {
+__device__ void refine_rr(const float* Ah, const float* Al, const float* Y32, float* Wh, float* Wl,
+                          float* E32, float* Soff, double* dS, int n, int ld, int lane) {
     // E = Y^T Y - I.
     sym_product_df(Y32, Y32, nullptr, n, ld, lane, [&](int i, int j, double v) {
         const float e = (float)(v - (i == j ? 1.0 : 0.0));
         E32[i * ld + j] = e;
         E32[j * ld + i] = e;
     });
-    // A = Ah + Al.
-    for_cols<WIDE>(lane, n, [&](int c) {
-        for (int i = 0; i < n; ++i) {
-            const double a = A[i * ld + c];
-            const float h = __double2float_rn(a);
-            Ah[i * ld + c] = h;
-            Al[i * ld + c] = __double2float_rn(a - (double)h);
-        }
-    });
-    __syncwarp();
     // W = A Y, column col: four rows at a time, then the remainder.
     for_cols<WIDE>(lane, n, [&](int col) {
         int i0 = 0;
@@ -1348,19 +1343,26 @@ __device__ void refine_rr(double* A, const float* Y32, float* Ah, float* Al, flo
         }
     });
     __syncwarp();
-    // A <- S = Y^T (A Y), symmetric.
+    // S = Y^T (A Y), symmetric: diagonal to dS, off-diagonal to Soff.
     sym_product_df(Y32, Wh, Wl, n, ld, lane, [&](int i, int j, double v) {
-        A[i * ld + j] = v;
-        A[j * ld + i] = v;
+        if (i == j) {
+            dS[i] = v;
+        } else {
+            Soff[i * ld + j] = (float)v;
+            Soff[j * ld + i] = (float)v;
+        }
     });
     __syncwarp();
-    for_cols<WIDE>(lane, n, [&](int c) { d[c] = A[c * ld + c]; });
-    __syncwarp();
+    // S' = S - E o (d_i + d_j)/2 (the diagonal last, after every lane has
+    // read the uncorrected one).
     for_cols<WIDE>(lane, n, [&](int c) {
-        const double dc = d[c];
+        const double dc = dS[c];
         for (int i = 0; i < n; ++i)
-            A[i * ld + c] -= (double)E32[i * ld + c] * (i == c ? dc : 0.5 * (d[i] + dc));
+            if (i != c)
+                Soff[i * ld + c] = (float)((double)Soff[i * ld + c] - (double)E32[i * ld + c] * 0.5 * (dS[i] + dc));
     });
+    __syncwarp();
+    for_cols<WIDE>(lane, n, [&](int c) { dS[c] -= (double)E32[c * ld + c] * dS[c]; });
     __syncwarp();
 }
 
@@ -1422,7 +1424,12 @@ __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f
         return;
     }
     const double aa = (k - 1) / beta;
-    double* A = sm.A;
+    // A (FP64) goes to shared memory as two binary32 halves.
+    auto put = [&](int i, int c, double v) {
+        const float h = __double2float_rn(v);
+        sm.Ah[i * ld + c] = h;
+        sm.Al[i * ld + c] = __double2float_rn(v - (double)h);
+    };
 
     // The symmetric matrix in FP64: A = Yh Yh^T (observation space) or
     // C = a I + Yh^T Yh with b = Yh^T d-hat (ensemble space); the basis X
@@ -1434,10 +1441,13 @@ __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f
             const int oc = sm.lidx[c];
             const double sl = sm.lsq[c];
             for (int i = 0; i < n; ++i)
-                A[i * ld + c] = sm.lsq[i] * o.G[(size_t)sm.lidx[i] * nobs + oc] * sl;
+                put(i, c, sm.lsq[i] * o.G[(size_t)sm.lidx[i] * nobs + oc] * sl);
         } else if (sc.C32) {
             const float* Cp = sc.C32 + (size_t)li * k * k;
-            for (int i = 0; i < n; ++i) A[i * ld + c] = (double)Cp[i * k + c];
+            for (int i = 0; i < n; ++i) {
+                sm.Ah[i * ld + c] = Cp[i * k + c];
+                sm.Al[i * ld + c] = 0.0f;
+            }
             sm.vb[c] = (double)sc.b32[(size_t)li * k + c];
         } else {
             double bj = 0.0;
@@ -1447,7 +1457,7 @@ __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f
                     const double* row = o.dY + (size_t)sm.lidx[l] * k;
                     s += sm.lsq[l] * sm.lsq[l] * row[i] * row[c];
                 }
-                A[i * ld + c] = s + (i == c ? aa : 0.0);
+                put(i, c, s + (i == c ? aa : 0.0));
             }
             for (int l = 0; l < p; ++l) bj += sm.lsq[l] * o.dY[(size_t)sm.lidx[l] * k + c] * sm.ldh[l];
             sm.vb[c] = bj;
@@ -1455,14 +1465,11 @@ __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f
         for (int i = 0; i < n; ++i) sm.Y32[i * ld + c] = Xp[(size_t)i * xr + c];
     });
     __syncwarp();
-    // Scratch of the refinement: the basis region holds A's binary32 halves,
-    // the W region those of A Y.
-    float* Yf = reinterpret_cast<float*>(sm.Y);
-    float* Wf = reinterpret_cast<float*>(sm.W);
-    refine_rr<WIDE>(A, sm.Y32, Yf, Yf + nm * ld, Wf, Wf + nm * ld, sm.E32, sm.v1, n, ld, lane);
+    refine_rr<WIDE>(sm.Ah, sm.Al, sm.Y32, sm.Wh, sm.Wl, sm.E32, sm.Ah, sm.dS, n, ld, lane);
     const float* E32 = sm.E32;
+    const float* Soff = sm.Ah;  // S' off the diagonal; its diagonal is dS
     float* Y32 = sm.Y32;
-    float* F32 = sm.F32;
+    float* F32 = sm.Wh;
     const float sk = (float)sqrt((double)(k - 1));
 
     if (obs_space) {
@@ -1470,7 +1477,7 @@ __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f
         // q(s) = (a+s)^{-1/2} for the square root. u_i = sqrt(a + s_ii).
         const double r = sqrt(aa);
         for_cols<WIDE>(lane, n, [&](int c) {
-            const double sii = A[c * ld + c];
+            const double sii = sm.dS[c];
             const double u = sqrt(aa + sii);
             sm.vu[c] = u;
             sm.vinv[c] = 1.0 / (u * (u + r));  // alpha_i
@@ -1488,7 +1495,7 @@ __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f
             float t = 0.0f, te = 0.0f;
             for (int j = 0; j < n; ++j) {
                 const float hj = (float)sm.vb[j];
-                if (j != c) t += (float)A[c * ld + j] * (hj * sm.t1f[j]);
+                if (j != c) t += Soff[c * ld + j] * (hj * sm.t1f[j]);
                 te += E32[c * ld + j] * (0.5f * (hi + hj)) * sm.t1f[j];
             }
             sm.t2f[c] = hi * (sm.t1f[c] - t) - te;
@@ -1505,7 +1512,7 @@ __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f
                     v = (float)(-sm.vinv[c] / r);
                 } else {
                     const float uj = (float)sm.vu[i];
-                    v = (float)A[i * ld + c] * (ui + uj + rf) * ai * aj / (rf * (ui + uj));
+                    v = Soff[i * ld + c] * (ui + uj + rf) * ai * aj / (rf * (ui + uj));
                 }
                 F32[i * ld + c] = v - E32[i * ld + c] * (0.5f * (gc - aj / rf));
             }
@@ -1591,7 +1598,7 @@ __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f
     } else {
         // Functions of S directly: 1/lambda for P-tilde, lambda^{-1/2} for W.
         for_cols<WIDE>(lane, n, [&](int c) {
-            const double lam = A[c * ld + c];
+            const double lam = sm.dS[c];
             sm.vu[c] = sqrt(lam);
             sm.vinv[c] = 1.0 / lam;
             float t = 0.0f;
@@ -1606,7 +1613,7 @@ __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f
             float t = 0.0f, te = 0.0f;
             for (int j = 0; j < n; ++j) {
                 const float fj = (float)sm.vinv[j];
-                if (j != c) t += (float)A[c * ld + j] * (fj * sm.t1f[j]);
+                if (j != c) t += Soff[c * ld + j] * (fj * sm.t1f[j]);
                 te += E32[c * ld + j] * (0.5f * (fc1 + fj)) * sm.t1f[j];
             }
             sm.t2f[c] = fc1 * (sm.t1f[c] - t) - te;
@@ -1619,13 +1626,13 @@ __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f
                 if (i == c) {
                     v = (float)(1.0 / sm.vu[c]);
                 } else {
-                    v = -(float)A[i * ld + c] / (si * sj * (si + sj));
+                    v = -Soff[i * ld + c] / (si * sj * (si + sj));
                 }
                 F32[i * ld + c] = v - E32[i * ld + c] * (0.5f * (1.0f / si + 1.0f / sj));
             }
         });
         __syncwarp();
-        float* YF = reinterpret_cast<float*>(A);  // S is no longer needed after w-bar
+        float* YF = sm.Al;  // A's low half is no longer needed
         for_cols<WIDE>(lane, n, [&](int c) {
             float t = 0.0f;
             for (int l = 0; l < n; ++l) t += Y32[c * ld + l] * sm.t2f[l];
