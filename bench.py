@@ -37,8 +37,11 @@ L2_NOTE = "state larger than L2: 151 MB per buffer in FP32, 302 MB in FP64 (L2 =
 # DRAM bytes (read + write) per launch from one ncu capture of the current
 # kernels (profiles/*_256x256_k64.md; ncu flushes L2 before each kernel).
 # Set an entry to None when its kernel changes until it is captured again.
+# Issue-slot utilisation of the two mixed-analysis kernels in the same ncu
+# capture (profiles/analysis_mixed_256x256_k64.md).
+ISSUE_ACTIVE = {"mixed_jacobi_kernel": 0.668, "analyze_mixed_kernel": 0.358}
 NCU_TRAFFIC = {
-    "analysis_mixed": 8 * (1.20832e6 + 0.973312e6 + 48.159488e6 + 0.028672e6),  # 8 chunks
+    "analysis_mixed": 8 * (1.207296e6 + 0.95616e6 + 48.156928e6 + 0.02944e6),  # 8 chunks
     "lbm_step_f32": 151.54816e6 + 98.665472e6,
     "analysis_fp64": 307.476736e6 + 242.607616e6,
 }
@@ -611,7 +614,11 @@ def main():
                 "peak": FP64_NOMINAL_GFLOPS / 1000.0, "unit": "TFLOP/s", "frac": ach / FP64_NOMINAL_GFLOPS,
                 "traffic": NCU_TRAFFIC["analysis_mixed"],
                 "peak_source": "GB300 FP64 nominal 1.25 TFLOP/s (FMA microbenchmark: 1.20)",
-                "work": "algorithmic FP64 flops: 9 n^3 symmetric eigensolve + 2 per multiply-add of the products"}
+                "work": "algorithmic FP64 flops: 9 n^3 symmetric eigensolve + 2 per multiply-add of the products",
+                "note": "the work of the method's FP64 formulation; the mixed path does most of it in binary32 "
+                        "(Jacobi) and double-binary32 (refinement), so frac > 1 is its gain over an FP64-bound "
+                        "path; what bounds it is instruction issue (ncu, per chunk)",
+                "issue_active": ISSUE_ACTIVE}
 
     adj = batch = None
     if args.case == "all":
