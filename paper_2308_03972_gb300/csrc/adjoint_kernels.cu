@@ -41,6 +41,14 @@ namespace {
 
 __host__ __device__ constexpr double wgt(int a) { return d2q9_w(a); }
 
+// Reciprocal and square root: IEEE in FP64; in binary32 the approximate
+// hardware forms (a few ulp; the binary32 adjoint is checked against the
+// FP64 one at 1e-3), without the special-case branches of the IEEE ones.
+__device__ __forceinline__ double rcp_(double x) { return 1.0 / x; }
+__device__ __forceinline__ float rcp_(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+__device__ __forceinline__ float sqrt_(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
+
 // Transposed collision Jacobian at one cell and member. f: the stored state
 // (g = f - w with SHIFT), g: adjoint of the post-collision values (in), out:
 // adjoint of the pre-collision values. Returns the C_s derivative term.
@@ -55,7 +63,7 @@ __device__ __forceinline__ T collide_vjp(const T (&f)[9], const T (&g)[9], T (&o
         jy += T(d2q9_cy(a)) * f[a];
     }
     const T rho = SHIFT ? T(1) + s : s;
-    const T ir = T(1) / rho;
+    const T ir = rcp_(rho);
     const T ux = jx * ir, uy = jy * ir;
     const T uu = ux * ux + uy * uy;
     T fneq[9];
@@ -73,12 +81,12 @@ __device__ __forceinline__ T collide_vjp(const T (&f)[9], const T (&g)[9], T (&o
         pxy += cx * cy * fneq[a];
         pyy += cy * cy * fneq[a];
     }
-    const T Q = sqrt(T(2) * (pxx * pxx + T(2) * pxy * pxy + pyy * pyy));
+    const T Q = sqrt_(T(2) * (pxx * pxx + T(2) * pxy * pxy + pyy * pyy));
     const T cs18 = T(18) * cs * cs;
-    const T S = sqrt(tau0 * tau0 + cs18 * Q * ir);
-    const T iS = T(1) / S;
-    const T om = T(2) / (tau0 + S);
-    const T iQ = Q > T(0) ? T(1) / Q : T(0);
+    const T S = sqrt_(tau0 * tau0 + cs18 * Q * ir);
+    const T iS = rcp_(S);
+    const T om = T(2) * rcp_(tau0 + S);
+    const T iQ = Q > T(0) ? rcp_(Q) : T(0);
     // Contractions of the incoming adjoint.
     T grho = T(0), gjx = T(0), gjy = T(0), gF = T(0), gcx = T(0), gcy = T(0), h = T(0);
 #pragma unroll
@@ -130,10 +138,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) adjoint_step_kern
 #pragma unroll
     for (int j = 0; j < V; ++j) dcs[j] = T(0);
     if (t < total) {
-        const int mv = (int)(t % kv);
-        const long long cell = t / kv;
-        const int x = (int)(cell % nx);
-        const int y = (int)(cell / nx);
+        int mv, x, y;
+        long long cell;
+        split_item(t, kv, nx, mv, cell, x, y);
         const size_t plane = (size_t)nx * ny * k;
         const size_t mo = (size_t)mv * V;
         const size_t here = (size_t)cell * k + mo;
@@ -179,10 +186,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) adjoint_step_kern
     for (int j = 0; j < V; ++j) part[threadIdx.x * V + j] = dcs[j];
     __syncthreads();
     const long long first = (long long)blockIdx.x * blockDim.x;
+    const int first_mv = (int)(first % kv);  // once per thread
     for (int m = threadIdx.x; m < k; m += blockDim.x) {
         const int mv = m / V, j = m % V;
         // First thread of the block holding member group mv.
-        int t0 = (int)((mv - first % kv + kv) % kv);
+        int t0 = mv - first_mv;
+        if (t0 < 0) t0 += kv;
         double acc = 0.0;
         for (; t0 < (int)blockDim.x; t0 += kv) acc += (double)part[t0 * V + j];
         if (acc != 0.0) atomicAdd(&gcs[m], acc);

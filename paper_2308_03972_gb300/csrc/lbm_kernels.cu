@@ -87,10 +87,9 @@ __device__ __forceinline__ void step_item(const T* __restrict__ fin, T* __restri
                                           T tau0, T cs18, T mu, int* __restrict__ flags,
                                           long long t) {
     const int kv = k / V;
-    const int mv = (int)(t % kv);
-    const long long cell = t / kv;
-    const int x = (int)(cell % nx);
-    const int y = (int)(cell / nx);
+    int mv, x, y;
+    long long cell;
+    split_item(t, kv, nx, mv, cell, x, y);
     const size_t plane = (size_t)nx * ny * k;  // elements per alpha
     const size_t src = (size_t)cell * k + (size_t)mv * V;
 

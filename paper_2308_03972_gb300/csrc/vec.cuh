@@ -53,4 +53,25 @@ struct Vec<float, 4> {
     }
 };
 
+// Work item t of a lattice kernel -> member group mv (of kv per cell), cell,
+// and its coordinates (x, y). The divisions run in 32 bits while t fits
+// (64-bit integer division is emulated and costs several times more).
+__device__ __forceinline__ void split_item(long long t, int kv, int nx, int& mv, long long& cell, int& x,
+                                           int& y) {
+    if (t < 0x100000000LL) {
+        const unsigned tt = (unsigned)t, ukv = (unsigned)kv, unx = (unsigned)nx;
+        const unsigned c = tt / ukv;
+        mv = (int)(tt - c * ukv);
+        cell = c;
+        const unsigned yy = c / unx;
+        y = (int)yy;
+        x = (int)(c - yy * unx);
+    } else {
+        mv = (int)(t % kv);
+        cell = t / kv;
+        x = (int)(cell % nx);
+        y = (int)(cell / nx);
+    }
+}
+
 }  // namespace lbmgpu
