@@ -203,6 +203,15 @@ def measure(cfg, precision, steps, warmup, sample_clocks=False, gpu_index=0):
         if sampler:
             sampler.__exit__()
     osse.ens.sync()
+    # RMSE of the ensemble mean against the nature run at the same step.
+    rmse = osse.rmse()
+    # Jacobi sweeps per grid point, from one more (untimed) cycle.
+    osse.ens.sweep_stats(True)
+    osse.cycle(obs[-1])
+    hist = osse.ens.sweep_stats(False, read=True)
+    cum = np.cumsum(hist)
+    sweeps = {"median": int(np.searchsorted(cum, cum[-1] / 2.0)), "max": int(np.nonzero(hist)[0].max()),
+              "points": int(cum[-1])}
     # The nature run (one FP64 member) is the OSSE's truth, timed apart from
     # the ensemble cycle: one cycle's worth of steps, a few times.
     nat = []
@@ -219,7 +228,6 @@ def measure(cfg, precision, steps, warmup, sample_clocks=False, gpu_index=0):
     lbm = [e[0].elapsed_time(e[1]) / cfg.steps_per_cycle for e in ev]
     obs_ms = [e[1].elapsed_time(e[2]) for e in ev]
     ana = [e[2].elapsed_time(e[3]) for e in ev]
-    rmse = osse.rmse()
     osse.close()
     # Kernels per cycle: the LBM steps, observe + Gram, then the analysis
     # (FP64: one launch; mixed: the FP32 copy of dY and two kernels per chunk
@@ -229,6 +237,7 @@ def measure(cfg, precision, steps, warmup, sample_clocks=False, gpu_index=0):
     return {"ms_per_cycle": total_ms / steps, "lbm_step_ms": statistics.mean(lbm),
             "observe_ms": statistics.mean(obs_ms), "analysis_ms": statistics.mean(ana),
             "rmse": rmse, "clocks": sampler.summary() if sampler else None, "nature_ms": nature_ms,
+            "sweeps": sweeps,
             "launches_per_cycle": cfg.steps_per_cycle + 2 + ana_launches}
 
 
@@ -597,6 +606,8 @@ def main():
         "grid_point_analyses_per_s_mixed": ncells / (mixed["analysis_ms"] * 1e-3),
         "grid_point_analyses_per_s_fp64": ncells / (fp64["analysis_ms"] * 1e-3),
         "nature_run_ms_per_cycle": mixed["nature_ms"],
+        "jacobi_sweeps_per_point_mixed": mixed["sweeps"],
+        "jacobi_sweeps_per_point_fp64": fp64["sweeps"],
     }
     lbm_share = mixed["lbm_step_ms"] * cfg.steps_per_cycle
     kern["lbm_step_f32"]["traffic"] = NCU_TRAFFIC["lbm_step_f32"]

@@ -172,6 +172,13 @@ int letkf_observe_rho(lbm_ctx *ctx, int npts, const int *ix, const int *iy,
 enum { LBM_PROD_FP64 = 0, LBM_PROD_FP32 = 1, LBM_PROD_TF32 = 2, LBM_PROD_BF16 = 3 };
 int letkf_set_products(lbm_ctx *ctx, int mode);
 
+/* Diagnostic: count the Jacobi sweeps of every local eigensolve of later
+ * analyses (enable != 0) into a 32-bin histogram (bin s: points that took s
+ * sweeps, the last one rotating nothing; bin 31: 31 or more, or the sweep
+ * cap). With hist (host, [32]) non-NULL the current counts are copied out
+ * and reset (synchronises). Recording adds one atomic per grid point. */
+int letkf_sweep_stats(lbm_ctx *ctx, int enable, int *hist);
+
 /* Set the Smagorinsky coefficient C_s of the eddy-viscosity closure
  * (Section 2) used by the following forecasts; finite, >= 0. */
 int lbm_set_closure(lbm_ctx *ctx, double cs_smag);

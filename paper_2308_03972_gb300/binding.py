@@ -54,6 +54,7 @@ SIGNATURES = {
     "letkf_analyze": (_I, [_P, _D, _D]),
     "lbm_set_closure": (_I, [_P, _D]),
     "letkf_set_products": (_I, [_P, _I]),
+    "letkf_sweep_stats": (_I, [_P, _I, _P]),
     "lbm_misfit": (_I, [_P, ctypes.POINTER(lbm_window), _P]),
     "lbm_misfit_gradient": (_I, [_P, ctypes.POINTER(lbm_window), _P, _P, _P, _P, _I]),
     "lbm_nudge": (_I, [_P, _I, _I, _P, _P, _P, _D]),
@@ -237,6 +238,15 @@ def letkf_observe_rho(ctx, ix, iy, yo_u, yo_v, yo_rho, sigma_u, sigma_v, sigma_r
                                          float(sigma_u), float(sigma_v), float(sigma_rho)))
 
 
+def letkf_sweep_stats(ctx, enable, read=False):
+    """Enable/disable sweep counting; with read=True return the 32-bin
+    histogram (and reset it)."""
+    h = np.zeros(32, np.int32) if read else None
+    _check(ctx, load().letkf_sweep_stats(ctx, 1 if enable else 0,
+                                         h.ctypes.data_as(ctypes.c_void_p) if read else None))
+    return h
+
+
 def letkf_set_products(ctx, mode):
     _check(ctx, load().letkf_set_products(ctx, int(mode)))
 
@@ -379,6 +389,9 @@ class Ensemble:
 
     def observe(self, ix, iy, yo_u, yo_v, sigma_u, sigma_v):
         letkf_observe(self.ctx, ix, iy, yo_u, yo_v, sigma_u, sigma_v)
+
+    def sweep_stats(self, enable, read=False):
+        return letkf_sweep_stats(self.ctx, enable, read)
 
     def set_products(self, mode):
         letkf_set_products(self.ctx, mode)

@@ -55,6 +55,7 @@ struct ObsParams {
     double sigma_r = 1.0;
     int plmax = 0;     // capacity of one grid point's local list (0: nobs); a
                        // point with more local scalars is reported too large
+    int* sweep_hist = nullptr;  // [32] Jacobi sweep counts per point, or null
 };
 
 // ---- lbm_kernels.cu -------------------------------------------------------

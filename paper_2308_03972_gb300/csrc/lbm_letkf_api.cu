@@ -52,6 +52,8 @@ struct lbm_ctx {
     bool obs_pending = false;
     double sigma_u = 0.0, sigma_v = 0.0, sigma_r = 1.0;
     int prod = PROD_FP64;  // ensemble-space Gram arithmetic (mixed precision)
+    int* sweep_hist = nullptr;  // [32] Jacobi sweeps per point (diagnostic)
+    bool sweep_stats = false;
     bool observed = false;
     char err[512] = {0};
 };
@@ -467,7 +469,7 @@ int analyze_prepare(lbm_ctx* c, double d_cut, double beta, AnalysisPlan* plan) {
 // Device part: the analysis kernels on the context stream (capturable).
 int analyze_launch(lbm_ctx* c, const AnalysisPlan& pl) {
     ObsParams o{c->npts, c->ix, c->iy, c->dY, c->d, c->G, c->sigma_u, c->sigma_v, c->dY32,
-                c->nvar, c->sigma_r, pl.plmax};
+                c->nvar, c->sigma_r, pl.plmax, c->sweep_stats ? c->sweep_hist : nullptr};
     CK(c, launch_analyze(c->f[c->cur], is_fp32(c), c->nx, c->ny, c->k, o, pl.d_cut, pl.beta, pl.nmax,
                          pl.prod, c->flags, c->ana_scratch, c->aux_ready ? &c->aux : nullptr, c->stream),
        "launching analysis");
@@ -712,6 +714,22 @@ int letkf_set_products(lbm_ctx* c, int mode) {
     return LBM_OK;
 }
 
+int letkf_sweep_stats(lbm_ctx* c, int enable, int* hist) {
+    if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (!c->sweep_hist) {
+        CK(c, cudaMalloc(&c->sweep_hist, 32 * sizeof(int)), "allocating sweep histogram");
+        CK(c, cudaMemsetAsync(c->sweep_hist, 0, 32 * sizeof(int), c->stream), "clearing sweep histogram");
+    }
+    if (hist) {
+        CK(c, cudaMemcpyAsync(hist, c->sweep_hist, 32 * sizeof(int), cudaMemcpyDeviceToHost, c->stream),
+           "reading sweep histogram");
+        CK(c, cudaMemsetAsync(c->sweep_hist, 0, 32 * sizeof(int), c->stream), "clearing sweep histogram");
+        CK(c, cudaStreamSynchronize(c->stream), "synchronising");
+    }
+    c->sweep_stats = enable != 0;
+    return LBM_OK;
+}
+
 int lbm_set_closure(lbm_ctx* c, double cs_smag) {
     if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
     if (!(cs_smag >= 0.0) || !std::isfinite(cs_smag)) return fail(c, LBM_EINVAL, "cs_smag must be finite and >= 0");
@@ -850,6 +868,7 @@ void lbm_destroy(lbm_ctx* c) {
     cudaFree(c->stage);
     cudaFree(c->ana_scratch);
     cudaFree(c->nudge_obs);
+    cudaFree(c->sweep_hist);
     if (c->aux_ready) {
         cudaStreamSynchronize(c->aux.s2);
         cudaEventDestroy(c->aux.start);

@@ -119,6 +119,12 @@ __global__ void obs_gram_kernel(const double* __restrict__ dY, int nobs, int k,
     G[(size_t)i * nobs + j] = s;
 }
 
+// Sweep count of one eigensolve into the optional histogram (bin 31: 31 or
+// more sweeps, or the sweep cap).
+__device__ __forceinline__ void record_sweeps(const ObsParams& o, int sweeps, int lane) {
+    if (o.sweep_hist && lane == 0) atomicAdd(&o.sweep_hist[(sweeps < 0 || sweeps > 31) ? 31 : sweeps], 1);
+}
+
 // Local observation set of grid point (x, y), in increasing point order:
 // point j is in range when r / d_cut < 2 and G(r / d_cut) > 0; it gives the
 // nvar scalars nvar*j + q (u, v, rho) with sqrt(rho-tilde) = sqrt(G) / sigma_q.
@@ -190,10 +196,10 @@ __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 // diagonal block analytically (a_pp - t a_pq, a_qq + t a_pq, 0), the
 // off-diagonal 2 x 2 blocks (P, Q), P < Q, as J_P^T X J_Q (mirrored), and the
 // rows of U. A rotation is skipped when |a_pq| <= rel ||A||_F; the solve ends
-// after a sweep without one. n <= 64 (at most 32 pairs). Returns false if
-// max_sweeps was reached.
+// after a sweep without one. n <= 64 (at most 32 pairs). Returns the number
+// of sweeps (the last one rotating nothing), or -1 if max_sweeps was reached.
 template <typename R>
-__device__ bool jacobi_sym_warp(R* A, R* U, int n, int ld, int lane, R* rc, R* rs, int* rp,
+__device__ int jacobi_sym_warp(R* A, R* U, int n, int ld, int lane, R* rc, R* rs, int* rp,
                                 int* rq, R rel, int max_sweeps) {
     const int np = n + (n & 1);
     const int half = np / 2;
@@ -298,9 +304,9 @@ __device__ bool jacobi_sym_warp(R* A, R* U, int n, int ld, int lane, R* rc, R* r
             }
             __syncwarp();
         }
-        if (!any_sweep) return true;
+        if (!any_sweep) return sweep + 1;
     }
-    return false;
+    return -1;
 }
 
 // Shared memory of the FP64 analysis kernel for problems up to NM.
@@ -463,10 +469,10 @@ __global__ void __launch_bounds__(32) analyze_fp64_kernel(double* __restrict__ f
     // neglected second-order term is (3e-8 ||A||_F / (a + s))^2, below
     // ~1e-11 relative even for ||A||_F ~ 100 a, i.e. ~1e-13 of the state).
     // Ensemble space converges fully and uses the diagonal directly.
-    if (!jacobi_sym_warp<double>(A, U, n, ld, lane, sm.rc, sm.rs, sm.rp, sm.rq,
-                                 obs_space ? 3e-8 : 1e-18, kMaxSweeps)) {
-        if (lane == 0) atomicOr(flags, FLAG_NOCONV);
-    }
+    const int sweeps = jacobi_sym_warp<double>(A, U, n, ld, lane, sm.rc, sm.rs, sm.rp, sm.rq,
+                                               obs_space ? 3e-8 : 1e-18, kMaxSweeps);
+    if (sweeps < 0 && lane == 0) atomicOr(flags, FLAG_NOCONV);
+    record_sweeps(o, sweeps, lane);
     __syncwarp();
 
     if (obs_space) {
@@ -629,7 +635,7 @@ constexpr int kJacWarps = 4;        // points per block in (A)
 // On entry a[i] = A[i][lane] (row i at position i); on return u[i] holds
 // U[i][lane], the eigenvector of player `lane`.
 template <int NS>
-__device__ bool jacobi32_reg(float (&a)[NS], float (&u)[NS], int lane, float rel, int max_sweeps) {
+__device__ int jacobi32_reg(float (&a)[NS], float (&u)[NS], int lane, float rel, int max_sweeps) {
     float dg = 0.0f;  // my diagonal entry A[lane][lane], tracked analytically
 #pragma unroll
     for (int i = 0; i < NS; ++i) {
@@ -714,9 +720,9 @@ __device__ bool jacobi32_reg(float (&a)[NS], float (&u)[NS], int lane, float rel
             }
             r = (r + 1 == m1) ? 0 : r + 1;
         }
-        if (!any_sweep) return true;
+        if (!any_sweep) return sweep + 1;
     }
-    return false;
+    return -1;
 }
 
 // One point of kernel (A): build column `lane` of the matrix (FP64, rounded
@@ -758,9 +764,9 @@ __device__ void jacobi_point(const ObsParams& o, int k, int n, int p, bool obs_s
     // Stop at 1e-6 ||A||_F: the FP64-class refinement takes the matrix
     // functions from there (its neglected terms are second order in the
     // remaining off-diagonal, ~1e-12 relative).
-    if (!jacobi32_reg<NS>(a, u, lane, 1e-6f, kMaxSweeps)) {
-        if (lane == 0) atomicOr(flags, FLAG_NOCONV);
-    }
+    const int sweeps = jacobi32_reg<NS>(a, u, lane, 1e-6f, kMaxSweeps);
+    if (sweeps < 0 && lane == 0) atomicOr(flags, FLAG_NOCONV);
+    record_sweeps(o, sweeps, lane);
     if (lane < n) {
 #pragma unroll
         for (int i = 0; i < NS; ++i)
@@ -1159,9 +1165,9 @@ __global__ void __launch_bounds__(32) mixed_jacobi_smem_kernel(int nx, int ny, i
         for (int i = 0; i < n; ++i) U[i * ld + c] = (i == c) ? 1.0f : 0.0f;
     }
     __syncwarp();
-    if (!jacobi_sym_warp<float>(A, U, n, ld, lane, rc, rs, rp, rq, 3e-8f, kMaxSweeps)) {
-        if (lane == 0) atomicOr(flags, FLAG_NOCONV);
-    }
+    const int sweeps = jacobi_sym_warp<float>(A, U, n, ld, lane, rc, rs, rp, rq, 3e-8f, kMaxSweeps);
+    if (sweeps < 0 && lane == 0) atomicOr(flags, FLAG_NOCONV);
+    record_sweeps(o, sweeps, lane);
     __syncwarp();
     const int xr = mix_xr(nm);
     float* Xp = sc.X + (size_t)li * xr * xr;

@@ -263,3 +263,28 @@ def test_mixed_analysis_over_many_odd_sized_chunks(gpu):
     ref = oracle.letkf_analyze(f, ix, iy, yu, yv, SIGMA, SIGMA, 3.0, 1.05, points=pts)
     y, x = pts // nx, pts % nx
     assert norm_rel(got[:, y, x, :], ref[:, y, x, :]) <= 1e-6
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_sweep_histogram_counts_every_eigensolve(gpu, prec):
+    """letkf_sweep_stats: one count per grid point with a non-empty local set,
+    none at the sweep cap; off again, nothing is counted."""
+    nx, ny, k = 24, 20, 8
+    f, ix, iy, yu, yv = _analysis_case(nx, ny, k, 4, 4, seed=12)
+    d_cut = 1.5  # support radius 3 < half the observation spacing: some points see nothing
+    expected = sum(1 for y in range(ny) for x in range(nx)
+                   if len(oracle.local_obs(nx, ny, x, y, ix, iy, SIGMA, SIGMA, d_cut)[0]) > 0)
+    p = gpu.LBM_FP64 if prec == "fp64" else gpu.LBM_MIXED
+    with gpu.Ensemble(nx, ny, k, TAU0, CS, MU, p, f0=f) as e:
+        e.sweep_stats(True)
+        e.observe(ix, iy, yu, yv, SIGMA, SIGMA)
+        e.analyze(d_cut, 1.05)
+        h = e.sweep_stats(False, read=True)
+        e.observe(ix, iy, yu, yv, SIGMA, SIGMA)
+        e.analyze(d_cut, 1.05)
+        h2 = e.sweep_stats(False, read=True)
+        e.sync()
+    assert 0 < expected < nx * ny
+    assert int(h.sum()) == expected
+    assert h[31] == 0 and h[0] == 0
+    assert int(h2.sum()) == 0
