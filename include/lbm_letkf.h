@@ -49,7 +49,7 @@ typedef struct lbm_ctx lbm_ctx;
 
 typedef enum {
     LBM_OK = 0,
-    LBM_EINVAL = 1,    /* bad argument, or local problem too large (min(k, p) > 64) */
+    LBM_EINVAL = 1,    /* bad argument, or local problem too large (see letkf_analyze) */
     LBM_ENOMEM = 2,    /* device allocation failed */
     LBM_ECUDA = 3,     /* CUDA runtime error (launch or copy) */
     LBM_EDIVERGED = 4, /* non-finite density/velocity or |u| > 0.5 seen */
@@ -167,7 +167,7 @@ int letkf_observe_rho(lbm_ctx *ctx, int npts, const int *ix, const int *iy,
  *   LBM_PROD_TF32  TF32 products on the tensor cores, binary32 accumulation;
  *   LBM_PROD_BF16  BF16 products on the tensor cores, binary32 accumulation.
  * The eigensolve stays FP64-accurate in every mode; the reduced modes apply
- * for members <= 64 (larger ensembles keep FP64). LBM_EINVAL for an unknown
+ * for members <= 128 (larger ensembles keep FP64). LBM_EINVAL for an unknown
  * mode or a reduced mode on an FP64 context. Applies to later analyses. */
 enum { LBM_PROD_FP64 = 0, LBM_PROD_FP32 = 1, LBM_PROD_TF32 = 2, LBM_PROD_BF16 = 3 };
 int letkf_set_products(lbm_ctx *ctx, int mode);
@@ -213,7 +213,10 @@ int lbm_misfit_gradient(lbm_ctx *ctx, const lbm_window *win, const double *w, do
  * Gaspari-Cohn weight G(r / d_cut), r the periodic distance, support
  * r < 2 d_cut; inflation P^f -> beta P^f). Uses the observations of the
  * last letkf_observe call, which it consumes. d_cut > 0, beta > 0,
- * members >= 2. Asynchronous. */
+ * members >= 2. Asynchronous. The local eigenproblem has size
+ * n = min(k, p), p the number of local observation scalars; a grid point
+ * with n > 64 (LBM_FP64) or n > 128 (LBM_MIXED) is reported as LBM_EINVAL
+ * at the next synchronising call and leaves that point unchanged. */
 int letkf_analyze(lbm_ctx *ctx, double d_cut, double beta);
 
 /* Nudging, the paper's comparison method (Section 3.1): every member is

@@ -115,7 +115,7 @@ int read_flags(lbm_ctx* c) {
     if (h & FLAG_DIVERGED)
         return fail(c, LBM_EDIVERGED, "state diverged: non-finite density/velocity or |u| > 0.5");
     if (h & FLAG_TOOLARGE)
-        return fail(c, LBM_EINVAL, "local analysis problem larger than the kernel supports (n = min(k, p) > 64)");
+        return fail(c, LBM_EINVAL, "local analysis problem larger than the kernel supports (n = min(k, p) > 64 in FP64, > 128 in mixed precision)");
     return fail(c, LBM_ENOCONV, "eigensolver reached its sweep cap");
 }
 

@@ -22,6 +22,7 @@
 // matrix held in shared memory, one column per lane.
 #include <cmath>
 #include <cstdint>
+#include <type_traits>
 
 #include <cuda_bf16.h>
 
@@ -31,8 +32,9 @@ namespace lbmgpu {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int NMAX = 64;  // largest local eigenproblem of the analysis kernels
-constexpr int NREG = 32;  // largest one handled by the register Jacobi
+constexpr int NMAX = 128;  // largest local eigenproblem of the mixed-precision analysis
+constexpr int NMID = 64;   // largest held wholly in shared memory; the FP64 analysis' limit
+constexpr int NREG = 32;   // largest one handled by the register Jacobi
 constexpr int kMaxSweeps = 30;
 
 template <typename R>
@@ -196,11 +198,14 @@ __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 // diagonal block analytically (a_pp - t a_pq, a_qq + t a_pq, 0), the
 // off-diagonal 2 x 2 blocks (P, Q), P < Q, as J_P^T X J_Q (mirrored), and the
 // rows of U. A rotation is skipped when |a_pq| <= rel ||A||_F; the solve ends
-// after a sweep without one. n <= 64 (at most 32 pairs). Returns the number
-// of sweeps (the last one rotating nothing), or -1 if max_sweeps was reached.
-template <typename R>
+// after a sweep without one. n <= 2 MAXH (at most MAXH pairs, 32 or 64; rc,
+// rs, rp, rq hold MAXH entries). Returns the number of sweeps (the last one
+// rotating nothing), or -1 if max_sweeps was reached.
+template <typename R, int MAXH = 32>
 __device__ int jacobi_sym_warp(R* A, R* U, int n, int ld, int lane, R* rc, R* rs, int* rp,
                                 int* rq, R rel, int max_sweeps) {
+    static_assert(MAXH == 32 || MAXH == 64, "32 or 64 pairs");
+    using Mask = typename std::conditional<(MAXH > 32), unsigned long long, unsigned>::type;
     const int np = n + (n & 1);
     const int half = np / 2;
     const int nb = half * (half - 1) / 2;
@@ -212,50 +217,65 @@ __device__ int jacobi_sym_warp(R* A, R* U, int n, int ld, int lane, R* rc, R* rs
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
         bool any_sweep = false;
         for (int r = 0; r + 1 < np; ++r) {
-            bool rot = false;
-            if (lane < half) {
-                const int pa = lane, pb = np - 1 - lane;
-                const int P = pa == 0 ? 0 : 1 + (pa - 1 + r) % (np - 1);
-                const int Q = 1 + (pb - 1 + r) % (np - 1);
-                const int p = P < Q ? P : Q, q = P < Q ? Q : P;
-                R c = R(1), sn = R(0);
-                if (q < n) {
-                    const R apq = A[p * ld + q];
-                    if (fabs(apq) > thresh) {
-                        // t = phi / (theta + sgn(theta) sqrt(theta^2 + phi^2)),
-                        // theta = a_qq - a_pp, phi = 2 a_pq: the smaller root of
-                        // t^2 + 2 (theta / phi) t - 1 = 0.
-                        const R app = A[p * ld + p], aqq = A[q * ld + q];
-                        const R th = aqq - app, ph = R(2) * apq;
-                        const R rr = sqrt(th * th + ph * ph);
-                        const R t = ph / (th >= R(0) ? th + rr : th - rr);
-                        c = rsq(R(1) + t * t);
-                        sn = t * c;
-                        rot = true;
-                        // Diagonal block of the pair, analytically.
-                        A[p * ld + p] = app - t * apq;
-                        A[q * ld + q] = aqq + t * apq;
-                        A[p * ld + q] = R(0);
-                        A[q * ld + p] = R(0);
+            Mask any = 0;
+#pragma unroll
+            for (int pr0 = 0; pr0 < MAXH; pr0 += 32) {
+                const int pr = pr0 + lane;
+                bool rot = false;
+                if (pr < half) {
+                    const int pa = pr, pb = np - 1 - pr;
+                    const int P = pa == 0 ? 0 : 1 + (pa - 1 + r) % (np - 1);
+                    const int Q = 1 + (pb - 1 + r) % (np - 1);
+                    const int p = P < Q ? P : Q, q = P < Q ? Q : P;
+                    R c = R(1), sn = R(0);
+                    if (q < n) {
+                        const R apq = A[p * ld + q];
+                        if (fabs(apq) > thresh) {
+                            // t = phi / (theta + sgn(theta) sqrt(theta^2 + phi^2)),
+                            // theta = a_qq - a_pp, phi = 2 a_pq: the smaller root of
+                            // t^2 + 2 (theta / phi) t - 1 = 0.
+                            const R app = A[p * ld + p], aqq = A[q * ld + q];
+                            const R th = aqq - app, ph = R(2) * apq;
+                            const R rr = sqrt(th * th + ph * ph);
+                            const R t = ph / (th >= R(0) ? th + rr : th - rr);
+                            c = rsq(R(1) + t * t);
+                            sn = t * c;
+                            rot = true;
+                            // Diagonal block of the pair, analytically.
+                            A[p * ld + p] = app - t * apq;
+                            A[q * ld + q] = aqq + t * apq;
+                            A[p * ld + q] = R(0);
+                            A[q * ld + p] = R(0);
+                        }
                     }
+                    rp[pr] = p;
+                    rq[pr] = q;
+                    rc[pr] = c;
+                    rs[pr] = sn;
                 }
-                rp[lane] = p;
-                rq[lane] = q;
-                rc[lane] = c;
-                rs[lane] = sn;
+                any |= (Mask)__ballot_sync(kFull, rot) << pr0;
             }
-            const unsigned any = __ballot_sync(kFull, rot);
             __syncwarp();
             if (any == 0) continue;
             any_sweep = true;
-            // Off-diagonal blocks (P, Q), P < Q, of the pairs of this round.
+            // Off-diagonal blocks (P, Q), P < Q, of the pairs of this round;
+            // block bb is entry Q0 of row P (Q = P + 1 + Q0) in the upper
+            // triangle of the pair matrix.
+            // With 64 pairs a lane advances its previous (P, Q0) by 32 blocks
+            // instead of decoding bb from row 0.
+            int P = 0, Q0 = 0;
             for (int bb = lane; bb < nb; bb += 32) {
-                int P = 0, Q = bb;
-                while (Q >= half - 1 - P) {
-                    Q -= half - 1 - P;
+                if (MAXH == 32 || bb == lane) {
+                    P = 0;
+                    Q0 = bb;
+                } else {
+                    Q0 += 32;
+                }
+                while (Q0 >= half - 1 - P) {
+                    Q0 -= half - 1 - P;
                     ++P;
                 }
-                Q += P + 1;
+                const int Q = P + 1 + Q0;
                 const bool rP = (any >> P) & 1u, rQ = (any >> Q) & 1u;
                 if (!rP && !rQ) continue;
                 const int pP = rp[P], qP = rq[P], pQ = rp[Q], qQ = rq[Q];
@@ -782,17 +802,27 @@ struct MixScratch {
     int* pcount;   // [chunk] number of local scalars
     float* C32;    // [chunk][k][k] a I + Yh^T Yh from the reduced-precision Gram, or null
     float* b32;    // [chunk][k] Yh^T d-hat from the same pass, or null
+    float* big;    // [chunk][4][nm][ld] kernel (B)'s A and A Y halves when nm > NMID, or null
 };
 
 // Row stride of the basis scratch: 128-byte rows for the register Jacobi.
-__host__ __device__ inline int mix_xr(int nm) { return nm <= NREG ? NREG : NMAX; }
+__host__ __device__ inline int mix_xr(int nm) { return nm <= NREG ? NREG : (nm <= NMID ? NMID : NMAX); }
+
+// Row stride of the matrices of kernel (B): nm + 1 rounded to odd.
+__host__ __device__ inline int mix_ld(int nm) { return (nm % 2 == 0) ? nm + 1 : nm; }
+
+// Floats per grid point of kernel (B)'s matrices kept in global scratch
+// (A and A Y, two binary32 halves each) when nm > NMID, else 0.
+__host__ __device__ inline size_t mix_big_floats(int nm) {
+    return nm > NMID ? 4 * (size_t)nm * mix_ld(nm) : 0;
+}
 
 // kg: members k when the reduced-precision Gram pass is used (its C and b
 // per point), else 0.
 __host__ __device__ inline size_t mix_scratch_bytes_per_point(int nobs, int nm, int kg) {
     const int xr = mix_xr(nm);
     return (size_t)xr * xr * sizeof(float) + (size_t)nobs * (sizeof(double) + sizeof(int)) +
-           sizeof(int) + (size_t)kg * (kg + 1) * sizeof(float);
+           sizeof(int) + (size_t)kg * (kg + 1) * sizeof(float) + mix_big_floats(nm) * sizeof(float);
 }
 
 // Grid points per chunk: the double-buffered scratch stays within ~96 MB of L2.
@@ -818,6 +848,8 @@ __host__ __device__ inline MixScratch mix_scratch_at(void* base, long long chunk
     m.C32 = kg ? reinterpret_cast<float*>(p) : nullptr;
     p += (size_t)chunk * kg * kg * sizeof(float);
     m.b32 = kg ? reinterpret_cast<float*>(p) : nullptr;
+    p += (size_t)chunk * kg * sizeof(float);
+    m.big = nm > NMID ? reinterpret_cast<float*>(p) : nullptr;
     return m;
 }
 
@@ -889,8 +921,12 @@ __global__ void __launch_bounds__(32 * kGramPts, 1) local_gram_kernel(int nx, in
                                                                      int ncell, MixScratch sc) {
     constexpr int KC = MODE == PROD_TF32 ? 8 : 16;        // rows per stage
     constexpr int LD = MODE == PROD_TF32 ? K + 8 : K + 4;  // conflict-free fragment reads
-    constexpr int MT = K / 16, NT = K / 8;
-    constexpr int NCOL = K > 32 ? 2 : 1;                   // columns per lane (FP32 path, b)
+    // Output columns per pass over the rows: all of them up to 64 members;
+    // 32 per pass at 128, so that the accumulators stay at 128 per lane.
+    constexpr int KB = K > 64 ? 32 : K;
+    constexpr int MT = K / 16, NT = KB / 8;
+    constexpr int NCOL = KB > 32 ? 2 : 1;  // output columns per lane and pass (FP32 path)
+    constexpr int NBC = K > 32 ? K / 32 : 1;  // entries of b per lane
     __shared__ float Ys[KC][LD];
     __shared__ float Ws[kGramPts][KC];  // rho-tilde = (sqrt(G) / sigma)^2 per point and row
     __shared__ float Ds[KC];
@@ -941,138 +977,146 @@ __global__ void __launch_bounds__(32 * kGramPts, 1) local_gram_kernel(int nx, in
     if (!any_ens) return;
     const int rows = total * nv;
     const int g = lane >> 2, t = lane & 3;
-    float acc[MODE == PROD_FP32 ? 1 : MT][MODE == PROD_FP32 ? 1 : NT][4];
-    float accf[MODE == PROD_FP32 ? K : 1][NCOL];
-    float bacc[NCOL];
-#pragma unroll
-    for (int c = 0; c < NCOL; ++c) bacc[c] = 0.0f;
-    if constexpr (MODE == PROD_FP32) {
-#pragma unroll
-        for (int m = 0; m < K; ++m)
-#pragma unroll
-            for (int c = 0; c < NCOL; ++c) accf[m][c] = 0.0f;
-    } else {
-#pragma unroll
-        for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-            for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-                for (int i = 0; i < 4; ++i) acc[mt][nt][i] = 0.0f;
-    }
-    for (int r0 = 0; r0 < rows; r0 += KC) {
-        for (int e = threadIdx.x; e < KC * K; e += 32 * kGramPts) {
-            const int rr = e / K, c = e % K, r = r0 + rr;
-            float v = 0.0f;
-            if (r < rows && c < k) v = o.dY32[(size_t)(nv * U[r / nv] + r % nv) * k + c];
-            Ys[rr][c] = v;
-        }
-        if (threadIdx.x < KC * kGramPts) {
-            const int q = threadIdx.x / KC, rr = threadIdx.x % KC, r = r0 + rr;
-            float wv = 0.0f;
-            if (r < rows && li0 + q < ncell) {
-                const int cell = cell0 + li0 + q;
-                const double sg = local_weight(o, U[r / nv], cell % nx, cell / nx, nx, ny, d_cut);
-                const double l = sg / sig[r % nv];
-                wv = (float)(l * l);
-            }
-            Ws[q][rr] = wv;
-        }
-        if (threadIdx.x < KC) {
-            const int r = r0 + threadIdx.x;
-            Ds[threadIdx.x] = r < rows ? (float)o.d[nv * U[r / nv] + r % nv] : 0.0f;
-        }
-        __syncthreads();
-        if constexpr (MODE == PROD_FP32) {
-            for (int rr = 0; rr < KC; ++rr) {
-                const float wl = Ws[w][rr];
-                if (wl == 0.0f) continue;
-                float yc[NCOL];
-#pragma unroll
-                for (int c = 0; c < NCOL; ++c) {
-                    yc[c] = (lane + 32 * c < K) ? Ys[rr][lane + 32 * c] : 0.0f;
-                    bacc[c] += wl * Ds[rr] * yc[c];
-                }
-#pragma unroll
-                for (int m = 0; m < K; ++m) {
-                    const float ym = wl * Ys[rr][m];
-#pragma unroll
-                    for (int c = 0; c < NCOL; ++c) accf[m][c] += ym * yc[c];
-                }
-            }
-        } else {
-#pragma unroll
-            for (int rr = 0; rr < KC; ++rr) {
-                const float wl = Ws[w][rr];
-#pragma unroll
-                for (int c = 0; c < NCOL; ++c)
-                    if (lane + 32 * c < K) bacc[c] += wl * Ds[rr] * Ys[rr][lane + 32 * c];
-            }
-            if constexpr (MODE == PROD_TF32) {
-                const float wa = Ws[w][t], wb = Ws[w][t + 4];
-                uint32_t bf[NT][2];
-#pragma unroll
-                for (int nt = 0; nt < NT; ++nt) {
-                    bf[nt][0] = to_tf32(Ys[t][8 * nt + g]);
-                    bf[nt][1] = to_tf32(Ys[t + 4][8 * nt + g]);
-                }
-#pragma unroll
-                for (int mt = 0; mt < MT; ++mt) {
-                    const uint32_t a0 = to_tf32(wa * Ys[t][16 * mt + g]);
-                    const uint32_t a1 = to_tf32(wa * Ys[t][16 * mt + g + 8]);
-                    const uint32_t a2 = to_tf32(wb * Ys[t + 4][16 * mt + g]);
-                    const uint32_t a3 = to_tf32(wb * Ys[t + 4][16 * mt + g + 8]);
-#pragma unroll
-                    for (int nt = 0; nt < NT; ++nt) mma_tf32(acc[mt][nt], a0, a1, a2, a3, bf[nt][0], bf[nt][1]);
-                }
-            } else {
-                const int r0a = 2 * t, r1a = 2 * t + 1, r0b = 2 * t + 8, r1b = 2 * t + 9;
-                const float w0 = Ws[w][r0a], w1 = Ws[w][r1a], w8 = Ws[w][r0b], w9 = Ws[w][r1b];
-                uint32_t bf[NT][2];
-#pragma unroll
-                for (int nt = 0; nt < NT; ++nt) {
-                    bf[nt][0] = pack_bf16(Ys[r0a][8 * nt + g], Ys[r1a][8 * nt + g]);
-                    bf[nt][1] = pack_bf16(Ys[r0b][8 * nt + g], Ys[r1b][8 * nt + g]);
-                }
-#pragma unroll
-                for (int mt = 0; mt < MT; ++mt) {
-                    const int m0 = 16 * mt + g, m1 = m0 + 8;
-                    const uint32_t a0 = pack_bf16(w0 * Ys[r0a][m0], w1 * Ys[r1a][m0]);
-                    const uint32_t a1 = pack_bf16(w0 * Ys[r0a][m1], w1 * Ys[r1a][m1]);
-                    const uint32_t a2 = pack_bf16(w8 * Ys[r0b][m0], w9 * Ys[r1b][m0]);
-                    const uint32_t a3 = pack_bf16(w8 * Ys[r0b][m1], w9 * Ys[r1b][m1]);
-#pragma unroll
-                    for (int nt = 0; nt < NT; ++nt) mma_bf16(acc[mt][nt], a0, a1, a2, a3, bf[nt][0], bf[nt][1]);
-                }
-            }
-        }
-        __syncthreads();
-    }
     const int li = li0 + w;
-    if (li >= ncell) return;
     float* C = sc.C32 + (size_t)li * k * k;
     const float fa = (float)aa;
-    if constexpr (MODE == PROD_FP32) {
+    float acc[MODE == PROD_FP32 ? 1 : MT][MODE == PROD_FP32 ? 1 : NT][4];
+    float accf[MODE == PROD_FP32 ? K : 1][NCOL];
+    float bacc[NBC];
 #pragma unroll
-        for (int m = 0; m < K; ++m)
+    for (int c = 0; c < NBC; ++c) bacc[c] = 0.0f;
+    for (int cb = 0; cb < K; cb += KB) {  // first column of this pass
+        if constexpr (MODE == PROD_FP32) {
 #pragma unroll
-            for (int c = 0; c < NCOL; ++c) {
-                const int n = lane + 32 * c;
-                if (m < k && n < k) C[m * k + n] = accf[m][c] + (m == n ? fa : 0.0f);
+            for (int m = 0; m < K; ++m)
+#pragma unroll
+                for (int c = 0; c < NCOL; ++c) accf[m][c] = 0.0f;
+        } else {
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) acc[mt][nt][i] = 0.0f;
+        }
+        for (int r0 = 0; r0 < rows; r0 += KC) {
+            for (int e = threadIdx.x; e < KC * K; e += 32 * kGramPts) {
+                const int rr = e / K, c = e % K, r = r0 + rr;
+                float v = 0.0f;
+                if (r < rows && c < k) v = o.dY32[(size_t)(nv * U[r / nv] + r % nv) * k + c];
+                Ys[rr][c] = v;
             }
-    } else {
-#pragma unroll
-        for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-            for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int m = 16 * mt + g + (i >= 2 ? 8 : 0);
-                    const int n = 8 * nt + 2 * t + (i & 1);
-                    if (m < k && n < k) C[m * k + n] = acc[mt][nt][i] + (m == n ? fa : 0.0f);
+            if (threadIdx.x < KC * kGramPts) {
+                const int q = threadIdx.x / KC, rr = threadIdx.x % KC, r = r0 + rr;
+                float wv = 0.0f;
+                if (r < rows && li0 + q < ncell) {
+                    const int cell = cell0 + li0 + q;
+                    const double sg = local_weight(o, U[r / nv], cell % nx, cell / nx, nx, ny, d_cut);
+                    const double l = sg / sig[r % nv];
+                    wv = (float)(l * l);
                 }
-    }
+                Ws[q][rr] = wv;
+            }
+            if (threadIdx.x < KC) {
+                const int r = r0 + threadIdx.x;
+                Ds[threadIdx.x] = r < rows ? (float)o.d[nv * U[r / nv] + r % nv] : 0.0f;
+            }
+            __syncthreads();
+            if constexpr (MODE == PROD_FP32) {
+                for (int rr = 0; rr < KC; ++rr) {
+                    const float wl = Ws[w][rr];
+                    if (wl == 0.0f) continue;
+                    float yc[NCOL];
 #pragma unroll
-    for (int c = 0; c < NCOL; ++c)
+                    for (int c = 0; c < NCOL; ++c) yc[c] = (lane + 32 * c < KB) ? Ys[rr][cb + lane + 32 * c] : 0.0f;
+                    if (cb == 0) {
+#pragma unroll
+                        for (int c = 0; c < NBC; ++c)
+                            bacc[c] += wl * Ds[rr] * ((lane + 32 * c < K) ? Ys[rr][lane + 32 * c] : 0.0f);
+                    }
+#pragma unroll
+                    for (int m = 0; m < K; ++m) {
+                        const float ym = wl * Ys[rr][m];
+#pragma unroll
+                        for (int c = 0; c < NCOL; ++c) accf[m][c] += ym * yc[c];
+                    }
+                }
+            } else {
+                if (cb == 0) {
+#pragma unroll
+                    for (int rr = 0; rr < KC; ++rr) {
+                        const float wl = Ws[w][rr];
+#pragma unroll
+                        for (int c = 0; c < NBC; ++c)
+                            if (lane + 32 * c < K) bacc[c] += wl * Ds[rr] * Ys[rr][lane + 32 * c];
+                    }
+                }
+                if constexpr (MODE == PROD_TF32) {
+                    const float wa = Ws[w][t], wb = Ws[w][t + 4];
+                    uint32_t bf[NT][2];
+#pragma unroll
+                    for (int nt = 0; nt < NT; ++nt) {
+                        bf[nt][0] = to_tf32(Ys[t][cb + 8 * nt + g]);
+                        bf[nt][1] = to_tf32(Ys[t + 4][cb + 8 * nt + g]);
+                    }
+#pragma unroll
+                    for (int mt = 0; mt < MT; ++mt) {
+                        const uint32_t a0 = to_tf32(wa * Ys[t][16 * mt + g]);
+                        const uint32_t a1 = to_tf32(wa * Ys[t][16 * mt + g + 8]);
+                        const uint32_t a2 = to_tf32(wb * Ys[t + 4][16 * mt + g]);
+                        const uint32_t a3 = to_tf32(wb * Ys[t + 4][16 * mt + g + 8]);
+#pragma unroll
+                        for (int nt = 0; nt < NT; ++nt) mma_tf32(acc[mt][nt], a0, a1, a2, a3, bf[nt][0], bf[nt][1]);
+                    }
+                } else {
+                    const int r0a = 2 * t, r1a = 2 * t + 1, r0b = 2 * t + 8, r1b = 2 * t + 9;
+                    const float w0 = Ws[w][r0a], w1 = Ws[w][r1a], w8 = Ws[w][r0b], w9 = Ws[w][r1b];
+                    uint32_t bf[NT][2];
+#pragma unroll
+                    for (int nt = 0; nt < NT; ++nt) {
+                        bf[nt][0] = pack_bf16(Ys[r0a][cb + 8 * nt + g], Ys[r1a][cb + 8 * nt + g]);
+                        bf[nt][1] = pack_bf16(Ys[r0b][cb + 8 * nt + g], Ys[r1b][cb + 8 * nt + g]);
+                    }
+#pragma unroll
+                    for (int mt = 0; mt < MT; ++mt) {
+                        const int m0 = 16 * mt + g, m1 = m0 + 8;
+                        const uint32_t a0 = pack_bf16(w0 * Ys[r0a][m0], w1 * Ys[r1a][m0]);
+                        const uint32_t a1 = pack_bf16(w0 * Ys[r0a][m1], w1 * Ys[r1a][m1]);
+                        const uint32_t a2 = pack_bf16(w8 * Ys[r0b][m0], w9 * Ys[r1b][m0]);
+                        const uint32_t a3 = pack_bf16(w8 * Ys[r0b][m1], w9 * Ys[r1b][m1]);
+#pragma unroll
+                        for (int nt = 0; nt < NT; ++nt) mma_bf16(acc[mt][nt], a0, a1, a2, a3, bf[nt][0], bf[nt][1]);
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        if (li < ncell) {
+            if constexpr (MODE == PROD_FP32) {
+#pragma unroll
+                for (int m = 0; m < K; ++m)
+#pragma unroll
+                    for (int c = 0; c < NCOL; ++c) {
+                        const int n = cb + lane + 32 * c;
+                        if (m < k && n < k && lane + 32 * c < KB) C[m * k + n] = accf[m][c] + (m == n ? fa : 0.0f);
+                    }
+            } else {
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+                    for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const int m = 16 * mt + g + (i >= 2 ? 8 : 0);
+                            const int n = cb + 8 * nt + 2 * t + (i & 1);
+                            if (m < k && n < k) C[m * k + n] = acc[mt][nt][i] + (m == n ? fa : 0.0f);
+                        }
+            }
+        }
+    }  // passes over the output columns
+    if (li >= ncell) return;
+#pragma unroll
+    for (int c = 0; c < NBC; ++c)
         if (lane + 32 * c < k) sc.b32[(size_t)li * k + lane + 32 * c] = bacc[c];
 }
 
@@ -1115,8 +1159,10 @@ __global__ void __launch_bounds__(32 * kJacWarps, 5) mixed_jacobi_kernel(int nx,
         jacobi_point<32>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, xr, flags, Cp);
 }
 
-// Kernel (A) for local problems of 33..64: the binary32 Jacobi in shared
-// memory (one warp per point, lanes own two columns), same output.
+// Kernel (A) for local problems of 33..128: the binary32 Jacobi in shared
+// memory (one warp per point, lanes own columns c = lane, lane + 32, ...),
+// same output. MAXH: Jacobi pairs, 32 for n <= 64, 64 for n <= 128.
+template <int MAXH>
 __global__ void __launch_bounds__(32) mixed_jacobi_smem_kernel(int nx, int ny, int k, ObsParams o,
                                                                double d_cut, double beta, int cell0,
                                                                int nm, MixScratch sc,
@@ -1127,9 +1173,9 @@ __global__ void __launch_bounds__(32) mixed_jacobi_smem_kernel(int nx, int ny, i
     float* A = reinterpret_cast<float*>(smem_raw);
     float* U = A + (size_t)nm * ld;
     float* rc = U + (size_t)nm * ld;
-    float* rs = rc + 32;
-    int* rp = reinterpret_cast<int*>(rs + 32);
-    int* rq = rp + 32;
+    float* rs = rc + MAXH;
+    int* rp = reinterpret_cast<int*>(rs + MAXH);
+    int* rq = rp + MAXH;
     const int lane = threadIdx.x;
     const int li = blockIdx.x;
     const int cell = cell0 + li;
@@ -1165,7 +1211,9 @@ __global__ void __launch_bounds__(32) mixed_jacobi_smem_kernel(int nx, int ny, i
         for (int i = 0; i < n; ++i) U[i * ld + c] = (i == c) ? 1.0f : 0.0f;
     }
     __syncwarp();
-    const int sweeps = jacobi_sym_warp<float>(A, U, n, ld, lane, rc, rs, rp, rq, 3e-8f, kMaxSweeps);
+    // Stop at 1e-6 ||A||_F, as the register Jacobi does: the refinement of
+    // kernel (B) is second order in what remains.
+    const int sweeps = jacobi_sym_warp<float, MAXH>(A, U, n, ld, lane, rc, rs, rp, rq, 1e-6f, kMaxSweeps);
     if (sweeps < 0 && lane == 0) atomicOr(flags, FLAG_NOCONV);
     record_sweeps(o, sweeps, lane);
     __syncwarp();
@@ -1203,16 +1251,18 @@ struct MixSmem {
     int* lidx;     // [nl]
 };
 
-__host__ __device__ inline int mix_ld(int nm) { return (nm % 2 == 0) ? nm + 1 : nm; }
-
+// Above NMID, Ah, Al, Wh and Wl live in the global scratch (MixScratch::big)
+// and shared memory holds only Y32 and E32 of the six matrices.
 __host__ __device__ inline size_t mix_smem_bytes(int k, int nl, int nm) {
     const int ld = mix_ld(nm);
     const size_t d = 2 * (size_t)nl + 4 * (size_t)nm;
-    const size_t f = 6 * (size_t)nm * ld + 9 * (size_t)k + 16 + 18 * (size_t)nm + 16 + 3 * (size_t)nm;
+    const size_t f = (nm > NMID ? 2 : 6) * (size_t)nm * ld + 9 * (size_t)k + 16 + 18 * (size_t)nm + 16 +
+                     3 * (size_t)nm;
     return d * sizeof(double) + ((f * sizeof(float) + 7) / 8) * 8 + (size_t)nl * sizeof(int);
 }
 
-__device__ inline MixSmem carve_mix(unsigned char* raw, int k, int nl, int nm) {
+// big: this grid point's 4 nm ld floats of global scratch, or null.
+__device__ inline MixSmem carve_mix(unsigned char* raw, int k, int nl, int nm, float* big) {
     const int ld = mix_ld(nm);
     MixSmem s;
     double* p = reinterpret_cast<double*>(raw);
@@ -1229,14 +1279,16 @@ __device__ inline MixSmem carve_mix(unsigned char* raw, int k, int nl, int nm) {
     s.vinv = p;
     p += nm;
     float* q = reinterpret_cast<float*>(p);
-    s.Ah = q;
-    q += nm * ld;
-    s.Al = q;
-    q += nm * ld;
-    s.Wh = q;
-    q += nm * ld;
-    s.Wl = q;
-    q += nm * ld;
+    float* m = big ? big : q;
+    s.Ah = m;
+    m += nm * ld;
+    s.Al = m;
+    m += nm * ld;
+    s.Wh = m;
+    m += nm * ld;
+    s.Wl = m;
+    m += nm * ld;
+    if (!big) q = m;
     s.Y32 = q;
     q += nm * ld;
     s.E32 = q;
@@ -1376,7 +1428,9 @@ __device__ void refine_rr(const float* Ah, const float* Al, const float* Y32, fl
     __syncwarp();
 }
 
-template <bool WIDE>
+// BIG (nm > NMID): A and A Y in global scratch (L2-resident), the rest as
+// below.
+template <bool WIDE, bool BIG>
 __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f, int nx, int ny,
                                                            int k, ObsParams o, double d_cut,
                                                            double beta, int cell0, int nm,
@@ -1385,10 +1439,10 @@ __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nobs = o.nvar * o.npts;
     const int cap = o.plmax > 0 ? o.plmax : nobs;
-    MixSmem sm = carve_mix(smem_raw, k, cap, nm);
+    const int li = blockIdx.x;
+    MixSmem sm = carve_mix(smem_raw, k, cap, nm, BIG ? sc.big + (size_t)li * mix_big_floats(nm) : nullptr);
     const int ld = mix_ld(nm);
     const int lane = threadIdx.x;
-    const int li = blockIdx.x;
     const int cell = cell0 + li;
     const size_t plane = (size_t)nx * ny * k;
     float* fc = f + (size_t)cell * k;
@@ -1708,7 +1762,7 @@ cudaError_t launch_obs_gram(const double* dY, int nobs, int k, double* G, cudaSt
 static int mixed_nm(int nmax) { return nmax < 2 ? 2 : (nmax > NMAX ? NMAX : nmax); }
 
 // Members k when the reduced-precision Gram pass runs (mixed precision, a
-// reduced product mode, k <= 64), else 0.
+// reduced product mode, k <= 128), else 0.
 static int gram_k(int fp32, int k, int prod) {
     return (fp32 && prod != PROD_FP64 && k <= NMAX) ? k : 0;
 }
@@ -1729,7 +1783,8 @@ static cudaError_t launch_gram_mode(int nx, int ny, int k, const ObsParams& o, d
     };
     if (k <= 16) return go(local_gram_kernel<MODE, 16>);
     if (k <= 32) return go(local_gram_kernel<MODE, 32>);
-    return go(local_gram_kernel<MODE, 64>);
+    if (k <= 64) return go(local_gram_kernel<MODE, 64>);
+    return go(local_gram_kernel<MODE, 128>);
 }
 
 static cudaError_t launch_gram(int prod, int nx, int ny, int k, const ObsParams& o, double d_cut,
@@ -1761,16 +1816,18 @@ cudaError_t launch_analyze(void* f, int fp32, int nx, int ny, int k, const ObsPa
         to_f32_kernel<<<(unsigned)((nd + 255) / 256), 256, 0, s>>>(o.dY, o.dY32, nd);
         const int cap = o.plmax > 0 ? o.plmax : nobs;
         const size_t shB = mix_smem_bytes(k, cap, nm);
-        const size_t shA = nm > NREG ? 2 * (size_t)nm * (nm + 1) * sizeof(float) + 64 * (sizeof(float) + sizeof(int)) : 0;
-        const bool wide = nm > NREG;
-        e = wide ? cudaFuncSetAttribute(analyze_mixed_kernel<true>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shB)
-                 : cudaFuncSetAttribute(analyze_mixed_kernel<false>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shB);
+        const int maxh = nm > NMID ? 64 : 32;  // Jacobi pairs of kernel (A) in shared memory
+        const size_t shA = nm > NREG ? 2 * (size_t)nm * (nm + 1) * sizeof(float) +
+                                           2 * (size_t)maxh * (sizeof(float) + sizeof(int))
+                                     : 0;
+        const bool wide = nm > NREG, big = nm > NMID;
+        auto kernB = big ? analyze_mixed_kernel<true, true>
+                         : (wide ? analyze_mixed_kernel<true, false> : analyze_mixed_kernel<false, false>);
+        auto kernA = big ? mixed_jacobi_smem_kernel<64> : mixed_jacobi_smem_kernel<32>;
+        e = cudaFuncSetAttribute(kernB, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shB);
         if (e != cudaSuccess) return e;
         if (nm > NREG) {
-            e = cudaFuncSetAttribute(mixed_jacobi_smem_kernel,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shA);
+            e = cudaFuncSetAttribute(kernA, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shA);
             if (e != cudaSuccess) return e;
         }
         const int kg = gram_k(fp32, k, prod);
@@ -1795,16 +1852,10 @@ cudaError_t launch_analyze(void* f, int fp32, int nx, int ny, int k, const ObsPa
                 mixed_jacobi_kernel<<<(unsigned)((nc + kJacWarps - 1) / kJacWarps), 32 * kJacWarps, 0,
                                       aux->s2>>>(nx, ny, k, o, d_cut, beta, (int)c0, nc, nm, sc, flags);
             else
-                mixed_jacobi_smem_kernel<<<(unsigned)nc, 32, shA, aux->s2>>>(nx, ny, k, o, d_cut, beta,
-                                                                              (int)c0, nm, sc, flags);
+                kernA<<<(unsigned)nc, 32, shA, aux->s2>>>(nx, ny, k, o, d_cut, beta, (int)c0, nm, sc, flags);
             if ((e = cudaEventRecord(aux->jac_done[b], aux->s2)) != cudaSuccess) return e;
             if ((e = cudaStreamWaitEvent(s, aux->jac_done[b], 0)) != cudaSuccess) return e;
-            if (wide)
-                analyze_mixed_kernel<true><<<(unsigned)nc, 32, shB, s>>>((float*)f, nx, ny, k, o, d_cut,
-                                                                         beta, (int)c0, nm, sc, flags);
-            else
-                analyze_mixed_kernel<false><<<(unsigned)nc, 32, shB, s>>>((float*)f, nx, ny, k, o, d_cut,
-                                                                          beta, (int)c0, nm, sc, flags);
+            kernB<<<(unsigned)nc, 32, shB, s>>>((float*)f, nx, ny, k, o, d_cut, beta, (int)c0, nm, sc, flags);
             if ((e = cudaEventRecord(aux->ref_done[b], s)) != cudaSuccess) return e;
         }
     } else {

@@ -119,15 +119,60 @@ def test_argument_errors(gpu):
 
 
 def test_oversized_local_problem_is_reported(gpu):
-    # 80 members and 72 observation scalars in range: n = 72 > 64.
+    """FP64 holds n = min(k, p) <= 64 and mixed precision n <= 128; a larger
+    local problem is reported as LBM_EINVAL at the next sync."""
+    # 80 members and 72 observation scalars in range: n = 72 > 64 (FP64).
     f, ix, iy, yu, yv = _analysis_case(24, 24, 80, 6, 6, seed=3)
+    with gpu.Ensemble(24, 24, 80, TAU0, CS, MU, gpu.LBM_FP64, f0=f) as e:
+        e.observe(ix, iy, yu, yv, SIGMA, SIGMA)
+        e.analyze(100.0, 1.0)
+        with pytest.raises(gpu.LbmError) as err:
+            e.sync()
+        assert err.value.code == gpu.LBM_EINVAL
+    # 136 members and 288 observation scalars in range: n = 136 > 128.
+    f, ix, iy, yu, yv = _analysis_case(24, 24, 136, 12, 12, seed=3, steps=1)
     for prec in (gpu.LBM_FP64, gpu.LBM_MIXED):
-        with gpu.Ensemble(24, 24, 80, TAU0, CS, MU, prec, f0=f) as e:
+        with gpu.Ensemble(24, 24, 136, TAU0, CS, MU, prec, f0=f) as e:
             e.observe(ix, iy, yu, yv, SIGMA, SIGMA)
             e.analyze(100.0, 1.0)
             with pytest.raises(gpu.LbmError) as err:
                 e.sync()
             assert err.value.code == gpu.LBM_EINVAL
+
+
+@pytest.mark.parametrize("nx,ny,k,nox,noy,d_cut", [
+    (24, 24, 80, 6, 6, 100.0),    # observation space, n = 72
+    (16, 16, 101, 8, 8, 100.0),   # ensemble space, n = k = 101 (odd)
+    (20, 20, 128, 8, 8, 6.0),     # n = 112..128 over the grid, both forms, ragged
+])
+def test_local_problems_65_to_128_match_oracle(gpu, nx, ny, k, nox, noy, d_cut):
+    """Mixed precision above n = 64: binary32 Jacobi with 64 round-robin
+    pairs in shared memory, the refinement's A and A Y in global scratch."""
+    f, ix, iy, yu, yv = _analysis_case(nx, ny, k, nox, noy, seed=70 + k)
+    ref = oracle.letkf_analyze(f, ix, iy, yu, yv, SIGMA, SIGMA, d_cut, 1.05)
+    got = _gpu_analysis(gpu, f, ix, iy, yu, yv, d_cut, 1.05, gpu.LBM_MIXED)
+    assert norm_rel(got, ref) <= 1e-6
+
+
+@pytest.mark.parametrize("mode,bound", [("fp32", 1e-6), ("tf32", 2e-4), ("bf16", 2e-3)])
+def test_reduced_gram_at_128_members(gpu, mode, bound):
+    """The reduced-precision Gram pass at k = 128 (four passes of 32 output
+    columns) in the ensemble-space form, against the FP64 oracle; bounds of
+    max |f^a| as in the precision sweep."""
+    nx, ny, k = 16, 16, 128
+    f, ix, iy, yu, yv = _analysis_case(nx, ny, k, 8, 8, seed=5)
+    ref = oracle.letkf_analyze(f, ix, iy, yu, yv, SIGMA, SIGMA, 100.0, 1.05)
+    code = {"fp32": gpu.LBM_PROD_FP32, "tf32": gpu.LBM_PROD_TF32, "bf16": gpu.LBM_PROD_BF16}[mode]
+    with gpu.Ensemble(nx, ny, k, TAU0, CS, MU, gpu.LBM_MIXED, f0=f) as e:
+        e.set_products(code)
+        e.observe(ix, iy, yu, yv, SIGMA, SIGMA)
+        e.analyze(100.0, 1.05)
+        got = e.get_f()
+        e.sync()
+    err = np.max(np.abs(got - ref)) / np.max(np.abs(ref))
+    assert err <= bound
+    # The increment is far above the bound: the pass did change the state.
+    assert np.max(np.abs(ref - f)) / np.max(np.abs(ref)) > 10 * bound
 
 
 @pytest.mark.parametrize("nx,ny,k,nox,noy,d_cut", [

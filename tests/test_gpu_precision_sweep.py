@@ -4,8 +4,8 @@ noise, localisation radius d_cut = 32 and d_cut = the observation spacing,
 and the Gram/b products in FP64, binary32, TF32 and BF16 (eigensolve
 FP64-accurate in all). Every case is checked against the FP64 oracle at
 sampled grid points; the error of each case is printed as a table (run with
--s to see it). Cases whose local problem exceeds n = min(k, p) = 64 must be
-refused with LBM_EINVAL."""
+-s to see it). Every case has n = min(k, p) <= 128, which the mixed path
+holds; a case above it would have to be refused with LBM_EINVAL."""
 import json
 import os
 
@@ -66,14 +66,14 @@ def test_precision_sweep_256(gpu):
                 for d_cut in sorted({32.0, float(NX // no)}):
                     n = _max_local(no, d_cut, k)
                     row = {"k": k, "obs": "%dx%d" % (no, no), "d_cut": d_cut, "n_max": n}
-                    if n > 64:
+                    if n > 128:
                         e.set_f(f0)
                         e.observe(ix, iy, yu, yv, CFG.sigma, CFG.sigma)
                         with pytest.raises(gpu.LbmError) as err:
                             e.analyze(d_cut, CFG.beta)
                             e.sync()  # the device reports the size at the next sync
                         assert err.value.code == gpu.LBM_EINVAL
-                        row["status"] = "refused: n > 64"
+                        row["status"] = "refused: n > 128"
                         rows.append(row)
                         continue
                     ref = oracle.letkf_analyze(f0, ix, iy, yu, yv, CFG.sigma, CFG.sigma, d_cut, CFG.beta,
