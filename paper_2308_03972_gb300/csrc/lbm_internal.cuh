@@ -18,6 +18,8 @@ enum : int {
 // the ensemble-space form of the mixed-precision analysis: FP64 (default),
 // or binary32 accumulation of binary32 / TF32 / BF16 products.
 enum : int { PROD_FP64 = 0, PROD_FP32 = 1, PROD_TF32 = 2, PROD_BF16 = 3 };
+// No ensemble-space grid point in this analysis: no Gram pass at all.
+constexpr int PROD_NONE = -1;
 
 // Speed limit used by the divergence check: |u| > 0.5 lattice units.
 constexpr double kUMax2 = 0.25;
@@ -118,7 +120,8 @@ struct AnalyzeAux {
 size_t analyze_scratch_bytes(int nx, int ny, int fp32, int nl, int nmax, int k, int prod);
 // nmax: largest local problem size n = min(p, k) over the grid (sizes the
 // mixed kernel's shared memory; points above it are reported as too large).
-// prod: PROD_* arithmetic of the ensemble-space Gram (mixed precision only).
+// prod: PROD_* arithmetic of the ensemble-space Gram (mixed precision only),
+// PROD_NONE when no grid point uses the ensemble-space form.
 cudaError_t launch_analyze(void* f, int fp32, int nx, int ny, int k, const ObsParams& o,
                            double d_cut, double beta, int nmax, int prod, int* flags, void* scratch,
                            const AnalyzeAux* aux, cudaStream_t s);

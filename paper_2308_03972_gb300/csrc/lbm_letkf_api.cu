@@ -443,7 +443,7 @@ int analyze_prepare(lbm_ctx* c, double d_cut, double beta, AnalysisPlan* plan) {
     const int nmax = largest_local_problem(c, d_cut);
     const int plmax = c->geo_pmax;
     // The reduced-precision Gram pass serves ensemble-space points only.
-    const int prod = c->geo_any_ens ? c->prod : PROD_FP64;
+    const int prod = c->geo_any_ens ? c->prod : PROD_NONE;
     const size_t scratch = analyze_scratch_bytes(c->nx, c->ny, is_fp32(c), plmax, nmax, c->k, prod);
     if (scratch > c->ana_scratch_bytes) {
         CK(c, cudaStreamSynchronize(c->stream), "synchronising");

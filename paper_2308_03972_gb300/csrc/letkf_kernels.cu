@@ -22,7 +22,6 @@
 // matrix held in shared memory, one column per lane.
 #include <cmath>
 #include <cstdint>
-#include <type_traits>
 
 #include <cuda_bf16.h>
 
@@ -198,14 +197,11 @@ __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 // diagonal block analytically (a_pp - t a_pq, a_qq + t a_pq, 0), the
 // off-diagonal 2 x 2 blocks (P, Q), P < Q, as J_P^T X J_Q (mirrored), and the
 // rows of U. A rotation is skipped when |a_pq| <= rel ||A||_F; the solve ends
-// after a sweep without one. n <= 2 MAXH (at most MAXH pairs, 32 or 64; rc,
-// rs, rp, rq hold MAXH entries). Returns the number of sweeps (the last one
-// rotating nothing), or -1 if max_sweeps was reached.
-template <typename R, int MAXH = 32>
+// after a sweep without one. n <= 64 (at most 32 pairs). Returns the number
+// of sweeps (the last one rotating nothing), or -1 if max_sweeps was reached.
+template <typename R>
 __device__ int jacobi_sym_warp(R* A, R* U, int n, int ld, int lane, R* rc, R* rs, int* rp,
                                 int* rq, R rel, int max_sweeps) {
-    static_assert(MAXH == 32 || MAXH == 64, "32 or 64 pairs");
-    using Mask = typename std::conditional<(MAXH > 32), unsigned long long, unsigned>::type;
     const int np = n + (n & 1);
     const int half = np / 2;
     const int nb = half * (half - 1) / 2;
@@ -217,65 +213,50 @@ __device__ int jacobi_sym_warp(R* A, R* U, int n, int ld, int lane, R* rc, R* rs
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
         bool any_sweep = false;
         for (int r = 0; r + 1 < np; ++r) {
-            Mask any = 0;
-#pragma unroll
-            for (int pr0 = 0; pr0 < MAXH; pr0 += 32) {
-                const int pr = pr0 + lane;
-                bool rot = false;
-                if (pr < half) {
-                    const int pa = pr, pb = np - 1 - pr;
-                    const int P = pa == 0 ? 0 : 1 + (pa - 1 + r) % (np - 1);
-                    const int Q = 1 + (pb - 1 + r) % (np - 1);
-                    const int p = P < Q ? P : Q, q = P < Q ? Q : P;
-                    R c = R(1), sn = R(0);
-                    if (q < n) {
-                        const R apq = A[p * ld + q];
-                        if (fabs(apq) > thresh) {
-                            // t = phi / (theta + sgn(theta) sqrt(theta^2 + phi^2)),
-                            // theta = a_qq - a_pp, phi = 2 a_pq: the smaller root of
-                            // t^2 + 2 (theta / phi) t - 1 = 0.
-                            const R app = A[p * ld + p], aqq = A[q * ld + q];
-                            const R th = aqq - app, ph = R(2) * apq;
-                            const R rr = sqrt(th * th + ph * ph);
-                            const R t = ph / (th >= R(0) ? th + rr : th - rr);
-                            c = rsq(R(1) + t * t);
-                            sn = t * c;
-                            rot = true;
-                            // Diagonal block of the pair, analytically.
-                            A[p * ld + p] = app - t * apq;
-                            A[q * ld + q] = aqq + t * apq;
-                            A[p * ld + q] = R(0);
-                            A[q * ld + p] = R(0);
-                        }
+            bool rot = false;
+            if (lane < half) {
+                const int pa = lane, pb = np - 1 - lane;
+                const int P = pa == 0 ? 0 : 1 + (pa - 1 + r) % (np - 1);
+                const int Q = 1 + (pb - 1 + r) % (np - 1);
+                const int p = P < Q ? P : Q, q = P < Q ? Q : P;
+                R c = R(1), sn = R(0);
+                if (q < n) {
+                    const R apq = A[p * ld + q];
+                    if (fabs(apq) > thresh) {
+                        // t = phi / (theta + sgn(theta) sqrt(theta^2 + phi^2)),
+                        // theta = a_qq - a_pp, phi = 2 a_pq: the smaller root of
+                        // t^2 + 2 (theta / phi) t - 1 = 0.
+                        const R app = A[p * ld + p], aqq = A[q * ld + q];
+                        const R th = aqq - app, ph = R(2) * apq;
+                        const R rr = sqrt(th * th + ph * ph);
+                        const R t = ph / (th >= R(0) ? th + rr : th - rr);
+                        c = rsq(R(1) + t * t);
+                        sn = t * c;
+                        rot = true;
+                        // Diagonal block of the pair, analytically.
+                        A[p * ld + p] = app - t * apq;
+                        A[q * ld + q] = aqq + t * apq;
+                        A[p * ld + q] = R(0);
+                        A[q * ld + p] = R(0);
                     }
-                    rp[pr] = p;
-                    rq[pr] = q;
-                    rc[pr] = c;
-                    rs[pr] = sn;
                 }
-                any |= (Mask)__ballot_sync(kFull, rot) << pr0;
+                rp[lane] = p;
+                rq[lane] = q;
+                rc[lane] = c;
+                rs[lane] = sn;
             }
+            const unsigned any = __ballot_sync(kFull, rot);
             __syncwarp();
             if (any == 0) continue;
             any_sweep = true;
-            // Off-diagonal blocks (P, Q), P < Q, of the pairs of this round;
-            // block bb is entry Q0 of row P (Q = P + 1 + Q0) in the upper
-            // triangle of the pair matrix.
-            // With 64 pairs a lane advances its previous (P, Q0) by 32 blocks
-            // instead of decoding bb from row 0.
-            int P = 0, Q0 = 0;
+            // Off-diagonal blocks (P, Q), P < Q, of the pairs of this round.
             for (int bb = lane; bb < nb; bb += 32) {
-                if (MAXH == 32 || bb == lane) {
-                    P = 0;
-                    Q0 = bb;
-                } else {
-                    Q0 += 32;
-                }
-                while (Q0 >= half - 1 - P) {
-                    Q0 -= half - 1 - P;
+                int P = 0, Q = bb;
+                while (Q >= half - 1 - P) {
+                    Q -= half - 1 - P;
                     ++P;
                 }
-                const int Q = P + 1 + Q0;
+                Q += P + 1;
                 const bool rP = (any >> P) & 1u, rQ = (any >> Q) & 1u;
                 if (!rP && !rQ) continue;
                 const int pP = rp[P], qP = rq[P], pQ = rp[Q], qQ = rq[Q];
@@ -323,6 +304,139 @@ __device__ int jacobi_sym_warp(R* A, R* U, int n, int ld, int lane, R* rc, R* rs
                 }
             }
             __syncwarp();
+        }
+        if (!any_sweep) return sweep + 1;
+    }
+    return -1;
+}
+
+// The cyclic Jacobi of jacobi_sym_warp (same rotations, same round-robin
+// order) for 65..128 (up to 64 pairs) by a block of NT = 256 threads: the
+// first 64 threads choose and apply the rotations of a round's pairs; then
+// every thread updates off-diagonal blocks and half a row of U (two threads
+// per row, 32 pairs each). The mask of rotated pairs alternates between two
+// shared slots by round parity, so it is not overwritten before every warp
+// has read it. mask: 4 words, red: NT / 32 floats. Binary32.
+template <int NT>
+__device__ int jacobi_sym_block(float* A, float* U, int n, int ld, float* rc, float* rs, int* rp, int* rq,
+                                unsigned* mask, float* red, float rel, int max_sweeps) {
+    static_assert(NT == 256, "two threads per row of U for n <= 128");
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int np = n + (n & 1);
+    const int half = np / 2;
+    const int nb = half * (half - 1) / 2;
+    float fro = 0.0f;
+    for (int e = tid; e < n * n; e += NT) {
+        const float v = A[(e / n) * ld + e % n];
+        fro += v * v;
+    }
+    fro = warp_sum(fro);
+    if (lane == 0) red[w] = fro;
+    __syncthreads();
+    fro = 0.0f;
+    for (int q = 0; q < NT / 32; ++q) fro += red[q];
+    const float thresh = rel * sqrtf(fro);
+    const int urow = tid >> 1, ut0 = (tid & 1) * 32;  // U: this thread's row and first pair
+    int parity = 0;
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+        bool any_sweep = false;
+        for (int r = 0; r + 1 < np; ++r) {
+            unsigned* mk = mask + 2 * parity;
+            parity ^= 1;
+            if (w < 2) {
+                const int pr = tid;
+                bool rot = false;
+                if (pr < half) {
+                    const int pa = pr, pb = np - 1 - pr;
+                    const int P = pa == 0 ? 0 : 1 + (pa - 1 + r) % (np - 1);
+                    const int Q = 1 + (pb - 1 + r) % (np - 1);
+                    const int p = P < Q ? P : Q, q = P < Q ? Q : P;
+                    float c = 1.0f, sn = 0.0f;
+                    if (q < n) {
+                        const float apq = A[p * ld + q];
+                        if (fabsf(apq) > thresh) {
+                            const float app = A[p * ld + p], aqq = A[q * ld + q];
+                            const float th = aqq - app, ph = 2.0f * apq;
+                            const float rr = sqrtf(th * th + ph * ph);
+                            const float t = ph / (th >= 0.0f ? th + rr : th - rr);
+                            c = rsqrtf(1.0f + t * t);
+                            sn = t * c;
+                            rot = true;
+                            A[p * ld + p] = app - t * apq;
+                            A[q * ld + q] = aqq + t * apq;
+                            A[p * ld + q] = 0.0f;
+                            A[q * ld + p] = 0.0f;
+                        }
+                    }
+                    rp[pr] = p;
+                    rq[pr] = q;
+                    rc[pr] = c;
+                    rs[pr] = sn;
+                }
+                const unsigned bal = __ballot_sync(kFull, rot);
+                if (lane == 0) mk[w] = bal;
+            }
+            __syncthreads();
+            const unsigned long long any = mk[0] | ((unsigned long long)mk[1] << 32);
+            if (any == 0) continue;
+            any_sweep = true;
+            // Off-diagonal blocks (P, Q), P < Q: block bb is entry Q0 of row
+            // P of the pair matrix's upper triangle; a thread advances its
+            // previous (P, Q0) by NT blocks.
+            int P = 0, Q0 = 0;
+            for (int bb = tid; bb < nb; bb += NT) {
+                if (bb == tid) {
+                    Q0 = bb;
+                } else {
+                    Q0 += NT;
+                }
+                while (Q0 >= half - 1 - P) {
+                    Q0 -= half - 1 - P;
+                    ++P;
+                }
+                const int Q = P + 1 + Q0;
+                if (!((any >> P) & 1ull) && !((any >> Q) & 1ull)) continue;
+                const int pP = rp[P], qP = rq[P], pQ = rp[Q], qQ = rq[Q];
+                // The padding player of odd n (always a q) reads as zero and
+                // is not written.
+                const bool vP = qP < n, vQ = qQ < n;
+                const float cP = rc[P], sP = rs[P], cQ = rc[Q], sQ = rs[Q];
+                const float x00 = A[pP * ld + pQ];
+                const float x01 = vQ ? A[pP * ld + qQ] : 0.0f;
+                const float x10 = vP ? A[qP * ld + pQ] : 0.0f;
+                const float x11 = (vP && vQ) ? A[qP * ld + qQ] : 0.0f;
+                const float y00 = cP * x00 - sP * x10, y01 = cP * x01 - sP * x11;
+                const float y10 = sP * x00 + cP * x10, y11 = sP * x01 + cP * x11;
+                const float z00 = cQ * y00 - sQ * y01, z01 = sQ * y00 + cQ * y01;
+                const float z10 = cQ * y10 - sQ * y11, z11 = sQ * y10 + cQ * y11;
+                A[pP * ld + pQ] = z00;
+                A[pQ * ld + pP] = z00;
+                if (vQ) {
+                    A[pP * ld + qQ] = z01;
+                    A[qQ * ld + pP] = z01;
+                }
+                if (vP) {
+                    A[qP * ld + pQ] = z10;
+                    A[pQ * ld + qP] = z10;
+                }
+                if (vP && vQ) {
+                    A[qP * ld + qQ] = z11;
+                    A[qQ * ld + qP] = z11;
+                }
+            }
+            // U <- U J on this thread's half row.
+            if (urow < n) {
+                const int t1 = ut0 + 32 < half ? ut0 + 32 : half;
+                for (int t = ut0; t < t1; ++t) {
+                    if (!((any >> t) & 1ull)) continue;
+                    const int p = rp[t], q = rq[t];
+                    const float c = rc[t], sn = rs[t];
+                    const float up = U[urow * ld + p], uq = U[urow * ld + q];
+                    U[urow * ld + p] = c * up - sn * uq;
+                    U[urow * ld + q] = sn * up + c * uq;
+                }
+            }
+            __syncthreads();
         }
         if (!any_sweep) return sweep + 1;
     }
@@ -750,7 +864,8 @@ __device__ int jacobi32_reg(float (&a)[NS], float (&u)[NS], int lane, float rel,
 template <int NS>
 __device__ void jacobi_point(const ObsParams& o, int k, int n, int p, bool obs_space, double aa,
                              const int* lidx, const double* lsq, int lane, float* __restrict__ Xp,
-                             int /*xr = NREG*/, int* flags, const float* __restrict__ Cp) {
+                             int /*xr = NREG*/, int* flags, const float* __restrict__ Cp,
+                             const double* __restrict__ Cd) {
     const int nobs = o.nvar * o.npts;
     float a[NS], u[NS];
     if (obs_space) {
@@ -764,6 +879,10 @@ __device__ void jacobi_point(const ObsParams& o, int k, int n, int p, bool obs_s
         // C from the reduced-precision Gram pass.
 #pragma unroll
         for (int i = 0; i < NS; ++i) a[i] = (lane < n && i < n) ? Cp[i * k + lane] : 0.0f;
+    } else if (Cd) {
+        // C from the FP64 Gram pass, rounded to binary32.
+#pragma unroll
+        for (int i = 0; i < NS; ++i) a[i] = (lane < n && i < n) ? (float)Cd[i * k + lane] : 0.0f;
     } else {
         // C = a I + Yh^T Yh in FP64; lane owns column `lane`.
 #pragma unroll
@@ -803,6 +922,8 @@ struct MixScratch {
     float* C32;    // [chunk][k][k] a I + Yh^T Yh from the reduced-precision Gram, or null
     float* b32;    // [chunk][k] Yh^T d-hat from the same pass, or null
     float* big;    // [chunk][4][nm][ld] kernel (B)'s A and A Y halves when nm > NMID, or null
+    double* C64;   // [chunk][k][k] a I + Yh^T Yh from the FP64 Gram pass, or null
+    double* b64;   // [chunk][k] Yh^T d-hat from the same pass, or null
 };
 
 // Row stride of the basis scratch: 128-byte rows for the register Jacobi.
@@ -817,24 +938,24 @@ __host__ __device__ inline size_t mix_big_floats(int nm) {
     return nm > NMID ? 4 * (size_t)nm * mix_ld(nm) : 0;
 }
 
-// kg: members k when the reduced-precision Gram pass is used (its C and b
-// per point), else 0.
-__host__ __device__ inline size_t mix_scratch_bytes_per_point(int nobs, int nm, int kg) {
+// kg: members k when a Gram pass is used (its C and b per point), else 0;
+// gsz: bytes of its elements (4 reduced precision, 8 FP64).
+__host__ __device__ inline size_t mix_scratch_bytes_per_point(int nobs, int nm, int kg, int gsz) {
     const int xr = mix_xr(nm);
     return (size_t)xr * xr * sizeof(float) + (size_t)nobs * (sizeof(double) + sizeof(int)) +
-           sizeof(int) + (size_t)kg * (kg + 1) * sizeof(float) + mix_big_floats(nm) * sizeof(float);
+           sizeof(int) + (size_t)kg * (kg + 1) * gsz + mix_big_floats(nm) * sizeof(float);
 }
 
 // Grid points per chunk: the double-buffered scratch stays within ~96 MB of L2.
-__host__ __device__ inline long long mix_chunk(long long cells, int nobs, int nm, int kg) {
-    long long c = (48ll << 20) / (long long)mix_scratch_bytes_per_point(nobs, nm, kg);
+__host__ __device__ inline long long mix_chunk(long long cells, int nobs, int nm, int kg, int gsz) {
+    long long c = (48ll << 20) / (long long)mix_scratch_bytes_per_point(nobs, nm, kg, gsz);
     if (c > kChunkCells) c = kChunkCells;
     if (c < 256) c = 256;
     return cells < c ? cells : c;
 }
 
 __host__ __device__ inline MixScratch mix_scratch_at(void* base, long long chunk, int nobs, int nm,
-                                                    int kg) {
+                                                    int kg, int gsz) {
     MixScratch m;
     unsigned char* p = reinterpret_cast<unsigned char*>(base);
     m.X = reinterpret_cast<float*>(p);
@@ -845,18 +966,20 @@ __host__ __device__ inline MixScratch mix_scratch_at(void* base, long long chunk
     p += (size_t)chunk * nobs * sizeof(int);
     m.pcount = reinterpret_cast<int*>(p);
     p += ((size_t)chunk * sizeof(int) + 15) / 16 * 16;
-    m.C32 = kg ? reinterpret_cast<float*>(p) : nullptr;
-    p += (size_t)chunk * kg * kg * sizeof(float);
-    m.b32 = kg ? reinterpret_cast<float*>(p) : nullptr;
-    p += (size_t)chunk * kg * sizeof(float);
+    m.C32 = (kg && gsz == 4) ? reinterpret_cast<float*>(p) : nullptr;
+    m.C64 = (kg && gsz == 8) ? reinterpret_cast<double*>(p) : nullptr;
+    p += (size_t)chunk * kg * kg * gsz;
+    m.b32 = (kg && gsz == 4) ? reinterpret_cast<float*>(p) : nullptr;
+    m.b64 = (kg && gsz == 8) ? reinterpret_cast<double*>(p) : nullptr;
+    p += (size_t)chunk * kg * gsz;
     m.big = nm > NMID ? reinterpret_cast<float*>(p) : nullptr;
     return m;
 }
 
 // Bytes of one scratch buffer, rounded up to 256 so that the second buffer of
 // the pair starts as aligned as the first (its FP64 arrays need 8 bytes).
-__host__ __device__ inline size_t mix_buf_bytes(long long chunk, int nobs, int nm, int kg) {
-    return ((size_t)chunk * mix_scratch_bytes_per_point(nobs, nm, kg) + 16 + 255) / 256 * 256;
+__host__ __device__ inline size_t mix_buf_bytes(long long chunk, int nobs, int nm, int kg, int gsz) {
+    return ((size_t)chunk * mix_scratch_bytes_per_point(nobs, nm, kg, gsz) + 16 + 255) / 256 * 256;
 }
 
 // ---- Local Gram matrices in reduced precision (ensemble-space form) --------
@@ -914,31 +1037,13 @@ __device__ __forceinline__ double local_weight(const ObsParams& o, int j, int x,
     return g > 0.0 ? sqrt(g) : 0.0;
 }
 
-template <int MODE, int K>
-__global__ void __launch_bounds__(32 * kGramPts, 1) local_gram_kernel(int nx, int ny, int k,
-                                                                     ObsParams o, double d_cut,
-                                                                     double aa, int cell0,
-                                                                     int ncell, MixScratch sc) {
-    constexpr int KC = MODE == PROD_TF32 ? 8 : 16;        // rows per stage
-    constexpr int LD = MODE == PROD_TF32 ? K + 8 : K + 4;  // conflict-free fragment reads
-    // Output columns per pass over the rows: all of them up to 64 members;
-    // 32 per pass at 128, so that the accumulators stay at 128 per lane.
-    constexpr int KB = K > 64 ? 32 : K;
-    constexpr int MT = K / 16, NT = KB / 8;
-    constexpr int NCOL = KB > 32 ? 2 : 1;  // output columns per lane and pass (FP32 path)
-    constexpr int NBC = K > 32 ? K / 32 : 1;  // entries of b per lane
-    __shared__ float Ys[KC][LD];
-    __shared__ float Ws[kGramPts][KC];  // rho-tilde = (sqrt(G) / sigma)^2 per point and row
-    __shared__ float Ds[KC];
-    __shared__ int wcount[kGramPts];
-    __shared__ int pcnt[kGramPts];  // local points of each grid point
-    extern __shared__ int U[];  // [npts] merged observation points
+// Merged local sets of the kGramPts grid points cell0 + li0 + q (q < kGramPts,
+// li0 + q < ncell), in increasing point order, into U; pcnt[q] counts the
+// local points of grid point q. Returns the merged count. Block-cooperative
+// (32 kGramPts threads).
+__device__ int gram_merge(const ObsParams& o, int nx, int ny, double d_cut, int cell0, int li0, int ncell,
+                          int* U, int* pcnt, int* wcount) {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int li0 = blockIdx.x * kGramPts;
-    const int nv = o.nvar;
-    const double sig[3] = {o.sigma_u, o.sigma_v, o.sigma_r};
-
-    // Merged local sets, in increasing point order, and each grid point's count.
     if (threadIdx.x < kGramPts) pcnt[threadIdx.x] = 0;
     __syncthreads();
     int total = 0;
@@ -971,6 +1076,34 @@ __global__ void __launch_bounds__(32 * kGramPts, 1) local_gram_kernel(int nx, in
         __syncthreads();
     }
 
+    return total;
+}
+
+template <int MODE, int K>
+__global__ void __launch_bounds__(32 * kGramPts, 1) local_gram_kernel(int nx, int ny, int k,
+                                                                     ObsParams o, double d_cut,
+                                                                     double aa, int cell0,
+                                                                     int ncell, MixScratch sc) {
+    constexpr int KC = MODE == PROD_TF32 ? 8 : 16;        // rows per stage
+    constexpr int LD = MODE == PROD_TF32 ? K + 8 : K + 4;  // conflict-free fragment reads
+    // Output columns per pass over the rows: all of them up to 64 members;
+    // 32 per pass at 128, so that the accumulators stay at 128 per lane.
+    constexpr int KB = K > 64 ? 32 : K;
+    constexpr int MT = K / 16, NT = KB / 8;
+    constexpr int NCOL = KB > 32 ? 2 : 1;  // output columns per lane and pass (FP32 path)
+    constexpr int NBC = K > 32 ? K / 32 : 1;  // entries of b per lane
+    __shared__ float Ys[KC][LD];
+    __shared__ float Ws[kGramPts][KC];  // rho-tilde = (sqrt(G) / sigma)^2 per point and row
+    __shared__ float Ds[KC];
+    __shared__ int wcount[kGramPts];
+    __shared__ int pcnt[kGramPts];  // local points of each grid point
+    extern __shared__ int U[];  // [npts] merged observation points
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int li0 = blockIdx.x * kGramPts;
+    const int nv = o.nvar;
+    const double sig[3] = {o.sigma_u, o.sigma_v, o.sigma_r};
+
+    const int total = gram_merge(o, nx, ny, d_cut, cell0, li0, ncell, U, pcnt, wcount);
     // Only grid points in the ensemble-space form (p >= k) read C and b.
     bool any_ens = false;
     for (int q = 0; q < kGramPts; ++q) any_ens |= pcnt[q] * nv >= k;
@@ -1120,6 +1253,102 @@ __global__ void __launch_bounds__(32 * kGramPts, 1) local_gram_kernel(int nx, in
         if (lane + 32 * c < k) sc.b32[(size_t)li * k + lane + 32 * c] = bacc[c];
 }
 
+// FP64 Gram (PROD_FP64): the same C and b in FP64 products and sums, from
+// the FP64 dY, for the ensemble-space points of a mixed-precision analysis
+// (kernel (A) starts its binary32 Jacobi from C rounded to binary32, kernel
+// (B) refines against C itself). Each lane owns one output column and a
+// range of K / RH rows, so a lane holds at most 64 FP64 accumulators; the
+// output columns are covered in passes of KB.
+template <int K>
+__global__ void __launch_bounds__(32 * kGramPts, 1) local_gram_fp64_kernel(int nx, int ny, int k,
+                                                                          ObsParams o, double d_cut,
+                                                                          double aa, int cell0,
+                                                                          int ncell, MixScratch sc) {
+    constexpr int KC = 16;                          // rows per stage
+    constexpr int RH = K > 64 ? 2 : 1;              // row ranges per column
+    constexpr int KB = (K < 32 ? K : 32) / RH;      // output columns per pass
+    constexpr int MR = K / RH;                      // rows per lane
+    constexpr int NBC = K > 32 ? K / 32 : 1;        // entries of b per lane
+    __shared__ double Ys[KC][K];
+    __shared__ double Ws[kGramPts][KC];
+    __shared__ double Ds[KC];
+    __shared__ int wcount[kGramPts];
+    __shared__ int pcnt[kGramPts];
+    extern __shared__ int U[];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int li0 = blockIdx.x * kGramPts;
+    const int nv = o.nvar;
+    const double sig[3] = {o.sigma_u, o.sigma_v, o.sigma_r};
+    const int total = gram_merge(o, nx, ny, d_cut, cell0, li0, ncell, U, pcnt, wcount);
+    bool any_ens = false;
+    for (int q = 0; q < kGramPts; ++q) any_ens |= pcnt[q] * nv >= k;
+    if (!any_ens) return;
+    const int rows = total * nv;
+    const int li = li0 + w;
+    const int col = lane % KB, rh = lane / KB;
+    const bool act = rh < RH;  // K = 16: lanes 16..31 own no column
+    double acc[MR];
+    double bacc[NBC];
+#pragma unroll
+    for (int c = 0; c < NBC; ++c) bacc[c] = 0.0;
+    for (int cb = 0; cb < K; cb += KB) {
+#pragma unroll
+        for (int m = 0; m < MR; ++m) acc[m] = 0.0;
+        for (int r0 = 0; r0 < rows; r0 += KC) {
+            for (int e = threadIdx.x; e < KC * K; e += 32 * kGramPts) {
+                const int rr = e / K, c = e % K, r = r0 + rr;
+                double v = 0.0;
+                if (r < rows && c < k) v = o.dY[(size_t)(nv * U[r / nv] + r % nv) * k + c];
+                Ys[rr][c] = v;
+            }
+            if (threadIdx.x < KC * kGramPts) {
+                const int q = threadIdx.x / KC, rr = threadIdx.x % KC, r = r0 + rr;
+                double wv = 0.0;
+                if (r < rows && li0 + q < ncell) {
+                    const int cell = cell0 + li0 + q;
+                    const double sg = local_weight(o, U[r / nv], cell % nx, cell / nx, nx, ny, d_cut);
+                    const double l = sg / sig[r % nv];
+                    wv = l * l;
+                }
+                Ws[q][rr] = wv;
+            }
+            if (threadIdx.x < KC) {
+                const int r = r0 + threadIdx.x;
+                Ds[threadIdx.x] = r < rows ? o.d[nv * U[r / nv] + r % nv] : 0.0;
+            }
+            __syncthreads();
+            for (int rr = 0; rr < KC; ++rr) {
+                const double wl = Ws[w][rr];
+                if (wl == 0.0) continue;
+                if (cb == 0) {
+#pragma unroll
+                    for (int c = 0; c < NBC; ++c)
+                        if (lane + 32 * c < K) bacc[c] += wl * Ds[rr] * Ys[rr][lane + 32 * c];
+                }
+                if (act) {
+                    const double wy = wl * Ys[rr][cb + col];
+#pragma unroll
+                    for (int m = 0; m < MR; ++m) acc[m] += Ys[rr][rh * MR + m] * wy;
+                }
+            }
+            __syncthreads();
+        }
+        if (li < ncell && act) {
+            double* C = sc.C64 + (size_t)li * k * k;
+            const int n = cb + col;
+#pragma unroll
+            for (int m = 0; m < MR; ++m) {
+                const int row = rh * MR + m;
+                if (row < k && n < k) C[(size_t)row * k + n] = acc[m] + (row == n ? aa : 0.0);
+            }
+        }
+    }
+    if (li >= ncell) return;
+#pragma unroll
+    for (int c = 0; c < NBC; ++c)
+        if (lane + 32 * c < k) sc.b64[(size_t)li * k + lane + 32 * c] = bacc[c];
+}
+
 __global__ void __launch_bounds__(32 * kJacWarps, 5) mixed_jacobi_kernel(int nx, int ny, int k,
                                                                       ObsParams o, double d_cut,
                                                                       double beta, int cell0,
@@ -1145,24 +1374,23 @@ __global__ void __launch_bounds__(32 * kJacWarps, 5) mixed_jacobi_kernel(int nx,
     constexpr int xr = NREG;  // this kernel serves nm <= NREG
     float* Xp = sc.X + (size_t)li * xr * xr;
     const float* Cp = sc.C32 ? sc.C32 + (size_t)li * k * k : nullptr;
+    const double* Cd = sc.C64 ? sc.C64 + (size_t)li * k * k : nullptr;
     if (n <= 8)
-        jacobi_point<8>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, xr, flags, Cp);
+        jacobi_point<8>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, xr, flags, Cp, Cd);
     else if (n <= 16)
-        jacobi_point<16>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, xr, flags, Cp);
+        jacobi_point<16>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, xr, flags, Cp, Cd);
     else if (n <= 24)
-        jacobi_point<24>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, xr, flags, Cp);
+        jacobi_point<24>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, xr, flags, Cp, Cd);
     else if (n <= 26)
-        jacobi_point<26>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, xr, flags, Cp);
+        jacobi_point<26>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, xr, flags, Cp, Cd);
     else if (n <= 28)
-        jacobi_point<28>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, xr, flags, Cp);
+        jacobi_point<28>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, xr, flags, Cp, Cd);
     else
-        jacobi_point<32>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, xr, flags, Cp);
+        jacobi_point<32>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, xr, flags, Cp, Cd);
 }
 
-// Kernel (A) for local problems of 33..128: the binary32 Jacobi in shared
-// memory (one warp per point, lanes own columns c = lane, lane + 32, ...),
-// same output. MAXH: Jacobi pairs, 32 for n <= 64, 64 for n <= 128.
-template <int MAXH>
+// Kernel (A) for local problems of 33..64: the binary32 Jacobi in shared
+// memory (one warp per point, lanes own two columns), same output.
 __global__ void __launch_bounds__(32) mixed_jacobi_smem_kernel(int nx, int ny, int k, ObsParams o,
                                                                double d_cut, double beta, int cell0,
                                                                int nm, MixScratch sc,
@@ -1173,9 +1401,9 @@ __global__ void __launch_bounds__(32) mixed_jacobi_smem_kernel(int nx, int ny, i
     float* A = reinterpret_cast<float*>(smem_raw);
     float* U = A + (size_t)nm * ld;
     float* rc = U + (size_t)nm * ld;
-    float* rs = rc + MAXH;
-    int* rp = reinterpret_cast<int*>(rs + MAXH);
-    int* rq = rp + MAXH;
+    float* rs = rc + 32;
+    int* rp = reinterpret_cast<int*>(rs + 32);
+    int* rq = rp + 32;
     const int lane = threadIdx.x;
     const int li = blockIdx.x;
     const int cell = cell0 + li;
@@ -1198,6 +1426,9 @@ __global__ void __launch_bounds__(32) mixed_jacobi_smem_kernel(int nx, int ny, i
         } else if (sc.C32) {
             const float* Cp = sc.C32 + (size_t)li * k * k;
             for (int i = 0; i < n; ++i) A[i * ld + c] = Cp[i * k + c];
+        } else if (sc.C64) {
+            const double* Cd = sc.C64 + (size_t)li * k * k;
+            for (int i = 0; i < n; ++i) A[i * ld + c] = (float)Cd[i * k + c];
         } else {
             for (int i = 0; i < n; ++i) {
                 double s = (i == c) ? aa : 0.0;
@@ -1213,7 +1444,7 @@ __global__ void __launch_bounds__(32) mixed_jacobi_smem_kernel(int nx, int ny, i
     __syncwarp();
     // Stop at 1e-6 ||A||_F, as the register Jacobi does: the refinement of
     // kernel (B) is second order in what remains.
-    const int sweeps = jacobi_sym_warp<float, MAXH>(A, U, n, ld, lane, rc, rs, rp, rq, 1e-6f, kMaxSweeps);
+    const int sweeps = jacobi_sym_warp<float>(A, U, n, ld, lane, rc, rs, rp, rq, 1e-6f, kMaxSweeps);
     if (sweeps < 0 && lane == 0) atomicOr(flags, FLAG_NOCONV);
     record_sweeps(o, sweeps, lane);
     __syncwarp();
@@ -1221,6 +1452,86 @@ __global__ void __launch_bounds__(32) mixed_jacobi_smem_kernel(int nx, int ny, i
     float* Xp = sc.X + (size_t)li * xr * xr;
     for (int c = lane; c < n; c += 32)
         for (int i = 0; i < n; ++i) Xp[(size_t)i * xr + c] = U[i * ld + c];
+}
+
+// Kernel (A) for local problems of 65..128: the binary32 Jacobi of
+// jacobi_sym_block, kBlkThreads threads per grid point, same output.
+constexpr int kBlkThreads = 256;
+
+__host__ __device__ inline size_t jacobi_block_smem_bytes(int nm) {
+    return 2 * (size_t)nm * (nm + 1) * sizeof(float) + 64 * (2 * sizeof(float) + 2 * sizeof(int)) +
+           4 * sizeof(unsigned) + (kBlkThreads / 32) * sizeof(float) + sizeof(int);
+}
+
+__global__ void __launch_bounds__(kBlkThreads) mixed_jacobi_block_kernel(int nx, int ny, int k, ObsParams o,
+                                                                         double d_cut, double beta,
+                                                                         int cell0, int nm, MixScratch sc,
+                                                                         int* __restrict__ flags) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nobs = o.nvar * o.npts;
+    const int ld = nm + 1;
+    float* A = reinterpret_cast<float*>(smem_raw);
+    float* U = A + (size_t)nm * ld;
+    float* rc = U + (size_t)nm * ld;
+    float* rs = rc + 64;
+    int* rp = reinterpret_cast<int*>(rs + 64);
+    int* rq = rp + 64;
+    unsigned* mask = reinterpret_cast<unsigned*>(rq + 64);
+    float* red = reinterpret_cast<float*>(mask + 4);
+    int* pshare = reinterpret_cast<int*>(red + kBlkThreads / 32);
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int li = blockIdx.x;
+    const int cell = cell0 + li;
+    const int x = cell % nx, y = cell / nx;
+    const int cap = o.plmax > 0 ? o.plmax : nobs;
+    double* lsq = sc.lsq + (size_t)li * cap;
+    int* lidx = sc.lidx + (size_t)li * cap;
+    if (w == 0) {
+        const int p = local_set(o, x, y, nx, ny, d_cut, lane, lidx, lsq, cap);
+        if (lane == 0) {
+            sc.pcount[li] = p;
+            *pshare = p;
+        }
+    }
+    __syncthreads();
+    const int p = *pshare;
+    if (p == 0 || p > cap) return;  // p > cap: reported by kernel (B)
+    const bool obs_space = p < k;
+    const int n = obs_space ? p : k;
+    if (n > nm) return;  // reported by kernel (B)
+    const double aa = (k - 1) / beta;
+    for (int e = tid; e < n * n; e += kBlkThreads) {
+        const int i = e / n, c = e % n;
+        float v;
+        if (obs_space) {
+            v = (float)(lsq[i] * o.G[(size_t)lidx[i] * nobs + lidx[c]] * lsq[c]);
+        } else if (sc.C32) {
+            v = sc.C32[(size_t)li * k * k + (size_t)i * k + c];
+        } else if (sc.C64) {
+            v = (float)sc.C64[(size_t)li * k * k + (size_t)i * k + c];
+        } else {
+            double s = (i == c) ? aa : 0.0;
+            for (int l = 0; l < p; ++l) {
+                const double* row = o.dY + (size_t)lidx[l] * k;
+                s += lsq[l] * lsq[l] * row[i] * row[c];
+            }
+            v = (float)s;
+        }
+        A[i * ld + c] = v;
+        U[i * ld + c] = (i == c) ? 1.0f : 0.0f;
+    }
+    __syncthreads();
+    // Stop at 1e-6 ||A||_F: the refinement of kernel (B) is second order in
+    // what remains.
+    const int sweeps = jacobi_sym_block<kBlkThreads>(A, U, n, ld, rc, rs, rp, rq, mask, red, 1e-6f, kMaxSweeps);
+    if (sweeps < 0 && tid == 0) atomicOr(flags, FLAG_NOCONV);
+    if (w == 0) record_sweeps(o, sweeps, lane);
+    const int xr = mix_xr(nm);
+    float* Xp = sc.X + (size_t)li * xr * xr;
+    for (int e = tid; e < n * n; e += kBlkThreads) {
+        const int i = e / n, c = e % n;
+        Xp[(size_t)i * xr + c] = U[i * ld + c];
+    }
 }
 
 // Shared memory of kernel (B). The matrices are nm x ld with nm the largest
@@ -1513,6 +1824,10 @@ __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f
                 sm.Al[i * ld + c] = 0.0f;
             }
             sm.vb[c] = (double)sc.b32[(size_t)li * k + c];
+        } else if (sc.C64) {
+            const double* Cd = sc.C64 + (size_t)li * k * k;
+            for (int i = 0; i < n; ++i) put(i, c, Cd[i * k + c]);
+            sm.vb[c] = sc.b64[(size_t)li * k + c];
         } else {
             double bj = 0.0;
             for (int i = 0; i < n; ++i) {
@@ -1761,11 +2076,12 @@ cudaError_t launch_obs_gram(const double* dY, int nobs, int k, double* G, cudaSt
 
 static int mixed_nm(int nmax) { return nmax < 2 ? 2 : (nmax > NMAX ? NMAX : nmax); }
 
-// Members k when the reduced-precision Gram pass runs (mixed precision, a
-// reduced product mode, k <= 128), else 0.
+// Members k when a Gram pass runs (mixed precision, some ensemble-space grid
+// point, k <= 128), else 0; the bytes of its elements.
 static int gram_k(int fp32, int k, int prod) {
-    return (fp32 && prod != PROD_FP64 && k <= NMAX) ? k : 0;
+    return (fp32 && prod != PROD_NONE && k <= NMAX) ? k : 0;
 }
+static int gram_sz(int prod) { return prod == PROD_FP64 ? 8 : 4; }
 
 template <int MODE>
 static cudaError_t launch_gram_mode(int nx, int ny, int k, const ObsParams& o, double d_cut,
@@ -1781,14 +2097,22 @@ static cudaError_t launch_gram_mode(int nx, int ny, int k, const ObsParams& o, d
         kern<<<grid, 32 * kGramPts, sh, s>>>(nx, ny, k, o, d_cut, aa, cell0, nc, sc);
         return cudaGetLastError();
     };
-    if (k <= 16) return go(local_gram_kernel<MODE, 16>);
-    if (k <= 32) return go(local_gram_kernel<MODE, 32>);
-    if (k <= 64) return go(local_gram_kernel<MODE, 64>);
-    return go(local_gram_kernel<MODE, 128>);
+    if constexpr (MODE == PROD_FP64) {
+        if (k <= 16) return go(local_gram_fp64_kernel<16>);
+        if (k <= 32) return go(local_gram_fp64_kernel<32>);
+        if (k <= 64) return go(local_gram_fp64_kernel<64>);
+        return go(local_gram_fp64_kernel<128>);
+    } else {
+        if (k <= 16) return go(local_gram_kernel<MODE, 16>);
+        if (k <= 32) return go(local_gram_kernel<MODE, 32>);
+        if (k <= 64) return go(local_gram_kernel<MODE, 64>);
+        return go(local_gram_kernel<MODE, 128>);
+    }
 }
 
 static cudaError_t launch_gram(int prod, int nx, int ny, int k, const ObsParams& o, double d_cut,
                                double aa, int cell0, int nc, const MixScratch& sc, cudaStream_t s) {
+    if (prod == PROD_FP64) return launch_gram_mode<PROD_FP64>(nx, ny, k, o, d_cut, aa, cell0, nc, sc, s);
     if (prod == PROD_FP32) return launch_gram_mode<PROD_FP32>(nx, ny, k, o, d_cut, aa, cell0, nc, sc, s);
     if (prod == PROD_TF32) return launch_gram_mode<PROD_TF32>(nx, ny, k, o, d_cut, aa, cell0, nc, sc, s);
     return launch_gram_mode<PROD_BF16>(nx, ny, k, o, d_cut, aa, cell0, nc, sc, s);
@@ -1797,9 +2121,9 @@ static cudaError_t launch_gram(int prod, int nx, int ny, int k, const ObsParams&
 size_t analyze_scratch_bytes(int nx, int ny, int fp32, int nl, int nmax, int k, int prod) {
     if (!fp32) return 0;
     const int nm = mixed_nm(nmax);
-    const int kg = gram_k(fp32, k, prod);
-    const long long chunk = mix_chunk((long long)nx * ny, nl, nm, kg);
-    return 2 * mix_buf_bytes(chunk, nl, nm, kg);  // double-buffered
+    const int kg = gram_k(fp32, k, prod), gsz = gram_sz(prod);
+    const long long chunk = mix_chunk((long long)nx * ny, nl, nm, kg, gsz);
+    return 2 * mix_buf_bytes(chunk, nl, nm, kg, gsz);  // double-buffered
 }
 
 cudaError_t launch_analyze(void* f, int fp32, int nx, int ny, int k, const ObsParams& o,
@@ -1816,23 +2140,24 @@ cudaError_t launch_analyze(void* f, int fp32, int nx, int ny, int k, const ObsPa
         to_f32_kernel<<<(unsigned)((nd + 255) / 256), 256, 0, s>>>(o.dY, o.dY32, nd);
         const int cap = o.plmax > 0 ? o.plmax : nobs;
         const size_t shB = mix_smem_bytes(k, cap, nm);
-        const int maxh = nm > NMID ? 64 : 32;  // Jacobi pairs of kernel (A) in shared memory
-        const size_t shA = nm > NREG ? 2 * (size_t)nm * (nm + 1) * sizeof(float) +
-                                           2 * (size_t)maxh * (sizeof(float) + sizeof(int))
-                                     : 0;
         const bool wide = nm > NREG, big = nm > NMID;
+        const size_t shA = big ? jacobi_block_smem_bytes(nm)
+                               : (wide ? 2 * (size_t)nm * (nm + 1) * sizeof(float) + 64 * (sizeof(float) + sizeof(int))
+                                       : 0);
         auto kernB = big ? analyze_mixed_kernel<true, true>
                          : (wide ? analyze_mixed_kernel<true, false> : analyze_mixed_kernel<false, false>);
-        auto kernA = big ? mixed_jacobi_smem_kernel<64> : mixed_jacobi_smem_kernel<32>;
         e = cudaFuncSetAttribute(kernB, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shB);
         if (e != cudaSuccess) return e;
-        if (nm > NREG) {
-            e = cudaFuncSetAttribute(kernA, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shA);
+        if (wide) {
+            e = big ? cudaFuncSetAttribute(mixed_jacobi_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)shA)
+                    : cudaFuncSetAttribute(mixed_jacobi_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)shA);
             if (e != cudaSuccess) return e;
         }
-        const int kg = gram_k(fp32, k, prod);
-        const long long chunk = mix_chunk(cells, cap, nm, kg);
-        const size_t buf_bytes = mix_buf_bytes(chunk, cap, nm, kg);
+        const int kg = gram_k(fp32, k, prod), gsz = gram_sz(prod);
+        const long long chunk = mix_chunk(cells, cap, nm, kg, gsz);
+        const size_t buf_bytes = mix_buf_bytes(chunk, cap, nm, kg, gsz);
         // Pipeline: (A) of chunk c on s2 overlaps (B) of chunk c-1 on s; the
         // scratch is double-buffered, (A) of chunk c waits for (B) of c-2.
         if ((e = cudaEventRecord(aux->start, s)) != cudaSuccess) return e;
@@ -1842,7 +2167,7 @@ cudaError_t launch_analyze(void* f, int fp32, int nx, int ny, int k, const ObsPa
             const int nc = (int)((cells - c0) < chunk ? (cells - c0) : chunk);
             const int b = c & 1;
             const MixScratch sc =
-                mix_scratch_at((unsigned char*)scratch + b * buf_bytes, chunk, cap, nm, kg);
+                mix_scratch_at((unsigned char*)scratch + b * buf_bytes, chunk, cap, nm, kg, gsz);
             if (c >= 2 && (e = cudaStreamWaitEvent(aux->s2, aux->ref_done[b], 0)) != cudaSuccess)
                 return e;
             if (kg && (e = launch_gram(prod, nx, ny, k, o, d_cut, (k - 1) / beta, (int)c0, nc, sc,
@@ -1851,8 +2176,12 @@ cudaError_t launch_analyze(void* f, int fp32, int nx, int ny, int k, const ObsPa
             if (nm <= NREG)
                 mixed_jacobi_kernel<<<(unsigned)((nc + kJacWarps - 1) / kJacWarps), 32 * kJacWarps, 0,
                                       aux->s2>>>(nx, ny, k, o, d_cut, beta, (int)c0, nc, nm, sc, flags);
+            else if (!big)
+                mixed_jacobi_smem_kernel<<<(unsigned)nc, 32, shA, aux->s2>>>(nx, ny, k, o, d_cut, beta,
+                                                                              (int)c0, nm, sc, flags);
             else
-                kernA<<<(unsigned)nc, 32, shA, aux->s2>>>(nx, ny, k, o, d_cut, beta, (int)c0, nm, sc, flags);
+                mixed_jacobi_block_kernel<<<(unsigned)nc, kBlkThreads, shA, aux->s2>>>(nx, ny, k, o, d_cut, beta,
+                                                                                       (int)c0, nm, sc, flags);
             if ((e = cudaEventRecord(aux->jac_done[b], aux->s2)) != cudaSuccess) return e;
             if ((e = cudaStreamWaitEvent(s, aux->jac_done[b], 0)) != cudaSuccess) return e;
             kernB<<<(unsigned)nc, 32, shB, s>>>((float*)f, nx, ny, k, o, d_cut, beta, (int)c0, nm, sc, flags);
