@@ -177,15 +177,25 @@ __device__ int local_set(const ObsParams& o, int x, int y, int nx, int ny, doubl
 }
 
 // ------------------------------------------------------------------ K3, FP64
-// Apply body(c) to the columns c a lane owns: c = lane when every problem
-// fits one lane per column (WIDE = false), else c = lane, lane + 32, ...
-template <bool WIDE, typename F>
-__device__ __forceinline__ void for_cols(int lane, int n, F&& body) {
+// Apply body(c) to the columns c a thread owns: c = lane when every problem
+// fits one lane per column (WIDE = false), else c = t, t + 32 NW, ... for
+// thread t of NW warps.
+template <bool WIDE, int NW = 1, typename F>
+__device__ __forceinline__ void for_cols(int t, int n, F&& body) {
     if (WIDE) {
-        for (int c = lane; c < n; c += 32) body(c);
-    } else if (lane < n) {
-        body(lane);
+        for (int c = t; c < n; c += 32 * NW) body(c);
+    } else if (t < n) {
+        body(t);
     }
+}
+
+// Barrier of the NW warps that share a grid point.
+template <int NW>
+__device__ __forceinline__ void point_sync() {
+    if (NW == 1)
+        __syncwarp();
+    else
+        __syncthreads();
 }
 
 __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
@@ -947,10 +957,14 @@ __host__ __device__ inline size_t mix_scratch_bytes_per_point(int nobs, int nm, 
 }
 
 // Grid points per chunk: the double-buffered scratch stays within ~96 MB of L2.
+// Above NMID both kernels hold one grid point per SM; their chunks are at
+// least four full waves of GB300's 152 SMs (the scratch then exceeds L2,
+// but only the grid points in flight are live at a time).
 __host__ __device__ inline long long mix_chunk(long long cells, int nobs, int nm, int kg, int gsz) {
     long long c = (48ll << 20) / (long long)mix_scratch_bytes_per_point(nobs, nm, kg, gsz);
     if (c > kChunkCells) c = kChunkCells;
-    if (c < 256) c = 256;
+    const long long cmin = nm > NMID ? 4 * 152 : 256;
+    if (c < cmin) c = cmin;
     return cells < c ? cells : c;
 }
 
@@ -1457,6 +1471,7 @@ __global__ void __launch_bounds__(32) mixed_jacobi_smem_kernel(int nx, int ny, i
 // Kernel (A) for local problems of 65..128: the binary32 Jacobi of
 // jacobi_sym_block, kBlkThreads threads per grid point, same output.
 constexpr int kBlkThreads = 256;
+constexpr int kBigWarps = 4;  // warps per grid point of kernel (B) above NMID
 
 __host__ __device__ inline size_t jacobi_block_smem_bytes(int nm) {
     return 2 * (size_t)nm * (nm + 1) * sizeof(float) + 64 * (2 * sizeof(float) + 2 * sizeof(int)) +
@@ -1654,11 +1669,12 @@ __device__ __forceinline__ double df_value(float s, float c) { return (double)s 
 
 // C = P^T Q over the upper triangle (mirrored) in double-binary32: P binary32,
 // Q = Qhi + Qlo (Qlo may be null). store(i, j, value) writes both halves.
-template <typename Store>
-__device__ void sym_product_df(const float* P, const float* Qhi, const float* Qlo, int n, int ld, int lane,
+// Thread t of NW warps takes entries t, t + 32 NW, ...
+template <int NW = 1, typename Store>
+__device__ void sym_product_df(const float* P, const float* Qhi, const float* Qlo, int n, int ld, int t,
                                Store&& store) {
     const int ne = n * (n + 1) / 2;
-    for (int e0 = lane; e0 < ne; e0 += 32) {
+    for (int e0 = t; e0 < ne; e0 += 32 * NW) {
         int i = 0, j = e0;
         while (j >= n - i) {
             j -= n - i;
@@ -1686,17 +1702,17 @@ __device__ void sym_product_df(const float* P, const float* Qhi, const float* Ql
 // diagonal of S' in dS (FP64) and its off-diagonal in Soff (binary32: the
 // entries are ~1e-6 of |A| and enter the matrix functions to first order).
 // Soff may alias Ah (A is not read after A Y).
-template <bool WIDE>
+template <bool WIDE, int NW = 1>
 __device__ void refine_rr(const float* Ah, const float* Al, const float* Y32, float* Wh, float* Wl,
-                          float* E32, float* Soff, double* dS, int n, int ld, int lane) {
+                          float* E32, float* Soff, double* dS, int n, int ld, int t) {
     // E = Y^T Y - I.
-    sym_product_df(Y32, Y32, nullptr, n, ld, lane, [&](int i, int j, double v) {
+    sym_product_df<NW>(Y32, Y32, nullptr, n, ld, t, [&](int i, int j, double v) {
         const float e = (float)(v - (i == j ? 1.0 : 0.0));
         E32[i * ld + j] = e;
         E32[j * ld + i] = e;
     });
     // W = A Y, column col: four rows at a time, then the remainder.
-    for_cols<WIDE>(lane, n, [&](int col) {
+    for_cols<WIDE, NW>(t, n, [&](int col) {
         int i0 = 0;
         for (; i0 + 3 < n; i0 += 4) {
             float s[4] = {0.0f, 0.0f, 0.0f, 0.0f}, c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
@@ -1715,9 +1731,9 @@ __device__ void refine_rr(const float* Ah, const float* Al, const float* Y32, fl
             two_sum(s, c, Wh[i0 * ld + col], Wl[i0 * ld + col]);
         }
     });
-    __syncwarp();
+    point_sync<NW>();
     // S = Y^T (A Y), symmetric: diagonal to dS, off-diagonal to Soff.
-    sym_product_df(Y32, Wh, Wl, n, ld, lane, [&](int i, int j, double v) {
+    sym_product_df<NW>(Y32, Wh, Wl, n, ld, t, [&](int i, int j, double v) {
         if (i == j) {
             dS[i] = v;
         } else {
@@ -1725,24 +1741,24 @@ __device__ void refine_rr(const float* Ah, const float* Al, const float* Y32, fl
             Soff[j * ld + i] = (float)v;
         }
     });
-    __syncwarp();
-    // S' = S - E o (d_i + d_j)/2 (the diagonal last, after every lane has
+    point_sync<NW>();
+    // S' = S - E o (d_i + d_j)/2 (the diagonal last, after every thread has
     // read the uncorrected one).
-    for_cols<WIDE>(lane, n, [&](int c) {
+    for_cols<WIDE, NW>(t, n, [&](int c) {
         const double dc = dS[c];
         for (int i = 0; i < n; ++i)
             if (i != c)
                 Soff[i * ld + c] = (float)((double)Soff[i * ld + c] - (double)E32[i * ld + c] * 0.5 * (dS[i] + dc));
     });
-    __syncwarp();
-    for_cols<WIDE>(lane, n, [&](int c) { dS[c] -= (double)E32[c * ld + c] * dS[c]; });
-    __syncwarp();
+    point_sync<NW>();
+    for_cols<WIDE, NW>(t, n, [&](int c) { dS[c] -= (double)E32[c * ld + c] * dS[c]; });
+    point_sync<NW>();
 }
 
 // BIG (nm > NMID): A and A Y in global scratch (L2-resident), the rest as
-// below.
-template <bool WIDE, bool BIG>
-__global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f, int nx, int ny,
+// below. NW warps share a grid point (1 up to NMID).
+template <bool WIDE, bool BIG, int NW>
+__global__ void __launch_bounds__(32 * NW) analyze_mixed_kernel(float* __restrict__ f, int nx, int ny,
                                                            int k, ObsParams o, double d_cut,
                                                            double beta, int cell0, int nm,
                                                            MixScratch sc,
@@ -1753,13 +1769,14 @@ __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f
     const int li = blockIdx.x;
     MixSmem sm = carve_mix(smem_raw, k, cap, nm, BIG ? sc.big + (size_t)li * mix_big_floats(nm) : nullptr);
     const int ld = mix_ld(nm);
-    const int lane = threadIdx.x;
+    constexpr int NTH = 32 * NW;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int cell = cell0 + li;
     const size_t plane = (size_t)nx * ny * k;
     float* fc = f + (size_t)cell * k;
 
     // Ensemble mean and perturbations in binary32.
-    for (int a = 0; a < 9; ++a) {
+    for (int a = wid; a < 9; a += NW) {  // one warp per component
         float s = 0.0f;
         for (int m = lane; m < k; m += 32) {
             const float xv = fc[a * plane + m];
@@ -1774,28 +1791,28 @@ __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f
     // Local set from kernel (A).
     const int p = sc.pcount[li];
     if (p > cap) {
-        if (lane == 0) atomicOr(flags, FLAG_TOOLARGE);
+        if (tid == 0) atomicOr(flags, FLAG_TOOLARGE);
         return;
     }
-    for (int i = lane; i < p; i += 32) {
+    for (int i = tid; i < p; i += NTH) {
         const int oi = sc.lidx[(size_t)li * cap + i];
         const double si = sc.lsq[(size_t)li * cap + i];
         sm.lidx[i] = oi;
         sm.lsq[i] = si;
         sm.ldh[i] = si * o.d[oi];
     }
-    __syncwarp();
+    point_sync<NW>();
 
     if (p == 0) {
         const float sb = (float)sqrt(beta);
         for (int a = 0; a < 9; ++a)
-            for (int m = lane; m < k; m += 32) fc[a * plane + m] = sm.xbar[a] + sb * sm.dX[a * k + m];
+            for (int m = tid; m < k; m += NTH) fc[a * plane + m] = sm.xbar[a] + sb * sm.dX[a * k + m];
         return;
     }
     const bool obs_space = p < k;
     const int n = obs_space ? p : k;
     if (n > nm) {
-        if (lane == 0) atomicOr(flags, FLAG_TOOLARGE);
+        if (tid == 0) atomicOr(flags, FLAG_TOOLARGE);
         return;
     }
     const double aa = (k - 1) / beta;
@@ -1811,7 +1828,7 @@ __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f
     // from kernel (A).
     const int xr = WIDE ? mix_xr(nm) : NREG;
     const float* Xp = sc.X + (size_t)li * xr * xr;
-    for_cols<WIDE>(lane, n, [&](int c) {
+    for_cols<WIDE, NW>(tid, n, [&](int c) {
         if (obs_space) {
             const int oc = sm.lidx[c];
             const double sl = sm.lsq[c];
@@ -1843,8 +1860,8 @@ __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f
         }
         for (int i = 0; i < n; ++i) sm.Y32[i * ld + c] = Xp[(size_t)i * xr + c];
     });
-    __syncwarp();
-    refine_rr<WIDE>(sm.Ah, sm.Al, sm.Y32, sm.Wh, sm.Wl, sm.E32, sm.Ah, sm.dS, n, ld, lane);
+    point_sync<NW>();
+    refine_rr<WIDE, NW>(sm.Ah, sm.Al, sm.Y32, sm.Wh, sm.Wl, sm.E32, sm.Ah, sm.dS, n, ld, tid);
     const float* E32 = sm.E32;
     const float* Soff = sm.Ah;  // S' off the diagonal; its diagonal is dS
     float* Y32 = sm.Y32;
@@ -1855,7 +1872,7 @@ __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f
         // Functions of a + S: h = 1/(a+s) for the weights, g(s) = q[s, 0] with
         // q(s) = (a+s)^{-1/2} for the square root. u_i = sqrt(a + s_ii).
         const double r = sqrt(aa);
-        for_cols<WIDE>(lane, n, [&](int c) {
+        for_cols<WIDE, NW>(tid, n, [&](int c) {
             const double sii = sm.dS[c];
             const double u = sqrt(aa + sii);
             sm.vu[c] = u;
@@ -1866,8 +1883,8 @@ __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f
             for (int l = 0; l < n; ++l) t += Y32[l * ld + c] * (float)sm.ldh[l];
             sm.t1f[c] = t;
         });
-        __syncwarp();
-        for_cols<WIDE>(lane, n, [&](int c) {
+        point_sync<NW>();
+        for_cols<WIDE, NW>(tid, n, [&](int c) {
             // t2 = h(S) t1 with h(S)_ii = h_i, h(S)_ij = -s_ij h_i h_j, and the
             // basis factor: minus E o (h_i + h_j)/2.
             const float hi = (float)sm.vb[c];
@@ -1896,8 +1913,8 @@ __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f
                 F32[i * ld + c] = v - E32[i * ld + c] * (0.5f * (gc - aj / rf));
             }
         });
-        __syncwarp();
-        for_cols<WIDE>(lane, n, [&](int c) {
+        point_sync<NW>();
+        for_cols<WIDE, NW>(tid, n, [&](int c) {
             float t = 0.0f;
             for (int l = 0; l < n; ++l) t += Y32[c * ld + l] * sm.t2f[l];
             sm.vf[c] = t;  // v = (a I + A)^{-1} d-hat
@@ -1915,13 +1932,13 @@ __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f
 #pragma unroll
             for (int a = 0; a < 9; ++a) sm.Z[a * nm + c] = sl * acc[a];
         });
-        __syncwarp();
-        if (lane < 9) {
+        point_sync<NW>();
+        if (tid < 9) {
             float s = 0.0f;
-            for (int i = 0; i < n; ++i) s += sm.Z[lane * nm + i] * sm.vf[i];
-            sm.zv[lane] = s;
+            for (int i = 0; i < n; ++i) s += sm.Z[tid * nm + i] * sm.vf[i];
+            sm.zv[tid] = s;
         }
-        for_cols<WIDE>(lane, n, [&](int col) {
+        for_cols<WIDE, NW>(tid, n, [&](int col) {
             float acc[9];
 #pragma unroll
             for (int a = 0; a < 9; ++a) acc[a] = 0.0f;
@@ -1933,8 +1950,8 @@ __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f
 #pragma unroll
             for (int a = 0; a < 9; ++a) sm.B[a * nm + col] = acc[a];  // Z Y
         });
-        __syncwarp();
-        for_cols<WIDE>(lane, n, [&](int col) {
+        point_sync<NW>();
+        for_cols<WIDE, NW>(tid, n, [&](int col) {
             float acc[9];
 #pragma unroll
             for (int a = 0; a < 9; ++a) acc[a] = 0.0f;
@@ -1946,8 +1963,8 @@ __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f
 #pragma unroll
             for (int a = 0; a < 9; ++a) sm.Z[a * nm + col] = acc[a];  // Z Y g(S)
         });
-        __syncwarp();
-        for_cols<WIDE>(lane, n, [&](int col) {
+        point_sync<NW>();
+        for_cols<WIDE, NW>(tid, n, [&](int col) {
             float acc[9];
 #pragma unroll
             for (int a = 0; a < 9; ++a) acc[a] = 0.0f;
@@ -1960,9 +1977,9 @@ __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f
 #pragma unroll
             for (int a = 0; a < 9; ++a) sm.B[a * nm + col] = sl * acc[a];  // sqrt(k-1) Z g(A) sqrt(rho)
         });
-        __syncwarp();
+        point_sync<NW>();
         const float sb = (float)sqrt(beta);
-        for (int m = lane; m < k; m += 32) {
+        for (int m = tid; m < k; m += NTH) {
             float acc[9];
 #pragma unroll
             for (int a = 0; a < 9; ++a) acc[a] = sm.xbar[a] + sm.zv[a] + sb * sm.dX[a * k + m];
@@ -1976,7 +1993,7 @@ __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f
         }
     } else {
         // Functions of S directly: 1/lambda for P-tilde, lambda^{-1/2} for W.
-        for_cols<WIDE>(lane, n, [&](int c) {
+        for_cols<WIDE, NW>(tid, n, [&](int c) {
             const double lam = sm.dS[c];
             sm.vu[c] = sqrt(lam);
             sm.vinv[c] = 1.0 / lam;
@@ -1984,8 +2001,8 @@ __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f
             for (int l = 0; l < n; ++l) t += Y32[l * ld + c] * (float)sm.vb[l];
             sm.t1f[c] = t;  // Y^T b
         });
-        __syncwarp();
-        for_cols<WIDE>(lane, n, [&](int c) {
+        point_sync<NW>();
+        for_cols<WIDE, NW>(tid, n, [&](int c) {
             // t2 = f1(S) t1, f1(S)_ii = 1/l_i, f1(S)_ij = -s_ij / (l_i l_j), and
             // the basis factor: minus E o (f1_i + f1_j)/2.
             const float fc1 = (float)sm.vinv[c];
@@ -2010,32 +2027,32 @@ __global__ void __launch_bounds__(32) analyze_mixed_kernel(float* __restrict__ f
                 F32[i * ld + c] = v - E32[i * ld + c] * (0.5f * (1.0f / si + 1.0f / sj));
             }
         });
-        __syncwarp();
+        point_sync<NW>();
         float* YF = sm.Al;  // A's low half is no longer needed
-        for_cols<WIDE>(lane, n, [&](int c) {
+        for_cols<WIDE, NW>(tid, n, [&](int c) {
             float t = 0.0f;
             for (int l = 0; l < n; ++l) t += Y32[c * ld + l] * sm.t2f[l];
             sm.vf[c] = t;  // w-bar
         });
-        __syncwarp();
-        for_cols<WIDE>(lane, n, [&](int c) {
+        point_sync<NW>();
+        for_cols<WIDE, NW>(tid, n, [&](int c) {
             for (int i = 0; i < n; ++i) {
                 float s = 0.0f;
                 for (int l = 0; l < n; ++l) s += Y32[i * ld + l] * F32[l * ld + c];
                 YF[i * ld + c] = s;
             }
     });
-        __syncwarp();
+        point_sync<NW>();
         // T = sqrt(k-1) Y f2(S) Y^T + w-bar 1^T, over F32.
-        for_cols<WIDE>(lane, n, [&](int c) {
+        for_cols<WIDE, NW>(tid, n, [&](int c) {
             for (int i = 0; i < n; ++i) {
                 float s = 0.0f;
                 for (int l = 0; l < n; ++l) s += YF[i * ld + l] * Y32[c * ld + l];
                 F32[i * ld + c] = sk * s + sm.vf[i];
             }
     });
-        __syncwarp();
-        for (int m = lane; m < k; m += 32) {
+        point_sync<NW>();
+        for (int m = tid; m < k; m += NTH) {
             for (int a = 0; a < 9; ++a) {
                 float s = 0.0f;
                 for (int j = 0; j < k; ++j) s += sm.dX[a * k + j] * F32[j * ld + m];
@@ -2144,8 +2161,10 @@ cudaError_t launch_analyze(void* f, int fp32, int nx, int ny, int k, const ObsPa
         const size_t shA = big ? jacobi_block_smem_bytes(nm)
                                : (wide ? 2 * (size_t)nm * (nm + 1) * sizeof(float) + 64 * (sizeof(float) + sizeof(int))
                                        : 0);
-        auto kernB = big ? analyze_mixed_kernel<true, true>
-                         : (wide ? analyze_mixed_kernel<true, false> : analyze_mixed_kernel<false, false>);
+        // Above NMID a grid point has kBigWarps warps in kernel (B).
+        auto kernB = big ? analyze_mixed_kernel<true, true, kBigWarps>
+                         : (wide ? analyze_mixed_kernel<true, false, 1> : analyze_mixed_kernel<false, false, 1>);
+        const int thB = big ? 32 * kBigWarps : 32;
         e = cudaFuncSetAttribute(kernB, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shB);
         if (e != cudaSuccess) return e;
         if (wide) {
@@ -2184,7 +2203,7 @@ cudaError_t launch_analyze(void* f, int fp32, int nx, int ny, int k, const ObsPa
                                                                                        (int)c0, nm, sc, flags);
             if ((e = cudaEventRecord(aux->jac_done[b], aux->s2)) != cudaSuccess) return e;
             if ((e = cudaStreamWaitEvent(s, aux->jac_done[b], 0)) != cudaSuccess) return e;
-            kernB<<<(unsigned)nc, 32, shB, s>>>((float*)f, nx, ny, k, o, d_cut, beta, (int)c0, nm, sc, flags);
+            kernB<<<(unsigned)nc, thB, shB, s>>>((float*)f, nx, ny, k, o, d_cut, beta, (int)c0, nm, sc, flags);
             if ((e = cudaEventRecord(aux->ref_done[b], s)) != cudaSuccess) return e;
         }
     } else {
