@@ -321,7 +321,7 @@ __device__ int jacobi_sym_warp(R* A, R* U, int n, int ld, int lane, R* rc, R* rs
 }
 
 // The cyclic Jacobi of jacobi_sym_warp (same rotations, same round-robin
-// order) for 65..128 (up to 64 pairs) by a block of NT = 256 threads: the
+// order) for 33..128 (up to 64 pairs) by a block of NT = 256 threads: the
 // first 64 threads choose and apply the rotations of a round's pairs; then
 // every thread updates off-diagonal blocks and half a row of U (two threads
 // per row, 32 pairs each). The mask of rotated pairs alternates between two
@@ -1403,75 +1403,10 @@ __global__ void __launch_bounds__(32 * kJacWarps, 5) mixed_jacobi_kernel(int nx,
         jacobi_point<32>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, xr, flags, Cp, Cd);
 }
 
-// Kernel (A) for local problems of 33..64: the binary32 Jacobi in shared
-// memory (one warp per point, lanes own two columns), same output.
-__global__ void __launch_bounds__(32) mixed_jacobi_smem_kernel(int nx, int ny, int k, ObsParams o,
-                                                               double d_cut, double beta, int cell0,
-                                                               int nm, MixScratch sc,
-                                                               int* __restrict__ flags) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int nobs = o.nvar * o.npts;
-    const int ld = nm + 1;
-    float* A = reinterpret_cast<float*>(smem_raw);
-    float* U = A + (size_t)nm * ld;
-    float* rc = U + (size_t)nm * ld;
-    float* rs = rc + 32;
-    int* rp = reinterpret_cast<int*>(rs + 32);
-    int* rq = rp + 32;
-    const int lane = threadIdx.x;
-    const int li = blockIdx.x;
-    const int cell = cell0 + li;
-    const int x = cell % nx, y = cell / nx;
-    const int cap = o.plmax > 0 ? o.plmax : nobs;
-    double* lsq = sc.lsq + (size_t)li * cap;
-    int* lidx = sc.lidx + (size_t)li * cap;
-    const int p = local_set(o, x, y, nx, ny, d_cut, lane, lidx, lsq, cap);
-    if (lane == 0) sc.pcount[li] = p;
-    if (p == 0 || p > cap) return;  // p > cap: reported by kernel (B)
-    const bool obs_space = p < k;
-    const int n = obs_space ? p : k;
-    if (n > nm) return;  // reported by kernel (B)
-    const double aa = (k - 1) / beta;
-    for (int c = lane; c < n; c += 32) {
-        if (obs_space) {
-            const int oc = lidx[c];
-            const double sc_ = lsq[c];
-            for (int i = 0; i < n; ++i) A[i * ld + c] = (float)(lsq[i] * o.G[(size_t)lidx[i] * nobs + oc] * sc_);
-        } else if (sc.C32) {
-            const float* Cp = sc.C32 + (size_t)li * k * k;
-            for (int i = 0; i < n; ++i) A[i * ld + c] = Cp[i * k + c];
-        } else if (sc.C64) {
-            const double* Cd = sc.C64 + (size_t)li * k * k;
-            for (int i = 0; i < n; ++i) A[i * ld + c] = (float)Cd[i * k + c];
-        } else {
-            for (int i = 0; i < n; ++i) {
-                double s = (i == c) ? aa : 0.0;
-                for (int l = 0; l < p; ++l) {
-                    const double* row = o.dY + (size_t)lidx[l] * k;
-                    s += lsq[l] * lsq[l] * row[i] * row[c];
-                }
-                A[i * ld + c] = (float)s;
-            }
-        }
-        for (int i = 0; i < n; ++i) U[i * ld + c] = (i == c) ? 1.0f : 0.0f;
-    }
-    __syncwarp();
-    // Stop at 1e-6 ||A||_F, as the register Jacobi does: the refinement of
-    // kernel (B) is second order in what remains.
-    const int sweeps = jacobi_sym_warp<float>(A, U, n, ld, lane, rc, rs, rp, rq, 1e-6f, kMaxSweeps);
-    if (sweeps < 0 && lane == 0) atomicOr(flags, FLAG_NOCONV);
-    record_sweeps(o, sweeps, lane);
-    __syncwarp();
-    const int xr = mix_xr(nm);
-    float* Xp = sc.X + (size_t)li * xr * xr;
-    for (int c = lane; c < n; c += 32)
-        for (int i = 0; i < n; ++i) Xp[(size_t)i * xr + c] = U[i * ld + c];
-}
-
-// Kernel (A) for local problems of 65..128: the binary32 Jacobi of
+// Kernel (A) for local problems of 33..128: the binary32 Jacobi of
 // jacobi_sym_block, kBlkThreads threads per grid point, same output.
 constexpr int kBlkThreads = 256;
-constexpr int kBigWarps = 4;  // warps per grid point of kernel (B) above NMID
+constexpr int kWideWarps = 4;  // warps per grid point of kernel (B) above NREG
 
 __host__ __device__ inline size_t jacobi_block_smem_bytes(int nm) {
     return 2 * (size_t)nm * (nm + 1) * sizeof(float) + 64 * (2 * sizeof(float) + 2 * sizeof(int)) +
@@ -1756,7 +1691,7 @@ __device__ void refine_rr(const float* Ah, const float* Al, const float* Y32, fl
 }
 
 // BIG (nm > NMID): A and A Y in global scratch (L2-resident), the rest as
-// below. NW warps share a grid point (1 up to NMID).
+// below. NW warps share a grid point (1 up to NREG).
 template <bool WIDE, bool BIG, int NW>
 __global__ void __launch_bounds__(32 * NW) analyze_mixed_kernel(float* __restrict__ f, int nx, int ny,
                                                            int k, ObsParams o, double d_cut,
@@ -2158,20 +2093,15 @@ cudaError_t launch_analyze(void* f, int fp32, int nx, int ny, int k, const ObsPa
         const int cap = o.plmax > 0 ? o.plmax : nobs;
         const size_t shB = mix_smem_bytes(k, cap, nm);
         const bool wide = nm > NREG, big = nm > NMID;
-        const size_t shA = big ? jacobi_block_smem_bytes(nm)
-                               : (wide ? 2 * (size_t)nm * (nm + 1) * sizeof(float) + 64 * (sizeof(float) + sizeof(int))
-                                       : 0);
-        // Above NMID a grid point has kBigWarps warps in kernel (B).
-        auto kernB = big ? analyze_mixed_kernel<true, true, kBigWarps>
-                         : (wide ? analyze_mixed_kernel<true, false, 1> : analyze_mixed_kernel<false, false, 1>);
-        const int thB = big ? 32 * kBigWarps : 32;
+        const size_t shA = wide ? jacobi_block_smem_bytes(nm) : 0;
+        // Above NREG a grid point has kWideWarps warps in kernel (B).
+        auto kernB = big ? analyze_mixed_kernel<true, true, kWideWarps>
+                         : (wide ? analyze_mixed_kernel<true, false, kWideWarps> : analyze_mixed_kernel<false, false, 1>);
+        const int thB = wide ? 32 * kWideWarps : 32;
         e = cudaFuncSetAttribute(kernB, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shB);
         if (e != cudaSuccess) return e;
         if (wide) {
-            e = big ? cudaFuncSetAttribute(mixed_jacobi_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)shA)
-                    : cudaFuncSetAttribute(mixed_jacobi_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)shA);
+            e = cudaFuncSetAttribute(mixed_jacobi_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shA);
             if (e != cudaSuccess) return e;
         }
         const int kg = gram_k(fp32, k, prod), gsz = gram_sz(prod);
@@ -2195,9 +2125,6 @@ cudaError_t launch_analyze(void* f, int fp32, int nx, int ny, int k, const ObsPa
             if (nm <= NREG)
                 mixed_jacobi_kernel<<<(unsigned)((nc + kJacWarps - 1) / kJacWarps), 32 * kJacWarps, 0,
                                       aux->s2>>>(nx, ny, k, o, d_cut, beta, (int)c0, nc, nm, sc, flags);
-            else if (!big)
-                mixed_jacobi_smem_kernel<<<(unsigned)nc, 32, shA, aux->s2>>>(nx, ny, k, o, d_cut, beta,
-                                                                              (int)c0, nm, sc, flags);
             else
                 mixed_jacobi_block_kernel<<<(unsigned)nc, kBlkThreads, shA, aux->s2>>>(nx, ny, k, o, d_cut, beta,
                                                                                        (int)c0, nm, sc, flags);

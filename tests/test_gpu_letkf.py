@@ -181,8 +181,9 @@ def test_reduced_gram_at_128_members(gpu, mode, bound):
     (20, 20, 64, 5, 5, 7.0),     # observation space, n up to ~40, ragged local sets
 ])
 def test_larger_local_problems_match_oracle(gpu, nx, ny, k, nox, noy, d_cut):
-    """Local problems of 33..64 (two columns per lane; binary32 Jacobi in
-    shared memory on the mixed path)."""
+    """Local problems of 33..64 (two columns per lane in FP64; on the mixed
+    path the 256-thread binary32 Jacobi and four warps per grid point in the
+    refinement)."""
     f, ix, iy, yu, yv = _analysis_case(nx, ny, k, nox, noy, seed=70 + k)
     ref = oracle.letkf_analyze(f, ix, iy, yu, yv, SIGMA, SIGMA, d_cut, 1.05)
     got = _gpu_analysis(gpu, f, ix, iy, yu, yv, d_cut, 1.05, gpu.LBM_FP64)
