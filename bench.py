@@ -39,11 +39,11 @@ L2_NOTE = "state larger than L2: 151 MB per buffer in FP32, 302 MB in FP64 (L2 =
 # Set an entry to None when its kernel changes until it is captured again.
 # Issue-slot utilisation of the two mixed-analysis kernels in the same ncu
 # capture (profiles/analysis_mixed_256x256_k64.md).
-ISSUE_ACTIVE = {"mixed_jacobi_kernel": 0.668, "analyze_mixed_kernel": 0.358}
+ISSUE_ACTIVE = {"mixed_jacobi_kernel": 0.660, "analyze_mixed_kernel": 0.357}
 NCU_TRAFFIC = {
-    "analysis_mixed": 8 * (1.207296e6 + 0.95616e6 + 48.156928e6 + 0.02944e6),  # 8 chunks
-    "lbm_step_f32": 151.54816e6 + 98.665472e6,
-    "analysis_fp64": 307.476736e6 + 242.607616e6,
+    "analysis_mixed": 8 * (1.21216e6 + 0.958464e6 + 48.159488e6 + 0.02432e6),  # 8 chunks
+    "lbm_step_f32": 151.54816e6 + 97.796096e6,
+    "analysis_fp64": 304.459264e6 + 241.096192e6,
 }
 
 
