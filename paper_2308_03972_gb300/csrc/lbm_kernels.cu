@@ -308,7 +308,11 @@ __global__ void moments_kernel(const T* __restrict__ f, int nx, int ny, int k,
     if (!(ux * ux + uy * uy <= kUMax2) || !(r > 0.0)) atomicOr(flags, FLAG_DIVERGED);
 }
 
-// Ensemble-mean velocity: one warp per cell, lanes over members.
+// Ensemble-mean velocity: one warp per cell, lanes over members. A member's
+// moments are taken in the precision of the stored state: FP64, or binary32
+// for the binary32 shifted state g = f - w (sum g, sum c g; rho = 1 + sum g),
+// whose own storage error (~1e-9 absolute in u) they match; the member mean
+// is summed in FP64.
 template <typename T, bool SHIFT>
 __global__ void mean_velocity_kernel(const T* __restrict__ f, int nx, int ny, int k,
                                      double* __restrict__ um, double* __restrict__ vm,
@@ -321,18 +325,19 @@ __global__ void mean_velocity_kernel(const T* __restrict__ f, int nx, int ny, in
     bool bad = false;
     for (int m = lane; m < k; m += 32) {
         const size_t i = (size_t)cell * k + m;
-        double r = SHIFT ? 1.0 : 0.0, jx = 0.0, jy = 0.0;
+        T r = T(0), jx = T(0), jy = T(0);
 #pragma unroll
         for (int a = 0; a < 9; ++a) {
-            const double g = (double)f[a * n + i];
+            const T g = f[a * n + i];
             r += g;
-            jx += d2q9_cx(a) * g;
-            jy += d2q9_cy(a) * g;
+            jx += T(d2q9_cx(a)) * g;
+            jy += T(d2q9_cy(a)) * g;
         }
-        const double ux = jx / r, uy = jy / r;
-        su += ux;
-        sv += uy;
-        bad |= !(ux * ux + uy * uy <= kUMax2) || !(r > 0.0);
+        if (SHIFT) r += T(1);
+        const T ux = jx / r, uy = jy / r;
+        su += (double)ux;
+        sv += (double)uy;
+        bad |= !((double)ux * ux + (double)uy * uy <= kUMax2) || !(r > T(0));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
