@@ -39,9 +39,10 @@ L2_NOTE = "state larger than L2: 151 MB per buffer in FP32, 302 MB in FP64 (L2 =
 # Set an entry to None when its kernel changes until it is captured again.
 # Issue-slot utilisation of the two mixed-analysis kernels in the same ncu
 # capture (profiles/analysis_mixed_256x256_k64.md).
-ISSUE_ACTIVE = {"mixed_jacobi_kernel": 0.660, "analyze_mixed_kernel": 0.357}
+ISSUE_ACTIVE = {"mixed_jacobi_kernel": 0.714, "analyze_mixed_kernel": 0.358}
+MIXED_CHUNK_CELLS = 65536  # grid points per mixed-analysis chunk at 256^2 x 64
 NCU_TRAFFIC = {
-    "analysis_mixed": 8 * (1.21216e6 + 0.958464e6 + 48.159488e6 + 0.02432e6),  # 8 chunks
+    "analysis_mixed": 40.620544e6 + 162.215168e6 + 384.285952e6 + 118.688768e6,  # (A) + (B), one chunk
     "lbm_step_f32": 151.54816e6 + 97.796096e6,
     "analysis_fp64": 304.459264e6 + 241.096192e6,
 }
@@ -230,9 +231,10 @@ def measure(cfg, precision, steps, warmup, sample_clocks=False, gpu_index=0):
     ana = [e[2].elapsed_time(e[3]) for e in ev]
     osse.close()
     # Kernels per cycle: the LBM steps, observe + Gram, then the analysis
-    # (FP64: one launch; mixed: the FP32 copy of dY and two kernels per chunk
-    # of 8192 grid points).
-    chunks = -(-cfg.nx * cfg.ny // 8192)
+    # (FP64: one launch; mixed: the FP32 copy of dY and two kernels per chunk;
+    # at this workload, 4.4 KB of scratch per grid point, a chunk is the
+    # library's largest, 65536 grid points).
+    chunks = -(-cfg.nx * cfg.ny // MIXED_CHUNK_CELLS)
     ana_launches = 1 if precision == binding.LBM_FP64 else 1 + 2 * chunks
     return {"ms_per_cycle": total_ms / steps, "lbm_step_ms": statistics.mean(lbm),
             "observe_ms": statistics.mean(obs_ms), "analysis_ms": statistics.mean(ana),
@@ -621,7 +623,7 @@ def main():
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback"}
     else:
         ach = kern["analysis_mixed"]["achieved_gflops"]
-        roof = {"kernel": "analysis stage: mixed_jacobi_kernel + analyze_mixed_kernel over 8 chunks",
+        roof = {"kernel": "analysis stage: mixed_jacobi_kernel + analyze_mixed_kernel (one chunk of 65536 grid points)",
                 "bound": "alu", "achieved": ach / 1000.0,
                 "peak": FP64_NOMINAL_GFLOPS / 1000.0, "unit": "TFLOP/s", "frac": ach / FP64_NOMINAL_GFLOPS,
                 "traffic": NCU_TRAFFIC["analysis_mixed"],

@@ -764,7 +764,7 @@ __global__ void __launch_bounds__(32) analyze_fp64_kernel(double* __restrict__ f
 //      (relative ~1e-11 at these sizes). The transform products and the update run in
 //      binary32 with binary32 accumulation.
 
-constexpr int kChunkCells = 8192;   // grid points per (A)+(B) pass (at most)
+constexpr int kChunkCells = 65536;  // grid points per (A)+(B) pass (at most)
 constexpr int kJacWarps = 4;        // points per block in (A)
 
 // Binary32 cyclic Jacobi with the column of A and of U held in registers.
@@ -956,12 +956,15 @@ __host__ __device__ inline size_t mix_scratch_bytes_per_point(int nobs, int nm, 
            sizeof(int) + (size_t)kg * (kg + 1) * gsz + mix_big_floats(nm) * sizeof(float);
 }
 
-// Grid points per chunk: the double-buffered scratch stays within ~96 MB of L2.
-// Above NMID both kernels hold one grid point per SM; their chunks are at
-// least four full waves of GB300's 152 SMs (the scratch then exceeds L2,
-// but only the grid points in flight are live at a time).
+// Grid points per chunk: up to kChunkCells, with at most 384 MiB of scratch
+// per buffer. Fewer, larger launches won over L2-resident chunks: at
+// 256^2 x 64 (4.4 KB per point) the analysis took 10.6 / 10.3 / 10.0 / 9.9 ms
+// with chunks of 8192 / 16384 / 32768 / 65536 points (11.9 ms at 4096),
+// although the basis scratch then round-trips through HBM. Above NMID both
+// kernels hold one grid point per SM; their chunks are at least four full
+// waves of GB300's 152 SMs.
 __host__ __device__ inline long long mix_chunk(long long cells, int nobs, int nm, int kg, int gsz) {
-    long long c = (48ll << 20) / (long long)mix_scratch_bytes_per_point(nobs, nm, kg, gsz);
+    long long c = (384ll << 20) / (long long)mix_scratch_bytes_per_point(nobs, nm, kg, gsz);
     if (c > kChunkCells) c = kChunkCells;
     const long long cmin = nm > NMID ? 4 * 152 : 256;
     if (c < cmin) c = cmin;
@@ -2074,8 +2077,9 @@ size_t analyze_scratch_bytes(int nx, int ny, int fp32, int nl, int nmax, int k, 
     if (!fp32) return 0;
     const int nm = mixed_nm(nmax);
     const int kg = gram_k(fp32, k, prod), gsz = gram_sz(prod);
-    const long long chunk = mix_chunk((long long)nx * ny, nl, nm, kg, gsz);
-    return 2 * mix_buf_bytes(chunk, nl, nm, kg, gsz);  // double-buffered
+    const long long cells = (long long)nx * ny;
+    const long long chunk = mix_chunk(cells, nl, nm, kg, gsz);
+    return (chunk < cells ? 2 : 1) * mix_buf_bytes(chunk, nl, nm, kg, gsz);  // double-buffered
 }
 
 cudaError_t launch_analyze(void* f, int fp32, int nx, int ny, int k, const ObsParams& o,

@@ -296,17 +296,20 @@ def test_odd_problem_sizes_match_oracle(gpu, prec, nx, ny, k, nox, noy, d_cut):
 
 
 def test_mixed_analysis_over_many_odd_sized_chunks(gpu):
-    """128^2 lattice with 32 x 32 observation points: the per-point scratch
-    makes the chunk 1755 grid points (odd), so the second buffer of the
-    double-buffered scratch starts at an odd multiple of 4 bytes unless the
-    buffer size is rounded; ten chunks run through both buffers."""
-    nx = ny = 128
-    k = 16
-    f, ix, iy, yu, yv = _analysis_case(nx, ny, k, 32, 32, seed=77, steps=2)
-    got = _gpu_analysis(gpu, f, ix, iy, yu, yv, 3.0, 1.05, gpu.LBM_MIXED)
+    """64^2 lattice, 100 members, 8 x 8 observation points all in range
+    (d_cut = 100), so every local problem is the ensemble-space n = 100
+    and a grid point needs 309,476 bytes of analysis scratch (basis, local
+    list, FP64 Gram, refinement matrices). The 384 MiB budget then gives
+    chunks of 1301 grid points (odd): four chunks alternate between the two
+    scratch buffers, and the second buffer starts at an odd multiple of 4
+    bytes unless the buffer size is rounded."""
+    nx = ny = 64
+    k = 100
+    f, ix, iy, yu, yv = _analysis_case(nx, ny, k, 8, 8, seed=77, steps=2)
+    got = _gpu_analysis(gpu, f, ix, iy, yu, yv, 100.0, 1.05, gpu.LBM_MIXED)
     rng = np.random.default_rng(5)
     pts = np.sort(rng.choice(nx * ny, 64, replace=False)).astype(np.int32)
-    ref = oracle.letkf_analyze(f, ix, iy, yu, yv, SIGMA, SIGMA, 3.0, 1.05, points=pts)
+    ref = oracle.letkf_analyze(f, ix, iy, yu, yv, SIGMA, SIGMA, 100.0, 1.05, points=pts)
     y, x = pts // nx, pts % nx
     assert norm_rel(got[:, y, x, :], ref[:, y, x, :]) <= 1e-6
 
