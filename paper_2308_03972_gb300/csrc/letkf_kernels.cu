@@ -1497,13 +1497,14 @@ struct MixSmem {
     float* Wh;     // [nm][ld] A Y, high half; then f(S) in binary32 (F32), then T
     float* Wl;     // [nm][ld] A Y, low half
     float* Y32;    // [nm][ld] the basis (binary32, exact)
-    float* E32;    // [nm][ld] E = Y^T Y - I (non-orthogonality of the basis)
+    float* E32;    // [nm][ld] E = Y^T Y - I (non-orthogonality of the basis); up to
+                   // NMID it shares Al's space (A's low half is dead once A Y is formed)
     double* lsq;   // [nl]
     double* ldh;   // [nl]
     double* vb;    // [nm]
     double* dS;    // [nm] diagonal of S' (FP64)
-    double* vu;    // [nm]
-    double* vinv;  // [nm]
+    float* vu;     // [nm] (binary32: only read as binary32 factors of f(S))
+    float* vinv;   // [nm]
     float* dX;     // [9][k]
     float* xbar;   // [16]
     float* Z;      // [9][nm]
@@ -1515,13 +1516,15 @@ struct MixSmem {
     int* lidx;     // [nl]
 };
 
-// Above NMID, Ah, Al, Wh and Wl live in the global scratch (MixScratch::big)
-// and shared memory holds only Y32 and E32 of the six matrices.
+// Up to NMID five matrices (E32 shares Al's space): at n = 28 and k = 64,
+// 22.3 KB per grid point, ten points per SM. Above NMID, Ah, Al, Wh and Wl
+// live in the global scratch (MixScratch::big) and shared memory holds Y32
+// and E32.
 __host__ __device__ inline size_t mix_smem_bytes(int k, int nl, int nm) {
     const int ld = mix_ld(nm);
-    const size_t d = 2 * (size_t)nl + 4 * (size_t)nm;
-    const size_t f = (nm > NMID ? 2 : 6) * (size_t)nm * ld + 9 * (size_t)k + 16 + 18 * (size_t)nm + 16 +
-                     3 * (size_t)nm;
+    const size_t d = 2 * (size_t)nl + 2 * (size_t)nm;
+    const size_t f = (nm > NMID ? 2 : 5) * (size_t)nm * ld + 9 * (size_t)k + 16 + 18 * (size_t)nm + 16 +
+                     5 * (size_t)nm;
     return d * sizeof(double) + ((f * sizeof(float) + 7) / 8) * 8 + (size_t)nl * sizeof(int);
 }
 
@@ -1538,10 +1541,6 @@ __device__ inline MixSmem carve_mix(unsigned char* raw, int k, int nl, int nm, f
     p += nm;
     s.dS = p;
     p += nm;
-    s.vu = p;
-    p += nm;
-    s.vinv = p;
-    p += nm;
     float* q = reinterpret_cast<float*>(p);
     float* m = big ? big : q;
     s.Ah = m;
@@ -1555,8 +1554,12 @@ __device__ inline MixSmem carve_mix(unsigned char* raw, int k, int nl, int nm, f
     if (!big) q = m;
     s.Y32 = q;
     q += nm * ld;
-    s.E32 = q;
-    q += nm * ld;
+    if (big) {
+        s.E32 = q;
+        q += nm * ld;
+    } else {
+        s.E32 = s.Al;
+    }
     s.dX = q;
     q += 9 * k;
     s.xbar = q;
@@ -1572,6 +1575,10 @@ __device__ inline MixSmem carve_mix(unsigned char* raw, int k, int nl, int nm, f
     s.t1f = q;
     q += nm;
     s.t2f = q;
+    q += nm;
+    s.vu = q;
+    q += nm;
+    s.vinv = q;
     q += nm;
     const size_t fbytes = (size_t)(q - reinterpret_cast<float*>(p)) * sizeof(float);
     s.lidx = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(p) + ((fbytes + 7) / 8) * 8);
@@ -1639,16 +1646,10 @@ __device__ void sym_product_df(const float* P, const float* Qhi, const float* Ql
 // Y^T (A Y) are double-binary32 (A Y goes to Wh + Wl). Leaves E in E32, the
 // diagonal of S' in dS (FP64) and its off-diagonal in Soff (binary32: the
 // entries are ~1e-6 of |A| and enter the matrix functions to first order).
-// Soff may alias Ah (A is not read after A Y).
+// Soff may alias Ah and E32 may alias Al (A is not read after A Y).
 template <bool WIDE, int NW = 1>
 __device__ void refine_rr(const float* Ah, const float* Al, const float* Y32, float* Wh, float* Wl,
                           float* E32, float* Soff, double* dS, int n, int ld, int t) {
-    // E = Y^T Y - I.
-    sym_product_df<NW>(Y32, Y32, nullptr, n, ld, t, [&](int i, int j, double v) {
-        const float e = (float)(v - (i == j ? 1.0 : 0.0));
-        E32[i * ld + j] = e;
-        E32[j * ld + i] = e;
-    });
     // W = A Y, column col: four rows at a time, then the remainder.
     for_cols<WIDE, NW>(t, n, [&](int col) {
         int i0 = 0;
@@ -1670,6 +1671,12 @@ __device__ void refine_rr(const float* Ah, const float* Al, const float* Y32, fl
         }
     });
     point_sync<NW>();
+    // E = Y^T Y - I.
+    sym_product_df<NW>(Y32, Y32, nullptr, n, ld, t, [&](int i, int j, double v) {
+        const float e = (float)(v - (i == j ? 1.0 : 0.0));
+        E32[i * ld + j] = e;
+        E32[j * ld + i] = e;
+    });
     // S = Y^T (A Y), symmetric: diagonal to dS, off-diagonal to Soff.
     sym_product_df<NW>(Y32, Wh, Wl, n, ld, t, [&](int i, int j, double v) {
         if (i == j) {
@@ -1813,8 +1820,8 @@ __global__ void __launch_bounds__(32 * NW) analyze_mixed_kernel(float* __restric
         for_cols<WIDE, NW>(tid, n, [&](int c) {
             const double sii = sm.dS[c];
             const double u = sqrt(aa + sii);
-            sm.vu[c] = u;
-            sm.vinv[c] = 1.0 / (u * (u + r));  // alpha_i
+            sm.vu[c] = (float)u;
+            sm.vinv[c] = (float)(1.0 / (u * (u + r)));  // alpha_i
             sm.vb[c] = 1.0 / (aa + sii);       // h_i = 1 / u_i^2
             // t1 = Y^T d-hat (binary32 transform product).
             float t = 0.0f;
@@ -1933,8 +1940,8 @@ __global__ void __launch_bounds__(32 * NW) analyze_mixed_kernel(float* __restric
         // Functions of S directly: 1/lambda for P-tilde, lambda^{-1/2} for W.
         for_cols<WIDE, NW>(tid, n, [&](int c) {
             const double lam = sm.dS[c];
-            sm.vu[c] = sqrt(lam);
-            sm.vinv[c] = 1.0 / lam;
+            sm.vu[c] = (float)sqrt(lam);
+            sm.vinv[c] = (float)(1.0 / lam);
             float t = 0.0f;
             for (int l = 0; l < n; ++l) t += Y32[l * ld + c] * (float)sm.vb[l];
             sm.t1f[c] = t;  // Y^T b
