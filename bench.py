@@ -39,10 +39,10 @@ L2_NOTE = "state larger than L2: 151 MB per buffer in FP32, 302 MB in FP64 (L2 =
 # Set an entry to None when its kernel changes until it is captured again.
 # Issue-slot utilisation of the two mixed-analysis kernels in the same ncu
 # capture (profiles/analysis_mixed_256x256_k64.md).
-ISSUE_ACTIVE = {"mixed_jacobi_kernel": 0.714, "analyze_mixed_kernel": 0.358}
+ISSUE_ACTIVE = {"mixed_jacobi_kernel": 0.714, "analyze_mixed_kernel": 0.403}
 MIXED_CHUNK_CELLS = 65536  # grid points per mixed-analysis chunk at 256^2 x 64
 NCU_TRAFFIC = {
-    "analysis_mixed": 40.620544e6 + 162.215168e6 + 384.285952e6 + 118.688768e6,  # (A) + (B), one chunk
+    "analysis_mixed": 40.731392e6 + 162.281216e6 + 384.31104e6 + 118.380544e6,  # (A) + (B), one chunk
     "lbm_step_f32": 151.54816e6 + 97.796096e6,
     "analysis_fp64": 304.459264e6 + 241.096192e6,
 }
