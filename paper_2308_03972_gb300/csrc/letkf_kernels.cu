@@ -752,8 +752,9 @@ __global__ void __launch_bounds__(32) analyze_fp64_kernel(double* __restrict__ f
 // fraction of the FP64 work, in two kernels over chunks of grid points:
 //  (A) mixed_jacobi_kernel: the local set, the matrix in FP64 rounded to
 //      binary32, and a binary32 cyclic Jacobi held in registers (no shared
-//      memory, so many warps per SM hide its latency). The basis X goes to a
-//      chunk-sized scratch that stays in L2.
+//      memory, so many warps per SM hide its latency); above n = 32 the
+//      block Jacobi in shared memory. The basis X goes to the chunk's
+//      scratch.
 //  (B) analyze_mixed_kernel: in FP64, form the Rayleigh-Ritz matrix
 //      S = X^T A X and the non-orthogonality E = X^T X - I of the binary32
 //      basis, correct S to first order in E (refine_rr), and evaluate
@@ -925,7 +926,7 @@ __device__ void jacobi_point(const ObsParams& o, int k, int n, int p, bool obs_s
 
 // Per-chunk scratch shared by kernels (A) and (B).
 struct MixScratch {
-    float* X;      // [chunk][xr][xr] binary32 basis, row i at i * xr (xr = 32 or 64)
+    float* X;      // [chunk][xr][xr] binary32 basis, row i at i * xr (xr = 32, 64 or 128)
     double* lsq;   // [chunk][nobs] sqrt(rho) of the local scalars
     int* lidx;     // [chunk][nobs] their observation indices
     int* pcount;   // [chunk] number of local scalars
