@@ -164,6 +164,15 @@ def test_first_order_refinement_of_a_binary32_basis(k, p, seed, rel):
     assert np.abs(X @ np.diag(g(s)) @ X.T - G_ref).max() > 10 * bound * np.abs(G_ref).max()
 
 
+@pytest.mark.parametrize("k,p,seed", [(160, 120, 7), (140, 128, 8)])
+def test_first_order_refinement_up_to_n_128(k, p, seed):
+    """The same second-order bound for the largest local problems the mixed
+    path takes (n = 120, 128), where a sweep of the binary32 Jacobi is about
+    twenty times as many rotations as at n = 28, at the kernels' threshold
+    of 1e-6 ||A||_F."""
+    test_first_order_refinement_of_a_binary32_basis(k, p, seed, 1e-6)
+
+
 def _two_sum(a, b):
     f = np.float32
     s = (a + b).astype(f)
