@@ -172,6 +172,19 @@ int letkf_observe_rho(lbm_ctx *ctx, int npts, const int *ix, const int *iy,
 enum { LBM_PROD_FP64 = 0, LBM_PROD_FP32 = 1, LBM_PROD_TF32 = 2, LBM_PROD_BF16 = 3 };
 int letkf_set_products(lbm_ctx *ctx, int mode);
 
+/* Grid points per run of the mixed-precision analysis (Section 3.2: the
+ * local analyses are independent, so they may be taken in any order). A
+ * run is run_len consecutive grid points of one lattice row, analysed by
+ * one warp over the union of their local observation sets: a scalar
+ * outside a point's support enters that point with weight zero, which
+ * leaves its analysis unchanged, and each point's binary32 Jacobi starts
+ * from the previous point's basis. Used when every grid point has
+ * p < members and every run's union holds at most 32 scalars; otherwise,
+ * and with run_len = 0, the analysis takes the chunked path (cold-started
+ * Jacobi per point). Default 8. LBM_EINVAL outside [0, 4096]. Applies to
+ * later analyses; results agree with either path to rounding. */
+int letkf_set_run_length(lbm_ctx *ctx, int run_len);
+
 /* Diagnostic: count the Jacobi sweeps of every local eigensolve of later
  * analyses (enable != 0) into a 32-bin histogram (bin s: points that took s
  * sweeps, the last one rotating nothing; bin 31: 31 or more, or the sweep

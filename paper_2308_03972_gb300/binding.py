@@ -54,6 +54,7 @@ SIGNATURES = {
     "letkf_analyze": (_I, [_P, _D, _D]),
     "lbm_set_closure": (_I, [_P, _D]),
     "letkf_set_products": (_I, [_P, _I]),
+    "letkf_set_run_length": (_I, [_P, _I]),
     "letkf_sweep_stats": (_I, [_P, _I, _P]),
     "lbm_misfit": (_I, [_P, ctypes.POINTER(lbm_window), _P]),
     "lbm_misfit_gradient": (_I, [_P, ctypes.POINTER(lbm_window), _P, _P, _P, _P, _I]),
@@ -251,6 +252,10 @@ def letkf_set_products(ctx, mode):
     _check(ctx, load().letkf_set_products(ctx, int(mode)))
 
 
+def letkf_set_run_length(ctx, run_len):
+    _check(ctx, load().letkf_set_run_length(ctx, int(run_len)))
+
+
 def lbm_set_closure(ctx, cs_smag):
     _check(ctx, load().lbm_set_closure(ctx, float(cs_smag)))
 
@@ -395,6 +400,9 @@ class Ensemble:
 
     def set_products(self, mode):
         letkf_set_products(self.ctx, mode)
+
+    def set_run_length(self, run_len):
+        letkf_set_run_length(self.ctx, run_len)
 
     def set_closure(self, cs_smag):
         lbm_set_closure(self.ctx, cs_smag)

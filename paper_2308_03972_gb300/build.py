@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "liblbm_letkf.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ("lbm_kernels.cu", "letkf_kernels.cu", "diag_kernels.cu", "adjoint_kernels.cu",
+SOURCES = ("lbm_kernels.cu", "letkf_kernels.cu", "letkf_runs.cu", "diag_kernels.cu", "adjoint_kernels.cu",
            "lbm_letkf_api.cu", "letkf_noalloc.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall"]

@@ -126,6 +126,24 @@ cudaError_t launch_analyze(void* f, int fp32, int nx, int ny, int k, const ObsPa
                            double d_cut, double beta, int nmax, int prod, int* flags, void* scratch,
                            const AnalyzeAux* aux, cudaStream_t s);
 
+// dst = (float) src, n elements.
+cudaError_t launch_to_f32(const double* src, float* dst, size_t n, cudaStream_t s);
+
+// ---- letkf_runs.cu --------------------------------------------------------
+// Mixed-precision analysis over runs of run_len consecutive grid points of a
+// row (one warp each; warm-started binary32 Jacobi over the union of the
+// run's local sets), observation-space form. Valid when every grid point
+// has p < k and the union of every run holds at most 32 scalars
+// (maxunion: that largest union, from the host's geometry). scratch holds
+// run_scratch_bytes(...) bytes: a split copy of the observation Gram and,
+// per chunk of runs, every grid point's binary32 basis and eigenvalue
+// estimates (handed from the Jacobi kernel to the refinement kernel).
+constexpr int kRunMaxUnion = 32;
+size_t run_scratch_bytes(int nx, int ny, int nobs, int run_len, int maxunion);
+cudaError_t launch_analyze_runs(float* f, int nx, int ny, int k, const ObsParams& o, double d_cut,
+                                double beta, int run_len, int maxunion, int* flags, void* scratch,
+                                cudaStream_t s);
+
 // ---- diag_kernels.cu ------------------------------------------------------
 // Member-averaged energy spectrum E[nshells] (device pointer); work holds
 // spectrum_work_bytes(nx, ny, k, nshells) bytes. Lattices whose row or column

@@ -42,6 +42,11 @@ struct lbm_ctx {
     int geo_nmax = 0;
     int geo_pmax = 0;  // largest local list (scalars) for geo_dcut
     bool geo_any_ens = false;  // some grid point has p >= k (ensemble-space form)
+    // Largest union of local sets over runs of run_len grid points of a row
+    // (the run analysis), for geo_dcut and union_rl.
+    int geo_maxunion = -1;
+    int union_rl = -1;
+    int run_len = 8;  // grid points per run of the mixed analysis (0: chunked two-kernel path)
     AnalyzeAux aux{};              // second stream + events (mixed precision)
     bool aux_ready = false;
     double* nudge_obs = nullptr;  // [3][noy][nox] nudging observations
@@ -168,10 +173,61 @@ int largest_local_problem(lbm_ctx* c, double d_cut) {
         if (v > vmax) vmax = v;
     }
     c->geo_dcut = d_cut;
+    c->geo_maxunion = -1;
     c->geo_nmax = nmax;
     c->geo_pmax = c->nvar * (vmax > 0 ? vmax : 1);
     c->geo_any_ens = c->nvar * vmax >= c->k;
     return nmax;
+}
+
+// Largest number of observation scalars in the union of the local sets of a
+// run of run_len consecutive grid points of a row (runs start at x = 0,
+// run_len, ...). An observation point belongs to a run when
+// r / d_cut < 2 at some cell of it, the kernels' own test; for each point
+// and row the cells in range form one interval |dx| <= dxmax(dy), and every
+// run that interval meets is counted.
+int largest_run_union(lbm_ctx* c, double d_cut, int run_len) {
+    largest_local_problem(c, d_cut);
+    if (c->geo_maxunion >= 0 && c->union_rl == run_len) return c->geo_maxunion;
+    const int nx = c->nx, ny = c->ny;
+    const int rx = (nx + run_len - 1) / run_len;
+    std::vector<int> cnt((size_t)ny * rx, 0);
+    std::vector<int> stamp((size_t)rx, -1);
+    const int R = (int)std::ceil(2.0 * d_cut) + 1;
+    const int hx = nx / 2, hy = ny / 2;
+    for (size_t j = 0; j < c->geo_ix.size(); ++j) {
+        for (int dy = -R; dy <= R; ++dy) {
+            if (dy > hy || dy < -hy) continue;          // outside the minimum image
+            if (ny % 2 == 0 && dy == -hy) continue;     // -n/2 maps to +n/2
+            const double dy2 = (double)dy * dy;
+            int dxmax = -1;
+            for (int dx = 0; dx <= hx; ++dx) {
+                if (std::sqrt((double)dx * dx + dy2) / d_cut < 2.0) dxmax = dx;
+                else break;
+            }
+            if (dxmax < 0) continue;
+            const int y = ((c->geo_iy[j] + dy) % ny + ny) % ny;
+            int* row = cnt.data() + (size_t)y * rx;
+            const int tag = (int)(j * (2 * R + 1) + (dy + R));
+            if (2 * dxmax + 1 >= nx) {
+                for (int q = 0; q < rx; ++q) row[q] += 1;
+                continue;
+            }
+            for (int dx = -dxmax; dx <= dxmax; ++dx) {
+                const int x = ((c->geo_ix[j] + dx) % nx + nx) % nx;
+                const int q = x / run_len;
+                if (stamp[q] != tag) {
+                    stamp[q] = tag;
+                    ++row[q];
+                }
+            }
+        }
+    }
+    int vmax = 0;
+    for (int v : cnt) vmax = v > vmax ? v : vmax;
+    c->geo_maxunion = c->nvar * vmax;
+    c->union_rl = run_len;
+    return c->geo_maxunion;
 }
 
 // Observation operator for (u, v) or, with yo_r, (u, v, rho) at each point:
@@ -241,6 +297,7 @@ int observe_impl(lbm_ctx* c, int npts, const int* ix, const int* iy, const doubl
         c->geo_ix.assign(ix, ix + npts);
         c->geo_iy.assign(iy, iy + npts);
         c->geo_dcut = -1.0;
+        c->geo_maxunion = -1;
     }
     c->npts = npts;
     c->nvar = nvar;
@@ -434,6 +491,7 @@ int misfit_impl(lbm_ctx* c, const lbm_window* win, const double* w, double* J, d
 struct AnalysisPlan {
     double d_cut = 0.0, beta = 0.0;
     int nmax = 0, plmax = 0, prod = PROD_FP64;
+    int run_len = 0, maxunion = 0;  // run_len > 0: the run analysis (mixed precision)
 };
 
 int analyze_prepare(lbm_ctx* c, double d_cut, double beta, AnalysisPlan* plan) {
@@ -444,7 +502,15 @@ int analyze_prepare(lbm_ctx* c, double d_cut, double beta, AnalysisPlan* plan) {
     const int plmax = c->geo_pmax;
     // The reduced-precision Gram pass serves ensemble-space points only.
     const int prod = c->geo_any_ens ? c->prod : PROD_NONE;
-    const size_t scratch = analyze_scratch_bytes(c->nx, c->ny, is_fp32(c), plmax, nmax, c->k, prod);
+    // Mixed precision, every grid point in observation space and every run's
+    // union within one warp: the run analysis (warm-started Jacobi).
+    int run_len = 0, maxunion = 0;
+    if (is_fp32(c) && c->run_len > 0 && !c->geo_any_ens) {
+        maxunion = largest_run_union(c, d_cut, c->run_len);
+        if (maxunion <= kRunMaxUnion) run_len = c->run_len;
+    }
+    const size_t scratch = run_len > 0 ? run_scratch_bytes(c->nx, c->ny, c->nvar * c->npts, run_len, maxunion)
+                                       : analyze_scratch_bytes(c->nx, c->ny, is_fp32(c), plmax, nmax, c->k, prod);
     if (scratch > c->ana_scratch_bytes) {
         CK(c, cudaStreamSynchronize(c->stream), "synchronising");
         cudaFree(c->ana_scratch);
@@ -462,7 +528,7 @@ int analyze_prepare(lbm_ctx* c, double d_cut, double beta, AnalysisPlan* plan) {
         }
         c->aux_ready = true;
     }
-    *plan = AnalysisPlan{d_cut, beta, nmax, plmax, prod};
+    *plan = AnalysisPlan{d_cut, beta, nmax, plmax, prod, run_len, maxunion};
     return LBM_OK;
 }
 
@@ -470,6 +536,12 @@ int analyze_prepare(lbm_ctx* c, double d_cut, double beta, AnalysisPlan* plan) {
 int analyze_launch(lbm_ctx* c, const AnalysisPlan& pl) {
     ObsParams o{c->npts, c->ix, c->iy, c->dY, c->d, c->G, c->sigma_u, c->sigma_v, c->dY32,
                 c->nvar, c->sigma_r, pl.plmax, c->sweep_stats ? c->sweep_hist : nullptr};
+    if (pl.run_len > 0) {
+        CK(c, launch_analyze_runs((float*)c->f[c->cur], c->nx, c->ny, c->k, o, pl.d_cut, pl.beta, pl.run_len,
+                                  pl.maxunion, c->flags, c->ana_scratch, c->stream),
+           "launching analysis");
+        return LBM_OK;
+    }
     CK(c, launch_analyze(c->f[c->cur], is_fp32(c), c->nx, c->ny, c->k, o, pl.d_cut, pl.beta, pl.nmax,
                          pl.prod, c->flags, c->ana_scratch, c->aux_ready ? &c->aux : nullptr, c->stream),
        "launching analysis");
@@ -711,6 +783,13 @@ int letkf_set_products(lbm_ctx* c, int mode) {
     if (mode != LBM_PROD_FP64 && !is_fp32(c))
         return fail(c, LBM_EINVAL, "reduced-precision products need a mixed-precision context");
     c->prod = mode;
+    return LBM_OK;
+}
+
+int letkf_set_run_length(lbm_ctx* c, int run_len) {
+    if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (run_len < 0 || run_len > 4096) return fail(c, LBM_EINVAL, "run_len must be in [0, 4096]");
+    c->run_len = run_len;
     return LBM_OK;
 }
 

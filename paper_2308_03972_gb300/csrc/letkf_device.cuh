@@ -1,0 +1,71 @@
+// Device helpers shared by the LETKF translation units (sm_103a). Internal
+// linkage: every translation unit that includes this header gets its own copy.
+#pragma once
+#include <cstdint>
+
+namespace lbmgpu {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+template <typename R>
+__device__ __forceinline__ R warp_sum(R v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// Periodic minimum-image displacement on a ring of n cells.
+__device__ __forceinline__ int min_image(int d, int n) {
+    if (d > n / 2) d -= n;
+    if (d < -(n / 2)) d += n;
+    return d;
+}
+
+// Gaspari-Cohn weight (Section 3.2.2), both branches in nested (Horner) form.
+__device__ __forceinline__ double gaspari_cohn(double d) {
+    if (d <= 1.0) return 1.0 + d * d * (-5.0 / 3.0 + d * (0.625 + d * (0.5 - 0.25 * d)));
+    if (d < 2.0)
+        return d * d * (5.0 / 3.0 + d * (0.625 + d * (-0.5 + d * (1.0 / 12.0)))) - 5.0 * d + 4.0 -
+               (2.0 / 3.0) / d;
+    return 0.0;
+}
+
+// ---- Double-binary32 arithmetic -------------------------------------------
+// GB300 issues FP64 at 1/64 of the binary32 rate, so accurate products run
+// in binary32 with error-free transformations and a second accumulator
+// (Knuth's TwoSum; the product error from one FMA, as in Dekker's
+// double-length products; accumulated as in Ogita, Rump and Oishi,
+// "Accurate sum and dot product", 2005). A binary32 factor y is exact and an
+// FP64 factor is split into hi + lo binary32 parts, so every term
+// a y = ah y + al y enters with ah y exact and al y to 2^-48; the sums carry
+// a relative error ~ n 2^-48 of sum |terms|. The _rn intrinsics keep the
+// compiler from fusing or reordering these steps.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float z = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
+}
+
+// (s, c) += (ah + al) y.
+__device__ __forceinline__ void df_acc(float& s, float& c, float ah, float al, float y) {
+    const float p = __fmul_rn(ah, y);
+    const float e = __fmaf_rn(ah, y, -p);  // ah y - p, exactly
+    float t;
+    two_sum(s, p, s, t);
+    c = __fadd_rn(c, __fadd_rn(t, __fmaf_rn(al, y, e)));
+}
+
+// (s, c) += a y for binary32 a and y (the product is exact as p + e).
+__device__ __forceinline__ void df_acc1(float& s, float& c, float a, float y) {
+    const float p = __fmul_rn(a, y);
+    const float e = __fmaf_rn(a, y, -p);
+    float t;
+    two_sum(s, p, s, t);
+    c = __fadd_rn(c, __fadd_rn(t, e));
+}
+
+__device__ __forceinline__ double df_value(float s, float c) { return (double)s + (double)c; }
+
+}  // namespace
+}  // namespace lbmgpu

@@ -26,37 +26,15 @@
 #include <cuda_bf16.h>
 
 #include "lbm_internal.cuh"
+#include "letkf_device.cuh"
 
 namespace lbmgpu {
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
 constexpr int NMAX = 128;  // largest local eigenproblem of the mixed-precision analysis
 constexpr int NMID = 64;   // largest held wholly in shared memory; the FP64 analysis' limit
 constexpr int NREG = 32;   // largest one handled by the register Jacobi
 constexpr int kMaxSweeps = 30;
-
-template <typename R>
-__device__ __forceinline__ R warp_sum(R v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    return v;
-}
-
-__device__ __forceinline__ int min_image(int d, int n) {
-    if (d > n / 2) d -= n;
-    if (d < -(n / 2)) d += n;
-    return d;
-}
-
-// Gaspari-Cohn weight, both branches in nested (Horner) form.
-__device__ __forceinline__ double gaspari_cohn(double d) {
-    if (d <= 1.0) return 1.0 + d * d * (-5.0 / 3.0 + d * (0.625 + d * (0.5 - 0.25 * d)));
-    if (d < 2.0)
-        return d * d * (5.0 / 3.0 + d * (0.625 + d * (-0.5 + d * (1.0 / 12.0)))) - 5.0 * d + 4.0 -
-               (2.0 / 3.0) / d;
-    return 0.0;
-}
 
 // ------------------------------------------------------------------ K2
 template <typename T, bool SHIFT>
@@ -1586,32 +1564,7 @@ __device__ inline MixSmem carve_mix(unsigned char* raw, int k, int nl, int nm, f
     return s;
 }
 
-// ---- Double-binary32 products ---------------------------------------------
-// GB300 issues FP64 at 1/64 of the binary32 rate, so the refinement's three
-// n^3 products run in binary32 with error-free transformations and a second
-// accumulator (Knuth's TwoSum; the product error from one FMA, as in
-// Dekker's double-length products; accumulated as in Ogita, Rump and Oishi,
-// "Accurate sum and dot product", 2005). A binary32 basis entry y is exact,
-// an FP64 matrix entry is split into hi + lo binary32 parts, so every term
-// a y = ah y + al y enters with ah y exact and al y to 2^-48; the sums carry
-// a relative error ~ n 2^-48 of sum |terms|, FP64-class. The _rn intrinsics
-// keep the compiler from fusing or reordering these steps.
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-    s = __fadd_rn(a, b);
-    const float z = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
-}
-
-// (s, c) += (ah + al) y.
-__device__ __forceinline__ void df_acc(float& s, float& c, float ah, float al, float y) {
-    const float p = __fmul_rn(ah, y);
-    const float e = __fmaf_rn(ah, y, -p);  // ah y - p, exactly
-    float t;
-    two_sum(s, p, s, t);
-    c = __fadd_rn(c, __fadd_rn(t, __fmaf_rn(al, y, e)));
-}
-
-__device__ __forceinline__ double df_value(float s, float c) { return (double)s + (double)c; }
+// ---- Double-binary32 products (two_sum, df_acc: letkf_device.cuh) ---------
 
 // C = P^T Q over the upper triangle (mirrored) in double-binary32: P binary32,
 // Q = Qhi + Qlo (Qlo may be null). store(i, j, value) writes both halves.
@@ -2034,6 +1987,12 @@ cudaError_t launch_obs_gram(const double* dY, int nobs, int k, double* G, cudaSt
     if (nobs <= 0) return cudaSuccess;
     dim3 grid((nobs + 127) / 128, nobs);
     obs_gram_kernel<<<grid, 128, 0, s>>>(dY, nobs, k, G);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_f32(const double* src, float* dst, size_t n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    to_f32_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, dst, n);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,1001 @@
+// Mixed-precision LETKF analysis over runs of neighbouring grid points
+// (arXiv 2308.03972, Section 3.2), observation-space form, unions of local
+// sets of up to 32 scalars.
+//
+// A run is R consecutive grid points of one lattice row. Its observation
+// scalars are the union of its points' local sets (Section 3.2.2: the
+// observations with r / d_cut < 2); at a point, a scalar outside its
+// support has weight zero, so the point's matrix A = Yh Yh^T
+// (Yh = diag(sqrt(rho)) dY over the union) has a zero row and column there.
+// Such a scalar adds nothing to the analysis: its entries of d-hat, of Yh
+// and of the transform's right-hand factor diag(sqrt(rho)) are zero. With
+// one index set for the whole run, the binary32 Jacobi of every point after
+// the first starts from the previous point's basis U: the Gaspari-Cohn
+// weights move by a few per cent from one grid point to the next, so
+// A' = U^T A U is already nearly diagonal (about 4% off the diagonal at
+// 256^2 with 8 x 8 observations) and the Jacobi needs about three sweeps
+// instead of six.
+//
+// Two kernels per chunk of runs:
+//  (J) run_jacobi_kernel, one warp per run, binary32: per point the weights
+//      (FP64 support test, the same as the other analysis kernels), A from a
+//      binary32 copy of the run's block of G = dY dY^T, the warm transform
+//      U^T A U, the cyclic Jacobi, a first-order re-orthonormalisation of
+//      the basis, U (I - E/2) with E = U^T U - I in binary32; the basis and
+//      the Jacobi's eigenvalue estimates go to scratch.
+//  (F) run_refine_kernel, one warp per point: A again, now in
+//      double-binary32, and the refinement, first order in the basis'
+//      non-orthogonality E = Y^T Y - I and in the off-diagonal of
+//      S = Y^T A Y:
+//        R = A Y - Y diag(l)   (double-binary32; l: the eigenvalue estimates,
+//                               so R is small),
+//        E                     (double-binary32),
+//        T = Y^T R             (binary32: R is ~1e-6 of A),
+//      so that S = (I + E) diag(l) + T exactly, and S' = M^{-1/2} S M^{-1/2}
+//      (M = I + E; Y M^{-1/2} is orthonormal) is, to first order in E,
+//        S'_ic = T_ic + E_ic (l_c - l_i) / 2   (i != c),
+//        S'_cc = l_c + T_cc - E_cc T_cc - E_cc^2 l_c   (FP64);
+//      then the first-order (Daleckii-Krein) matrix functions
+//      h(S') = (aI+S')^{-1} and g(S') = ((aI+S')^{-1/2} - a^{-1/2} I) S'^{-1}
+//      with the same first-order basis factor, the binary32 transform and
+//      the in-place update of the nine f.
+// With w-bar = Yh^T (aI+A)^{-1} d-hat and C^{-1/2} = a^{-1/2} I + Yh^T g(A) Yh
+// (C = aI + Yh^T Yh, a = (k-1)/beta) the update is
+//   x^a_m = xbar + Z v + sqrt(beta) dx_m + sqrt(k-1) Z g(A) yh_m,
+//   Z = dX Yh^T, v = (aI+A)^{-1} d-hat.
+#include <cmath>
+#include <cstdint>
+
+#include "lbm_internal.cuh"
+#include "letkf_device.cuh"
+
+namespace lbmgpu {
+namespace {
+
+constexpr int kRunSweeps = 30;  // sweep cap of one Jacobi
+
+struct RunArgs {
+    float* f;
+    int nx, ny, k, R;
+    ObsParams o;
+    const float2* G2;   // [nobs][nobs] G = dY dY^T as binary32 (hi, lo)
+    double d_cut, beta;
+    int* flags;
+    int run0, nruns;    // runs of this chunk
+    float* Yg;          // [chunk cells][NS][NS] basis, row c = column c of Y
+    float* lamg;        // [chunk cells][NS] eigenvalue estimates
+    int* rinfo;         // [chunk runs][1 + 32] union size, then its scalars
+};
+
+__host__ __device__ inline int run_cell_floats(int ns) { return ns * ns + ns; }
+constexpr int kInfo = 33;
+
+// ---- cp.async staging of one grid point's ensemble ------------------------
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// The nine rows f[a][cell][0..k) into dX[a][0..k).
+__device__ __forceinline__ void stage_point(const RunArgs& ra, float* dX, size_t cell, int lane) {
+    const size_t plane = (size_t)ra.nx * ra.ny * ra.k;
+    const int k = ra.k;
+    if ((k & 3) == 0) {
+        const int kq = k >> 2;
+        for (int e = lane; e < 9 * kq; e += 32) {
+            const int a = e / kq, m4 = e - a * kq;
+            cp_async16(dX + a * k + 4 * m4, ra.f + a * plane + cell * k + 4 * m4);
+        }
+    } else {
+        for (int e = lane; e < 9 * k; e += 32) {
+            const int a = e / k, m = e - a * k;
+            cp_async4(dX + a * k + m, ra.f + a * plane + cell * k + m);
+        }
+    }
+    cp_async_commit();
+}
+
+// a[idx] for a runtime idx in [0, NS), NS <= 32: five levels of selects on
+// the bits of idx (depth 5 instead of a chain of NS).
+template <int NS>
+__device__ __forceinline__ float pick_reg(const float (&a)[NS], int idx) {
+    static_assert(NS >= 2 && NS <= 32, "pick_reg");
+    constexpr int N1 = (NS + 1) / 2, N2 = (N1 + 1) / 2, N3 = (N2 + 1) / 2, N4 = (N3 + 1) / 2;
+    const bool b0 = idx & 1, b1 = idx & 2, b2 = idx & 4, b3 = idx & 8, b4 = idx & 16;
+    float v1[N1], v2[N2], v3[N3], v4[N4];
+#pragma unroll
+    for (int i = 0; i < N1; ++i) v1[i] = (2 * i + 1 < NS && b0) ? a[2 * i + 1 < NS ? 2 * i + 1 : 2 * i] : a[2 * i];
+#pragma unroll
+    for (int i = 0; i < N2; ++i) v2[i] = (2 * i + 1 < N1 && b1) ? v1[2 * i + 1 < N1 ? 2 * i + 1 : 2 * i] : v1[2 * i];
+#pragma unroll
+    for (int i = 0; i < N3; ++i) v3[i] = (2 * i + 1 < N2 && b2) ? v2[2 * i + 1 < N2 ? 2 * i + 1 : 2 * i] : v2[2 * i];
+#pragma unroll
+    for (int i = 0; i < N4; ++i) v4[i] = (2 * i + 1 < N3 && b3) ? v3[2 * i + 1 < N3 ? 2 * i + 1 : 2 * i] : v3[2 * i];
+    return (N4 > 1 && b4) ? v4[N4 > 1 ? 1 : 0] : v4[0];
+}
+
+// Weight sqrt(rho-tilde) of observation point j for scalar q at grid point
+// (x, y): the local-set test of the other analysis kernels (FP64, the same
+// operations), zero outside the support.
+__device__ __forceinline__ double obs_weight(const RunArgs& ra, int j, int q, int x, int y) {
+    const ObsParams& o = ra.o;
+    const int dx = min_image(o.ix[j] - x, ra.nx);
+    const int dy = min_image(o.iy[j] - y, ra.ny);
+    const double d2 = (double)dx * dx + (double)dy * dy;
+    const double lim2 = (2.0 * ra.d_cut + 1.0) * (2.0 * ra.d_cut + 1.0);
+    if (d2 > lim2) return 0.0;
+    const double dist = sqrt(d2) / ra.d_cut;
+    if (!(dist < 2.0)) return 0.0;
+    const double g = gaspari_cohn(dist);
+    if (!(g > 0.0)) return 0.0;
+    const double sig = q == 0 ? o.sigma_u : (q == 1 ? o.sigma_v : o.sigma_r);
+    return sqrt(g) / sig;
+}
+
+// ---- per-run union of the local sets --------------------------------------
+// Observation points with r / d_cut < 2 at some cell of [xa, xb) in row y,
+// in increasing order, into pts; their scalars into gi. The test is the
+// local-set test on the smallest squared distance over the cells (the test
+// is monotone in it). Returns the number of scalars; above cap the lists
+// are incomplete.
+__device__ int run_union(const RunArgs& ra, int* pts, int* gi, int y, int xa, int xb, int cap, int lane) {
+    const ObsParams& o = ra.o;
+    const double lim2 = (2.0 * ra.d_cut + 1.0) * (2.0 * ra.d_cut + 1.0);
+    const int maxpts = cap / o.nvar;
+    int count = 0;
+    for (int j0 = 0; j0 < o.npts; j0 += 32) {
+        const int j = j0 + lane;
+        bool in = false;
+        if (j < o.npts) {
+            const int dy = min_image(o.iy[j] - y, ra.ny);
+            int dxm = ra.nx;
+            for (int x = xa; x < xb; ++x) {
+                const int dx = abs(min_image(o.ix[j] - x, ra.nx));
+                dxm = dx < dxm ? dx : dxm;
+            }
+            const double d2 = (double)dxm * dxm + (double)dy * dy;
+            if (d2 <= lim2) in = sqrt(d2) / ra.d_cut < 2.0;
+        }
+        const unsigned bal = __ballot_sync(kFull, in);
+        if (in) {
+            const int pos = count + __popc(bal & ((1u << lane) - 1u));
+            if (pos < maxpts) pts[pos] = j;
+        }
+        count += __popc(bal);
+    }
+    __syncwarp();
+    const int nu = o.nvar * count;
+    if (nu <= cap)
+        for (int c = lane; c < nu; c += 32) gi[c] = o.nvar * pts[c / o.nvar] + c % o.nvar;
+    __syncwarp();
+    return nu;
+}
+
+// ---- binary32 Jacobi, warm or cold (kernel J) -----------------------------
+// Cyclic Jacobi with the round-robin (tournament) ordering on NS players
+// (NS even; players >= n are zero padding). Lane L owns column L of A, and
+// row L of the accumulated rotations U. The rows of A and the columns of U
+// are held in tournament-position order, so every round rotates the fixed
+// register pairs (t, NS-1-t) of both: the row rotation of A (J^T A) and the
+// column rotation of U (U J) combine the same two positions with the same
+// (c, s), which every lane has anyway; only A's column rotation (A J) needs
+// the partner lane's column. After a round, rows and columns move one
+// position (q -> q-1 for q >= 2, 1 -> NS-1, 0 stays); the player at
+// position q in round r is 0 for q = 0, else 1 + (q-1+r) mod (NS-1), and a
+// sweep of NS-1 rounds returns every row to its place. The rotated entry is
+// not reset to zero: what rounding leaves there is far below the
+// threshold. A rotation is skipped when |a_pq| <= thresh, a_pq as held by
+// the pair's p side (the lane at the lower position). The solve stops before
+// a sweep in which no pair would rotate: pmask (p_side_mask) marks the
+// players this lane meets as the p side, so the test reads exactly the
+// entries the sweep would test (rounding leaves A slightly asymmetric, so
+// the other side's copies do not decide). Returns the number of sweeps
+// counting that last one, or -1 at the cap; lam: the lane's diagonal entry,
+// tracked analytically.
+template <int NS>
+__device__ unsigned p_side_mask(int lane) {
+    constexpr int m1 = NS - 1;
+    unsigned mask = 0u;
+    if (lane >= NS) return 0u;
+    for (int r = 0; r < m1; ++r) {
+        const int q = (lane == 0) ? 0 : 1 + ((lane - 1 - r + 2 * m1) % m1);
+        const int qp = m1 - q;
+        const int partner = (qp == 0) ? 0 : 1 + ((qp - 1 + r) % m1);
+        if (q < NS / 2) mask |= 1u << partner;
+    }
+    return mask;
+}
+
+template <int NS>
+__device__ int jacobi_rows(float (&a)[NS], float (&ur)[NS], int lane, unsigned pmask, float thresh, float& lam) {
+    float dg = pick_reg<NS>(a, lane < NS ? lane : 0);
+    if (lane >= NS) dg = 0.0f;
+    constexpr int m1 = NS - 1;
+    for (int sweep = 0; sweep < kRunSweeps; ++sweep) {
+        float mx = 0.0f;
+#pragma unroll
+        for (int i = 0; i < NS; ++i) mx = ((pmask >> i) & 1u) ? fmaxf(mx, fabsf(a[i])) : mx;
+        if (__all_sync(kFull, !(mx > thresh))) {
+            lam = dg;
+            return sweep + 1;
+        }
+        for (int r = 0; r < m1; ++r) {
+            const int q = (lane == 0) ? 0 : 1 + ((lane - 1 - r + 2 * m1) % m1);
+            const int qp = m1 - q;
+            const int partner = (qp == 0) ? 0 : 1 + ((qp - 1 + r) % m1);
+            const bool pside = q < NS / 2;
+            const float off = pick_reg<NS>(a, qp < NS ? qp : 0);
+            const float dp = __shfl_sync(kFull, dg, partner & 31);
+            float c = 1.0f, s = 0.0f, t = 0.0f;
+            bool rot = false;
+            if (pside && lane < NS && fabsf(off) > thresh) {
+                // Angle from the approximate reciprocal and rsqrt (a few
+                // ulp, no special cases): the refinement takes the basis
+                // from here. sqrt(x) = x rsqrt(x) on [1, 1e30]; the clamp
+                // keeps tau^2 finite, where the rotation is negligible.
+                const float tau = __fdividef(dp - dg, 2.0f * off);
+                const float x = fminf(fmaf(tau, tau, 1.0f), 1e30f);
+                const float root = x * rsqrtf(x);
+                t = __fdividef(tau >= 0.0f ? 1.0f : -1.0f, fabsf(tau) + root);
+                c = rsqrtf(fmaf(t, t, 1.0f));
+                s = t * c;
+                rot = true;
+            }
+            if (__ballot_sync(kFull, rot) != 0u) {
+#pragma unroll
+                for (int tt = 0; tt < NS / 2; ++tt) {
+                    const int pl = (tt == 0) ? 0 : 1 + ((tt - 1 + r) % m1);
+                    const float ct = __shfl_sync(kFull, c, pl);
+                    const float st = __shfl_sync(kFull, s, pl);
+                    const float x0 = a[tt], x1 = a[NS - 1 - tt];
+                    a[tt] = fmaf(-st, x1, ct * x0);
+                    a[NS - 1 - tt] = fmaf(st, x0, ct * x1);
+                    const float y0 = ur[tt], y1 = ur[NS - 1 - tt];
+                    ur[tt] = fmaf(-st, y1, ct * y0);
+                    ur[NS - 1 - tt] = fmaf(st, y0, ct * y1);
+                }
+                const int pl_mine = pside ? lane : partner;
+                const float cm = __shfl_sync(kFull, c, pl_mine & 31);
+                const float sm_ = __shfl_sync(kFull, s, pl_mine & 31);
+                const float tm = __shfl_sync(kFull, t, pl_mine & 31);
+                const float om = __shfl_sync(kFull, off, pl_mine & 31);
+                dg = pside ? dg - tm * om : dg + tm * om;
+                const float sg = pside ? -sm_ : sm_;
+#pragma unroll
+                for (int i = 0; i < NS; ++i) {
+                    const float th = __shfl_sync(kFull, a[i], partner & 31);
+                    a[i] = fmaf(sg, th, cm * a[i]);
+                }
+            }
+            {
+                const float a1 = a[1], u1 = ur[1];
+#pragma unroll
+                for (int i = 1; i < NS - 1; ++i) {
+                    a[i] = a[i + 1];
+                    ur[i] = ur[i + 1];
+                }
+                a[NS - 1] = a1;
+                ur[NS - 1] = u1;
+            }
+        }
+    }
+    lam = dg;
+    return -1;
+}
+
+// Shared memory of one warp of kernel J (floats): header pts[32], gi[32]
+// (ints), weights w[NS], the run's block of G (GU, binary32), the basis rows
+// Us (row i of U) and a scratch matrix Vs.
+template <int NS>
+struct JLayout {
+    static constexpr int w = 64, GU = w + NS, Us = GU + NS * NS, Vs = Us + NS * NS;
+    static constexpr int total = Vs + NS * NS;
+};
+
+template <int NS>
+__global__ void __launch_bounds__(32, 18) run_jacobi_kernel(RunArgs ra) {
+    extern __shared__ __align__(16) float smj[];
+    using L = JLayout<NS>;
+    int* const pts = reinterpret_cast<int*>(smj);
+    int* const gi = pts + 32;
+    float* const wv = smj + L::w;
+    float* const GU = smj + L::GU;
+    float* const Us = smj + L::Us;
+    float* const Vs = smj + L::Vs;
+    const int lane = threadIdx.x;
+    const int rl = blockIdx.x;  // run within the chunk
+    const int run = ra.run0 + rl;
+    const int runs_x = (ra.nx + ra.R - 1) / ra.R;
+    const int y = run / runs_x;
+    const int xa = (run - y * runs_x) * ra.R;
+    const int xb = xa + ra.R < ra.nx ? xa + ra.R : ra.nx;
+    const ObsParams& o = ra.o;
+    const int nobs = o.nvar * o.npts;
+    int* info = ra.rinfo + (size_t)rl * kInfo;
+    const int nu = run_union(ra, pts, gi, y, xa, xb, NS, lane);
+    if (nu > NS) {  // the host sizes NS for the largest union; not reached
+        if (lane == 0) {
+            atomicOr(ra.flags, FLAG_TOOLARGE);
+            info[0] = -1;
+        }
+        return;
+    }
+    if (lane == 0) info[0] = nu;
+    if (lane < nu) info[1 + lane] = gi[lane];
+    const bool own = lane < NS, real = lane < nu;
+    const int c = lane;
+    const int gic = real ? gi[c] : 0;
+    const int jc = real ? pts[c / o.nvar] : 0;
+    const int qc = real ? c % o.nvar : 0;
+    // The run's block of G, binary32 (column c by lane c).
+    {
+        float gcol[NS];
+#pragma unroll
+        for (int i = 0; i < NS; ++i) gcol[i] = (real && i < nu) ? ra.G2[(size_t)gi[i] * nobs + gic].x : 0.0f;
+        if (own) {
+#pragma unroll
+            for (int i = 0; i < NS; ++i) GU[i * NS + c] = gcol[i];
+        }
+    }
+    float ur[NS];
+#pragma unroll
+    for (int i = 0; i < NS; ++i) ur[i] = (i == c) ? 1.0f : 0.0f;
+    const unsigned pmask = p_side_mask<NS>(lane);
+    bool warm = false;
+    for (int x = xa; x < xb; ++x) {
+        const size_t lc = (size_t)(rl * ra.R + (x - xa));  // cell within the chunk
+        const double w = real ? obs_weight(ra, jc, qc, x, y) : 0.0;
+        const float wf = (float)w;
+        const bool any = __ballot_sync(kFull, w > 0.0) != 0u;
+        if (!any) {
+            // No observation in range: nothing to solve (kernel F inflates).
+            if (lane == 0) ra.lamg[lc * NS] = -1.0f;  // marker read by kernel F
+            continue;
+        }
+        __syncwarp();  // the previous point is done with wv and Vs
+        if (own) wv[c] = wf;
+        __syncwarp();
+        // Column c of A = w_i G_ic w_c (binary32).
+        float a[NS];
+#pragma unroll
+        for (int i4 = 0; i4 < NS / 4; ++i4) {
+            const float4 w4 = reinterpret_cast<const float4*>(wv)[i4];
+            const float wi[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+            for (int r = 0; r < 4; ++r) a[4 * i4 + r] = own ? wi[r] * GU[(4 * i4 + r) * NS + c] * wf : 0.0f;
+        }
+        if (warm) {
+            // V = A U (row c of V: sum_j A_cj U_j.), then X = U^T V (row c of
+            // X: sum_i U_ic V_i.); X is symmetric, so row c is column c.
+            float acc[NS];
+#pragma unroll
+            for (int i = 0; i < NS; ++i) acc[i] = 0.0f;
+#pragma unroll
+            for (int j = 0; j < NS; ++j) {
+#pragma unroll
+                for (int i4 = 0; i4 < NS / 4; ++i4) {
+                    const float4 u4 = reinterpret_cast<const float4*>(Us + j * NS)[i4];
+                    acc[4 * i4] = fmaf(a[j], u4.x, acc[4 * i4]);
+                    acc[4 * i4 + 1] = fmaf(a[j], u4.y, acc[4 * i4 + 1]);
+                    acc[4 * i4 + 2] = fmaf(a[j], u4.z, acc[4 * i4 + 2]);
+                    acc[4 * i4 + 3] = fmaf(a[j], u4.w, acc[4 * i4 + 3]);
+                }
+            }
+            if (own) {
+#pragma unroll
+                for (int i4 = 0; i4 < NS / 4; ++i4)
+                    reinterpret_cast<float4*>(Vs + c * NS)[i4] =
+                        make_float4(acc[4 * i4], acc[4 * i4 + 1], acc[4 * i4 + 2], acc[4 * i4 + 3]);
+            }
+            __syncwarp();
+#pragma unroll
+            for (int i = 0; i < NS; ++i) acc[i] = 0.0f;
+#pragma unroll
+            for (int i = 0; i < NS; ++i) {
+                const float uic = own ? Us[i * NS + c] : 0.0f;
+#pragma unroll
+                for (int j4 = 0; j4 < NS / 4; ++j4) {
+                    const float4 v4 = reinterpret_cast<const float4*>(Vs + i * NS)[j4];
+                    acc[4 * j4] = fmaf(uic, v4.x, acc[4 * j4]);
+                    acc[4 * j4 + 1] = fmaf(uic, v4.y, acc[4 * j4 + 1]);
+                    acc[4 * j4 + 2] = fmaf(uic, v4.z, acc[4 * j4 + 2]);
+                    acc[4 * j4 + 3] = fmaf(uic, v4.w, acc[4 * j4 + 3]);
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < NS; ++i) a[i] = acc[i];
+            // The carried basis rows back from shared memory.
+            if (own) {
+#pragma unroll
+                for (int i4 = 0; i4 < NS / 4; ++i4) {
+                    const float4 u4 = reinterpret_cast<const float4*>(Us + c * NS)[i4];
+                    ur[4 * i4] = u4.x;
+                    ur[4 * i4 + 1] = u4.y;
+                    ur[4 * i4 + 2] = u4.z;
+                    ur[4 * i4 + 3] = u4.w;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < NS; ++i) ur[i] = (i == c) ? 1.0f : 0.0f;
+        }
+        float fro = 0.0f;
+#pragma unroll
+        for (int i = 0; i < NS; ++i) fro = fmaf(a[i], a[i], fro);
+        fro = warp_sum(fro);
+        float lamc = 0.0f;
+        // Stop at 1e-6 ||A||_F: the refinement is second order in the rest.
+        const int sweeps = jacobi_rows<NS>(a, ur, lane, pmask, 1e-6f * sqrtf(fro), lamc);
+        if (sweeps < 0 && lane == 0) atomicOr(ra.flags, FLAG_NOCONV);
+        if (o.sweep_hist && lane == 0) atomicAdd(&o.sweep_hist[(sweeps < 0 || sweeps > 31) ? 31 : sweeps], 1);
+        // Re-orthonormalise to first order: E = U^T U - I (binary32 is
+        // enough here: the refinement recomputes E exactly for the basis it
+        // receives), U <- U (I - E/2).
+        __syncwarp();
+        if (own) {
+#pragma unroll
+            for (int i4 = 0; i4 < NS / 4; ++i4)
+                reinterpret_cast<float4*>(Us + c * NS)[i4] = make_float4(ur[4 * i4], ur[4 * i4 + 1], ur[4 * i4 + 2], ur[4 * i4 + 3]);
+        }
+        __syncwarp();
+        {
+            float acc[NS];
+#pragma unroll
+            for (int i = 0; i < NS; ++i) acc[i] = (i == c) ? -1.0f : 0.0f;
+#pragma unroll
+            for (int i = 0; i < NS; ++i) {
+                const float uic = own ? Us[i * NS + c] : 0.0f;
+#pragma unroll
+                for (int j4 = 0; j4 < NS / 4; ++j4) {
+                    const float4 u4 = reinterpret_cast<const float4*>(Us + i * NS)[j4];
+                    acc[4 * j4] = fmaf(uic, u4.x, acc[4 * j4]);
+                    acc[4 * j4 + 1] = fmaf(uic, u4.y, acc[4 * j4 + 1]);
+                    acc[4 * j4 + 2] = fmaf(uic, u4.z, acc[4 * j4 + 2]);
+                    acc[4 * j4 + 3] = fmaf(uic, u4.w, acc[4 * j4 + 3]);
+                }
+            }
+            // Row c of E (= column c) into Vs.
+            if (own) {
+#pragma unroll
+                for (int i4 = 0; i4 < NS / 4; ++i4)
+                    reinterpret_cast<float4*>(Vs + c * NS)[i4] =
+                        make_float4(acc[4 * i4], acc[4 * i4 + 1], acc[4 * i4 + 2], acc[4 * i4 + 3]);
+            }
+        }
+        __syncwarp();
+        {
+            float acc[NS];
+#pragma unroll
+            for (int i = 0; i < NS; ++i) acc[i] = 0.0f;
+#pragma unroll
+            for (int j = 0; j < NS; ++j) {
+#pragma unroll
+                for (int i4 = 0; i4 < NS / 4; ++i4) {
+                    const float4 e4 = reinterpret_cast<const float4*>(Vs + j * NS)[i4];
+                    acc[4 * i4] = fmaf(ur[j], e4.x, acc[4 * i4]);
+                    acc[4 * i4 + 1] = fmaf(ur[j], e4.y, acc[4 * i4 + 1]);
+                    acc[4 * i4 + 2] = fmaf(ur[j], e4.z, acc[4 * i4 + 2]);
+                    acc[4 * i4 + 3] = fmaf(ur[j], e4.w, acc[4 * i4 + 3]);
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < NS; ++i) ur[i] = fmaf(-0.5f, acc[i], ur[i]);
+        }
+        __syncwarp();  // Us is rewritten below
+        if (own) {
+#pragma unroll
+            for (int i4 = 0; i4 < NS / 4; ++i4)
+                reinterpret_cast<float4*>(Us + c * NS)[i4] = make_float4(ur[4 * i4], ur[4 * i4 + 1], ur[4 * i4 + 2], ur[4 * i4 + 3]);
+        }
+        __syncwarp();
+        // Out: row c of Y^T (= column c of Y = column c of Us) and l_c.
+        if (own) {
+            float* yo = ra.Yg + lc * NS * NS + (size_t)c * NS;
+#pragma unroll
+            for (int i4 = 0; i4 < NS / 4; ++i4)
+                reinterpret_cast<float4*>(yo)[i4] =
+                    make_float4(Us[(4 * i4) * NS + c], Us[(4 * i4 + 1) * NS + c], Us[(4 * i4 + 2) * NS + c],
+                                Us[(4 * i4 + 3) * NS + c]);
+            ra.lamg[lc * NS + c] = lamc;
+        }
+        warm = true;
+    }
+}
+
+// Shared memory of one warp of kernel F (floats), matrices of row stride NS:
+//   Ah  [NS][NS]  A, high half; then E
+//   Al  [NS][NS]  A, low half; then S' (off the diagonal), then g(S')
+//   Yt  [NS][NS]  basis: row c holds column c of Y
+//   Zb  [NS][NS]  scratch: R, then Z (rows 0..8) and Z Y (rows 9..17)
+//   lsq [NS] (FP64) sqrt(rho-tilde); wh, wl its binary32 halves; dh d-hat;
+//   lam eigenvalue estimates; vu sqrt(a + s_i); va 1/(u_i (u_i + sqrt a));
+//   vh 1/(a + s_i); vt1 Y^T d-hat; vt2 h(S') vt1; vv Y vt2; xbar [32]
+//   means (0..8) and Z v (9..17); gi [32] (ints); dX [9][k].
+template <int NS>
+struct FLayout {
+    static constexpr int ZR = NS > 18 ? NS : 18;
+    static constexpr int Ah = 0, Al = NS * NS, Yt = 2 * NS * NS, Zb = 3 * NS * NS;
+    static constexpr int lsq = Zb + ZR * NS;
+    static constexpr int wh = lsq + 2 * NS, wl = wh + NS, dh = wl + NS, lam = dh + NS;
+    static constexpr int vu = lam + NS, va = vu + NS, vh = va + NS, vt1 = vh + NS, vt2 = vt1 + NS;
+    static constexpr int vv = vt2 + NS, xbar = vv + NS, gi = xbar + 32, dX = gi + 32;
+    static_assert(NS % 4 == 0, "rows of 16 bytes");
+};
+
+template <int NS>
+__host__ __device__ inline size_t run_f_smem_bytes(int k) {
+    return ((size_t)FLayout<NS>::dX + 9 * (size_t)k) * 4;
+}
+
+template <int NS>
+__global__ void __launch_bounds__(32, 12) run_refine_kernel(RunArgs ra) {
+    extern __shared__ __align__(16) float smf[];
+    using L = FLayout<NS>;
+    float* const Ah = smf + L::Ah;
+    float* const Al = smf + L::Al;
+    float* const Yt = smf + L::Yt;
+    float* const Zb = smf + L::Zb;
+    double* const lsq = reinterpret_cast<double*>(smf + L::lsq);
+    float* const vwh = smf + L::wh;
+    float* const vwl = smf + L::wl;
+    float* const dh = smf + L::dh;
+    float* const vlam = smf + L::lam;
+    float* const vu = smf + L::vu;
+    float* const va = smf + L::va;
+    float* const vh = smf + L::vh;
+    float* const vt1 = smf + L::vt1;
+    float* const vt2 = smf + L::vt2;
+    float* const vv = smf + L::vv;
+    float* const xbar = smf + L::xbar;
+    int* const gi = reinterpret_cast<int*>(smf + L::gi);
+    float* const dX = smf + L::dX;
+    const ObsParams& o = ra.o;
+    const int k = ra.k;
+    const int nobs = o.nvar * o.npts;
+    const size_t plane = (size_t)ra.nx * ra.ny * k;
+    const int lane = threadIdx.x;
+    const int lc = blockIdx.x;  // cell within the chunk
+    const int rl = lc / ra.R;
+    const int run = ra.run0 + rl;
+    const int runs_x = (ra.nx + ra.R - 1) / ra.R;
+    const int y = run / runs_x;
+    const int x = (run - y * runs_x) * ra.R + (lc - rl * ra.R);
+    if (x >= ra.nx) return;  // past the end of a ragged last run
+    const size_t cell = (size_t)y * ra.nx + x;
+    stage_point(ra, dX, cell, lane);
+    const float sbeta = (float)sqrt(ra.beta);
+    const int* info = ra.rinfo + (size_t)rl * kInfo;
+    const int nu = info[0];
+    const float lam_mark = ra.lamg[(size_t)lc * NS];
+    if (nu < 0) return;  // reported by kernel J
+    if (nu == 0 || lam_mark == -1.0f) {
+        // No observation in range: x^a = xbar + sqrt(beta) dx.
+        cp_async_wait_all();
+        __syncwarp();
+        float* fc = ra.f + cell * k;
+        for (int aq = 0; aq < 9; ++aq) {
+            float s = 0.0f;
+            for (int m = lane; m < k; m += 32) s += dX[aq * k + m];
+            const float mean = warp_sum(s) / (float)k;
+            for (int m = lane; m < k; m += 32) fc[aq * plane + m] = fmaf(sbeta, dX[aq * k + m] - mean, mean);
+        }
+        return;
+    }
+    const double aa = (k - 1) / ra.beta;
+    const double rs = sqrt(aa);
+    const float rsf = (float)rs;
+    const float sk = (float)sqrt((double)(k - 1));
+    const bool own = lane < NS;
+    const bool real = lane < nu;
+    const int c = lane;
+    if (lane < nu) gi[lane] = info[1 + lane];
+    // The basis (Y^T rows) and eigenvalue estimates.
+    {
+        const float4* src = reinterpret_cast<const float4*>(ra.Yg + (size_t)lc * NS * NS);
+        for (int e = lane; e < NS * NS / 4; e += 32) reinterpret_cast<float4*>(Yt)[e] = src[e];
+        if (own) vlam[c] = ra.lamg[(size_t)lc * NS + c];
+    }
+    __syncwarp();
+    const int gic = real ? gi[c] : 0;
+    const double w = real ? obs_weight(ra, gic / o.nvar, gic % o.nvar, x, y) : 0.0;
+    const float w_h = (float)w;
+    const float w_l = (float)(w - (double)w_h);
+    if (own) {
+        lsq[c] = w;
+        vwh[c] = w_h;
+        vwl[c] = w_l;
+        dh[c] = (float)(w * (real ? o.d[gic] : 0.0));
+    }
+    __syncwarp();
+    // Column c of A = w_i G_ic w_c in double-binary32, as hi + lo.
+    {
+        float2 gv[NS];
+#pragma unroll
+        for (int i = 0; i < NS; ++i)
+            gv[i] = (real && i < nu) ? ra.G2[(size_t)gi[i] * nobs + gic] : make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+            // w_i w_c in double-binary32, formed the same way by lanes i and
+            // c (so A is exactly symmetric), then times G_ic.
+            const float wih = vwh[i], wil = vwl[i];
+            const float p = wih * w_h;
+            float e = fmaf(wih, w_h, -p);
+            e += wih * w_l + wil * w_h;
+            const float q = p * gv[i].x;
+            float qe = fmaf(p, gv[i].x, -q);
+            qe = fmaf(p, gv[i].y, fmaf(e, gv[i].x, qe));
+            const float hv = q + qe;
+            const float lv = qe - (hv - q);
+            if (own) {
+                Ah[i * NS + c] = hv;
+                Al[i * NS + c] = lv;
+            }
+        }
+    }
+    float u[NS];  // column c of Y
+    if (own) {
+#pragma unroll
+        for (int i4 = 0; i4 < NS / 4; ++i4) {
+            const float4 y4 = reinterpret_cast<const float4*>(Yt + c * NS)[i4];
+            u[4 * i4] = y4.x;
+            u[4 * i4 + 1] = y4.y;
+            u[4 * i4 + 2] = y4.z;
+            u[4 * i4 + 3] = y4.w;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < NS; ++i) u[i] = 0.0f;
+    }
+    const float lamc = own ? vlam[c] : 0.0f;
+    __syncwarp();
+    // R = A Y - Y diag(l), column c, double-binary32, into Zb; four rows at
+    // a time (independent accumulations).
+    for (int i0 = 0; i0 < NS; i0 += 4) {
+        float sacc[4] = {0.0f, 0.0f, 0.0f, 0.0f}, cacc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int j4 = 0; j4 < NS / 4; ++j4) {
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const float4 h = reinterpret_cast<const float4*>(Ah + (i0 + r) * NS)[j4];
+                const float4 l = reinterpret_cast<const float4*>(Al + (i0 + r) * NS)[j4];
+                df_acc(sacc[r], cacc[r], h.x, l.x, u[4 * j4]);
+                df_acc(sacc[r], cacc[r], h.y, l.y, u[4 * j4 + 1]);
+                df_acc(sacc[r], cacc[r], h.z, l.z, u[4 * j4 + 2]);
+                df_acc(sacc[r], cacc[r], h.w, l.w, u[4 * j4 + 3]);
+            }
+        }
+        const float4 y4 = own ? reinterpret_cast<const float4*>(Yt + c * NS)[i0 / 4] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float yr[4] = {y4.x, y4.y, y4.z, y4.w};
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const float p = __fmul_rn(yr[r], lamc);
+            const float pe = __fmaf_rn(yr[r], lamc, -p);
+            if (own) Zb[(i0 + r) * NS + c] = __fadd_rn(__fsub_rn(sacc[r], p), __fsub_rn(cacc[r], pe));
+        }
+    }
+    float rr[NS];
+#pragma unroll
+    for (int j = 0; j < NS; ++j) rr[j] = own ? Zb[j * NS + c] : 0.0f;  // R column c
+    __syncwarp();  // A is no longer read: E and S' take its place
+    // E = Y^T Y - I (double-binary32) and T = Y^T R (binary32); S', four rows
+    // at a time.
+    float ecc = 0.0f, tcc = 0.0f;
+    for (int i0 = 0; i0 < NS; i0 += 4) {
+        float es[4] = {0.f, 0.f, 0.f, 0.f}, ec[4] = {0.f, 0.f, 0.f, 0.f}, tq[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int j4 = 0; j4 < NS / 4; ++j4) {
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const float4 yv = reinterpret_cast<const float4*>(Yt + (i0 + r) * NS)[j4];
+                df_acc1(es[r], ec[r], yv.x, u[4 * j4]);
+                df_acc1(es[r], ec[r], yv.y, u[4 * j4 + 1]);
+                df_acc1(es[r], ec[r], yv.z, u[4 * j4 + 2]);
+                df_acc1(es[r], ec[r], yv.w, u[4 * j4 + 3]);
+                tq[r] = fmaf(yv.x, rr[4 * j4], tq[r]);
+                tq[r] = fmaf(yv.y, rr[4 * j4 + 1], tq[r]);
+                tq[r] = fmaf(yv.z, rr[4 * j4 + 2], tq[r]);
+                tq[r] = fmaf(yv.w, rr[4 * j4 + 3], tq[r]);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int i = i0 + r;
+            const float e = __fadd_rn(__fsub_rn(es[r], i == c ? 1.0f : 0.0f), ec[r]);
+            if (i == c) {
+                ecc = e;
+                tcc = tq[r];
+            }
+            if (own) {
+                Ah[i * NS + c] = e;
+                Al[i * NS + c] = (i == c) ? 0.0f : fmaf(e, 0.5f * (lamc - vlam[i]), tq[r]);
+            }
+        }
+    }
+    // Matrix functions of S' (observation space).
+    const double dS = (double)lamc + (double)(tcc - ecc * tcc - ecc * ecc * lamc);
+    const double uu = sqrt(aa + dS);
+    const double alpha = 1.0 / (uu * (uu + rs));
+    const double hh = 1.0 / (aa + dS);
+    float t1c = 0.0f;
+#pragma unroll
+    for (int l = 0; l < NS; ++l) t1c = fmaf(u[l], dh[l], t1c);  // (Y^T d-hat)_c
+    const float hc = (float)hh, ac = (float)alpha, uc = (float)uu;
+    if (own) {
+        vu[c] = uc;
+        va[c] = ac;
+        vh[c] = hc;
+        vt1[c] = t1c;
+    }
+    __syncwarp();
+    {
+        // t2 = h(S') t1: h_ii = h_i, h_ij = -S'_ij h_i h_j, and the basis
+        // factor, minus E o (h_i + h_j)/2. g(S') column c over S'.
+        float tt = 0.0f, te = 0.0f;
+        const float gc = -ac / rsf;
+        for (int j = 0; j < NS; ++j) {
+            const float hj = vh[j], t1j = vt1[j];
+            const float sv = own ? Al[j * NS + c] : 0.0f;  // S'_jc (zero at j = c)
+            const float ev = own ? Ah[j * NS + c] : 0.0f;
+            tt = fmaf(sv, hj * t1j, tt);
+            te = fmaf(ev * (0.5f * (hc + hj)), t1j, te);
+            // g(S')_jc: diagonal -alpha/sqrt(a); off the diagonal
+            // S'_jc (u_j + u_c + sqrt a) alpha_j alpha_c / (sqrt(a) (u_j + u_c));
+            // minus E_jc (g_j + g_c)/2.
+            const float uj = vu[j], aj = va[j];
+            float gv;
+            if (j == c)
+                gv = gc;
+            else
+                gv = sv * (uj + uc + rsf) * aj * ac / (rsf * (uj + uc));
+            gv -= ev * (0.5f * (gc - aj / rsf));
+            if (own) Al[j * NS + c] = gv;
+        }
+        if (own) vt2[c] = hc * (t1c - tt) - te;
+    }
+    __syncwarp();
+    // v = Y t2 (lane c takes row c of Y: column c of Yt).
+    {
+        float v0 = 0.0f, v1 = 0.0f;
+#pragma unroll
+        for (int l = 0; l < NS; l += 2) {
+            v0 = fmaf(own ? Yt[l * NS + c] : 0.0f, vt2[l], v0);
+            v1 = fmaf(own ? Yt[(l + 1) * NS + c] : 0.0f, vt2[l + 1], v1);
+        }
+        if (own) vv[c] = v0 + v1;
+    }
+    // Transform. The ensemble of this point has arrived in dX.
+    cp_async_wait_all();
+    __syncwarp();
+    for (int aq = 0; aq < 9; ++aq) {
+        float s = 0.0f;
+        for (int m = lane; m < k; m += 32) s += dX[aq * k + m];
+        s = warp_sum(s);
+        const float mean = s / (float)k;
+        for (int m = lane; m < k; m += 32) dX[aq * k + m] -= mean;
+        if (lane == 0) xbar[aq] = mean;
+    }
+    __syncwarp();
+    // Z = dX Yh^T, column c: sqrt(rho)_c dX dY32[gi_c]^T.
+    float* const Z = Zb;            // [9][NS]
+    float* const ZY = Zb + 9 * NS;  // [9][NS]
+    {
+        float acc[9];
+#pragma unroll
+        for (int aq = 0; aq < 9; ++aq) acc[aq] = 0.0f;
+        if (real) {
+            const float* row = o.dY32 + (size_t)gic * k;
+            if ((k & 3) == 0) {
+                const float4* row4 = reinterpret_cast<const float4*>(row);
+#pragma unroll 4
+                for (int m4 = 0; m4 < (k >> 2); ++m4) {
+                    const float4 dy = row4[m4];
+#pragma unroll
+                    for (int aq = 0; aq < 9; ++aq) {
+                        const float4 xv = reinterpret_cast<const float4*>(dX + aq * k)[m4];
+                        acc[aq] = fmaf(xv.x, dy.x, acc[aq]);
+                        acc[aq] = fmaf(xv.y, dy.y, acc[aq]);
+                        acc[aq] = fmaf(xv.z, dy.z, acc[aq]);
+                        acc[aq] = fmaf(xv.w, dy.w, acc[aq]);
+                    }
+                }
+            } else {
+                for (int m = 0; m < k; ++m) {
+                    const float dy = row[m];
+#pragma unroll
+                    for (int aq = 0; aq < 9; ++aq) acc[aq] = fmaf(dX[aq * k + m], dy, acc[aq]);
+                }
+            }
+        }
+        if (own) {
+#pragma unroll
+            for (int aq = 0; aq < 9; ++aq) Z[aq * NS + c] = w_h * acc[aq];
+        }
+    }
+    __syncwarp();
+    // Z v, Z Y (column c).
+    if (lane < 9) {
+        float s = 0.0f;
+        for (int i = 0; i < NS; ++i) s = fmaf(Z[lane * NS + i], vv[i], s);
+        xbar[9 + lane] = s;
+    }
+    {
+        float acc[9];
+#pragma unroll
+        for (int aq = 0; aq < 9; ++aq) acc[aq] = 0.0f;
+#pragma unroll
+        for (int l = 0; l < NS; ++l) {
+#pragma unroll
+            for (int aq = 0; aq < 9; ++aq) acc[aq] = fmaf(Z[aq * NS + l], u[l], acc[aq]);
+        }
+        if (own) {
+#pragma unroll
+            for (int aq = 0; aq < 9; ++aq) ZY[aq * NS + c] = acc[aq];
+        }
+    }
+    __syncwarp();
+    // (Z Y) g(S') (column c) into Z.
+    {
+        float acc[9];
+#pragma unroll
+        for (int aq = 0; aq < 9; ++aq) acc[aq] = 0.0f;
+        for (int j = 0; j < NS; ++j) {
+            const float gj = own ? Al[j * NS + c] : 0.0f;
+#pragma unroll
+            for (int aq = 0; aq < 9; ++aq) acc[aq] = fmaf(ZY[aq * NS + j], gj, acc[aq]);
+        }
+        __syncwarp();  // Z is read (Z v, Z Y) before it is overwritten
+        if (own) {
+#pragma unroll
+            for (int aq = 0; aq < 9; ++aq) Z[aq * NS + c] = acc[aq];
+        }
+    }
+    __syncwarp();
+    // B = sqrt(k-1) (Z Y g) Y^T diag(sqrt rho), column c into ZY.
+    {
+        float acc[9];
+#pragma unroll
+        for (int aq = 0; aq < 9; ++aq) acc[aq] = 0.0f;
+        for (int i = 0; i < NS; ++i) {
+            const float yci = own ? Yt[i * NS + c] : 0.0f;  // Y[c][i]
+#pragma unroll
+            for (int aq = 0; aq < 9; ++aq) acc[aq] = fmaf(Z[aq * NS + i], yci, acc[aq]);
+        }
+        const float sl = sk * w_h;
+        __syncwarp();
+        if (own) {
+#pragma unroll
+            for (int aq = 0; aq < 9; ++aq) ZY[aq * NS + c] = sl * acc[aq];
+        }
+    }
+    __syncwarp();
+    // Update: x^a_m = xbar + Z v + sqrt(beta) dx_m + B yh_m.
+    {
+        float* fc = ra.f + cell * k;
+        for (int m = lane; m < k; m += 32) {
+            float acc[9];
+#pragma unroll
+            for (int aq = 0; aq < 9; ++aq) acc[aq] = fmaf(sbeta, dX[aq * k + m], xbar[aq] + xbar[9 + aq]);
+#pragma unroll 4
+            for (int i = 0; i < nu; ++i) {
+                const float dy = o.dY32[(size_t)gi[i] * k + m];
+#pragma unroll
+                for (int aq = 0; aq < 9; ++aq) acc[aq] = fmaf(ZY[aq * NS + i], dy, acc[aq]);
+            }
+#pragma unroll
+            for (int aq = 0; aq < 9; ++aq) fc[aq * plane + m] = acc[aq];
+        }
+    }
+}
+
+// G = dY dY^T split into binary32 (hi, lo).
+__global__ void split_gram_kernel(const double* __restrict__ G, float2* __restrict__ G2, size_t n) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        const double v = G[i];
+        const float h = (float)v;
+        G2[i] = make_float2(h, (float)(v - (double)h));
+    }
+}
+
+int run_ns(int maxunion) {
+    if (maxunion <= 8) return 8;
+    if (maxunion <= 16) return 16;
+    if (maxunion <= 24) return 24;
+    if (maxunion <= 28) return 28;
+    return 32;
+}
+
+constexpr size_t kRunScratchBudget = 320ull << 20;  // basis scratch per chunk
+
+long long run_chunk_runs(long long runs, int R, int ns) {
+    const size_t per_run = (size_t)R * run_cell_floats(ns) * 4 + kInfo * 4;
+    long long c = (long long)(kRunScratchBudget / per_run);
+    if (c < 1) c = 1;
+    return runs < c ? runs : c;
+}
+
+template <int NS>
+cudaError_t launch_runs_ns(RunArgs ra, long long runs, long long chunk, cudaStream_t s) {
+    const size_t shJ = (size_t)JLayout<NS>::total * 4;
+    const size_t shF = run_f_smem_bytes<NS>(ra.k);
+    cudaError_t e = cudaFuncSetAttribute(run_jacobi_kernel<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shJ);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(run_refine_kernel<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shF);
+    if (e != cudaSuccess) return e;
+    for (long long r0 = 0; r0 < runs; r0 += chunk) {
+        const long long nr = runs - r0 < chunk ? runs - r0 : chunk;
+        ra.run0 = (int)r0;
+        ra.nruns = (int)nr;
+        run_jacobi_kernel<NS><<<(unsigned)nr, 32, shJ, s>>>(ra);
+        run_refine_kernel<NS><<<(unsigned)(nr * ra.R), 32, shF, s>>>(ra);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t run_scratch_bytes(int nx, int ny, int nobs, int run_len, int maxunion) {
+    const int ns = run_ns(maxunion);
+    const long long runs = (long long)ny * ((nx + run_len - 1) / run_len);
+    const long long chunk = run_chunk_runs(runs, run_len, ns);
+    const size_t g2 = ((size_t)nobs * nobs * sizeof(float2) + 255) / 256 * 256;
+    const size_t yb = ((size_t)chunk * run_len * ns * ns * 4 + 255) / 256 * 256;
+    const size_t lb = ((size_t)chunk * run_len * ns * 4 + 255) / 256 * 256;
+    const size_t ib = (size_t)chunk * kInfo * 4;
+    return g2 + yb + lb + ib;
+}
+
+cudaError_t launch_analyze_runs(float* f, int nx, int ny, int k, const ObsParams& o, double d_cut,
+                                double beta, int run_len, int maxunion, int* flags, void* scratch,
+                                cudaStream_t s) {
+    if (run_len < 1 || maxunion > kRunMaxUnion || !o.dY32 || !scratch) return cudaErrorInvalidValue;
+    const int nobs = o.nvar * o.npts;
+    const size_t ng = (size_t)nobs * nobs;
+    const int ns = run_ns(maxunion);
+    const long long runs = (long long)ny * ((nx + run_len - 1) / run_len);
+    if (runs > 0x7fffffffLL / run_len) return cudaErrorInvalidConfiguration;
+    const long long chunk = run_chunk_runs(runs, run_len, ns);
+    unsigned char* p = reinterpret_cast<unsigned char*>(scratch);
+    float2* G2 = reinterpret_cast<float2*>(p);
+    p += (ng * sizeof(float2) + 255) / 256 * 256;
+    float* Yg = reinterpret_cast<float*>(p);
+    p += ((size_t)chunk * run_len * ns * ns * 4 + 255) / 256 * 256;
+    float* lamg = reinterpret_cast<float*>(p);
+    p += ((size_t)chunk * run_len * ns * 4 + 255) / 256 * 256;
+    int* rinfo = reinterpret_cast<int*>(p);
+    // dY in binary32 for the transform (the same copy the chunked path makes).
+    cudaError_t e = launch_to_f32(o.dY, o.dY32, (size_t)nobs * k, s);
+    if (e != cudaSuccess) return e;
+    split_gram_kernel<<<(unsigned)((ng + 255) / 256), 256, 0, s>>>(o.G, G2, ng);
+    RunArgs ra;
+    ra.f = f;
+    ra.nx = nx;
+    ra.ny = ny;
+    ra.k = k;
+    ra.R = run_len;
+    ra.o = o;
+    ra.G2 = G2;
+    ra.d_cut = d_cut;
+    ra.beta = beta;
+    ra.flags = flags;
+    ra.run0 = 0;
+    ra.nruns = 0;
+    ra.Yg = Yg;
+    ra.lamg = lamg;
+    ra.rinfo = rinfo;
+    switch (ns) {
+        case 8: return launch_runs_ns<8>(ra, runs, chunk, s);
+        case 16: return launch_runs_ns<16>(ra, runs, chunk, s);
+        case 24: return launch_runs_ns<24>(ra, runs, chunk, s);
+        case 28: return launch_runs_ns<28>(ra, runs, chunk, s);
+        default: return launch_runs_ns<32>(ra, runs, chunk, s);
+    }
+}
+
+}  // namespace lbmgpu
