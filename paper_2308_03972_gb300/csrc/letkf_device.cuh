@@ -67,5 +67,69 @@ __device__ __forceinline__ void df_acc1(float& s, float& c, float a, float y) {
 
 __device__ __forceinline__ double df_value(float s, float c) { return (double)s + (double)c; }
 
+// ---- Packed binary32 pairs (sm_100 family: add/sub/mul/fma .f32x2) --------
+// Two independent binary32 values in one 64-bit register, low half first
+// (the lower address when loaded from memory). Each packed operation rounds
+// each half exactly as the scalar operation would.
+typedef unsigned long long f2x;
+
+__device__ __forceinline__ f2x f2pack(float lo, float hi) {
+    f2x r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2unpack(f2x v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2x f2add(f2x a, f2x b) {
+    f2x d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2x f2sub(f2x a, f2x b) {
+    f2x d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2x f2mul(f2x a, f2x b) {
+    f2x d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2x f2fma(f2x a, f2x b, f2x c) {
+    f2x d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// df_acc on two independent accumulations at once: (S, C) += (AH + AL) Y,
+// with NY = -Y. The steps, and so every rounding, are those of df_acc: the
+// product's error is fma(ah, y, -p) with -p = ah (-y) exact, and TwoSum's
+// b - z is taken as -(z + (-p)).
+__device__ __forceinline__ void df2_acc(f2x& S, f2x& C, f2x AH, f2x AL, f2x Y, f2x NY) {
+    const f2x NP = f2mul(AH, NY);    // -p
+    const f2x E = f2fma(AH, Y, NP);  // ah y - p, exactly
+    const f2x S1 = f2sub(S, NP);     // s + p
+    const f2x Z = f2sub(S1, S);
+    const f2x T2 = f2sub(S, f2sub(S1, Z));
+    const f2x T3 = f2add(Z, NP);     // -(p - z)
+    const f2x T = f2sub(T2, T3);
+    C = f2add(C, f2add(T, f2fma(AL, Y, E)));
+    S = S1;
+}
+
+// df_acc1 on two accumulations: (S, C) += A Y (A binary32).
+__device__ __forceinline__ void df2_acc1(f2x& S, f2x& C, f2x A, f2x Y, f2x NY) {
+    const f2x NP = f2mul(A, NY);
+    const f2x E = f2fma(A, Y, NP);
+    const f2x S1 = f2sub(S, NP);
+    const f2x Z = f2sub(S1, S);
+    const f2x T2 = f2sub(S, f2sub(S1, Z));
+    const f2x T3 = f2add(Z, NP);
+    const f2x T = f2sub(T2, T3);
+    C = f2add(C, f2add(T, E));
+    S = S1;
+}
+
 }  // namespace
 }  // namespace lbmgpu

@@ -212,11 +212,22 @@ __device__ unsigned p_side_mask(int lane) {
     return mask;
 }
 
+// Rounds of a sweep are taken in blocks of UB (UB divides NS - 1): within a
+// block the rows stay where they are and round b of the block finds
+// position t in register reg(t, b) = 1 + (t - 1 + b) mod (NS - 1) (t >= 1),
+// so the registers move once per block, by UB positions.
+template <int NS>
+__host__ __device__ constexpr int jacobi_block() {
+    return ((NS - 1) % 3 == 0) ? 3 : 1;
+}
+
 template <int NS>
 __device__ int jacobi_rows(float (&a)[NS], float (&ur)[NS], int lane, unsigned pmask, float thresh, float& lam) {
+    constexpr int m1 = NS - 1;
+    constexpr int UB = jacobi_block<NS>();
+    static_assert(m1 % UB == 0, "block of rounds");
     float dg = pick_reg<NS>(a, lane < NS ? lane : 0);
     if (lane >= NS) dg = 0.0f;
-    constexpr int m1 = NS - 1;
     for (int sweep = 0; sweep < kRunSweeps; ++sweep) {
         float mx = 0.0f;
 #pragma unroll
@@ -225,63 +236,77 @@ __device__ int jacobi_rows(float (&a)[NS], float (&ur)[NS], int lane, unsigned p
             lam = dg;
             return sweep + 1;
         }
-        for (int r = 0; r < m1; ++r) {
-            const int q = (lane == 0) ? 0 : 1 + ((lane - 1 - r + 2 * m1) % m1);
-            const int qp = m1 - q;
-            const int partner = (qp == 0) ? 0 : 1 + ((qp - 1 + r) % m1);
-            const bool pside = q < NS / 2;
-            const float off = pick_reg<NS>(a, qp < NS ? qp : 0);
-            const float dp = __shfl_sync(kFull, dg, partner & 31);
-            float c = 1.0f, s = 0.0f, t = 0.0f;
-            bool rot = false;
-            if (pside && lane < NS && fabsf(off) > thresh) {
-                // Angle from the approximate reciprocal and rsqrt (a few
-                // ulp, no special cases): the refinement takes the basis
-                // from here. sqrt(x) = x rsqrt(x) on [1, 1e30]; the clamp
-                // keeps tau^2 finite, where the rotation is negligible.
-                const float tau = __fdividef(dp - dg, 2.0f * off);
-                const float x = fminf(fmaf(tau, tau, 1.0f), 1e30f);
-                const float root = x * rsqrtf(x);
-                t = __fdividef(tau >= 0.0f ? 1.0f : -1.0f, fabsf(tau) + root);
-                c = rsqrtf(fmaf(t, t, 1.0f));
-                s = t * c;
-                rot = true;
+        for (int r0 = 0; r0 < m1; r0 += UB) {
+#pragma unroll
+            for (int b = 0; b < UB; ++b) {
+                const int r = r0 + b;
+                const int q = (lane == 0) ? 0 : 1 + ((lane - 1 - r + 2 * m1) % m1);
+                const int qp = m1 - q;
+                const int partner = (qp == 0) ? 0 : 1 + ((qp - 1 + r) % m1);
+                const bool pside = q < NS / 2;
+                // Register of position qp in this block's frame.
+                int rq = qp - 1 + b;
+                rq = (qp == 0) ? 0 : 1 + (rq >= m1 ? rq - m1 : rq);
+                const float off = pick_reg<NS>(a, rq < NS ? rq : 0);
+                const float dp = __shfl_sync(kFull, dg, partner & 31);
+                float c = 1.0f, s = 0.0f, t = 0.0f;
+                bool rot = false;
+                if (pside && lane < NS && fabsf(off) > thresh) {
+                    // Angle from the approximate reciprocal and rsqrt (a few
+                    // ulp, no special cases): the refinement takes the basis
+                    // from here. sqrt(x) = x rsqrt(x) on [1, 1e30]; the clamp
+                    // keeps tau^2 finite, where the rotation is negligible.
+                    const float tau = __fdividef(dp - dg, 2.0f * off);
+                    const float x = fminf(fmaf(tau, tau, 1.0f), 1e30f);
+                    const float root = x * rsqrtf(x);
+                    t = __fdividef(tau >= 0.0f ? 1.0f : -1.0f, fabsf(tau) + root);
+                    c = rsqrtf(fmaf(t, t, 1.0f));
+                    s = t * c;
+                    rot = true;
+                }
+                if (__ballot_sync(kFull, rot) != 0u) {
+#pragma unroll
+                    for (int tt = 0; tt < NS / 2; ++tt) {
+                        int v = tt - 1 + r;
+                        v = v >= m1 ? v - m1 : v;
+                        const int pl = (tt == 0) ? 0 : 1 + v;
+                        const float ct = __shfl_sync(kFull, c, pl);
+                        const float st = __shfl_sync(kFull, s, pl);
+                        const int i0 = (tt == 0) ? 0 : 1 + ((tt - 1 + b) % m1);
+                        const int i1 = 1 + ((NS - 2 - tt + b) % m1);
+                        const float x0 = a[i0], x1 = a[i1];
+                        a[i0] = fmaf(-st, x1, ct * x0);
+                        a[i1] = fmaf(st, x0, ct * x1);
+                        const float y0 = ur[i0], y1 = ur[i1];
+                        ur[i0] = fmaf(-st, y1, ct * y0);
+                        ur[i1] = fmaf(st, y0, ct * y1);
+                    }
+                    const int pl_mine = pside ? lane : partner;
+                    const float cm = __shfl_sync(kFull, c, pl_mine & 31);
+                    const float sm_ = __shfl_sync(kFull, s, pl_mine & 31);
+                    const float tm = __shfl_sync(kFull, t, pl_mine & 31);
+                    const float om = __shfl_sync(kFull, off, pl_mine & 31);
+                    dg = pside ? dg - tm * om : dg + tm * om;
+                    const float sg = pside ? -sm_ : sm_;
+#pragma unroll
+                    for (int i = 0; i < NS; ++i) {
+                        const float th = __shfl_sync(kFull, a[i], partner & 31);
+                        a[i] = fmaf(sg, th, cm * a[i]);
+                    }
+                }
             }
-            if (__ballot_sync(kFull, rot) != 0u) {
+            // Rows move UB positions: position t takes register reg(t, UB).
+            float ta[NS], tu[NS];
 #pragma unroll
-                for (int tt = 0; tt < NS / 2; ++tt) {
-                    const int pl = (tt == 0) ? 0 : 1 + ((tt - 1 + r) % m1);
-                    const float ct = __shfl_sync(kFull, c, pl);
-                    const float st = __shfl_sync(kFull, s, pl);
-                    const float x0 = a[tt], x1 = a[NS - 1 - tt];
-                    a[tt] = fmaf(-st, x1, ct * x0);
-                    a[NS - 1 - tt] = fmaf(st, x0, ct * x1);
-                    const float y0 = ur[tt], y1 = ur[NS - 1 - tt];
-                    ur[tt] = fmaf(-st, y1, ct * y0);
-                    ur[NS - 1 - tt] = fmaf(st, y0, ct * y1);
-                }
-                const int pl_mine = pside ? lane : partner;
-                const float cm = __shfl_sync(kFull, c, pl_mine & 31);
-                const float sm_ = __shfl_sync(kFull, s, pl_mine & 31);
-                const float tm = __shfl_sync(kFull, t, pl_mine & 31);
-                const float om = __shfl_sync(kFull, off, pl_mine & 31);
-                dg = pside ? dg - tm * om : dg + tm * om;
-                const float sg = pside ? -sm_ : sm_;
-#pragma unroll
-                for (int i = 0; i < NS; ++i) {
-                    const float th = __shfl_sync(kFull, a[i], partner & 31);
-                    a[i] = fmaf(sg, th, cm * a[i]);
-                }
+            for (int i = 0; i < NS; ++i) {
+                const int src = (i == 0) ? 0 : 1 + ((i - 1 + UB) % m1);
+                ta[i] = a[src];
+                tu[i] = ur[src];
             }
-            {
-                const float a1 = a[1], u1 = ur[1];
 #pragma unroll
-                for (int i = 1; i < NS - 1; ++i) {
-                    a[i] = a[i + 1];
-                    ur[i] = ur[i + 1];
-                }
-                a[NS - 1] = a1;
-                ur[NS - 1] = u1;
+            for (int i = 0; i < NS; ++i) {
+                a[i] = ta[i];
+                ur[i] = tu[i];
             }
         }
     }
@@ -299,7 +324,7 @@ struct JLayout {
 };
 
 template <int NS>
-__global__ void __launch_bounds__(32, 18) run_jacobi_kernel(RunArgs ra) {
+__global__ void __launch_bounds__(32, 16) run_jacobi_kernel(RunArgs ra) {
     extern __shared__ __align__(16) float smj[];
     using L = JLayout<NS>;
     int* const pts = reinterpret_cast<int*>(smj);
@@ -372,19 +397,21 @@ __global__ void __launch_bounds__(32, 18) run_jacobi_kernel(RunArgs ra) {
         }
         if (warm) {
             // V = A U (row c of V: sum_j A_cj U_j.), then X = U^T V (row c of
-            // X: sum_i U_ic V_i.); X is symmetric, so row c is column c.
+            // X: sum_i U_ic V_i.); X is symmetric, so row c is column c. G's
+            // block is symmetric, so A_cj = w_c GU_cj w_j.
             float acc[NS];
 #pragma unroll
             for (int i = 0; i < NS; ++i) acc[i] = 0.0f;
-#pragma unroll
             for (int j = 0; j < NS; ++j) {
+                const float acj = own ? wv[j] * GU[c * NS + j] * wf : 0.0f;
+                const float4* u4 = reinterpret_cast<const float4*>(Us + j * NS);
 #pragma unroll
                 for (int i4 = 0; i4 < NS / 4; ++i4) {
-                    const float4 u4 = reinterpret_cast<const float4*>(Us + j * NS)[i4];
-                    acc[4 * i4] = fmaf(a[j], u4.x, acc[4 * i4]);
-                    acc[4 * i4 + 1] = fmaf(a[j], u4.y, acc[4 * i4 + 1]);
-                    acc[4 * i4 + 2] = fmaf(a[j], u4.z, acc[4 * i4 + 2]);
-                    acc[4 * i4 + 3] = fmaf(a[j], u4.w, acc[4 * i4 + 3]);
+                    const float4 uv = u4[i4];
+                    acc[4 * i4] = fmaf(acj, uv.x, acc[4 * i4]);
+                    acc[4 * i4 + 1] = fmaf(acj, uv.y, acc[4 * i4 + 1]);
+                    acc[4 * i4 + 2] = fmaf(acj, uv.z, acc[4 * i4 + 2]);
+                    acc[4 * i4 + 3] = fmaf(acj, uv.w, acc[4 * i4 + 3]);
                 }
             }
             if (own) {
@@ -396,16 +423,16 @@ __global__ void __launch_bounds__(32, 18) run_jacobi_kernel(RunArgs ra) {
             __syncwarp();
 #pragma unroll
             for (int i = 0; i < NS; ++i) acc[i] = 0.0f;
-#pragma unroll
             for (int i = 0; i < NS; ++i) {
                 const float uic = own ? Us[i * NS + c] : 0.0f;
+                const float4* v4 = reinterpret_cast<const float4*>(Vs + i * NS);
 #pragma unroll
                 for (int j4 = 0; j4 < NS / 4; ++j4) {
-                    const float4 v4 = reinterpret_cast<const float4*>(Vs + i * NS)[j4];
-                    acc[4 * j4] = fmaf(uic, v4.x, acc[4 * j4]);
-                    acc[4 * j4 + 1] = fmaf(uic, v4.y, acc[4 * j4 + 1]);
-                    acc[4 * j4 + 2] = fmaf(uic, v4.z, acc[4 * j4 + 2]);
-                    acc[4 * j4 + 3] = fmaf(uic, v4.w, acc[4 * j4 + 3]);
+                    const float4 vv = v4[j4];
+                    acc[4 * j4] = fmaf(uic, vv.x, acc[4 * j4]);
+                    acc[4 * j4 + 1] = fmaf(uic, vv.y, acc[4 * j4 + 1]);
+                    acc[4 * j4 + 2] = fmaf(uic, vv.z, acc[4 * j4 + 2]);
+                    acc[4 * j4 + 3] = fmaf(uic, vv.w, acc[4 * j4 + 3]);
                 }
             }
 #pragma unroll
@@ -448,16 +475,16 @@ __global__ void __launch_bounds__(32, 18) run_jacobi_kernel(RunArgs ra) {
             float acc[NS];
 #pragma unroll
             for (int i = 0; i < NS; ++i) acc[i] = (i == c) ? -1.0f : 0.0f;
-#pragma unroll
             for (int i = 0; i < NS; ++i) {
                 const float uic = own ? Us[i * NS + c] : 0.0f;
+                const float4* u4 = reinterpret_cast<const float4*>(Us + i * NS);
 #pragma unroll
                 for (int j4 = 0; j4 < NS / 4; ++j4) {
-                    const float4 u4 = reinterpret_cast<const float4*>(Us + i * NS)[j4];
-                    acc[4 * j4] = fmaf(uic, u4.x, acc[4 * j4]);
-                    acc[4 * j4 + 1] = fmaf(uic, u4.y, acc[4 * j4 + 1]);
-                    acc[4 * j4 + 2] = fmaf(uic, u4.z, acc[4 * j4 + 2]);
-                    acc[4 * j4 + 3] = fmaf(uic, u4.w, acc[4 * j4 + 3]);
+                    const float4 uv = u4[j4];
+                    acc[4 * j4] = fmaf(uic, uv.x, acc[4 * j4]);
+                    acc[4 * j4 + 1] = fmaf(uic, uv.y, acc[4 * j4 + 1]);
+                    acc[4 * j4 + 2] = fmaf(uic, uv.z, acc[4 * j4 + 2]);
+                    acc[4 * j4 + 3] = fmaf(uic, uv.w, acc[4 * j4 + 3]);
                 }
             }
             // Row c of E (= column c) into Vs.
@@ -470,18 +497,20 @@ __global__ void __launch_bounds__(32, 18) run_jacobi_kernel(RunArgs ra) {
         }
         __syncwarp();
         {
+            // U <- U (I - E/2), row c: sum_j U_cj E_j. (U_cj from shared memory).
             float acc[NS];
 #pragma unroll
             for (int i = 0; i < NS; ++i) acc[i] = 0.0f;
-#pragma unroll
             for (int j = 0; j < NS; ++j) {
+                const float ucj = own ? Us[c * NS + j] : 0.0f;
+                const float4* e4 = reinterpret_cast<const float4*>(Vs + j * NS);
 #pragma unroll
                 for (int i4 = 0; i4 < NS / 4; ++i4) {
-                    const float4 e4 = reinterpret_cast<const float4*>(Vs + j * NS)[i4];
-                    acc[4 * i4] = fmaf(ur[j], e4.x, acc[4 * i4]);
-                    acc[4 * i4 + 1] = fmaf(ur[j], e4.y, acc[4 * i4 + 1]);
-                    acc[4 * i4 + 2] = fmaf(ur[j], e4.z, acc[4 * i4 + 2]);
-                    acc[4 * i4 + 3] = fmaf(ur[j], e4.w, acc[4 * i4 + 3]);
+                    const float4 ev = e4[i4];
+                    acc[4 * i4] = fmaf(ucj, ev.x, acc[4 * i4]);
+                    acc[4 * i4 + 1] = fmaf(ucj, ev.y, acc[4 * i4 + 1]);
+                    acc[4 * i4 + 2] = fmaf(ucj, ev.z, acc[4 * i4 + 2]);
+                    acc[4 * i4 + 3] = fmaf(ucj, ev.w, acc[4 * i4 + 3]);
                 }
             }
 #pragma unroll
@@ -494,14 +523,12 @@ __global__ void __launch_bounds__(32, 18) run_jacobi_kernel(RunArgs ra) {
                 reinterpret_cast<float4*>(Us + c * NS)[i4] = make_float4(ur[4 * i4], ur[4 * i4 + 1], ur[4 * i4 + 2], ur[4 * i4 + 3]);
         }
         __syncwarp();
-        // Out: row c of Y^T (= column c of Y = column c of Us) and l_c.
+        // Out: row c of Y (= the re-orthonormalised U) and l_c.
         if (own) {
             float* yo = ra.Yg + lc * NS * NS + (size_t)c * NS;
 #pragma unroll
             for (int i4 = 0; i4 < NS / 4; ++i4)
-                reinterpret_cast<float4*>(yo)[i4] =
-                    make_float4(Us[(4 * i4) * NS + c], Us[(4 * i4 + 1) * NS + c], Us[(4 * i4 + 2) * NS + c],
-                                Us[(4 * i4 + 3) * NS + c]);
+                reinterpret_cast<float4*>(yo)[i4] = make_float4(ur[4 * i4], ur[4 * i4 + 1], ur[4 * i4 + 2], ur[4 * i4 + 3]);
             ra.lamg[lc * NS + c] = lamc;
         }
         warm = true;
@@ -511,8 +538,11 @@ __global__ void __launch_bounds__(32, 18) run_jacobi_kernel(RunArgs ra) {
 // Shared memory of one warp of kernel F (floats), matrices of row stride NS:
 //   Ah  [NS][NS]  A, high half; then E
 //   Al  [NS][NS]  A, low half; then S' (off the diagonal), then g(S')
-//   Yt  [NS][NS]  basis: row c holds column c of Y
+//   Ys  [NS][NS]  basis Y, row-major
 //   Zb  [NS][NS]  scratch: R, then Z (rows 0..8) and Z Y (rows 9..17)
+// Row groups of 8 read up to 4 floats past a matrix's last row; what
+// follows each matrix in this layout is in bounds and the values are not
+// used.
 //   lsq [NS] (FP64) sqrt(rho-tilde); wh, wl its binary32 halves; dh d-hat;
 //   lam eigenvalue estimates; vu sqrt(a + s_i); va 1/(u_i (u_i + sqrt a));
 //   vh 1/(a + s_i); vt1 Y^T d-hat; vt2 h(S') vt1; vv Y vt2; xbar [32]
@@ -539,7 +569,7 @@ __global__ void __launch_bounds__(32, 12) run_refine_kernel(RunArgs ra) {
     using L = FLayout<NS>;
     float* const Ah = smf + L::Ah;
     float* const Al = smf + L::Al;
-    float* const Yt = smf + L::Yt;
+    float* const Ys = smf + L::Yt;
     float* const Zb = smf + L::Zb;
     double* const lsq = reinterpret_cast<double*>(smf + L::lsq);
     float* const vwh = smf + L::wh;
@@ -595,10 +625,10 @@ __global__ void __launch_bounds__(32, 12) run_refine_kernel(RunArgs ra) {
     const bool real = lane < nu;
     const int c = lane;
     if (lane < nu) gi[lane] = info[1 + lane];
-    // The basis (Y^T rows) and eigenvalue estimates.
+    // The basis (row-major) and eigenvalue estimates.
     {
         const float4* src = reinterpret_cast<const float4*>(ra.Yg + (size_t)lc * NS * NS);
-        for (int e = lane; e < NS * NS / 4; e += 32) reinterpret_cast<float4*>(Yt)[e] = src[e];
+        for (int e = lane; e < NS * NS / 4; e += 32) reinterpret_cast<float4*>(Ys)[e] = src[e];
         if (own) vlam[c] = ra.lamg[(size_t)lc * NS + c];
     }
     __syncwarp();
@@ -639,81 +669,92 @@ __global__ void __launch_bounds__(32, 12) run_refine_kernel(RunArgs ra) {
         }
     }
     float u[NS];  // column c of Y
-    if (own) {
 #pragma unroll
-        for (int i4 = 0; i4 < NS / 4; ++i4) {
-            const float4 y4 = reinterpret_cast<const float4*>(Yt + c * NS)[i4];
-            u[4 * i4] = y4.x;
-            u[4 * i4 + 1] = y4.y;
-            u[4 * i4 + 2] = y4.z;
-            u[4 * i4 + 3] = y4.w;
-        }
-    } else {
-#pragma unroll
-        for (int i = 0; i < NS; ++i) u[i] = 0.0f;
-    }
+    for (int j = 0; j < NS; ++j) u[j] = own ? Ys[j * NS + c] : 0.0f;
     const float lamc = own ? vlam[c] : 0.0f;
     __syncwarp();
-    // R = A Y - Y diag(l), column c, double-binary32, into Zb; four rows at
-    // a time (independent accumulations).
-    for (int i0 = 0; i0 < NS; i0 += 4) {
-        float sacc[4] = {0.0f, 0.0f, 0.0f, 0.0f}, cacc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    // R = A Y - Y diag(l), column c, double-binary32, into Zb. Rows in
+    // groups of 8, two per packed register: A is symmetric, so rows i..i+7
+    // of column j are entries i..i+7 of row j.
+    for (int i0 = 0; i0 < NS; i0 += 8) {
+        f2x S[4], C[4];
 #pragma unroll
-        for (int j4 = 0; j4 < NS / 4; ++j4) {
+        for (int q = 0; q < 4; ++q) S[q] = C[q] = 0ull;
 #pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const float4 h = reinterpret_cast<const float4*>(Ah + (i0 + r) * NS)[j4];
-                const float4 l = reinterpret_cast<const float4*>(Al + (i0 + r) * NS)[j4];
-                df_acc(sacc[r], cacc[r], h.x, l.x, u[4 * j4]);
-                df_acc(sacc[r], cacc[r], h.y, l.y, u[4 * j4 + 1]);
-                df_acc(sacc[r], cacc[r], h.z, l.z, u[4 * j4 + 2]);
-                df_acc(sacc[r], cacc[r], h.w, l.w, u[4 * j4 + 3]);
-            }
+        for (int j = 0; j < NS; ++j) {
+            const f2x Y2 = f2pack(u[j], u[j]), NY2 = f2pack(-u[j], -u[j]);
+            const ulonglong2 h0 = *reinterpret_cast<const ulonglong2*>(Ah + j * NS + i0);
+            const ulonglong2 h1 = *reinterpret_cast<const ulonglong2*>(Ah + j * NS + i0 + 4);
+            const ulonglong2 l0 = *reinterpret_cast<const ulonglong2*>(Al + j * NS + i0);
+            const ulonglong2 l1 = *reinterpret_cast<const ulonglong2*>(Al + j * NS + i0 + 4);
+            df2_acc(S[0], C[0], h0.x, l0.x, Y2, NY2);
+            df2_acc(S[1], C[1], h0.y, l0.y, Y2, NY2);
+            df2_acc(S[2], C[2], h1.x, l1.x, Y2, NY2);
+            df2_acc(S[3], C[3], h1.y, l1.y, Y2, NY2);
         }
-        const float4 y4 = own ? reinterpret_cast<const float4*>(Yt + c * NS)[i0 / 4] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float yr[4] = {y4.x, y4.y, y4.z, y4.w};
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const float p = __fmul_rn(yr[r], lamc);
-            const float pe = __fmaf_rn(yr[r], lamc, -p);
-            if (own) Zb[(i0 + r) * NS + c] = __fadd_rn(__fsub_rn(sacc[r], p), __fsub_rn(cacc[r], pe));
+        for (int q = 0; q < 4; ++q) {
+            float s2[2], c2[2];
+            f2unpack(S[q], s2[0], s2[1]);
+            f2unpack(C[q], c2[0], c2[1]);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int i = i0 + 2 * q + h;
+                if (i < NS) {
+                    const float yi = own ? Ys[i * NS + c] : 0.0f;
+                    const float p = __fmul_rn(yi, lamc);
+                    const float pe = __fmaf_rn(yi, lamc, -p);
+                    if (own) Zb[i * NS + c] = __fadd_rn(__fsub_rn(s2[h], p), __fsub_rn(c2[h], pe));
+                }
+            }
         }
     }
     float rr[NS];
 #pragma unroll
     for (int j = 0; j < NS; ++j) rr[j] = own ? Zb[j * NS + c] : 0.0f;  // R column c
     __syncwarp();  // A is no longer read: E and S' take its place
-    // E = Y^T Y - I (double-binary32) and T = Y^T R (binary32); S', four rows
-    // at a time.
+    // E = Y^T Y - I (double-binary32) and T = Y^T R (binary32); S'. Rows in
+    // groups of 8: E_ic = sum_j Y_ji Y_jc, so rows i..i+7 read entries
+    // i..i+7 of row j of Y.
     float ecc = 0.0f, tcc = 0.0f;
-    for (int i0 = 0; i0 < NS; i0 += 4) {
-        float es[4] = {0.f, 0.f, 0.f, 0.f}, ec[4] = {0.f, 0.f, 0.f, 0.f}, tq[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int i0 = 0; i0 < NS; i0 += 8) {
+        f2x ES[4], EC[4], TQ[4];
 #pragma unroll
-        for (int j4 = 0; j4 < NS / 4; ++j4) {
+        for (int q = 0; q < 4; ++q) ES[q] = EC[q] = TQ[q] = 0ull;
 #pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const float4 yv = reinterpret_cast<const float4*>(Yt + (i0 + r) * NS)[j4];
-                df_acc1(es[r], ec[r], yv.x, u[4 * j4]);
-                df_acc1(es[r], ec[r], yv.y, u[4 * j4 + 1]);
-                df_acc1(es[r], ec[r], yv.z, u[4 * j4 + 2]);
-                df_acc1(es[r], ec[r], yv.w, u[4 * j4 + 3]);
-                tq[r] = fmaf(yv.x, rr[4 * j4], tq[r]);
-                tq[r] = fmaf(yv.y, rr[4 * j4 + 1], tq[r]);
-                tq[r] = fmaf(yv.z, rr[4 * j4 + 2], tq[r]);
-                tq[r] = fmaf(yv.w, rr[4 * j4 + 3], tq[r]);
-            }
+        for (int j = 0; j < NS; ++j) {
+            const f2x Y2 = f2pack(u[j], u[j]), NY2 = f2pack(-u[j], -u[j]), R2 = f2pack(rr[j], rr[j]);
+            const ulonglong2 y0 = *reinterpret_cast<const ulonglong2*>(Ys + j * NS + i0);
+            const ulonglong2 y1 = *reinterpret_cast<const ulonglong2*>(Ys + j * NS + i0 + 4);
+            df2_acc1(ES[0], EC[0], y0.x, Y2, NY2);
+            df2_acc1(ES[1], EC[1], y0.y, Y2, NY2);
+            df2_acc1(ES[2], EC[2], y1.x, Y2, NY2);
+            df2_acc1(ES[3], EC[3], y1.y, Y2, NY2);
+            TQ[0] = f2fma(y0.x, R2, TQ[0]);
+            TQ[1] = f2fma(y0.y, R2, TQ[1]);
+            TQ[2] = f2fma(y1.x, R2, TQ[2]);
+            TQ[3] = f2fma(y1.y, R2, TQ[3]);
         }
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int i = i0 + r;
-            const float e = __fadd_rn(__fsub_rn(es[r], i == c ? 1.0f : 0.0f), ec[r]);
-            if (i == c) {
-                ecc = e;
-                tcc = tq[r];
-            }
-            if (own) {
-                Ah[i * NS + c] = e;
-                Al[i * NS + c] = (i == c) ? 0.0f : fmaf(e, 0.5f * (lamc - vlam[i]), tq[r]);
+        for (int q = 0; q < 4; ++q) {
+            float es2[2], ec2[2], tq2[2];
+            f2unpack(ES[q], es2[0], es2[1]);
+            f2unpack(EC[q], ec2[0], ec2[1]);
+            f2unpack(TQ[q], tq2[0], tq2[1]);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int i = i0 + 2 * q + h;
+                if (i < NS) {
+                    const float e = __fadd_rn(__fsub_rn(es2[h], i == c ? 1.0f : 0.0f), ec2[h]);
+                    if (i == c) {
+                        ecc = e;
+                        tcc = tq2[h];
+                    }
+                    if (own) {
+                        Ah[i * NS + c] = e;
+                        Al[i * NS + c] = (i == c) ? 0.0f : fmaf(e, 0.5f * (lamc - vlam[i]), tq2[h]);
+                    }
+                }
             }
         }
     }
@@ -759,13 +800,13 @@ __global__ void __launch_bounds__(32, 12) run_refine_kernel(RunArgs ra) {
         if (own) vt2[c] = hc * (t1c - tt) - te;
     }
     __syncwarp();
-    // v = Y t2 (lane c takes row c of Y: column c of Yt).
+    // v = Y t2 (lane c takes row c of Y).
     {
         float v0 = 0.0f, v1 = 0.0f;
 #pragma unroll
         for (int l = 0; l < NS; l += 2) {
-            v0 = fmaf(own ? Yt[l * NS + c] : 0.0f, vt2[l], v0);
-            v1 = fmaf(own ? Yt[(l + 1) * NS + c] : 0.0f, vt2[l + 1], v1);
+            v0 = fmaf(own ? Ys[c * NS + l] : 0.0f, vt2[l], v0);
+            v1 = fmaf(own ? Ys[c * NS + l + 1] : 0.0f, vt2[l + 1], v1);
         }
         if (own) vv[c] = v0 + v1;
     }
@@ -862,7 +903,7 @@ __global__ void __launch_bounds__(32, 12) run_refine_kernel(RunArgs ra) {
 #pragma unroll
         for (int aq = 0; aq < 9; ++aq) acc[aq] = 0.0f;
         for (int i = 0; i < NS; ++i) {
-            const float yci = own ? Yt[i * NS + c] : 0.0f;  // Y[c][i]
+            const float yci = own ? Ys[c * NS + i] : 0.0f;  // Y[c][i]
 #pragma unroll
             for (int aq = 0; aq < 9; ++aq) acc[aq] = fmaf(Z[aq * NS + i], yci, acc[aq]);
         }
