@@ -680,9 +680,10 @@ __global__ void __launch_bounds__(32, 12) run_refine_kernel(RunArgs ra) {
         f2x S[4], C[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) S[q] = C[q] = 0ull;
-#pragma unroll
+#pragma unroll 2
         for (int j = 0; j < NS; ++j) {
-            const f2x Y2 = f2pack(u[j], u[j]), NY2 = f2pack(-u[j], -u[j]);
+            const float uj = own ? Ys[j * NS + c] : 0.0f;  // Y_jc
+            const f2x Y2 = f2pack(uj, uj), NY2 = f2pack(-uj, -uj);
             const ulonglong2 h0 = *reinterpret_cast<const ulonglong2*>(Ah + j * NS + i0);
             const ulonglong2 h1 = *reinterpret_cast<const ulonglong2*>(Ah + j * NS + i0 + 4);
             const ulonglong2 l0 = *reinterpret_cast<const ulonglong2*>(Al + j * NS + i0);
@@ -709,9 +710,6 @@ __global__ void __launch_bounds__(32, 12) run_refine_kernel(RunArgs ra) {
             }
         }
     }
-    float rr[NS];
-#pragma unroll
-    for (int j = 0; j < NS; ++j) rr[j] = own ? Zb[j * NS + c] : 0.0f;  // R column c
     __syncwarp();  // A is no longer read: E and S' take its place
     // E = Y^T Y - I (double-binary32) and T = Y^T R (binary32); S'. Rows in
     // groups of 8: E_ic = sum_j Y_ji Y_jc, so rows i..i+7 read entries
@@ -721,9 +719,11 @@ __global__ void __launch_bounds__(32, 12) run_refine_kernel(RunArgs ra) {
         f2x ES[4], EC[4], TQ[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) ES[q] = EC[q] = TQ[q] = 0ull;
-#pragma unroll
+#pragma unroll 2
         for (int j = 0; j < NS; ++j) {
-            const f2x Y2 = f2pack(u[j], u[j]), NY2 = f2pack(-u[j], -u[j]), R2 = f2pack(rr[j], rr[j]);
+            const float uj = own ? Ys[j * NS + c] : 0.0f;  // Y_jc
+            const float rj = own ? Zb[j * NS + c] : 0.0f;  // R_jc
+            const f2x Y2 = f2pack(uj, uj), NY2 = f2pack(-uj, -uj), R2 = f2pack(rj, rj);
             const ulonglong2 y0 = *reinterpret_cast<const ulonglong2*>(Ys + j * NS + i0);
             const ulonglong2 y1 = *reinterpret_cast<const ulonglong2*>(Ys + j * NS + i0 + 4);
             df2_acc1(ES[0], EC[0], y0.x, Y2, NY2);
