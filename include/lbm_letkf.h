@@ -232,6 +232,21 @@ int lbm_misfit_gradient(lbm_ctx *ctx, const lbm_window *win, const double *w, do
  * at the next synchronising call and leaves that point unchanged. */
 int letkf_analyze(lbm_ctx *ctx, double d_cut, double beta);
 
+/* Diagnostic of the mixed-precision analysis (Section 3.2: w-bar, W and the
+ * transform x^a_m = xbar + sum_j dx_j (w-bar_j + W_jm)). For the grid points
+ * cells[npoints] (host array of y * nx + x, 1 <= npoints <= 4096), writes
+ * T[p][j][m] = w-bar_j + W[j][m] ([npoints][members][members], FP64, host or
+ * device per ptr_kind) as the run analysis represents it: the same
+ * warm-started binary32 bases and the same first-order refinement as
+ * letkf_analyze, with the resulting matrix functions applied in FP64 instead
+ * of the binary32 transform. Same arguments as the following letkf_analyze;
+ * the state is not changed and the observation is not consumed. Needs a
+ * mixed-precision context on the run path (run length > 0, every grid point
+ * with p < members, every run's union of local sets within 32 scalars);
+ * otherwise LBM_EINVAL. Synchronises. */
+int letkf_probe_transform(lbm_ctx *ctx, double d_cut, double beta, int npoints, const int *cells,
+                          double *T, int ptr_kind);
+
 /* Nudging, the paper's comparison method (Section 3.1): every member is
  * relaxed toward the equilibrium of the observed macroscopic field,
  * f_alpha <- f_alpha + gamma (f^eq_alpha(rho^, u^, v^) - f_alpha), 0 <= gamma <= 1.

@@ -52,6 +52,7 @@ SIGNATURES = {
     "letkf_observe": (_I, [_P, _I, _P, _P, _P, _P, _D, _D]),
     "letkf_observe_rho": (_I, [_P, _I, _P, _P, _P, _P, _P, _D, _D, _D]),
     "letkf_analyze": (_I, [_P, _D, _D]),
+    "letkf_probe_transform": (_I, [_P, _D, _D, _I, _P, _P, _I]),
     "lbm_set_closure": (_I, [_P, _D]),
     "letkf_set_products": (_I, [_P, _I]),
     "letkf_set_run_length": (_I, [_P, _I]),
@@ -298,6 +299,17 @@ def letkf_analyze(ctx, d_cut, beta):
     _check(ctx, load().letkf_analyze(ctx, float(d_cut), float(beta)))
 
 
+def letkf_probe_transform(ctx, d_cut, beta, cells, members):
+    """T [len(cells)][members][members] (numpy, FP64): the mixed analysis'
+    transform at the grid points `cells` (y * nx + x), state unchanged."""
+    cells = np.ascontiguousarray(cells, dtype=np.int32)
+    T = np.zeros((len(cells), members, members))
+    _check(ctx, load().letkf_probe_transform(ctx, float(d_cut), float(beta), len(cells),
+                                             cells.ctypes.data_as(ctypes.c_void_p),
+                                             T.ctypes.data_as(ctypes.c_void_p), LBM_PTR_HOST))
+    return T
+
+
 def lbm_nudge(ctx, rho_o, u_o, v_o, gamma):
     """Nudge every member toward f^eq of observed fields [nobs_y][nobs_x]."""
     rho_o = np.ascontiguousarray(rho_o, dtype=np.float64)
@@ -419,6 +431,9 @@ class Ensemble:
 
     def observe_rho(self, ix, iy, yo_u, yo_v, yo_rho, sigma_u, sigma_v, sigma_rho):
         letkf_observe_rho(self.ctx, ix, iy, yo_u, yo_v, yo_rho, sigma_u, sigma_v, sigma_rho)
+
+    def probe_transform(self, d_cut, beta, cells):
+        return letkf_probe_transform(self.ctx, d_cut, beta, cells, self.members)
 
     def analyze(self, d_cut, beta):
         letkf_analyze(self.ctx, d_cut, beta)

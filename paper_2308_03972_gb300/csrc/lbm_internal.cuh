@@ -143,6 +143,14 @@ size_t run_scratch_bytes(int nx, int ny, int nobs, int run_len, int maxunion);
 cudaError_t launch_analyze_runs(float* f, int nx, int ny, int k, const ObsParams& o, double d_cut,
                                 double beta, int run_len, int maxunion, int* flags, void* scratch,
                                 cudaStream_t s);
+// Diagnostic: the ensemble transform T = w-bar 1^T + W [npoints][k][k]
+// (FP64) that the run analysis' refined representation gives at the listed
+// grid points cells[npoints] (device), evaluated in FP64; f is not
+// changed. work: probe_work_bytes(npoints, maxunion, k) bytes.
+size_t probe_work_bytes(int npoints, int maxunion, int k);
+cudaError_t launch_probe_runs(float* f, int nx, int ny, int k, const ObsParams& o, double d_cut, double beta,
+                              int run_len, int maxunion, int* flags, void* scratch, const int* cells,
+                              int npoints, double* T, double* work, cudaStream_t s);
 
 // ---- diag_kernels.cu ------------------------------------------------------
 // Member-averaged energy spectrum E[nshells] (device pointer); work holds

@@ -850,6 +850,44 @@ int letkf_analyze(lbm_ctx* c, double d_cut, double beta) {
     return LBM_OK;
 }
 
+int letkf_probe_transform(lbm_ctx* c, double d_cut, double beta, int npoints, const int* cells, double* T,
+                          int ptr_kind) {
+    if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (!is_fp32(c)) return fail(c, LBM_EINVAL, "the transform probe covers the mixed-precision analysis");
+    if (!c->observed) return fail(c, LBM_EINVAL, "letkf_observe must precede letkf_probe_transform");
+    if (npoints < 1 || npoints > 4096) return fail(c, LBM_EINVAL, "npoints must be in [1, 4096]");
+    if (!cells || !T) return fail(c, LBM_EINVAL, "NULL argument");
+    if (!ptr_kind_ok(ptr_kind)) return fail(c, LBM_EINVAL, "bad ptr_kind");
+    const long long ncell = (long long)c->nx * c->ny;
+    for (int i = 0; i < npoints; ++i)
+        if (cells[i] < 0 || cells[i] >= ncell) return fail(c, LBM_EINVAL, "grid point %d outside the lattice", i);
+    AnalysisPlan plan;
+    int st = analyze_prepare(c, d_cut, beta, &plan);
+    if (st) return st;
+    if (plan.run_len == 0)
+        return fail(c, LBM_EINVAL,
+                    "the transform probe needs the run analysis (run length > 0, every grid point with p < members, "
+                    "unions of at most 32 scalars)");
+    StreamScratch sc(c->stream);
+    void *d_cells, *d_work, *d_T = T;
+    const size_t tbytes = (size_t)npoints * c->k * c->k * sizeof(double);
+    CK(c, sc.get(&d_cells, (size_t)npoints * sizeof(int)), "allocating probe points");
+    CK(c, sc.get(&d_work, probe_work_bytes(npoints, plan.maxunion, c->k)), "allocating probe scratch");
+    if (ptr_kind == LBM_PTR_HOST) CK(c, sc.get(&d_T, tbytes), "allocating probe output");
+    CK(c, cudaMemcpyAsync(d_cells, cells, (size_t)npoints * sizeof(int), cudaMemcpyHostToDevice, c->stream),
+       "copy probe points");
+    ObsParams o{c->npts, c->ix, c->iy, c->dY, c->d, c->G, c->sigma_u, c->sigma_v, c->dY32,
+                c->nvar, c->sigma_r, plan.plmax, nullptr};
+    CK(c, launch_probe_runs((float*)c->f[c->cur], c->nx, c->ny, c->k, o, plan.d_cut, plan.beta, plan.run_len,
+                            plan.maxunion, c->flags, c->ana_scratch, (const int*)d_cells, npoints, (double*)d_T,
+                            (double*)d_work, c->stream),
+       "launching the transform probe");
+    if (ptr_kind == LBM_PTR_HOST)
+        CK(c, cudaMemcpyAsync(T, d_T, tbytes, cudaMemcpyDeviceToHost, c->stream), "copy probe output");
+    CK(c, cudaStreamSynchronize(c->stream), "synchronising");
+    return read_flags(c);
+}
+
 int lbm_nudge(lbm_ctx* c, int nobs_x, int nobs_y, const double* rho_o, const double* u_o,
               const double* v_o, double gamma) {
     if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");

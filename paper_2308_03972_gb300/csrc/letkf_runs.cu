@@ -563,8 +563,27 @@ __host__ __device__ inline size_t run_f_smem_bytes(int k) {
     return ((size_t)FLayout<NS>::dX + 9 * (size_t)k) * 4;
 }
 
+// Diagnostic output of the refinement kernel (PROBE = true): for listed
+// grid points, the ensemble transform T = w-bar 1^T + W the refined
+// representation gives, evaluated in FP64 (see probe_tail).
+struct ProbeArgs {
+    const int* cells;  // [npoints] grid points y * nx + x
+    int npoints;
+    double* T;         // [npoints][k][k]
+    double* work;      // [npoints][probe_stride(NS, k)]
+};
+
+__host__ __device__ inline size_t probe_stride(int ns, int k) {
+    return 8 * (size_t)ns + (size_t)ns * ns + 2 * (size_t)ns * k;
+}
+
 template <int NS>
-__global__ void __launch_bounds__(32, 12) run_refine_kernel(RunArgs ra) {
+__device__ void probe_tail(const RunArgs& ra, const ProbeArgs& pa, int pt, const float* Ys, const float* Ew,
+                           const float* Sw, const double* lsq, const int* gi, int nu, double uu, double alpha,
+                           double hh, int lane);
+
+template <int NS, bool PROBE>
+__global__ void __launch_bounds__(32, 12) run_refine_kernel(RunArgs ra, ProbeArgs pa) {
     extern __shared__ __align__(16) float smf[];
     using L = FLayout<NS>;
     float* const Ah = smf + L::Ah;
@@ -590,20 +609,38 @@ __global__ void __launch_bounds__(32, 12) run_refine_kernel(RunArgs ra) {
     const int nobs = o.nvar * o.npts;
     const size_t plane = (size_t)ra.nx * ra.ny * k;
     const int lane = threadIdx.x;
-    const int lc = blockIdx.x;  // cell within the chunk
-    const int rl = lc / ra.R;
-    const int run = ra.run0 + rl;
     const int runs_x = (ra.nx + ra.R - 1) / ra.R;
-    const int y = run / runs_x;
-    const int x = (run - y * runs_x) * ra.R + (lc - rl * ra.R);
-    if (x >= ra.nx) return;  // past the end of a ragged last run
+    int lc, rl, x, y;
+    if (PROBE) {
+        // Block b takes listed point b if its run is in this chunk.
+        const int cl = pa.cells[blockIdx.x];
+        y = cl / ra.nx;
+        x = cl - y * ra.nx;
+        const int run = y * runs_x + x / ra.R;
+        if (run < ra.run0 || run >= ra.run0 + ra.nruns) return;
+        rl = run - ra.run0;
+        lc = rl * ra.R + (x - (x / ra.R) * ra.R);
+    } else {
+        lc = blockIdx.x;  // cell within the chunk
+        rl = lc / ra.R;
+        const int run = ra.run0 + rl;
+        y = run / runs_x;
+        x = (run - y * runs_x) * ra.R + (lc - rl * ra.R);
+        if (x >= ra.nx) return;  // past the end of a ragged last run
+    }
     const size_t cell = (size_t)y * ra.nx + x;
-    stage_point(ra, dX, cell, lane);
+    if (!PROBE) stage_point(ra, dX, cell, lane);
     const float sbeta = (float)sqrt(ra.beta);
     const int* info = ra.rinfo + (size_t)rl * kInfo;
     const int nu = info[0];
     const float lam_mark = ra.lamg[(size_t)lc * NS];
     if (nu < 0) return;  // reported by kernel J
+    if (PROBE && (nu == 0 || lam_mark == -1.0f)) {
+        // No observation in range: T = sqrt(beta) I.
+        double* Tp = pa.T + (size_t)blockIdx.x * k * k;
+        for (int e = lane; e < k * k; e += 32) Tp[e] = (e / k == e % k) ? sqrt(ra.beta) : 0.0;
+        return;
+    }
     if (nu == 0 || lam_mark == -1.0f) {
         // No observation in range: x^a = xbar + sqrt(beta) dx.
         cp_async_wait_all();
@@ -763,6 +800,11 @@ __global__ void __launch_bounds__(32, 12) run_refine_kernel(RunArgs ra) {
     const double uu = sqrt(aa + dS);
     const double alpha = 1.0 / (uu * (uu + rs));
     const double hh = 1.0 / (aa + dS);
+    if constexpr (PROBE) {
+        __syncwarp();
+        probe_tail<NS>(ra, pa, blockIdx.x, Ys, Ah, Al, lsq, gi, nu, uu, alpha, hh, lane);
+        return;
+    }
     float t1c = 0.0f;
 #pragma unroll
     for (int l = 0; l < NS; ++l) t1c = fmaf(u[l], dh[l], t1c);  // (Y^T d-hat)_c
@@ -934,6 +976,113 @@ __global__ void __launch_bounds__(32, 12) run_refine_kernel(RunArgs ra) {
     }
 }
 
+// FP64 evaluation of the ensemble transform from the refined representation
+// of one grid point: basis Y (binary32, row-major in Ys), E = Y^T Y - I
+// (column c of Ew), S' off the diagonal (column c of Sw) and, per lane c, the
+// FP64 eigenvalue functions u_c = sqrt(a + s'_cc), alpha_c, h_c. With the
+// same first-order formulas as the analysis (h(S') t1 and g(S')), but every
+// product in FP64:
+//   t1 = Y^T d-hat, t2 = h(S') t1, v = Y t2, F = g(S') (the basis factor
+//   included), g(A) = Y F Y^T,
+//   w-bar = Yh^T v, W = sqrt(beta) I + sqrt(k-1) Yh^T g(A) Yh,
+//   T[j][m] = w-bar_j + W[j][m],
+// the transform x^a_m = xbar + sum_j dx_j T[j][m] of Section 3.2.
+template <int NS>
+__device__ void probe_tail(const RunArgs& ra, const ProbeArgs& pa, int pt, const float* Ys, const float* Ew,
+                           const float* Sw, const double* lsq, const int* gi, int nu, double uu, double alpha,
+                           double hh, int lane) {
+    const int k = ra.k;
+    const bool own = lane < NS;
+    const int c = lane;
+    const ObsParams& o = ra.o;
+    double* wk = pa.work + (size_t)pt * probe_stride(NS, k);
+    double* U = wk;
+    double* AL = U + NS;
+    double* H = AL + NS;
+    double* T1 = H + NS;
+    double* T2 = T1 + NS;
+    double* V = T2 + NS;
+    double* LS = V + NS;
+    double* DH = LS + NS;
+    double* F = DH + NS;
+    double* C1 = F + NS * NS;
+    double* C2 = C1 + (size_t)NS * k;
+    const double aa = (k - 1) / ra.beta;
+    const double rs = sqrt(aa);
+    if (own) {
+        U[c] = uu;
+        AL[c] = alpha;
+        H[c] = hh;
+        LS[c] = lsq[c];
+        DH[c] = (c < nu) ? lsq[c] * o.d[gi[c]] : 0.0;
+    }
+    __syncwarp();
+    if (own) {
+        double t = 0.0;
+        for (int l = 0; l < NS; ++l) t += (double)Ys[l * NS + c] * DH[l];
+        T1[c] = t;
+    }
+    __syncwarp();
+    if (own) {
+        double tt = 0.0, te = 0.0;
+        for (int j = 0; j < NS; ++j) {
+            const double sv = (j == c) ? 0.0 : (double)Sw[j * NS + c];
+            const double ev = (double)Ew[j * NS + c];
+            tt += sv * H[j] * T1[j];
+            te += ev * 0.5 * (hh + H[j]) * T1[j];
+        }
+        T2[c] = hh * (T1[c] - tt) - te;
+        const double gc = -alpha / rs;
+        for (int j = 0; j < NS; ++j) {
+            const double ev = (double)Ew[j * NS + c];
+            double g = gc;
+            if (j != c) g = (double)Sw[j * NS + c] * (U[j] + uu + rs) * AL[j] * alpha / (rs * (U[j] + uu));
+            F[j * NS + c] = g - ev * 0.5 * (gc - AL[j] / rs);
+        }
+    }
+    __syncwarp();
+    if (own) {
+        double v = 0.0;
+        for (int l = 0; l < NS; ++l) v += (double)Ys[c * NS + l] * T2[l];
+        V[c] = v;
+    }
+    // C1 = Y^T Yh, Yh[l][m] = sqrt(rho)_l dY[gi_l][m].
+    for (int m = lane; m < k; m += 32)
+        for (int q = 0; q < NS; ++q) {
+            double acc = 0.0;
+            for (int l = 0; l < nu; ++l) acc += (double)Ys[l * NS + q] * LS[l] * o.dY[(size_t)gi[l] * k + m];
+            C1[(size_t)q * k + m] = acc;
+        }
+    __syncwarp();
+    // C2 = F C1, then B = Y C2 (into C1).
+    for (int m = lane; m < k; m += 32)
+        for (int p = 0; p < NS; ++p) {
+            double acc = 0.0;
+            for (int q = 0; q < NS; ++q) acc += F[p * NS + q] * C1[(size_t)q * k + m];
+            C2[(size_t)p * k + m] = acc;
+        }
+    __syncwarp();
+    for (int m = lane; m < k; m += 32)
+        for (int i = 0; i < NS; ++i) {
+            double acc = 0.0;
+            for (int p = 0; p < NS; ++p) acc += (double)Ys[i * NS + p] * C2[(size_t)p * k + m];
+            C1[(size_t)i * k + m] = acc;
+        }
+    __syncwarp();
+    const double sq = sqrt((double)(k - 1)), sb = sqrt(ra.beta);
+    double* Tp = pa.T + (size_t)pt * k * k;
+    for (int m = lane; m < k; m += 32)
+        for (int j = 0; j < k; ++j) {
+            double wb = 0.0, s = 0.0;
+            for (int i = 0; i < nu; ++i) {
+                const double yh = LS[i] * o.dY[(size_t)gi[i] * k + j];
+                wb += yh * V[i];
+                s += yh * C1[(size_t)i * k + m];
+            }
+            Tp[(size_t)j * k + m] = wb + sq * s + (j == m ? sb : 0.0);
+        }
+}
+
 // G = dY dY^T split into binary32 (hi, lo).
 __global__ void split_gram_kernel(const double* __restrict__ G, float2* __restrict__ G2, size_t n) {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -961,40 +1110,34 @@ long long run_chunk_runs(long long runs, int R, int ns) {
     return runs < c ? runs : c;
 }
 
+// Per chunk of runs: kernel J, then kernel F over the chunk's grid points,
+// or (pa.npoints > 0) the probe variant of F over the listed points.
 template <int NS>
-cudaError_t launch_runs_ns(RunArgs ra, long long runs, long long chunk, cudaStream_t s) {
+cudaError_t launch_runs_ns(RunArgs ra, long long runs, long long chunk, const ProbeArgs& pa, cudaStream_t s) {
     const size_t shJ = (size_t)JLayout<NS>::total * 4;
     const size_t shF = run_f_smem_bytes<NS>(ra.k);
+    const bool probe = pa.npoints > 0;
     cudaError_t e = cudaFuncSetAttribute(run_jacobi_kernel<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shJ);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(run_refine_kernel<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shF);
+    e = probe ? cudaFuncSetAttribute(run_refine_kernel<NS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shF)
+              : cudaFuncSetAttribute(run_refine_kernel<NS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shF);
     if (e != cudaSuccess) return e;
     for (long long r0 = 0; r0 < runs; r0 += chunk) {
         const long long nr = runs - r0 < chunk ? runs - r0 : chunk;
         ra.run0 = (int)r0;
         ra.nruns = (int)nr;
         run_jacobi_kernel<NS><<<(unsigned)nr, 32, shJ, s>>>(ra);
-        run_refine_kernel<NS><<<(unsigned)(nr * ra.R), 32, shF, s>>>(ra);
+        if (probe)
+            run_refine_kernel<NS, true><<<(unsigned)pa.npoints, 32, shF, s>>>(ra, pa);
+        else
+            run_refine_kernel<NS, false><<<(unsigned)(nr * ra.R), 32, shF, s>>>(ra, pa);
     }
     return cudaGetLastError();
 }
 
-}  // namespace
-
-size_t run_scratch_bytes(int nx, int ny, int nobs, int run_len, int maxunion) {
-    const int ns = run_ns(maxunion);
-    const long long runs = (long long)ny * ((nx + run_len - 1) / run_len);
-    const long long chunk = run_chunk_runs(runs, run_len, ns);
-    const size_t g2 = ((size_t)nobs * nobs * sizeof(float2) + 255) / 256 * 256;
-    const size_t yb = ((size_t)chunk * run_len * ns * ns * 4 + 255) / 256 * 256;
-    const size_t lb = ((size_t)chunk * run_len * ns * 4 + 255) / 256 * 256;
-    const size_t ib = (size_t)chunk * kInfo * 4;
-    return g2 + yb + lb + ib;
-}
-
-cudaError_t launch_analyze_runs(float* f, int nx, int ny, int k, const ObsParams& o, double d_cut,
-                                double beta, int run_len, int maxunion, int* flags, void* scratch,
-                                cudaStream_t s) {
+cudaError_t launch_runs(float* f, int nx, int ny, int k, const ObsParams& o, double d_cut, double beta,
+                        int run_len, int maxunion, int* flags, void* scratch, const ProbeArgs& pa,
+                        cudaStream_t s) {
     if (run_len < 1 || maxunion > kRunMaxUnion || !o.dY32 || !scratch) return cudaErrorInvalidValue;
     const int nobs = o.nvar * o.npts;
     const size_t ng = (size_t)nobs * nobs;
@@ -1031,12 +1174,44 @@ cudaError_t launch_analyze_runs(float* f, int nx, int ny, int k, const ObsParams
     ra.lamg = lamg;
     ra.rinfo = rinfo;
     switch (ns) {
-        case 8: return launch_runs_ns<8>(ra, runs, chunk, s);
-        case 16: return launch_runs_ns<16>(ra, runs, chunk, s);
-        case 24: return launch_runs_ns<24>(ra, runs, chunk, s);
-        case 28: return launch_runs_ns<28>(ra, runs, chunk, s);
-        default: return launch_runs_ns<32>(ra, runs, chunk, s);
+        case 8: return launch_runs_ns<8>(ra, runs, chunk, pa, s);
+        case 16: return launch_runs_ns<16>(ra, runs, chunk, pa, s);
+        case 24: return launch_runs_ns<24>(ra, runs, chunk, pa, s);
+        case 28: return launch_runs_ns<28>(ra, runs, chunk, pa, s);
+        default: return launch_runs_ns<32>(ra, runs, chunk, pa, s);
     }
+}
+
+}  // namespace
+
+size_t run_scratch_bytes(int nx, int ny, int nobs, int run_len, int maxunion) {
+    const int ns = run_ns(maxunion);
+    const long long runs = (long long)ny * ((nx + run_len - 1) / run_len);
+    const long long chunk = run_chunk_runs(runs, run_len, ns);
+    const size_t g2 = ((size_t)nobs * nobs * sizeof(float2) + 255) / 256 * 256;
+    const size_t yb = ((size_t)chunk * run_len * ns * ns * 4 + 255) / 256 * 256;
+    const size_t lb = ((size_t)chunk * run_len * ns * 4 + 255) / 256 * 256;
+    const size_t ib = (size_t)chunk * kInfo * 4;
+    return g2 + yb + lb + ib;
+}
+
+cudaError_t launch_analyze_runs(float* f, int nx, int ny, int k, const ObsParams& o, double d_cut,
+                                double beta, int run_len, int maxunion, int* flags, void* scratch,
+                                cudaStream_t s) {
+    const ProbeArgs none{nullptr, 0, nullptr, nullptr};
+    return launch_runs(f, nx, ny, k, o, d_cut, beta, run_len, maxunion, flags, scratch, none, s);
+}
+
+size_t probe_work_bytes(int npoints, int maxunion, int k) {
+    return (size_t)npoints * probe_stride(run_ns(maxunion), k) * sizeof(double);
+}
+
+cudaError_t launch_probe_runs(float* f, int nx, int ny, int k, const ObsParams& o, double d_cut, double beta,
+                              int run_len, int maxunion, int* flags, void* scratch, const int* cells,
+                              int npoints, double* T, double* work, cudaStream_t s) {
+    if (npoints < 1 || !cells || !T || !work) return cudaErrorInvalidValue;
+    const ProbeArgs pa{cells, npoints, T, work};
+    return launch_runs(f, nx, ny, k, o, d_cut, beta, run_len, maxunion, flags, scratch, pa, s);
 }
 
 }  // namespace lbmgpu
