@@ -122,6 +122,16 @@ int lbm_moments(lbm_ctx *ctx, double *rho, double *u, double *v, int ptr_kind);
  * may be NULL. With LBM_PTR_HOST the call synchronises. */
 int lbm_mean_velocity(lbm_ctx *ctx, double *u, double *v, int ptr_kind);
 
+/* Velocity RMSE of ctx's ensemble mean against truth's (Section 4.3 scores
+ * the ensemble mean against the nature run):
+ *   rmse = sqrt( (nx ny)^-1 sum_xi (ubar - ubar_t)^2 + (vbar - vbar_t)^2 ),
+ * ubar the member mean of each context (the truth usually has one member).
+ * Both lattices must have the same size. FP64, reduced on the device in a
+ * fixed order; the truth's queued work is waited for on ctx's stream.
+ * rmse: one double, host or device per ptr_kind (LBM_PTR_HOST
+ * synchronises). */
+int lbm_velocity_rmse(lbm_ctx *ctx, lbm_ctx *truth, double *rmse, int ptr_kind);
+
 /* Energy spectrum of the ensemble (Section 4.1, shell-averaged spectrum;
  * Section 4.3 takes the mean of the members' spectra). For every member,
  * u-hat(k') = N^{-1} sum_xi u(xi) exp(-i k'.xi) over the N = nx*ny cells for
@@ -208,17 +218,21 @@ int lbm_misfit(lbm_ctx *ctx, const lbm_window *win, double *J);
 /* lbm_misfit and its gradient by the hand-written adjoint of the forecast
  * (reverse sweep through the transposed collision Jacobian and the pulled
  * streaming, with the forward states recomputed from checkpoints). For
- * F = sum_m w_m J_m (w: host [members], NULL = all ones):
+ * F = sum_m w_m J_m (w: [members], NULL = all ones; host or device per
+ * ptr_kind, device weights are not checked for finiteness):
  *   grad_f0 [9][ny][nx][members]  dF/df at the current state (FP64; host
  *                                 or device per ptr_kind),
- *   grad_cs [members] (host)      w_m dJ_m/dC_s (their sum is dF/dC_s).
- * Either output may be NULL. In mixed precision the forecast and the
- * adjoint run in binary32 (C_s derivative summed in FP64); in FP64 mode
- * everything is FP64. Scratch of about (nsteps / checkpoint_every +
- * checkpoint_every + 3) states is allocated and released on the context
- * stream. Synchronises. */
+ *   grad_cs [members] (host)      w_m dJ_m/dC_s,
+ *   dcs     [1]                   dF/dC_s = sum_m w_m dJ_m/dC_s, summed on
+ *                                 the device in member order (host or
+ *                                 device per ptr_kind).
+ * J stays a host array [members]. Any output may be NULL. In mixed
+ * precision the forecast and the adjoint run in binary32 (C_s derivative
+ * summed in FP64); in FP64 mode everything is FP64. Scratch of about
+ * (nsteps / checkpoint_every + checkpoint_every + 3) states is allocated
+ * and released on the context stream. Synchronises. */
 int lbm_misfit_gradient(lbm_ctx *ctx, const lbm_window *win, const double *w, double *J,
-                        double *grad_f0, double *grad_cs, int ptr_kind);
+                        double *grad_f0, double *grad_cs, double *dcs, int ptr_kind);
 
 /* LETKF analysis of the nine f_alpha at every grid point, in place
  * (Section 3.2: w-bar, P-tilde, delta-W = [(k-1) P-tilde]^{1/2} symmetric,
@@ -299,9 +313,14 @@ void lbm_destroy(lbm_ctx *ctx);
  * call before any stream capture. Every call shares the array and overwrites
  * it; two calls that overlap on the GPU (different streams, or different
  * host threads) race on it and must be serialised by the caller. The call
- * synchronises the stream and returns LBM_OK, LBM_EINVAL (bad argument or
+ * synchronises the stream and returns LBM_OK, LBM_EINVAL (bad argument, or a
  * local problem larger than the kernel holds), LBM_ENOCONV or LBM_ECUDA;
- * lbm_last_error(NULL) gives the message. */
+ * lbm_last_error(NULL) gives the message. The analysis is the FP64 one, so
+ * a grid point's local problem must satisfy n = min(members, 2 p) <= 64 (p
+ * observation points in range): with more than 64 members, dense
+ * observations are refused. On LBM_EINVAL for a too-large local problem and
+ * on LBM_ENOCONV the state is partly updated: every grid point that fitted
+ * or converged has been analysed, the others are unchanged. */
 int letkf_analyze_noalloc(double *f, int nx, int ny, int members, int npts,
                           const int *ix, const int *iy, const double *yo_u,
                           const double *yo_v, double sigma_u, double sigma_v,

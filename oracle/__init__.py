@@ -65,6 +65,7 @@ def _load():
             "orc_local_obs": (I, [I, I, I, I, I, P, P, D, D, D, P, P]),
             "orc_letkf_analyze": (I, [I, I, I, P, I, P, P, P, P, D, D, D, D, I, P]),
             "orc_num_threads": (I, []),
+            "orc_set_num_threads": (None, [I]),
             "orc_nudge": (None, [I, I, I, P, I, I, P, P, P, D]),
             "orc_energy_spectrum": (None, [I, I, I, P, I, P]),
             "orc_observe_vars": (None, [I, I, I, P, I, P, P, I, P]),
@@ -298,3 +299,8 @@ def energy_spectrum(f: np.ndarray, nshells: int | None = None) -> np.ndarray:
 
 def num_threads() -> int:
     return _load().orc_num_threads()
+
+
+def set_num_threads(n: int) -> None:
+    """Threads the oracle's OpenMP loops use from now on (n >= 1)."""
+    _load().orc_set_num_threads(int(n))

@@ -132,6 +132,8 @@ void orc_energy_spectrum(int nx, int ny, int k, const double *f, int nshells, do
 
 /* Number of OpenMP threads the oracle will use (1 without OpenMP). */
 int orc_num_threads(void);
+/* Threads of the following OpenMP regions (timing of the CPU baseline). */
+void orc_set_num_threads(int n);
 
 #ifdef __cplusplus
 }

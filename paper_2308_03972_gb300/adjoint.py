@@ -6,12 +6,12 @@ f0 (float64 tensor [9][ny][nx][k], CUDA) with Smagorinsky coefficient cs
 (0-dim float64 tensor), using the context ``ens`` (a ``binding.Ensemble`` of
 the same shape; its precision decides FP64 or binary32 arithmetic). Its
 backward calls ``lbm_misfit_gradient`` with the incoming gradient as member
-weights, so dL/df0 and dL/dcs come from the CUDA adjoint sweep (with step
-checkpointing), not from autograd tracing. Argument marshalling only.
+weights (on the device), so dL/df0 and dL/dcs (summed over members on the
+device) come from the CUDA adjoint sweep (with step checkpointing), not
+from autograd tracing. Argument marshalling only.
 """
 from __future__ import annotations
 
-import numpy as np
 import torch
 
 from . import binding
@@ -37,9 +37,10 @@ class WindowMisfit(torch.autograd.Function):
         ens.set_f(f0)
         ens.set_closure(float(cs))
         grad = torch.empty_like(f0)
-        w = np.ascontiguousarray(gJ.detach().to("cpu", torch.float64).numpy())
-        _, gcs = binding.lbm_misfit_gradient(ens.ctx, win, ens.members, weights=w, grad_f0=grad)
-        gc = torch.tensor(float(np.sum(gcs)), dtype=cs.dtype, device=cs.device)
+        w = gJ.detach().to(device=f0.device, dtype=torch.float64).contiguous()
+        dcs = torch.empty(1, dtype=torch.float64, device=f0.device)
+        binding.lbm_misfit_gradient(ens.ctx, win, ens.members, weights=w, grad_f0=grad, dcs=dcs)
+        gc = dcs.reshape(()).to(device=cs.device, dtype=cs.dtype)
         return grad, gc, None, None
 
 

@@ -48,6 +48,7 @@ SIGNATURES = {
     "lbm_forecast": (_I, [_P, _I]),
     "lbm_moments": (_I, [_P, _P, _P, _P, _I]),
     "lbm_mean_velocity": (_I, [_P, _P, _P, _I]),
+    "lbm_velocity_rmse": (_I, [_P, _P, _P, _I]),
     "lbm_energy_spectrum": (_I, [_P, _P, _I, _I]),
     "letkf_observe": (_I, [_P, _I, _P, _P, _P, _P, _D, _D]),
     "letkf_observe_rho": (_I, [_P, _I, _P, _P, _P, _P, _P, _D, _D, _D]),
@@ -58,7 +59,7 @@ SIGNATURES = {
     "letkf_set_run_length": (_I, [_P, _I]),
     "letkf_sweep_stats": (_I, [_P, _I, _P]),
     "lbm_misfit": (_I, [_P, ctypes.POINTER(lbm_window), _P]),
-    "lbm_misfit_gradient": (_I, [_P, ctypes.POINTER(lbm_window), _P, _P, _P, _P, _I]),
+    "lbm_misfit_gradient": (_I, [_P, ctypes.POINTER(lbm_window), _P, _P, _P, _P, _P, _I]),
     "lbm_nudge": (_I, [_P, _I, _I, _P, _P, _P, _D]),
     "lbm_get_f": (_I, [_P, _P, _I]),
     "lbm_set_f": (_I, [_P, _P, _I]),
@@ -282,17 +283,27 @@ def lbm_misfit(ctx, win: Window, members: int):
     return J
 
 
-def lbm_misfit_gradient(ctx, win: Window, members: int, weights=None, grad_f0=None):
-    """Return (J [k], grad_cs [k]); grad_f0 (numpy or CUDA tensor, float64
-    [9][ny][nx][k]) is filled in place when given."""
+def lbm_misfit_gradient(ctx, win: Window, members: int, weights=None, grad_f0=None, dcs=None):
+    """Return (J [k], grad_cs [k]); grad_f0 (float64 [9][ny][nx][k]) and dcs
+    (float64 [1], dF/dC_s) are filled in place when given. weights, grad_f0
+    and dcs are numpy arrays or CUDA tensors (all of one kind)."""
     J = np.zeros(members)
     gcs = np.zeros(members)
-    w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
-    pw = None if w is None else w.ctypes.data_as(ctypes.c_void_p)
+    pw, kw, _kw = _arr(weights)
     pg, kg, _keep = _arr(grad_f0, writable=True)
+    pd, kd, _kd = _arr(dcs, writable=True)
+    kind = _kind(kw if weights is not None else None, kg if grad_f0 is not None else None,
+                 kd if dcs is not None else None)
     _check(ctx, load().lbm_misfit_gradient(ctx, ctypes.byref(win.c), pw, J.ctypes.data_as(ctypes.c_void_p),
-                                           pg, gcs.ctypes.data_as(ctypes.c_void_p), kg))
+                                           pg, gcs.ctypes.data_as(ctypes.c_void_p), pd, kind))
     return J, gcs
+
+
+def lbm_velocity_rmse(ctx, truth_ctx):
+    """Ensemble-mean velocity RMSE of ctx against truth_ctx (a float)."""
+    r = np.zeros(1)
+    _check(ctx, load().lbm_velocity_rmse(ctx, truth_ctx, r.ctypes.data_as(ctypes.c_void_p), LBM_PTR_HOST))
+    return float(r[0])
 
 
 def letkf_analyze(ctx, d_cut, beta):
@@ -352,11 +363,18 @@ def letkf_analyze_noalloc(f, ix, iy, yo_u, yo_v, sigma_u, sigma_v, d_cut, beta, 
     f [9][ny][nx][members] in place; observations are host arrays."""
     if not _is_torch(f) or not f.is_cuda or f.dim() != 4:
         raise TypeError("f must be a 4-d CUDA float64 tensor [9][ny][nx][members]")
+    import torch
+
+    if f.device.index != torch.cuda.current_device():
+        raise ValueError("f must be on the current CUDA device (the scratch address and the stream are "
+                         "the current device's)")
     pf, _, _a = _arr(f)
     ix = np.ascontiguousarray(ix, dtype=np.int32)
     iy = np.ascontiguousarray(iy, dtype=np.int32)
     yo_u = np.ascontiguousarray(yo_u, dtype=np.float64)
     yo_v = np.ascontiguousarray(yo_v, dtype=np.float64)
+    if not (len(ix) == len(iy) == len(yo_u) == len(yo_v)):
+        raise ValueError("ix, iy, yo_u and yo_v must have the same length")
     if stream == "current":
         stream = default_stream()
     p = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
@@ -428,6 +446,10 @@ class Ensemble:
             grad_f0 = np.zeros((9, self.ny, self.nx, self.members))
         J, gcs = lbm_misfit_gradient(self.ctx, win, self.members, weights, grad_f0)
         return J, grad_f0, gcs
+
+    def velocity_rmse(self, truth):
+        """Ensemble-mean velocity RMSE against another Ensemble (the truth)."""
+        return lbm_velocity_rmse(self.ctx, truth.ctx)
 
     def observe_rho(self, ix, iy, yo_u, yo_v, yo_rho, sigma_u, sigma_v, sigma_rho):
         letkf_observe_rho(self.ctx, ix, iy, yo_u, yo_v, yo_rho, sigma_u, sigma_v, sigma_rho)

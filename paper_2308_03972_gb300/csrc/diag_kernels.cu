@@ -160,6 +160,44 @@ __global__ void spectrum_reduce_kernel(const double* __restrict__ P, int k, int 
     E[s] = acc / k;
 }
 
+// RMSE of two velocity fields (Section 4.3 scores the ensemble mean
+// against the truth): sum over cells of (u1 - u2)^2 + (v1 - v2)^2 in FP64,
+// block partials in a fixed order, then one block sums the partials in
+// order and writes sqrt(sum / n).
+constexpr int kRmseBlocks = 256, kRmseThreads = 256;
+
+__global__ void __launch_bounds__(kRmseThreads) rmse_partial_kernel(const double* __restrict__ u1,
+                                                                   const double* __restrict__ v1,
+                                                                   const double* __restrict__ u2,
+                                                                   const double* __restrict__ v2, size_t n,
+                                                                   double* __restrict__ partial) {
+    __shared__ double red[kRmseThreads];
+    double s = 0.0;
+    for (size_t i = (size_t)blockIdx.x * kRmseThreads + threadIdx.x; i < n; i += (size_t)kRmseBlocks * kRmseThreads) {
+        const double du = u1[i] - u2[i], dv = v1[i] - v2[i];
+        s += du * du + dv * dv;
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int h = kRmseThreads / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+__global__ void __launch_bounds__(kRmseThreads) rmse_final_kernel(const double* __restrict__ partial, size_t n,
+                                                                 double* __restrict__ out) {
+    __shared__ double red[kRmseThreads];
+    red[threadIdx.x] = threadIdx.x < kRmseBlocks ? partial[threadIdx.x] : 0.0;
+    __syncthreads();
+    for (int h = kRmseThreads / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sqrt(red[0] / (double)n);
+}
+
 }  // namespace
 
 size_t spectrum_work_bytes(int nx, int ny, int k, int nshells) {
@@ -200,6 +238,16 @@ cudaError_t launch_energy_spectrum(const void* f, int fp32, int nx, int ny, int 
                                                                            nshells, P);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     spectrum_reduce_kernel<<<(nshells + 127) / 128, 128, 0, s>>>(P, k, hx, nshells, E);
+    return cudaGetLastError();
+}
+
+size_t rmse_work_doubles() { return kRmseBlocks; }
+
+cudaError_t launch_velocity_rmse(const double* u1, const double* v1, const double* u2, const double* v2, size_t n,
+                                 double* work, double* out, cudaStream_t s) {
+    if (n == 0) return cudaErrorInvalidValue;
+    rmse_partial_kernel<<<kRmseBlocks, kRmseThreads, 0, s>>>(u1, v1, u2, v2, n, work);
+    rmse_final_kernel<<<1, kRmseThreads, 0, s>>>(work, n, out);
     return cudaGetLastError();
 }
 

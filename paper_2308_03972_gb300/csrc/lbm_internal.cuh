@@ -160,6 +160,12 @@ size_t spectrum_work_bytes(int nx, int ny, int k, int nshells);
 cudaError_t launch_energy_spectrum(const void* f, int fp32, int nx, int ny, int k, double* E,
                                    int nshells, void* work, int* flags, cudaStream_t s);
 
+// *out = sqrt(n^-1 sum_i (u1 - u2)^2 + (v1 - v2)^2), FP64, fixed summation
+// order; work: rmse_work_doubles() doubles.
+size_t rmse_work_doubles();
+cudaError_t launch_velocity_rmse(const double* u1, const double* v1, const double* u2, const double* v2, size_t n,
+                                 double* work, double* out, cudaStream_t s);
+
 // ---- adjoint_kernels.cu ---------------------------------------------------
 // Adjoint of one LBM step at the stored state f_t: lam_out = (df_{t+1}/df_t)^T
 // lam_in; dJ/dCs of every member added to gcs[k] (FP64). fp32: FP32 shifted

@@ -331,7 +331,7 @@ struct StreamScratch {
 // its checkpoint and the step adjoint runs back through them, adding the
 // misfit derivative at each observation time.
 int misfit_impl(lbm_ctx* c, const lbm_window* win, const double* w, double* J, double* grad_f0,
-                double* grad_cs, int ptr_kind, bool want_grad) {
+                double* grad_cs, double* dcs, int ptr_kind, bool want_grad) {
     if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
     if (!win) return fail(c, LBM_EINVAL, "window is NULL");
     if (!ptr_kind_ok(ptr_kind)) return fail(c, LBM_EINVAL, "bad ptr_kind");
@@ -352,7 +352,10 @@ int misfit_impl(lbm_ctx* c, const lbm_window* win, const double* w, double* J, d
             if (!std::isfinite(win->yo_u[i]) || !std::isfinite(win->yo_v[i]))
                 return fail(c, LBM_EINVAL, "observation %zu is not finite", i);
     }
-    if (w)
+    // Host weights are checked here; device weights (ptr_kind device) are the
+    // caller's responsibility.
+    const bool w_dev = w && ptr_kind == LBM_PTR_DEVICE;
+    if (w && !w_dev)
         for (int m = 0; m < c->k; ++m)
             if (!std::isfinite(w[m])) return fail(c, LBM_EINVAL, "weight %d is not finite", m);
     const int fp32 = is_fp32(c);
@@ -394,7 +397,7 @@ int misfit_impl(lbm_ctx* c, const lbm_window* win, const double* w, double* J, d
         hyo[2 * i] = win->yo_u[i];
         hyo[2 * i + 1] = win->yo_v[i];
     }
-    if (w) std::copy(w, w + k, hw.begin());
+    if (w && !w_dev) std::copy(w, w + k, hw.begin());
     const int* ixd = (const int*)d_pos;
     const int* iyd = ixd + np;
     const double* yod = (const double*)d_yo;
@@ -405,8 +408,12 @@ int misfit_impl(lbm_ctx* c, const lbm_window* win, const double* w, double* J, d
             CK(c, cudaMemcpyAsync(d_yo, hyo.data(), hyo.size() * sizeof(double),
                                   cudaMemcpyHostToDevice, c->stream), "copy observations");
     }
-    CK(c, cudaMemcpyAsync(d_w, hw.data(), (size_t)k * sizeof(double), cudaMemcpyHostToDevice, c->stream),
-       "copy weights");
+    if (w_dev)
+        CK(c, cudaMemcpyAsync(d_w, w, (size_t)k * sizeof(double), cudaMemcpyDeviceToDevice, c->stream),
+           "copy weights");
+    else
+        CK(c, cudaMemcpyAsync(d_w, hw.data(), (size_t)k * sizeof(double), cudaMemcpyHostToDevice, c->stream),
+           "copy weights");
     auto obs_time = [&](int t) { return (np > 0 && t >= 1 && t % E == 0 && t / E <= nt) ? t / E - 1 : -1; };
 
     // Forward sweep.
@@ -480,6 +487,16 @@ int misfit_impl(lbm_ctx* c, const lbm_window* win, const double* w, double* J, d
         if (grad_cs)
             CK(c, cudaMemcpyAsync(grad_cs, d_gcs, (size_t)k * sizeof(double), cudaMemcpyDeviceToHost,
                                   c->stream), "copy C_s gradient");
+        if (dcs) {
+            // dF/dC_s = sum_m w_m dJ_m/dC_s, summed on the device in member order.
+            void* d_dcs = dcs;
+            if (ptr_kind != LBM_PTR_DEVICE) CK(c, sc.get(&d_dcs, sizeof(double)), "allocating C_s gradient sum");
+            CK(c, launch_misfit_reduce((const double*)d_gcs, k, 1, (double*)d_dcs, c->stream),
+               "launching C_s gradient sum");
+            if (ptr_kind != LBM_PTR_DEVICE)
+                CK(c, cudaMemcpyAsync(dcs, d_dcs, sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+                   "copy C_s gradient sum");
+        }
     }
     CK(c, cudaStreamSynchronize(c->stream), "synchronising");
     return read_flags(c);
@@ -746,6 +763,37 @@ int lbm_mean_velocity(lbm_ctx* c, double* u, double* v, int ptr_kind) {
     return read_flags(c);
 }
 
+int lbm_velocity_rmse(lbm_ctx* c, lbm_ctx* truth, double* rmse, int ptr_kind) {
+    if (!c || !truth) return fail(c, LBM_EINVAL, "ctx is NULL");
+    if (!rmse) return fail(c, LBM_EINVAL, "rmse is NULL");
+    if (!ptr_kind_ok(ptr_kind)) return fail(c, LBM_EINVAL, "bad ptr_kind");
+    if (truth->nx != c->nx || truth->ny != c->ny) return fail(c, LBM_EINVAL, "the two lattices differ");
+    const size_t n = (size_t)c->nx * c->ny;
+    // The truth's state as queued on its own stream.
+    if (truth->stream != c->stream) {
+        cudaEvent_t ev;
+        CK(c, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "creating event");
+        cudaError_t e = cudaEventRecord(ev, truth->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, ev, 0);
+        cudaEventDestroy(ev);
+        CK(c, e, "ordering the two streams");
+    }
+    StreamScratch sc(c->stream);
+    void* buf;
+    CK(c, sc.get(&buf, (4 * n + rmse_work_doubles() + 1) * sizeof(double)), "allocating RMSE scratch");
+    double* b = (double*)buf;
+    double* out = ptr_kind == LBM_PTR_DEVICE ? rmse : b + 4 * n + rmse_work_doubles();
+    CK(c, launch_mean_velocity(c->f[c->cur], is_fp32(c), c->nx, c->ny, c->k, b, b + n, c->flags, c->stream),
+       "launching mean velocity");
+    CK(c, launch_mean_velocity(truth->f[truth->cur], is_fp32(truth), truth->nx, truth->ny, truth->k, b + 2 * n,
+                               b + 3 * n, truth->flags, c->stream),
+       "launching mean velocity");
+    CK(c, launch_velocity_rmse(b, b + n, b + 2 * n, b + 3 * n, n, b + 4 * n, out, c->stream), "launching RMSE");
+    if (ptr_kind == LBM_PTR_DEVICE) return LBM_OK;
+    CK(c, cudaMemcpyAsync(rmse, out, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy RMSE");
+    return read_flags(c);
+}
+
 int lbm_energy_spectrum(lbm_ctx* c, double* E, int nshells, int ptr_kind) {
     if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
     if (!ptr_kind_ok(ptr_kind)) return fail(c, LBM_EINVAL, "bad ptr_kind");
@@ -818,12 +866,12 @@ int lbm_set_closure(lbm_ctx* c, double cs_smag) {
 
 int lbm_misfit(lbm_ctx* c, const lbm_window* win, double* J) {
     if (c && !J) return fail(c, LBM_EINVAL, "J is NULL");
-    return misfit_impl(c, win, nullptr, J, nullptr, nullptr, LBM_PTR_HOST, false);
+    return misfit_impl(c, win, nullptr, J, nullptr, nullptr, nullptr, LBM_PTR_HOST, false);
 }
 
 int lbm_misfit_gradient(lbm_ctx* c, const lbm_window* win, const double* w, double* J,
-                        double* grad_f0, double* grad_cs, int ptr_kind) {
-    return misfit_impl(c, win, w, J, grad_f0, grad_cs, ptr_kind, true);
+                        double* grad_f0, double* grad_cs, double* dcs, int ptr_kind) {
+    return misfit_impl(c, win, w, J, grad_f0, grad_cs, dcs, ptr_kind, true);
 }
 
 int letkf_observe(lbm_ctx* c, int npts, const int* ix, const int* iy, const double* yo_u,

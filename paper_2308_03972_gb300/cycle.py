@@ -103,10 +103,9 @@ class Osse:
         self.cycle_index += 1
 
     def rmse(self):
-        """Velocity RMSE of the ensemble mean against the nature run."""
-        ut, vt = self.truth_velocity()
-        um, vm = self.ens.mean_velocity()
-        return float(np.sqrt(np.mean((um - ut) ** 2 + (vm - vt) ** 2)))
+        """Velocity RMSE of the ensemble mean against the nature run (reduced
+        on the device, lbm_velocity_rmse)."""
+        return self.ens.velocity_rmse(self.nature)
 
     def close(self):
         self.ens.close()

@@ -171,3 +171,27 @@ def test_adjoint_window_256x256_batch_64(gpu):
     np.testing.assert_allclose(J32, J64, rtol=1e-4)
     assert norm_rel(g32, g64) <= 1e-3
     np.testing.assert_allclose(c32, c64, rtol=1e-2)
+
+
+def test_cs_gradient_sum_on_the_device(gpu):
+    """dcs = sum_m w_m dJ_m/dC_s, summed on the device, host and device
+    outputs, against the oracle's C_s derivative; device weights."""
+    import torch
+
+    nx = ny = 32
+    k = 4
+    f0, force, w = _window_case(nx, ny, k, 30, 10, 4, seed=9)
+    weights = np.array([0.5, 1.0, -1.5, 2.0])
+    _, _, cr = oracle_adjoint.misfit_gradient(f0, force, TAU0, CS, MU, w, weights=weights)
+    with gpu.Ensemble(nx, ny, k, TAU0, CS, MU, gpu.LBM_FP64, f0=f0, force=force) as e:
+        dh = np.zeros(1)
+        _, gcs = gpu.lbm_misfit_gradient(e.ctx, _win(gpu, w), k, weights=weights, dcs=dh)
+        wd = torch.tensor(weights, dtype=torch.float64, device="cuda")
+        gd = torch.empty((9, ny, nx, k), dtype=torch.float64, device="cuda")
+        dd = torch.zeros(1, dtype=torch.float64, device="cuda")
+        gpu.lbm_misfit_gradient(e.ctx, _win(gpu, w), k, weights=wd, grad_f0=gd, dcs=dd)
+        e.sync()
+    total = float(np.sum(cr))
+    assert abs(dh[0] - np.sum(gcs)) <= 1e-14 * np.abs(gcs).sum()
+    assert abs(dh[0] - total) <= 1e-9 * abs(total) + 1e-12 * np.abs(cr).max()
+    assert abs(float(dd.item()) - dh[0]) <= 1e-13 * abs(dh[0])  # per-block atomics: order varies

@@ -87,3 +87,24 @@ def test_single_mode_lands_in_its_shell(gpu):
         e.sync()
     assert abs(E[10] - A * A / 4) <= 1e-13 * A * A
     assert np.max(np.abs(np.delete(E, 10))) <= 1e-14 * A * A
+
+
+def test_velocity_rmse_on_the_device(gpu):
+    """lbm_velocity_rmse against the RMSE of the two contexts' mean
+    velocities (one member for the truth, several for the ensemble)."""
+    nx, ny, k = 40, 24, 6
+    u, v = inputs.ensemble_velocity(nx, ny, k, 7, U_RMS)
+    tu, tv = inputs.random_velocity(nx, ny, 8, U_RMS)
+    for prec in (gpu.LBM_FP64, gpu.LBM_MIXED):
+        with gpu.Ensemble(nx, ny, k, 0.55, 0.2, 0.0, prec) as e, \
+                gpu.Ensemble(nx, ny, 1, 0.55, 0.2, 0.0, gpu.LBM_FP64) as t:
+            e.set_equilibrium(None, u, v)
+            t.set_equilibrium(None, tu[:, :, None].copy(), tv[:, :, None].copy())
+            e.forecast(3)
+            t.forecast(3)
+            r = e.velocity_rmse(t)
+            um, vm = e.mean_velocity()
+            ut, vt = t.mean_velocity()
+            e.sync()
+        ref = np.sqrt(np.mean((um - ut) ** 2 + (vm - vt) ** 2))
+        assert abs(r / ref - 1) <= 1e-13

@@ -6,7 +6,8 @@ synchronisation is not allowed where they call from). It keeps its
 intermediates in a fixed device array instead of context buffers. Here it
 runs on a caller-owned CUDA tensor, through the C ABI, two calls in a row,
 and each result is compared with letkf_observe + letkf_analyze on a context
-holding the same ensemble. This file is collected last on purpose.
+holding the same ensemble, and the first also with the FP64 oracle. This
+file is collected last on purpose.
 """
 import numpy as np
 import pytest
@@ -48,6 +49,8 @@ def test_noalloc_analysis_matches_context_path_twice(gpu, nx, ny, k, nobs, d_cut
         torch.cuda.synchronize()
         assert norm_rel(f.cpu().numpy(), ref) <= TOL_FP64
     assert norm_rel(refs[1], refs[0]) > 1e-9  # the second call did new work
+    ix, iy, yu, yv = obs[0]
+    assert norm_rel(refs[0], oracle.letkf_analyze(f0, ix, iy, yu, yv, SIGMA, SIGMA, d_cut, 1.05)) <= TOL_FP64
 
 
 def test_noalloc_rejects_sizes_beyond_its_limits(gpu):
@@ -64,3 +67,21 @@ def test_noalloc_rejects_sizes_beyond_its_limits(gpu):
     with pytest.raises(gpu.LbmError) as err:
         gpu.letkf_analyze_noalloc(f, ix[:1], ix[:1], [0.0], [0.0], 0.1, 0.1, 2.0, 1.0)
     assert err.value.code == gpu.LBM_EINVAL
+
+
+def test_noalloc_refuses_local_problems_above_64(gpu):
+    """More than 64 members with dense observations: min(k, 2p) > 64 at
+    some grid point, which the FP64 analysis does not hold."""
+    import torch
+
+    nx = ny = 32
+    k = 128
+    f0 = turbulent_state(oracle, nx, ny, k, seed=3)
+    tu, tv = inputs.random_velocity(nx, ny, 5, U_RMS)
+    ix, iy, yu, yv = osse_observations(nx, ny, 8, 8, 4, 1, tu, tv, SIGMA)
+    f = torch.tensor(f0, dtype=torch.float64, device="cuda")
+    with pytest.raises(gpu.LbmError) as err:
+        gpu.letkf_analyze_noalloc(f, ix, iy, yu, yv, SIGMA, SIGMA, 8.0, 1.05)
+    assert err.value.code == gpu.LBM_EINVAL
+    with pytest.raises(ValueError):
+        gpu.letkf_analyze_noalloc(f, ix, iy[:-1], yu, yv, SIGMA, SIGMA, 8.0, 1.05)
