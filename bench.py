@@ -41,13 +41,13 @@ L2_NOTE = "state larger than L2: 151 MB per buffer in FP32, 302 MB in FP64 (L2 =
 # Set an entry to None when its kernel changes until it is captured again.
 # Issue-slot utilisation of the two mixed-analysis kernels in the same ncu
 # capture (profiles/analysis_mixed_256x256_k64.md).
-ISSUE_ACTIVE = {"run_jacobi_kernel<28>": 0.61, "run_refine_kernel<28>": 0.45}
+ISSUE_ACTIVE = {"run_jacobi_kernel<28>": 0.689, "run_refine_kernel<28>": 0.569}
 # Launches of one mixed analysis at 256^2 x 64 (runs of 8 grid points, one
 # chunk of runs): binary32 copy of dY, split of the observation Gram, the
 # Jacobi kernel and the refinement kernel.
 MIXED_ANALYSIS_LAUNCHES = 4
 NCU_TRAFFIC = {
-    "analysis_mixed": None,  # run kernels changed since the last capture
+    "analysis_mixed": 1.319424e6 + 154.980352e6 + 365.209856e6 + 115.742464e6,  # run kernels J + F
     "lbm_step_f32": 151.54816e6 + 97.796096e6,
     "analysis_fp64": 304.459264e6 + 241.096192e6,
 }
@@ -171,7 +171,7 @@ def analysis_flops(cfg, p):
     return float(np.sum(eig + np.where(obs, prod_obs, prod_ens)))
 
 
-def measure(cfg, precision, steps, warmup, sample_clocks=False, gpu_index=0):
+def measure(cfg, precision, steps, warmup, sample_clocks=False, gpu_index=0, run_length=8):
     import torch
 
     from paper_2308_03972_gb300 import binding
@@ -179,6 +179,8 @@ def measure(cfg, precision, steps, warmup, sample_clocks=False, gpu_index=0):
 
     stream = torch.cuda.current_stream()
     osse = Osse(cfg, precision, stream=stream.cuda_stream)
+    if precision == binding.LBM_MIXED:
+        osse.ens.set_run_length(run_length)
     obs = osse.observations(warmup + steps)
     for c in range(warmup):
         osse.cycle(obs[c])
@@ -620,6 +622,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--run-length", type=int, default=8,
+                    help="grid points per run of the mixed analysis (0: the chunked path)")
     ap.add_argument("--window", type=int, default=200, help="adjoint window steps (--case adjoint)")
     ap.add_argument("--checkpoint", type=int, default=20, help="adjoint checkpoint spacing (--case adjoint)")
     ap.add_argument("--case", default="all", choices=["all", "cycle", "adjoint", "sweep", "batch", "osse"],
@@ -674,7 +678,8 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
-    mixed = measure(cfg, binding.LBM_MIXED, args.steps, args.warmup, sample_clocks=(rank == 0), gpu_index=local)
+    mixed = measure(cfg, binding.LBM_MIXED, args.steps, args.warmup, sample_clocks=(rank == 0), gpu_index=local,
+                    run_length=args.run_length)
     ms = barrier_max(mixed["ms_per_cycle"])
     fp64 = measure(cfg, binding.LBM_FP64, max(3, args.steps // 3), args.warmup)
     ms64 = barrier_max(fp64["ms_per_cycle"])
