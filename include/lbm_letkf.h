@@ -370,6 +370,16 @@ int lbm_batch_cycle(lbm_batch *b, int nsteps, const int *npts, const int *const 
 /* Wait for the batch's work; reports a timed-out grid barrier, then each
  * context's deferred status (as lbm_sync). */
 int lbm_batch_sync(lbm_batch *b);
+
+/* Bound of every grid-barrier wait of the batch's persistent forecast:
+ * spin_limit rounds of a 100 ns sleep (1 .. 20,000,000, the default; about
+ * 2-4 s). absent = 1 makes each barrier wait for one participant more than
+ * the grid holds, so every wait runs out: the forecast stops after its first
+ * step, every block returns, and lbm_batch_sync reports LBM_ECUDA ("a grid
+ * barrier ... timed out"); this exercises the timeout path without a fault.
+ * absent = 0 restores normal operation. Synchronises; a captured cycle is
+ * captured again. LBM_EINVAL outside these ranges. */
+int lbm_batch_set_barrier(lbm_batch *b, long long spin_limit, int absent);
 const char *lbm_batch_last_error(const lbm_batch *b);
 void lbm_batch_destroy(lbm_batch *b);
 

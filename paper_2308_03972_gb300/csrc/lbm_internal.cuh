@@ -82,9 +82,13 @@ struct MultiExp {
 constexpr int kMaxMultiExp = 64;
 // Cooperative launch of `blocks` x `threads` advancing every experiment
 // nsteps steps (ex_dev: device array). bar: two zeroed words (reset here);
-// status: set to 1 if a grid barrier timed out.
+// status: set to 1 if a grid barrier timed out. Each barrier wait spins at
+// most spin_limit rounds of a 100 ns sleep; absent > 0 makes every wait run
+// out (participants that never arrive).
+constexpr long long kBarrierSpins = 20000000;  // default: ~2-4 s
 cudaError_t launch_lbm_multi(const MultiExp* ex_dev, int nexp, long long total, int nsteps, int fp32,
-                             int blocks, int threads, unsigned* bar, int* status, cudaStream_t s);
+                             int blocks, int threads, unsigned* bar, int* status, long long spin_limit,
+                             unsigned absent, cudaStream_t s);
 // Largest co-resident grid for the multi kernel (0 on error).
 int lbm_multi_max_blocks(int fp32, int threads);
 // Nudging toward f^eq of observations on a uniform lattice; obs = rho, u, v

@@ -145,9 +145,8 @@ __global__ void __launch_bounds__(256) lbm_step_kernel(const T* __restrict__ fin
 // Every experiment (its own lattice, members, parameters and state buffers)
 // contributes nx * ny * k / V work items per step; a cooperative grid strides
 // over the items of all experiments, then meets at a grid barrier before the
-// next step. The barrier spins at most kBarrierSpins rounds (with a short
+// next step. The barrier spins at most spin_limit rounds (with a short
 // sleep): on timeout the block records it in status and the kernel stops.
-constexpr long long kBarrierSpins = 20000000;  // ~2-4 s of 100 ns sleeps
 
 template <typename T>
 __device__ __forceinline__ void multi_item(const MultiExp& e, int step, long long t) {
@@ -168,8 +167,11 @@ __device__ __forceinline__ void multi_item(const MultiExp& e, int step, long lon
 }
 
 // Sense-reversing grid barrier over gridDim.x blocks (count, gen in global
-// memory, both zero before the launch). Returns false on timeout.
-__device__ bool grid_barrier(unsigned* count, unsigned* gen, int* status) {
+// memory, both zero before the launch), waiting for gridDim.x + absent
+// arrivals: absent > 0 stands for participants that never arrive, so every
+// wait runs out (the timeout path, exercised on purpose). Returns false on
+// timeout.
+__device__ bool grid_barrier(unsigned* count, unsigned* gen, int* status, long long spin_limit, unsigned absent) {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -177,14 +179,14 @@ __device__ bool grid_barrier(unsigned* count, unsigned* gen, int* status) {
         volatile unsigned* vg = gen;
         const unsigned g = *vg;
         __threadfence();
-        if (atomicAdd(count, 1u) == gridDim.x - 1) {
+        if (atomicAdd(count, 1u) == gridDim.x + absent - 1) {
             *count = 0u;
             __threadfence();
             atomicAdd(gen, 1u);
         } else {
             long long spins = 0;
             while (*vg == g) {
-                if (++spins > kBarrierSpins) {
+                if (++spins > spin_limit) {
                     atomicOr(status, 1);
                     ok = 0;
                     break;
@@ -202,7 +204,8 @@ template <typename T>
 __global__ void __launch_bounds__(512) lbm_multi_kernel(const MultiExp* __restrict__ ex, int nexp,
                                                         long long total, int nsteps,
                                                         unsigned* __restrict__ bar,
-                                                        int* __restrict__ status) {
+                                                        int* __restrict__ status, long long spin_limit,
+                                                        unsigned absent) {
     __shared__ MultiExp se[kMaxMultiExp];
     for (int i = threadIdx.x; i < nexp; i += blockDim.x) se[i] = ex[i];
     __syncthreads();
@@ -213,7 +216,7 @@ __global__ void __launch_bounds__(512) lbm_multi_kernel(const MultiExp* __restri
             while (t >= se[e].offset + se[e].items) ++e;  // items are in experiment order
             multi_item<T>(se[e], step, t - se[e].offset);
         }
-        if (step + 1 < nsteps && !grid_barrier(bar, bar + 1, status)) return;
+        if (step + 1 < nsteps && !grid_barrier(bar, bar + 1, status, spin_limit, absent)) return;
     }
 }
 
@@ -411,10 +414,11 @@ cudaError_t launch_lbm_step_f32(const float* gin, float* gout, const float* forc
 }
 
 cudaError_t launch_lbm_multi(const MultiExp* ex_dev, int nexp, long long total, int nsteps, int fp32,
-                             int blocks, int threads, unsigned* bar, int* status, cudaStream_t s) {
-    if (nexp < 1 || nexp > kMaxMultiExp || nsteps < 1 || blocks < 1) return cudaErrorInvalidValue;
+                             int blocks, int threads, unsigned* bar, int* status, long long spin_limit,
+                             unsigned absent, cudaStream_t s) {
+    if (nexp < 1 || nexp > kMaxMultiExp || nsteps < 1 || blocks < 1 || spin_limit < 1) return cudaErrorInvalidValue;
     void* args[] = {(void*)&ex_dev, (void*)&nexp, (void*)&total, (void*)&nsteps, (void*)&bar,
-                    (void*)&status};
+                    (void*)&status, (void*)&spin_limit, (void*)&absent};
     cudaError_t e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     if (fp32)

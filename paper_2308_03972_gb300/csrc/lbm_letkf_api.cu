@@ -1061,6 +1061,8 @@ struct lbm_batch {
     long long total = 0;
     unsigned* bar = nullptr;      // grid barrier words
     int* status = nullptr;        // barrier timeout flag (device)
+    long long spin_limit = kBarrierSpins;  // bound of each grid-barrier wait
+    unsigned absent = 0;          // arrivals that never come (timeout path)
     int threads = 256, blocks = 0;
     bool tuned = false;
     // Cycle state: fixed observation positions per experiment, pinned
@@ -1129,7 +1131,7 @@ int batch_forecast_impl(lbm_batch* b, int nsteps) {
                           b->stream),
        "copy experiment table");
     BK(b, launch_lbm_multi(b->ex_dev, (int)b->ex.size(), b->total, nsteps, b->fp32, b->blocks, b->threads,
-                           b->bar, b->status, b->stream),
+                           b->bar, b->status, b->spin_limit, b->absent, b->stream),
        "launching persistent forecast");
     for (lbm_ctx* c : b->ctx) {
         c->cur = (c->cur + nsteps) & 1;
@@ -1215,7 +1217,7 @@ int lbm_batch_autotune(lbm_batch* b, int* threads, int* blocks) {
             for (int r = 0; r < 3; ++r) {
                 cudaEventRecord(t0, b->stream);
                 cudaError_t e = launch_lbm_multi(b->ex_dev, (int)b->ex.size(), b->total, 1, b->fp32, nb, th,
-                                                 b->bar, b->status, b->stream);
+                                                 b->bar, b->status, b->spin_limit, b->absent, b->stream);
                 cudaEventRecord(t1, b->stream);
                 if (e != cudaSuccess || cudaEventSynchronize(t1) != cudaSuccess) {
                     cudaEventDestroy(t0);
@@ -1339,7 +1341,7 @@ int lbm_batch_cycle(lbm_batch* b, int nsteps, const int* npts, const int* const*
         for (lbm_ctx* c : b->ctx) c->stream = b->cap;
         BK(b, cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal), "beginning capture");
         cudaError_t e = launch_lbm_multi(b->ex_dev, n, b->total, nsteps, b->fp32, b->blocks, b->threads, b->bar,
-                                         b->status, b->cap);
+                                         b->status, b->spin_limit, b->absent, b->cap);
         int st = e == cudaSuccess ? LBM_OK : LBM_ECUDA;
         for (int i = 0; i < n && st == LBM_OK; ++i) {
             st = observe_from_pinned(b->ctx[i], b->h_yo[i]);
@@ -1360,6 +1362,26 @@ int lbm_batch_cycle(lbm_batch* b, int nsteps, const int* npts, const int* const*
     BK(b, cudaEventRecord(b->done, b->stream), "recording event");
     b->launched = true;
     ++b->cycles;
+    return LBM_OK;
+}
+
+int lbm_batch_set_barrier(lbm_batch* b, long long spin_limit, int absent) {
+    if (!b) return bfail(nullptr, LBM_EINVAL, "batch is NULL");
+    if (spin_limit < 1 || spin_limit > kBarrierSpins) return bfail(b, LBM_EINVAL, "spin_limit out of range");
+    if (absent < 0 || absent > 1) return bfail(b, LBM_EINVAL, "absent must be 0 or 1");
+    BK(b, cudaStreamSynchronize(b->stream), "synchronising");
+    b->spin_limit = spin_limit;
+    b->absent = (unsigned)absent;
+    // A captured cycle holds the old values: capture again on the next cycle.
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    if (b->graph) {
+        cudaGraphDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    b->graph_steps = -1;
     return LBM_OK;
 }
 

@@ -162,3 +162,88 @@ def test_batch_argument_errors(gpu):
             b.cycle(9, _obs(1)[:1], [6.0], [1.05], use_graph=True)  # odd nsteps with a graph
     for e in a + c + [other]:
         e.close()
+
+
+def test_barrier_timeout_is_reported_and_the_batch_recovers(gpu):
+    """Every grid-barrier wait runs out (one participant that never
+    arrives, short spin limit): every block returns, lbm_batch_sync reports
+    the timeout, and with normal barriers the batch works again."""
+    states = _states()
+    ens = _ensembles(gpu, gpu.LBM_MIXED, states)
+    with gpu.Batch(ens) as b:
+        b.set_barrier(20000, absent=1)
+        b.forecast(3)  # stops at the first barrier, after one step
+        with pytest.raises(gpu.LbmError) as err:
+            b.sync()
+        assert err.value.code == gpu.LBM_ECUDA and "timed out" in str(err.value)
+        b.set_barrier(20000000, absent=0)
+        b.forecast(2)
+        b.sync()
+    ref = _ensembles(gpu, gpu.LBM_MIXED, states)
+    for e, r in zip(ens, ref):
+        r.forecast(3)
+        assert np.array_equal(e.get_f(), r.get_f())
+        e.close()
+        r.close()
+    with gpu.Batch(_ensembles(gpu, gpu.LBM_MIXED, states[:1])) as b:
+        with pytest.raises(gpu.LbmError):
+            b.set_barrier(0)
+        with pytest.raises(gpu.LbmError):
+            b.set_barrier(1000, absent=2)
+
+
+# The twelve experiments of the benchmark's batch leg: lattice side, members,
+# observation lattice side, localisation radius.
+TWELVE = [(128, 16, 8, 16.0), (128, 32, 16, 16.0), (128, 64, 8, 16.0), (128, 128, 8, 16.0),
+          (256, 16, 16, 32.0), (256, 32, 8, 32.0), (256, 64, 8, 32.0), (256, 128, 16, 16.0),
+          (512, 16, 32, 32.0), (512, 32, 16, 64.0), (512, 64, 8, 64.0), (512, 128, 32, 16.0)]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_twelve_experiments_match_oracle_at_sampled_points(gpu, prec):
+    """One batch cycle (graph-captured) of the twelve uneven experiments;
+    every experiment's analysis checked against the oracle's analysis of the
+    same forecast state at sampled grid points."""
+    p = gpu.LBM_FP64 if prec == "fp64" else gpu.LBM_MIXED
+    tol = TOL_FP64 if prec == "fp64" else 5e-8
+    rng = np.random.default_rng(7)
+    made, obs, dcs = [], [], []
+    for i, (n, k, no, dc) in enumerate(TWELVE):
+        u, v = inputs.ensemble_velocity(n, n, k, 50 + i, U_RMS, 0.2)
+        force = inputs.forcing_field(n, n, seed=60 + i, amp=3.5e-6)
+        ix, iy = inputs.uniform_obs_points(n, n, no, no)
+        tu, tv = inputs.random_velocity(n, n, 70 + i, U_RMS)
+        nu, nv = inputs.obs_noise(4, 1, len(ix))
+        obs.append((ix, iy, tu[iy, ix] + SIGMA * nu, tv[iy, ix] + SIGMA * nv, SIGMA, SIGMA))
+        made.append((n, k, u, v, force))
+        dcs.append(dc)
+
+    def build():
+        out = []
+        for n, k, u, v, force in made:
+            e = gpu.Ensemble(n, n, k, TAU0, CS, MU, p, force=force)
+            e.set_equilibrium(None, u, v)
+            out.append(e)
+        return out
+
+    # The forecast state each analysis starts from (the batch forecast is
+    # bit-identical to the cycle's, see the tests above).
+    fc = build()
+    with gpu.Batch(fc) as b:
+        b.forecast(10)
+        b.sync()
+    ens = build()
+    with gpu.Batch(ens) as b:
+        b.cycle(10, obs, dcs, [1.05] * len(TWELVE), use_graph=True)
+        b.sync()
+    for i, (e, f) in enumerate(zip(ens, fc)):
+        n = TWELVE[i][0]
+        pts = np.unique(np.concatenate([rng.integers(0, n * n, 24), [0, n - 1, n * n - 1]])).astype(np.int32)
+        f0 = f.get_f()
+        ix, iy, yu, yv, su, sv = obs[i]
+        ref = oracle.letkf_analyze(f0, ix, iy, yu, yv, su, sv, dcs[i], 1.05, points=pts)
+        k = f0.shape[3]
+        got = e.get_f().reshape(9, n * n, k)[:, pts]
+        assert norm_rel(got, ref.reshape(9, n * n, k)[:, pts]) <= tol, "experiment %d" % i
+        e.close()
+        f.close()
