@@ -182,17 +182,20 @@ int letkf_observe_rho(lbm_ctx *ctx, int npts, const int *ix, const int *iy,
 enum { LBM_PROD_FP64 = 0, LBM_PROD_FP32 = 1, LBM_PROD_TF32 = 2, LBM_PROD_BF16 = 3 };
 int letkf_set_products(lbm_ctx *ctx, int mode);
 
-/* Grid points per run of the mixed-precision analysis (Section 3.2: the
- * local analyses are independent, so they may be taken in any order). A
- * run is run_len consecutive grid points of one lattice row, analysed by
- * one warp over the union of their local observation sets: a scalar
- * outside a point's support enters that point with weight zero, which
- * leaves its analysis unchanged, and each point's binary32 Jacobi starts
- * from the previous point's basis. Used when every grid point has
- * p < members and every run's union holds at most 32 scalars; otherwise,
- * and with run_len = 0, the analysis takes the chunked path (cold-started
- * Jacobi per point). Default 8. LBM_EINVAL outside [0, 4096]. Applies to
- * later analyses; results agree with either path to rounding. */
+/* Grid points per run of the analysis (Section 3.2: the local analyses are
+ * independent, so they may be taken in any order). A run is run_len
+ * consecutive grid points of one lattice row, analysed by one warp over the
+ * union of their local observation sets: a scalar outside a point's
+ * support enters that point with weight zero, which leaves its analysis
+ * unchanged, and each point's binary32 Jacobi starts from the previous
+ * point's basis. In a mixed-precision context that basis is refined to
+ * FP64-class accuracy; in a double-precision context an FP64 Jacobi starts
+ * from it and runs to the cold path's stopping rule, so the eigenpairs are
+ * FP64's. Used when every grid point has p < members and every run's union
+ * holds at most 32 scalars; otherwise, and with run_len = 0, the analysis
+ * takes the cold-started path (one Jacobi per point from the identity).
+ * Default 8. LBM_EINVAL outside [0, 4096]. Applies to later analyses;
+ * results agree with either path to rounding. */
 int letkf_set_run_length(lbm_ctx *ctx, int run_len);
 
 /* Diagnostic: count the Jacobi sweeps of every local eigensolve of later

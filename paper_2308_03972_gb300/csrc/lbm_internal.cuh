@@ -147,6 +147,20 @@ size_t run_scratch_bytes(int nx, int ny, int nobs, int run_len, int maxunion);
 cudaError_t launch_analyze_runs(float* f, int nx, int ny, int k, const ObsParams& o, double d_cut,
                                 double beta, int run_len, int maxunion, int* flags, void* scratch,
                                 cudaStream_t s);
+// The same runs for a double-precision context: the binary32 Jacobi of the
+// run gives each grid point a starting basis, and an FP64 Jacobi from it
+// (launch_run_fp64, letkf_kernels.cu) gives the eigenpairs; transform and
+// update in FP64. scratch as above.
+cudaError_t launch_analyze_runs_fp64(double* f, int nx, int ny, int k, const ObsParams& o, double d_cut,
+                                     double beta, int run_len, int maxunion, int* flags, void* scratch,
+                                     cudaStream_t s);
+// FP64 warm-started analysis of the nruns * run_len grid points of the runs
+// run0.. (chunk-local basis Yg [.][ns][ns], eigenvalue estimates lamg
+// [.][ns] with -1 marking a point with no observation in range, union
+// lists rinfo [.][info_stride]).
+cudaError_t launch_run_fp64(double* f, int nx, int ny, int k, const ObsParams& o, double d_cut, double beta,
+                            int run_len, int run0, int nruns, int ns, const float* Yg, const float* lamg,
+                            const int* rinfo, int info_stride, int* flags, cudaStream_t s);
 // Diagnostic: the ensemble transform T = w-bar 1^T + W [npoints][k][k]
 // (FP64) that the run analysis' refined representation gives at the listed
 // grid points cells[npoints] (device), evaluated in FP64; f is not

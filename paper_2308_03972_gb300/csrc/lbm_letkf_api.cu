@@ -508,7 +508,7 @@ int misfit_impl(lbm_ctx* c, const lbm_window* win, const double* w, double* J, d
 struct AnalysisPlan {
     double d_cut = 0.0, beta = 0.0;
     int nmax = 0, plmax = 0, prod = PROD_FP64;
-    int run_len = 0, maxunion = 0;  // run_len > 0: the run analysis (mixed precision)
+    int run_len = 0, maxunion = 0;  // run_len > 0: the run analysis
 };
 
 int analyze_prepare(lbm_ctx* c, double d_cut, double beta, AnalysisPlan* plan) {
@@ -519,10 +519,11 @@ int analyze_prepare(lbm_ctx* c, double d_cut, double beta, AnalysisPlan* plan) {
     const int plmax = c->geo_pmax;
     // The reduced-precision Gram pass serves ensemble-space points only.
     const int prod = c->geo_any_ens ? c->prod : PROD_NONE;
-    // Mixed precision, every grid point in observation space and every run's
-    // union within one warp: the run analysis (warm-started Jacobi).
+    // Every grid point in observation space and every run's union within
+    // one warp: the run analysis (Jacobi warm-started along runs; in double
+    // precision the FP64 Jacobi starts from the run's binary32 basis).
     int run_len = 0, maxunion = 0;
-    if (is_fp32(c) && c->run_len > 0 && !c->geo_any_ens) {
+    if (c->run_len > 0 && !c->geo_any_ens) {
         maxunion = largest_run_union(c, d_cut, c->run_len);
         if (maxunion <= kRunMaxUnion) run_len = c->run_len;
     }
@@ -554,9 +555,14 @@ int analyze_launch(lbm_ctx* c, const AnalysisPlan& pl) {
     ObsParams o{c->npts, c->ix, c->iy, c->dY, c->d, c->G, c->sigma_u, c->sigma_v, c->dY32,
                 c->nvar, c->sigma_r, pl.plmax, c->sweep_stats ? c->sweep_hist : nullptr};
     if (pl.run_len > 0) {
-        CK(c, launch_analyze_runs((float*)c->f[c->cur], c->nx, c->ny, c->k, o, pl.d_cut, pl.beta, pl.run_len,
-                                  pl.maxunion, c->flags, c->ana_scratch, c->stream),
-           "launching analysis");
+        if (is_fp32(c))
+            CK(c, launch_analyze_runs((float*)c->f[c->cur], c->nx, c->ny, c->k, o, pl.d_cut, pl.beta, pl.run_len,
+                                      pl.maxunion, c->flags, c->ana_scratch, c->stream),
+               "launching analysis");
+        else
+            CK(c, launch_analyze_runs_fp64((double*)c->f[c->cur], c->nx, c->ny, c->k, o, pl.d_cut, pl.beta,
+                                           pl.run_len, pl.maxunion, c->flags, c->ana_scratch, c->stream),
+               "launching analysis");
         return LBM_OK;
     }
     CK(c, launch_analyze(c->f[c->cur], is_fp32(c), c->nx, c->ny, c->k, o, pl.d_cut, pl.beta, pl.nmax,

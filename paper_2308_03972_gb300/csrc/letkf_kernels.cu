@@ -503,6 +503,110 @@ struct AnaSmem {
     }
 };
 
+// Observation-space transform and update of one grid point (FP64), after
+// the eigensolve: A holds S = U^T A U (nearly diagonal), U the basis;
+// lidx, lsq, ldh the n local scalars (zero weight on padding), dX and
+// xbar the staged state; the result goes to fc. One warp.
+template <int NM>
+__device__ void fp64_obs_update(AnaSmem<NM>& sm, double* __restrict__ fc, size_t plane, int k, int n,
+                                double aa, double beta, const ObsParams& o, int lane) {
+    constexpr int ld = AnaSmem<NM>::kLd;
+    double* A = sm.A;
+    double* U = sm.U;
+    // With u_i = sqrt(a + s_ii), h(s) = 1/(a+s) and g(s) = ((a+s)^{-1/2} - a^{-1/2}) / s:
+    //   h(S)_ii = 1/u_i^2, h(S)_ij = -s_ij / (u_i^2 u_j^2),
+    //   g(S)_ii = -alpha_i / r, g(S)_ij = s_ij (u_i+u_j+r) alpha_i alpha_j / (r (u_i+u_j)),
+    // alpha_i = 1 / (u_i (u_i + r)), r = sqrt(a).
+    const double rr = sqrt(aa);
+    const double ir = 1.0 / rr;
+    for (int c = lane; c < n; c += 32) {
+        const double sii = A[c * ld + c];
+        const double u = sqrt(aa + sii);
+        sm.v3[c] = u;
+        sm.v4[c] = 1.0 / (aa + sii);      // h_i
+        sm.v5[c] = 1.0 / (u * (u + rr));  // alpha_i
+        double t = 0.0;
+        for (int l = 0; l < n; ++l) t += U[l * ld + c] * sm.ldh[l];
+        sm.v1[c] = t;  // t1 = U^T d-hat
+    }
+    __syncwarp();
+    for (int c = lane; c < n; c += 32) {
+        double t = 0.0;
+        for (int j = 0; j < n; ++j)
+            if (j != c) t += A[c * ld + j] * (sm.v4[j] * sm.v1[j]);
+        sm.v2[c] = sm.v4[c] * (sm.v1[c] - t);  // t2 = h(S) t1
+    }
+    __syncwarp();
+    for (int c = lane; c < n; c += 32) {
+        // g(S), column c, over S (each column is read and written by one lane).
+        const double ui = sm.v3[c];
+        const double ai = sm.v5[c];
+        for (int j = 0; j < n; ++j) {
+            const double uj = sm.v3[j];
+            A[j * ld + c] = (j == c) ? -ai * ir : A[j * ld + c] * (ui + uj + rr) * ai * sm.v5[j] * ir / (ui + uj);
+        }
+        double t = 0.0;
+        for (int l = 0; l < n; ++l) t += U[c * ld + l] * sm.v2[l];
+        sm.v1[c] = t;  // v = U t2 = (a I + A)^{-1} d-hat
+        // Z = dX Yh^T, column c.
+        const double* row = o.dY + (size_t)sm.lidx[c] * k;
+        double acc[9];
+#pragma unroll
+        for (int a = 0; a < 9; ++a) acc[a] = 0.0;
+        for (int m = 0; m < k; ++m) {
+            const double dy = row[m];
+#pragma unroll
+            for (int a = 0; a < 9; ++a) acc[a] += sm.dX[a * k + m] * dy;
+        }
+#pragma unroll
+        for (int a = 0; a < 9; ++a) sm.Z[a * NM + c] = sm.lsq[c] * acc[a];
+    }
+    __syncwarp();
+    // zv = Z v (= dX w-bar); B = Z U.
+    if (lane < 9) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) s += sm.Z[lane * NM + i] * sm.v1[i];
+        sm.zv[lane] = s;
+    }
+    for (int c = lane; c < n; c += 32)
+        for (int a = 0; a < 9; ++a) {
+            double s = 0.0;
+            for (int l = 0; l < n; ++l) s += sm.Z[a * NM + l] * U[l * ld + c];
+            sm.B[a * NM + c] = s;
+        }
+    __syncwarp();
+    // Z <- (Z U) g(S).
+    for (int c = lane; c < n; c += 32)
+        for (int a = 0; a < 9; ++a) {
+            double s = 0.0;
+            for (int j = 0; j < n; ++j) s += sm.B[a * NM + j] * A[j * ld + c];
+            sm.Z[a * NM + c] = s;
+        }
+    __syncwarp();
+    // B <- sqrt(k-1) Z U^T diag(sqrt(rho)), ready to meet dY.
+    const double sk = sqrt((double)(k - 1));
+    for (int c = lane; c < n; c += 32)
+        for (int a = 0; a < 9; ++a) {
+            double s = 0.0;
+            for (int l = 0; l < n; ++l) s += sm.Z[a * NM + l] * U[c * ld + l];
+            sm.B[a * NM + c] = sk * sm.lsq[c] * s;
+        }
+    __syncwarp();
+    const double sb = sqrt(beta);
+    for (int m = lane; m < k; m += 32) {
+        double acc[9];
+#pragma unroll
+        for (int a = 0; a < 9; ++a) acc[a] = sm.xbar[a] + sm.zv[a] + sb * sm.dX[a * k + m];
+        for (int i = 0; i < n; ++i) {
+            const double dy = o.dY[(size_t)sm.lidx[i] * k + m];
+#pragma unroll
+            for (int a = 0; a < 9; ++a) acc[a] += sm.B[a * NM + i] * dy;
+        }
+#pragma unroll
+        for (int a = 0; a < 9; ++a) fc[a * plane + m] = acc[a];
+    }
+}
+
 // FP64 analysis, one warp per grid point, local problems up to NM (32 or 64;
 // lanes own columns c = lane, lane + 32, ...).
 template <int NM>
@@ -598,99 +702,7 @@ __global__ void __launch_bounds__(32) analyze_fp64_kernel(double* __restrict__ f
     __syncwarp();
 
     if (obs_space) {
-        // S = U^T A U (nearly diagonal, in A). With u_i = sqrt(a + s_ii),
-        // h(s) = 1/(a+s) and g(s) = ((a+s)^{-1/2} - a^{-1/2}) / s:
-        //   h(S)_ii = 1/u_i^2, h(S)_ij = -s_ij / (u_i^2 u_j^2),
-        //   g(S)_ii = -alpha_i / r, g(S)_ij = s_ij (u_i+u_j+r) alpha_i alpha_j / (r (u_i+u_j)),
-        // alpha_i = 1 / (u_i (u_i + r)), r = sqrt(a).
-        const double rr = sqrt(aa);
-        const double ir = 1.0 / rr;
-        for (int c = lane; c < n; c += 32) {
-            const double sii = A[c * ld + c];
-            const double u = sqrt(aa + sii);
-            sm.v3[c] = u;
-            sm.v4[c] = 1.0 / (aa + sii);      // h_i
-            sm.v5[c] = 1.0 / (u * (u + rr));  // alpha_i
-            double t = 0.0;
-            for (int l = 0; l < n; ++l) t += U[l * ld + c] * sm.ldh[l];
-            sm.v1[c] = t;  // t1 = U^T d-hat
-        }
-        __syncwarp();
-        for (int c = lane; c < n; c += 32) {
-            double t = 0.0;
-            for (int j = 0; j < n; ++j)
-                if (j != c) t += A[c * ld + j] * (sm.v4[j] * sm.v1[j]);
-            sm.v2[c] = sm.v4[c] * (sm.v1[c] - t);  // t2 = h(S) t1
-        }
-        __syncwarp();
-        for (int c = lane; c < n; c += 32) {
-            // g(S), column c, over S (each column is read and written by one lane).
-            const double ui = sm.v3[c];
-            const double ai = sm.v5[c];
-            for (int j = 0; j < n; ++j) {
-                const double uj = sm.v3[j];
-                A[j * ld + c] = (j == c) ? -ai * ir : A[j * ld + c] * (ui + uj + rr) * ai * sm.v5[j] * ir / (ui + uj);
-            }
-            double t = 0.0;
-            for (int l = 0; l < n; ++l) t += U[c * ld + l] * sm.v2[l];
-            sm.v1[c] = t;  // v = U t2 = (a I + A)^{-1} d-hat
-            // Z = dX Yh^T, column c.
-            const double* row = o.dY + (size_t)sm.lidx[c] * k;
-            double acc[9];
-#pragma unroll
-            for (int a = 0; a < 9; ++a) acc[a] = 0.0;
-            for (int m = 0; m < k; ++m) {
-                const double dy = row[m];
-#pragma unroll
-                for (int a = 0; a < 9; ++a) acc[a] += sm.dX[a * k + m] * dy;
-            }
-#pragma unroll
-            for (int a = 0; a < 9; ++a) sm.Z[a * NM + c] = sm.lsq[c] * acc[a];
-        }
-        __syncwarp();
-        // zv = Z v (= dX w-bar); B = Z U.
-        if (lane < 9) {
-            double s = 0.0;
-            for (int i = 0; i < n; ++i) s += sm.Z[lane * NM + i] * sm.v1[i];
-            sm.zv[lane] = s;
-        }
-        for (int c = lane; c < n; c += 32)
-            for (int a = 0; a < 9; ++a) {
-                double s = 0.0;
-                for (int l = 0; l < n; ++l) s += sm.Z[a * NM + l] * U[l * ld + c];
-                sm.B[a * NM + c] = s;
-            }
-        __syncwarp();
-        // Z <- (Z U) g(S).
-        for (int c = lane; c < n; c += 32)
-            for (int a = 0; a < 9; ++a) {
-                double s = 0.0;
-                for (int j = 0; j < n; ++j) s += sm.B[a * NM + j] * A[j * ld + c];
-                sm.Z[a * NM + c] = s;
-            }
-        __syncwarp();
-        // B <- sqrt(k-1) Z U^T diag(sqrt(rho)), ready to meet dY.
-        const double sk = sqrt((double)(k - 1));
-        for (int c = lane; c < n; c += 32)
-            for (int a = 0; a < 9; ++a) {
-                double s = 0.0;
-                for (int l = 0; l < n; ++l) s += sm.Z[a * NM + l] * U[c * ld + l];
-                sm.B[a * NM + c] = sk * sm.lsq[c] * s;
-            }
-        __syncwarp();
-        const double sb = sqrt(beta);
-        for (int m = lane; m < k; m += 32) {
-            double acc[9];
-#pragma unroll
-            for (int a = 0; a < 9; ++a) acc[a] = sm.xbar[a] + sm.zv[a] + sb * sm.dX[a * k + m];
-            for (int i = 0; i < n; ++i) {
-                const double dy = o.dY[(size_t)sm.lidx[i] * k + m];
-#pragma unroll
-                for (int a = 0; a < 9; ++a) acc[a] += sm.B[a * NM + i] * dy;
-            }
-#pragma unroll
-            for (int a = 0; a < 9; ++a) fc[a * plane + m] = acc[a];
-        }
+        fp64_obs_update<NM>(sm, fc, plane, k, n, aa, beta, o, lane);
     } else {
         // lam = diag; w-bar = U diag(1/lam) U^T b; T = W + w-bar 1^T with
         // W = sqrt(k-1) U diag(lam^{-1/2}) U^T, stored over A.
@@ -723,6 +735,176 @@ __global__ void __launch_bounds__(32) analyze_fp64_kernel(double* __restrict__ f
             }
         }
     }
+}
+
+// FP64 analysis warm-started from a binary32 basis: the run path of a
+// double-precision context, one warp per grid point. The binary32 Jacobi
+// over the run (kernel J in letkf_runs.cu) leaves per point a basis Y of the
+// run's union of local scalars (NS x NS, row-major, Y_ic = component i of
+// vector c). Union scalars outside this point's support have weight zero, so
+// their rows and columns of A vanish and the result is that of the point's
+// own local set (exactly, in exact arithmetic). In FP64:
+//  1. Y1 = Y (I - E/2) with E = Y^T Y - I: Y is orthonormal to ~1e-7 in
+//     binary32, Y1 to ~|E|^2.
+//  2. A' = Y1^T A Y1 (symmetrised), diagonal to ~1e-6 of ||A||.
+//  3. The FP64 cyclic Jacobi of the cold path from A' with U = Y1 at the
+//     start and the same stopping rule (3e-8 ||A||_F): one rotating sweep
+//     where a cold start needs five or six.
+//  4. The FP64 transform and update of the cold path.
+// The eigenpairs are FP64's; the binary32 basis is only where the FP64
+// Jacobi starts.
+template <int NS>
+__global__ void __launch_bounds__(32) run_fp64_kernel(double* __restrict__ f, int nx, int ny, int k, ObsParams o,
+                                                      double d_cut, double beta, int R, int run0,
+                                                      const float* __restrict__ Yg, const float* __restrict__ lamg,
+                                                      const int* __restrict__ rinfo, int info_stride,
+                                                      int* __restrict__ flags) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int ld = AnaSmem<NS>::kLd;
+    AnaSmem<NS> sm;
+    sm.carve(smem_raw, k, NS);
+    double* A = sm.A;
+    double* U = sm.U;
+    const int lane = threadIdx.x;
+    const int runs_x = (nx + R - 1) / R;
+    const int lc = blockIdx.x;  // grid point within the chunk of runs
+    const int rl = lc / R;
+    const int run = run0 + rl;
+    const int y = run / runs_x;
+    const int x = (run - y * runs_x) * R + (lc - rl * R);
+    if (x >= nx) return;  // past the end of a ragged last run
+    const size_t cell = (size_t)y * nx + x;
+    const size_t plane = (size_t)nx * ny * k;
+    double* fc = f + cell * k;
+
+    for (int a = 0; a < 9; ++a) {
+        double s = 0.0;
+        for (int m = lane; m < k; m += 32) {
+            const double xv = fc[a * plane + m];
+            sm.dX[a * k + m] = xv;
+            s += xv;
+        }
+        const double mean = warp_sum(s) / k;
+        for (int m = lane; m < k; m += 32) sm.dX[a * k + m] -= mean;
+        if (lane == 0) sm.xbar[a] = mean;
+    }
+    const int* info = rinfo + (size_t)rl * info_stride;
+    const int nu = info[0];
+    if (nu < 0) return;  // reported by kernel J
+    if (nu == 0 || lamg[(size_t)lc * NS] == -1.0f) {
+        // No observation in range: x^a_m = xbar + sqrt(beta) dx_m.
+        __syncwarp();
+        const double sb = sqrt(beta);
+        for (int a = 0; a < 9; ++a)
+            for (int m = lane; m < k; m += 32) fc[a * plane + m] = sm.xbar[a] + sb * sm.dX[a * k + m];
+        return;
+    }
+    // The union's scalars with this point's weights (the FP64 operations of
+    // local_set; zero outside the support and on padding).
+    const double lim2 = (2.0 * d_cut + 1.0) * (2.0 * d_cut + 1.0);
+    for (int c = lane; c < NS; c += 32) {
+        int g = 0;
+        double w = 0.0;
+        if (c < nu) {
+            g = info[1 + c];
+            const int j = g / o.nvar;
+            const int dx = min_image(o.ix[j] - x, nx);
+            const int dy = min_image(o.iy[j] - y, ny);
+            const double d2 = (double)dx * dx + (double)dy * dy;
+            if (d2 <= lim2) {
+                const double dist = sqrt(d2) / d_cut;
+                if (dist < 2.0) {
+                    const double gc = gaspari_cohn(dist);
+                    const int q = g % o.nvar;
+                    if (gc > 0.0) w = sqrt(gc) / (q == 0 ? o.sigma_u : (q == 1 ? o.sigma_v : o.sigma_r));
+                }
+            }
+        }
+        sm.lidx[c] = g;
+        sm.lsq[c] = w;
+        sm.ldh[c] = c < nu ? w * o.d[g] : 0.0;
+    }
+    // Y (binary32 values, exact in FP64) into U.
+    const float* Yp = Yg + (size_t)lc * NS * NS;
+    for (int e = lane; e < NS * NS; e += 32) U[(e / NS) * ld + e % NS] = (double)Yp[e];
+    __syncwarp();
+    const int c = lane < NS ? lane : NS - 1;  // lanes past NS compute a copy and store nothing
+    // 1. E = Y^T Y - I (in A), then Y1 = Y (I - E/2) (in U).
+    {
+        double e[NS];
+#pragma unroll
+        for (int i = 0; i < NS; ++i) e[i] = 0.0;
+#pragma unroll 1
+        for (int j = 0; j < NS; ++j) {
+            const double yjc = U[j * ld + c];
+#pragma unroll
+            for (int i = 0; i < NS; ++i) e[i] += U[j * ld + i] * yjc;
+        }
+        if (lane < NS) {
+#pragma unroll
+            for (int i = 0; i < NS; ++i) A[i * ld + c] = e[i] - (i == c ? 1.0 : 0.0);
+        }
+    }
+    __syncwarp();
+    {
+        double col[NS];
+#pragma unroll
+        for (int i = 0; i < NS; ++i) col[i] = U[i * ld + c];
+#pragma unroll 1
+        for (int j = 0; j < NS; ++j) {
+            const double h = 0.5 * A[j * ld + c];
+#pragma unroll
+            for (int i = 0; i < NS; ++i) col[i] -= U[i * ld + j] * h;
+        }
+        __syncwarp();
+        if (lane < NS) {
+#pragma unroll
+            for (int i = 0; i < NS; ++i) U[i * ld + c] = col[i];
+        }
+    }
+    __syncwarp();
+    // A = Yh Yh^T from the global Gram (over E), as in the cold path.
+    for (int cc = lane; cc < NS; cc += 32) {
+        const int oc = sm.lidx[cc];
+        const double sc = sm.lsq[cc];
+        for (int i = 0; i < NS; ++i) A[i * ld + cc] = sm.lsq[i] * o.G[(size_t)sm.lidx[i] * (o.nvar * o.npts) + oc] * sc;
+    }
+    __syncwarp();
+    // 2. A' = Y1^T (A Y1), column c; then symmetrised.
+    {
+        double v[NS];
+#pragma unroll
+        for (int i = 0; i < NS; ++i) v[i] = 0.0;
+#pragma unroll 1
+        for (int j = 0; j < NS; ++j) {
+            const double ujc = U[j * ld + c];
+#pragma unroll
+            for (int i = 0; i < NS; ++i) v[i] += A[i * ld + j] * ujc;
+        }
+        __syncwarp();  // A is read by every lane above and rewritten below
+        for (int i = 0; i < NS; ++i) {
+            double s = 0.0;
+#pragma unroll
+            for (int j = 0; j < NS; ++j) s += U[j * ld + i] * v[j];
+            if (lane < NS) A[i * ld + c] = s;
+        }
+    }
+    __syncwarp();
+    if (lane < NS) {
+        for (int i = 0; i < c; ++i) {
+            const double m = 0.5 * (A[i * ld + c] + A[c * ld + i]);
+            A[i * ld + c] = m;
+            A[c * ld + i] = m;
+        }
+    }
+    __syncwarp();
+    // 3. FP64 Jacobi from A' with U = Y1.
+    const int sweeps = jacobi_sym_warp<double>(A, U, NS, ld, lane, sm.rc, sm.rs, sm.rp, sm.rq, 3e-8, kMaxSweeps);
+    if (sweeps < 0 && lane == 0) atomicOr(flags, FLAG_NOCONV);
+    record_sweeps(o, sweeps, lane);
+    __syncwarp();
+    // 4. Transform and update.
+    fp64_obs_update<NS>(sm, fc, plane, k, NS, (k - 1) / beta, beta, o, lane);
 }
 
 // ------------------------------------------------------------------ K3, mixed precision
@@ -1967,6 +2149,26 @@ __global__ void to_f32_kernel(const double* __restrict__ src, float* __restrict_
 }
 
 }  // namespace
+
+cudaError_t launch_run_fp64(double* f, int nx, int ny, int k, const ObsParams& o, double d_cut, double beta,
+                            int run_len, int run0, int nruns, int ns, const float* Yg, const float* lamg,
+                            const int* rinfo, int info_stride, int* flags, cudaStream_t s) {
+    auto go = [&](auto kern, size_t sh) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+        if (e != cudaSuccess) return e;
+        kern<<<(unsigned)((size_t)nruns * run_len), 32, sh, s>>>(f, nx, ny, k, o, d_cut, beta, run_len, run0, Yg,
+                                                                  lamg, rinfo, info_stride, flags);
+        return cudaGetLastError();
+    };
+    switch (ns) {
+        case 8: return go(run_fp64_kernel<8>, AnaSmem<8>::bytes(k, 8));
+        case 16: return go(run_fp64_kernel<16>, AnaSmem<16>::bytes(k, 16));
+        case 24: return go(run_fp64_kernel<24>, AnaSmem<24>::bytes(k, 24));
+        case 28: return go(run_fp64_kernel<28>, AnaSmem<28>::bytes(k, 28));
+        case 32: return go(run_fp64_kernel<32>, AnaSmem<32>::bytes(k, 32));
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 cudaError_t launch_observe(const void* f, int fp32, int nx, int ny, int k, int npts, int nvar,
                            const int* ix, const int* iy, const double* yo, double* dY, double* d,

@@ -55,16 +55,18 @@ namespace {
 constexpr int kRunSweeps = 30;  // sweep cap of one Jacobi
 
 struct RunArgs {
-    float* f;
+    float* f;           // binary32 state (null for a double-precision context)
+    double* f64;        // FP64 state of a double-precision context, else null
     int nx, ny, k, R;
     ObsParams o;
     const float2* G2;   // [nobs][nobs] G = dY dY^T as binary32 (hi, lo)
     double d_cut, beta;
     int* flags;
     int run0, nruns;    // runs of this chunk
-    float* Yg;          // [chunk cells][NS][NS] basis, row c = column c of Y
+    float* Yg;          // [chunk cells][NS][NS] basis Y, row-major (Y_ic: component i of vector c)
     float* lamg;        // [chunk cells][NS] eigenvalue estimates
     int* rinfo;         // [chunk runs][1 + 32] union size, then its scalars
+    int* fp64_hist;     // sweep histogram of the FP64 Jacobi (double precision), or null
 };
 
 __host__ __device__ inline int run_cell_floats(int ns) { return ns * ns + ns; }
@@ -1119,7 +1121,8 @@ cudaError_t launch_runs_ns(RunArgs ra, long long runs, long long chunk, const Pr
     const bool probe = pa.npoints > 0;
     cudaError_t e = cudaFuncSetAttribute(run_jacobi_kernel<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shJ);
     if (e != cudaSuccess) return e;
-    e = probe ? cudaFuncSetAttribute(run_refine_kernel<NS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shF)
+    if (!ra.f64)
+        e = probe ? cudaFuncSetAttribute(run_refine_kernel<NS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shF)
               : cudaFuncSetAttribute(run_refine_kernel<NS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shF);
     if (e != cudaSuccess) return e;
     for (long long r0 = 0; r0 < runs; r0 += chunk) {
@@ -1127,7 +1130,14 @@ cudaError_t launch_runs_ns(RunArgs ra, long long runs, long long chunk, const Pr
         ra.run0 = (int)r0;
         ra.nruns = (int)nr;
         run_jacobi_kernel<NS><<<(unsigned)nr, 32, shJ, s>>>(ra);
-        if (probe)
+        if (ra.f64) {
+            // Double-precision context: the FP64 Jacobi from J's basis.
+            ObsParams o = ra.o;
+            o.sweep_hist = ra.fp64_hist;
+            e = launch_run_fp64(ra.f64, ra.nx, ra.ny, ra.k, o, ra.d_cut, ra.beta, ra.R, ra.run0, ra.nruns, NS,
+                                ra.Yg, ra.lamg, ra.rinfo, kInfo, ra.flags, s);
+            if (e != cudaSuccess) return e;
+        } else if (probe)
             run_refine_kernel<NS, true><<<(unsigned)pa.npoints, 32, shF, s>>>(ra, pa);
         else
             run_refine_kernel<NS, false><<<(unsigned)(nr * ra.R), 32, shF, s>>>(ra, pa);
@@ -1135,10 +1145,13 @@ cudaError_t launch_runs_ns(RunArgs ra, long long runs, long long chunk, const Pr
     return cudaGetLastError();
 }
 
-cudaError_t launch_runs(float* f, int nx, int ny, int k, const ObsParams& o, double d_cut, double beta,
-                        int run_len, int maxunion, int* flags, void* scratch, const ProbeArgs& pa,
+cudaError_t launch_runs(float* f, double* f64, int nx, int ny, int k, const ObsParams& o, double d_cut,
+                        double beta, int run_len, int maxunion, int* flags, void* scratch, const ProbeArgs& pa,
                         cudaStream_t s) {
-    if (run_len < 1 || maxunion > kRunMaxUnion || !o.dY32 || !scratch) return cudaErrorInvalidValue;
+    if (run_len < 1 || maxunion > kRunMaxUnion || !scratch || (f == nullptr) == (f64 == nullptr))
+        return cudaErrorInvalidValue;
+    if (f && !o.dY32) return cudaErrorInvalidValue;
+    if (f64 && pa.npoints > 0) return cudaErrorInvalidValue;
     const int nobs = o.nvar * o.npts;
     const size_t ng = (size_t)nobs * nobs;
     const int ns = run_ns(maxunion);
@@ -1154,11 +1167,14 @@ cudaError_t launch_runs(float* f, int nx, int ny, int k, const ObsParams& o, dou
     p += ((size_t)chunk * run_len * ns * 4 + 255) / 256 * 256;
     int* rinfo = reinterpret_cast<int*>(p);
     // dY in binary32 for the transform (the same copy the chunked path makes).
-    cudaError_t e = launch_to_f32(o.dY, o.dY32, (size_t)nobs * k, s);
-    if (e != cudaSuccess) return e;
+    if (f) {
+        const cudaError_t e = launch_to_f32(o.dY, o.dY32, (size_t)nobs * k, s);
+        if (e != cudaSuccess) return e;
+    }
     split_gram_kernel<<<(unsigned)((ng + 255) / 256), 256, 0, s>>>(o.G, G2, ng);
     RunArgs ra;
     ra.f = f;
+    ra.f64 = f64;
     ra.nx = nx;
     ra.ny = ny;
     ra.k = k;
@@ -1173,6 +1189,12 @@ cudaError_t launch_runs(float* f, int nx, int ny, int k, const ObsParams& o, dou
     ra.Yg = Yg;
     ra.lamg = lamg;
     ra.rinfo = rinfo;
+    ra.fp64_hist = nullptr;
+    if (f64) {
+        // The histogram records the FP64 solve, not the binary32 start.
+        ra.fp64_hist = o.sweep_hist;
+        ra.o.sweep_hist = nullptr;
+    }
     switch (ns) {
         case 8: return launch_runs_ns<8>(ra, runs, chunk, pa, s);
         case 16: return launch_runs_ns<16>(ra, runs, chunk, pa, s);
@@ -1199,7 +1221,14 @@ cudaError_t launch_analyze_runs(float* f, int nx, int ny, int k, const ObsParams
                                 double beta, int run_len, int maxunion, int* flags, void* scratch,
                                 cudaStream_t s) {
     const ProbeArgs none{nullptr, 0, nullptr, nullptr};
-    return launch_runs(f, nx, ny, k, o, d_cut, beta, run_len, maxunion, flags, scratch, none, s);
+    return launch_runs(f, nullptr, nx, ny, k, o, d_cut, beta, run_len, maxunion, flags, scratch, none, s);
+}
+
+cudaError_t launch_analyze_runs_fp64(double* f, int nx, int ny, int k, const ObsParams& o, double d_cut,
+                                     double beta, int run_len, int maxunion, int* flags, void* scratch,
+                                     cudaStream_t s) {
+    const ProbeArgs none{nullptr, 0, nullptr, nullptr};
+    return launch_runs(nullptr, f, nx, ny, k, o, d_cut, beta, run_len, maxunion, flags, scratch, none, s);
 }
 
 size_t probe_work_bytes(int npoints, int maxunion, int k) {
@@ -1211,7 +1240,7 @@ cudaError_t launch_probe_runs(float* f, int nx, int ny, int k, const ObsParams& 
                               int npoints, double* T, double* work, cudaStream_t s) {
     if (npoints < 1 || !cells || !T || !work) return cudaErrorInvalidValue;
     const ProbeArgs pa{cells, npoints, T, work};
-    return launch_runs(f, nx, ny, k, o, d_cut, beta, run_len, maxunion, flags, scratch, pa, s);
+    return launch_runs(f, nullptr, nx, ny, k, o, d_cut, beta, run_len, maxunion, flags, scratch, pa, s);
 }
 
 }  // namespace lbmgpu

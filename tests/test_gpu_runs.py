@@ -1,4 +1,4 @@
-"""The mixed-precision analysis over runs of neighbouring grid points
+"""The analysis over runs of neighbouring grid points, mixed precision and FP64
 (warm-started binary32 Jacobi over the union of a run's local sets, Section
 3.2) against the FP64 oracle and against the chunked path (cold starts),
 through the C ABI."""
@@ -113,3 +113,69 @@ def test_run_length_argument(gpu):
         assert err.value.code == gpu.LBM_EINVAL
         e.set_run_length(0)
         e.set_run_length(16)
+
+
+# ---- double precision: the FP64 Jacobi warm-started from the run's basis --
+
+def _fp64(b, f, ix, iy, yu, yv, d_cut, beta, run_len, hist=False):
+    _, ny, nx, k = f.shape
+    with b.Ensemble(nx, ny, k, TAU0, CS, MU, b.LBM_FP64, f0=f) as e:
+        e.set_run_length(run_len)
+        if hist:
+            e.sweep_stats(True)
+        e.observe(ix, iy, yu, yv, SIGMA, SIGMA)
+        e.analyze(d_cut, beta)
+        out = e.get_f()
+        h = e.sweep_stats(False, read=True) if hist else None
+        e.sync()
+    return out, h
+
+
+@pytest.mark.parametrize("nx,ny,k,nox,noy,d_cut", CASES)
+@pytest.mark.parametrize("run_len", [1, 3, 8, 1000])
+def test_fp64_runs_match_oracle(gpu, nx, ny, k, nox, noy, d_cut, run_len):
+    f, ix, iy, yu, yv = _case(nx, ny, k, nox, noy, seed=nx + 3 * k)
+    got, _ = _fp64(gpu, f, ix, iy, yu, yv, d_cut, 1.05, run_len)
+    ref = oracle.letkf_analyze(f, ix, iy, yu, yv, SIGMA, SIGMA, d_cut, 1.05)
+    assert norm_rel(got, ref) <= 1e-12
+    assert norm_rel(ref, f) > 1e-6
+
+
+@pytest.mark.parametrize("nx,ny,k,nox,noy,d_cut", CASES)
+def test_fp64_runs_match_cold_path(gpu, nx, ny, k, nox, noy, d_cut):
+    f, ix, iy, yu, yv = _case(nx, ny, k, nox, noy, seed=nx + 4 * k)
+    runs, _ = _fp64(gpu, f, ix, iy, yu, yv, d_cut, 1.05, 8)
+    cold, _ = _fp64(gpu, f, ix, iy, yu, yv, d_cut, 1.05, 0)
+    assert norm_rel(runs, cold) <= 1e-13
+
+
+def test_fp64_warm_starts_take_fewer_sweeps(gpu):
+    """Paper-scale geometry: the FP64 Jacobi from the binary32 basis against
+    the cold FP64 Jacobi (sweeps counted up to and including the one that
+    finds convergence)."""
+    nx = ny = 256
+    k = 64
+    f, ix, iy, yu, yv = _case(nx, ny, k, 8, 8, seed=6, steps=1)
+    _, hw = _fp64(gpu, f, ix, iy, yu, yv, 32.0, 1.05, 8, hist=True)
+    _, hc = _fp64(gpu, f, ix, iy, yu, yv, 32.0, 1.05, 0, hist=True)
+    assert hw.sum() == hc.sum() == nx * ny
+    assert hw[31] == 0 and hc[31] == 0
+    meanw = (hw * np.arange(32)).sum() / hw.sum()
+    meanc = (hc * np.arange(32)).sum() / hc.sum()
+    assert meanw <= 3.0 and meanw < 0.5 * meanc
+
+
+def test_fp64_paper_scale_runs_sampled_points(gpu):
+    """256^2 x 64, 8 x 8 observation points, d_cut = 32, runs of 8, FP64:
+    sampled grid points against the oracle at the FP64 bound."""
+    nx = ny = 256
+    k = 64
+    f, ix, iy, yu, yv = _case(nx, ny, k, 8, 8, seed=29, steps=1)
+    got, _ = _fp64(gpu, f, ix, iy, yu, yv, 32.0, 1.05, 8)
+    rng = np.random.default_rng(2)
+    pts = np.unique(np.concatenate([rng.integers(0, nx * ny, 120),
+                                    [0, 7, 8, 255, 256 * 100 + 63, 256 * 100 + 64, nx * ny - 1]]))
+    ref = oracle.letkf_analyze(f, ix, iy, yu, yv, SIGMA, SIGMA, 32.0, 1.05, points=pts.astype(np.int32))
+    g = got.reshape(9, nx * ny, k)[:, pts]
+    r = ref.reshape(9, nx * ny, k)[:, pts]
+    assert norm_rel(g, r) <= 1e-12
