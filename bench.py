@@ -455,7 +455,16 @@ def measure_batch(cfg, cycles=3):
                            for n, k, no, dc in BATCH_EXPERIMENTS]}
     with binding.Batch(ens) as b:
         res["autotuned_threads"], res["autotuned_blocks"] = b.autotune()
+        # One plain cycle, then the run length per size class of the batched
+        # analyses, tuned on the next observations (states unchanged).
         c = 1
+        b.cycle(10, obs(c), dcs, betas, use_graph=False)
+        c += 1
+        b.forecast(10)
+        for e, o in zip(ens, obs(c)):
+            e.observe(*o)
+        c += 1
+        res["autotuned_run_len"] = b.autotune_analysis(dcs, betas)
         for _ in range(2):  # uncaptured first cycle, then capture
             b.cycle(10, obs(c), dcs, betas, use_graph=True)
             c += 1

@@ -355,10 +355,29 @@ int lbm_batch_forecast(lbm_batch *b, int nsteps);
  * Synchronises. */
 int lbm_batch_autotune(lbm_batch *b, int *threads, int *blocks);
 
+/* Pick the run length (grid points per warp, letkf_set_run_length) of the
+ * batch's analyses per size class: experiments whose analysis takes the
+ * run path (every grid point with p < members) are grouped by the union
+ * size of their runs (up to 8, 16, 24, 28, 32 scalars), and each class
+ * times its batched analysis (kernel J over every run of the class in one
+ * launch, kernel F over every grid point in one launch) at run lengths 4,
+ * 8, 16 and 32, best of three, keeping the fastest. The timed analyses
+ * work on copies of the current states in the spare buffers: states and
+ * observations are unchanged. Every context must be observed
+ * (letkf_observe) with the observations the analyses will use (d_cut[i],
+ * beta[i]). run_len[i] (may be NULL) receives each experiment's run length
+ * (unchanged for experiments off the run path). Synchronises; a captured
+ * cycle is captured again. */
+int lbm_batch_autotune_analysis(lbm_batch *b, const double *d_cut, const double *beta, int *run_len);
+
 /* One DA cycle of every experiment i: forecast nsteps (one persistent
  * launch for all), observe (u, v) at npts[i] points (ix[i], iy[i]) with
  * values yo_u[i], yo_v[i] and errors sigma[2i], sigma[2i+1], and the LETKF
- * analysis with d_cut[i], beta[i]. With use_graph, once a cycle has run
+ * analysis with d_cut[i], beta[i]. The analyses of experiments on the run
+ * path share launches: per size class one launch of kernel J over all
+ * their runs and one of kernel F over all their grid points (the analysis
+ * scratch of each is then sized for all its runs at once); the others are
+ * analysed one by one. With use_graph, once a cycle has run
  * uncaptured with the same positions, nsteps, d_cut and beta, the next call
  * captures the whole cycle of all experiments in a CUDA graph and later
  * calls replay it, staging only the new observed values through pinned

@@ -69,6 +69,7 @@ SIGNATURES = {
     "lbm_batch_create": (_I, [_P, _I, ctypes.POINTER(_P)]),
     "lbm_batch_forecast": (_I, [_P, _I]),
     "lbm_batch_autotune": (_I, [_P, _P, _P]),
+    "lbm_batch_autotune_analysis": (_I, [_P, _P, _P, _P]),
     "lbm_batch_cycle": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _P, _P, _I]),
     "lbm_batch_sync": (_I, [_P]),
     "lbm_batch_set_barrier": (_I, [_P, ctypes.c_longlong, _I]),
@@ -518,6 +519,19 @@ class Batch:
         t, n = ctypes.c_int(0), ctypes.c_int(0)
         _bcheck(self.b, load().lbm_batch_autotune(self.b, ctypes.byref(t), ctypes.byref(n)))
         return t.value, n.value
+
+    def autotune_analysis(self, d_cut, beta):
+        """Run length per size class of the batched run analyses; every
+        experiment must be observed. Returns each experiment's run length."""
+        n = len(self.ens)
+        dc = np.ascontiguousarray(d_cut, dtype=np.float64)
+        bt = np.ascontiguousarray(beta, dtype=np.float64)
+        if dc.shape != (n,) or bt.shape != (n,):
+            raise ValueError("d_cut and beta need one value per experiment")
+        out = np.zeros(n, dtype=np.int32)
+        p = lambda a: a.ctypes.data_as(_P)  # noqa: E731
+        _bcheck(self.b, load().lbm_batch_autotune_analysis(self.b, p(dc), p(bt), p(out)))
+        return out.tolist()
 
     def cycle(self, nsteps, obs, d_cut, beta, use_graph=True):
         """obs: per experiment (ix, iy, yo_u, yo_v, sigma_u, sigma_v)."""

@@ -143,7 +143,9 @@ cudaError_t launch_to_f32(const double* src, float* dst, size_t n, cudaStream_t 
 // per chunk of runs, every grid point's binary32 basis and eigenvalue
 // estimates (handed from the Jacobi kernel to the refinement kernel).
 constexpr int kRunMaxUnion = 32;
-size_t run_scratch_bytes(int nx, int ny, int nobs, int run_len, int maxunion);
+// whole: scratch for every run at once (the batched launch) rather than for
+// chunks of runs within a fixed budget.
+size_t run_scratch_bytes(int nx, int ny, int nobs, int run_len, int maxunion, bool whole = false);
 cudaError_t launch_analyze_runs(float* f, int nx, int ny, int k, const ObsParams& o, double d_cut,
                                 double beta, int run_len, int maxunion, int* flags, void* scratch,
                                 cudaStream_t s);
@@ -161,6 +163,21 @@ cudaError_t launch_analyze_runs_fp64(double* f, int nx, int ny, int k, const Obs
 cudaError_t launch_run_fp64(double* f, int nx, int ny, int k, const ObsParams& o, double d_cut, double beta,
                             int run_len, int run0, int nruns, int ns, const float* Yg, const float* lamg,
                             const int* rinfo, int info_stride, int* flags, cudaStream_t s);
+// The run analyses of several experiments (one lattice, state and
+// observation set each) in batched launches: kernel J over the runs of
+// every experiment of a size class in one launch, then kernel F over their
+// grid points in one launch (the FP64 kernel per experiment for FP64
+// states). Each item's scratch holds run_scratch_bytes(..., whole = true).
+struct RunItem {
+    float* f;      // binary32 state, or null
+    double* f64;   // FP64 state, or null
+    int nx, ny, k, run_len, maxunion;
+    ObsParams o;
+    double d_cut, beta;
+    int* flags;
+    void* scratch;
+};
+cudaError_t launch_analyze_runs_batch(const RunItem* items, int n, cudaStream_t s);
 // Diagnostic: the ensemble transform T = w-bar 1^T + W [npoints][k][k]
 // (FP64) that the run analysis' refined representation gives at the listed
 // grid points cells[npoints] (device), evaluated in FP64; f is not

@@ -511,7 +511,9 @@ struct AnalysisPlan {
     int run_len = 0, maxunion = 0;  // run_len > 0: the run analysis
 };
 
-int analyze_prepare(lbm_ctx* c, double d_cut, double beta, AnalysisPlan* plan) {
+// whole: size the run analysis' scratch for every run at once (batched
+// launches) instead of chunks within a fixed budget.
+int analyze_prepare(lbm_ctx* c, double d_cut, double beta, AnalysisPlan* plan, bool whole = false) {
     if (c->k < 2) return fail(c, LBM_EINVAL, "the analysis needs members >= 2");
     if (!(d_cut > 0.0) || !std::isfinite(d_cut)) return fail(c, LBM_EINVAL, "d_cut must be > 0");
     if (!(beta > 0.0) || !std::isfinite(beta)) return fail(c, LBM_EINVAL, "beta must be > 0");
@@ -527,7 +529,7 @@ int analyze_prepare(lbm_ctx* c, double d_cut, double beta, AnalysisPlan* plan) {
         maxunion = largest_run_union(c, d_cut, c->run_len);
         if (maxunion <= kRunMaxUnion) run_len = c->run_len;
     }
-    const size_t scratch = run_len > 0 ? run_scratch_bytes(c->nx, c->ny, c->nvar * c->npts, run_len, maxunion)
+    const size_t scratch = run_len > 0 ? run_scratch_bytes(c->nx, c->ny, c->nvar * c->npts, run_len, maxunion, whole)
                                        : analyze_scratch_bytes(c->nx, c->ny, is_fp32(c), plmax, nmax, c->k, prod);
     if (scratch > c->ana_scratch_bytes) {
         CK(c, cudaStreamSynchronize(c->stream), "synchronising");
@@ -550,10 +552,15 @@ int analyze_prepare(lbm_ctx* c, double d_cut, double beta, AnalysisPlan* plan) {
     return LBM_OK;
 }
 
+ObsParams obs_params(lbm_ctx* c, const AnalysisPlan& pl) {
+    return ObsParams{c->npts, c->ix,    c->iy,   c->dY,       c->d,
+                     c->G,    c->sigma_u, c->sigma_v, c->dY32, c->nvar,
+                     c->sigma_r, pl.plmax, c->sweep_stats ? c->sweep_hist : nullptr};
+}
+
 // Device part: the analysis kernels on the context stream (capturable).
 int analyze_launch(lbm_ctx* c, const AnalysisPlan& pl) {
-    ObsParams o{c->npts, c->ix, c->iy, c->dY, c->d, c->G, c->sigma_u, c->sigma_v, c->dY32,
-                c->nvar, c->sigma_r, pl.plmax, c->sweep_stats ? c->sweep_hist : nullptr};
+    const ObsParams o = obs_params(c, pl);
     if (pl.run_len > 0) {
         if (is_fp32(c))
             CK(c, launch_analyze_runs((float*)c->f[c->cur], c->nx, c->ny, c->k, o, pl.d_cut, pl.beta, pl.run_len,
@@ -1146,6 +1153,40 @@ int batch_forecast_impl(lbm_batch* b, int nsteps) {
     return LBM_OK;
 }
 
+// The analyses of a batch on stream s: every experiment on the run path in
+// batched launches (kernel J over all their runs, then kernel F over all
+// their grid points, per size class), the others one by one. The plans
+// come from analyze_prepare(..., whole = true).
+int batch_analyze(lbm_batch* b, const std::vector<AnalysisPlan>& plans, const std::vector<int>& which,
+                  cudaStream_t s) {
+    std::vector<RunItem> items;
+    for (int i : which) {
+        lbm_ctx* c = b->ctx[i];
+        const AnalysisPlan& pl = plans[i];
+        if (pl.run_len > 0) {
+            const bool f32 = is_fp32(c);
+            items.push_back(RunItem{f32 ? (float*)c->f[c->cur] : nullptr, f32 ? nullptr : (double*)c->f[c->cur],
+                                    c->nx, c->ny, c->k, pl.run_len, pl.maxunion, obs_params(c, pl), pl.d_cut,
+                                    pl.beta, c->flags, c->ana_scratch});
+        } else {
+            const cudaStream_t own = c->stream;
+            c->stream = s;
+            const int st = analyze_launch(c, pl);
+            c->stream = own;
+            if (st) return bfail(b, st, "experiment %d: %s", i, c->err);
+        }
+    }
+    if (!items.empty())
+        BK(b, launch_analyze_runs_batch(items.data(), (int)items.size(), s), "launching batched run analysis");
+    return LBM_OK;
+}
+
+std::vector<int> all_experiments(const lbm_batch* b) {
+    std::vector<int> v(b->ctx.size());
+    for (size_t i = 0; i < v.size(); ++i) v[i] = (int)i;
+    return v;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1251,6 +1292,99 @@ int lbm_batch_autotune(lbm_batch* b, int* threads, int* blocks) {
     return LBM_OK;
 }
 
+int lbm_batch_autotune_analysis(lbm_batch* b, const double* d_cut, const double* beta, int* run_len) {
+    if (!b) return bfail(nullptr, LBM_EINVAL, "batch is NULL");
+    if (!d_cut || !beta) return bfail(b, LBM_EINVAL, "NULL argument");
+    const int n = (int)b->ctx.size();
+    for (int i = 0; i < n; ++i)
+        if (!b->ctx[i]->observed)
+            return bfail(b, LBM_EINVAL, "experiment %d: letkf_observe must precede the analysis autotuning", i);
+    // Size classes: the run analysis' union size class at the default run
+    // length; experiments off the run path (ensemble-space points) are not
+    // tuned.
+    std::vector<int> cls(n, -1);
+    for (int i = 0; i < n; ++i) {
+        lbm_ctx* c = b->ctx[i];
+        if (!(d_cut[i] > 0.0) || !std::isfinite(d_cut[i]) || !(beta[i] > 0.0) || !std::isfinite(beta[i]))
+            return bfail(b, LBM_EINVAL, "experiment %d: d_cut and beta must be finite and > 0", i);
+        largest_local_problem(c, d_cut[i]);
+        if (c->geo_any_ens) continue;
+        const int u = largest_run_union(c, d_cut[i], 8);
+        if (u <= kRunMaxUnion) cls[i] = u <= 8 ? 8 : (u <= 16 ? 16 : (u <= 24 ? 24 : (u <= 28 ? 28 : 32)));
+    }
+    const int cand[] = {4, 8, 16, 32};
+    cudaEvent_t t0, t1;
+    BK(b, cudaEventCreate(&t0), "creating event");
+    BK(b, cudaEventCreate(&t1), "creating event");
+    int st = LBM_OK;
+    std::vector<int> done(n, 0);
+    for (int i0 = 0; i0 < n && st == LBM_OK; ++i0) {
+        if (cls[i0] < 0 || done[i0]) continue;
+        std::vector<int> which;
+        for (int i = i0; i < n; ++i)
+            if (cls[i] == cls[i0]) {
+                which.push_back(i);
+                done[i] = 1;
+            }
+        float best = 1e30f;
+        int best_r = b->ctx[which[0]]->run_len;
+        for (int r : cand) {
+            // Each timing analyses copies of the current states in the spare
+            // buffers; the states and the observations are not changed.
+            std::vector<AnalysisPlan> plans(n);
+            for (int i : which) {
+                lbm_ctx* c = b->ctx[i];
+                c->run_len = r;
+                st = analyze_prepare(c, d_cut[i], beta[i], &plans[i], true);
+                if (st) break;
+            }
+            if (st) break;
+            float tbest = 1e30f;
+            for (int rep = 0; rep < 3 && st == LBM_OK; ++rep) {
+                for (int i : which) {
+                    lbm_ctx* c = b->ctx[i];
+                    const size_t bytes = (size_t)9 * c->nx * c->ny * c->k * (is_fp32(c) ? 4 : 8);
+                    if (cudaMemcpyAsync(c->f[1 - c->cur], c->f[c->cur], bytes, cudaMemcpyDeviceToDevice, b->stream) !=
+                        cudaSuccess)
+                        st = bfail(b, LBM_ECUDA, "copying a state for the autotuning");
+                    c->cur ^= 1;
+                }
+                cudaEventRecord(t0, b->stream);
+                if (st == LBM_OK) st = batch_analyze(b, plans, which, b->stream);
+                cudaEventRecord(t1, b->stream);
+                for (int i : which) b->ctx[i]->cur ^= 1;
+                if (st == LBM_OK && cudaEventSynchronize(t1) != cudaSuccess)
+                    st = bfail(b, LBM_ECUDA, "autotuning the analysis");
+                float ms = 0.f;
+                if (st == LBM_OK) cudaEventElapsedTime(&ms, t0, t1);
+                if (ms < tbest) tbest = ms;
+            }
+            if (st) break;
+            if (tbest < best) {
+                best = tbest;
+                best_r = r;
+            }
+        }
+        for (int i : which) b->ctx[i]->run_len = best_r;
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    if (st) return st;
+    // A captured cycle holds the old shapes: capture again on the next cycle.
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    if (b->graph) {
+        cudaGraphDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    b->graph_steps = -1;
+    if (run_len)
+        for (int i = 0; i < n; ++i) run_len[i] = b->ctx[i]->run_len;
+    return LBM_OK;
+}
+
 int lbm_batch_cycle(lbm_batch* b, int nsteps, const int* npts, const int* const* ix, const int* const* iy,
                     const double* const* yo_u, const double* const* yo_v, const double* sigma,
                     const double* d_cut, const double* beta, int use_graph) {
@@ -1295,12 +1429,18 @@ int lbm_batch_cycle(lbm_batch* b, int nsteps, const int* npts, const int* const*
         }
         int st = batch_forecast_impl(b, nsteps);
         if (st) return st;
+        std::vector<AnalysisPlan> plans(n);
         for (int i = 0; i < n; ++i) {
             lbm_ctx* c = b->ctx[i];
             st = letkf_observe(c, npts[i], ix[i], iy[i], yo_u[i], yo_v[i], sigma[2 * i], sigma[2 * i + 1]);
             if (st) return bfail(b, st, "experiment %d: %s", i, c->err);
-            st = letkf_analyze(c, d_cut[i], beta[i]);
+            st = analyze_prepare(c, d_cut[i], beta[i], &plans[i], true);
             if (st) return bfail(b, st, "experiment %d: %s", i, c->err);
+        }
+        st = batch_analyze(b, plans, all_experiments(b), b->stream);
+        if (st) return st;
+        for (int i = 0; i < n; ++i) {
+            b->ctx[i]->observed = false;
             if (npts[i] > b->npts[i]) {
                 if (b->h_yo[i]) cudaFreeHost(b->h_yo[i]);
                 b->h_yo[i] = nullptr;
@@ -1331,7 +1471,7 @@ int lbm_batch_cycle(lbm_batch* b, int nsteps, const int* npts, const int* const*
         std::vector<AnalysisPlan> plans(n);
         for (int i = 0; i < n; ++i) {
             lbm_ctx* c = b->ctx[i];
-            int st = analyze_prepare(c, d_cut[i], beta[i], &plans[i]);
+            int st = analyze_prepare(c, d_cut[i], beta[i], &plans[i], true);
             if (st) return bfail(b, st, "experiment %d: %s", i, c->err);
         }
         batch_table(b);
@@ -1349,10 +1489,8 @@ int lbm_batch_cycle(lbm_batch* b, int nsteps, const int* npts, const int* const*
         cudaError_t e = launch_lbm_multi(b->ex_dev, n, b->total, nsteps, b->fp32, b->blocks, b->threads, b->bar,
                                          b->status, b->spin_limit, b->absent, b->cap);
         int st = e == cudaSuccess ? LBM_OK : LBM_ECUDA;
-        for (int i = 0; i < n && st == LBM_OK; ++i) {
-            st = observe_from_pinned(b->ctx[i], b->h_yo[i]);
-            if (st == LBM_OK) st = analyze_launch(b->ctx[i], plans[i]);
-        }
+        for (int i = 0; i < n && st == LBM_OK; ++i) st = observe_from_pinned(b->ctx[i], b->h_yo[i]);
+        if (st == LBM_OK) st = batch_analyze(b, plans, all_experiments(b), b->cap);
         cudaGraph_t g = nullptr;
         const cudaError_t ee = cudaStreamEndCapture(b->cap, &g);
         for (lbm_ctx* c : b->ctx) c->stream = shared;

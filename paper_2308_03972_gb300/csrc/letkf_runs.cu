@@ -43,8 +43,10 @@
 // (C = aI + Yh^T Yh, a = (k-1)/beta) the update is
 //   x^a_m = xbar + Z v + sqrt(beta) dx_m + sqrt(k-1) Z g(A) yh_m,
 //   Z = dX Yh^T, v = (aI+A)^{-1} d-hat.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <vector>
 
 #include "lbm_internal.cuh"
 #include "letkf_device.cuh"
@@ -326,7 +328,7 @@ struct JLayout {
 };
 
 template <int NS>
-__global__ void __launch_bounds__(32, 16) run_jacobi_kernel(RunArgs ra) {
+__device__ __forceinline__ void run_jacobi_body(const RunArgs& ra, int blk) {
     extern __shared__ __align__(16) float smj[];
     using L = JLayout<NS>;
     int* const pts = reinterpret_cast<int*>(smj);
@@ -336,7 +338,7 @@ __global__ void __launch_bounds__(32, 16) run_jacobi_kernel(RunArgs ra) {
     float* const Us = smj + L::Us;
     float* const Vs = smj + L::Vs;
     const int lane = threadIdx.x;
-    const int rl = blockIdx.x;  // run within the chunk
+    const int rl = blk;  // run within the chunk
     const int run = ra.run0 + rl;
     const int runs_x = (ra.nx + ra.R - 1) / ra.R;
     const int y = run / runs_x;
@@ -585,7 +587,7 @@ __device__ void probe_tail(const RunArgs& ra, const ProbeArgs& pa, int pt, const
                            double hh, int lane);
 
 template <int NS, bool PROBE>
-__global__ void __launch_bounds__(32, 12) run_refine_kernel(RunArgs ra, ProbeArgs pa) {
+__device__ __forceinline__ void run_refine_body(const RunArgs& ra, const ProbeArgs& pa, int blk) {
     extern __shared__ __align__(16) float smf[];
     using L = FLayout<NS>;
     float* const Ah = smf + L::Ah;
@@ -615,7 +617,7 @@ __global__ void __launch_bounds__(32, 12) run_refine_kernel(RunArgs ra, ProbeArg
     int lc, rl, x, y;
     if (PROBE) {
         // Block b takes listed point b if its run is in this chunk.
-        const int cl = pa.cells[blockIdx.x];
+        const int cl = pa.cells[blk];
         y = cl / ra.nx;
         x = cl - y * ra.nx;
         const int run = y * runs_x + x / ra.R;
@@ -623,7 +625,7 @@ __global__ void __launch_bounds__(32, 12) run_refine_kernel(RunArgs ra, ProbeArg
         rl = run - ra.run0;
         lc = rl * ra.R + (x - (x / ra.R) * ra.R);
     } else {
-        lc = blockIdx.x;  // cell within the chunk
+        lc = blk;  // cell within the chunk
         rl = lc / ra.R;
         const int run = ra.run0 + rl;
         y = run / runs_x;
@@ -639,7 +641,7 @@ __global__ void __launch_bounds__(32, 12) run_refine_kernel(RunArgs ra, ProbeArg
     if (nu < 0) return;  // reported by kernel J
     if (PROBE && (nu == 0 || lam_mark == -1.0f)) {
         // No observation in range: T = sqrt(beta) I.
-        double* Tp = pa.T + (size_t)blockIdx.x * k * k;
+        double* Tp = pa.T + (size_t)blk * k * k;
         for (int e = lane; e < k * k; e += 32) Tp[e] = (e / k == e % k) ? sqrt(ra.beta) : 0.0;
         return;
     }
@@ -804,7 +806,7 @@ __global__ void __launch_bounds__(32, 12) run_refine_kernel(RunArgs ra, ProbeArg
     const double hh = 1.0 / (aa + dS);
     if constexpr (PROBE) {
         __syncwarp();
-        probe_tail<NS>(ra, pa, blockIdx.x, Ys, Ah, Al, lsq, gi, nu, uu, alpha, hh, lane);
+        probe_tail<NS>(ra, pa, blk, Ys, Ah, Al, lsq, gi, nu, uu, alpha, hh, lane);
         return;
     }
     float t1c = 0.0f;
@@ -1085,6 +1087,50 @@ __device__ void probe_tail(const RunArgs& ra, const ProbeArgs& pa, int pt, const
         }
 }
 
+// ---- kernels: one experiment, or a batch of experiments ------------------
+// A batch launch covers the runs (kernel J) or grid points (kernel F) of up
+// to kRunBatch experiments of one size class (NS): block b belongs to the
+// experiment e with start[e] <= b < start[e + 1]. The table travels as a
+// kernel parameter.
+constexpr int kRunBatch = 16;
+
+struct RunBatch {
+    int n;
+    int jstart[kRunBatch + 1];  // first run of each experiment
+    int fstart[kRunBatch + 1];  // first grid point of each experiment
+    RunArgs ex[kRunBatch];
+};
+
+__device__ __forceinline__ int batch_item(const int* start, int n, int blk) {
+    int e = 0;
+    while (e + 1 < n && blk >= start[e + 1]) ++e;
+    return e;
+}
+
+template <int NS>
+__global__ void __launch_bounds__(32, 16) run_jacobi_kernel(const __grid_constant__ RunArgs ra) {
+    run_jacobi_body<NS>(ra, blockIdx.x);
+}
+
+template <int NS>
+__global__ void __launch_bounds__(32, 16) run_jacobi_batch_kernel(const __grid_constant__ RunBatch tb) {
+    const int e = batch_item(tb.jstart, tb.n, blockIdx.x);
+    run_jacobi_body<NS>(tb.ex[e], blockIdx.x - tb.jstart[e]);
+}
+
+template <int NS, bool PROBE>
+__global__ void __launch_bounds__(32, 12) run_refine_kernel(const __grid_constant__ RunArgs ra,
+                                                            const __grid_constant__ ProbeArgs pa) {
+    run_refine_body<NS, PROBE>(ra, pa, blockIdx.x);
+}
+
+template <int NS>
+__global__ void __launch_bounds__(32, 12) run_refine_batch_kernel(const __grid_constant__ RunBatch tb) {
+    const int e = batch_item(tb.fstart, tb.n, blockIdx.x);
+    const ProbeArgs none{nullptr, 0, nullptr, nullptr};
+    run_refine_body<NS, false>(tb.ex[e], none, blockIdx.x - tb.fstart[e]);
+}
+
 // G = dY dY^T split into binary32 (hi, lo).
 __global__ void split_gram_kernel(const double* __restrict__ G, float2* __restrict__ G2, size_t n) {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1145,19 +1191,19 @@ cudaError_t launch_runs_ns(RunArgs ra, long long runs, long long chunk, const Pr
     return cudaGetLastError();
 }
 
-cudaError_t launch_runs(float* f, double* f64, int nx, int ny, int k, const ObsParams& o, double d_cut,
-                        double beta, int run_len, int maxunion, int* flags, void* scratch, const ProbeArgs& pa,
-                        cudaStream_t s) {
+// Run arguments of one analysis: the scratch laid out for `chunk` runs per
+// pass (G2, then the basis, eigenvalue estimates and union lists of a
+// chunk), and the preparation kernels queued (the binary32 copy of dY for a
+// binary32 state, the split Gram).
+cudaError_t run_setup(float* f, double* f64, int nx, int ny, int k, const ObsParams& o, double d_cut, double beta,
+                      int run_len, int maxunion, int* flags, void* scratch, long long chunk, RunArgs& ra,
+                      cudaStream_t s) {
     if (run_len < 1 || maxunion > kRunMaxUnion || !scratch || (f == nullptr) == (f64 == nullptr))
         return cudaErrorInvalidValue;
     if (f && !o.dY32) return cudaErrorInvalidValue;
-    if (f64 && pa.npoints > 0) return cudaErrorInvalidValue;
     const int nobs = o.nvar * o.npts;
     const size_t ng = (size_t)nobs * nobs;
     const int ns = run_ns(maxunion);
-    const long long runs = (long long)ny * ((nx + run_len - 1) / run_len);
-    if (runs > 0x7fffffffLL / run_len) return cudaErrorInvalidConfiguration;
-    const long long chunk = run_chunk_runs(runs, run_len, ns);
     unsigned char* p = reinterpret_cast<unsigned char*>(scratch);
     float2* G2 = reinterpret_cast<float2*>(p);
     p += (ng * sizeof(float2) + 255) / 256 * 256;
@@ -1172,7 +1218,6 @@ cudaError_t launch_runs(float* f, double* f64, int nx, int ny, int k, const ObsP
         if (e != cudaSuccess) return e;
     }
     split_gram_kernel<<<(unsigned)((ng + 255) / 256), 256, 0, s>>>(o.G, G2, ng);
-    RunArgs ra;
     ra.f = f;
     ra.f64 = f64;
     ra.nx = nx;
@@ -1195,6 +1240,23 @@ cudaError_t launch_runs(float* f, double* f64, int nx, int ny, int k, const ObsP
         ra.fp64_hist = o.sweep_hist;
         ra.o.sweep_hist = nullptr;
     }
+    return cudaGetLastError();
+}
+
+long long run_count(int nx, int ny, int run_len) { return (long long)ny * ((nx + run_len - 1) / run_len); }
+
+cudaError_t launch_runs(float* f, double* f64, int nx, int ny, int k, const ObsParams& o, double d_cut,
+                        double beta, int run_len, int maxunion, int* flags, void* scratch, const ProbeArgs& pa,
+                        cudaStream_t s) {
+    if (f64 && pa.npoints > 0) return cudaErrorInvalidValue;
+    if (run_len < 1) return cudaErrorInvalidValue;
+    const int ns = run_ns(maxunion);
+    const long long runs = run_count(nx, ny, run_len);
+    if (runs > 0x7fffffffLL / run_len) return cudaErrorInvalidConfiguration;
+    const long long chunk = run_chunk_runs(runs, run_len, ns);
+    RunArgs ra;
+    const cudaError_t e = run_setup(f, f64, nx, ny, k, o, d_cut, beta, run_len, maxunion, flags, scratch, chunk, ra, s);
+    if (e != cudaSuccess) return e;
     switch (ns) {
         case 8: return launch_runs_ns<8>(ra, runs, chunk, pa, s);
         case 16: return launch_runs_ns<16>(ra, runs, chunk, pa, s);
@@ -1204,12 +1266,63 @@ cudaError_t launch_runs(float* f, double* f64, int nx, int ny, int k, const ObsP
     }
 }
 
+// One size class of a batch: kernel J over every run of the experiments,
+// then kernel F over every grid point (binary32 states) or the FP64
+// kernel per experiment (FP64 states), in launches of kRunBatch
+// experiments.
+template <int NS>
+cudaError_t launch_runs_batch_ns(const std::vector<RunArgs>& ex, cudaStream_t s) {
+    const size_t shJ = (size_t)JLayout<NS>::total * 4;
+    int kmax = 0;
+    for (const RunArgs& ra : ex) kmax = ra.k > kmax ? ra.k : kmax;
+    const size_t shF = run_f_smem_bytes<NS>(kmax);
+    cudaError_t e = cudaFuncSetAttribute(run_jacobi_batch_kernel<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)shJ);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(run_refine_batch_kernel<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shF);
+    if (e != cudaSuccess) return e;
+    for (size_t i0 = 0; i0 < ex.size(); i0 += kRunBatch) {
+        const int n = (int)std::min<size_t>(kRunBatch, ex.size() - i0);
+        RunBatch tb{};
+        tb.n = n;
+        long long jt = 0, ft = 0;
+        bool fp64 = false;
+        for (int i = 0; i < n; ++i) {
+            tb.ex[i] = ex[i0 + i];
+            tb.jstart[i] = (int)jt;
+            tb.fstart[i] = (int)ft;
+            jt += tb.ex[i].nruns;
+            ft += (long long)tb.ex[i].nruns * tb.ex[i].R;
+            fp64 = fp64 || tb.ex[i].f64;
+            if (ft > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+        }
+        tb.jstart[n] = (int)jt;
+        tb.fstart[n] = (int)ft;
+        run_jacobi_batch_kernel<NS><<<(unsigned)jt, 32, shJ, s>>>(tb);
+        if (!fp64) {
+            run_refine_batch_kernel<NS><<<(unsigned)ft, 32, shF, s>>>(tb);
+        } else {
+            for (int i = 0; i < n; ++i) {
+                const RunArgs& ra = tb.ex[i];
+                ObsParams o = ra.o;
+                o.sweep_hist = ra.fp64_hist;
+                e = launch_run_fp64(ra.f64, ra.nx, ra.ny, ra.k, o, ra.d_cut, ra.beta, ra.R, 0, ra.nruns, NS, ra.Yg,
+                                    ra.lamg, ra.rinfo, kInfo, ra.flags, s);
+                if (e != cudaSuccess) return e;
+            }
+        }
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 }  // namespace
 
-size_t run_scratch_bytes(int nx, int ny, int nobs, int run_len, int maxunion) {
+size_t run_scratch_bytes(int nx, int ny, int nobs, int run_len, int maxunion, bool whole) {
     const int ns = run_ns(maxunion);
-    const long long runs = (long long)ny * ((nx + run_len - 1) / run_len);
-    const long long chunk = run_chunk_runs(runs, run_len, ns);
+    const long long runs = run_count(nx, ny, run_len);
+    const long long chunk = whole ? runs : run_chunk_runs(runs, run_len, ns);
     const size_t g2 = ((size_t)nobs * nobs * sizeof(float2) + 255) / 256 * 256;
     const size_t yb = ((size_t)chunk * run_len * ns * ns * 4 + 255) / 256 * 256;
     const size_t lb = ((size_t)chunk * run_len * ns * 4 + 255) / 256 * 256;
@@ -1241,6 +1354,34 @@ cudaError_t launch_probe_runs(float* f, int nx, int ny, int k, const ObsParams& 
     if (npoints < 1 || !cells || !T || !work) return cudaErrorInvalidValue;
     const ProbeArgs pa{cells, npoints, T, work};
     return launch_runs(f, nullptr, nx, ny, k, o, d_cut, beta, run_len, maxunion, flags, scratch, pa, s);
+}
+
+cudaError_t launch_analyze_runs_batch(const RunItem* items, int n, cudaStream_t s) {
+    // Preparation per experiment (scratch for every run at once), then one
+    // size class after another.
+    std::vector<RunArgs> cls[5];
+    const int sizes[5] = {8, 16, 24, 28, 32};
+    for (int i = 0; i < n; ++i) {
+        const RunItem& it = items[i];
+        if (it.run_len < 1) return cudaErrorInvalidValue;
+        const long long runs = run_count(it.nx, it.ny, it.run_len);
+        if (runs > 0x7fffffffLL / it.run_len) return cudaErrorInvalidConfiguration;
+        RunArgs ra;
+        const cudaError_t e = run_setup(it.f, it.f64, it.nx, it.ny, it.k, it.o, it.d_cut, it.beta, it.run_len,
+                                        it.maxunion, it.flags, it.scratch, runs, ra, s);
+        if (e != cudaSuccess) return e;
+        ra.nruns = (int)runs;
+        const int ns = run_ns(it.maxunion);
+        for (int c = 0; c < 5; ++c)
+            if (ns == sizes[c]) cls[c].push_back(ra);
+    }
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess && !cls[0].empty()) e = launch_runs_batch_ns<8>(cls[0], s);
+    if (e == cudaSuccess && !cls[1].empty()) e = launch_runs_batch_ns<16>(cls[1], s);
+    if (e == cudaSuccess && !cls[2].empty()) e = launch_runs_batch_ns<24>(cls[2], s);
+    if (e == cudaSuccess && !cls[3].empty()) e = launch_runs_batch_ns<28>(cls[3], s);
+    if (e == cudaSuccess && !cls[4].empty()) e = launch_runs_batch_ns<32>(cls[4], s);
+    return e;
 }
 
 }  // namespace lbmgpu

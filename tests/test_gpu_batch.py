@@ -247,3 +247,78 @@ def test_twelve_experiments_match_oracle_at_sampled_points(gpu, prec):
         assert norm_rel(got, ref.reshape(9, n * n, k)[:, pts]) <= tol, "experiment %d" % i
         e.close()
         f.close()
+
+
+def test_analysis_autotuner_keeps_states_and_cycles_match(gpu):
+    """lbm_batch_autotune_analysis: run lengths per size class timed on
+    copies of the states (the states are unchanged), then batch cycles with
+    the chosen run lengths equal to single-context cycles with the same
+    run lengths, bit for bit (same kernels)."""
+    picks = [(128, 64, 8, 16.0), (128, 128, 8, 16.0), (256, 32, 8, 32.0), (128, 16, 8, 16.0)]
+    made, obs = [], []
+    for i, (n, k, no, dc) in enumerate(picks):
+        u, v = inputs.ensemble_velocity(n, n, k, 80 + i, U_RMS, 0.2)
+        force = inputs.forcing_field(n, n, seed=90 + i, amp=3.5e-6)
+        ix, iy = inputs.uniform_obs_points(n, n, no, no)
+        tu, tv = inputs.random_velocity(n, n, 100 + i, U_RMS)
+        made.append((n, k, u, v, force))
+        obs.append((ix, iy, tu, tv))
+    dcs = [p[3] for p in picks]
+    betas = [1.05] * len(picks)
+
+    def cycle_obs(c):
+        out = []
+        for ix, iy, tu, tv in obs:
+            nu, nv = inputs.obs_noise(4, c, len(ix))
+            out.append((ix, iy, tu[iy, ix] + SIGMA * nu, tv[iy, ix] + SIGMA * nv, SIGMA, SIGMA))
+        return out
+
+    def build():
+        out = []
+        for n, k, u, v, force in made:
+            e = gpu.Ensemble(n, n, k, TAU0, CS, MU, gpu.LBM_MIXED, force=force)
+            e.set_equilibrium(None, u, v)
+            out.append(e)
+        return out
+
+    ens = build()
+    with gpu.Batch(ens) as b:
+        b.forecast(10)
+        for e, o in zip(ens, cycle_obs(1)):
+            e.observe(*o)
+        before = [e.get_f() for e in ens]
+        rl = b.autotune_analysis(dcs, betas)
+        for e, f0 in zip(ens, before):
+            assert np.array_equal(e.get_f(), f0)
+        # The first three take the run path; 16 members with 8 x 8 points
+        # has ensemble-space points, so its run length is not tuned.
+        assert all(r in (4, 8, 16, 32) for r in rl[:3])
+        assert rl[3] == 8
+        for c in (2, 3):
+            b.cycle(10, cycle_obs(c), dcs, betas, use_graph=True)
+        b.sync()
+    ref = build()
+    for e, r in zip(ref, rl):
+        e.set_run_length(r)
+        e.forecast(10)
+    for c in (2, 3):
+        for e, o, dc in zip(ref, cycle_obs(c), dcs):
+            e.forecast(10)
+            e.observe(*o)
+            e.analyze(dc, 1.05)
+    for e, r in zip(ens, ref):
+        assert np.array_equal(e.get_f(), r.get_f())
+        e.close()
+        r.close()
+
+
+def test_analysis_autotuner_needs_observations(gpu):
+    ens = [gpu.Ensemble(16, 16, 8, TAU0, CS, MU, gpu.LBM_MIXED) for _ in range(2)]
+    with gpu.Batch(ens) as b:
+        with pytest.raises(gpu.LbmError) as err:
+            b.autotune_analysis([4.0, 4.0], [1.05, 1.05])
+        assert err.value.code == gpu.LBM_EINVAL
+        with pytest.raises(ValueError):
+            b.autotune_analysis([4.0], [1.05])
+    for e in ens:
+        e.close()
