@@ -363,12 +363,13 @@ def measure_adjoint(cfg, reps=3, nsteps=200, ckpt=20):
             "achieved_gbs": byts / (ms * 1e6)}
 
 
-def measure_sweep(cfg, reps=2):
+def measure_sweep(cfg, reps=2, only=None):
     """Analysis time of the precision sweep at 256^2 (binary32 LBM state):
     k in {16, 32, 64, 128}, observation lattices 8^2 .. 64^2, d_cut = 32 and
     d_cut = the observation spacing, Gram/b products FP64 / binary32 / TF32 /
     BF16. Every case fits the mixed path (n = min(k, p) <= 128); one above
-    it would be listed as refused."""
+    it would be listed as refused. only = (k, obs side, d_cut) restricts the
+    sweep to that case."""
     import torch
 
     from paper_2308_03972_gb300 import binding, inputs
@@ -381,6 +382,8 @@ def measure_sweep(cfg, reps=2):
              ("tf32", binding.LBM_PROD_TF32), ("bf16", binding.LBM_PROD_BF16))
     out = []
     for k in (16, 32, 64, 128):
+        if only and k != only[0]:
+            continue
         eu, ev = inputs.ensemble_velocity(nx, ny, k, cfg.seeds["ensemble"], cfg.u_rms, cfg.ens_pert)
         ens = binding.Ensemble(nx, ny, k, cfg.tau0, cfg.cs_smag, cfg.mu, binding.LBM_MIXED, force=force)
         ens.set_equilibrium(None, eu, ev)
@@ -390,6 +393,8 @@ def measure_sweep(cfg, reps=2):
             nu, nv = inputs.obs_noise(cfg.seeds["noise"], 1, len(ix))
             yu, yv = tu[iy, ix] + cfg.sigma * nu, tv[iy, ix] + cfg.sigma * nv
             for d_cut in sorted({32.0, float(nx // no)}):
+                if only and (no != only[1] or d_cut != only[2]):
+                    continue
                 row = {"k": k, "obs": "%dx%d" % (no, no), "d_cut": d_cut}
                 for name, mode in modes:
                     ens.set_products(mode)
@@ -635,6 +640,8 @@ def main():
                     help="grid points per run of the mixed analysis (0: the chunked path)")
     ap.add_argument("--window", type=int, default=200, help="adjoint window steps (--case adjoint)")
     ap.add_argument("--checkpoint", type=int, default=20, help="adjoint checkpoint spacing (--case adjoint)")
+    ap.add_argument("--sweep-only", default=None,
+                    help="k:obs:d_cut, one case of the precision sweep (--case sweep)")
     ap.add_argument("--case", default="all", choices=["all", "cycle", "adjoint", "sweep", "batch", "osse"],
                     help="cycle: the headline line without the adjoint, batch and OSSE legs; adjoint: only "
                          "the adjoint-window leg; sweep: precision-sweep timings; batch: twelve uneven "
@@ -668,7 +675,11 @@ def main():
             print(json.dumps({"case": "batch", **res}))
         return
     if args.case == "sweep":
-        for row in measure_sweep(cfg):
+        only = None
+        if args.sweep_only:
+            kk, no, dc = args.sweep_only.split(":")
+            only = (int(kk), int(no), float(dc))
+        for row in measure_sweep(cfg, only=only):
             if rank == 0:
                 print(json.dumps({"case": "sweep", **row}))
         return

@@ -174,8 +174,14 @@ int letkf_observe_rho(lbm_ctx *ctx, int npts, const int *ix, const int *iy,
  * ensemble-space form (p >= k) of a mixed-precision context's analysis:
  *   LBM_PROD_FP64  FP64 products and sums (default);
  *   LBM_PROD_FP32  binary32 products, binary32 accumulation (CUDA cores);
- *   LBM_PROD_TF32  TF32 products on the tensor cores, binary32 accumulation;
- *   LBM_PROD_BF16  BF16 products on the tensor cores, binary32 accumulation.
+ *   LBM_PROD_TF32  TF32 products on the tcgen05 tensor cores, binary32
+ *                  accumulation in tensor memory (rows staged by TMA);
+ *   LBM_PROD_BF16  BF16 products, likewise.
+ * A bounded wait of the tensor-core pass that runs out is reported by the
+ * next synchronising call as LBM_ECUDA. The merged observation list of
+ * eight neighbouring grid points must fit shared memory with the operand
+ * tiles (about 30,000 observation points); beyond it the launch fails with
+ * LBM_ECUDA.
  * The eigensolve stays FP64-accurate in every mode; the reduced modes apply
  * for members <= 128 (larger ensembles keep FP64). LBM_EINVAL for an unknown
  * mode or a reduced mode on an FP64 context. Applies to later analyses. */

@@ -11,7 +11,8 @@ namespace lbmgpu {
 enum : int {
     FLAG_DIVERGED = 1,  // non-finite or |u| above the limit
     FLAG_NOCONV = 2,    // eigensolver sweep cap reached
-    FLAG_TOOLARGE = 4   // local problem larger than the analysis kernel holds
+    FLAG_TOOLARGE = 4,  // local problem larger than the analysis kernel holds
+    FLAG_TCWAIT = 8     // a bounded wait of the tensor-core Gram ran out
 };
 
 // Arithmetic of the local Gram matrix C = a I + Yh^T Yh and b = Yh^T d-hat in

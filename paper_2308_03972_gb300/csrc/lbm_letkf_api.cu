@@ -121,6 +121,8 @@ int read_flags(lbm_ctx* c) {
         return fail(c, LBM_EDIVERGED, "state diverged: non-finite density/velocity or |u| > 0.5");
     if (h & FLAG_TOOLARGE)
         return fail(c, LBM_EINVAL, "local analysis problem larger than the kernel supports (n = min(k, p) > 64 in FP64, > 128 in mixed precision)");
+    if (h & FLAG_TCWAIT)
+        return fail(c, LBM_ECUDA, "a bounded wait of the tensor-core Gram ran out (its analysis is incomplete)");
     return fail(c, LBM_ENOCONV, "eigensolver reached its sweep cap");
 }
 

@@ -22,11 +22,14 @@
 // matrix held in shared memory, one column per lane.
 #include <cmath>
 #include <cstdint>
+#include <cstring>
 
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
 
 #include "lbm_internal.cuh"
 #include "letkf_device.cuh"
+#include "tc_ptx.cuh"
 
 namespace lbmgpu {
 namespace {
@@ -1163,8 +1166,9 @@ __host__ __device__ inline size_t mix_buf_bytes(long long chunk, int nobs, int n
 // ---- Local Gram matrices in reduced precision (ensemble-space form) --------
 // C = a I + Yh^T Yh and b = Yh^T d-hat for every grid point of a chunk, with
 // Yh = diag(sqrt(rho)) dY_loc (Section 3.2), from the binary32 copy of dY:
-// PROD_FP32 on the CUDA cores, PROD_TF32 (mma m16n8k8) and PROD_BF16 (mma
-// m16n8k16) on the tensor cores, all accumulating in binary32. A block takes
+// PROD_FP32 on the CUDA cores (local_gram_kernel), PROD_TF32 and PROD_BF16
+// on the tcgen05 tensor cores (local_gram_tc_kernel), all accumulating in
+// binary32. A block takes
 // kGramPts consecutive grid points, one warp each; their local sets are
 // merged into one list of observation points, whose rows are staged once per
 // block in shared memory and weighted per point (rows outside a point's set
@@ -1172,33 +1176,9 @@ __host__ __device__ inline size_t mix_buf_bytes(long long chunk, int nobs, int n
 // set uses, rounded to binary32.
 constexpr int kGramPts = 8;
 
-__device__ __forceinline__ uint32_t to_tf32(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
-}
-
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<const uint32_t*>(&v);
-}
-
-__device__ __forceinline__ void mma_tf32(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2,
-                                         uint32_t a3, uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-        "{%8,%9}, {%0,%1,%2,%3};"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-__device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2,
-                                         uint32_t a3, uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-        "{%8,%9}, {%0,%1,%2,%3};"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
 // sqrt(G(r / d_cut)) of observation point j seen from (x, y), 0 outside the
@@ -1257,18 +1237,19 @@ __device__ int gram_merge(const ObsParams& o, int nx, int ny, double d_cut, int 
     return total;
 }
 
-template <int MODE, int K>
+// PROD_FP32: binary32 products and sums on the CUDA cores. Warp w is grid
+// point w of the block; lane c owns output columns c (and c + 32 at 64
+// members); at 128 members the columns go in passes of 32 so that the
+// accumulators stay at 128 per lane.
+template <int K>
 __global__ void __launch_bounds__(32 * kGramPts, 1) local_gram_kernel(int nx, int ny, int k,
                                                                      ObsParams o, double d_cut,
                                                                      double aa, int cell0,
                                                                      int ncell, MixScratch sc) {
-    constexpr int KC = MODE == PROD_TF32 ? 8 : 16;        // rows per stage
-    constexpr int LD = MODE == PROD_TF32 ? K + 8 : K + 4;  // conflict-free fragment reads
-    // Output columns per pass over the rows: all of them up to 64 members;
-    // 32 per pass at 128, so that the accumulators stay at 128 per lane.
-    constexpr int KB = K > 64 ? 32 : K;
-    constexpr int MT = K / 16, NT = KB / 8;
-    constexpr int NCOL = KB > 32 ? 2 : 1;  // output columns per lane and pass (FP32 path)
+    constexpr int KC = 16;     // rows per stage
+    constexpr int LD = K + 4;
+    constexpr int KB = K > 64 ? 32 : K;       // output columns per pass over the rows
+    constexpr int NCOL = KB > 32 ? 2 : 1;     // output columns per lane and pass
     constexpr int NBC = K > 32 ? K / 32 : 1;  // entries of b per lane
     __shared__ float Ys[KC][LD];
     __shared__ float Ws[kGramPts][KC];  // rho-tilde = (sqrt(G) / sigma)^2 per point and row
@@ -1279,7 +1260,6 @@ __global__ void __launch_bounds__(32 * kGramPts, 1) local_gram_kernel(int nx, in
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int li0 = blockIdx.x * kGramPts;
     const int nv = o.nvar;
-    const double sig[3] = {o.sigma_u, o.sigma_v, o.sigma_r};
 
     const int total = gram_merge(o, nx, ny, d_cut, cell0, li0, ncell, U, pcnt, wcount);
     // Only grid points in the ensemble-space form (p >= k) read C and b.
@@ -1287,29 +1267,18 @@ __global__ void __launch_bounds__(32 * kGramPts, 1) local_gram_kernel(int nx, in
     for (int q = 0; q < kGramPts; ++q) any_ens |= pcnt[q] * nv >= k;
     if (!any_ens) return;
     const int rows = total * nv;
-    const int g = lane >> 2, t = lane & 3;
     const int li = li0 + w;
     float* C = sc.C32 + (size_t)li * k * k;
     const float fa = (float)aa;
-    float acc[MODE == PROD_FP32 ? 1 : MT][MODE == PROD_FP32 ? 1 : NT][4];
-    float accf[MODE == PROD_FP32 ? K : 1][NCOL];
+    float accf[K][NCOL];
     float bacc[NBC];
 #pragma unroll
     for (int c = 0; c < NBC; ++c) bacc[c] = 0.0f;
     for (int cb = 0; cb < K; cb += KB) {  // first column of this pass
-        if constexpr (MODE == PROD_FP32) {
 #pragma unroll
-            for (int m = 0; m < K; ++m)
+        for (int m = 0; m < K; ++m)
 #pragma unroll
-                for (int c = 0; c < NCOL; ++c) accf[m][c] = 0.0f;
-        } else {
-#pragma unroll
-            for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-                for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) acc[mt][nt][i] = 0.0f;
-        }
+            for (int c = 0; c < NCOL; ++c) accf[m][c] = 0.0f;
         for (int r0 = 0; r0 < rows; r0 += KC) {
             for (int e = threadIdx.x; e < KC * K; e += 32 * kGramPts) {
                 const int rr = e / K, c = e % K, r = r0 + rr;
@@ -1323,7 +1292,8 @@ __global__ void __launch_bounds__(32 * kGramPts, 1) local_gram_kernel(int nx, in
                 if (r < rows && li0 + q < ncell) {
                     const int cell = cell0 + li0 + q;
                     const double sg = local_weight(o, U[r / nv], cell % nx, cell / nx, nx, ny, d_cut);
-                    const double l = sg / sig[r % nv];
+                    const int qv = r % nv;
+                    const double l = sg / (qv == 0 ? o.sigma_u : (qv == 1 ? o.sigma_v : o.sigma_r));
                     wv = (float)(l * l);
                 }
                 Ws[q][rr] = wv;
@@ -1333,102 +1303,324 @@ __global__ void __launch_bounds__(32 * kGramPts, 1) local_gram_kernel(int nx, in
                 Ds[threadIdx.x] = r < rows ? (float)o.d[nv * U[r / nv] + r % nv] : 0.0f;
             }
             __syncthreads();
-            if constexpr (MODE == PROD_FP32) {
-                for (int rr = 0; rr < KC; ++rr) {
-                    const float wl = Ws[w][rr];
-                    if (wl == 0.0f) continue;
-                    float yc[NCOL];
+            for (int rr = 0; rr < KC; ++rr) {
+                const float wl = Ws[w][rr];
+                if (wl == 0.0f) continue;
+                float yc[NCOL];
 #pragma unroll
-                    for (int c = 0; c < NCOL; ++c) yc[c] = (lane + 32 * c < KB) ? Ys[rr][cb + lane + 32 * c] : 0.0f;
-                    if (cb == 0) {
-#pragma unroll
-                        for (int c = 0; c < NBC; ++c)
-                            bacc[c] += wl * Ds[rr] * ((lane + 32 * c < K) ? Ys[rr][lane + 32 * c] : 0.0f);
-                    }
-#pragma unroll
-                    for (int m = 0; m < K; ++m) {
-                        const float ym = wl * Ys[rr][m];
-#pragma unroll
-                        for (int c = 0; c < NCOL; ++c) accf[m][c] += ym * yc[c];
-                    }
-                }
-            } else {
+                for (int c = 0; c < NCOL; ++c) yc[c] = (lane + 32 * c < KB) ? Ys[rr][cb + lane + 32 * c] : 0.0f;
                 if (cb == 0) {
 #pragma unroll
-                    for (int rr = 0; rr < KC; ++rr) {
-                        const float wl = Ws[w][rr];
-#pragma unroll
-                        for (int c = 0; c < NBC; ++c)
-                            if (lane + 32 * c < K) bacc[c] += wl * Ds[rr] * Ys[rr][lane + 32 * c];
-                    }
+                    for (int c = 0; c < NBC; ++c)
+                        bacc[c] += wl * Ds[rr] * ((lane + 32 * c < K) ? Ys[rr][lane + 32 * c] : 0.0f);
                 }
-                if constexpr (MODE == PROD_TF32) {
-                    const float wa = Ws[w][t], wb = Ws[w][t + 4];
-                    uint32_t bf[NT][2];
 #pragma unroll
-                    for (int nt = 0; nt < NT; ++nt) {
-                        bf[nt][0] = to_tf32(Ys[t][cb + 8 * nt + g]);
-                        bf[nt][1] = to_tf32(Ys[t + 4][cb + 8 * nt + g]);
-                    }
+                for (int m = 0; m < K; ++m) {
+                    const float ym = wl * Ys[rr][m];
 #pragma unroll
-                    for (int mt = 0; mt < MT; ++mt) {
-                        const uint32_t a0 = to_tf32(wa * Ys[t][16 * mt + g]);
-                        const uint32_t a1 = to_tf32(wa * Ys[t][16 * mt + g + 8]);
-                        const uint32_t a2 = to_tf32(wb * Ys[t + 4][16 * mt + g]);
-                        const uint32_t a3 = to_tf32(wb * Ys[t + 4][16 * mt + g + 8]);
-#pragma unroll
-                        for (int nt = 0; nt < NT; ++nt) mma_tf32(acc[mt][nt], a0, a1, a2, a3, bf[nt][0], bf[nt][1]);
-                    }
-                } else {
-                    const int r0a = 2 * t, r1a = 2 * t + 1, r0b = 2 * t + 8, r1b = 2 * t + 9;
-                    const float w0 = Ws[w][r0a], w1 = Ws[w][r1a], w8 = Ws[w][r0b], w9 = Ws[w][r1b];
-                    uint32_t bf[NT][2];
-#pragma unroll
-                    for (int nt = 0; nt < NT; ++nt) {
-                        bf[nt][0] = pack_bf16(Ys[r0a][cb + 8 * nt + g], Ys[r1a][cb + 8 * nt + g]);
-                        bf[nt][1] = pack_bf16(Ys[r0b][cb + 8 * nt + g], Ys[r1b][cb + 8 * nt + g]);
-                    }
-#pragma unroll
-                    for (int mt = 0; mt < MT; ++mt) {
-                        const int m0 = 16 * mt + g, m1 = m0 + 8;
-                        const uint32_t a0 = pack_bf16(w0 * Ys[r0a][m0], w1 * Ys[r1a][m0]);
-                        const uint32_t a1 = pack_bf16(w0 * Ys[r0a][m1], w1 * Ys[r1a][m1]);
-                        const uint32_t a2 = pack_bf16(w8 * Ys[r0b][m0], w9 * Ys[r1b][m0]);
-                        const uint32_t a3 = pack_bf16(w8 * Ys[r0b][m1], w9 * Ys[r1b][m1]);
-#pragma unroll
-                        for (int nt = 0; nt < NT; ++nt) mma_bf16(acc[mt][nt], a0, a1, a2, a3, bf[nt][0], bf[nt][1]);
-                    }
+                    for (int c = 0; c < NCOL; ++c) accf[m][c] += ym * yc[c];
                 }
             }
             __syncthreads();
         }
         if (li < ncell) {
-            if constexpr (MODE == PROD_FP32) {
 #pragma unroll
-                for (int m = 0; m < K; ++m)
+            for (int m = 0; m < K; ++m)
 #pragma unroll
-                    for (int c = 0; c < NCOL; ++c) {
-                        const int n = cb + lane + 32 * c;
-                        if (m < k && n < k && lane + 32 * c < KB) C[m * k + n] = accf[m][c] + (m == n ? fa : 0.0f);
-                    }
-            } else {
-#pragma unroll
-                for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-                    for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            const int m = 16 * mt + g + (i >= 2 ? 8 : 0);
-                            const int n = cb + 8 * nt + 2 * t + (i & 1);
-                            if (m < k && n < k) C[m * k + n] = acc[mt][nt][i] + (m == n ? fa : 0.0f);
-                        }
-            }
+                for (int c = 0; c < NCOL; ++c) {
+                    const int n = cb + lane + 32 * c;
+                    if (m < k && n < k && lane + 32 * c < KB) C[m * k + n] = accf[m][c] + (m == n ? fa : 0.0f);
+                }
         }
     }  // passes over the output columns
     if (li >= ncell) return;
 #pragma unroll
     for (int c = 0; c < NBC; ++c)
         if (lane + 32 * c < k) sc.b32[(size_t)li * k + lane + 32 * c] = bacc[c];
+}
+
+// ---- reduced-precision Gram on the tcgen05 tensor cores ------------------
+// The same C = a I + sum_r rho_q(r) y_r y_r^T per grid point q of a block of
+// kGramPts points (Section 3.2's Yh^T Yh in the ensemble-space form), with
+// TF32 or BF16 products and FP32 accumulation in tensor memory. One
+// tcgen05.mma computes D[128 x KP] += A[128 x Kmma] B[Kmma x KP] (K = the
+// rows r of the block's merged local set):
+//   B[n][r] = y_r[n]                 (n < k, zero up to KP)
+//   A[p KP + m][r] = rho_q(r) y_r[m]  (the 128 / KP points q of one group
+//                                      stacked along M; zero for m >= k)
+// so D row p KP + m, column n is C_q[m][n] - a. Both operands are K-major
+// in the no-swizzle core-matrix layout (8 rows x 16 bytes per core matrix,
+// LBO = 128 bytes between core matrices along K, SBO between 8-row groups).
+// Per stage of 32 rows: TMA brings each row of the merged set (a one-row
+// box of the binary32 copy of dY, gathered through the merged index list)
+// into a 128-byte aligned row of shared memory; the block weights, rounds and lays out A and B; one
+// thread issues the MMAs and commits them to an mbarrier; the next stage
+// waits for them before rewriting the operands. The accumulators are read
+// back with tcgen05.ld. b = Yh^T d-hat stays on the CUDA cores. Every wait
+// is bounded: on a timeout the block records FLAG_TCWAIT, waits (bounded)
+// for its MMAs in flight, frees its tensor memory and returns.
+constexpr int kTcKC = 32;  // rows (K) per stage
+
+template <bool TF32, int KP>
+struct TcGram {
+    static constexpr int ES = TF32 ? 4 : 2;                  // operand element bytes
+    static constexpr int T = 16 / ES;                        // elements per 16-byte core-matrix row
+    static constexpr int KCOL = kTcKC * ES / 16;             // core matrices along K per stage
+    static constexpr int SBO = KCOL * 128;                   // bytes between 8-row groups
+    static constexpr int PG = 128 / KP;                      // points per MMA group
+    static constexpr int G = KP == 128 ? 4 : kGramPts / PG;  // groups per pass
+    static constexpr int PASSES = KP == 128 ? 2 : 1;
+    static constexpr int PPP = G * PG;                       // points per pass
+    static constexpr int KMMA = TF32 ? 8 : 16;               // K of one MMA (32 bytes)
+    static constexpr int NCOLS = G * KP < 32 ? 32 : G * KP;  // TMEM columns
+    static constexpr int A_BYTES = 128 * kTcKC * ES;         // one group's A per stage
+    static constexpr int B_BYTES = KP * kTcKC * ES;
+    static constexpr int oA = 0;
+    static constexpr int oB = oA + G * A_BYTES;
+    static constexpr int SP = KP < 32 ? 32 : KP;             // staged row pitch (floats): 128-byte rows
+    static constexpr int oS = oB + B_BYTES;                  // staged rows [KC][SP] binary32
+    static constexpr int oW = oS + kTcKC * SP * 4;           // rho [kGramPts][KC]
+    static constexpr int oD = oW + kGramPts * kTcKC * 4;     // innovations [KC]
+    static constexpr int oBar = oD + kTcKC * 4;              // mbarriers: TMA, MMA
+    static constexpr int oTm = oBar + 16;                    // TMEM base address
+    static constexpr int oU = oTm + 16;                      // merged list [npts]
+    static_assert(PPP * PASSES == kGramPts, "every point of the block in one pass");
+    static_assert(NCOLS == 32 || NCOLS == 64 || NCOLS == 128 || NCOLS == 256 || NCOLS == 512,
+                  "TMEM columns");
+    static_assert(oS % 128 == 0 && (SP * 4) % 128 == 0 && (oU % 16) == 0, "TMA destinations on 128 bytes");
+};
+
+__device__ __forceinline__ uint32_t tf32_bits(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+// One 16-byte core-matrix row from T binary32 values, rounded.
+template <bool TF32>
+__device__ __forceinline__ void store_core_row(unsigned char* dst, const float* v) {
+    uint4 u;
+    if constexpr (TF32) {
+        u = make_uint4(tf32_bits(v[0]), tf32_bits(v[1]), tf32_bits(v[2]), tf32_bits(v[3]));
+    } else {
+        u = make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
+    }
+    *reinterpret_cast<uint4*>(dst) = u;
+}
+
+constexpr long long kTcWaitPolls = 1ll << 22;  // polls of ~50 ns: a few tenths of a second
+
+template <bool TF32, int KP>
+__global__ void __launch_bounds__(32 * kGramPts, 1)
+    local_gram_tc_kernel(int nx, int ny, int k, ObsParams o, double d_cut, double aa, int cell0, int ncell,
+                         MixScratch sc, const __grid_constant__ CUtensorMap ymap, int use_tma, int* flags) {
+    using L = TcGram<TF32, KP>;
+    extern __shared__ unsigned char tc_raw[];
+    // 1024-byte aligned base (the launch adds the slack).
+    unsigned char* tsm = tc_raw + ((1024u - (smem_u32(tc_raw) & 1023u)) & 1023u);
+    unsigned char* Aop = tsm + L::oA;
+    unsigned char* Bop = tsm + L::oB;
+    float* Sg = reinterpret_cast<float*>(tsm + L::oS);
+    float* Ws = reinterpret_cast<float*>(tsm + L::oW);
+    float* Ds = reinterpret_cast<float*>(tsm + L::oD);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(tsm + L::oBar);
+    uint32_t* tbase = reinterpret_cast<uint32_t*>(tsm + L::oTm);
+    int* U = reinterpret_cast<int*>(tsm + L::oU);
+    __shared__ int wcount[kGramPts];
+    __shared__ int pcnt[kGramPts];
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    const int li0 = blockIdx.x * kGramPts;
+    const int nv = o.nvar;
+
+    const int total = gram_merge(o, nx, ny, d_cut, cell0, li0, ncell, U, pcnt, wcount);
+    // Only grid points in the ensemble-space form (p >= k) read C and b.
+    bool any_ens = false;
+    for (int q = 0; q < kGramPts; ++q) any_ens |= pcnt[q] * nv >= k;
+    if (!any_ens) return;
+    const int rows = total * nv;
+    const int nst = (rows + kTcKC - 1) / kTcKC;
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        mbar_fence_init();
+    }
+    if (w == 0) {
+        tmem_alloc(tbase, L::NCOLS);
+        tmem_relinquish();
+    }
+    tc_fence_before_sync();
+    __syncthreads();
+    tc_fence_after_sync();
+    const uint32_t tmem = *tbase;
+    constexpr uint32_t idesc = umma_idesc(TF32 ? 2u : 1u, 128, KP);
+    constexpr int NBC = KP > 32 ? KP / 32 : 1;
+    float bacc[NBC];
+#pragma unroll
+    for (int c = 0; c < NBC; ++c) bacc[c] = 0.0f;
+    bool ok = true;
+    uint32_t tphase = 0, mphase = 0;  // parity of the next phase to wait for
+    bool mma_pending = false, tma_pending = false;
+    for (int pass = 0; pass < L::PASSES && ok; ++pass) {
+        const int q0 = pass * L::PPP;
+        for (int s = 0; s < nst && ok; ++s) {
+            const int r0 = s * kTcKC;
+            const int nr = rows - r0 < kTcKC ? rows - r0 : kTcKC;
+            // Stage rows r0 .. r0 + nr - 1 of the merged set.
+            if (use_tma) {
+                if (tid == 0) {
+                    mbar_arrive_expect_tx(&bars[0], (uint32_t)(nr * k * 4));
+                    for (int rr = 0; rr < nr; ++rr) {
+                        const int r = r0 + rr;
+                        tma_load_2d(Sg + rr * L::SP, &ymap, 0, nv * U[r / nv] + r % nv, &bars[0]);
+                    }
+                }
+                tma_pending = true;
+            } else {
+                for (int e = tid; e < nr * k; e += 32 * kGramPts) {
+                    const int rr = e / k, c = e - rr * k, r = r0 + rr;
+                    Sg[rr * L::SP + c] = o.dY32[(size_t)(nv * U[r / nv] + r % nv) * k + c];
+                }
+            }
+            // rho of every point for the stage's rows, and the innovations.
+            if (tid < kTcKC * kGramPts) {
+                const int q = tid / kTcKC, rr = tid % kTcKC, r = r0 + rr;
+                float wv = 0.0f;
+                if (rr < nr && li0 + q < ncell) {
+                    const int cell = cell0 + li0 + q;
+                    const double sg = local_weight(o, U[r / nv], cell % nx, cell / nx, nx, ny, d_cut);
+                    const int qv = r % nv;
+                    const double l = sg / (qv == 0 ? o.sigma_u : (qv == 1 ? o.sigma_v : o.sigma_r));
+                    wv = (float)(l * l);
+                }
+                Ws[q * kTcKC + rr] = wv;
+            }
+            if (tid < kTcKC) {
+                const int r = r0 + tid;
+                Ds[tid] = tid < nr ? (float)o.d[nv * U[r / nv] + r % nv] : 0.0f;
+            }
+            if (tma_pending) {
+                ok = mbar_wait(&bars[0], tphase, kTcWaitPolls);
+                tphase ^= 1u;
+                tma_pending = !ok;
+            }
+            // The previous stage's MMAs read the operands being rewritten.
+            if (mma_pending && ok) {
+                ok = mbar_wait(&bars[1], mphase, kTcWaitPolls);
+                mphase ^= 1u;
+                mma_pending = !ok;
+            }
+            ok = __syncthreads_and(ok) != 0;
+            if (!ok) break;
+            // B[n][rr] = y_rr[n].
+            for (int e = tid; e < KP * L::KCOL; e += 32 * kGramPts) {
+                const int n = e / L::KCOL, kc = e - n * L::KCOL;
+                float v[L::T];
+#pragma unroll
+                for (int t = 0; t < L::T; ++t) {
+                    const int rr = kc * L::T + t;
+                    v[t] = (n < k && rr < nr) ? Sg[rr * L::SP + n] : 0.0f;
+                }
+                store_core_row<TF32>(Bop + (n >> 3) * L::SBO + kc * 128 + (n & 7) * 16, v);
+            }
+            // A_g[p KP + m][rr] = rho_q(rr) y_rr[m], q = q0 + g PG + p.
+            for (int e = tid; e < L::G * 128 * L::KCOL; e += 32 * kGramPts) {
+                const int g = e / (128 * L::KCOL);
+                const int rem = e - g * 128 * L::KCOL;
+                const int R = rem / L::KCOL, kc = rem - R * L::KCOL;
+                const int p = R / KP, m = R - p * KP, q = q0 + g * L::PG + p;
+                float v[L::T];
+#pragma unroll
+                for (int t = 0; t < L::T; ++t) {
+                    const int rr = kc * L::T + t;
+                    v[t] = (m < k && rr < nr) ? Ws[q * kTcKC + rr] * Sg[rr * L::SP + m] : 0.0f;
+                }
+                store_core_row<TF32>(Aop + g * L::A_BYTES + (R >> 3) * L::SBO + kc * 128 + (R & 7) * 16, v);
+            }
+            // b = Yh^T d-hat on the CUDA cores (first pass; warp w is point w).
+            if (pass == 0) {
+                for (int rr = 0; rr < nr; ++rr) {
+                    const float wd = Ws[w * kTcKC + rr] * Ds[rr];
+#pragma unroll
+                    for (int c = 0; c < NBC; ++c)
+                        if (lane + 32 * c < k) bacc[c] += wd * Sg[rr * L::SP + lane + 32 * c];
+                }
+            }
+            fence_async_smem();
+            tc_fence_before_sync();
+            __syncthreads();
+            if (tid == 0) {
+                tc_fence_after_sync();
+                const uint32_t a0 = smem_u32(Aop), b0 = smem_u32(Bop);
+#pragma unroll
+                for (int j = 0; j < kTcKC / L::KMMA; ++j) {
+                    const uint64_t bd = umma_smem_desc(b0 + j * 256, 128, L::SBO);
+#pragma unroll
+                    for (int g = 0; g < L::G; ++g) {
+                        const uint64_t ad = umma_smem_desc(a0 + g * L::A_BYTES + j * 256, 128, L::SBO);
+                        umma<TF32>(tmem + (uint32_t)(g * KP), ad, bd, idesc, (s > 0 || j > 0) ? 1u : 0u);
+                    }
+                }
+                umma_commit(&bars[1]);
+            }
+            mma_pending = true;
+        }
+        if (!ok) break;
+        ok = mbar_wait(&bars[1], mphase, kTcWaitPolls);
+        mphase ^= 1u;
+        mma_pending = !ok;
+        ok = __syncthreads_and(ok) != 0;
+        if (!ok) break;
+        tc_fence_after_sync();
+        // Epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows of D)
+        // of the groups g with g % 2 == w / 4.
+        {
+            const int quarter = w & 3;
+            const int R = 32 * quarter + lane;
+            const int p = R / KP, m = R - p * KP;
+            for (int g = w >> 2; g < L::G; g += 2) {
+                const int li = li0 + q0 + g * L::PG + p;
+                for (int c0 = 0; c0 < KP; c0 += 16) {
+                    float v[16];
+                    tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(g * KP + c0), v);
+                    if (li < ncell && m < k) {
+                        float* C = sc.C32 + (size_t)li * k * k + (size_t)m * k;
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) {
+                            const int n = c0 + i;
+                            if (n < k) C[n] = v[i] + (m == n ? (float)aa : 0.0f);
+                        }
+                    }
+                }
+            }
+        }
+        tc_fence_before_sync();
+        __syncthreads();  // the next pass overwrites the accumulators
+        tc_fence_after_sync();
+    }
+    if (!ok) {
+        // A wait ran out: record it, then let the copies and MMAs this block
+        // issued finish (bounded) before its tensor memory is freed.
+        if (tid == 0) atomicOr(flags, FLAG_TCWAIT);
+        if (tma_pending) mbar_wait(&bars[0], tphase, kTcWaitPolls);
+        if (mma_pending) mbar_wait(&bars[1], mphase, kTcWaitPolls);
+    }
+    tc_fence_before_sync();
+    __syncthreads();
+    if (w == 0) {
+        tc_fence_after_sync();
+        tmem_dealloc(tmem, L::NCOLS);
+    }
+    if (!ok) return;
+    const int li = li0 + w;
+    if (li >= ncell) return;
+#pragma unroll
+    for (int c = 0; c < NBC; ++c)
+        if (lane + 32 * c < k) sc.b32[(size_t)li * k + lane + 32 * c] = bacc[c];
+}
+
+template <bool TF32, int KP>
+size_t tc_gram_smem(int npts) {
+    return (size_t)TcGram<TF32, KP>::oU + (size_t)(npts > 0 ? npts : 1) * sizeof(int) + 1024;
 }
 
 // FP64 Gram (PROD_FP64): the same C and b in FP64 products and sums, from
@@ -2227,19 +2419,75 @@ static cudaError_t launch_gram_mode(int nx, int ny, int k, const ObsParams& o, d
         if (k <= 64) return go(local_gram_fp64_kernel<64>);
         return go(local_gram_fp64_kernel<128>);
     } else {
-        if (k <= 16) return go(local_gram_kernel<MODE, 16>);
-        if (k <= 32) return go(local_gram_kernel<MODE, 32>);
-        if (k <= 64) return go(local_gram_kernel<MODE, 64>);
-        return go(local_gram_kernel<MODE, 128>);
+        if (k <= 16) return go(local_gram_kernel<16>);
+        if (k <= 32) return go(local_gram_kernel<32>);
+        if (k <= 64) return go(local_gram_kernel<64>);
+        return go(local_gram_kernel<128>);
     }
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library), or null.
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// Tensor map of the binary32 dY [nobs][k] with boxes of one row (k values):
+// TMA needs k * 4 bytes to be a multiple of 16 and a 16-byte aligned base.
+static bool make_row_map(CUtensorMap* map, const float* dY32, int nobs, int k) {
+    const auto enc = tensor_map_encoder();
+    if (!enc || k % 4 != 0 || k > 256 || nobs < 1 || (reinterpret_cast<uintptr_t>(dY32) & 15u)) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)k, (cuuint64_t)nobs};
+    const cuuint64_t strides[1] = {(cuuint64_t)k * 4};
+    const cuuint32_t box[2] = {(cuuint32_t)k, 1};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(dY32), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <bool TF32, int KP>
+static cudaError_t launch_gram_tc_kp(int nx, int ny, int k, const ObsParams& o, double d_cut, double aa,
+                                     int cell0, int nc, const MixScratch& sc, int* flags, cudaStream_t s) {
+    CUtensorMap map;
+    memset(&map, 0, sizeof map);
+    const int use_tma = make_row_map(&map, o.dY32, o.nvar * o.npts, k) ? 1 : 0;
+    const size_t sh = tc_gram_smem<TF32, KP>(o.npts);
+    if (sh > 227 * 1024) return cudaErrorInvalidValue;  // merged list too long for shared memory
+    const auto kern = local_gram_tc_kernel<TF32, KP>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+    if (e != cudaSuccess) return e;
+    const unsigned grid = (unsigned)((nc + kGramPts - 1) / kGramPts);
+    kern<<<grid, 32 * kGramPts, sh, s>>>(nx, ny, k, o, d_cut, aa, cell0, nc, sc, map, use_tma, flags);
+    return cudaGetLastError();
+}
+
+template <bool TF32>
+static cudaError_t launch_gram_tc(int nx, int ny, int k, const ObsParams& o, double d_cut, double aa, int cell0,
+                                  int nc, const MixScratch& sc, int* flags, cudaStream_t s) {
+    if (k <= 16) return launch_gram_tc_kp<TF32, 16>(nx, ny, k, o, d_cut, aa, cell0, nc, sc, flags, s);
+    if (k <= 32) return launch_gram_tc_kp<TF32, 32>(nx, ny, k, o, d_cut, aa, cell0, nc, sc, flags, s);
+    if (k <= 64) return launch_gram_tc_kp<TF32, 64>(nx, ny, k, o, d_cut, aa, cell0, nc, sc, flags, s);
+    return launch_gram_tc_kp<TF32, 128>(nx, ny, k, o, d_cut, aa, cell0, nc, sc, flags, s);
+}
+
 static cudaError_t launch_gram(int prod, int nx, int ny, int k, const ObsParams& o, double d_cut,
-                               double aa, int cell0, int nc, const MixScratch& sc, cudaStream_t s) {
+                               double aa, int cell0, int nc, const MixScratch& sc, int* flags, cudaStream_t s) {
     if (prod == PROD_FP64) return launch_gram_mode<PROD_FP64>(nx, ny, k, o, d_cut, aa, cell0, nc, sc, s);
     if (prod == PROD_FP32) return launch_gram_mode<PROD_FP32>(nx, ny, k, o, d_cut, aa, cell0, nc, sc, s);
-    if (prod == PROD_TF32) return launch_gram_mode<PROD_TF32>(nx, ny, k, o, d_cut, aa, cell0, nc, sc, s);
-    return launch_gram_mode<PROD_BF16>(nx, ny, k, o, d_cut, aa, cell0, nc, sc, s);
+    if (prod == PROD_TF32) return launch_gram_tc<true>(nx, ny, k, o, d_cut, aa, cell0, nc, sc, flags, s);
+    return launch_gram_tc<false>(nx, ny, k, o, d_cut, aa, cell0, nc, sc, flags, s);
 }
 
 size_t analyze_scratch_bytes(int nx, int ny, int fp32, int nl, int nmax, int k, int prod) {
@@ -2292,7 +2540,7 @@ cudaError_t launch_analyze(void* f, int fp32, int nx, int ny, int k, const ObsPa
                 mix_scratch_at((unsigned char*)scratch + b * buf_bytes, chunk, cap, nm, kg, gsz);
             if (c >= 2 && (e = cudaStreamWaitEvent(aux->s2, aux->ref_done[b], 0)) != cudaSuccess)
                 return e;
-            if (kg && (e = launch_gram(prod, nx, ny, k, o, d_cut, (k - 1) / beta, (int)c0, nc, sc,
+            if (kg && (e = launch_gram(prod, nx, ny, k, o, d_cut, (k - 1) / beta, (int)c0, nc, sc, flags,
                                        aux->s2)) != cudaSuccess)
                 return e;
             if (nm <= NREG)
