@@ -1511,9 +1511,11 @@ __global__ void __launch_bounds__(32 * kGramPts, 1)
             }
             ok = __syncthreads_and(ok) != 0;
             if (!ok) break;
-            // B[n][rr] = y_rr[n].
+            // B[n][rr] = y_rr[n]. Eight consecutive threads write the eight
+            // 16-byte rows of one core matrix (128 contiguous bytes).
             for (int e = tid; e < KP * L::KCOL; e += 32 * kGramPts) {
-                const int n = e / L::KCOL, kc = e - n * L::KCOL;
+                const int cm = e >> 3, kc = cm % L::KCOL;
+                const int n = (cm / L::KCOL) * 8 + (e & 7);
                 float v[L::T];
 #pragma unroll
                 for (int t = 0; t < L::T; ++t) {
@@ -1526,7 +1528,8 @@ __global__ void __launch_bounds__(32 * kGramPts, 1)
             for (int e = tid; e < L::G * 128 * L::KCOL; e += 32 * kGramPts) {
                 const int g = e / (128 * L::KCOL);
                 const int rem = e - g * 128 * L::KCOL;
-                const int R = rem / L::KCOL, kc = rem - R * L::KCOL;
+                const int cm = rem >> 3, kc = cm % L::KCOL;
+                const int R = (cm / L::KCOL) * 8 + (rem & 7);
                 const int p = R / KP, m = R - p * KP, q = q0 + g * L::PG + p;
                 float v[L::T];
 #pragma unroll
