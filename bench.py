@@ -366,8 +366,8 @@ def measure_adjoint(cfg, reps=3, nsteps=200, ckpt=20):
 def measure_sweep(cfg, reps=2, only=None):
     """Analysis time of the precision sweep at 256^2 (binary32 LBM state):
     k in {16, 32, 64, 128}, observation lattices 8^2 .. 64^2, d_cut = 32 and
-    d_cut = the observation spacing, Gram/b products FP64 / binary32 / TF32 /
-    BF16. Every case fits the mixed path (n = min(k, p) <= 128); one above
+    d_cut = the observation spacing, Gram/b products double-binary32 / FP64 /
+    binary32 / TF32 / BF16. Every case fits the mixed path (n = min(k, p) <= 128); one above
     it would be listed as refused. only = (k, obs side, d_cut) restricts the
     sweep to that case."""
     import torch
@@ -378,7 +378,7 @@ def measure_sweep(cfg, reps=2, only=None):
     force = inputs.forcing_field(nx, ny, cfg.seeds["forcing"], cfg.force_amp, cfg.force_kmin, cfg.force_kmax)
     tu, tv = inputs.random_velocity(nx, ny, cfg.seeds["nature"], cfg.u_rms)
     stream = torch.cuda.current_stream()
-    modes = (("fp64", binding.LBM_PROD_FP64), ("fp32", binding.LBM_PROD_FP32),
+    modes = (("df32", binding.LBM_PROD_DF32), ("fp64", binding.LBM_PROD_FP64), ("fp32", binding.LBM_PROD_FP32),
              ("tf32", binding.LBM_PROD_TF32), ("bf16", binding.LBM_PROD_BF16))
     out = []
     for k in (16, 32, 64, 128):

@@ -172,7 +172,11 @@ int letkf_observe_rho(lbm_ctx *ctx, int npts, const int *ix, const int *iy,
 /* Arithmetic of the local Gram matrix C = (k-1)/beta I + Yh^T Yh and of
  * b = Yh^T d-hat (Section 3.2, with Yh = R_loc^{-1/2} dY_loc) in the
  * ensemble-space form (p >= k) of a mixed-precision context's analysis:
- *   LBM_PROD_FP64  FP64 products and sums (default);
+ *   LBM_PROD_DF32  FP64-class: double-binary32 products and sums on the
+ *                  binary32 units (each value split into two binary32
+ *                  halves, rounding errors recovered exactly; C within
+ *                  ~1e-14 relative of FP64), the default;
+ *   LBM_PROD_FP64  FP64 products and sums;
  *   LBM_PROD_FP32  binary32 products, binary32 accumulation (CUDA cores);
  *   LBM_PROD_TF32  TF32 products on the tcgen05 tensor cores, binary32
  *                  accumulation in tensor memory (rows staged by TMA);
@@ -182,10 +186,11 @@ int letkf_observe_rho(lbm_ctx *ctx, int npts, const int *ix, const int *iy,
  * eight neighbouring grid points must fit shared memory with the operand
  * tiles (about 30,000 observation points); beyond it the launch fails with
  * LBM_ECUDA.
- * The eigensolve stays FP64-accurate in every mode; the reduced modes apply
- * for members <= 128 (larger ensembles keep FP64). LBM_EINVAL for an unknown
- * mode or a reduced mode on an FP64 context. Applies to later analyses. */
-enum { LBM_PROD_FP64 = 0, LBM_PROD_FP32 = 1, LBM_PROD_TF32 = 2, LBM_PROD_BF16 = 3 };
+ * The eigensolve stays FP64-accurate in every mode; the modes apply for
+ * members <= 128 (larger ensembles form C in FP64 per grid point).
+ * LBM_EINVAL for an unknown mode or a mode other than LBM_PROD_FP64 on an
+ * FP64 context. Applies to later analyses. */
+enum { LBM_PROD_FP64 = 0, LBM_PROD_FP32 = 1, LBM_PROD_TF32 = 2, LBM_PROD_BF16 = 3, LBM_PROD_DF32 = 4 };
 int letkf_set_products(lbm_ctx *ctx, int mode);
 
 /* Grid points per run of the analysis (Section 3.2: the local analyses are

@@ -21,7 +21,7 @@ from . import build as _build
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EDIVERGED, LBM_ENOCONV = range(6)
 LBM_FP64, LBM_MIXED = 0, 1
 LBM_PTR_HOST, LBM_PTR_DEVICE = 0, 1
-LBM_PROD_FP64, LBM_PROD_FP32, LBM_PROD_TF32, LBM_PROD_BF16 = range(4)
+LBM_PROD_FP64, LBM_PROD_FP32, LBM_PROD_TF32, LBM_PROD_BF16, LBM_PROD_DF32 = range(5)
 
 STATUS_NAMES = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA",
                 4: "LBM_EDIVERGED", 5: "LBM_ENOCONV"}

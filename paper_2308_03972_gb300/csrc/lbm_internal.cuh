@@ -16,9 +16,10 @@ enum : int {
 };
 
 // Arithmetic of the local Gram matrix C = a I + Yh^T Yh and b = Yh^T d-hat in
-// the ensemble-space form of the mixed-precision analysis: FP64 (default),
-// or binary32 accumulation of binary32 / TF32 / BF16 products.
-enum : int { PROD_FP64 = 0, PROD_FP32 = 1, PROD_TF32 = 2, PROD_BF16 = 3 };
+// the ensemble-space form of the mixed-precision analysis: FP64,
+// double-binary32 (FP64-class, the default), or binary32 accumulation of
+// binary32 / TF32 / BF16 products.
+enum : int { PROD_FP64 = 0, PROD_FP32 = 1, PROD_TF32 = 2, PROD_BF16 = 3, PROD_DF32 = 4 };
 // No ensemble-space grid point in this analysis: no Gram pass at all.
 constexpr int PROD_NONE = -1;
 

@@ -632,6 +632,7 @@ int lbm_init(const lbm_config* cfg, const double* f0, const double* force, int p
     c->cs = cfg->cs_smag;
     c->mu = cfg->mu;
     c->precision = cfg->precision;
+    if (c->precision == LBM_MIXED) c->prod = PROD_DF32;
     c->stream = (cudaStream_t)cfg->stream;
 
     int st = LBM_OK;
@@ -842,9 +843,9 @@ int lbm_energy_spectrum(lbm_ctx* c, double* E, int nshells, int ptr_kind) {
 
 int letkf_set_products(lbm_ctx* c, int mode) {
     if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
-    if (mode < LBM_PROD_FP64 || mode > LBM_PROD_BF16) return fail(c, LBM_EINVAL, "unknown product mode %d", mode);
+    if (mode < LBM_PROD_FP64 || mode > LBM_PROD_DF32) return fail(c, LBM_EINVAL, "unknown product mode %d", mode);
     if (mode != LBM_PROD_FP64 && !is_fp32(c))
-        return fail(c, LBM_EINVAL, "reduced-precision products need a mixed-precision context");
+        return fail(c, LBM_EINVAL, "product modes other than FP64 need a mixed-precision context");
     c->prod = mode;
     return LBM_OK;
 }

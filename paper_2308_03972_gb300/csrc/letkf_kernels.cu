@@ -1722,6 +1722,128 @@ __global__ void __launch_bounds__(32 * kGramPts, 1) local_gram_fp64_kernel(int n
         if (lane + 32 * c < k) sc.b64[(size_t)li * k + lane + 32 * c] = bacc[c];
 }
 
+// Double-binary32 Gram (PROD_DF32, the default of a mixed-precision
+// context): the C and b of the FP64 Gram pass to FP64-class accuracy on the
+// binary32 units. The staged rows are split once into binary32 halves
+// (y = yh + yl, exact to 2^-48); each lane's weighted column value
+// wy = rho y_n is formed in FP64 and split likewise; every product
+// (yh + yl)(wyh + wyl) enters a double-binary32 sum: yh wyh exactly
+// (its rounding error recovered with one FMA), the cross terms yh wyl and
+// yl wyh in binary32 (relative 2^-48), yl wyl dropped (2^-48 of the
+// product); the sum carries its error through TwoSum (Knuth; Dekker 1971;
+// Ogita, Rump and Oishi 2005). Two rows per packed .f32x2 instruction, as
+// in the refinement. Output layout and roles as the FP64 pass (C64, b64;
+// b stays FP64).
+template <int K>
+__global__ void __launch_bounds__(32 * kGramPts, 1) local_gram_df_kernel(int nx, int ny, int k,
+                                                                        ObsParams o, double d_cut,
+                                                                        double aa, int cell0,
+                                                                        int ncell, MixScratch sc) {
+    constexpr int KC = 16;                      // rows per stage
+    constexpr int RH = K > 64 ? 2 : 1;          // row ranges per column
+    constexpr int KB = (K < 32 ? K : 32) / RH;  // output columns per pass
+    constexpr int MR = K / RH;                  // rows per lane (even)
+    constexpr int NBC = K > 32 ? K / 32 : 1;    // entries of b per lane
+    static_assert(MR % 2 == 0, "row pairs");
+    __shared__ double Ys[KC][K];
+    __shared__ __align__(8) float Yh[KC][K];
+    __shared__ __align__(8) float Yl[KC][K];
+    __shared__ double Ws[kGramPts][KC];
+    __shared__ double Ds[KC];
+    __shared__ int wcount[kGramPts];
+    __shared__ int pcnt[kGramPts];
+    extern __shared__ int U[];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int li0 = blockIdx.x * kGramPts;
+    const int nv = o.nvar;
+    const int total = gram_merge(o, nx, ny, d_cut, cell0, li0, ncell, U, pcnt, wcount);
+    bool any_ens = false;
+    for (int q = 0; q < kGramPts; ++q) any_ens |= pcnt[q] * nv >= k;
+    if (!any_ens) return;
+    const int rows = total * nv;
+    const int li = li0 + w;
+    const int col = lane % KB, rh = lane / KB;
+    const bool act = rh < RH;  // K = 16: lanes 16..31 own no column
+    f2x S[MR / 2], Cc[MR / 2];
+    double bacc[NBC];
+#pragma unroll
+    for (int c = 0; c < NBC; ++c) bacc[c] = 0.0;
+    for (int cb = 0; cb < K; cb += KB) {
+#pragma unroll
+        for (int m = 0; m < MR / 2; ++m) S[m] = Cc[m] = 0ull;
+        for (int r0 = 0; r0 < rows; r0 += KC) {
+            for (int e = threadIdx.x; e < KC * K; e += 32 * kGramPts) {
+                const int rr = e / K, c = e % K, r = r0 + rr;
+                double v = 0.0;
+                if (r < rows && c < k) v = o.dY[(size_t)(nv * U[r / nv] + r % nv) * k + c];
+                const float h = (float)v;
+                Ys[rr][c] = v;
+                Yh[rr][c] = h;
+                Yl[rr][c] = (float)(v - (double)h);
+            }
+            if (threadIdx.x < KC * kGramPts) {
+                const int q = threadIdx.x / KC, rr = threadIdx.x % KC, r = r0 + rr;
+                double wv = 0.0;
+                if (r < rows && li0 + q < ncell) {
+                    const int cell = cell0 + li0 + q;
+                    const double sg = local_weight(o, U[r / nv], cell % nx, cell / nx, nx, ny, d_cut);
+                    const int qv = r % nv;
+                    const double l = sg / (qv == 0 ? o.sigma_u : (qv == 1 ? o.sigma_v : o.sigma_r));
+                    wv = l * l;
+                }
+                Ws[q][rr] = wv;
+            }
+            if (threadIdx.x < KC) {
+                const int r = r0 + threadIdx.x;
+                Ds[threadIdx.x] = r < rows ? o.d[nv * U[r / nv] + r % nv] : 0.0;
+            }
+            __syncthreads();
+            for (int rr = 0; rr < KC; ++rr) {
+                const double wl = Ws[w][rr];
+                if (wl == 0.0) continue;
+                if (cb == 0) {
+#pragma unroll
+                    for (int c = 0; c < NBC; ++c)
+                        if (lane + 32 * c < K) bacc[c] += wl * Ds[rr] * Ys[rr][lane + 32 * c];
+                }
+                if (act) {
+                    const double wy = wl * Ys[rr][cb + col];
+                    const float wh = (float)wy;
+                    const float wlo = (float)(wy - (double)wh);
+                    const f2x WH = f2pack(wh, wh), NWH = f2pack(-wh, -wh), WL = f2pack(wlo, wlo);
+                    const f2x* yh2 = reinterpret_cast<const f2x*>(&Yh[rr][rh * MR]);
+                    const f2x* yl2 = reinterpret_cast<const f2x*>(&Yl[rr][rh * MR]);
+#pragma unroll
+                    for (int m = 0; m < MR / 2; ++m) {
+                        const f2x AH = yh2[m], AL = yl2[m];
+                        df2_acc(S[m], Cc[m], AH, AL, WH, NWH);
+                        Cc[m] = f2fma(AH, WL, Cc[m]);
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        if (li < ncell && act) {
+            double* C = sc.C64 + (size_t)li * k * k;
+            const int n = cb + col;
+#pragma unroll
+            for (int m = 0; m < MR / 2; ++m) {
+                float s0, s1, c0, c1;
+                f2unpack(S[m], s0, s1);
+                f2unpack(Cc[m], c0, c1);
+                const int row0 = rh * MR + 2 * m;
+                if (row0 < k && n < k) C[(size_t)row0 * k + n] = df_value(s0, c0) + (row0 == n ? aa : 0.0);
+                if (row0 + 1 < k && n < k)
+                    C[(size_t)(row0 + 1) * k + n] = df_value(s1, c1) + (row0 + 1 == n ? aa : 0.0);
+            }
+        }
+    }
+    if (li >= ncell) return;
+#pragma unroll
+    for (int c = 0; c < NBC; ++c)
+        if (lane + 32 * c < k) sc.b64[(size_t)li * k + lane + 32 * c] = bacc[c];
+}
+
 __global__ void __launch_bounds__(32 * kJacWarps, 5) mixed_jacobi_kernel(int nx, int ny, int k,
                                                                       ObsParams o, double d_cut,
                                                                       double beta, int cell0,
@@ -2400,7 +2522,7 @@ static int mixed_nm(int nmax) { return nmax < 2 ? 2 : (nmax > NMAX ? NMAX : nmax
 static int gram_k(int fp32, int k, int prod) {
     return (fp32 && prod != PROD_NONE && k <= NMAX) ? k : 0;
 }
-static int gram_sz(int prod) { return prod == PROD_FP64 ? 8 : 4; }
+static int gram_sz(int prod) { return (prod == PROD_FP64 || prod == PROD_DF32) ? 8 : 4; }
 
 template <int MODE>
 static cudaError_t launch_gram_mode(int nx, int ny, int k, const ObsParams& o, double d_cut,
@@ -2409,9 +2531,8 @@ static cudaError_t launch_gram_mode(int nx, int ny, int k, const ObsParams& o, d
     const size_t sh = (size_t)(o.npts > 0 ? o.npts : 1) * sizeof(int);
     const unsigned grid = (unsigned)((nc + kGramPts - 1) / kGramPts);
     auto go = [&](auto kern) {
-        cudaError_t e = cudaSuccess;
-        if (sh > 48 * 1024)
-            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+        // The limit covers static plus dynamic shared memory above 48 KB.
+        const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
         if (e != cudaSuccess) return e;
         kern<<<grid, 32 * kGramPts, sh, s>>>(nx, ny, k, o, d_cut, aa, cell0, nc, sc);
         return cudaGetLastError();
@@ -2421,6 +2542,11 @@ static cudaError_t launch_gram_mode(int nx, int ny, int k, const ObsParams& o, d
         if (k <= 32) return go(local_gram_fp64_kernel<32>);
         if (k <= 64) return go(local_gram_fp64_kernel<64>);
         return go(local_gram_fp64_kernel<128>);
+    } else if constexpr (MODE == PROD_DF32) {
+        if (k <= 16) return go(local_gram_df_kernel<16>);
+        if (k <= 32) return go(local_gram_df_kernel<32>);
+        if (k <= 64) return go(local_gram_df_kernel<64>);
+        return go(local_gram_df_kernel<128>);
     } else {
         if (k <= 16) return go(local_gram_kernel<16>);
         if (k <= 32) return go(local_gram_kernel<32>);
@@ -2488,6 +2614,7 @@ static cudaError_t launch_gram_tc(int nx, int ny, int k, const ObsParams& o, dou
 static cudaError_t launch_gram(int prod, int nx, int ny, int k, const ObsParams& o, double d_cut,
                                double aa, int cell0, int nc, const MixScratch& sc, int* flags, cudaStream_t s) {
     if (prod == PROD_FP64) return launch_gram_mode<PROD_FP64>(nx, ny, k, o, d_cut, aa, cell0, nc, sc, s);
+    if (prod == PROD_DF32) return launch_gram_mode<PROD_DF32>(nx, ny, k, o, d_cut, aa, cell0, nc, sc, s);
     if (prod == PROD_FP32) return launch_gram_mode<PROD_FP32>(nx, ny, k, o, d_cut, aa, cell0, nc, sc, s);
     if (prod == PROD_TF32) return launch_gram_tc<true>(nx, ny, k, o, d_cut, aa, cell0, nc, sc, flags, s);
     return launch_gram_tc<false>(nx, ny, k, o, d_cut, aa, cell0, nc, sc, flags, s);

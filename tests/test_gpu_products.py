@@ -78,3 +78,42 @@ def test_product_mode_arguments(gpu):
     with gpu.Ensemble(8, 8, 4, TAU0, CS, MU, gpu.LBM_MIXED, f0=f) as e:
         with pytest.raises(gpu.LbmError):
             e.set_products(7)
+
+
+@pytest.mark.parametrize("nx,ny,k,nox,noy,d_cut", [
+    (32, 32, 16, 8, 8, 6.0),
+    (32, 32, 64, 16, 16, 6.0),
+    (24, 24, 20, 6, 6, 9.0),
+    (16, 16, 128, 8, 8, 100.0),  # two row ranges per column, passes of 16 columns
+])
+def test_double_binary32_gram_matches_fp64_gram(gpu, nx, ny, k, nox, noy, d_cut):
+    """LBM_PROD_DF32 (the mixed context's default): C and b to FP64-class
+    accuracy on the binary32 units. The analysis equals the FP64-product one
+    to the binary32 storage of the state, and the default is this mode."""
+    f, ix, iy, yu, yv = _case(nx, ny, k, nox, noy, seed=2 * nx + k)
+    ref = oracle.letkf_analyze(f, ix, iy, yu, yv, SIGMA, SIGMA, d_cut, 1.05)
+    fp64 = _run(gpu, f, ix, iy, yu, yv, d_cut, gpu.LBM_PROD_FP64)
+    df32 = _run(gpu, f, ix, iy, yu, yv, d_cut, gpu.LBM_PROD_DF32)
+    assert norm_rel(df32, ref) <= 1e-6
+    # A Gram entry within ~1e-14 of FP64 moves the stored state by at most a
+    # few binary32 units of g = f - w (|g| < 0.05): ~1e-8 of max |f|.
+    assert norm_rel(df32, fp64) <= 2e-8
+    _, ny_, nx_, k_ = f.shape
+    with gpu.Ensemble(nx_, ny_, k_, TAU0, CS, MU, gpu.LBM_MIXED, f0=f) as e:
+        e.observe(ix, iy, yu, yv, SIGMA, SIGMA)
+        e.analyze(d_cut, 1.05)
+        default = e.get_f()
+        e.sync()
+    assert np.array_equal(default, df32)
+
+
+def test_double_binary32_mode_needs_a_mixed_context(gpu):
+    f = turbulent_state(oracle, 8, 8, 4, seed=1)
+    with gpu.Ensemble(8, 8, 4, TAU0, CS, MU, gpu.LBM_FP64, f0=f) as e:
+        with pytest.raises(gpu.LbmError) as err:
+            e.set_products(gpu.LBM_PROD_DF32)
+        assert err.value.code == gpu.LBM_EINVAL
+    with gpu.Ensemble(8, 8, 4, TAU0, CS, MU, gpu.LBM_MIXED, f0=f) as e:
+        e.set_products(gpu.LBM_PROD_DF32)
+        with pytest.raises(gpu.LbmError):
+            e.set_products(5)
