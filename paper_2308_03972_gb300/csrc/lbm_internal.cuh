@@ -128,9 +128,12 @@ size_t analyze_scratch_bytes(int nx, int ny, int fp32, int nl, int nmax, int k, 
 // mixed kernel's shared memory; points above it are reported as too large).
 // prod: PROD_* arithmetic of the ensemble-space Gram (mixed precision only),
 // PROD_NONE when no grid point uses the ensemble-space form.
+// warm_run > 1 (binary32 states with a Gram pass): kernel (A) takes runs of
+// warm_run consecutive grid points per warp and starts each ensemble-space
+// point's Jacobi from the previous one's basis.
 cudaError_t launch_analyze(void* f, int fp32, int nx, int ny, int k, const ObsParams& o,
-                           double d_cut, double beta, int nmax, int prod, int* flags, void* scratch,
-                           const AnalyzeAux* aux, cudaStream_t s);
+                           double d_cut, double beta, int nmax, int prod, int warm_run, int* flags,
+                           void* scratch, const AnalyzeAux* aux, cudaStream_t s);
 
 // dst = (float) src, n elements.
 cudaError_t launch_to_f32(const double* src, float* dst, size_t n, cudaStream_t s);

@@ -575,7 +575,8 @@ int analyze_launch(lbm_ctx* c, const AnalysisPlan& pl) {
         return LBM_OK;
     }
     CK(c, launch_analyze(c->f[c->cur], is_fp32(c), c->nx, c->ny, c->k, o, pl.d_cut, pl.beta, pl.nmax,
-                         pl.prod, c->flags, c->ana_scratch, c->aux_ready ? &c->aux : nullptr, c->stream),
+                         pl.prod, c->run_len, c->flags, c->ana_scratch, c->aux_ready ? &c->aux : nullptr,
+                         c->stream),
        "launching analysis");
     return LBM_OK;
 }

@@ -1087,6 +1087,124 @@ __device__ void jacobi_point(const ObsParams& o, int k, int n, int p, bool obs_s
     }
 }
 
+// Kernel (A) for an ensemble-space point that follows another one in the
+// same run of grid points: C (k x k, from the Gram pass) is solved from the
+// previous point's basis U (lane c holds column c of U in up[]):
+//   A' = U^T C U (column c: v = C u_c, then A'_ic = u_i . v), in binary32
+//   through the warp's shared staging Cs / Us (row-major NS x NS);
+//   the register Jacobi of A' gives J; the basis is U J, re-orthonormalised
+//   to first order, U J (I - E/2) with E = (U J)^T (U J) - I, so that its
+//   drift does not grow along the run. Neighbouring points differ by a
+//   smooth change of the localisation weights, so A' is nearly diagonal and
+//   the Jacobi needs fewer sweeps than from the identity. On return up[]
+//   holds the new basis (for the next point) and X is stored as by
+//   jacobi_point.
+template <int NS>
+__device__ void jacobi_point_warm(const ObsParams& o, int k, int n, int lane, float* __restrict__ Xp,
+                                  int* flags, const float* __restrict__ Cp, const double* __restrict__ Cd,
+                                  float (&up)[NREG], float* Cs, float* Us) {
+    // Every product below runs its outer index at run time and reads this
+    // lane's own column back from shared memory, so that at most two
+    // register columns are live (the register Jacobi needs the rest).
+    float a[NS], u[NS];
+    const bool own = lane < n;
+    const int c = lane < NS ? lane : 0;  // lanes past NS compute a copy and store nothing
+    __syncwarp();  // the previous point is done with Cs / Us
+    if (lane < NS) {
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+            float v = 0.0f;
+            if (own && i < n) v = Cp ? Cp[i * k + lane] : (float)Cd[i * k + lane];
+            Cs[i * NS + lane] = v;      // C symmetric: column lane
+            Us[i * NS + lane] = up[i];  // column lane of U
+        }
+    }
+    __syncwarp();
+    // v = C u_c: v_i = sum_j C_ij U_jc (C_ij = C_ji = Cs row j).
+#pragma unroll
+    for (int i = 0; i < NS; ++i) u[i] = 0.0f;
+#pragma unroll 2
+    for (int j = 0; j < NS; ++j) {
+        const float ujc = Us[j * NS + c];
+#pragma unroll
+        for (int i = 0; i < NS; ++i) u[i] = fmaf(Cs[j * NS + i], ujc, u[i]);
+    }
+    __syncwarp();  // Cs takes v
+    if (lane < NS) {
+#pragma unroll
+        for (int i = 0; i < NS; ++i) Cs[i * NS + lane] = u[i];
+    }
+    __syncwarp();
+    // A'_ic = sum_j U_ji v_j.
+#pragma unroll
+    for (int i = 0; i < NS; ++i) a[i] = 0.0f;
+#pragma unroll 2
+    for (int j = 0; j < NS; ++j) {
+        const float vj = Cs[j * NS + c];
+#pragma unroll
+        for (int i = 0; i < NS; ++i) a[i] = fmaf(Us[j * NS + i], vj, a[i]);
+    }
+    if (lane >= NS) {
+#pragma unroll
+        for (int i = 0; i < NS; ++i) a[i] = 0.0f;
+    }
+    const int sweeps = jacobi32_reg<NS>(a, u, lane, 1e-6f, kMaxSweeps);
+    if (sweeps < 0 && lane == 0) atomicOr(flags, FLAG_NOCONV);
+    record_sweeps(o, sweeps, lane);
+    __syncwarp();  // Cs takes J
+    if (lane < NS) {
+#pragma unroll
+        for (int i = 0; i < NS; ++i) Cs[i * NS + lane] = u[i];
+    }
+    __syncwarp();
+    // W = U J, column c: W_ic = sum_j U_ij J_jc (into a).
+#pragma unroll
+    for (int i = 0; i < NS; ++i) a[i] = 0.0f;
+#pragma unroll 2
+    for (int j = 0; j < NS; ++j) {
+        const float jjc = Cs[j * NS + c];
+#pragma unroll
+        for (int i = 0; i < NS; ++i) a[i] = fmaf(Us[i * NS + j], jjc, a[i]);
+    }
+    __syncwarp();  // Us takes W
+    if (lane < NS) {
+#pragma unroll
+        for (int i = 0; i < NS; ++i) Us[i * NS + lane] = a[i];
+    }
+    __syncwarp();
+    // E column c: E_jc = sum_i W_ij W_ic - delta_jc (into u).
+#pragma unroll
+    for (int j = 0; j < NS; ++j) u[j] = (j == lane) ? -1.0f : 0.0f;
+#pragma unroll 2
+    for (int i = 0; i < NS; ++i) {
+        const float wic = Us[i * NS + c];
+#pragma unroll
+        for (int j = 0; j < NS; ++j) u[j] = fmaf(Us[i * NS + j], wic, u[j]);
+    }
+    __syncwarp();  // Cs takes E
+    if (lane < NS) {
+#pragma unroll
+        for (int j = 0; j < NS; ++j) Cs[j * NS + lane] = u[j];
+    }
+    __syncwarp();
+    // U_new = W (I - E/2), column c: W_ic - 1/2 sum_j W_ij E_jc.
+#pragma unroll
+    for (int i = 0; i < NS; ++i) u[i] = 0.0f;
+#pragma unroll 2
+    for (int j = 0; j < NS; ++j) {
+        const float ejc = Cs[j * NS + c];
+#pragma unroll
+        for (int i = 0; i < NS; ++i) u[i] = fmaf(Us[i * NS + j], ejc, u[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < NS; ++i) up[i] = lane < NS ? fmaf(-0.5f, u[i], a[i]) : 0.0f;
+    if (lane < n) {
+#pragma unroll
+        for (int i = 0; i < NS; ++i)
+            if (i < n) Xp[(size_t)i * NREG + lane] = up[i];
+    }
+}
+
 // Per-chunk scratch shared by kernels (A) and (B).
 struct MixScratch {
     float* X;      // [chunk][xr][xr] binary32 basis, row i at i * xr (xr = 32, 64 or 128)
@@ -1884,6 +2002,70 @@ __global__ void __launch_bounds__(32 * kJacWarps, 5) mixed_jacobi_kernel(int nx,
         jacobi_point<32>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, xr, flags, Cp, Cd);
 }
 
+// Observation-space points of the run kernel below, outside its register
+// allocation.
+template <int NS>
+__device__ __noinline__ void jacobi_point_call(const ObsParams& o, int k, int n, int p, bool obs_space, double aa,
+                                               const int* lidx, const double* lsq, int lane, float* Xp, int* flags,
+                                               const float* Cp, const double* Cd) {
+    jacobi_point<NS>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, NREG, flags, Cp, Cd);
+}
+
+// Kernel (A), one warp per run of `run` consecutive grid points of the
+// chunk. Ensemble-space points (n = k, tile NE) start from the previous
+// such point's basis (jacobi_point_warm; the first of a run from the
+// identity through the same path); observation-space points are solved
+// from the identity (jacobi_point).
+template <int NE>
+__global__ void __launch_bounds__(32 * kJacWarps, 4) mixed_jacobi_run_kernel(int nx, int ny, int k,
+                                                                          ObsParams o, double d_cut,
+                                                                          double beta, int cell0,
+                                                                          int ncell, int nm, int run,
+                                                                          MixScratch sc,
+                                                                          int* __restrict__ flags) {
+    extern __shared__ __align__(16) float jsm[];  // [kJacWarps][2][NE * NE]
+    const int nobs = o.nvar * o.npts;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float* Cs = jsm + (size_t)w * 2 * NE * NE;
+    float* Us = Cs + NE * NE;
+    float up[NREG];
+#pragma unroll
+    for (int i = 0; i < NREG; ++i) up[i] = (i == lane) ? 1.0f : 0.0f;
+    for (int t = 0; t < run; ++t) {
+        const long long lil = ((long long)blockIdx.x * kJacWarps + w) * run + t;
+        if (lil >= ncell) return;
+        const int li = (int)lil;
+        const int cell = cell0 + li;
+        const int x = cell % nx, y = cell / nx;
+        const int cap = o.plmax > 0 ? o.plmax : nobs;
+        double* lsq = sc.lsq + (size_t)li * cap;
+        int* lidx = sc.lidx + (size_t)li * cap;
+        const int p = local_set(o, x, y, nx, ny, d_cut, lane, lidx, lsq, cap);
+        if (lane == 0) sc.pcount[li] = p;
+        if (p == 0 || p > cap) continue;  // p > cap: reported by kernel (B)
+        const bool obs_space = p < k;
+        const int n = obs_space ? p : k;
+        if (n > nm || n > NREG) continue;  // reported by kernel (B)
+        const double aa = (k - 1) / beta;
+        float* Xp = sc.X + (size_t)li * NREG * NREG;
+        const float* Cp = sc.C32 ? sc.C32 + (size_t)li * k * k : nullptr;
+        const double* Cd = sc.C64 ? sc.C64 + (size_t)li * k * k : nullptr;
+        if (!obs_space && (Cp || Cd)) {
+            jacobi_point_warm<NE>(o, k, n, lane, Xp, flags, Cp, Cd, up, Cs, Us);
+        } else if (n <= 8) {
+            jacobi_point_call<8>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, flags, Cp, Cd);
+        } else if (n <= 16) {
+            jacobi_point_call<16>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, flags, Cp, Cd);
+        } else if (n <= 24) {
+            jacobi_point_call<24>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, flags, Cp, Cd);
+        } else if (n <= 28) {
+            jacobi_point_call<28>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, flags, Cp, Cd);
+        } else {
+            jacobi_point_call<32>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, flags, Cp, Cd);
+        }
+    }
+}
+
 // Kernel (A) for local problems of 33..128: the binary32 Jacobi of
 // jacobi_sym_block, kBlkThreads threads per grid point, same output.
 constexpr int kBlkThreads = 256;
@@ -2630,8 +2812,8 @@ size_t analyze_scratch_bytes(int nx, int ny, int fp32, int nl, int nmax, int k, 
 }
 
 cudaError_t launch_analyze(void* f, int fp32, int nx, int ny, int k, const ObsParams& o,
-                           double d_cut, double beta, int nmax, int prod, int* flags, void* scratch,
-                           const AnalyzeAux* aux, cudaStream_t s) {
+                           double d_cut, double beta, int nmax, int prod, int warm_run, int* flags,
+                           void* scratch, const AnalyzeAux* aux, cudaStream_t s) {
     const long long cells = (long long)nx * ny;
     if (cells > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     cudaError_t e;
@@ -2656,6 +2838,20 @@ cudaError_t launch_analyze(void* f, int fp32, int nx, int ny, int k, const ObsPa
             if (e != cudaSuccess) return e;
         }
         const int kg = gram_k(fp32, k, prod), gsz = gram_sz(prod);
+        // Runs of kernel (A): warm starts between ensemble-space points
+        // (their C comes from the Gram pass).
+        const int runA = (kg && warm_run > 1) ? warm_run : 1;
+        const int ne = k <= 8 ? 8 : (k <= 16 ? 16 : (k <= 24 ? 24 : (k <= 28 ? 28 : 32)));
+        const size_t shJ = runA > 1 ? (size_t)kJacWarps * 2 * ne * ne * sizeof(float) : 0;
+        auto kernJ = ne == 8 ? mixed_jacobi_run_kernel<8>
+                             : (ne == 16 ? mixed_jacobi_run_kernel<16>
+                                         : (ne == 24 ? mixed_jacobi_run_kernel<24>
+                                                     : (ne == 28 ? mixed_jacobi_run_kernel<28>
+                                                                 : mixed_jacobi_run_kernel<32>)));
+        if (runA > 1 && nm <= NREG) {
+            e = cudaFuncSetAttribute(kernJ, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shJ);
+            if (e != cudaSuccess) return e;
+        }
         const long long chunk = mix_chunk(cells, cap, nm, kg, gsz);
         const size_t buf_bytes = mix_buf_bytes(chunk, cap, nm, kg, gsz);
         // Pipeline: (A) of chunk c on s2 overlaps (B) of chunk c-1 on s; the
@@ -2673,7 +2869,10 @@ cudaError_t launch_analyze(void* f, int fp32, int nx, int ny, int k, const ObsPa
             if (kg && (e = launch_gram(prod, nx, ny, k, o, d_cut, (k - 1) / beta, (int)c0, nc, sc, flags,
                                        aux->s2)) != cudaSuccess)
                 return e;
-            if (nm <= NREG)
+            if (nm <= NREG && runA > 1)
+                kernJ<<<(unsigned)((nc + kJacWarps * runA - 1) / (kJacWarps * runA)), 32 * kJacWarps, shJ,
+                        aux->s2>>>(nx, ny, k, o, d_cut, beta, (int)c0, nc, nm, runA, sc, flags);
+            else if (nm <= NREG)
                 mixed_jacobi_kernel<<<(unsigned)((nc + kJacWarps - 1) / kJacWarps), 32 * kJacWarps, 0,
                                       aux->s2>>>(nx, ny, k, o, d_cut, beta, (int)c0, nc, nm, sc, flags);
             else

@@ -133,7 +133,7 @@ extern "C" int letkf_analyze_noalloc(double* f, int nx, int ny, int members, int
     // No host-side stamp of the local sets here: size the kernel for the
     // largest problem the inputs allow, min(k, p) with p = 2 * npts.
     const int nmax = members < 2 * npts ? members : 2 * npts;
-    e = launch_analyze(f, 0, nx, ny, members, o, d_cut, beta, nmax, PROD_FP64, flags, nullptr,
+    e = launch_analyze(f, 0, nx, ny, members, o, d_cut, beta, nmax, PROD_FP64, 0, flags, nullptr,
                        nullptr, s);
     if (e != cudaSuccess) return cuda_fail(e, "launching the analysis");
     int h = 0;

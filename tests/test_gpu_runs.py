@@ -179,3 +179,40 @@ def test_fp64_paper_scale_runs_sampled_points(gpu):
     g = got.reshape(9, nx * ny, k)[:, pts]
     r = ref.reshape(9, nx * ny, k)[:, pts]
     assert norm_rel(g, r) <= 1e-12
+
+
+# ---- ensemble-space points: kernel (A) warm-started along runs -------------
+
+ENS_CASES = [
+    (40, 32, 16, 10, 8, 8.0),   # every point in ensemble space, tile 16
+    (36, 36, 32, 12, 12, 7.0),  # tile 32, 36 = 4 x 8 + 4: ragged runs
+    (30, 28, 20, 10, 7, 6.0),   # k = 20: tile 24 with padding players
+    (40, 40, 24, 4, 4, 9.0),    # both forms on one lattice (p from 2 to ~30)
+]
+
+
+@pytest.mark.parametrize("nx,ny,k,nox,noy,d_cut", ENS_CASES)
+@pytest.mark.parametrize("run_len", [0, 1, 3, 8])
+def test_ensemble_space_runs_match_oracle(gpu, nx, ny, k, nox, noy, d_cut, run_len):
+    f, ix, iy, yu, yv = _case(nx, ny, k, nox, noy, seed=nx + 5 * k)
+    f = _binary32_exact(f)
+    got, _ = _mixed(gpu, f, ix, iy, yu, yv, d_cut, 1.05, run_len)
+    ref = oracle.letkf_analyze(f, ix, iy, yu, yv, SIGMA, SIGMA, d_cut, 1.05)
+    assert norm_rel(got, ref) <= 5e-8
+    assert norm_rel(ref, f) > 1e-6
+
+
+def test_ensemble_space_warm_starts_take_fewer_sweeps(gpu):
+    """256^2, 32 members, 16^2 observation points, d_cut = 32: every grid
+    point in ensemble space (p ~ 100 > k); runs of 8 against one point per
+    run."""
+    nx = ny = 256
+    k = 32
+    f, ix, iy, yu, yv = _case(nx, ny, k, 16, 16, seed=8, steps=1)
+    _, h8 = _mixed(gpu, f, ix, iy, yu, yv, 32.0, 1.05, 8, hist=True)
+    _, h1 = _mixed(gpu, f, ix, iy, yu, yv, 32.0, 1.05, 1, hist=True)
+    assert h8.sum() == h1.sum() == nx * ny
+    assert h8[31] == 0 and h1[31] == 0
+    mean8 = (h8 * np.arange(32)).sum() / h8.sum()
+    mean1 = (h1 * np.arange(32)).sum() / h1.sum()
+    assert mean8 < 0.8 * mean1
