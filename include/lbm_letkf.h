@@ -209,6 +209,18 @@ int letkf_set_products(lbm_ctx *ctx, int mode);
  * results agree with either path to rounding. */
 int letkf_set_run_length(lbm_ctx *ctx, int run_len);
 
+/* Pipelining of the run analysis (Section 3.2's local analyses taken in
+ * chunks of runs): with runs > 0 and more than one chunk, the runs are
+ * taken in chunks of `runs`, the Jacobi kernel of chunk c + 1 running on a
+ * second stream of the context beside the refinement (mixed precision) or
+ * the FP64 kernel (double precision) of chunk c, so that the two share the
+ * GPU's SMs; the result is the same as unpipelined, bit for bit. 0 turns it
+ * off, the default: at 256^2 x 64 members every chunk size measured slower
+ * than one pass (4.97-8.8 ms against 4.88 ms mixed, 38.1-44.5 against
+ * 37.8 ms FP64 for chunks of 4096 down to 512 runs). LBM_EINVAL outside
+ * [0, 2^24]. Applies to later analyses. */
+int letkf_set_run_pipeline(lbm_ctx *ctx, int runs);
+
 /* Diagnostic: count the Jacobi sweeps of every local eigensolve of later
  * analyses (enable != 0) into a 32-bin histogram (bin s: points that took s
  * sweeps, the last one rotating nothing; bin 31: 31 or more, or the sweep
@@ -369,15 +381,18 @@ int lbm_batch_autotune(lbm_batch *b, int *threads, int *blocks);
 /* Pick the run length (grid points per warp, letkf_set_run_length) of the
  * batch's analyses per size class: experiments whose analysis takes the
  * run path (every grid point with p < members) are grouped by the union
- * size of their runs (up to 8, 16, 24, 28, 32 scalars), and each class
- * times its batched analysis (kernel J over every run of the class in one
- * launch, kernel F over every grid point in one launch) at run lengths 4,
- * 8, 16 and 32, best of three, keeping the fastest. The timed analyses
+ * size of their runs (up to 8, 16, 24, 28, 32 scalars); mixed-precision
+ * experiments with ensemble-space points and at most 32 members (whose
+ * Jacobi kernel warm-starts along runs) by their member tile (8, 16, 24,
+ * 28, 32). Each class times its batched analysis (on the run path kernel J
+ * over every run of the class in one launch, kernel F over every grid
+ * point in one launch) at run lengths 4, 8, 16 and 32, best of three,
+ * keeping the fastest. The timed analyses
  * work on copies of the current states in the spare buffers: states and
  * observations are unchanged. Every context must be observed
  * (letkf_observe) with the observations the analyses will use (d_cut[i],
  * beta[i]). run_len[i] (may be NULL) receives each experiment's run length
- * (unchanged for experiments off the run path). Synchronises; a captured
+ * (unchanged for experiments in no class). Synchronises; a captured
  * cycle is captured again. */
 int lbm_batch_autotune_analysis(lbm_batch *b, const double *d_cut, const double *beta, int *run_len);
 

@@ -57,6 +57,7 @@ SIGNATURES = {
     "lbm_set_closure": (_I, [_P, _D]),
     "letkf_set_products": (_I, [_P, _I]),
     "letkf_set_run_length": (_I, [_P, _I]),
+    "letkf_set_run_pipeline": (_I, [_P, _I]),
     "letkf_sweep_stats": (_I, [_P, _I, _P]),
     "lbm_misfit": (_I, [_P, ctypes.POINTER(lbm_window), _P]),
     "lbm_misfit_gradient": (_I, [_P, ctypes.POINTER(lbm_window), _P, _P, _P, _P, _P, _I]),
@@ -260,6 +261,10 @@ def letkf_set_run_length(ctx, run_len):
     _check(ctx, load().letkf_set_run_length(ctx, int(run_len)))
 
 
+def letkf_set_run_pipeline(ctx, runs):
+    _check(ctx, load().letkf_set_run_pipeline(ctx, int(runs)))
+
+
 def lbm_set_closure(ctx, cs_smag):
     _check(ctx, load().lbm_set_closure(ctx, float(cs_smag)))
 
@@ -435,6 +440,9 @@ class Ensemble:
 
     def set_run_length(self, run_len):
         letkf_set_run_length(self.ctx, run_len)
+
+    def set_run_pipeline(self, runs):
+        letkf_set_run_pipeline(self.ctx, runs)
 
     def set_closure(self, cs_smag):
         lbm_set_closure(self.ctx, cs_smag)

@@ -151,16 +151,18 @@ constexpr int kRunMaxUnion = 32;
 // whole: scratch for every run at once (the batched launch) rather than for
 // chunks of runs within a fixed budget.
 size_t run_scratch_bytes(int nx, int ny, int nobs, int run_len, int maxunion, bool whole = false);
+// aux (may be null) and pipe_runs > 0: chunks of pipe_runs runs with kernel
+// J on aux->s2 beside the refinement of the previous chunk on s.
 cudaError_t launch_analyze_runs(float* f, int nx, int ny, int k, const ObsParams& o, double d_cut,
                                 double beta, int run_len, int maxunion, int* flags, void* scratch,
-                                cudaStream_t s);
+                                const AnalyzeAux* aux, int pipe_runs, cudaStream_t s);
 // The same runs for a double-precision context: the binary32 Jacobi of the
 // run gives each grid point a starting basis, and an FP64 Jacobi from it
 // (launch_run_fp64, letkf_kernels.cu) gives the eigenpairs; transform and
 // update in FP64. scratch as above.
 cudaError_t launch_analyze_runs_fp64(double* f, int nx, int ny, int k, const ObsParams& o, double d_cut,
                                      double beta, int run_len, int maxunion, int* flags, void* scratch,
-                                     cudaStream_t s);
+                                     const AnalyzeAux* aux, int pipe_runs, cudaStream_t s);
 // FP64 warm-started analysis of the nruns * run_len grid points of the runs
 // run0.. (chunk-local basis Yg [.][ns][ns], eigenvalue estimates lamg
 // [.][ns] with -1 marking a point with no observation in range, union

@@ -57,6 +57,7 @@ struct lbm_ctx {
     bool obs_pending = false;
     double sigma_u = 0.0, sigma_v = 0.0, sigma_r = 1.0;
     int prod = PROD_FP64;  // ensemble-space Gram arithmetic (mixed precision)
+    int run_pipe = 0;      // runs per pipelined chunk of the run analysis (0: not pipelined)
     int* sweep_hist = nullptr;  // [32] Jacobi sweeps per point (diagnostic)
     bool sweep_stats = false;
     bool observed = false;
@@ -541,7 +542,7 @@ int analyze_prepare(lbm_ctx* c, double d_cut, double beta, AnalysisPlan* plan, b
         CK(c, cudaMalloc(&c->ana_scratch, scratch), "allocating analysis scratch");
         c->ana_scratch_bytes = scratch;
     }
-    if (is_fp32(c) && !c->aux_ready) {
+    if ((is_fp32(c) || run_len > 0) && !c->aux_ready) {
         CK(c, cudaStreamCreateWithFlags(&c->aux.s2, cudaStreamNonBlocking), "creating stream");
         CK(c, cudaEventCreateWithFlags(&c->aux.start, cudaEventDisableTiming), "creating event");
         for (int b = 0; b < 2; ++b) {
@@ -564,13 +565,15 @@ ObsParams obs_params(lbm_ctx* c, const AnalysisPlan& pl) {
 int analyze_launch(lbm_ctx* c, const AnalysisPlan& pl) {
     const ObsParams o = obs_params(c, pl);
     if (pl.run_len > 0) {
+        const AnalyzeAux* aux = c->aux_ready ? &c->aux : nullptr;
         if (is_fp32(c))
             CK(c, launch_analyze_runs((float*)c->f[c->cur], c->nx, c->ny, c->k, o, pl.d_cut, pl.beta, pl.run_len,
-                                      pl.maxunion, c->flags, c->ana_scratch, c->stream),
+                                      pl.maxunion, c->flags, c->ana_scratch, aux, c->run_pipe, c->stream),
                "launching analysis");
         else
             CK(c, launch_analyze_runs_fp64((double*)c->f[c->cur], c->nx, c->ny, c->k, o, pl.d_cut, pl.beta,
-                                           pl.run_len, pl.maxunion, c->flags, c->ana_scratch, c->stream),
+                                           pl.run_len, pl.maxunion, c->flags, c->ana_scratch, aux, c->run_pipe,
+                                           c->stream),
                "launching analysis");
         return LBM_OK;
     }
@@ -848,6 +851,13 @@ int letkf_set_products(lbm_ctx* c, int mode) {
     if (mode != LBM_PROD_FP64 && !is_fp32(c))
         return fail(c, LBM_EINVAL, "product modes other than FP64 need a mixed-precision context");
     c->prod = mode;
+    return LBM_OK;
+}
+
+int letkf_set_run_pipeline(lbm_ctx* c, int runs) {
+    if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (runs < 0 || runs > (1 << 24)) return fail(c, LBM_EINVAL, "runs must be in [0, 2^24]");
+    c->run_pipe = runs;
     return LBM_OK;
 }
 
@@ -1303,18 +1313,23 @@ int lbm_batch_autotune_analysis(lbm_batch* b, const double* d_cut, const double*
     for (int i = 0; i < n; ++i)
         if (!b->ctx[i]->observed)
             return bfail(b, LBM_EINVAL, "experiment %d: letkf_observe must precede the analysis autotuning", i);
-    // Size classes: the run analysis' union size class at the default run
-    // length; experiments off the run path (ensemble-space points) are not
-    // tuned.
+    // Size classes: on the run path, the union size class at the default
+    // run length; with ensemble-space points (chunked path, whose kernel (A)
+    // warm-starts along runs when members <= 32), the member tile (classes
+    // 100 + tile). Other experiments are not tuned.
+    auto tile = [](int v) { return v <= 8 ? 8 : (v <= 16 ? 16 : (v <= 24 ? 24 : (v <= 28 ? 28 : 32))); };
     std::vector<int> cls(n, -1);
     for (int i = 0; i < n; ++i) {
         lbm_ctx* c = b->ctx[i];
         if (!(d_cut[i] > 0.0) || !std::isfinite(d_cut[i]) || !(beta[i] > 0.0) || !std::isfinite(beta[i]))
             return bfail(b, LBM_EINVAL, "experiment %d: d_cut and beta must be finite and > 0", i);
-        largest_local_problem(c, d_cut[i]);
-        if (c->geo_any_ens) continue;
+        const int nmax = largest_local_problem(c, d_cut[i]);
+        if (c->geo_any_ens) {
+            if (is_fp32(c) && c->k <= 32 && nmax <= 32) cls[i] = 100 + tile(c->k);
+            continue;
+        }
         const int u = largest_run_union(c, d_cut[i], 8);
-        if (u <= kRunMaxUnion) cls[i] = u <= 8 ? 8 : (u <= 16 ? 16 : (u <= 24 ? 24 : (u <= 28 ? 28 : 32)));
+        if (u <= kRunMaxUnion) cls[i] = tile(u);
     }
     const int cand[] = {4, 8, 16, 32};
     cudaEvent_t t0, t1;

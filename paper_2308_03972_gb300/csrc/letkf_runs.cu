@@ -1191,6 +1191,57 @@ cudaError_t launch_runs_ns(RunArgs ra, long long runs, long long chunk, const Pr
     return cudaGetLastError();
 }
 
+// Pipelined form of launch_runs_ns: chunks of `pipe` runs, kernel J of
+// chunk c + 1 on the second stream while kernel F (or the FP64 kernel) of
+// chunk c runs on s, so that the issue-bound Jacobi and the latency-bound
+// (or FP64-pipe-bound) refinement share the SMs. A chunk of ~2,000 runs is
+// under one wave of J, so F's blocks find room beside it. The basis scratch
+// (sized for `cap` runs per pass, cap >= 2 pipe) holds two buffers of
+// `pipe` runs; J of chunk c waits for F of chunk c - 2 before reusing one.
+template <int NS>
+cudaError_t launch_runs_pipe(RunArgs ra, long long runs, long long pipe, const AnalyzeAux& aux, cudaStream_t s) {
+    const size_t shJ = (size_t)JLayout<NS>::total * 4;
+    const size_t shF = run_f_smem_bytes<NS>(ra.k);
+    cudaError_t e = cudaFuncSetAttribute(run_jacobi_kernel<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shJ);
+    if (e != cudaSuccess) return e;
+    if (!ra.f64) {
+        e = cudaFuncSetAttribute(run_refine_kernel<NS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shF);
+        if (e != cudaSuccess) return e;
+    }
+    float* Yb[2] = {ra.Yg, ra.Yg + (size_t)pipe * ra.R * NS * NS};
+    float* Lb[2] = {ra.lamg, ra.lamg + (size_t)pipe * ra.R * NS};
+    int* Ib[2] = {ra.rinfo, ra.rinfo + (size_t)pipe * kInfo};
+    if ((e = cudaEventRecord(aux.start, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(aux.s2, aux.start, 0)) != cudaSuccess) return e;
+    int c = 0;
+    for (long long r0 = 0; r0 < runs; r0 += pipe, ++c) {
+        const int b = c & 1;
+        const long long nr = runs - r0 < pipe ? runs - r0 : pipe;
+        RunArgs rb = ra;
+        rb.run0 = (int)r0;
+        rb.nruns = (int)nr;
+        rb.Yg = Yb[b];
+        rb.lamg = Lb[b];
+        rb.rinfo = Ib[b];
+        if (c >= 2 && (e = cudaStreamWaitEvent(aux.s2, aux.ref_done[b], 0)) != cudaSuccess) return e;
+        run_jacobi_kernel<NS><<<(unsigned)nr, 32, shJ, aux.s2>>>(rb);
+        if ((e = cudaEventRecord(aux.jac_done[b], aux.s2)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(s, aux.jac_done[b], 0)) != cudaSuccess) return e;
+        if (rb.f64) {
+            ObsParams o = rb.o;
+            o.sweep_hist = rb.fp64_hist;
+            e = launch_run_fp64(rb.f64, rb.nx, rb.ny, rb.k, o, rb.d_cut, rb.beta, rb.R, rb.run0, rb.nruns, NS, rb.Yg,
+                                rb.lamg, rb.rinfo, kInfo, rb.flags, s);
+            if (e != cudaSuccess) return e;
+        } else {
+            const ProbeArgs none{nullptr, 0, nullptr, nullptr};
+            run_refine_kernel<NS, false><<<(unsigned)(nr * rb.R), 32, shF, s>>>(rb, none);
+        }
+        if ((e = cudaEventRecord(aux.ref_done[b], s)) != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
+}
+
 // Run arguments of one analysis: the scratch laid out for `chunk` runs per
 // pass (G2, then the basis, eigenvalue estimates and union lists of a
 // chunk), and the preparation kernels queued (the binary32 copy of dY for a
@@ -1247,7 +1298,7 @@ long long run_count(int nx, int ny, int run_len) { return (long long)ny * ((nx +
 
 cudaError_t launch_runs(float* f, double* f64, int nx, int ny, int k, const ObsParams& o, double d_cut,
                         double beta, int run_len, int maxunion, int* flags, void* scratch, const ProbeArgs& pa,
-                        cudaStream_t s) {
+                        const AnalyzeAux* aux, int pipe_runs, cudaStream_t s) {
     if (f64 && pa.npoints > 0) return cudaErrorInvalidValue;
     if (run_len < 1) return cudaErrorInvalidValue;
     const int ns = run_ns(maxunion);
@@ -1257,6 +1308,17 @@ cudaError_t launch_runs(float* f, double* f64, int nx, int ny, int k, const ObsP
     RunArgs ra;
     const cudaError_t e = run_setup(f, f64, nx, ny, k, o, d_cut, beta, run_len, maxunion, flags, scratch, chunk, ra, s);
     if (e != cudaSuccess) return e;
+    // Pipelined when there is a second stream, more than one chunk of
+    // pipe_runs, and room for two of them in the scratch.
+    if (aux && pa.npoints == 0 && pipe_runs > 0 && runs > pipe_runs && 2 * (long long)pipe_runs <= chunk) {
+        switch (ns) {
+            case 8: return launch_runs_pipe<8>(ra, runs, pipe_runs, *aux, s);
+            case 16: return launch_runs_pipe<16>(ra, runs, pipe_runs, *aux, s);
+            case 24: return launch_runs_pipe<24>(ra, runs, pipe_runs, *aux, s);
+            case 28: return launch_runs_pipe<28>(ra, runs, pipe_runs, *aux, s);
+            default: return launch_runs_pipe<32>(ra, runs, pipe_runs, *aux, s);
+        }
+    }
     switch (ns) {
         case 8: return launch_runs_ns<8>(ra, runs, chunk, pa, s);
         case 16: return launch_runs_ns<16>(ra, runs, chunk, pa, s);
@@ -1332,16 +1394,18 @@ size_t run_scratch_bytes(int nx, int ny, int nobs, int run_len, int maxunion, bo
 
 cudaError_t launch_analyze_runs(float* f, int nx, int ny, int k, const ObsParams& o, double d_cut,
                                 double beta, int run_len, int maxunion, int* flags, void* scratch,
-                                cudaStream_t s) {
+                                const AnalyzeAux* aux, int pipe_runs, cudaStream_t s) {
     const ProbeArgs none{nullptr, 0, nullptr, nullptr};
-    return launch_runs(f, nullptr, nx, ny, k, o, d_cut, beta, run_len, maxunion, flags, scratch, none, s);
+    return launch_runs(f, nullptr, nx, ny, k, o, d_cut, beta, run_len, maxunion, flags, scratch, none, aux,
+                       pipe_runs, s);
 }
 
 cudaError_t launch_analyze_runs_fp64(double* f, int nx, int ny, int k, const ObsParams& o, double d_cut,
                                      double beta, int run_len, int maxunion, int* flags, void* scratch,
-                                     cudaStream_t s) {
+                                     const AnalyzeAux* aux, int pipe_runs, cudaStream_t s) {
     const ProbeArgs none{nullptr, 0, nullptr, nullptr};
-    return launch_runs(nullptr, f, nx, ny, k, o, d_cut, beta, run_len, maxunion, flags, scratch, none, s);
+    return launch_runs(nullptr, f, nx, ny, k, o, d_cut, beta, run_len, maxunion, flags, scratch, none, aux,
+                       pipe_runs, s);
 }
 
 size_t probe_work_bytes(int npoints, int maxunion, int k) {
@@ -1353,7 +1417,7 @@ cudaError_t launch_probe_runs(float* f, int nx, int ny, int k, const ObsParams& 
                               int npoints, double* T, double* work, cudaStream_t s) {
     if (npoints < 1 || !cells || !T || !work) return cudaErrorInvalidValue;
     const ProbeArgs pa{cells, npoints, T, work};
-    return launch_runs(f, nullptr, nx, ny, k, o, d_cut, beta, run_len, maxunion, flags, scratch, pa, s);
+    return launch_runs(f, nullptr, nx, ny, k, o, d_cut, beta, run_len, maxunion, flags, scratch, pa, nullptr, 0, s);
 }
 
 cudaError_t launch_analyze_runs_batch(const RunItem* items, int n, cudaStream_t s) {

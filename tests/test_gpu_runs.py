@@ -216,3 +216,40 @@ def test_ensemble_space_warm_starts_take_fewer_sweeps(gpu):
     mean8 = (h8 * np.arange(32)).sum() / h8.sum()
     mean1 = (h1 * np.arange(32)).sum() / h1.sum()
     assert mean8 < 0.8 * mean1
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+@pytest.mark.parametrize("nx,ny,k,nox,noy,d_cut,pipe", [
+    (36, 20, 64, 3, 2, 9.0, 3),       # chunks of 3 runs, ragged last chunk and ragged runs
+    (256, 256, 64, 8, 8, 32.0, 1024),  # the paper-scale lattice, 8 chunks
+])
+def test_pipelined_runs_equal_unpipelined(gpu, precision, nx, ny, k, nox, noy, d_cut, pipe):
+    """letkf_set_run_pipeline: kernel J of the next chunk on the second
+    stream beside the refinement of the current one gives the same state,
+    bit for bit, as one chunk after another."""
+    f, ix, iy, yu, yv = _case(nx, ny, k, nox, noy, seed=nx + 7 * k, steps=1)
+    if precision == "mixed":
+        f = _binary32_exact(f)
+    prec = gpu.LBM_MIXED if precision == "mixed" else gpu.LBM_FP64
+    out = []
+    for p in (0, pipe):
+        with gpu.Ensemble(nx, ny, k, TAU0, CS, MU, prec, f0=f) as e:
+            e.set_run_length(8)
+            e.set_run_pipeline(p)
+            e.observe(ix, iy, yu, yv, SIGMA, SIGMA)
+            e.analyze(d_cut, 1.05)
+            out.append(e.get_f())
+            e.sync()
+    assert np.array_equal(out[0], out[1])
+    if nx <= 64:
+        ref = oracle.letkf_analyze(f, ix, iy, yu, yv, SIGMA, SIGMA, d_cut, 1.05)
+        assert norm_rel(out[1], ref) <= (5e-8 if precision == "mixed" else 1e-12)
+
+
+def test_run_pipeline_argument(gpu):
+    with gpu.Ensemble(8, 8, 4, TAU0, CS, MU, gpu.LBM_MIXED) as e:
+        with pytest.raises(gpu.LbmError) as err:
+            e.set_run_pipeline(-1)
+        assert err.value.code == gpu.LBM_EINVAL
+        e.set_run_pipeline(0)
+        e.set_run_pipeline(4096)
