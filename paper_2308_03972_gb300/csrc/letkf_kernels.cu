@@ -746,9 +746,11 @@ __global__ void __launch_bounds__(32) analyze_fp64_kernel(double* __restrict__ f
 // run's union of local scalars (NS x NS, row-major, Y_ic = component i of
 // vector c). Union scalars outside this point's support have weight zero, so
 // their rows and columns of A vanish and the result is that of the point's
-// own local set (exactly, in exact arithmetic). In FP64:
+// own local set (exactly, in exact arithmetic). Then:
 //  1. Y1 = Y (I - E/2) with E = Y^T Y - I: Y is orthonormal to ~1e-7 in
-//     binary32, Y1 to ~|E|^2.
+//     binary32, Y1 to ~1e-13. E and the correction Y E run on the binary32
+//     units (double-binary32 sums of exact products for E); Y1 is FP64.
+// In FP64:
 //  2. A' = Y1^T A Y1 (symmetrised), diagonal to ~1e-6 of ||A||.
 //  3. The FP64 cyclic Jacobi of the cold path from A' with U = Y1 at the
 //     start and the same stopping rule (3e-8 ||A||_F): one rotating sweep
@@ -827,42 +829,64 @@ __global__ void __launch_bounds__(32) run_fp64_kernel(double* __restrict__ f, in
         sm.lsq[c] = w;
         sm.ldh[c] = c < nu ? w * o.d[g] : 0.0;
     }
-    // Y (binary32 values, exact in FP64) into U.
+    // 1. Y1 = Y (I - E/2), E = Y^T Y - I, on the binary32 units: Y is
+    // binary32, so E comes exactly enough from double-binary32 sums of
+    // exact products (|E| ~ 1e-7, kept to ~1e-15 absolute in binary32), and
+    // the correction Y E / 2 (entries ~1e-7) needs only binary32 relative
+    // precision (~1e-14 absolute). Y1 is then orthonormal to ~1e-13; the
+    // FP64 work starts with A' below. Yf (binary32 Y) sits over A, Ef over
+    // Z and B until they are used.
+    float* Yf = reinterpret_cast<float*>(A);
+    float* Ef = reinterpret_cast<float*>(sm.Z);
     const float* Yp = Yg + (size_t)lc * NS * NS;
-    for (int e = lane; e < NS * NS; e += 32) U[(e / NS) * ld + e % NS] = (double)Yp[e];
+    for (int e = lane; e < NS * NS; e += 32) Yf[e] = Yp[e];
     __syncwarp();
     const int c = lane < NS ? lane : NS - 1;  // lanes past NS compute a copy and store nothing
-    // 1. E = Y^T Y - I (in A), then Y1 = Y (I - E/2) (in U).
     {
-        double e[NS];
+        // E column c, rows in groups of 8 (two per packed register):
+        // E_ic = sum_j Y_ji Y_jc, rows i..i+7 of row j of Yf.
+        for (int i0 = 0; i0 < NS; i0 += 8) {
+            f2x S2[4], C2[4];
 #pragma unroll
-        for (int i = 0; i < NS; ++i) e[i] = 0.0;
-#pragma unroll 1
-        for (int j = 0; j < NS; ++j) {
-            const double yjc = U[j * ld + c];
+            for (int q = 0; q < 4; ++q) S2[q] = C2[q] = 0ull;
+#pragma unroll 2
+            for (int j = 0; j < NS; ++j) {
+                const float yjc = Yf[j * NS + c];
+                const f2x Y2 = f2pack(yjc, yjc), NY2 = f2pack(-yjc, -yjc);
 #pragma unroll
-            for (int i = 0; i < NS; ++i) e[i] += U[j * ld + i] * yjc;
-        }
-        if (lane < NS) {
+                for (int q = 0; q < 4; ++q) {
+                    const int i = i0 + 2 * q;
+                    const f2x A2 = i + 1 < NS ? *reinterpret_cast<const f2x*>(Yf + j * NS + i)
+                                              : f2pack(i < NS ? Yf[j * NS + i] : 0.0f, 0.0f);
+                    df2_acc1(S2[q], C2[q], A2, Y2, NY2);
+                }
+            }
 #pragma unroll
-            for (int i = 0; i < NS; ++i) A[i * ld + c] = e[i] - (i == c ? 1.0 : 0.0);
+            for (int q = 0; q < 4; ++q) {
+                float s0, s1, c0, c1;
+                f2unpack(S2[q], s0, s1);
+                f2unpack(C2[q], c0, c1);
+                const int i = i0 + 2 * q;
+                if (lane < NS && i < NS) Ef[i * NS + c] = (float)(df_value(s0, c0) - (i == c ? 1.0 : 0.0));
+                if (lane < NS && i + 1 < NS) Ef[(i + 1) * NS + c] = (float)(df_value(s1, c1) - (i + 1 == c ? 1.0 : 0.0));
+            }
         }
     }
     __syncwarp();
     {
-        double col[NS];
+        // (Y E)_ic for column c, then Y1 = Y - (Y E) / 2 in FP64 (into U).
+        float ye[NS];
 #pragma unroll
-        for (int i = 0; i < NS; ++i) col[i] = U[i * ld + c];
-#pragma unroll 1
+        for (int i = 0; i < NS; ++i) ye[i] = 0.0f;
+#pragma unroll 2
         for (int j = 0; j < NS; ++j) {
-            const double h = 0.5 * A[j * ld + c];
+            const float ejc = Ef[j * NS + c];
 #pragma unroll
-            for (int i = 0; i < NS; ++i) col[i] -= U[i * ld + j] * h;
+            for (int i = 0; i < NS; ++i) ye[i] = fmaf(Yf[i * NS + j], ejc, ye[i]);
         }
-        __syncwarp();
         if (lane < NS) {
 #pragma unroll
-            for (int i = 0; i < NS; ++i) U[i * ld + c] = col[i];
+            for (int i = 0; i < NS; ++i) U[i * ld + c] = fma(-0.5, (double)ye[i], (double)Yf[i * NS + c]);
         }
     }
     __syncwarp();
