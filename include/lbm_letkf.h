@@ -175,7 +175,7 @@ int letkf_observe_rho(lbm_ctx *ctx, int npts, const int *ix, const int *iy,
  *   LBM_PROD_DF32  FP64-class: double-binary32 products and sums on the
  *                  binary32 units (each value split into two binary32
  *                  halves, rounding errors recovered exactly; C within
- *                  ~1e-14 relative of FP64), the default;
+ *                  a few 1e-13 relative of FP64), the default;
  *   LBM_PROD_FP64  FP64 products and sums;
  *   LBM_PROD_FP32  binary32 products, binary32 accumulation (CUDA cores);
  *   LBM_PROD_TF32  TF32 products on the tcgen05 tensor cores, binary32

@@ -224,3 +224,117 @@ def test_double_binary32_products_are_fp64_class(k, p, seed):
     # The same sums in plain binary32 are orders of magnitude worse.
     S32 = (X.T @ (Ah @ X)).astype(np.float64)
     assert np.abs(S32 - Xd.T @ A @ Xd).max() > 1e-9 * scale
+
+
+@pytest.mark.parametrize("k,p,seed", [(32, 104, 11), (64, 200, 12), (128, 90, 13)])
+def test_double_binary32_gram_is_fp64_class(k, p, seed):
+    """The arithmetic of the double-binary32 Gram pass (LBM_PROD_DF32):
+    C = sum_r rho_r y_r y_r^T with the FP64 rows split into binary32 halves,
+    each lane's weighted value w y_n formed in FP64 and split likewise,
+    yh (wy)h accumulated with its exact product error, the cross terms yh
+    (wy)l and yl (wy)h in binary32, yl (wy)l dropped. It must match the
+    FP64 Gram to a few 1e-13 of |C| over sums of up to 200 rows (the
+    binary32 compensation term limits it; binary32 products give ~1e-7)."""
+    dY, rho, d, a = _problem(k, p, seed)
+    f = np.float32
+    Yh = dY.astype(f)
+    Yl = (dY - Yh.astype(np.float64)).astype(f)
+    s = np.zeros((k, k), f)
+    c = np.zeros((k, k), f)
+    for r in range(p):
+        wy = rho[r] * dY[r, :]           # FP64, one value per output column n
+        wh = wy.astype(f)
+        wl = (wy - wh.astype(np.float64)).astype(f)
+        s, c = _df_acc(s, c, Yh[r, :][:, None], Yl[r, :][:, None], wh[None, :])
+        # c += yh (wy)l as one FMA.
+        c = (c.astype(np.float64) + Yh[r, :][:, None].astype(np.float64) * wl[None, :]).astype(f)
+    C_df = s.astype(np.float64) + c
+    C_ref = (dY.T * rho) @ dY
+    scale = np.abs(C_ref).max()
+    assert np.abs(C_df - C_ref).max() <= 5e-13 * scale
+    C32 = ((dY.T * rho).astype(f) @ dY.astype(f)).astype(np.float64)
+    assert np.abs(C32 - C_ref).max() > 1e-10 * scale
+
+
+def _jacobi64(A, U, rel=3e-8, max_sweeps=30):
+    """Cyclic FP64 Jacobi from (A, U) with the kernels' stopping rule (no
+    rotation above rel ||A||_F); returns U, A and the sweeps counted with
+    the last, rotation-free one."""
+    A = A.copy()
+    U = U.copy()
+    n = A.shape[0]
+    thresh = rel * np.sqrt((A * A).sum())
+    for sweep in range(max_sweeps):
+        rotated = False
+        for pp in range(n - 1):
+            for qq in range(pp + 1, n):
+                apq = A[pp, qq]
+                if abs(apq) <= thresh:
+                    continue
+                rotated = True
+                th, ph = A[qq, qq] - A[pp, pp], 2.0 * apq
+                rr = np.hypot(th, ph)
+                t = ph / (th + rr if th >= 0 else th - rr)
+                cs = 1.0 / np.sqrt(1.0 + t * t)
+                sn = t * cs
+                J = np.array([[cs, sn], [-sn, cs]])
+                A[:, [pp, qq]] = A[:, [pp, qq]] @ J
+                A[[pp, qq], :] = J.T @ A[[pp, qq], :]
+                U[:, [pp, qq]] = U[:, [pp, qq]] @ J
+        if not rotated:
+            return U, A, sweep + 1
+    return U, A, -1
+
+
+@pytest.mark.parametrize("k,p,seed", [(64, 28, 21), (64, 20, 22), (48, 28, 23)])
+def test_fp64_jacobi_from_an_orthonormalised_binary32_basis(k, p, seed):
+    """The FP64 run path: a binary32 Jacobi basis Y (stopped at 1e-6 of
+    ||A||_F) made orthonormal on the binary32 units (E = Y^T Y - I from
+    exact products summed in double-binary32, the correction Y E in
+    binary32, Y1 = Y - Y E / 2 in FP64), then the FP64 Jacobi from
+    A' = Y1^T A Y1 with U = Y1. Y1 is orthonormal to second order in the
+    basis' binary32 non-orthogonality (~1e-13), the FP64
+    Jacobi needs far fewer sweeps than from the identity, and the matrix
+    functions from it are FP64-accurate."""
+    dY, rho, d, a = _problem(k, p, seed)
+    Yh = np.sqrt(rho)[:, None] * dY
+    A = Yh @ Yh.T
+    f = np.float32
+    Y = _jacobi32(A, rel=1e-6).astype(f)
+    n = p
+    # Kernel J's own first-order re-orthonormalisation in binary32, which
+    # leaves |Y^T Y - I| at the binary32 level (~1e-7).
+    E32 = (Y.T @ Y - np.eye(n, dtype=f)).astype(f)
+    Y = (Y - f(0.5) * (Y @ E32)).astype(f)
+    e0 = np.abs(Y.astype(np.float64).T @ Y.astype(np.float64) - np.eye(n)).max()
+    assert e0 < 1e-6
+    z = np.zeros((n, n), f)
+    s, c = z.copy(), z.copy()
+    for r in range(n):
+        s, c = _df_acc(s, c, Y[r, :][:, None], z[r, :][:, None], Y[r, :][None, :])
+    E = (s.astype(np.float64) + c - np.eye(n)).astype(f)
+    YE = (Y @ E).astype(np.float64)  # binary32 products and sums
+    Y1 = Y.astype(np.float64) - 0.5 * YE
+    # One step leaves the non-orthogonality at second order in e0.
+    assert np.abs(Y1.T @ Y1 - np.eye(n)).max() <= n * e0 * e0 + 1e-13
+    Ap = Y1.T @ A @ Y1
+    Ap = 0.5 * (Ap + Ap.T)
+    U, S, sweeps = _jacobi64(Ap, Y1)
+    _, _, cold = _jacobi64(A, np.eye(n))
+    assert 0 < sweeps <= 3 and sweeps < cold
+    # Matrix functions from the FP64 eigenpairs (first order in the
+    # remaining off-diagonal, as the kernel takes them).
+    S = U.T @ A @ U
+    sd = np.diag(S)
+    r = np.sqrt(a)
+    u = np.sqrt(a + sd)
+    alpha = 1.0 / (u * (u + r))
+    G = S * (u[:, None] + u[None, :] + r) * np.outer(alpha, alpha) / (r * (u[:, None] + u[None, :]))
+    np.fill_diagonal(G, -alpha / r)
+    H = -S / np.outer(a + sd, a + sd)
+    np.fill_diagonal(H, 1.0 / (a + sd))
+    g = lambda x: ((a + x) ** -0.5 - a ** -0.5) / x  # noqa: E731
+    G_ref = _fun(A, g)
+    H_ref = np.linalg.inv(a * np.eye(p) + A)
+    assert np.abs(U @ G @ U.T - G_ref).max() <= 1e-12 * np.abs(G_ref).max()
+    assert np.abs(U @ H @ U.T - H_ref).max() <= 1e-12 * np.abs(H_ref).max()
