@@ -226,7 +226,12 @@ __host__ __device__ constexpr int jacobi_block() {
 }
 
 template <int NS>
-__device__ int jacobi_rows(float (&a)[NS], float (&ur)[NS], int lane, unsigned pmask, float thresh, float& lam) {
+__device__ int jacobi_rows(float (&a)[NS], float (&ur)[NS], int lane, unsigned pmask, float thresh, float& lam,
+                           float* rs) {
+    // rs: the warp's rotation slots, by pair (the p side's position): (c, s)
+    // of pair t at rs[2t], (t, a_pq) at rs[NS + 2t]; 16-byte aligned.
+    float2* const CS = reinterpret_cast<float2*>(rs);
+    float2* const TO = reinterpret_cast<float2*>(rs + NS);
     constexpr int m1 = NS - 1;
     constexpr int UB = jacobi_block<NS>();
     static_assert(m1 % UB == 0, "block of rounds");
@@ -269,13 +274,27 @@ __device__ int jacobi_rows(float (&a)[NS], float (&ur)[NS], int lane, unsigned p
                     rot = true;
                 }
                 if (__ballot_sync(kFull, rot) != 0u) {
+                    // Every pair's rotation goes to its slot (the p side
+                    // writes); all lanes read them back by position.
+                    __syncwarp();  // the previous round's reads are done
+                    if (pside && lane < NS) {
+                        CS[q] = make_float2(c, s);
+                        TO[q] = make_float2(t, off);
+                    }
+                    __syncwarp();
 #pragma unroll
                     for (int tt = 0; tt < NS / 2; ++tt) {
-                        int v = tt - 1 + r;
-                        v = v >= m1 ? v - m1 : v;
-                        const int pl = (tt == 0) ? 0 : 1 + v;
-                        const float ct = __shfl_sync(kFull, c, pl);
-                        const float st = __shfl_sync(kFull, s, pl);
+                        // Pair tt's (c, s): two pairs per 16-byte load.
+                        float ct, st;
+                        if ((tt & 1) == 0) {
+                            const float4 cs2 = reinterpret_cast<const float4*>(CS)[tt >> 1];
+                            ct = cs2.x;
+                            st = cs2.y;
+                        } else {
+                            const float4 cs2 = reinterpret_cast<const float4*>(CS)[tt >> 1];
+                            ct = cs2.z;
+                            st = cs2.w;
+                        }
                         const int i0 = (tt == 0) ? 0 : 1 + ((tt - 1 + b) % m1);
                         const int i1 = 1 + ((NS - 2 - tt + b) % m1);
                         const float x0 = a[i0], x1 = a[i1];
@@ -285,11 +304,11 @@ __device__ int jacobi_rows(float (&a)[NS], float (&ur)[NS], int lane, unsigned p
                         ur[i0] = fmaf(-st, y1, ct * y0);
                         ur[i1] = fmaf(st, y0, ct * y1);
                     }
-                    const int pl_mine = pside ? lane : partner;
-                    const float cm = __shfl_sync(kFull, c, pl_mine & 31);
-                    const float sm_ = __shfl_sync(kFull, s, pl_mine & 31);
-                    const float tm = __shfl_sync(kFull, t, pl_mine & 31);
-                    const float om = __shfl_sync(kFull, off, pl_mine & 31);
+                    // This lane's own pair, from its slot.
+                    const int pair = lane < NS ? (pside ? q : qp) : 0;
+                    const float2 csm = CS[pair];
+                    const float2 tom = TO[pair];
+                    const float cm = csm.x, sm_ = csm.y, tm = tom.x, om = tom.y;
                     dg = pside ? dg - tm * om : dg + tm * om;
                     const float sg = pside ? -sm_ : sm_;
 #pragma unroll
@@ -320,11 +339,13 @@ __device__ int jacobi_rows(float (&a)[NS], float (&ur)[NS], int lane, unsigned p
 
 // Shared memory of one warp of kernel J (floats): header pts[32], gi[32]
 // (ints), weights w[NS], the run's block of G (GU, binary32), the basis rows
-// Us (row i of U) and a scratch matrix Vs.
+// Us (row i of U), a scratch matrix Vs and the Jacobi's rotation slots.
 template <int NS>
 struct JLayout {
     static constexpr int w = 64, GU = w + NS, Us = GU + NS * NS, Vs = Us + NS * NS;
-    static constexpr int total = Vs + NS * NS;
+    static constexpr int rs = Vs + NS * NS;  // rotation slots (2 NS floats)
+    static constexpr int total = rs + 2 * NS;
+    static_assert(rs % 4 == 0, "16-byte aligned rotation slots");
 };
 
 template <int NS>
@@ -462,7 +483,7 @@ __device__ __forceinline__ void run_jacobi_body(const RunArgs& ra, int blk) {
         fro = warp_sum(fro);
         float lamc = 0.0f;
         // Stop at 1e-6 ||A||_F: the refinement is second order in the rest.
-        const int sweeps = jacobi_rows<NS>(a, ur, lane, pmask, 1e-6f * sqrtf(fro), lamc);
+        const int sweeps = jacobi_rows<NS>(a, ur, lane, pmask, 1e-6f * sqrtf(fro), lamc, smj + L::rs);
         if (sweeps < 0 && lane == 0) atomicOr(ra.flags, FLAG_NOCONV);
         if (o.sweep_hist && lane == 0) atomicAdd(&o.sweep_hist[(sweeps < 0 || sweeps > 31) ? 31 : sweeps], 1);
         // Re-orthonormalise to first order: E = U^T U - I (binary32 is
