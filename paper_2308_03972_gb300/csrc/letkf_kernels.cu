@@ -967,7 +967,11 @@ constexpr int kJacWarps = 4;        // points per block in (A)
 // On entry a[i] = A[i][lane] (row i at position i); on return u[i] holds
 // U[i][lane], the eigenvector of player `lane`.
 template <int NS>
-__device__ int jacobi32_reg(float (&a)[NS], float (&u)[NS], int lane, float rel, int max_sweeps) {
+__device__ int jacobi32_reg(float (&a)[NS], float (&u)[NS], int lane, float rel, int max_sweeps, float* rs) {
+    // rs: the warp's rotation slots (16-byte aligned, 2 NS floats): (c, s)
+    // of pair t at rs[2t], (t, a_pq) at rs[NS + 2t].
+    float2* const CS = reinterpret_cast<float2*>(rs);
+    float2* const TO = reinterpret_cast<float2*>(rs + NS);
     float dg = 0.0f;  // my diagonal entry A[lane][lane], tracked analytically
 #pragma unroll
     for (int i = 0; i < NS; ++i) {
@@ -1013,23 +1017,30 @@ __device__ int jacobi32_reg(float (&a)[NS], float (&u)[NS], int lane, float rel,
             }
             if (__ballot_sync(kFull, rot) != 0u) {
                 any_sweep = true;
+                // Every pair's rotation goes to its slot (the p side writes);
+                // all lanes read them back by position.
+                __syncwarp();  // the previous round's reads are done
+                if (pside && lane < NS) {
+                    CS[q] = make_float2(c, s);
+                    TO[q] = make_float2(t, off);
+                }
+                __syncwarp();
                 // Row rotations: position t (row p) with position NS-1-t (row q).
 #pragma unroll
                 for (int tt = 0; tt < NS / 2; ++tt) {
-                    const int pl = (tt == 0) ? 0 : 1 + ((tt - 1 + r) % m1);
-                    const float ct = __shfl_sync(kFull, c, pl);
-                    const float st = __shfl_sync(kFull, s, pl);
+                    const float4 cs2 = reinterpret_cast<const float4*>(CS)[tt >> 1];
+                    const float ct = (tt & 1) ? cs2.z : cs2.x;
+                    const float st = (tt & 1) ? cs2.w : cs2.y;
                     const float x0 = a[tt], x1 = a[NS - 1 - tt];
                     a[tt] = ct * x0 - st * x1;
                     a[NS - 1 - tt] = st * x0 + ct * x1;
                 }
                 // Column rotations with the partner lane; the diagonal moves
                 // by -/+ t a_pq on the p/q side.
-                const int pl_mine = pside ? lane : partner;
-                const float cm = __shfl_sync(kFull, c, pl_mine & 31);
-                const float sm_ = __shfl_sync(kFull, s, pl_mine & 31);
-                const float tm = __shfl_sync(kFull, t, pl_mine & 31);
-                const float om = __shfl_sync(kFull, off, pl_mine & 31);
+                const int pair = lane < NS ? (pside ? q : qp) : 0;
+                const float2 csm = CS[pair];
+                const float2 tom = TO[pair];
+                const float cm = csm.x, sm_ = csm.y, tm = tom.x, om = tom.y;
                 dg = pside ? dg - tm * om : dg + tm * om;
                 const float sg = pside ? -sm_ : sm_;
                 // The rotated off-diagonal entry (row position qp) is zero by
@@ -1063,7 +1074,7 @@ template <int NS>
 __device__ void jacobi_point(const ObsParams& o, int k, int n, int p, bool obs_space, double aa,
                              const int* lidx, const double* lsq, int lane, float* __restrict__ Xp,
                              int /*xr = NREG*/, int* flags, const float* __restrict__ Cp,
-                             const double* __restrict__ Cd) {
+                             const double* __restrict__ Cd, float* rs) {
     const int nobs = o.nvar * o.npts;
     float a[NS], u[NS];
     if (obs_space) {
@@ -1101,7 +1112,7 @@ __device__ void jacobi_point(const ObsParams& o, int k, int n, int p, bool obs_s
     // Stop at 1e-6 ||A||_F: the FP64-class refinement takes the matrix
     // functions from there (its neglected terms are second order in the
     // remaining off-diagonal, ~1e-12 relative).
-    const int sweeps = jacobi32_reg<NS>(a, u, lane, 1e-6f, kMaxSweeps);
+    const int sweeps = jacobi32_reg<NS>(a, u, lane, 1e-6f, kMaxSweeps, rs);
     if (sweeps < 0 && lane == 0) atomicOr(flags, FLAG_NOCONV);
     record_sweeps(o, sweeps, lane);
     if (lane < n) {
@@ -1126,7 +1137,7 @@ __device__ void jacobi_point(const ObsParams& o, int k, int n, int p, bool obs_s
 template <int NS>
 __device__ void jacobi_point_warm(const ObsParams& o, int k, int n, int lane, float* __restrict__ Xp,
                                   int* flags, const float* __restrict__ Cp, const double* __restrict__ Cd,
-                                  float (&up)[NREG], float* Cs, float* Us) {
+                                  float (&up)[NREG], float* Cs, float* Us, float* rs) {
     // Every product below runs its outer index at run time and reads this
     // lane's own column back from shared memory, so that at most two
     // register columns are live (the register Jacobi needs the rest).
@@ -1172,7 +1183,7 @@ __device__ void jacobi_point_warm(const ObsParams& o, int k, int n, int lane, fl
 #pragma unroll
         for (int i = 0; i < NS; ++i) a[i] = 0.0f;
     }
-    const int sweeps = jacobi32_reg<NS>(a, u, lane, 1e-6f, kMaxSweeps);
+    const int sweeps = jacobi32_reg<NS>(a, u, lane, 1e-6f, kMaxSweeps, rs);
     if (sweeps < 0 && lane == 0) atomicOr(flags, FLAG_NOCONV);
     record_sweeps(o, sweeps, lane);
     __syncwarp();  // Cs takes J
@@ -1992,6 +2003,7 @@ __global__ void __launch_bounds__(32 * kJacWarps, 5) mixed_jacobi_kernel(int nx,
                                                                       int ncell, int nm,
                                                                       MixScratch sc,
                                                                       int* __restrict__ flags) {
+    __shared__ __align__(16) float jrs[kJacWarps][2 * NREG];  // rotation slots per warp
     const int nobs = o.nvar * o.npts;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int li = blockIdx.x * kJacWarps + w;
@@ -2013,17 +2025,17 @@ __global__ void __launch_bounds__(32 * kJacWarps, 5) mixed_jacobi_kernel(int nx,
     const float* Cp = sc.C32 ? sc.C32 + (size_t)li * k * k : nullptr;
     const double* Cd = sc.C64 ? sc.C64 + (size_t)li * k * k : nullptr;
     if (n <= 8)
-        jacobi_point<8>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, xr, flags, Cp, Cd);
+        jacobi_point<8>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, xr, flags, Cp, Cd, jrs[w]);
     else if (n <= 16)
-        jacobi_point<16>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, xr, flags, Cp, Cd);
+        jacobi_point<16>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, xr, flags, Cp, Cd, jrs[w]);
     else if (n <= 24)
-        jacobi_point<24>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, xr, flags, Cp, Cd);
+        jacobi_point<24>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, xr, flags, Cp, Cd, jrs[w]);
     else if (n <= 26)
-        jacobi_point<26>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, xr, flags, Cp, Cd);
+        jacobi_point<26>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, xr, flags, Cp, Cd, jrs[w]);
     else if (n <= 28)
-        jacobi_point<28>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, xr, flags, Cp, Cd);
+        jacobi_point<28>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, xr, flags, Cp, Cd, jrs[w]);
     else
-        jacobi_point<32>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, xr, flags, Cp, Cd);
+        jacobi_point<32>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, xr, flags, Cp, Cd, jrs[w]);
 }
 
 // Observation-space points of the run kernel below, outside its register
@@ -2031,8 +2043,8 @@ __global__ void __launch_bounds__(32 * kJacWarps, 5) mixed_jacobi_kernel(int nx,
 template <int NS>
 __device__ __noinline__ void jacobi_point_call(const ObsParams& o, int k, int n, int p, bool obs_space, double aa,
                                                const int* lidx, const double* lsq, int lane, float* Xp, int* flags,
-                                               const float* Cp, const double* Cd) {
-    jacobi_point<NS>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, NREG, flags, Cp, Cd);
+                                               const float* Cp, const double* Cd, float* rs) {
+    jacobi_point<NS>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, NREG, flags, Cp, Cd, rs);
 }
 
 // Kernel (A), one warp per run of `run` consecutive grid points of the
@@ -2048,6 +2060,7 @@ __global__ void __launch_bounds__(32 * kJacWarps, 4) mixed_jacobi_run_kernel(int
                                                                           MixScratch sc,
                                                                           int* __restrict__ flags) {
     extern __shared__ __align__(16) float jsm[];  // [kJacWarps][2][NE * NE]
+    __shared__ __align__(16) float jrs[kJacWarps][2 * NREG];  // rotation slots per warp
     const int nobs = o.nvar * o.npts;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float* Cs = jsm + (size_t)w * 2 * NE * NE;
@@ -2075,17 +2088,17 @@ __global__ void __launch_bounds__(32 * kJacWarps, 4) mixed_jacobi_run_kernel(int
         const float* Cp = sc.C32 ? sc.C32 + (size_t)li * k * k : nullptr;
         const double* Cd = sc.C64 ? sc.C64 + (size_t)li * k * k : nullptr;
         if (!obs_space && (Cp || Cd)) {
-            jacobi_point_warm<NE>(o, k, n, lane, Xp, flags, Cp, Cd, up, Cs, Us);
+            jacobi_point_warm<NE>(o, k, n, lane, Xp, flags, Cp, Cd, up, Cs, Us, jrs[w]);
         } else if (n <= 8) {
-            jacobi_point_call<8>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, flags, Cp, Cd);
+            jacobi_point_call<8>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, flags, Cp, Cd, jrs[w]);
         } else if (n <= 16) {
-            jacobi_point_call<16>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, flags, Cp, Cd);
+            jacobi_point_call<16>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, flags, Cp, Cd, jrs[w]);
         } else if (n <= 24) {
-            jacobi_point_call<24>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, flags, Cp, Cd);
+            jacobi_point_call<24>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, flags, Cp, Cd, jrs[w]);
         } else if (n <= 28) {
-            jacobi_point_call<28>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, flags, Cp, Cd);
+            jacobi_point_call<28>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, flags, Cp, Cd, jrs[w]);
         } else {
-            jacobi_point_call<32>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, flags, Cp, Cd);
+            jacobi_point_call<32>(o, k, n, p, obs_space, aa, lidx, lsq, lane, Xp, flags, Cp, Cd, jrs[w]);
         }
     }
 }
