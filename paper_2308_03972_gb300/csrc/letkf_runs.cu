@@ -565,7 +565,7 @@ __device__ __forceinline__ void run_jacobi_body(const RunArgs& ra, int blk) {
 //   Al  [NS][NS]  A, low half; then S' (off the diagonal), then g(S')
 //   Ys  [NS][NS]  basis Y, row-major
 //   Zb  [NS][NS]  scratch: R, then Z (rows 0..8) and Z Y (rows 9..17)
-// Row groups of 8 read up to 4 floats past a matrix's last row; what
+// Row groups of 8 or 16 read up to 8 floats past a matrix's last row; what
 // follows each matrix in this layout is in bounds and the values are not
 // used.
 //   lsq [NS] (FP64) sqrt(rho-tilde); wh, wl its binary32 halves; dh d-hat;
@@ -736,27 +736,30 @@ __device__ __forceinline__ void run_refine_body(const RunArgs& ra, const ProbeAr
     const float lamc = own ? vlam[c] : 0.0f;
     __syncwarp();
     // R = A Y - Y diag(l), column c, double-binary32, into Zb. Rows in
-    // groups of 8, two per packed register: A is symmetric, so rows i..i+7
-    // of column j are entries i..i+7 of row j.
-    for (int i0 = 0; i0 < NS; i0 += 8) {
-        f2x S[4], C[4];
+    // groups of RG, two per packed register: A is symmetric, so rows
+    // i..i+RG-1 of column j are entries i..i+RG-1 of row j. A group reads up
+    // to RG - (NS mod RG) floats past a row's end; what follows each matrix
+    // in this layout is in bounds and the extra rows are not stored.
+    constexpr int RG = NS >= 16 ? 16 : 8;  // rows per group: RG / 2 independent sums
+    constexpr int NQ = RG / 2;
+    for (int i0 = 0; i0 < NS; i0 += RG) {
+        f2x S[NQ], C[NQ];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) S[q] = C[q] = 0ull;
+        for (int q = 0; q < NQ; ++q) S[q] = C[q] = 0ull;
 #pragma unroll 2
         for (int j = 0; j < NS; ++j) {
             const float uj = own ? Ys[j * NS + c] : 0.0f;  // Y_jc
             const f2x Y2 = f2pack(uj, uj), NY2 = f2pack(-uj, -uj);
-            const ulonglong2 h0 = *reinterpret_cast<const ulonglong2*>(Ah + j * NS + i0);
-            const ulonglong2 h1 = *reinterpret_cast<const ulonglong2*>(Ah + j * NS + i0 + 4);
-            const ulonglong2 l0 = *reinterpret_cast<const ulonglong2*>(Al + j * NS + i0);
-            const ulonglong2 l1 = *reinterpret_cast<const ulonglong2*>(Al + j * NS + i0 + 4);
-            df2_acc(S[0], C[0], h0.x, l0.x, Y2, NY2);
-            df2_acc(S[1], C[1], h0.y, l0.y, Y2, NY2);
-            df2_acc(S[2], C[2], h1.x, l1.x, Y2, NY2);
-            df2_acc(S[3], C[3], h1.y, l1.y, Y2, NY2);
+#pragma unroll
+            for (int g = 0; g < RG / 4; ++g) {
+                const ulonglong2 h = *reinterpret_cast<const ulonglong2*>(Ah + j * NS + i0 + 4 * g);
+                const ulonglong2 l = *reinterpret_cast<const ulonglong2*>(Al + j * NS + i0 + 4 * g);
+                df2_acc(S[2 * g], C[2 * g], h.x, l.x, Y2, NY2);
+                df2_acc(S[2 * g + 1], C[2 * g + 1], h.y, l.y, Y2, NY2);
+            }
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < NQ; ++q) {
             float s2[2], c2[2];
             f2unpack(S[q], s2[0], s2[1]);
             f2unpack(C[q], c2[0], c2[1]);
@@ -774,31 +777,29 @@ __device__ __forceinline__ void run_refine_body(const RunArgs& ra, const ProbeAr
     }
     __syncwarp();  // A is no longer read: E and S' take its place
     // E = Y^T Y - I (double-binary32) and T = Y^T R (binary32); S'. Rows in
-    // groups of 8: E_ic = sum_j Y_ji Y_jc, so rows i..i+7 read entries
-    // i..i+7 of row j of Y.
+    // groups of RG: E_ic = sum_j Y_ji Y_jc, so rows i..i+RG-1 read entries
+    // i..i+RG-1 of row j of Y.
     float ecc = 0.0f, tcc = 0.0f;
-    for (int i0 = 0; i0 < NS; i0 += 8) {
-        f2x ES[4], EC[4], TQ[4];
+    for (int i0 = 0; i0 < NS; i0 += RG) {
+        f2x ES[NQ], EC[NQ], TQ[NQ];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) ES[q] = EC[q] = TQ[q] = 0ull;
+        for (int q = 0; q < NQ; ++q) ES[q] = EC[q] = TQ[q] = 0ull;
 #pragma unroll 2
         for (int j = 0; j < NS; ++j) {
             const float uj = own ? Ys[j * NS + c] : 0.0f;  // Y_jc
             const float rj = own ? Zb[j * NS + c] : 0.0f;  // R_jc
             const f2x Y2 = f2pack(uj, uj), NY2 = f2pack(-uj, -uj), R2 = f2pack(rj, rj);
-            const ulonglong2 y0 = *reinterpret_cast<const ulonglong2*>(Ys + j * NS + i0);
-            const ulonglong2 y1 = *reinterpret_cast<const ulonglong2*>(Ys + j * NS + i0 + 4);
-            df2_acc1(ES[0], EC[0], y0.x, Y2, NY2);
-            df2_acc1(ES[1], EC[1], y0.y, Y2, NY2);
-            df2_acc1(ES[2], EC[2], y1.x, Y2, NY2);
-            df2_acc1(ES[3], EC[3], y1.y, Y2, NY2);
-            TQ[0] = f2fma(y0.x, R2, TQ[0]);
-            TQ[1] = f2fma(y0.y, R2, TQ[1]);
-            TQ[2] = f2fma(y1.x, R2, TQ[2]);
-            TQ[3] = f2fma(y1.y, R2, TQ[3]);
+#pragma unroll
+            for (int g = 0; g < RG / 4; ++g) {
+                const ulonglong2 y = *reinterpret_cast<const ulonglong2*>(Ys + j * NS + i0 + 4 * g);
+                df2_acc1(ES[2 * g], EC[2 * g], y.x, Y2, NY2);
+                df2_acc1(ES[2 * g + 1], EC[2 * g + 1], y.y, Y2, NY2);
+                TQ[2 * g] = f2fma(y.x, R2, TQ[2 * g]);
+                TQ[2 * g + 1] = f2fma(y.y, R2, TQ[2 * g + 1]);
+            }
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < NQ; ++q) {
             float es2[2], ec2[2], tq2[2];
             f2unpack(ES[q], es2[0], es2[1]);
             f2unpack(EC[q], ec2[0], ec2[1]);
