@@ -291,9 +291,9 @@ def test_analysis_autotuner_keeps_states_and_cycles_match(gpu):
         for e, f0 in zip(ens, before):
             assert np.array_equal(e.get_f(), f0)
         # The first three take the run path; 16 members with 8 x 8 points
-        # has ensemble-space points, so its run length is not tuned.
-        assert all(r in (4, 8, 16, 32) for r in rl[:3])
-        assert rl[3] == 8
+        # has ensemble-space points (its Jacobi kernel warm-starts along
+        # runs): all four are tuned.
+        assert all(r in (4, 8, 16, 32) for r in rl)
         for c in (2, 3):
             b.cycle(10, cycle_obs(c), dcs, betas, use_graph=True)
         b.sync()
