@@ -180,9 +180,8 @@ __device__ __forceinline__ void point_sync() {
 }
 
 __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
-__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 
-// Cyclic Jacobi (R = double or float) on the symmetric n x n matrix A (shared memory, row
+// Cyclic Jacobi (R = double) on the symmetric n x n matrix A (shared memory, row
 // stride ld), round-robin order (position 0 fixed, the others rotating), one
 // warp. Only what symmetry requires is updated: each rotated pair's 2 x 2
 // diagonal block analytically (a_pp - t a_pq, a_qq + t a_pq, 0), the
