@@ -340,7 +340,9 @@ __global__ void mean_velocity_kernel(const T* __restrict__ f, int nx, int ny, in
         const T ux = jx / r, uy = jy / r;
         su += (double)ux;
         sv += (double)uy;
-        bad |= !((double)ux * ux + (double)uy * uy <= kUMax2) || !(r > T(0));
+        // The divergence test in the state's precision, as the LBM step
+        // makes it (0.25 is exact in binary32).
+        bad |= !(ux * ux + uy * uy <= T(kUMax2)) || !(r > T(0));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
