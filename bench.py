@@ -511,6 +511,7 @@ def measure_batch(cfg, cycles=3):
             e.observe(*o)
         c += 1
         res["autotuned_run_len"] = b.autotune_analysis(dcs, betas)
+        res["autotuned_run_batched"] = b.run_batched
         for _ in range(2):  # uncaptured first cycle, then capture
             b.cycle(10, obs(c), dcs, betas, use_graph=True)
             c += 1

@@ -384,17 +384,22 @@ int lbm_batch_autotune(lbm_batch *b, int *threads, int *blocks);
  * size of their runs (up to 8, 16, 24, 28, 32 scalars); mixed-precision
  * experiments with ensemble-space points and at most 32 members (whose
  * Jacobi kernel warm-starts along runs) by their member tile (8, 16, 24,
- * 28, 32). Each class times its batched analysis (on the run path kernel J
- * over every run of the class in one launch, kernel F over every grid
- * point in one launch) at run lengths 4, 8, 16 and 32, best of three,
- * keeping the fastest. The timed analyses
- * work on copies of the current states in the spare buffers: states and
- * observations are unchanged. Every context must be observed
- * (letkf_observe) with the observations the analyses will use (d_cut[i],
- * beta[i]). run_len[i] (may be NULL) receives each experiment's run length
- * (unchanged for experiments in no class). Synchronises; a captured
- * cycle is captured again. */
-int lbm_batch_autotune_analysis(lbm_batch *b, const double *d_cut, const double *beta, int *run_len);
+ * 28, 32). Each class times its analyses at run lengths 4, 8, 16 and 32,
+ * best of three, keeping the fastest; a run-path class times two forms at
+ * each length: batched (kernel J over every run of the class in one
+ * launch, kernel F over every grid point in one launch) and one experiment
+ * after another (each with its own launches, as lbm_analyze makes them).
+ * lbm_batch_cycle then analyses the class in the form chosen; the results
+ * are the same in both forms. The timed analyses work on copies of the
+ * current states in the spare buffers: states and observations are
+ * unchanged. Every context must be observed (letkf_observe) with the
+ * observations the analyses will use (d_cut[i], beta[i]). run_len[i] (may
+ * be NULL) receives each experiment's run length (unchanged for
+ * experiments in no class); batched[i] (may be NULL) 1 if its run
+ * analysis goes into the batched launches, else 0 (the default before
+ * tuning is 1). Synchronises; a captured cycle is captured again. */
+int lbm_batch_autotune_analysis(lbm_batch *b, const double *d_cut, const double *beta, int *run_len,
+                                int *batched);
 
 /* One DA cycle of every experiment i: forecast nsteps (one persistent
  * launch for all), observe (u, v) at npts[i] points (ix[i], iy[i]) with

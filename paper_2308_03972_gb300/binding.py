@@ -70,7 +70,7 @@ SIGNATURES = {
     "lbm_batch_create": (_I, [_P, _I, ctypes.POINTER(_P)]),
     "lbm_batch_forecast": (_I, [_P, _I]),
     "lbm_batch_autotune": (_I, [_P, _P, _P]),
-    "lbm_batch_autotune_analysis": (_I, [_P, _P, _P, _P]),
+    "lbm_batch_autotune_analysis": (_I, [_P, _P, _P, _P, _P]),
     "lbm_batch_cycle": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _P, _P, _I]),
     "lbm_batch_sync": (_I, [_P]),
     "lbm_batch_set_barrier": (_I, [_P, ctypes.c_longlong, _I]),
@@ -515,6 +515,7 @@ class Batch:
 
     def __init__(self, ensembles):
         self.ens = list(ensembles)
+        self.run_batched = [1] * len(self.ens)
         arr = (_P * len(self.ens))(*[e.ctx for e in self.ens])
         out = _P()
         _bcheck(None, load().lbm_batch_create(arr, len(self.ens), ctypes.byref(out)))
@@ -529,16 +530,21 @@ class Batch:
         return t.value, n.value
 
     def autotune_analysis(self, d_cut, beta):
-        """Run length per size class of the batched run analyses; every
-        experiment must be observed. Returns each experiment's run length."""
+        """Run length per size class of the batch's analyses, and for the
+        run-path classes batched or one-by-one launches; every experiment
+        must be observed. Returns each experiment's run length; the launch
+        form per experiment (1 batched, 0 on its own) is left in
+        `self.run_batched`."""
         n = len(self.ens)
         dc = np.ascontiguousarray(d_cut, dtype=np.float64)
         bt = np.ascontiguousarray(beta, dtype=np.float64)
         if dc.shape != (n,) or bt.shape != (n,):
             raise ValueError("d_cut and beta need one value per experiment")
         out = np.zeros(n, dtype=np.int32)
+        form = np.zeros(n, dtype=np.int32)
         p = lambda a: a.ctypes.data_as(_P)  # noqa: E731
-        _bcheck(self.b, load().lbm_batch_autotune_analysis(self.b, p(dc), p(bt), p(out)))
+        _bcheck(self.b, load().lbm_batch_autotune_analysis(self.b, p(dc), p(bt), p(out), p(form)))
+        self.run_batched = form.tolist()
         return out.tolist()
 
     def cycle(self, nsteps, obs, d_cut, beta, use_graph=True):

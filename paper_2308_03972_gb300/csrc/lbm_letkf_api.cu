@@ -58,6 +58,7 @@ struct lbm_ctx {
     double sigma_u = 0.0, sigma_v = 0.0, sigma_r = 1.0;
     int prod = PROD_FP64;  // ensemble-space Gram arithmetic (mixed precision)
     int run_pipe = 0;      // runs per pipelined chunk of the run analysis (0: not pipelined)
+    int run_batched = 1;   // in a batch: run analysis in the batched launches (0: launched on its own)
     int* sweep_hist = nullptr;  // [32] Jacobi sweeps per point (diagnostic)
     bool sweep_stats = false;
     bool observed = false;
@@ -1167,17 +1168,18 @@ int batch_forecast_impl(lbm_batch* b, int nsteps) {
     return LBM_OK;
 }
 
-// The analyses of a batch on stream s: every experiment on the run path in
-// batched launches (kernel J over all their runs, then kernel F over all
-// their grid points, per size class), the others one by one. The plans
-// come from analyze_prepare(..., whole = true).
+// The analyses of a batch on stream s: the experiments on the run path
+// marked batched (the default; the analysis autotuner may unmark a size
+// class) in batched launches (kernel J over all their runs, then kernel F
+// over all their grid points, per size class), the others one by one. The
+// plans come from analyze_prepare(..., whole = true).
 int batch_analyze(lbm_batch* b, const std::vector<AnalysisPlan>& plans, const std::vector<int>& which,
                   cudaStream_t s) {
     std::vector<RunItem> items;
     for (int i : which) {
         lbm_ctx* c = b->ctx[i];
         const AnalysisPlan& pl = plans[i];
-        if (pl.run_len > 0) {
+        if (pl.run_len > 0 && c->run_batched) {
             const bool f32 = is_fp32(c);
             items.push_back(RunItem{f32 ? (float*)c->f[c->cur] : nullptr, f32 ? nullptr : (double*)c->f[c->cur],
                                     c->nx, c->ny, c->k, pl.run_len, pl.maxunion, obs_params(c, pl), pl.d_cut,
@@ -1306,7 +1308,8 @@ int lbm_batch_autotune(lbm_batch* b, int* threads, int* blocks) {
     return LBM_OK;
 }
 
-int lbm_batch_autotune_analysis(lbm_batch* b, const double* d_cut, const double* beta, int* run_len) {
+int lbm_batch_autotune_analysis(lbm_batch* b, const double* d_cut, const double* beta, int* run_len,
+                                int* batched) {
     if (!b) return bfail(nullptr, LBM_EINVAL, "batch is NULL");
     if (!d_cut || !beta) return bfail(b, LBM_EINVAL, "NULL argument");
     const int n = (int)b->ctx.size();
@@ -1346,14 +1349,19 @@ int lbm_batch_autotune_analysis(lbm_batch* b, const double* d_cut, const double*
                 done[i] = 1;
             }
         float best = 1e30f;
-        int best_r = b->ctx[which[0]]->run_len;
-        for (int r : cand) {
+        int best_r = b->ctx[which[0]]->run_len, best_m = 1;
+        // Run-path classes also time the class's analyses launched one
+        // experiment at a time against the batched launches.
+        const int nmodes = cls[i0] < 100 ? 2 : 1;
+        for (int ci = 0; ci < 4 * nmodes && st == LBM_OK; ++ci) {
+            const int r = cand[ci % 4], mode = ci < 4 ? 1 : 0;
             // Each timing analyses copies of the current states in the spare
             // buffers; the states and the observations are not changed.
             std::vector<AnalysisPlan> plans(n);
             for (int i : which) {
                 lbm_ctx* c = b->ctx[i];
                 c->run_len = r;
+                c->run_batched = mode;
                 st = analyze_prepare(c, d_cut[i], beta[i], &plans[i], true);
                 if (st) break;
             }
@@ -1382,9 +1390,13 @@ int lbm_batch_autotune_analysis(lbm_batch* b, const double* d_cut, const double*
             if (tbest < best) {
                 best = tbest;
                 best_r = r;
+                best_m = mode;
             }
         }
-        for (int i : which) b->ctx[i]->run_len = best_r;
+        for (int i : which) {
+            b->ctx[i]->run_len = best_r;
+            b->ctx[i]->run_batched = best_m;
+        }
     }
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
@@ -1399,8 +1411,10 @@ int lbm_batch_autotune_analysis(lbm_batch* b, const double* d_cut, const double*
         b->graph = nullptr;
     }
     b->graph_steps = -1;
-    if (run_len)
-        for (int i = 0; i < n; ++i) run_len[i] = b->ctx[i]->run_len;
+    for (int i = 0; i < n; ++i) {
+        if (run_len) run_len[i] = b->ctx[i]->run_len;
+        if (batched) batched[i] = b->ctx[i]->run_batched;
+    }
     return LBM_OK;
 }
 

@@ -250,10 +250,11 @@ def test_twelve_experiments_match_oracle_at_sampled_points(gpu, prec):
 
 
 def test_analysis_autotuner_keeps_states_and_cycles_match(gpu):
-    """lbm_batch_autotune_analysis: run lengths per size class timed on
-    copies of the states (the states are unchanged), then batch cycles with
-    the chosen run lengths equal to single-context cycles with the same
-    run lengths, bit for bit (same kernels)."""
+    """lbm_batch_autotune_analysis: run lengths and launch forms per size
+    class timed on copies of the states (the states are unchanged), then
+    batch cycles with the chosen run lengths and forms equal to
+    single-context cycles with the same run lengths, bit for bit (same
+    kernels)."""
     picks = [(128, 64, 8, 16.0), (128, 128, 8, 16.0), (256, 32, 8, 32.0), (128, 16, 8, 16.0)]
     made, obs = [], []
     for i, (n, k, no, dc) in enumerate(picks):
@@ -294,6 +295,10 @@ def test_analysis_autotuner_keeps_states_and_cycles_match(gpu):
         # has ensemble-space points (its Jacobi kernel warm-starts along
         # runs): all four are tuned.
         assert all(r in (4, 8, 16, 32) for r in rl)
+        # Launch form per experiment: either for the run-path classes; the
+        # ensemble-space experiment keeps its own launches' default.
+        assert all(m in (0, 1) for m in b.run_batched[:3])
+        assert b.run_batched[3] == 1
         for c in (2, 3):
             b.cycle(10, cycle_obs(c), dcs, betas, use_graph=True)
         b.sync()
