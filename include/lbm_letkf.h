@@ -387,8 +387,9 @@ int lbm_batch_autotune(lbm_batch *b, int *threads, int *blocks);
  * 28, 32). Each class times its analyses at run lengths 4, 8, 16 and 32,
  * best of three, keeping the fastest; a run-path class times two forms at
  * each length: batched (kernel J over every run of the class in one
- * launch, kernel F over every grid point in one launch) and one experiment
- * after another (each with its own launches, as lbm_analyze makes them).
+ * launch, then kernel F per experiment over all its grid points) and one
+ * experiment after another (each with its own launches in chunks of runs,
+ * as lbm_analyze makes them).
  * lbm_batch_cycle then analyses the class in the form chosen; the results
  * are the same in both forms. The timed analyses work on copies of the
  * current states in the spare buffers: states and observations are
@@ -406,9 +407,10 @@ int lbm_batch_autotune_analysis(lbm_batch *b, const double *d_cut, const double 
  * values yo_u[i], yo_v[i] and errors sigma[2i], sigma[2i+1], and the LETKF
  * analysis with d_cut[i], beta[i]. The analyses of experiments on the run
  * path share launches: per size class one launch of kernel J over all
- * their runs and one of kernel F over all their grid points (the analysis
- * scratch of each is then sized for all its runs at once); the others are
- * analysed one by one. With use_graph, once a cycle has run
+ * their runs, then one launch of kernel F per experiment over all its grid
+ * points (the analysis scratch of each is then sized for all its runs at
+ * once); the others, and run-path classes the analysis autotuner found
+ * faster so, are analysed one by one. With use_graph, once a cycle has run
  * uncaptured with the same positions, nsteps, d_cut and beta, the next call
  * captures the whole cycle of all experiments in a CUDA graph and later
  * calls replay it, staging only the new observed values through pinned

@@ -1110,16 +1110,19 @@ __device__ void probe_tail(const RunArgs& ra, const ProbeArgs& pa, int pt, const
 }
 
 // ---- kernels: one experiment, or a batch of experiments ------------------
-// A batch launch covers the runs (kernel J) or grid points (kernel F) of up
-// to kRunBatch experiments of one size class (NS): block b belongs to the
-// experiment e with start[e] <= b < start[e + 1]. The table travels as a
-// kernel parameter.
+// A batch launch of kernel J covers the runs of up to kRunBatch experiments
+// of one size class (NS): block b belongs to the experiment e with
+// jstart[e] <= b < jstart[e + 1]. The table travels as a kernel parameter.
+// Kernel F is launched per experiment: its shared memory depends on the
+// members k, and sizing it for a batch's largest k costs the others
+// occupancy in this latency-bound kernel (a batched F was 12% slower than
+// the per-experiment launches over the seven run-path experiments of the
+// uneven batch, against 5% gained by batching J).
 constexpr int kRunBatch = 16;
 
 struct RunBatch {
     int n;
     int jstart[kRunBatch + 1];  // first run of each experiment
-    int fstart[kRunBatch + 1];  // first grid point of each experiment
     RunArgs ex[kRunBatch];
 };
 
@@ -1144,13 +1147,6 @@ template <int NS, bool PROBE>
 __global__ void __launch_bounds__(32, 12) run_refine_kernel(const __grid_constant__ RunArgs ra,
                                                             const __grid_constant__ ProbeArgs pa) {
     run_refine_body<NS, PROBE>(ra, pa, blockIdx.x);
-}
-
-template <int NS>
-__global__ void __launch_bounds__(32, 12) run_refine_batch_kernel(const __grid_constant__ RunBatch tb) {
-    const int e = batch_item(tb.fstart, tb.n, blockIdx.x);
-    const ProbeArgs none{nullptr, 0, nullptr, nullptr};
-    run_refine_body<NS, false>(tb.ex[e], none, blockIdx.x - tb.fstart[e]);
 }
 
 // G = dY dY^T split into binary32 (hi, lo).
@@ -1350,49 +1346,46 @@ cudaError_t launch_runs(float* f, double* f64, int nx, int ny, int k, const ObsP
     }
 }
 
-// One size class of a batch: kernel J over every run of the experiments,
-// then kernel F over every grid point (binary32 states) or the FP64
-// kernel per experiment (FP64 states), in launches of kRunBatch
-// experiments.
+// One size class of a batch: kernel J over every run of the experiments in
+// launches of kRunBatch experiments, then per experiment kernel F over its
+// grid points (binary32 states) or the FP64 kernel (FP64 states).
 template <int NS>
 cudaError_t launch_runs_batch_ns(const std::vector<RunArgs>& ex, cudaStream_t s) {
     const size_t shJ = (size_t)JLayout<NS>::total * 4;
     int kmax = 0;
     for (const RunArgs& ra : ex) kmax = ra.k > kmax ? ra.k : kmax;
-    const size_t shF = run_f_smem_bytes<NS>(kmax);
     cudaError_t e = cudaFuncSetAttribute(run_jacobi_batch_kernel<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)shJ);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(run_refine_batch_kernel<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shF);
+    e = cudaFuncSetAttribute(run_refine_kernel<NS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)run_f_smem_bytes<NS>(kmax));
     if (e != cudaSuccess) return e;
+    const ProbeArgs none{nullptr, 0, nullptr, nullptr};
     for (size_t i0 = 0; i0 < ex.size(); i0 += kRunBatch) {
         const int n = (int)std::min<size_t>(kRunBatch, ex.size() - i0);
         RunBatch tb{};
         tb.n = n;
-        long long jt = 0, ft = 0;
-        bool fp64 = false;
+        long long jt = 0;
         for (int i = 0; i < n; ++i) {
             tb.ex[i] = ex[i0 + i];
             tb.jstart[i] = (int)jt;
-            tb.fstart[i] = (int)ft;
             jt += tb.ex[i].nruns;
-            ft += (long long)tb.ex[i].nruns * tb.ex[i].R;
-            fp64 = fp64 || tb.ex[i].f64;
-            if (ft > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+            if (jt > 0x7fffffffLL || (long long)tb.ex[i].nruns * tb.ex[i].R > 0x7fffffffLL)
+                return cudaErrorInvalidConfiguration;
         }
         tb.jstart[n] = (int)jt;
-        tb.fstart[n] = (int)ft;
         run_jacobi_batch_kernel<NS><<<(unsigned)jt, 32, shJ, s>>>(tb);
-        if (!fp64) {
-            run_refine_batch_kernel<NS><<<(unsigned)ft, 32, shF, s>>>(tb);
-        } else {
-            for (int i = 0; i < n; ++i) {
-                const RunArgs& ra = tb.ex[i];
+        for (int i = 0; i < n; ++i) {
+            const RunArgs& ra = tb.ex[i];
+            if (ra.f64) {
                 ObsParams o = ra.o;
                 o.sweep_hist = ra.fp64_hist;
                 e = launch_run_fp64(ra.f64, ra.nx, ra.ny, ra.k, o, ra.d_cut, ra.beta, ra.R, 0, ra.nruns, NS, ra.Yg,
                                     ra.lamg, ra.rinfo, kInfo, ra.flags, s);
                 if (e != cudaSuccess) return e;
+            } else {
+                run_refine_kernel<NS, false>
+                    <<<(unsigned)((long long)ra.nruns * ra.R), 32, run_f_smem_bytes<NS>(ra.k), s>>>(ra, none);
             }
         }
         e = cudaGetLastError();
