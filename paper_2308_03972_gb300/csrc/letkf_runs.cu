@@ -63,10 +63,14 @@ struct RunArgs {
     ObsParams o;
     const float2* G2;   // [nobs][nobs] G = dY dY^T as binary32 (hi, lo)
     double d_cut, beta;
+    // Launch constants in binary32, rounded from FP64 on the host: a =
+    // (k-1)/beta, sqrt(a), sqrt(beta), sqrt(k-1).
+    float a_f, sqrt_a_f, sqrt_beta_f, sqrt_k1_f;
     int* flags;
     int run0, nruns;    // runs of this chunk
     float* Yg;          // [chunk cells][NS][NS] basis Y, row-major (Y_ic: component i of vector c)
     float* lamg;        // [chunk cells][NS] eigenvalue estimates
+    double* wg;         // [chunk cells][NS] localisation weights w_c of the union's scalars (kernel J's)
     int* rinfo;         // [chunk runs][1 + 32] union size, then its scalars
     int* fp64_hist;     // sweep histogram of the FP64 Jacobi (double precision), or null
 };
@@ -403,6 +407,7 @@ __device__ __forceinline__ void run_jacobi_body(const RunArgs& ra, int blk) {
         const double w = real ? obs_weight(ra, jc, qc, x, y) : 0.0;
         const float wf = (float)w;
         const bool any = __ballot_sync(kFull, w > 0.0) != 0u;
+        if (any && own) ra.wg[lc * NS + c] = w;  // for kernel F
         if (!any) {
             // No observation in range: nothing to solve (kernel F inflates).
             if (lane == 0) ra.lamg[lc * NS] = -1.0f;  // marker read by kernel F
@@ -655,7 +660,7 @@ __device__ __forceinline__ void run_refine_body(const RunArgs& ra, const ProbeAr
     }
     const size_t cell = (size_t)y * ra.nx + x;
     if (!PROBE) stage_point(ra, dX, cell, lane);
-    const float sbeta = (float)sqrt(ra.beta);
+    const float sbeta = ra.sqrt_beta_f;
     const int* info = ra.rinfo + (size_t)rl * kInfo;
     const int nu = info[0];
     const float lam_mark = ra.lamg[(size_t)lc * NS];
@@ -679,10 +684,8 @@ __device__ __forceinline__ void run_refine_body(const RunArgs& ra, const ProbeAr
         }
         return;
     }
-    const double aa = (k - 1) / ra.beta;
-    const double rs = sqrt(aa);
-    const float rsf = (float)rs;
-    const float sk = (float)sqrt((double)(k - 1));
+    const float rsf = ra.sqrt_a_f;
+    const float sk = ra.sqrt_k1_f;
     const bool own = lane < NS;
     const bool real = lane < nu;
     const int c = lane;
@@ -695,7 +698,7 @@ __device__ __forceinline__ void run_refine_body(const RunArgs& ra, const ProbeAr
     }
     __syncwarp();
     const int gic = real ? gi[c] : 0;
-    const double w = real ? obs_weight(ra, gic / o.nvar, gic % o.nvar, x, y) : 0.0;
+    const double w = real ? ra.wg[(size_t)lc * NS + c] : 0.0;  // kernel J's weight of scalar c
     const float w_h = (float)w;
     const float w_l = (float)(w - (double)w_h);
     if (own) {
@@ -821,12 +824,17 @@ __device__ __forceinline__ void run_refine_body(const RunArgs& ra, const ProbeAr
             }
         }
     }
-    // Matrix functions of S' (observation space).
-    const double dS = (double)lamc + (double)(tcc - ecc * tcc - ecc * ecc * lamc);
-    const double uu = sqrt(aa + dS);
-    const double alpha = 1.0 / (uu * (uu + rs));
-    const double hh = 1.0 / (aa + dS);
+    // Matrix functions of S' (observation space): the diagonal entry s_c of
+    // S' and u_c = sqrt(a + s_c), alpha_c = 1 / (u_c (u_c + sqrt a)),
+    // h_c = 1 / (a + s_c). The probe evaluates them in FP64; the update
+    // uses them in binary32 products, so it evaluates them in binary32.
     if constexpr (PROBE) {
+        const double aa = (k - 1) / ra.beta;
+        const double rs = sqrt(aa);
+        const double dS = (double)lamc + (double)(tcc - ecc * tcc - ecc * ecc * lamc);
+        const double uu = sqrt(aa + dS);
+        const double alpha = 1.0 / (uu * (uu + rs));
+        const double hh = 1.0 / (aa + dS);
         __syncwarp();
         probe_tail<NS>(ra, pa, blk, Ys, Ah, Al, lsq, gi, nu, uu, alpha, hh, lane);
         return;
@@ -834,7 +842,10 @@ __device__ __forceinline__ void run_refine_body(const RunArgs& ra, const ProbeAr
     float t1c = 0.0f;
 #pragma unroll
     for (int l = 0; l < NS; ++l) t1c = fmaf(u[l], dh[l], t1c);  // (Y^T d-hat)_c
-    const float hc = (float)hh, ac = (float)alpha, uc = (float)uu;
+    const float ap = ra.a_f + (lamc + (tcc - ecc * tcc - ecc * ecc * lamc));  // a + s_c
+    const float uc = sqrtf(ap);
+    const float ac = 1.0f / (uc * (uc + rsf));
+    const float hc = 1.0f / ap;
     if (own) {
         vu[c] = uc;
         va[c] = ac;
@@ -1170,7 +1181,7 @@ int run_ns(int maxunion) {
 constexpr size_t kRunScratchBudget = 320ull << 20;  // basis scratch per chunk
 
 long long run_chunk_runs(long long runs, int R, int ns) {
-    const size_t per_run = (size_t)R * run_cell_floats(ns) * 4 + kInfo * 4;
+    const size_t per_run = (size_t)R * (run_cell_floats(ns) * 4 + ns * 8) + kInfo * 4;
     long long c = (long long)(kRunScratchBudget / per_run);
     if (c < 1) c = 1;
     return runs < c ? runs : c;
@@ -1228,6 +1239,7 @@ cudaError_t launch_runs_pipe(RunArgs ra, long long runs, long long pipe, const A
     }
     float* Yb[2] = {ra.Yg, ra.Yg + (size_t)pipe * ra.R * NS * NS};
     float* Lb[2] = {ra.lamg, ra.lamg + (size_t)pipe * ra.R * NS};
+    double* Wb[2] = {ra.wg, ra.wg + (size_t)pipe * ra.R * NS};
     int* Ib[2] = {ra.rinfo, ra.rinfo + (size_t)pipe * kInfo};
     if ((e = cudaEventRecord(aux.start, s)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(aux.s2, aux.start, 0)) != cudaSuccess) return e;
@@ -1240,6 +1252,7 @@ cudaError_t launch_runs_pipe(RunArgs ra, long long runs, long long pipe, const A
         rb.nruns = (int)nr;
         rb.Yg = Yb[b];
         rb.lamg = Lb[b];
+        rb.wg = Wb[b];
         rb.rinfo = Ib[b];
         if (c >= 2 && (e = cudaStreamWaitEvent(aux.s2, aux.ref_done[b], 0)) != cudaSuccess) return e;
         run_jacobi_kernel<NS><<<(unsigned)nr, 32, shJ, aux.s2>>>(rb);
@@ -1261,8 +1274,8 @@ cudaError_t launch_runs_pipe(RunArgs ra, long long runs, long long pipe, const A
 }
 
 // Run arguments of one analysis: the scratch laid out for `chunk` runs per
-// pass (G2, then the basis, eigenvalue estimates and union lists of a
-// chunk), and the preparation kernels queued (the binary32 copy of dY for a
+// pass (G2, then the basis, eigenvalue estimates, weights and union lists
+// of a chunk), and the preparation kernels queued (the binary32 copy of dY for a
 // binary32 state, the split Gram).
 cudaError_t run_setup(float* f, double* f64, int nx, int ny, int k, const ObsParams& o, double d_cut, double beta,
                       int run_len, int maxunion, int* flags, void* scratch, long long chunk, RunArgs& ra,
@@ -1280,6 +1293,8 @@ cudaError_t run_setup(float* f, double* f64, int nx, int ny, int k, const ObsPar
     p += ((size_t)chunk * run_len * ns * ns * 4 + 255) / 256 * 256;
     float* lamg = reinterpret_cast<float*>(p);
     p += ((size_t)chunk * run_len * ns * 4 + 255) / 256 * 256;
+    double* wg = reinterpret_cast<double*>(p);
+    p += ((size_t)chunk * run_len * ns * 8 + 255) / 256 * 256;
     int* rinfo = reinterpret_cast<int*>(p);
     // dY in binary32 for the transform (the same copy the chunked path makes).
     if (f) {
@@ -1297,11 +1312,16 @@ cudaError_t run_setup(float* f, double* f64, int nx, int ny, int k, const ObsPar
     ra.G2 = G2;
     ra.d_cut = d_cut;
     ra.beta = beta;
+    ra.a_f = (float)((k - 1) / beta);
+    ra.sqrt_a_f = (float)std::sqrt((k - 1) / beta);
+    ra.sqrt_beta_f = (float)std::sqrt(beta);
+    ra.sqrt_k1_f = (float)std::sqrt((double)(k - 1));
     ra.flags = flags;
     ra.run0 = 0;
     ra.nruns = 0;
     ra.Yg = Yg;
     ra.lamg = lamg;
+    ra.wg = wg;
     ra.rinfo = rinfo;
     ra.fp64_hist = nullptr;
     if (f64) {
@@ -1403,8 +1423,9 @@ size_t run_scratch_bytes(int nx, int ny, int nobs, int run_len, int maxunion, bo
     const size_t g2 = ((size_t)nobs * nobs * sizeof(float2) + 255) / 256 * 256;
     const size_t yb = ((size_t)chunk * run_len * ns * ns * 4 + 255) / 256 * 256;
     const size_t lb = ((size_t)chunk * run_len * ns * 4 + 255) / 256 * 256;
+    const size_t wb = ((size_t)chunk * run_len * ns * 8 + 255) / 256 * 256;
     const size_t ib = (size_t)chunk * kInfo * 4;
-    return g2 + yb + lb + ib;
+    return g2 + yb + lb + wb + ib;
 }
 
 cudaError_t launch_analyze_runs(float* f, int nx, int ny, int k, const ObsParams& o, double d_cut,
