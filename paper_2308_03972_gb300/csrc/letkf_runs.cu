@@ -743,18 +743,23 @@ __device__ __forceinline__ void run_refine_body(const RunArgs& ra, const ProbeAr
     // i..i+RG-1 of column j are entries i..i+RG-1 of row j. A group reads up
     // to RG - (NS mod RG) floats past a row's end; what follows each matrix
     // in this layout is in bounds and the extra rows are not stored.
-    constexpr int RG = NS >= 16 ? 16 : 8;  // rows per group: RG / 2 independent sums
+    constexpr int RG = NS >= 16 ? 16 : 8;  // rows per group of E and T: RG / 2 independent sums
     constexpr int NQ = RG / 2;
-    for (int i0 = 0; i0 < NS; i0 += RG) {
-        f2x S[NQ], C[NQ];
+    // R: all rows in one group (NS / 2 independent sums per lane; F is
+    // stalled on fixed-latency dependences, and this fits the registers
+    // of 3 warps per sub-partition). E and T in one group need more
+    // registers and measured slower.
+    constexpr int RG1 = NS, NQ1 = RG1 / 2;
+    for (int i0 = 0; i0 < NS; i0 += RG1) {
+        f2x S[NQ1], C[NQ1];
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) S[q] = C[q] = 0ull;
+        for (int q = 0; q < NQ1; ++q) S[q] = C[q] = 0ull;
 #pragma unroll 2
         for (int j = 0; j < NS; ++j) {
             const float uj = own ? Ys[j * NS + c] : 0.0f;  // Y_jc
             const f2x Y2 = f2pack(uj, uj), NY2 = f2pack(-uj, -uj);
 #pragma unroll
-            for (int g = 0; g < RG / 4; ++g) {
+            for (int g = 0; g < RG1 / 4; ++g) {
                 const ulonglong2 h = *reinterpret_cast<const ulonglong2*>(Ah + j * NS + i0 + 4 * g);
                 const ulonglong2 l = *reinterpret_cast<const ulonglong2*>(Al + j * NS + i0 + 4 * g);
                 df2_acc(S[2 * g], C[2 * g], h.x, l.x, Y2, NY2);
@@ -762,7 +767,7 @@ __device__ __forceinline__ void run_refine_body(const RunArgs& ra, const ProbeAr
             }
         }
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) {
+        for (int q = 0; q < NQ1; ++q) {
             float s2[2], c2[2];
             f2unpack(S[q], s2[0], s2[1]);
             f2unpack(C[q], c2[0], c2[1]);
