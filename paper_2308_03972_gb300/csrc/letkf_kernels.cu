@@ -1877,15 +1877,20 @@ __global__ void __launch_bounds__(32 * kGramPts, 1) local_gram_fp64_kernel(int n
 // Double-binary32 Gram (PROD_DF32, the default of a mixed-precision
 // context): the C and b of the FP64 Gram pass to FP64-class accuracy on the
 // binary32 units. The staged rows are split once into binary32 halves
-// (y = yh + yl, exact to 2^-48); each lane's weighted column value
-// wy = rho y_n is formed in FP64 and split likewise; every product
-// (yh + yl)(wyh + wyl) enters a double-binary32 sum: yh wyh exactly
-// (its rounding error recovered with one FMA), the cross terms yh wyl and
-// yl wyh in binary32 (relative 2^-48), yl wyl dropped (2^-48 of the
-// product); the sum carries its error through TwoSum (Knuth; Dekker 1971;
-// Ogita, Rump and Oishi 2005). Two rows per packed .f32x2 instruction, as
-// in the refinement. Output layout and roles as the FP64 pass (C64, b64;
-// b stays FP64).
+// (y = yh + yl, exact to 2^-48), and so is each grid point's weight of a
+// row (rho = rh + rl), when the row is staged. A lane's weighted column
+// value wy = rho y_n is then formed in double-binary32: rh yh exactly (its
+// rounding error recovered with one FMA) plus the cross terms rh yl and
+// rl yh in binary32, rl yl dropped (relative ~3 2^-48 in all), renormalised
+// into wyh + wyl. Every product (yh + yl)(wyh + wyl) enters a
+// double-binary32 sum: yh wyh exactly (its error recovered with one FMA),
+// the cross terms yh wyl and yl wyh in binary32 (relative 2^-48), yl wyl
+// dropped (2^-48 of the product); the sum carries its error through TwoSum
+// (Knuth; Dekker 1971; Ogita, Rump and Oishi 2005). Two rows per packed
+// .f32x2 instruction, as in the refinement. b = sum rho d y stays FP64, with
+// rho d formed once per grid point and row. GB300 issues FP64 at 1/64 of
+// the binary32 rate, so no FP64 operation is left per lane and output
+// entry. Output layout and roles as the FP64 pass (C64, b64).
 template <int K>
 __global__ void __launch_bounds__(32 * kGramPts, 1) local_gram_df_kernel(int nx, int ny, int k,
                                                                         ObsParams o, double d_cut,
@@ -1900,8 +1905,9 @@ __global__ void __launch_bounds__(32 * kGramPts, 1) local_gram_df_kernel(int nx,
     __shared__ double Ys[KC][K];
     __shared__ __align__(8) float Yh[KC][K];
     __shared__ __align__(8) float Yl[KC][K];
-    __shared__ double Ws[kGramPts][KC];
-    __shared__ double Ds[KC];
+    __shared__ double WDs[kGramPts][KC];          // rho d of (point, row)
+    __shared__ __align__(8) float Wh[kGramPts][KC];  // rho = Wh + Wl
+    __shared__ __align__(8) float Wl[kGramPts][KC];
     __shared__ int wcount[kGramPts];
     __shared__ int pcnt[kGramPts];
     extern __shared__ int U[];
@@ -1935,33 +1941,38 @@ __global__ void __launch_bounds__(32 * kGramPts, 1) local_gram_df_kernel(int nx,
             }
             if (threadIdx.x < KC * kGramPts) {
                 const int q = threadIdx.x / KC, rr = threadIdx.x % KC, r = r0 + rr;
-                double wv = 0.0;
+                double wv = 0.0, dv = 0.0;
                 if (r < rows && li0 + q < ncell) {
                     const int cell = cell0 + li0 + q;
                     const double sg = local_weight(o, U[r / nv], cell % nx, cell / nx, nx, ny, d_cut);
                     const int qv = r % nv;
                     const double l = sg / (qv == 0 ? o.sigma_u : (qv == 1 ? o.sigma_v : o.sigma_r));
                     wv = l * l;
+                    dv = o.d[nv * U[r / nv] + qv];
                 }
-                Ws[q][rr] = wv;
-            }
-            if (threadIdx.x < KC) {
-                const int r = r0 + threadIdx.x;
-                Ds[threadIdx.x] = r < rows ? o.d[nv * U[r / nv] + r % nv] : 0.0;
+                const float h = (float)wv;
+                Wh[q][rr] = h;
+                Wl[q][rr] = (float)(wv - (double)h);
+                WDs[q][rr] = wv * dv;
             }
             __syncthreads();
             for (int rr = 0; rr < KC; ++rr) {
-                const double wl = Ws[w][rr];
-                if (wl == 0.0) continue;
+                const float rhh = Wh[w][rr], rhl = Wl[w][rr];
+                if (rhh == 0.0f) continue;  // rho = 0 (rh = 0 only then)
                 if (cb == 0) {
+                    const double wd = WDs[w][rr];
 #pragma unroll
                     for (int c = 0; c < NBC; ++c)
-                        if (lane + 32 * c < K) bacc[c] += wl * Ds[rr] * Ys[rr][lane + 32 * c];
+                        if (lane + 32 * c < K) bacc[c] = fma(wd, Ys[rr][lane + 32 * c], bacc[c]);
                 }
                 if (act) {
-                    const double wy = wl * Ys[rr][cb + col];
-                    const float wh = (float)wy;
-                    const float wlo = (float)(wy - (double)wh);
+                    // wy = rho y_n in double-binary32, renormalised (|e| << |p|).
+                    const float yh = Yh[rr][cb + col], yl = Yl[rr][cb + col];
+                    const float p = __fmul_rn(rhh, yh);
+                    float e = __fmaf_rn(rhh, yh, -p);
+                    e = __fmaf_rn(rhh, yl, __fmaf_rn(rhl, yh, e));
+                    const float wh = __fadd_rn(p, e);
+                    const float wlo = __fsub_rn(e, __fsub_rn(wh, p));
                     const f2x WH = f2pack(wh, wh), NWH = f2pack(-wh, -wh), WL = f2pack(wlo, wlo);
                     const f2x* yh2 = reinterpret_cast<const f2x*>(&Yh[rr][rh * MR]);
                     const f2x* yl2 = reinterpret_cast<const f2x*>(&Yl[rr][rh * MR]);

@@ -229,22 +229,34 @@ def test_double_binary32_products_are_fp64_class(k, p, seed):
 @pytest.mark.parametrize("k,p,seed", [(32, 104, 11), (64, 200, 12), (128, 90, 13)])
 def test_double_binary32_gram_is_fp64_class(k, p, seed):
     """The arithmetic of the double-binary32 Gram pass (LBM_PROD_DF32):
-    C = sum_r rho_r y_r y_r^T with the FP64 rows split into binary32 halves,
-    each lane's weighted value w y_n formed in FP64 and split likewise,
-    yh (wy)h accumulated with its exact product error, the cross terms yh
-    (wy)l and yl (wy)h in binary32, yl (wy)l dropped. It must match the
-    FP64 Gram to a few 1e-13 of |C| over sums of up to 200 rows (the
-    binary32 compensation term limits it; binary32 products give ~1e-7)."""
+    C = sum_r rho_r y_r y_r^T with the FP64 rows and weights split into
+    binary32 halves, each lane's weighted value rho y_n formed in
+    double-binary32 (rh yh with its exact product error, plus rh yl and
+    rl yh, renormalised into (wy)h + (wy)l), yh (wy)h accumulated with its
+    exact product error, the cross terms yh (wy)l and yl (wy)h in binary32,
+    yl (wy)l dropped. It must match the FP64 Gram to a few 1e-13 of |C|
+    over sums of up to 200 rows (the binary32 compensation term limits it;
+    binary32 products give ~1e-7)."""
     dY, rho, d, a = _problem(k, p, seed)
     f = np.float32
     Yh = dY.astype(f)
     Yl = (dY - Yh.astype(np.float64)).astype(f)
     s = np.zeros((k, k), f)
     c = np.zeros((k, k), f)
+    d64 = np.float64
     for r in range(p):
-        wy = rho[r] * dY[r, :]           # FP64, one value per output column n
-        wh = wy.astype(f)
-        wl = (wy - wh.astype(np.float64)).astype(f)
+        # rho y_n in double-binary32, one value per output column n; each
+        # binary32 rounding is taken from the exact FP64 value (a product
+        # of two binary32 numbers is exact in FP64).
+        rh = f(rho[r])
+        rl = f(rho[r] - d64(rh))
+        yh, yl = Yh[r, :], Yl[r, :]
+        pr = (rh * yh).astype(f)
+        e = (d64(rh) * yh.astype(d64) - pr.astype(d64)).astype(f)  # exact error of rh yh
+        e = (d64(rl) * yh.astype(d64) + e.astype(d64)).astype(f)
+        e = (d64(rh) * yl.astype(d64) + e.astype(d64)).astype(f)
+        wh = (pr + e).astype(f)
+        wl = (e - (wh - pr).astype(f)).astype(f)
         s, c = _df_acc(s, c, Yh[r, :][:, None], Yl[r, :][:, None], wh[None, :])
         # c += yh (wy)l as one FMA.
         c = (c.astype(np.float64) + Yh[r, :][:, None].astype(np.float64) * wl[None, :]).astype(f)
