@@ -1,6 +1,7 @@
 // Device helpers shared by the LETKF translation units (sm_103a). Internal
 // linkage: every translation unit that includes this header gets its own copy.
 #pragma once
+#include <cmath>
 #include <cstdint>
 
 namespace lbmgpu {
@@ -20,6 +21,19 @@ __device__ __forceinline__ int min_image(int d, int n) {
     if (d > n / 2) d -= n;
     if (d < -(n / 2)) d += n;
     return d;
+}
+
+// Support prefilter of the local-set test on integers: dx^2 + dy^2 is an
+// exact integer, and for values below 2^53 (distances below 9.4e7 cells)
+// d2 <= floor((2 d_cut + 1)^2) decides exactly as the FP64 comparison of
+// d2 with (2 d_cut + 1)^2, on the integer units instead of GB300's
+// 1/64-rate FP64 pipe.
+__device__ __forceinline__ long long dist2(int dx, int dy) {
+    return (long long)dx * dx + (long long)dy * dy;
+}
+__host__ __device__ __forceinline__ long long support_lim2(double d_cut) {
+    const double l2 = (2.0 * d_cut + 1.0) * (2.0 * d_cut + 1.0);
+    return l2 >= 9.0e18 ? 0x7fffffffffffffffLL : (long long)floor(l2);
 }
 
 // Gaspari-Cohn weight (Section 3.2.2), both branches in nested (Horner) form.

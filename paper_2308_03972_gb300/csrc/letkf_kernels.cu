@@ -115,7 +115,7 @@ __device__ __forceinline__ void record_sweeps(const ObsParams& o, int sweeps, in
 __device__ int local_set(const ObsParams& o, int x, int y, int nx, int ny, double d_cut, int lane,
                          int* lidx, double* lsq, int cap) {
     int count = 0;
-    const double lim2 = (2.0 * d_cut + 1.0) * (2.0 * d_cut + 1.0);
+    const long long lim2 = support_lim2(d_cut);
     for (int j0 = 0; j0 < o.npts; j0 += 32) {
         const int j = j0 + lane;
         bool in = false;
@@ -123,10 +123,10 @@ __device__ int local_set(const ObsParams& o, int x, int y, int nx, int ny, doubl
         if (j < o.npts) {
             const int dx = min_image(o.ix[j] - x, nx);
             const int dy = min_image(o.iy[j] - y, ny);
-            const double d2 = (double)dx * dx + (double)dy * dy;
             // Integer prefilter well outside the support (r > 2 d_cut + 1);
             // the decision itself is r / d_cut < 2 in FP64.
-            if (d2 <= lim2) {
+            if (dist2(dx, dy) <= lim2) {
+                const double d2 = (double)dx * dx + (double)dy * dy;
                 const double dist = sqrt(d2) / d_cut;
                 if (dist < 2.0) {
                     g = gaspari_cohn(dist);
@@ -1250,7 +1250,21 @@ struct MixScratch {
     float* big;    // [chunk][4][nm][ld] kernel (B)'s A and A Y halves when nm > NMID, or null
     double* C64;   // [chunk][k][k] a I + Yh^T Yh from the FP64 Gram pass, or null
     double* b64;   // [chunk][k] Yh^T d-hat from the same pass, or null
+    // Double-binary32 Gram pass: C as two binary32 planes in C64's space,
+    // C32 = the high halves ([chunk][k][k], C rounded to binary32) and Clo
+    // the low ones (C = C32 + Clo to FP64-class accuracy); b in b64.
+    float* Clo;
 };
+
+// The double-binary32 pass's view of a scratch carved for 8-byte elements.
+__host__ __device__ inline MixScratch mix_scratch_df2(MixScratch m, long long chunk, int kg) {
+    if (m.C64) {
+        m.C32 = reinterpret_cast<float*>(m.C64);
+        m.Clo = m.C32 + (size_t)chunk * kg * kg;
+        m.C64 = nullptr;
+    }
+    return m;
+}
 
 // Row stride of the basis scratch: 128-byte rows for the register Jacobi.
 __host__ __device__ inline int mix_xr(int nm) { return nm <= NREG ? NREG : (nm <= NMID ? NMID : NMAX); }
@@ -1304,6 +1318,7 @@ __host__ __device__ inline MixScratch mix_scratch_at(void* base, long long chunk
     p += (size_t)chunk * kg * kg * gsz;
     m.b32 = (kg && gsz == 4) ? reinterpret_cast<float*>(p) : nullptr;
     m.b64 = (kg && gsz == 8) ? reinterpret_cast<double*>(p) : nullptr;
+    m.Clo = nullptr;
     p += (size_t)chunk * kg * gsz;
     m.big = nm > NMID ? reinterpret_cast<float*>(p) : nullptr;
     return m;
@@ -1336,11 +1351,11 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
 // sqrt(G(r / d_cut)) of observation point j seen from (x, y), 0 outside the
 // support: the same FP64 operations as local_set.
 __device__ __forceinline__ double local_weight(const ObsParams& o, int j, int x, int y, int nx,
-                                               int ny, double d_cut) {
+                                               int ny, double d_cut, long long lim2) {
     const int dx = min_image(o.ix[j] - x, nx);
     const int dy = min_image(o.iy[j] - y, ny);
+    if (dist2(dx, dy) > lim2) return 0.0;  // lim2 = support_lim2(d_cut)
     const double d2 = (double)dx * dx + (double)dy * dy;
-    if (d2 > (2.0 * d_cut + 1.0) * (2.0 * d_cut + 1.0)) return 0.0;
     const double dist = sqrt(d2) / d_cut;
     if (!(dist < 2.0)) return 0.0;
     const double g = gaspari_cohn(dist);
@@ -1354,6 +1369,7 @@ __device__ __forceinline__ double local_weight(const ObsParams& o, int j, int x,
 __device__ int gram_merge(const ObsParams& o, int nx, int ny, double d_cut, int cell0, int li0, int ncell,
                           int* U, int* pcnt, int* wcount) {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long lim2 = support_lim2(d_cut);
     if (threadIdx.x < kGramPts) pcnt[threadIdx.x] = 0;
     __syncthreads();
     int total = 0;
@@ -1364,7 +1380,7 @@ __device__ int gram_merge(const ObsParams& o, int nx, int ny, double d_cut, int 
             for (int q = 0; q < kGramPts; ++q) {
                 if (li0 + q >= ncell) break;
                 const int cell = cell0 + li0 + q;
-                if (local_weight(o, j, cell % nx, cell / nx, nx, ny, d_cut) > 0.0) bits |= 1u << q;
+                if (local_weight(o, j, cell % nx, cell / nx, nx, ny, d_cut, lim2) > 0.0) bits |= 1u << q;
             }
         }
         const bool in = bits != 0u;
@@ -1414,6 +1430,7 @@ __global__ void __launch_bounds__(32 * kGramPts, 1) local_gram_kernel(int nx, in
     const int nv = o.nvar;
 
     const int total = gram_merge(o, nx, ny, d_cut, cell0, li0, ncell, U, pcnt, wcount);
+    const long long lim2 = support_lim2(d_cut);
     // Only grid points in the ensemble-space form (p >= k) read C and b.
     bool any_ens = false;
     for (int q = 0; q < kGramPts; ++q) any_ens |= pcnt[q] * nv >= k;
@@ -1443,7 +1460,7 @@ __global__ void __launch_bounds__(32 * kGramPts, 1) local_gram_kernel(int nx, in
                 float wv = 0.0f;
                 if (r < rows && li0 + q < ncell) {
                     const int cell = cell0 + li0 + q;
-                    const double sg = local_weight(o, U[r / nv], cell % nx, cell / nx, nx, ny, d_cut);
+                    const double sg = local_weight(o, U[r / nv], cell % nx, cell / nx, nx, ny, d_cut, lim2);
                     const int qv = r % nv;
                     const double l = sg / (qv == 0 ? o.sigma_u : (qv == 1 ? o.sigma_v : o.sigma_r));
                     wv = (float)(l * l);
@@ -1585,6 +1602,7 @@ __global__ void __launch_bounds__(32 * kGramPts, 1)
     const int nv = o.nvar;
 
     const int total = gram_merge(o, nx, ny, d_cut, cell0, li0, ncell, U, pcnt, wcount);
+    const long long lim2 = support_lim2(d_cut);
     // Only grid points in the ensemble-space form (p >= k) read C and b.
     bool any_ens = false;
     for (int q = 0; q < kGramPts; ++q) any_ens |= pcnt[q] * nv >= k;
@@ -1639,7 +1657,7 @@ __global__ void __launch_bounds__(32 * kGramPts, 1)
                 float wv = 0.0f;
                 if (rr < nr && li0 + q < ncell) {
                     const int cell = cell0 + li0 + q;
-                    const double sg = local_weight(o, U[r / nv], cell % nx, cell / nx, nx, ny, d_cut);
+                    const double sg = local_weight(o, U[r / nv], cell % nx, cell / nx, nx, ny, d_cut, lim2);
                     const int qv = r % nv;
                     const double l = sg / (qv == 0 ? o.sigma_u : (qv == 1 ? o.sigma_v : o.sigma_r));
                     wv = (float)(l * l);
@@ -1805,6 +1823,7 @@ __global__ void __launch_bounds__(32 * kGramPts, 1) local_gram_fp64_kernel(int n
     const int nv = o.nvar;
     const double sig[3] = {o.sigma_u, o.sigma_v, o.sigma_r};
     const int total = gram_merge(o, nx, ny, d_cut, cell0, li0, ncell, U, pcnt, wcount);
+    const long long lim2 = support_lim2(d_cut);
     bool any_ens = false;
     for (int q = 0; q < kGramPts; ++q) any_ens |= pcnt[q] * nv >= k;
     if (!any_ens) return;
@@ -1831,7 +1850,7 @@ __global__ void __launch_bounds__(32 * kGramPts, 1) local_gram_fp64_kernel(int n
                 double wv = 0.0;
                 if (r < rows && li0 + q < ncell) {
                     const int cell = cell0 + li0 + q;
-                    const double sg = local_weight(o, U[r / nv], cell % nx, cell / nx, nx, ny, d_cut);
+                    const double sg = local_weight(o, U[r / nv], cell % nx, cell / nx, nx, ny, d_cut, lim2);
                     const double l = sg / sig[r % nv];
                     wv = l * l;
                 }
@@ -1874,6 +1893,21 @@ __global__ void __launch_bounds__(32 * kGramPts, 1) local_gram_fp64_kernel(int n
         if (lane + 32 * c < k) sc.b64[(size_t)li * k + lane + 32 * c] = bacc[c];
 }
 
+// A double-binary32 sum (s, c), plus (ah + al) when diag, renormalised into
+// binary32 high and low halves (Fast2Sum: the compensated sum's s dominates).
+__device__ __forceinline__ void df_pair_out(float s, float c, bool diag, float ah, float al, float& hi,
+                                            float& lo) {
+    if (diag) {
+        float t, e;
+        two_sum(s, ah, t, e);
+        c = __fadd_rn(c, __fadd_rn(e, al));
+        s = t;
+    }
+    const float h = __fadd_rn(s, c);
+    hi = h;
+    lo = __fsub_rn(c, __fsub_rn(h, s));
+}
+
 // Double-binary32 Gram (PROD_DF32, the default of a mixed-precision
 // context): the C and b of the FP64 Gram pass to FP64-class accuracy on the
 // binary32 units. The staged rows are split once into binary32 halves
@@ -1890,7 +1924,10 @@ __global__ void __launch_bounds__(32 * kGramPts, 1) local_gram_fp64_kernel(int n
 // .f32x2 instruction, as in the refinement. b = sum rho d y stays FP64, with
 // rho d formed once per grid point and row. GB300 issues FP64 at 1/64 of
 // the binary32 rate, so no FP64 operation is left per lane and output
-// entry. Output layout and roles as the FP64 pass (C64, b64).
+// entry. C goes out as renormalised binary32 pairs, high and low halves in
+// two planes (MixScratch::C32, Clo), so that kernel (A) reads C rounded to
+// binary32 and kernel (B) the pair without FP64 conversions; b stays FP64
+// (b64).
 template <int K>
 __global__ void __launch_bounds__(32 * kGramPts, 1) local_gram_df_kernel(int nx, int ny, int k,
                                                                         ObsParams o, double d_cut,
@@ -1915,6 +1952,8 @@ __global__ void __launch_bounds__(32 * kGramPts, 1) local_gram_df_kernel(int nx,
     const int li0 = blockIdx.x * kGramPts;
     const int nv = o.nvar;
     const int total = gram_merge(o, nx, ny, d_cut, cell0, li0, ncell, U, pcnt, wcount);
+    const long long lim2 = support_lim2(d_cut);
+    const float aah = (float)aa, aal = (float)(aa - (double)aah);  // a = aah + aal
     bool any_ens = false;
     for (int q = 0; q < kGramPts; ++q) any_ens |= pcnt[q] * nv >= k;
     if (!any_ens) return;
@@ -1944,7 +1983,7 @@ __global__ void __launch_bounds__(32 * kGramPts, 1) local_gram_df_kernel(int nx,
                 double wv = 0.0, dv = 0.0;
                 if (r < rows && li0 + q < ncell) {
                     const int cell = cell0 + li0 + q;
-                    const double sg = local_weight(o, U[r / nv], cell % nx, cell / nx, nx, ny, d_cut);
+                    const double sg = local_weight(o, U[r / nv], cell % nx, cell / nx, nx, ny, d_cut, lim2);
                     const int qv = r % nv;
                     const double l = sg / (qv == 0 ? o.sigma_u : (qv == 1 ? o.sigma_v : o.sigma_r));
                     wv = l * l;
@@ -1987,7 +2026,9 @@ __global__ void __launch_bounds__(32 * kGramPts, 1) local_gram_df_kernel(int nx,
             __syncthreads();
         }
         if (li < ncell && act) {
-            double* C = sc.C64 + (size_t)li * k * k;
+            // C = (s, c) + a I as renormalised binary32 pairs (high, low).
+            float* Ch = sc.C32 + (size_t)li * k * k;
+            float* Cl = sc.Clo + (size_t)li * k * k;
             const int n = cb + col;
 #pragma unroll
             for (int m = 0; m < MR / 2; ++m) {
@@ -1995,9 +2036,14 @@ __global__ void __launch_bounds__(32 * kGramPts, 1) local_gram_df_kernel(int nx,
                 f2unpack(S[m], s0, s1);
                 f2unpack(Cc[m], c0, c1);
                 const int row0 = rh * MR + 2 * m;
-                if (row0 < k && n < k) C[(size_t)row0 * k + n] = df_value(s0, c0) + (row0 == n ? aa : 0.0);
-                if (row0 + 1 < k && n < k)
-                    C[(size_t)(row0 + 1) * k + n] = df_value(s1, c1) + (row0 + 1 == n ? aa : 0.0);
+                if (row0 < k && n < k) {
+                    const size_t e0 = (size_t)row0 * k + n;
+                    df_pair_out(s0, c0, row0 == n, aah, aal, Ch[e0], Cl[e0]);
+                }
+                if (row0 + 1 < k && n < k) {
+                    const size_t e1 = (size_t)(row0 + 1) * k + n;
+                    df_pair_out(s1, c1, row0 + 1 == n, aah, aal, Ch[e1], Cl[e1]);
+                }
             }
         }
     }
@@ -2461,6 +2507,14 @@ __global__ void __launch_bounds__(32 * NW) analyze_mixed_kernel(float* __restric
             const double sl = sm.lsq[c];
             for (int i = 0; i < n; ++i)
                 put(i, c, sm.lsq[i] * o.G[(size_t)sm.lidx[i] * nobs + oc] * sl);
+        } else if (sc.Clo) {
+            const float* Cp = sc.C32 + (size_t)li * k * k;
+            const float* Cl = sc.Clo + (size_t)li * k * k;
+            for (int i = 0; i < n; ++i) {
+                sm.Ah[i * ld + c] = Cp[i * k + c];
+                sm.Al[i * ld + c] = Cl[i * k + c];
+            }
+            sm.vb[c] = sc.b64[(size_t)li * k + c];
         } else if (sc.C32) {
             const float* Cp = sc.C32 + (size_t)li * k * k;
             for (int i = 0; i < n; ++i) {
@@ -2497,42 +2551,47 @@ __global__ void __launch_bounds__(32 * NW) analyze_mixed_kernel(float* __restric
 
     if (obs_space) {
         // Functions of a + S: h = 1/(a+s) for the weights, g(s) = q[s, 0] with
-        // q(s) = (a+s)^{-1/2} for the square root. u_i = sqrt(a + s_ii).
-        const double r = sqrt(aa);
+        // q(s) = (a+s)^{-1/2} for the square root. u_i = sqrt(a + s_ii). The
+        // scalars u_i, alpha_i and h_i enter binary32 products only, so they
+        // are evaluated in binary32 (GB300's FP64 rate is 1/64 of it).
+        const float af = (float)aa;
+        const float rf = sqrtf(af);
+        // d-hat in binary32, once (t2f is free until t2 is formed).
+        for (int l = tid; l < n; l += NTH) sm.t2f[l] = (float)sm.ldh[l];
+        point_sync<NW>();
         for_cols<WIDE, NW>(tid, n, [&](int c) {
-            const double sii = sm.dS[c];
-            const double u = sqrt(aa + sii);
-            sm.vu[c] = (float)u;
-            sm.vinv[c] = (float)(1.0 / (u * (u + r)));  // alpha_i
-            sm.vb[c] = 1.0 / (aa + sii);       // h_i = 1 / u_i^2
+            const float ap = af + (float)sm.dS[c];  // a + s_ii
+            const float u = sqrtf(ap);
+            sm.vu[c] = u;
+            sm.vinv[c] = 1.0f / (u * (u + rf));  // alpha_i
+            sm.vf[c] = 1.0f / ap;                // h_i = 1 / u_i^2 (vf is free until v)
             // t1 = Y^T d-hat (binary32 transform product).
             float t = 0.0f;
-            for (int l = 0; l < n; ++l) t += Y32[l * ld + c] * (float)sm.ldh[l];
+            for (int l = 0; l < n; ++l) t += Y32[l * ld + c] * sm.t2f[l];
             sm.t1f[c] = t;
         });
         point_sync<NW>();
         for_cols<WIDE, NW>(tid, n, [&](int c) {
             // t2 = h(S) t1 with h(S)_ii = h_i, h(S)_ij = -s_ij h_i h_j, and the
             // basis factor: minus E o (h_i + h_j)/2.
-            const float hi = (float)sm.vb[c];
+            const float hi = sm.vf[c];
             float t = 0.0f, te = 0.0f;
             for (int j = 0; j < n; ++j) {
-                const float hj = (float)sm.vb[j];
+                const float hj = sm.vf[j];
                 if (j != c) t += Soff[c * ld + j] * (hj * sm.t1f[j]);
                 te += E32[c * ld + j] * (0.5f * (hi + hj)) * sm.t1f[j];
             }
-            sm.t2f[c] = hi * (sm.t1f[c] - t) - te;
+            sm.t2f[c] = hi * (sm.t1f[c] - t) - te;  // d-hat in t2f is read in the loop above only
             // g(S) in binary32: diagonal -alpha_i / r, off-diagonal
             // s_ij (u_i + u_j + r) alpha_i alpha_j / (r (u_i + u_j)).
-            const float ai = (float)sm.vinv[c];
-            const float ui = (float)sm.vu[c];
-            const float rf = (float)r;
+            const float ai = sm.vinv[c];
+            const float ui = sm.vu[c];
             const float gc = -ai / rf;
             for (int i = 0; i < n; ++i) {
                 float v;
-                const float aj = (float)sm.vinv[i];
+                const float aj = sm.vinv[i];
                 if (i == c) {
-                    v = (float)(-sm.vinv[c] / r);
+                    v = gc;
                 } else {
                     const float uj = (float)sm.vu[i];
                     v = Soff[i * ld + c] * (ui + uj + rf) * ai * aj / (rf * (ui + uj));
@@ -2619,13 +2678,16 @@ __global__ void __launch_bounds__(32 * NW) analyze_mixed_kernel(float* __restric
             for (int a = 0; a < 9; ++a) fc[a * plane + m] = acc[a];
         }
     } else {
-        // Functions of S directly: 1/lambda for P-tilde, lambda^{-1/2} for W.
+        // Functions of S directly: 1/lambda for P-tilde, lambda^{-1/2} for W,
+        // evaluated in binary32 (they enter binary32 products only).
+        for (int l = tid; l < n; l += NTH) sm.vf[l] = (float)sm.vb[l];  // b, once (vf is free until w-bar)
+        point_sync<NW>();
         for_cols<WIDE, NW>(tid, n, [&](int c) {
-            const double lam = sm.dS[c];
-            sm.vu[c] = (float)sqrt(lam);
-            sm.vinv[c] = (float)(1.0 / lam);
+            const float lam = (float)sm.dS[c];
+            sm.vu[c] = sqrtf(lam);
+            sm.vinv[c] = 1.0f / lam;
             float t = 0.0f;
-            for (int l = 0; l < n; ++l) t += Y32[l * ld + c] * (float)sm.vb[l];
+            for (int l = 0; l < n; ++l) t += Y32[l * ld + c] * sm.vf[l];
             sm.t1f[c] = t;  // Y^T b
         });
         point_sync<NW>();
@@ -2647,7 +2709,7 @@ __global__ void __launch_bounds__(32 * NW) analyze_mixed_kernel(float* __restric
                 float v;
                 const float sj = (float)sm.vu[i];
                 if (i == c) {
-                    v = (float)(1.0 / sm.vu[c]);
+                    v = 1.0f / si;
                 } else {
                     v = -Soff[i * ld + c] / (si * sj * (si + sj));
                 }
@@ -2909,8 +2971,8 @@ cudaError_t launch_analyze(void* f, int fp32, int nx, int ny, int k, const ObsPa
         for (long long c0 = 0; c0 < cells; c0 += chunk, ++c) {
             const int nc = (int)((cells - c0) < chunk ? (cells - c0) : chunk);
             const int b = c & 1;
-            const MixScratch sc =
-                mix_scratch_at((unsigned char*)scratch + b * buf_bytes, chunk, cap, nm, kg, gsz);
+            MixScratch sc = mix_scratch_at((unsigned char*)scratch + b * buf_bytes, chunk, cap, nm, kg, gsz);
+            if (prod == PROD_DF32) sc = mix_scratch_df2(sc, chunk, kg);
             if (c >= 2 && (e = cudaStreamWaitEvent(aux->s2, aux->ref_done[b], 0)) != cudaSuccess)
                 return e;
             if (kg && (e = launch_gram(prod, nx, ny, k, o, d_cut, (k - 1) / beta, (int)c0, nc, sc, flags,

@@ -63,6 +63,7 @@ struct RunArgs {
     ObsParams o;
     const float2* G2;   // [nobs][nobs] G = dY dY^T as binary32 (hi, lo)
     double d_cut, beta;
+    long long lim2;     // support_lim2(d_cut)
     // Launch constants in binary32, rounded from FP64 on the host: a =
     // (k-1)/beta, sqrt(a), sqrt(beta), sqrt(k-1).
     float a_f, sqrt_a_f, sqrt_beta_f, sqrt_k1_f;
@@ -135,9 +136,8 @@ __device__ __forceinline__ double obs_weight(const RunArgs& ra, int j, int q, in
     const ObsParams& o = ra.o;
     const int dx = min_image(o.ix[j] - x, ra.nx);
     const int dy = min_image(o.iy[j] - y, ra.ny);
+    if (dist2(dx, dy) > ra.lim2) return 0.0;
     const double d2 = (double)dx * dx + (double)dy * dy;
-    const double lim2 = (2.0 * ra.d_cut + 1.0) * (2.0 * ra.d_cut + 1.0);
-    if (d2 > lim2) return 0.0;
     const double dist = sqrt(d2) / ra.d_cut;
     if (!(dist < 2.0)) return 0.0;
     const double g = gaspari_cohn(dist);
@@ -154,7 +154,7 @@ __device__ __forceinline__ double obs_weight(const RunArgs& ra, int j, int q, in
 // are incomplete.
 __device__ int run_union(const RunArgs& ra, int* pts, int* gi, int y, int xa, int xb, int cap, int lane) {
     const ObsParams& o = ra.o;
-    const double lim2 = (2.0 * ra.d_cut + 1.0) * (2.0 * ra.d_cut + 1.0);
+    const long long lim2 = ra.lim2;
     const int maxpts = cap / o.nvar;
     int count = 0;
     for (int j0 = 0; j0 < o.npts; j0 += 32) {
@@ -167,8 +167,7 @@ __device__ int run_union(const RunArgs& ra, int* pts, int* gi, int y, int xa, in
                 const int dx = abs(min_image(o.ix[j] - x, ra.nx));
                 dxm = dx < dxm ? dx : dxm;
             }
-            const double d2 = (double)dxm * dxm + (double)dy * dy;
-            if (d2 <= lim2) in = sqrt(d2) / ra.d_cut < 2.0;
+            if (dist2(dxm, dy) <= lim2) in = sqrt((double)dxm * dxm + (double)dy * dy) / ra.d_cut < 2.0;
         }
         const unsigned bal = __ballot_sync(kFull, in);
         if (in) {
@@ -1317,6 +1316,7 @@ cudaError_t run_setup(float* f, double* f64, int nx, int ny, int k, const ObsPar
     ra.G2 = G2;
     ra.d_cut = d_cut;
     ra.beta = beta;
+    ra.lim2 = support_lim2(d_cut);
     ra.a_f = (float)((k - 1) / beta);
     ra.sqrt_a_f = (float)std::sqrt((k - 1) / beta);
     ra.sqrt_beta_f = (float)std::sqrt(beta);
