@@ -21,10 +21,11 @@
 //      (FP64 support test, the same as the other analysis kernels), A from a
 //      binary32 copy of the run's block of G = dY dY^T, the warm transform
 //      U^T A U, the cyclic Jacobi, a first-order re-orthonormalisation of
-//      the basis, U (I - E/2) with E = U^T U - I in binary32; the basis and
-//      the Jacobi's eigenvalue estimates go to scratch.
-//  (F) run_refine_kernel, one warp per point: A again, now in
-//      double-binary32, and the refinement, first order in the basis'
+//      the basis, U (I - E/2) with E = U^T U - I in binary32; the basis,
+//      the Jacobi's eigenvalue estimates and the FP64 weights go to
+//      scratch.
+//  (F) run_refine_kernel, one warp per point: A again from J's weights, now
+//      in double-binary32, and the refinement, first order in the basis'
 //      non-orthogonality E = Y^T Y - I and in the off-diagonal of
 //      S = Y^T A Y:
 //        R = A Y - Y diag(l)   (double-binary32; l: the eigenvalue estimates,
@@ -34,11 +35,14 @@
 //      so that S = (I + E) diag(l) + T exactly, and S' = M^{-1/2} S M^{-1/2}
 //      (M = I + E; Y M^{-1/2} is orthonormal) is, to first order in E,
 //        S'_ic = T_ic + E_ic (l_c - l_i) / 2   (i != c),
-//        S'_cc = l_c + T_cc - E_cc T_cc - E_cc^2 l_c   (FP64);
+//        S'_cc = l_c + T_cc - E_cc T_cc - E_cc^2 l_c;
 //      then the first-order (Daleckii-Krein) matrix functions
 //      h(S') = (aI+S')^{-1} and g(S') = ((aI+S')^{-1/2} - a^{-1/2} I) S'^{-1}
-//      with the same first-order basis factor, the binary32 transform and
-//      the in-place update of the nine f.
+//      with the same first-order basis factor (their scalars in binary32,
+//      FP64 in the probe variant), the binary32 transform and the in-place
+//      update of the nine f.
+// A batch of experiments runs kernel J over all runs of a size class in one
+// launch, then kernel F per experiment.
 // With w-bar = Yh^T (aI+A)^{-1} d-hat and C^{-1/2} = a^{-1/2} I + Yh^T g(A) Yh
 // (C = aI + Yh^T Yh, a = (k-1)/beta) the update is
 //   x^a_m = xbar + Z v + sqrt(beta) dx_m + sqrt(k-1) Z g(A) yh_m,
