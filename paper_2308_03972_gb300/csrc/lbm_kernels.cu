@@ -312,9 +312,9 @@ __global__ void moments_kernel(const T* __restrict__ f, int nx, int ny, int k,
 }
 
 // Ensemble-mean velocity: one warp per cell, lanes over members. A member's
-// moments are taken in the precision of the stored state: FP64, or binary32
-// for the binary32 shifted state g = f - w (sum g, sum c g; rho = 1 + sum g),
-// whose own storage error (~1e-9 absolute in u) they match; the member mean
+// moments are taken in the precision of the stored state (FP64 here; the
+// binary32 shifted state g = f - w has its own kernel below, whose moments
+// match that state's storage error, ~1e-9 absolute in u); the member mean
 // is summed in FP64.
 template <typename T, bool SHIFT>
 __global__ void mean_velocity_kernel(const T* __restrict__ f, int nx, int ny, int k,
@@ -354,6 +354,82 @@ __global__ void mean_velocity_kernel(const T* __restrict__ f, int nx, int ny, in
         if (vm) vm[cell] = sv / k;
     }
     if (bad) atomicOr(flags, FLAG_DIVERGED);
+}
+
+// Knuth's TwoSum in binary32: s + e = a + b exactly.
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float z = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
+}
+
+// (h, l) += (bh, bl) in double-binary32: the high parts by TwoSum, the low
+// parts and the error in binary32.
+__device__ __forceinline__ void df_add(float& h, float& l, float bh, float bl) {
+    float s, e;
+    two_sum_f(h, bh, s, e);
+    h = s;
+    l = __fadd_rn(l, __fadd_rn(bl, e));
+}
+
+// Ensemble-mean velocity of a binary32 state (g = f - w): each member's
+// moments in binary32 (sum g, sum c g; rho = 1 + sum g), as the LBM step
+// takes them, and the divergence test in binary32; their sum
+// in double-binary32 (TwoSum per member and per step of the warp's
+// butterfly), about as exact as an FP64 sum of the binary32 velocities,
+// without FP64 work per member (GB300's FP64 rate is 1/64 of binary32).
+// A block of 8 warps takes 8 cells; its first 16 threads form the 8 means
+// of u and v in FP64.
+__global__ void mean_velocity_f32_kernel(const float* __restrict__ f, int nx, int ny, int k,
+                                         double* __restrict__ um, double* __restrict__ vm,
+                                         int* __restrict__ flags) {
+    __shared__ float2 part[2][8];  // (high, low) sums of u and v per cell of the block
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long ncell = (long long)nx * ny;
+    const long long cell0 = (long long)blockIdx.x * 8;
+    const long long cell = cell0 + w;
+    const size_t n = (size_t)ncell * k;
+    float uh = 0.0f, ul = 0.0f, vh = 0.0f, vl = 0.0f;
+    bool bad = false;
+    if (cell < ncell) {
+        for (int m = lane; m < k; m += 32) {
+            const size_t i = (size_t)cell * k + m;
+            float r = 0.0f, jx = 0.0f, jy = 0.0f;
+#pragma unroll
+            for (int a = 0; a < 9; ++a) {
+                const float g = f[a * n + i];
+                r += g;
+                jx += float(d2q9_cx(a)) * g;
+                jy += float(d2q9_cy(a)) * g;
+            }
+            r += 1.0f;
+            const float ux = jx / r, uy = jy / r;
+            df_add(uh, ul, ux, 0.0f);
+            df_add(vh, vl, uy, 0.0f);
+            bad |= !(ux * ux + uy * uy <= float(kUMax2)) || !(r > 0.0f);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ouh = __shfl_xor_sync(0xffffffffu, uh, o), oul = __shfl_xor_sync(0xffffffffu, ul, o);
+        const float ovh = __shfl_xor_sync(0xffffffffu, vh, o), ovl = __shfl_xor_sync(0xffffffffu, vl, o);
+        df_add(uh, ul, ouh, oul);
+        df_add(vh, vl, ovh, ovl);
+    }
+    if (lane == 0) {
+        part[0][w] = make_float2(uh, ul);
+        part[1][w] = make_float2(vh, vl);
+    }
+    if (bad) atomicOr(flags, FLAG_DIVERGED);
+    __syncthreads();
+    if (threadIdx.x < 16) {
+        const int q = threadIdx.x & 7, comp = threadIdx.x >> 3;
+        double* out = comp ? vm : um;
+        if (cell0 + q < ncell && out) {
+            const float2 p = part[comp][q];
+            out[cell0 + q] = ((double)p.x + (double)p.y) / k;
+        }
+    }
 }
 
 template <typename T, bool SHIFT>
@@ -482,8 +558,8 @@ cudaError_t launch_mean_velocity(const void* f, int fp32, int nx, int ny, int k,
     const size_t threads = (size_t)nx * ny * 32;
     if (threads == 0) return cudaSuccess;
     if (fp32)
-        mean_velocity_kernel<float, true><<<blocks_for(threads, 256), 256, 0, s>>>(
-            (const float*)f, nx, ny, k, u, v, flags);
+        mean_velocity_f32_kernel<<<blocks_for(threads, 256), 256, 0, s>>>((const float*)f, nx, ny, k, u, v,
+                                                                          flags);
     else
         mean_velocity_kernel<double, false><<<blocks_for(threads, 256), 256, 0, s>>>(
             (const double*)f, nx, ny, k, u, v, flags);
