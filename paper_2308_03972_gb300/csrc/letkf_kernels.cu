@@ -941,7 +941,8 @@ __global__ void __launch_bounds__(32) run_fp64_kernel(double* __restrict__ f, in
 //      memory, so many warps per SM hide its latency); above n = 32 the
 //      block Jacobi in shared memory. The basis X goes to the chunk's
 //      scratch.
-//  (B) analyze_mixed_kernel: in FP64, form the Rayleigh-Ritz matrix
+//  (B) analyze_mixed_kernel: to FP64-class accuracy (double-binary32
+//      products on the binary32 units), form the Rayleigh-Ritz matrix
 //      S = X^T A X and the non-orthogonality E = X^T X - I of the binary32
 //      basis, correct S to first order in E (refine_rr), and evaluate
 //      f(A) = X (f(S') - E o (f_i + f_j)/2) X^T with f(S') to first order in
