@@ -402,6 +402,16 @@ int lbm_batch_autotune(lbm_batch *b, int *threads, int *blocks);
 int lbm_batch_autotune_analysis(lbm_batch *b, const double *d_cut, const double *beta, int *run_len,
                                 int *batched);
 
+/* Set the launch form of each experiment's run analysis in lbm_batch_cycle
+ * (the choice lbm_batch_autotune_analysis makes): batched[i] = 1 puts
+ * experiment i's run analysis into the size class's batched launch of
+ * kernel J, 0 launches it on its own (as lbm_analyze does). Results are
+ * the same in both forms; experiments off the run path ignore it. One value
+ * per context of the batch (host array, read before the call returns);
+ * LBM_EINVAL for a value other than 0 or 1. A captured cycle is captured
+ * again. */
+int lbm_batch_set_analysis_form(lbm_batch *b, const int *batched);
+
 /* One DA cycle of every experiment i: forecast nsteps (one persistent
  * launch for all), observe (u, v) at npts[i] points (ix[i], iy[i]) with
  * values yo_u[i], yo_v[i] and errors sigma[2i], sigma[2i+1], and the LETKF

@@ -74,6 +74,7 @@ SIGNATURES = {
     "lbm_batch_cycle": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _P, _P, _I]),
     "lbm_batch_sync": (_I, [_P]),
     "lbm_batch_set_barrier": (_I, [_P, ctypes.c_longlong, _I]),
+    "lbm_batch_set_analysis_form": (_I, [_P, _P]),
     "lbm_batch_last_error": (ctypes.c_char_p, [_P]),
     "lbm_batch_destroy": (None, [_P]),
     "letkf_analyze_noalloc": (_I, [_P, _I, _I, _I, _I, _P, _P, _P, _P, _D, _D, _D, _D, _P]),
@@ -564,6 +565,14 @@ class Batch:
         _bcheck(self.b, load().lbm_batch_cycle(self.b, int(nsteps), p(npts), arrs(0, np.int32), arrs(1, np.int32),
                                                arrs(2, np.float64), arrs(3, np.float64), p(sig), p(dc), p(bt),
                                                1 if use_graph else 0))
+
+    def set_analysis_form(self, batched):
+        """Launch form of each experiment's run analysis: 1 batched, 0 on its own."""
+        form = np.ascontiguousarray(batched, dtype=np.int32)
+        if form.shape != (len(self.ens),):
+            raise ValueError("one launch form per experiment")
+        _bcheck(self.b, load().lbm_batch_set_analysis_form(self.b, form.ctypes.data_as(_P)))
+        self.run_batched = form.tolist()
 
     def set_barrier(self, spin_limit, absent=0):
         _bcheck(self.b, load().lbm_batch_set_barrier(self.b, int(spin_limit), int(absent)))

@@ -1562,6 +1562,27 @@ int lbm_batch_set_barrier(lbm_batch* b, long long spin_limit, int absent) {
     return LBM_OK;
 }
 
+int lbm_batch_set_analysis_form(lbm_batch* b, const int* batched) {
+    if (!b) return bfail(nullptr, LBM_EINVAL, "batch is NULL");
+    if (!batched) return bfail(b, LBM_EINVAL, "batched is NULL");
+    const int n = (int)b->ctx.size();
+    for (int i = 0; i < n; ++i)
+        if (batched[i] != 0 && batched[i] != 1) return bfail(b, LBM_EINVAL, "batched[%d] must be 0 or 1", i);
+    for (int i = 0; i < n; ++i) b->ctx[i]->run_batched = batched[i];
+    // A captured cycle holds the old launches: capture again on the next cycle.
+    if (b->exec) {
+        BK(b, cudaStreamSynchronize(b->stream), "synchronising");
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    if (b->graph) {
+        cudaGraphDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    b->graph_steps = -1;
+    return LBM_OK;
+}
+
 int lbm_batch_sync(lbm_batch* b) {
     if (!b) return bfail(nullptr, LBM_EINVAL, "batch is NULL");
     BK(b, cudaStreamSynchronize(b->stream), "synchronising");

@@ -327,3 +327,65 @@ def test_analysis_autotuner_needs_observations(gpu):
             b.autotune_analysis([4.0], [1.05])
     for e in ens:
         e.close()
+
+
+# Experiments on the run path (every grid point with p < k, unions of at
+# most 32 scalars): the analysis launch form of the batch applies to them.
+RUN_EXPS = [(64, 64, 64, 4, 4, 12.0), (48, 40, 48, 4, 4, 8.0)]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batch_analysis_forms_agree(gpu, prec):
+    """lbm_batch_set_analysis_form: the run analyses in the batched launch
+    of kernel J and launched one experiment at a time give the same states,
+    bit for bit, over uncaptured and graph-captured cycles."""
+    p = gpu.LBM_FP64 if prec == "fp64" else gpu.LBM_MIXED
+    dcs = [e[5] for e in RUN_EXPS]
+    betas = [1.05] * len(RUN_EXPS)
+
+    def build():
+        out = []
+        for i, (nx, ny, k, _, _, _) in enumerate(RUN_EXPS):
+            u, v = inputs.ensemble_velocity(nx, ny, k, 60 + i, U_RMS, 0.2)
+            force = inputs.forcing_field(nx, ny, seed=70 + i, amp=3.5e-6)
+            e = gpu.Ensemble(nx, ny, k, TAU0, CS, MU, p, force=force)
+            e.set_equilibrium(None, u, v)
+            out.append(e)
+        return out
+
+    def obs(c):
+        out = []
+        for i, (nx, ny, _, nox, noy, _) in enumerate(RUN_EXPS):
+            ix, iy = inputs.uniform_obs_points(nx, ny, nox, noy)
+            tu, tv = inputs.random_velocity(nx, ny, 300 + i, U_RMS)
+            nu, nv = inputs.obs_noise(6, c, len(ix))
+            out.append((ix, iy, tu[iy, ix] + SIGMA * nu, tv[iy, ix] + SIGMA * nv, SIGMA, SIGMA))
+        return out
+
+    results = []
+    for form in (1, 0):
+        ens = build()
+        with gpu.Batch(ens) as b:
+            b.set_analysis_form([form] * len(ens))
+            assert b.run_batched == [form] * len(ens)
+            for c in (1, 2, 3):  # uncaptured, then captured and replayed
+                b.cycle(4, obs(c), dcs, betas, use_graph=c > 1)
+            b.sync()
+            results.append([e.get_f() for e in ens])
+        for e in ens:
+            e.close()
+    for a, b_ in zip(*results):
+        assert np.array_equal(a, b_)
+
+
+def test_batch_analysis_form_arguments(gpu):
+    ens = [gpu.Ensemble(16, 16, 8, TAU0, CS, MU, gpu.LBM_MIXED) for _ in range(2)]
+    with gpu.Batch(ens) as b:
+        with pytest.raises(gpu.LbmError) as err:
+            b.set_analysis_form([2, 0])
+        assert err.value.code == gpu.LBM_EINVAL
+        with pytest.raises(ValueError):
+            b.set_analysis_form([1])
+        b.set_analysis_form([0, 1])
+    for e in ens:
+        e.close()
