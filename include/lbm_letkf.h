@@ -419,8 +419,9 @@ int lbm_batch_set_analysis_form(lbm_batch *b, const int *batched);
  * path share launches: per size class one launch of kernel J over all
  * their runs, then one launch of kernel F per experiment over all its grid
  * points (the analysis scratch of each is then sized for all its runs at
- * once); the others, and run-path classes the analysis autotuner found
- * faster so, are analysed one by one. With use_graph, once a cycle has run
+ * once); the others, and run-path experiments whose launch form is set to
+ * 0 (lbm_batch_autotune_analysis, lbm_batch_set_analysis_form), are
+ * analysed one by one. With use_graph, once a cycle has run
  * uncaptured with the same positions, nsteps, d_cut and beta, the next call
  * captures the whole cycle of all experiments in a CUDA graph and later
  * calls replay it, staging only the new observed values through pinned
