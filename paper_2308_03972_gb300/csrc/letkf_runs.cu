@@ -791,6 +791,8 @@ __device__ __forceinline__ void run_refine_body(const RunArgs& ra, const ProbeAr
     // groups of RG: E_ic = sum_j Y_ji Y_jc, so rows i..i+RG-1 read entries
     // i..i+RG-1 of row j of Y.
     float ecc = 0.0f, tcc = 0.0f;
+    // Unrolled: in the last group the sums of rows past NS are dead and go.
+#pragma unroll
     for (int i0 = 0; i0 < NS; i0 += RG) {
         f2x ES[NQ], EC[NQ], TQ[NQ];
 #pragma unroll
